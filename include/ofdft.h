@@ -1,0 +1,229 @@
+/*
+ * ofdft.h - C ABI of the GB300 (sm_103a) library for the Augmented Lagrangian
+ * formulation of orbital-free DFT (Suryanarayana & Phanish, arXiv:1405.6456).
+ *
+ * The library finds the electronic ground state u* = sqrt(rho*) of an isolated
+ * cluster of M nuclei (Sec. 2, Eq. GroundStateElectronic) on a uniform
+ * finite-difference grid with zero Dirichlet values for u and phi (Sec. 4), using
+ * the Augmented Lagrangian outer loop of Algorithm 1 around Polak-Ribiere nonlinear
+ * CG (Sec. 4), one conjugate-gradient Poisson solve per gradient evaluation
+ * (Sec. 4, Eq. Poisson:Discretized), and returns the energy and the forces of
+ * Eq. Force:Nuclei.
+ *
+ * Conventions shared by every call:
+ *   - atomic units (bohr, hartree); R is M x 3 row-major, Z has M entries;
+ *   - a grid has n[0] x n[1] x n[2] nodes of spacing h; node (i,j,k) sits at
+ *     origin + (i+1/2, j+1/2, k+1/2) h; field arrays are x-fastest:
+ *     idx = i + n[0]*(j + n[1]*k), no padding;
+ *   - fd_order = 2n, n = 1..6 (Eq. FD:Laplacian, radius-n star stencil);
+ *   - `prec` (OFDFT_PREC_FP64 or OFDFT_PREC_MIXED) fixes the element type of every
+ *     device field buffer a call takes: double for FP64, float for MIXED.  In
+ *     MIXED mode stencils, CG vectors and the functional run in FP32 while every
+ *     dot product, the constraint, the multipliers, energies and forces are
+ *     accumulated in FP64, and Poisson solves end with an FP64 residual
+ *     correction;
+ *   - device pointers are CUDA device addresses on the context's device, owned
+ *     by the caller, at least 256-byte aligned for best speed (any element
+ *     alignment is accepted); host pointers are ordinary host memory owned by
+ *     the caller;
+ *   - calls that return host scalars synchronise the context's stream; others
+ *     are asynchronous on it;
+ *   - every call returns an ofdft_status; on failure ofdft_last_error(ctx)
+ *     describes it.  No C++ exception crosses this interface.  A context is not
+ *     safe for concurrent use from several host threads.
+ */
+#ifndef OFDFT_H
+#define OFDFT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  OFDFT_OK = 0,
+  OFDFT_EINVAL = 1,     /* bad argument (sizes, order, null pointer, ...) */
+  OFDFT_ENOMEM = 2,     /* device workspace does not fit */
+  OFDFT_ENOTCONV = 3,   /* an iteration hit its cap before its tolerance */
+  OFDFT_ENONFINITE = 4, /* NaN or Inf in an input or an intermediate scalar */
+  OFDFT_ETIMEOUT = 5,   /* a bounded device wait ran out */
+  OFDFT_ECUDA = 6       /* a CUDA runtime error */
+} ofdft_status;
+
+enum { OFDFT_PREC_FP64 = 0, OFDFT_PREC_MIXED = 1 };
+
+/* energy terms of Eq. F (Sec. 2) */
+enum { OFDFT_TERM_TF = 1, OFDFT_TERM_VW = 2, OFDFT_TERM_XC = 4, OFDFT_TERM_ES = 8,
+       OFDFT_TERM_ALL = 15 };
+
+/* constraint treatment: Algorithm 1, or the penalty method (eta_q = 0, Sec. 5.3.2) */
+enum { OFDFT_METHOD_AL = 0, OFDFT_METHOD_PENALTY = 1 };
+
+/* force expression: Eq. Force:Nuclei with the FD gradient of Sec. 4 (paper), or
+ * the exact derivative of the discrete energy at fixed grid (exact). */
+enum { OFDFT_FORCE_PAPER = 0, OFDFT_FORCE_EXACT = 1 };
+
+typedef struct ofdft_ctx ofdft_ctx;
+
+typedef struct {
+  int n[3];
+  double h;
+  double origin[3];
+} ofdft_grid;
+
+typedef struct {
+  int fd_order;       /* 2n: 2, 4, ..., 12 (Sec. 4) */
+  int terms;          /* OFDFT_TERM_* mask */
+  int method;         /* OFDFT_METHOD_* */
+  int precision;      /* OFDFT_PREC_* */
+  double lambda;      /* vW weight, 0.2 (Sec. 5) */
+  double eta0, mu0, kappa; /* Algorithm 1 inputs: -0.2, 1, 0.1 (Sec. 5.3.1) */
+  double sigma, rc;   /* Gaussian nuclei V_J = -Z erf(r/sigma)/r, b_J cut at r_c */
+  double guess_sigma, guess_cut; /* Gaussian atomic densities of the starting guess */
+  double tol_E;       /* Algorithm 1 stops when |E_{q+1} - E_q| < tol_E * M (Ha/atom) */
+  double tol_inner;   /* NLCG stops when h^3 r.s < tol_inner (Ha, whole system) */
+  double tol_poisson; /* CG stops when ||r||_2 <= tol_poisson ||4 pi rho||_2 */
+  int max_outer, max_nlcg, max_cg, max_secant;
+  double sigma0;      /* secant trial step along the preconditioned direction */
+  double eps_secant;  /* secant loop stops when alpha^2 h^3 d.d <= eps_secant^2 N */
+  int restart_every;  /* Polak-Ribiere restart period */
+  int force_variant;  /* OFDFT_FORCE_* */
+  int ezz_correction; /* 1: add the Gaussian-overlap repulsion correction (App. A) */
+  double vacuum;      /* box rule of ofdft_grid_for_atoms: vacuum on every side */
+  int round_to;       /* box rule: node counts rounded up to a multiple of this */
+  int refine_every;   /* MIXED: FP64 residual correction every this many FP32 CG steps */
+} ofdft_params;
+
+typedef struct {
+  int iterations;      /* CG iterations (stencil applications inside the CG) */
+  double rel_residual; /* final ||r|| / ||4 pi rho|| */
+} ofdft_cg_stats;
+
+typedef struct {
+  double L;       /* augmented Lagrangian, Eq. AugLag */
+  double E;       /* discrete energy (Eq. F at the computed phi, Sec. 4 quadrature) */
+  double E_tf, E_vw, E_xc, E_es, E_self, E_zz_corr;
+  double C;       /* C_h(u) = h^3 sum u^2 - N (Sec. 4) */
+  double gd;      /* h^3 G.d when d was given */
+  double gs_old;  /* h^3 G.s_old when s_old was given */
+  double gnorm2;  /* h^3 G.G */
+  double rs;      /* h^3 r.s, r = -G, s = r / Jacobi diagonal */
+  ofdft_cg_stats poisson;
+} ofdft_energy;
+
+typedef struct {
+  double E, eta, C;   /* E*, eta* (Algorithm 1 output), C_h(u*) */
+  ofdft_energy parts; /* terms at u* */
+  int outer_iters, nlcg_iters, grad_evals, cg_iters;
+  long long stencil_apps; /* "matrix-vector products" counted as in Sec. 5.3 */
+  int converged;
+  ofdft_grid grid;    /* grid the solve used */
+} ofdft_solve_stats;
+
+/* Fills p with the paper's defaults (Sec. 5) and this library's readings of the
+ * knobs the paper leaves open (NLCG constants, Gaussian nuclei, box rule). */
+void ofdft_default_params(ofdft_params* p);
+
+/* Creates a context on CUDA device `device` whose work goes to `cuda_stream`
+ * (a cudaStream_t; NULL means the legacy default stream).  The context owns its
+ * device workspaces; they grow on demand and are freed by ofdft_destroy. */
+int ofdft_create(ofdft_ctx** ctx, int device, void* cuda_stream);
+int ofdft_destroy(ofdft_ctx* ctx);
+/* Message describing the last failure on ctx (never NULL; "" after success). */
+const char* ofdft_last_error(const ofdft_ctx* ctx);
+
+/* Box rule (host only, Sec. 4): bounding box of R grown by `vacuum` on each side,
+ * n_d = ceil(L_d/h) rounded up to a multiple of round_to, nodes cell-centred with
+ * the spare length split evenly.  Output grid g. */
+int ofdft_grid_for_atoms(const double* R, int M, double h, double vacuum, int round_to,
+                         ofdft_grid* g);
+
+/* S2 - out = L_h f, the radius-n star stencil of Sec. 4 Eq. FD:Laplacian with
+ * weights w_0 = -(1/h^2) sum 1/q^2 (centre counted six times) and
+ * w_p = 2(-1)^{p+1}(n!)^2/(h^2 p^2 (n-p)!(n+p)!), zero at every index outside the
+ * grid.  f and out: device arrays of n[0]n[1]n[2] elements of the `prec` type;
+ * they must not overlap. */
+int ofdft_stencil(ofdft_ctx* ctx, const ofdft_grid* g, int fd_order, int prec, const void* f,
+                  void* out);
+
+/* S1 - nuclear pseudocharge b = sum_J b_J with b_J = -(1/4 pi) L_h V_J on nodes
+ * within r_c of R_J (Sec. 4, Eq. b:Pseudopotential), V_J = -Z_J erf(r/sigma)/r
+ * evaluated analytically at every stencil neighbour, and the self energy
+ * E_self = (1/2) sum_J h^3 sum b_J V_J (Eq. ElectroststaticReformulation).
+ * R (M x 3) and Z (M) are host arrays; b is a device array of the `prec` type
+ * (overwritten); *E_self (host) is computed in FP64. */
+int ofdft_pseudocharge(ofdft_ctx* ctx, const ofdft_grid* g, int fd_order, const double* R,
+                       const double* Z, int M, double sigma, double rc, int prec, void* b,
+                       double* E_self);
+
+/* S1 - starting guess of Sec. 4: sqrt of the superposed Gaussian atomic densities
+ * Z_J (2 pi s^2)^{-3/2} exp(-r^2/(2 s^2)) (r < cut), scaled so h^3 sum u^2 = N.
+ * u: device array of the `prec` type (overwritten). */
+int ofdft_initial_guess(ofdft_ctx* ctx, const ofdft_grid* g, const double* R, const double* Z,
+                        int M, double guess_sigma, double guess_cut, double N, int prec,
+                        void* u);
+
+/* S3 - Poisson problem of Sec. 4 (Eq. Poisson:Discretized):
+ * -(1/4 pi) L_h phi = rho with zero Dirichlet values, written as the SPD system
+ * (-L_h) phi = 4 pi rho and solved by conjugate gradients (the paper uses GMRES;
+ * both reach the same solution of this SPD system) from the incoming phi (the
+ * previous solution, Sec. 4).  rho is the device array `rho` if it is not NULL,
+ * otherwise u^2 + b from the device arrays u and b.  Stops when
+ * ||r||_2 <= tol ||4 pi rho||_2 or after max_it iterations (then OFDFT_ENOTCONV,
+ * phi holds the last iterate).  phi: device array, in: guess, out: solution. */
+int ofdft_poisson(ofdft_ctx* ctx, const ofdft_grid* g, int fd_order, int prec, const void* rho,
+                  const void* u, const void* b, void* phi, double tol, int max_it,
+                  ofdft_cg_stats* st);
+
+/* S3+S4+S5+S6 - one evaluation of the augmented Lagrangian (Eq. AugLag) and its
+ * gradient at u (the unit of work of the method):
+ *   if solve_poisson, phi is first updated by ofdft_poisson from its incoming
+ *   value (tolerance p->tol_poisson); then at that phi
+ *   E = h^3 sum [C_F u^{10/3} + eps_xc(u) u^2] - (lambda/2) h^3 u.L_h u
+ *       + h^3 sum [phi L_h phi/(8 pi) + (u^2 + b) phi] - E_self   (Eq. F)
+ *   C = h^3 sum u^2 - N,  L = E - eta C + C^2/(2 mu)
+ *   G = -lambda L_h u + 2 (V_K + V_xc + phi) u + 2 (-eta + C/mu) u
+ * G is (1/h^3) dL/du, twice the discrete Euler-Lagrange expression of Sec. 4
+ * (Eq. EulerLagrangeDiscretized).  Optional device outputs: grad (G) and s (the
+ * Jacobi-preconditioned residual -G/diag); optional device inputs d and s_old
+ * give out->gd = h^3 G.d and out->gs_old = h^3 G.s_old.  mu = +inf drops the
+ * penalty term.  u, b, phi, grad, s, d, s_old: device arrays of the `prec` type
+ * (p->precision).  Synchronises; results in *out. */
+int ofdft_energy_grad(ofdft_ctx* ctx, const ofdft_grid* g, const ofdft_params* p, const void* u,
+                      const void* b, void* phi, double E_self, double eta, double mu, double N,
+                      int solve_poisson, void* grad, void* s, const void* d, const void* s_old,
+                      ofdft_energy* out);
+
+/* S9 - forces on the nuclei (Eq. Force:Nuclei) at phi:
+ *   OFDFT_FORCE_PAPER: f_J = h^3 sum_{|x-R_J|<r_c} grad_h b_J (phi - V_J), grad_h the
+ *                      FD gradient of Sec. 4 with weights w~_p;
+ *   OFDFT_FORCE_EXACT: f_J = -h^3 sum (db_J/dR_J)(phi - V_J) with
+ *                      db_J/dR_J = (1/4 pi) L_h grad V_J (exact derivative of the
+ *                      discrete energy at fixed grid).
+ * phi: device array of the `prec` type; F: host array M x 3 (output, FP64). */
+int ofdft_forces(ofdft_ctx* ctx, const ofdft_grid* g, int fd_order, const double* R,
+                 const double* Z, int M, double sigma, double rc, int variant, int prec,
+                 const void* phi, double* F);
+
+/* S1..S9 - ground state at fixed nuclei (Eq. GroundStateElectronic) by
+ * Algorithm 1 (or the penalty method) around PR nonlinear CG with a secant line
+ * search, the Jacobi preconditioner and u <- |u| (Sec. 4), then the forces.
+ *   grid: the grid to use, or NULL for ofdft_grid_for_atoms(R, M, h, p->vacuum,
+ *         p->round_to) (the grid used is returned in st->grid);
+ *   u_out, phi_out: optional device arrays (p->precision type) receiving u*, phi*
+ *         (they must hold the grid's node count; query it with
+ *         ofdft_grid_for_atoms first when grid is NULL);
+ *   energy: host scalar E* (Ha); forces: host M x 3 array or NULL; st: stats.
+ * Returns OFDFT_ENOTCONV when Algorithm 1 hits p->max_outer (results are still
+ * written), OFDFT_ENOMEM when the workspace does not fit on the device. */
+int ofdft_solve(ofdft_ctx* ctx, const ofdft_grid* grid, const double* R, const double* Z, int M,
+                double h, const ofdft_params* p, void* u_out, void* phi_out, double* energy,
+                double* forces, ofdft_solve_stats* st);
+
+/* Device bytes a solve of this grid needs in the context workspace (for
+ * admission control by callers that pack several solves on one device). */
+long long ofdft_workspace_bytes(const ofdft_grid* g, int fd_order, int prec);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OFDFT_H */
