@@ -80,7 +80,7 @@ typedef struct {
   double sigma, rc;   /* Gaussian nuclei V_J = -Z erf(r/sigma)/r, b_J cut at r_c */
   double guess_sigma, guess_cut; /* Gaussian atomic densities of the starting guess */
   double tol_E;       /* Algorithm 1 stops when |E_{q+1} - E_q| < tol_E * M (Ha/atom) */
-  double tol_inner;   /* NLCG stops when h^3 r.s < tol_inner (Ha, whole system) */
+  double tol_inner;   /* NLCG stops when h^3 r.s < tol_inner * M (Ha/atom) */
   double tol_poisson; /* CG stops when ||r||_2 <= tol_poisson ||4 pi rho||_2 */
   int max_outer, max_nlcg, max_cg, max_secant;
   double sigma0;      /* secant trial step along the preconditioned direction */
@@ -218,6 +218,34 @@ int ofdft_forces(ofdft_ctx* ctx, const ofdft_grid* g, int fd_order, const double
 int ofdft_solve(ofdft_ctx* ctx, const ofdft_grid* grid, const double* R, const double* Z, int M,
                 double h, const ofdft_params* p, void* u_out, void* phi_out, double* energy,
                 double* forces, ofdft_solve_stats* st);
+
+/* Kernel kinds counted by the context (trace counters). */
+enum {
+  OFDFT_K_STENCIL = 0,          /* S2 plain stencil */
+  OFDFT_K_CG_DIR_STENCIL = 1,   /* S3 CG: p = r + beta p, Ap = -L_h p, p.Ap */
+  OFDFT_K_CG_UPDATE = 2,        /* S3 CG: x += alpha p, r -= alpha Ap, r.r */
+  OFDFT_K_RESIDUAL = 3,         /* S3/S5/S10 residual 4 pi rho + L_h phi (FP64 in MIXED) */
+  OFDFT_K_FUNCTIONAL = 4,       /* S4 fused energy + gradient */
+  OFDFT_K_VECTOR = 5,           /* S6/S7 dots, NLCG updates, conversions */
+  OFDFT_K_ATOMS = 6,            /* S1/S9 pseudocharge, guess, forces */
+  OFDFT_K_COUNT = 8
+};
+
+typedef struct {
+  long long launches;                      /* kernels launched by this context */
+  long long kind_launches[OFDFT_K_COUNT];  /* per OFDFT_K_* kind */
+  long long timed_launches[OFDFT_K_COUNT]; /* launches bracketed by CUDA events */
+  double timed_ms[OFDFT_K_COUNT];          /* summed event durations (ms) */
+} ofdft_counters;
+
+/* Tracing (no counterpart in the paper, which reports wall time and counts of
+ * matrix-vector products): with enable != 0 every kernel launch on the context's
+ * stream is bracketed by a pair of CUDA events and its duration is summed per
+ * kind; with 0 only launches are counted.  Costs two event records per launch. */
+int ofdft_profile(ofdft_ctx* ctx, int enable);
+/* Copies the counters (synchronises the stream first). */
+int ofdft_get_counters(ofdft_ctx* ctx, ofdft_counters* out);
+int ofdft_reset_counters(ofdft_ctx* ctx);
 
 /* Device bytes a solve of this grid needs in the context workspace (for
  * admission control by callers that pack several solves on one device). */

@@ -81,10 +81,11 @@ def build(force: bool = False) -> str:
     """Compile the oracle with gcc into oracle/liboracle.so (idempotent)."""
     with _lock:
         stale = (not os.path.exists(_LIB) or
-                 os.path.getmtime(_LIB) < max(os.path.getmtime(_SRC), os.path.getmtime(_HDR)))
+                 os.path.getmtime(_LIB) < max(os.path.getmtime(_SRC), os.path.getmtime(_HDR),
+                                              os.path.getmtime(__file__)))
         if force or stale:
             tmp = _LIB + f".tmp{os.getpid()}"
-            cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+            cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
             subprocess.run(cmd, check=True, cwd=_HERE)
             os.replace(tmp, _LIB)
     return _LIB

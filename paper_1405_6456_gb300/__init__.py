@@ -5,14 +5,12 @@ orbital-free DFT (Suryanarayana & Phanish, arXiv:1405.6456).
 include/ofdft.h (argument marshalling only; every step runs in the CUDA library).
 `paper_1405_6456_gb300.workloads` holds the seeded synthetic cluster generators.
 """
-__all__ = ["ofdft", "workloads"]
+import importlib
+
+__all__ = ["ofdft", "workloads", "build", "serving"]
 
 
 def __getattr__(name):
-    if name == "ofdft":
-        from . import ofdft
-        return ofdft
-    if name == "workloads":
-        from . import workloads
-        return workloads
+    if name in __all__:
+        return importlib.import_module(f"{__name__}.{name}")
     raise AttributeError(name)

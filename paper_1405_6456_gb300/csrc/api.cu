@@ -1,0 +1,1314 @@
+// Host side of the library: the C ABI of include/ofdft.h, device workspaces,
+// kernel launch configuration, and the control flow of the method (Poisson CG
+// loop, secant/Polak-Ribiere nonlinear CG, Algorithm 1).  All arithmetic on
+// fields runs in the kernels of kernels.cuh; the host only moves scalars.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/ofdft.h"
+#include "kernels.cuh"
+
+using namespace ofd;
+
+// ----------------------------------------------------------------- context --
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct ofdft_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  int sms = 152;
+  // reduction scratch
+  DevBuf partials;
+  unsigned int* counter = nullptr;
+  // small device scalars: CG scalars (2 sets), functional outputs, dot outputs
+  CgScalars* sc = nullptr;
+  CgScalars* sc32 = nullptr;
+  double* scal = nullptr;  // 64 doubles
+  double* host_scal = nullptr;  // pinned mirror
+  // named vector workspaces
+  DevBuf v[24];
+  // launch counters and optional CUDA-event timing of every launch
+  long long launches = 0;
+  long long kind_launches[OFDFT_K_COUNT] = {0};
+  long long timed_launches[OFDFT_K_COUNT] = {0};
+  double timed_ms[OFDFT_K_COUNT] = {0};
+  int prof = 0;
+  struct Pending {
+    cudaEvent_t a, b;
+    int kind;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> free_events;
+};
+
+namespace {
+
+enum Vec {
+  V_R = 0, V_P0, V_P1, V_AP,           // CG vectors (prec type)
+  V_R64, V_PHI64, V_B64, V_E32,        // mixed refinement (FP64 r, phi, b; FP32 correction)
+  V_U, V_UT, V_PHI, V_B,               // solve state
+  V_G, V_GT, V_S, V_ST, V_SN, V_D,     // NLCG vectors
+  V_ATOM0, V_ATOM1, V_ATOM2,           // atom scratch
+  V_COUNT
+};
+
+int fail(ofdft_ctx* c, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return code;
+}
+
+#define CU(call)                                                                   \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess)                                                         \
+      return fail(c, e_ == cudaErrorMemoryAllocation ? OFDFT_ENOMEM : OFDFT_ECUDA, \
+                  "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)
+
+#define TRY(expr)            \
+  do {                       \
+    int rc_ = (expr);        \
+    if (rc_ != OFDFT_OK) return rc_; \
+  } while (0)
+
+int ensure(ofdft_ctx* c, DevBuf& b, size_t bytes) {
+  if (b.bytes >= bytes && b.p) return OFDFT_OK;
+  if (b.p) {
+    CU(cudaStreamSynchronize(c->stream));
+    CU(cudaFree(b.p));
+    b.p = nullptr;
+    b.bytes = 0;
+  }
+  const size_t want = std::max<size_t>(bytes, 256);
+  CU(cudaMalloc(&b.p, want));
+  b.bytes = want;
+  return OFDFT_OK;
+}
+
+template <typename T>
+T* vec(ofdft_ctx* c, int which) {
+  return static_cast<T*>(c->v[which].p);
+}
+
+cudaEvent_t take_event(ofdft_ctx* c) {
+  if (!c->free_events.empty()) {
+    cudaEvent_t e = c->free_events.back();
+    c->free_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Folds the durations of completed timed launches into the totals (call after
+// the stream has been synchronised) and recycles their events.
+void harvest(ofdft_ctx* c) {
+  for (auto& p : c->pending) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      c->timed_ms[p.kind] += ms;
+      c->timed_launches[p.kind] += 1;
+    }
+    c->free_events.push_back(p.a);
+    c->free_events.push_back(p.b);
+  }
+  c->pending.clear();
+}
+
+// Counts a kernel launch of `kind`; with profiling on, brackets it with events.
+struct ProfScope {
+  ofdft_ctx* c;
+  int kind;
+  cudaEvent_t a = nullptr, b = nullptr;
+  ProfScope(ofdft_ctx* c_, int k) : c(c_), kind(k) {
+    c->launches++;
+    c->kind_launches[k]++;
+    if (c->prof) {
+      a = take_event(c);
+      b = take_event(c);
+      if (a && b) cudaEventRecord(a, c->stream);
+    }
+  }
+  ~ProfScope() {
+    if (a && b) {
+      cudaEventRecord(b, c->stream);
+      c->pending.push_back({a, b, kind});
+      if (c->pending.size() > 4096) {
+        cudaEventSynchronize(b);
+        harvest(c);
+      }
+    }
+  }
+};
+
+RedBuf red(ofdft_ctx* c) { return RedBuf{static_cast<double*>(c->partials.p), c->counter}; }
+
+int ensure_partials(ofdft_ctx* c, long long nblocks, int K) {
+  return ensure(c, c->partials, (size_t)nblocks * K * sizeof(double) + 64);
+}
+
+GridDev gdev(const ofdft_grid* g) {
+  GridDev d;
+  d.n1 = g->n[0];
+  d.n2 = g->n[1];
+  d.n3 = g->n[2];
+  d.G = (long long)d.n1 * d.n2 * d.n3;
+  return d;
+}
+
+int check_grid(ofdft_ctx* c, const ofdft_grid* g) {
+  if (!g) return fail(c, OFDFT_EINVAL, "grid is NULL");
+  for (int d = 0; d < 3; ++d)
+    if (g->n[d] < 1 || g->n[d] > (1 << 16)) return fail(c, OFDFT_EINVAL, "grid dimension %d is %d", d, g->n[d]);
+  if (!(g->h > 0.0) || !isfinite(g->h)) return fail(c, OFDFT_EINVAL, "grid spacing must be positive");
+  return OFDFT_OK;
+}
+
+int check_order(ofdft_ctx* c, int fd_order) {
+  if (fd_order < 2 || fd_order > 2 * kMaxR || (fd_order & 1))
+    return fail(c, OFDFT_EINVAL, "fd_order must be even in [2, %d], got %d", 2 * kMaxR, fd_order);
+  return OFDFT_OK;
+}
+
+int check_prec(ofdft_ctx* c, int prec) {
+  if (prec != OFDFT_PREC_FP64 && prec != OFDFT_PREC_MIXED)
+    return fail(c, OFDFT_EINVAL, "precision must be OFDFT_PREC_FP64 or OFDFT_PREC_MIXED");
+  return OFDFT_OK;
+}
+
+// Laplacian weights of Sec. 4 (Eq. FD:Laplacian) in FP64, scaled by `scale`;
+// c = 6 w_0 (the p = 0 term counts the centre six times).
+Weights<double> lap_weights(int R, double h, double scale) {
+  Weights<double> W;
+  memset(&W, 0, sizeof(W));
+  double s = 0.0;
+  for (int q = 1; q <= R; ++q) s += 1.0 / ((double)q * q);
+  W.c = scale * 6.0 * (-s / (h * h));
+  // (R!)^2 / ((R-p)! (R+p)!) as a running product
+  for (int p = 1; p <= R; ++p) {
+    double ratio = 1.0;
+    for (int i = 1; i <= p; ++i) ratio *= (double)(R - p + i) / (double)(R + i);
+    const double sign = (p & 1) ? 1.0 : -1.0;
+    W.w[p] = scale * 2.0 * sign * ratio / (h * h * (double)p * p);
+  }
+  return W;
+}
+
+// Gradient weights of Sec. 4: w~_p = (-1)^{p+1} (R!)^2 / (h p (R-p)! (R+p)!).
+Weights<double> grad_weights(int R, double h) {
+  Weights<double> W;
+  memset(&W, 0, sizeof(W));
+  for (int p = 1; p <= R; ++p) {
+    double ratio = 1.0;
+    for (int i = 1; i <= p; ++i) ratio *= (double)(R - p + i) / (double)(R + i);
+    const double sign = (p & 1) ? 1.0 : -1.0;
+    W.w[p] = sign * ratio / (h * (double)p);
+  }
+  return W;
+}
+
+template <typename T>
+Weights<T> cast_weights(const Weights<double>& W) {
+  Weights<T> o;
+  o.c = (T)W.c;
+  for (int p = 0; p <= kMaxR; ++p) o.w[p] = (T)W.w[p];
+  return o;
+}
+
+int pointwise_blocks(ofdft_ctx* c, long long G) {
+  long long b = (G + 255) / 256;
+  return (int)std::max<long long>(1, std::min<long long>(b, (long long)c->sms * 8));
+}
+
+// z-streaming launch shape: BX x BY columns, z split so that the grid holds
+// about four blocks per SM, each z-chunk at least 2R planes deep.
+struct ZShape {
+  dim3 grid;
+  int zchunk;
+  long long nblocks;
+};
+
+ZShape zshape(ofdft_ctx* c, const GridDev& g, int R) {
+  ZShape s;
+  const int gx = (g.n1 + BX - 1) / BX, gy = (g.n2 + BY - 1) / BY;
+  const long long tiles = (long long)gx * gy;
+  const long long want = (long long)c->sms * 4;
+  int nz = (int)std::max<long long>(1, (want + tiles - 1) / tiles);
+  nz = std::min(nz, std::max(1, g.n3 / std::max(2 * R, 4)));
+  int zc = (g.n3 + nz - 1) / nz;
+  nz = (g.n3 + zc - 1) / zc;
+  s.grid = dim3(gx, gy, nz);
+  s.zchunk = zc;
+  s.nblocks = (long long)gx * gy * nz;
+  return s;
+}
+
+template <typename T, int R, class L, class E>
+int launch_z(ofdft_ctx* c, const GridDev& g, const Weights<double>& W, L ld, E ep, int kind) {
+  const ZShape s = zshape(c, g, R);
+  if (E::K > 0) TRY(ensure_partials(c, s.nblocks, E::K));
+  {
+    ProfScope ps_(c, kind);
+    zstream_kernel<T, R, L, E><<<s.grid, dim3(BX, BY), 0, c->stream>>>(g, cast_weights<T>(W), s.zchunk, ld, ep,
+                                                                       red(c));
+  }
+  CU(cudaGetLastError());
+  return OFDFT_OK;
+}
+
+// Runtime radius -> template radius.
+template <typename T, class L, class E>
+int launch_z_r(ofdft_ctx* c, int R, const GridDev& g, const Weights<double>& W, L ld, E ep, int kind) {
+  switch (R) {
+    case 1: return launch_z<T, 1>(c, g, W, ld, ep, kind);
+    case 2: return launch_z<T, 2>(c, g, W, ld, ep, kind);
+    case 3: return launch_z<T, 3>(c, g, W, ld, ep, kind);
+    case 4: return launch_z<T, 4>(c, g, W, ld, ep, kind);
+    case 5: return launch_z<T, 5>(c, g, W, ld, ep, kind);
+    case 6: return launch_z<T, 6>(c, g, W, ld, ep, kind);
+  }
+  return fail(c, OFDFT_EINVAL, "stencil radius %d not supported", R);
+}
+
+int sync_scalars(ofdft_ctx* c, const void* dev, size_t bytes, void* host) {
+  CU(cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  if (!c->pending.empty()) harvest(c);
+  return OFDFT_OK;
+}
+
+// ------------------------------------------------------------ Poisson (S3) --
+// Plain CG iterations on the prepared scalars `sc` (residual r, iterate x),
+// checking the device `done` flag every `chunk` iterations.
+template <typename T>
+int cg_iterate(ofdft_ctx* c, int R, const GridDev& g, const Weights<double>& Wneg, T* x, T* r, CgScalars* sc,
+               int max_it, CgScalars* host_sc) {
+  T* p0 = vec<T>(c, V_P0);
+  T* p1 = vec<T>(c, V_P1);
+  T* Ap = vec<T>(c, V_AP);
+  const int pb = pointwise_blocks(c, g.G);
+  TRY(ensure_partials(c, pb, 1));
+  const int chunk = 8;
+  int launched = 0;
+  while (launched < max_it) {
+    for (int i = 0; i < chunk && launched < max_it; ++i, ++launched) {
+      T* pp = (launched & 1) ? p1 : p0;  // previous direction
+      T* pc = (launched & 1) ? p0 : p1;  // new direction
+      TRY(launch_z_r<T>(c, R, g, Wneg, LoadCgDir<T>{r, pp, sc}, EpiCgA<T>{pc, Ap, sc}, OFDFT_K_CG_DIR_STENCIL));
+      {
+        ProfScope ps_(c, OFDFT_K_CG_UPDATE);
+        cg_update_kernel<T><<<pb, 256, 0, c->stream>>>(g.G, x, r, pc, Ap, sc, red(c));
+      }
+      CU(cudaGetLastError());
+    }
+    TRY(sync_scalars(c, sc, sizeof(CgScalars), host_sc));
+    if (host_sc->done) break;
+  }
+  TRY(sync_scalars(c, sc, sizeof(CgScalars), host_sc));
+  return OFDFT_OK;
+}
+
+// Workspace sizes for a solve (vectors of the prec type, plus FP64 mixed extras).
+int ensure_cg_vectors(ofdft_ctx* c, long long G, size_t es, bool mixed) {
+  TRY(ensure(c, c->v[V_R], G * es));
+  TRY(ensure(c, c->v[V_P0], G * es));
+  TRY(ensure(c, c->v[V_P1], G * es));
+  TRY(ensure(c, c->v[V_AP], G * es));
+  if (mixed) {
+    TRY(ensure(c, c->v[V_R64], G * sizeof(double)));
+    TRY(ensure(c, c->v[V_E32], G * sizeof(float)));
+  }
+  return OFDFT_OK;
+}
+
+// FP64 Poisson solve: r = 4 pi rho + L phi, then CG.  rho = rho_in or u^2 + b.
+// On return r (V_R) holds the final recursive residual; st gets the stats.
+int poisson_fp64(ofdft_ctx* c, int R, const GridDev& g, double h, const double* rho, const double* u,
+                 const double* b, double* phi, double tol, int max_it, ofdft_cg_stats* st) {
+  TRY(ensure_cg_vectors(c, g.G, sizeof(double), false));
+  const Weights<double> W = lap_weights(R, h, 1.0), Wneg = lap_weights(R, h, -1.0);
+  double* r = vec<double>(c, V_R);
+  TRY(launch_z_r<double>(c, R, g, W, LoadPlain<double>{phi},
+                         EpiResidual<double>{rho, u, b, r, c->sc, tol, max_it, 1}, OFDFT_K_RESIDUAL));
+  CgScalars hs;
+  TRY(sync_scalars(c, c->sc, sizeof(CgScalars), &hs));
+  if (!hs.done) TRY(cg_iterate<double>(c, R, g, Wneg, phi, r, c->sc, max_it, &hs));
+  if (st) {
+    st->iterations = hs.iters;
+    st->rel_residual = sqrt(hs.rr / (hs.bb > 0 ? hs.bb : 1.0));
+  }
+  if (!isfinite(hs.rr)) return fail(c, OFDFT_ENONFINITE, "Poisson residual is not finite");
+  if (hs.rr > tol * tol * (hs.bb > 0 ? hs.bb : 1.0))
+    return fail(c, OFDFT_ENOTCONV, "Poisson CG reached %d iterations at relative residual %.3e", hs.iters,
+                sqrt(hs.rr / (hs.bb > 0 ? hs.bb : 1.0)));
+  return OFDFT_OK;
+}
+
+// Mixed Poisson solve (S3 + S10): phi64 is the FP64 iterate; each round computes
+// the FP64 residual r64 = 4 pi (u^2 + b64) + L_h phi64 with the FP64 stencil,
+// then solves A e = r64 by FP32 CG (relative tolerance 1e-5 or refine_every
+// steps) and sets phi64 += e, phi32 = (float) phi64.  Ends when the FP64
+// residual meets tol.  rho32 (optional) replaces u^2 + b.
+int poisson_mixed(ofdft_ctx* c, int R, const GridDev& g, double h, const float* rho32, const float* u,
+                  const double* b64, double* phi64, float* phi32, double tol, int max_it,
+                  int refine_every, ofdft_cg_stats* st) {
+  TRY(ensure_cg_vectors(c, g.G, sizeof(float), true));
+  const Weights<double> W = lap_weights(R, h, 1.0), Wneg = lap_weights(R, h, -1.0);
+  double* r64 = vec<double>(c, V_R64);
+  float* r32 = vec<float>(c, V_R);
+  float* e32 = vec<float>(c, V_E32);
+  const int pb = pointwise_blocks(c, g.G);
+  int total = 0;
+  CgScalars hs, hs32;
+  const int max_rounds = 40;
+  for (int round = 0; round <= max_rounds; ++round) {
+    if (rho32)
+      TRY(launch_z_r<double>(c, R, g, W, LoadPlain<double>{phi64},
+                             EpiResidual<double, float, double>{rho32, nullptr, nullptr, r64, c->sc, tol, max_it, 1}, OFDFT_K_RESIDUAL));
+    else
+      TRY(launch_z_r<double>(c, R, g, W, LoadPlain<double>{phi64},
+                             EpiResidual<double, float, double>{nullptr, u, b64, r64, c->sc, tol, max_it, 1}, OFDFT_K_RESIDUAL));
+    TRY(sync_scalars(c, c->sc, sizeof(CgScalars), &hs));
+    const double bb = hs.bb > 0 ? hs.bb : 1.0;
+    if (st) {
+      st->iterations = total;
+      st->rel_residual = sqrt(hs.rr / bb);
+    }
+    if (!isfinite(hs.rr)) return fail(c, OFDFT_ENONFINITE, "Poisson residual is not finite");
+    if (hs.rr <= tol * tol * bb) return OFDFT_OK;
+    if (total >= max_it || round == max_rounds)
+      return fail(c, OFDFT_ENOTCONV, "mixed Poisson reached %d FP32 iterations at relative residual %.3e", total,
+                  sqrt(hs.rr / bb));
+    const int budget = std::min(refine_every, max_it - total);
+    TRY(ensure_partials(c, pb, 1));
+    {
+      ProfScope ps_(c, OFDFT_K_VECTOR);
+      refine_init_kernel<<<pb, 256, 0, c->stream>>>(g.G, r32, e32, r64, c->sc32, 1e-5, budget, red(c));
+    }
+    CU(cudaGetLastError());
+    TRY(cg_iterate<float>(c, R, g, Wneg, e32, r32, c->sc32, budget, &hs32));
+    total += std::max(hs32.iters, 1);
+    {
+      ProfScope ps_(c, OFDFT_K_VECTOR);
+      refine_apply_kernel<<<pb, 256, 0, c->stream>>>(g.G, phi64, phi32, e32);
+    }
+    CU(cudaGetLastError());
+  }
+  return OFDFT_OK;
+}
+
+// ------------------------------------------------------ functional (S4) ---
+struct EvalOut {
+  double sums[10];
+};
+
+template <typename T>
+int functional_pass(ofdft_ctx* c, int R, const GridDev& g, double h, const ofdft_params* p, const T* u,
+                    const T* b, const T* phi, const T* rcg, double eta, double mu, double N,
+                    const double* sum_uu_dev, T* G, T* s, const T* d, const T* s_old, EvalOut* out) {
+  const Weights<double> W = lap_weights(R, h, 1.0);
+  FuncScalars f;
+  f.h3 = h * h * h;
+  f.N = N;
+  f.eta = eta;
+  f.inv_mu = 1.0 / mu;
+  f.lambda = p->lambda;
+  f.CF = 0.3 * pow(3.0 * kPi * kPi, 2.0 / 3.0);
+  f.kin_vw = -p->lambda * W.c;  // -lambda 6 w_0 > 0
+  f.terms = p->terms;
+  const bool es = p->terms & OFDFT_TERM_ES;
+  EpiFunctional<T> ep{es ? phi : nullptr, b, es ? rcg : nullptr, d, s_old, G, s, sum_uu_dev, f, c->scal};
+  TRY(launch_z_r<T>(c, R, g, W, LoadPlain<T>{u}, ep, OFDFT_K_FUNCTIONAL));
+  TRY(sync_scalars(c, c->scal, 10 * sizeof(double), out->sums));
+  return OFDFT_OK;
+}
+
+void fill_energy(const EvalOut& o, double h, const ofdft_params* p, double E_self, double ezz, double eta,
+                 double mu, ofdft_energy* e) {
+  const double h3 = h * h * h;
+  const bool es = p->terms & OFDFT_TERM_ES;
+  e->E_tf = h3 * o.sums[0];
+  e->E_vw = -0.5 * p->lambda * h3 * o.sums[1];
+  e->E_xc = h3 * o.sums[2];
+  e->E_self = es ? E_self : 0.0;
+  e->E_es = es ? h3 * (0.5 * o.sums[3] + o.sums[4] / (8.0 * kPi)) - E_self : 0.0;
+  e->E_zz_corr = ezz;
+  e->E = e->E_tf + e->E_vw + e->E_xc + e->E_es + ezz;
+  e->C = o.sums[9];
+  e->L = e->E - eta * e->C + 0.5 * e->C * e->C / mu;
+  e->gd = h3 * o.sums[5];
+  e->gs_old = h3 * o.sums[6];
+  e->rs = h3 * o.sums[7];
+  e->gnorm2 = h3 * o.sums[8];
+}
+
+// ------------------------------------------------------------- solve state --
+// One energy/gradient evaluation of the solver (S3 + S4): Poisson at u (warm
+// start from the state's phi), then the functional.  T is the field type.
+template <typename T>
+struct Solver {
+  ofdft_ctx* c;
+  const ofdft_params* p;
+  GridDev g;
+  double h, N, E_self, ezz;
+  int R, M;
+  bool mixed;
+  T *u, *ut, *phi, *b, *G, *Gt, *s, *st, *sn, *d;
+  double* b64;    // mixed: FP64 pseudocharge
+  double* phi64;  // mixed: FP64 potential
+  ofdft_solve_stats* stats;
+  ofdft_energy e;  // at the current point
+  int trace = 0;   // OFDFT_TRACE=1: one line per evaluation on stderr
+
+  int eval(const T* at, T* Gout, T* sout, const T* dd, const T* s_old, double eta, double mu, ofdft_energy* out) {
+    const int rc = eval_inner(at, Gout, sout, dd, s_old, eta, mu, out);
+    if (trace)
+      fprintf(stderr, "[ofdft] eval %d rc=%d L=%.12g E=%.12g C=%.3e gd=%.4e rs=%.4e cg=%d rel=%.2e\n",
+              stats->grad_evals, rc, out->L, out->E, out->C, out->gd, out->rs, out->poisson.iterations,
+              out->poisson.rel_residual);
+    return rc;
+  }
+
+  int eval_inner(const T* at, T* Gout, T* sout, const T* dd, const T* s_old, double eta, double mu,
+                 ofdft_energy* out) {
+    ofdft_cg_stats cs{0, 0.0};
+    const bool es = p->terms & OFDFT_TERM_ES;
+    const double* sum_uu = &c->sc->sum_uu;
+    if (es) {
+      int rc;
+      if (!mixed)
+        rc = poisson_fp64(c, R, g, h, nullptr, (const double*)at, (const double*)b, (double*)phi, p->tol_poisson,
+                          p->max_cg, &cs);
+      else
+        rc = poisson_mixed(c, R, g, h, nullptr, (const float*)at, b64, phi64, (float*)phi, p->tol_poisson,
+                           p->max_cg, std::max(p->refine_every, 1), &cs);
+      if (rc != OFDFT_OK) return rc;
+      stats->stencil_apps += cs.iterations + 1;
+      stats->cg_iters += cs.iterations;
+    } else {
+      const int pb = pointwise_blocks(c, g.G);
+      TRY(ensure_partials(c, pb, 2));
+      {
+        ProfScope ps_(c, OFDFT_K_VECTOR);
+        dot2_kernel<T><<<pb, 256, 0, c->stream>>>(g.G, at, at, nullptr, nullptr, c->scal + 16, red(c));
+      }
+      CU(cudaGetLastError());
+      sum_uu = c->scal + 16;
+    }
+    const T* rcg = nullptr;
+    if (es) {
+      if (mixed) {
+        // FP32 copy of the FP64 residual for the phi.r energy term
+        const int pb = pointwise_blocks(c, g.G);
+        {
+          ProfScope ps_(c, OFDFT_K_VECTOR);
+          convert_kernel<double, float><<<pb, 256, 0, c->stream>>>(g.G, vec<float>(c, V_R), vec<double>(c, V_R64));
+        }
+        CU(cudaGetLastError());
+      }
+      rcg = vec<T>(c, V_R);
+    }
+    EvalOut o;
+    TRY(functional_pass<T>(c, R, g, h, p, at, b, phi, rcg, eta, mu, N, sum_uu, Gout, sout, dd, s_old, &o));
+    stats->stencil_apps += 2;
+    stats->grad_evals += 1;
+    fill_energy(o, h, p, E_self, ezz, eta, mu, out);
+    out->poisson = cs;
+    return OFDFT_OK;
+  }
+
+  int dots(const T* a, const T* bb, const T* cc, const T* ee, double* r2) {
+    const int pb = pointwise_blocks(c, g.G);
+    TRY(ensure_partials(c, pb, 2));
+    {
+      ProfScope ps_(c, OFDFT_K_VECTOR);
+      dot2_kernel<T><<<pb, 256, 0, c->stream>>>(g.G, a, bb, cc, ee, c->scal + 16, red(c));
+    }
+    CU(cudaGetLastError());
+    TRY(sync_scalars(c, c->scal + 16, 2 * sizeof(double), r2));
+    return OFDFT_OK;
+  }
+
+  int axpy_abs(T* out, const T* a, const T* bb, double alpha) {
+    {
+      ProfScope ps_(c, OFDFT_K_VECTOR);
+      axpy_abs_kernel<T><<<pointwise_blocks(c, g.G), 256, 0, c->stream>>>(g.G, out, a, bb, alpha);
+    }
+    CU(cudaGetLastError());
+    return OFDFT_OK;
+  }
+
+  int direction(double beta) {
+    {
+      ProfScope ps_(c, OFDFT_K_VECTOR);
+      direction_kernel<T><<<pointwise_blocks(c, g.G), 256, 0, c->stream>>>(g.G, d, s, beta);
+    }
+    CU(cudaGetLastError());
+    return OFDFT_OK;
+  }
+
+  // Polak-Ribiere nonlinear CG with a secant line search and the Jacobi
+  // preconditioner, u <- |u| after every update (Sec. 4), on L(., eta, mu).
+  int nlcg(double eta, double mu, int* converged) {
+    *converged = 0;
+    const double h3 = h * h * h;
+    const double tol_in = p->tol_inner * M;
+    TRY(eval(u, G, s, nullptr, nullptr, eta, mu, &e));
+    TRY(direction(0.0));  // d = s
+    double delta_new = e.rs;
+    int k = 0;
+    for (int it = 0; it < p->max_nlcg; ++it) {
+      if (e.rs < tol_in) {
+        *converged = 1;
+        break;
+      }
+      if (!isfinite(e.L) || !isfinite(e.rs)) return fail(c, OFDFT_ENONFINITE, "augmented Lagrangian is not finite");
+      stats->nlcg_iters++;
+      T* s_old = s;
+      double gdd[2];
+      TRY(dots(G, d, d, d, gdd));
+      double g0 = h3 * gdd[0];
+      double dd = h3 * gdd[1];
+      if (!(g0 < 0.0)) {  // not a descent direction: restart along s
+        TRY(direction(0.0));
+        k = 0;
+        TRY(dots(G, d, d, d, gdd));
+        g0 = h3 * gdd[0];
+        dd = h3 * gdd[1];
+      }
+      // trial point at sigma0 along d
+      TRY(axpy_abs(ut, u, d, p->sigma0));
+      ofdft_energy et;
+      TRY(eval(ut, Gt, st, d, s_old, eta, mu, &et));
+      double alpha = -p->sigma0, gprev = et.gd, gcur = g0;
+      if (!((gcur - gprev) / alpha > 0.0)) {
+        // no positive curvature between 0 and sigma0: keep the trial point
+        std::swap(u, ut);
+        std::swap(G, Gt);
+        std::swap(s, st);
+        e = et;
+      } else {
+        T* snew = sn;
+        for (int j = 1; j <= p->max_secant; ++j) {
+          alpha = alpha * gcur / (gprev - gcur);
+          TRY(axpy_abs(u, u, d, alpha));
+          TRY(eval(u, G, snew, d, s_old, eta, mu, &e));
+          gprev = gcur;
+          gcur = e.gd;
+          if (j == p->max_secant || alpha * alpha * dd <= p->eps_secant * p->eps_secant * N) break;
+          if (!((gcur - gprev) / alpha > 0.0)) break;
+        }
+        // the new s lives in snew; the old s buffer becomes spare
+        sn = s;
+        s = snew;
+      }
+      const double delta_old = delta_new;
+      const double delta_mid = -e.gs_old;
+      delta_new = e.rs;
+      const double beta = (delta_new - delta_mid) / delta_old;
+      ++k;
+      if (k >= p->restart_every || !(beta > 0.0)) {
+        TRY(direction(0.0));
+        k = 0;
+      } else {
+        TRY(direction(beta));
+      }
+    }
+    if (!*converged && e.rs < tol_in) *converged = 1;
+    return OFDFT_OK;
+  }
+};
+
+template <typename T>
+int device_pseudocharge(ofdft_ctx* c, const ofdft_grid* gr, int R, const double* R_host, const double* Z_host,
+                        int M, double sigma, double rc, T* b, double* E_self);
+template <typename T>
+int device_guess(ofdft_ctx* c, const ofdft_grid* gr, const double* R_host, const double* Z_host, int M,
+                 double gsig, double gcut, double N, T* u);
+template <typename T>
+int device_forces(ofdft_ctx* c, const ofdft_grid* gr, int R, const double* R_host, const double* Z_host, int M,
+                  double sigma, double rc, int variant, const T* phi, double* F);
+int device_ezz(ofdft_ctx* c, const double* R_host, const double* Z_host, int M, double sigma, double* E,
+               double* F);
+
+// Copies atoms to a device scratch buffer (V_ATOM0): R (3M) then Z (M).
+int upload_atoms(ofdft_ctx* c, const double* R_host, const double* Z_host, int M, AtomArgs* A,
+                 const ofdft_grid* g, double sigma, double rc) {
+  TRY(ensure(c, c->v[V_ATOM0], (size_t)4 * M * sizeof(double)));
+  double* dR = vec<double>(c, V_ATOM0);
+  CU(cudaMemcpyAsync(dR, R_host, 3 * M * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CU(cudaMemcpyAsync(dR + 3 * M, Z_host, M * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  A->R = dR;
+  A->Z = dR + 3 * M;
+  A->M = M;
+  A->h = g ? g->h : 1.0;
+  A->ox = g ? g->origin[0] : 0.0;
+  A->oy = g ? g->origin[1] : 0.0;
+  A->oz = g ? g->origin[2] : 0.0;
+  A->sigma = sigma;
+  A->rc = rc;
+  return OFDFT_OK;
+}
+
+int check_atoms(ofdft_ctx* c, const double* R, const double* Z, int M) {
+  if (M < 1 || !R || !Z) return fail(c, OFDFT_EINVAL, "need M >= 1 atoms with positions and charges");
+  for (int i = 0; i < 3 * M; ++i)
+    if (!isfinite(R[i])) return fail(c, OFDFT_ENONFINITE, "atom coordinate %d is not finite", i);
+  for (int i = 0; i < M; ++i)
+    if (!isfinite(Z[i])) return fail(c, OFDFT_ENONFINITE, "charge %d is not finite", i);
+  return OFDFT_OK;
+}
+
+template <typename T, int R>
+int launch_pseudocharge(ofdft_ctx* c, const GridDev& g, const AtomArgs& A, const Weights<double>& W, T* b) {
+  dim3 grid((g.n1 + AT - 1) / AT, (g.n2 + AT - 1) / AT, (g.n3 + AT - 1) / AT);
+  TRY(ensure_partials(c, (long long)grid.x * grid.y * grid.z, 1));
+  {
+    ProfScope ps_(c, OFDFT_K_ATOMS);
+    pseudocharge_kernel<T, R><<<grid, dim3(AT, AT, AT), 0, c->stream>>>(g, A, W, b, c->scal + 20, red(c));
+  }
+  CU(cudaGetLastError());
+  return OFDFT_OK;
+}
+
+template <typename T>
+int device_pseudocharge(ofdft_ctx* c, const ofdft_grid* gr, int R, const double* R_host, const double* Z_host,
+                        int M, double sigma, double rc, T* b, double* E_self) {
+  AtomArgs A;
+  TRY(upload_atoms(c, R_host, Z_host, M, &A, gr, sigma, rc));
+  const GridDev g = gdev(gr);
+  const Weights<double> W = lap_weights(R, gr->h, 1.0);
+  switch (R) {
+    case 1: TRY((launch_pseudocharge<T, 1>(c, g, A, W, b))); break;
+    case 2: TRY((launch_pseudocharge<T, 2>(c, g, A, W, b))); break;
+    case 3: TRY((launch_pseudocharge<T, 3>(c, g, A, W, b))); break;
+    case 4: TRY((launch_pseudocharge<T, 4>(c, g, A, W, b))); break;
+    case 5: TRY((launch_pseudocharge<T, 5>(c, g, A, W, b))); break;
+    case 6: TRY((launch_pseudocharge<T, 6>(c, g, A, W, b))); break;
+    default: return fail(c, OFDFT_EINVAL, "stencil radius %d", R);
+  }
+  double es;
+  TRY(sync_scalars(c, c->scal + 20, sizeof(double), &es));
+  *E_self = 0.5 * gr->h * gr->h * gr->h * es;
+  return OFDFT_OK;
+}
+
+template <typename T>
+int device_guess(ofdft_ctx* c, const ofdft_grid* gr, const double* R_host, const double* Z_host, int M,
+                 double gsig, double gcut, double N, T* u) {
+  AtomArgs A;
+  TRY(upload_atoms(c, R_host, Z_host, M, &A, gr, 1.0, 1.0));
+  const GridDev g = gdev(gr);
+  dim3 grid((g.n1 + AT - 1) / AT, (g.n2 + AT - 1) / AT, (g.n3 + AT - 1) / AT);
+  TRY(ensure_partials(c, (long long)grid.x * grid.y * grid.z, 1));
+  {
+    ProfScope ps_(c, OFDFT_K_ATOMS);
+    guess_kernel<T><<<grid, dim3(AT, AT, AT), 0, c->stream>>>(g, A, gsig, gcut, u, c->scal + 21, red(c));
+  }
+  CU(cudaGetLastError());
+  {
+    ProfScope ps_(c, OFDFT_K_ATOMS);
+    normalise_kernel<T><<<pointwise_blocks(c, g.G), 256, 0, c->stream>>>(g.G, u, c->scal + 21,
+                                                                        gr->h * gr->h * gr->h, N);
+  }
+  CU(cudaGetLastError());
+  return OFDFT_OK;
+}
+
+template <typename T, int R>
+int launch_force_boxes(ofdft_ctx* c, const AtomArgs& A, int a0, int na, int vdim, int bdim, const int* lo,
+                       const Weights<double>& W, double* vbox, double* bbox) {
+  {
+    ProfScope ps_(c, OFDFT_K_ATOMS);
+    force_vbox_kernel<<<c->sms * 8, 256, 0, c->stream>>>(A, a0, na, vdim, R, lo, vbox);
+  }
+  CU(cudaGetLastError());
+  {
+    ProfScope ps_(c, OFDFT_K_ATOMS);
+    force_bbox_kernel<R><<<c->sms * 8, 256, 0, c->stream>>>(A, a0, na, vdim, bdim, lo, W, vbox, bbox);
+  }
+  CU(cudaGetLastError());
+  return OFDFT_OK;
+}
+
+template <typename T, int R>
+int launch_force_ball(ofdft_ctx* c, const GridDev& g, const AtomArgs& A, int a0, int na, int bdim, int box,
+                      const int* lo, const Weights<double>& W, const Weights<double>& Wt, const double* bbox,
+                      const T* phi, int exact, double* partial, int nblk) {
+  {
+    ProfScope ps_(c, OFDFT_K_ATOMS);
+    force_ball_kernel<T, R><<<dim3(nblk, na), 256, 0, c->stream>>>(g, A, a0, bdim, box, lo, W, Wt, bbox, phi, exact,
+                                                                    partial);
+  }
+  CU(cudaGetLastError());
+  return OFDFT_OK;
+}
+
+template <typename T>
+int device_forces(ofdft_ctx* c, const ofdft_grid* gr, int R, const double* R_host, const double* Z_host, int M,
+                  double sigma, double rc, int variant, const T* phi, double* F) {
+  AtomArgs A;
+  TRY(upload_atoms(c, R_host, Z_host, M, &A, gr, sigma, rc));
+  const GridDev g = gdev(gr);
+  const double h = gr->h;
+  // per-atom box: nodes whose centre can lie within r_c, plus one node of slack
+  const int rb = (int)ceil(rc / h) + 1;
+  const int box = 2 * rb + 1;
+  const int bdim = box + 2 * R, vdim = box + 4 * R;
+  const long long vper = (long long)vdim * vdim * vdim, bper = (long long)bdim * bdim * bdim;
+  const bool exact = (variant == OFDFT_FORCE_EXACT);
+  // atoms per batch: keep the box scratch near 256 MB
+  int batch = (int)std::max<long long>(1, std::min<long long>(M, (256ll << 20) / ((vper + bper) * 8)));
+  if (exact) batch = std::min(M, 4096);
+  const int nblk = std::max(1, std::min(64, (int)((long long)box * box * box / 2048) + 1));
+  TRY(ensure(c, c->v[V_ATOM1], exact ? 256 : (size_t)batch * (vper + bper) * sizeof(double)));
+  TRY(ensure(c, c->v[V_ATOM2], (size_t)batch * (3 + nblk * 3) * sizeof(double) + (size_t)batch * 3 * sizeof(int) +
+                                  (size_t)3 * M * sizeof(double) + 64));
+  double* vbox = vec<double>(c, V_ATOM1);
+  double* bbox = vbox + (size_t)batch * vper;
+  double* partial = vec<double>(c, V_ATOM2);
+  double* Fdev = partial + (size_t)batch * nblk * 3;
+  int* lo_dev = (int*)(Fdev + (size_t)3 * M);
+  std::vector<int> lo((size_t)3 * batch);
+  const Weights<double> W = lap_weights(R, h, 1.0), Wt = grad_weights(R, h);
+  for (int a0 = 0; a0 < M; a0 += batch) {
+    const int na = std::min(batch, M - a0);
+    for (int a = 0; a < na; ++a)
+      for (int d = 0; d < 3; ++d)
+        lo[3 * a + d] = (int)floor((R_host[3 * (a0 + a) + d] - gr->origin[d]) / h - 0.5) - rb + 1;
+    CU(cudaMemcpyAsync(lo_dev, lo.data(), 3 * na * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    if (!exact) {
+      switch (R) {
+        case 1: TRY((launch_force_boxes<T, 1>(c, A, a0, na, vdim, bdim, lo_dev, W, vbox, bbox))); break;
+        case 2: TRY((launch_force_boxes<T, 2>(c, A, a0, na, vdim, bdim, lo_dev, W, vbox, bbox))); break;
+        case 3: TRY((launch_force_boxes<T, 3>(c, A, a0, na, vdim, bdim, lo_dev, W, vbox, bbox))); break;
+        case 4: TRY((launch_force_boxes<T, 4>(c, A, a0, na, vdim, bdim, lo_dev, W, vbox, bbox))); break;
+        case 5: TRY((launch_force_boxes<T, 5>(c, A, a0, na, vdim, bdim, lo_dev, W, vbox, bbox))); break;
+        case 6: TRY((launch_force_boxes<T, 6>(c, A, a0, na, vdim, bdim, lo_dev, W, vbox, bbox))); break;
+      }
+    }
+    switch (R) {
+      case 1: TRY((launch_force_ball<T, 1>(c, g, A, a0, na, bdim, box, lo_dev, W, Wt, bbox, phi, exact, partial, nblk))); break;
+      case 2: TRY((launch_force_ball<T, 2>(c, g, A, a0, na, bdim, box, lo_dev, W, Wt, bbox, phi, exact, partial, nblk))); break;
+      case 3: TRY((launch_force_ball<T, 3>(c, g, A, a0, na, bdim, box, lo_dev, W, Wt, bbox, phi, exact, partial, nblk))); break;
+      case 4: TRY((launch_force_ball<T, 4>(c, g, A, a0, na, bdim, box, lo_dev, W, Wt, bbox, phi, exact, partial, nblk))); break;
+      case 5: TRY((launch_force_ball<T, 5>(c, g, A, a0, na, bdim, box, lo_dev, W, Wt, bbox, phi, exact, partial, nblk))); break;
+      case 6: TRY((launch_force_ball<T, 6>(c, g, A, a0, na, bdim, box, lo_dev, W, Wt, bbox, phi, exact, partial, nblk))); break;
+    }
+    {
+      ProfScope ps_(c, OFDFT_K_ATOMS);
+      force_sum_kernel<<<(na + 127) / 128, 128, 0, c->stream>>>(a0, na, nblk, h * h * h, partial, Fdev);
+    }
+    CU(cudaGetLastError());
+  }
+  CU(cudaMemcpyAsync(F, Fdev, 3 * M * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return OFDFT_OK;
+}
+
+int device_ezz(ofdft_ctx* c, const double* R_host, const double* Z_host, int M, double sigma, double* E,
+               double* F) {
+  AtomArgs A;
+  TRY(upload_atoms(c, R_host, Z_host, M, &A, nullptr, sigma, 1.0));
+  TRY(ensure(c, c->v[V_ATOM2], (size_t)4 * M * sizeof(double) + 64));
+  double* eI = vec<double>(c, V_ATOM2);
+  double* Fd = eI + M;
+  {
+    ProfScope ps_(c, OFDFT_K_ATOMS);
+    ezz_kernel<<<(M + 127) / 128, 128, 0, c->stream>>>(A, eI, Fd);
+  }
+  CU(cudaGetLastError());
+  std::vector<double> e(M), f(3 * (size_t)M);
+  CU(cudaMemcpyAsync(e.data(), eI, M * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaMemcpyAsync(f.data(), Fd, 3 * M * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  double s = 0.0;
+  for (int i = 0; i < M; ++i) s += e[i];
+  *E = s;
+  if (F)
+    for (int i = 0; i < 3 * M; ++i) F[i] = f[i];
+  return OFDFT_OK;
+}
+
+template <typename T>
+int solve_impl(ofdft_ctx* c, const ofdft_grid* gr, const double* R_host, const double* Z_host, int M,
+               const ofdft_params* p, void* u_out, void* phi_out, double* energy, double* forces,
+               ofdft_solve_stats* st) {
+  const bool mixed = (p->precision == OFDFT_PREC_MIXED);
+  const GridDev g = gdev(gr);
+  const int R = p->fd_order / 2;
+  const size_t es = sizeof(T);
+  // workspace
+  for (int v : {V_U, V_UT, V_PHI, V_B, V_G, V_GT, V_S, V_ST, V_SN, V_D}) TRY(ensure(c, c->v[v], g.G * es));
+  TRY(ensure_cg_vectors(c, g.G, es, mixed));
+  if (mixed) {
+    TRY(ensure(c, c->v[V_B64], g.G * sizeof(double)));
+    TRY(ensure(c, c->v[V_PHI64], g.G * sizeof(double)));
+  }
+  double N = 0.0;
+  for (int J = 0; J < M; ++J) N += Z_host[J];
+  Solver<T> S;
+  S.c = c;
+  S.p = p;
+  S.g = g;
+  S.h = gr->h;
+  S.N = N;
+  S.R = R;
+  S.M = M;
+  S.mixed = mixed;
+  S.stats = st;
+  S.trace = getenv("OFDFT_TRACE") && getenv("OFDFT_TRACE")[0] == '1';
+  S.u = vec<T>(c, V_U);
+  S.ut = vec<T>(c, V_UT);
+  S.phi = vec<T>(c, V_PHI);
+  S.b = vec<T>(c, V_B);
+  S.G = vec<T>(c, V_G);
+  S.Gt = vec<T>(c, V_GT);
+  S.s = vec<T>(c, V_S);
+  S.st = vec<T>(c, V_ST);
+  S.sn = vec<T>(c, V_SN);
+  S.d = vec<T>(c, V_D);
+  S.b64 = mixed ? vec<double>(c, V_B64) : nullptr;
+  S.phi64 = mixed ? vec<double>(c, V_PHI64) : nullptr;
+  // S1: pseudocharge (FP64 for the mixed path too), starting guess, phi = 0
+  if (!mixed) {
+    TRY(device_pseudocharge<double>(c, gr, R, R_host, Z_host, M, p->sigma, p->rc, (double*)S.b, &S.E_self));
+  } else {
+    TRY(device_pseudocharge<double>(c, gr, R, R_host, Z_host, M, p->sigma, p->rc, S.b64, &S.E_self));
+    {
+      ProfScope ps_(c, OFDFT_K_VECTOR);
+      convert_kernel<double, float><<<pointwise_blocks(c, g.G), 256, 0, c->stream>>>(g.G, (float*)S.b, S.b64);
+    }
+    CU(cudaGetLastError());
+    CU(cudaMemsetAsync(S.phi64, 0, g.G * sizeof(double), c->stream));
+  }
+  TRY(device_guess<T>(c, gr, R_host, Z_host, M, p->guess_sigma, p->guess_cut, N, S.u));
+  CU(cudaMemsetAsync(S.phi, 0, g.G * es, c->stream));
+  S.ezz = 0.0;
+  std::vector<double> Fz(3 * (size_t)M, 0.0);
+  if (p->ezz_correction) TRY(device_ezz(c, R_host, Z_host, M, p->sigma, &S.ezz, Fz.data()));
+  // Algorithm 1
+  double eta = (p->method == OFDFT_METHOD_PENALTY) ? 0.0 : p->eta0;
+  double mu = p->mu0;
+  TRY(S.eval(S.u, S.G, S.s, nullptr, nullptr, eta, mu, &S.e));
+  double E_prev = S.e.E;
+  int converged = 0;
+  const double tolE = p->tol_E * M;
+  for (int q = 0; q < p->max_outer; ++q) {
+    int inner_ok = 0;
+    TRY(S.nlcg(eta, mu, &inner_ok));
+    st->outer_iters++;
+    const double E = S.e.E, C = S.e.C;
+    if (!isfinite(E) || !isfinite(C)) return fail(c, OFDFT_ENONFINITE, "energy or constraint is not finite");
+    const double eta_eff = eta - C / mu;  // multiplier update of Algorithm 1
+    st->eta = eta_eff;
+    if (p->method == OFDFT_METHOD_AL) eta = eta_eff;
+    mu = p->kappa * mu;
+    if (fabs(E - E_prev) < tolE) {
+      converged = 1;
+      break;
+    }
+    E_prev = E;
+  }
+  st->E = S.e.E;
+  st->C = S.e.C;
+  st->parts = S.e;
+  st->converged = converged;
+  st->grid = *gr;
+  *energy = S.e.E;
+  // S9: forces at phi*
+  if (forces) {
+    TRY(device_forces<T>(c, gr, R, R_host, Z_host, M, p->sigma, p->rc, p->force_variant, S.phi, forces));
+    if (p->ezz_correction)
+      for (int i = 0; i < 3 * M; ++i) forces[i] += Fz[i];
+  }
+  if (u_out) CU(cudaMemcpyAsync(u_out, S.u, g.G * es, cudaMemcpyDeviceToDevice, c->stream));
+  if (phi_out) CU(cudaMemcpyAsync(phi_out, S.phi, g.G * es, cudaMemcpyDeviceToDevice, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return converged ? OFDFT_OK : fail(c, OFDFT_ENOTCONV, "Algorithm 1 reached %d outer iterations", p->max_outer);
+}
+
+int check_params(ofdft_ctx* c, const ofdft_params* p) {
+  if (!p) return fail(c, OFDFT_EINVAL, "params is NULL");
+  TRY(check_order(c, p->fd_order));
+  TRY(check_prec(c, p->precision));
+  if (p->method != OFDFT_METHOD_AL && p->method != OFDFT_METHOD_PENALTY)
+    return fail(c, OFDFT_EINVAL, "method must be OFDFT_METHOD_AL or OFDFT_METHOD_PENALTY");
+  if (!(p->mu0 > 0.0) || !(p->kappa > 0.0 && p->kappa < 1.0))
+    return fail(c, OFDFT_EINVAL, "Algorithm 1 needs mu0 > 0 and 0 < kappa < 1");
+  if (!(p->tol_poisson > 0.0) || p->max_cg < 1 || p->max_nlcg < 0 || p->max_outer < 1 || p->max_secant < 1)
+    return fail(c, OFDFT_EINVAL, "tolerances must be positive and iteration caps >= 1");
+  if (!(p->sigma > 0.0) || !(p->rc > 0.0)) return fail(c, OFDFT_EINVAL, "sigma and rc must be positive");
+  return OFDFT_OK;
+}
+
+}  // namespace
+
+// ===================================================================== C ABI
+extern "C" {
+
+void ofdft_default_params(ofdft_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->fd_order = 12;
+  p->terms = OFDFT_TERM_ALL;
+  p->method = OFDFT_METHOD_AL;
+  p->precision = OFDFT_PREC_FP64;
+  p->lambda = 0.2;
+  p->eta0 = -0.2;
+  p->mu0 = 1.0;
+  p->kappa = 0.1;
+  p->sigma = 1.0;
+  p->rc = 7.0;
+  p->guess_sigma = 2.0;
+  p->guess_cut = 8.0;
+  p->tol_E = 1e-6;
+  p->tol_inner = 1e-8;
+  p->tol_poisson = 1e-10;
+  p->max_outer = 30;
+  p->max_nlcg = 2000;
+  p->max_cg = 20000;
+  p->max_secant = 1;
+  p->sigma0 = 0.5;
+  p->eps_secant = 1e-7;
+  p->restart_every = 20;
+  p->force_variant = OFDFT_FORCE_PAPER;
+  p->ezz_correction = 0;
+  p->vacuum = 8.0;
+  p->round_to = 16;
+  p->refine_every = 200;
+}
+
+int ofdft_create(ofdft_ctx** out, int device, void* stream) {
+  if (!out) return OFDFT_EINVAL;
+  *out = nullptr;
+  ofdft_ctx* c = new ofdft_ctx();
+  c->device = device;
+  c->stream = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) {
+    delete c;
+    return OFDFT_ECUDA;
+  }
+  cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
+  if (cudaMalloc(&c->counter, 64) != cudaSuccess || cudaMemset(c->counter, 0, 64) != cudaSuccess ||
+      cudaMalloc(&c->sc, 2 * sizeof(CgScalars)) != cudaSuccess ||
+      cudaMalloc(&c->scal, 64 * sizeof(double)) != cudaSuccess ||
+      cudaMallocHost(&c->host_scal, 64 * sizeof(double)) != cudaSuccess) {
+    delete c;
+    return OFDFT_ENOMEM;
+  }
+  c->sc32 = c->sc + 1;
+  cudaMemset(c->sc, 0, 2 * sizeof(CgScalars));
+  cudaMemset(c->scal, 0, 64 * sizeof(double));
+  cudaDeviceSynchronize();
+  *out = c;
+  return OFDFT_OK;
+}
+
+int ofdft_destroy(ofdft_ctx* c) {
+  if (!c) return OFDFT_OK;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  cudaDeviceSynchronize();
+  harvest(c);
+  for (cudaEvent_t e : c->free_events) cudaEventDestroy(e);
+  cudaFree(c->partials.p);
+  for (auto& b : c->v) cudaFree(b.p);
+  cudaFree(c->counter);
+  cudaFree(c->sc);
+  cudaFree(c->scal);
+  cudaFreeHost(c->host_scal);
+  delete c;
+  return OFDFT_OK;
+}
+
+const char* ofdft_last_error(const ofdft_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int ofdft_profile(ofdft_ctx* c, int enable) {
+  if (!c) return OFDFT_EINVAL;
+  c->prof = enable ? 1 : 0;
+  return OFDFT_OK;
+}
+
+int ofdft_get_counters(ofdft_ctx* c, ofdft_counters* out) {
+  if (!c || !out) return OFDFT_EINVAL;
+  CU(cudaSetDevice(c->device));
+  CU(cudaStreamSynchronize(c->stream));
+  harvest(c);
+  out->launches = c->launches;
+  for (int k = 0; k < OFDFT_K_COUNT; ++k) {
+    out->kind_launches[k] = c->kind_launches[k];
+    out->timed_launches[k] = c->timed_launches[k];
+    out->timed_ms[k] = c->timed_ms[k];
+  }
+  return OFDFT_OK;
+}
+
+int ofdft_reset_counters(ofdft_ctx* c) {
+  if (!c) return OFDFT_EINVAL;
+  CU(cudaSetDevice(c->device));
+  CU(cudaStreamSynchronize(c->stream));
+  harvest(c);
+  c->launches = 0;
+  for (int k = 0; k < OFDFT_K_COUNT; ++k) {
+    c->kind_launches[k] = 0;
+    c->timed_launches[k] = 0;
+    c->timed_ms[k] = 0.0;
+  }
+  return OFDFT_OK;
+}
+
+int ofdft_grid_for_atoms(const double* R, int M, double h, double vacuum, int round_to, ofdft_grid* g) {
+  if (!R || M < 1 || !g || !(h > 0.0) || round_to < 1 || !(vacuum >= 0.0)) return OFDFT_EINVAL;
+  for (int d = 0; d < 3; ++d) {
+    double lo = R[d], hi = R[d];
+    for (int J = 1; J < M; ++J) {
+      lo = std::min(lo, R[3 * J + d]);
+      hi = std::max(hi, R[3 * J + d]);
+    }
+    if (!isfinite(lo) || !isfinite(hi)) return OFDFT_ENONFINITE;
+    lo -= vacuum;
+    hi += vacuum;
+    const double L = hi - lo;
+    long long n = (long long)ceil(L / h - 1e-9);
+    if (n < 1) n = 1;
+    n = ((n + round_to - 1) / round_to) * round_to;
+    if (n > (1 << 16)) return OFDFT_EINVAL;
+    g->n[d] = (int)n;
+    g->origin[d] = lo - 0.5 * ((double)n * h - L);
+  }
+  g->h = h;
+  return OFDFT_OK;
+}
+
+long long ofdft_workspace_bytes(const ofdft_grid* g, int fd_order, int prec) {
+  if (!g) return -1;
+  const long long G = (long long)g->n[0] * g->n[1] * g->n[2];
+  const long long es = (prec == OFDFT_PREC_MIXED) ? 4 : 8;
+  long long bytes = G * es * 14;                 // solve state, NLCG and CG vectors
+  if (prec == OFDFT_PREC_MIXED) bytes += G * 8 * 3 + G * 4;  // r64, phi64, b64, e32
+  (void)fd_order;
+  return bytes;
+}
+
+int ofdft_stencil(ofdft_ctx* c, const ofdft_grid* g, int fd_order, int prec, const void* f, void* out) {
+  if (!c) return OFDFT_EINVAL;
+  c->err.clear();
+  TRY(check_grid(c, g));
+  TRY(check_order(c, fd_order));
+  TRY(check_prec(c, prec));
+  if (!f || !out) return fail(c, OFDFT_EINVAL, "null field pointer");
+  if (f == out) return fail(c, OFDFT_EINVAL, "in-place stencil is not supported");
+  CU(cudaSetDevice(c->device));
+  const GridDev gd = gdev(g);
+  const Weights<double> W = lap_weights(fd_order / 2, g->h, 1.0);
+  if (prec == OFDFT_PREC_FP64)
+    return launch_z_r<double>(c, fd_order / 2, gd, W, LoadPlain<double>{(const double*)f}, EpiStore<double>{(double*)out}, OFDFT_K_STENCIL);
+  return launch_z_r<float>(c, fd_order / 2, gd, W, LoadPlain<float>{(const float*)f}, EpiStore<float>{(float*)out}, OFDFT_K_STENCIL);
+}
+
+int ofdft_pseudocharge(ofdft_ctx* c, const ofdft_grid* g, int fd_order, const double* R, const double* Z, int M,
+                       double sigma, double rc, int prec, void* b, double* E_self) {
+  if (!c) return OFDFT_EINVAL;
+  c->err.clear();
+  TRY(check_grid(c, g));
+  TRY(check_order(c, fd_order));
+  TRY(check_prec(c, prec));
+  TRY(check_atoms(c, R, Z, M));
+  if (!b || !E_self) return fail(c, OFDFT_EINVAL, "null output pointer");
+  if (!(sigma > 0.0) || !(rc > 0.0)) return fail(c, OFDFT_EINVAL, "sigma and rc must be positive");
+  CU(cudaSetDevice(c->device));
+  if (prec == OFDFT_PREC_FP64)
+    return device_pseudocharge<double>(c, g, fd_order / 2, R, Z, M, sigma, rc, (double*)b, E_self);
+  return device_pseudocharge<float>(c, g, fd_order / 2, R, Z, M, sigma, rc, (float*)b, E_self);
+}
+
+int ofdft_initial_guess(ofdft_ctx* c, const ofdft_grid* g, const double* R, const double* Z, int M,
+                        double guess_sigma, double guess_cut, double N, int prec, void* u) {
+  if (!c) return OFDFT_EINVAL;
+  c->err.clear();
+  TRY(check_grid(c, g));
+  TRY(check_prec(c, prec));
+  TRY(check_atoms(c, R, Z, M));
+  if (!u) return fail(c, OFDFT_EINVAL, "null output pointer");
+  if (!(guess_sigma > 0.0) || !(guess_cut > 0.0) || !(N > 0.0)) return fail(c, OFDFT_EINVAL, "bad guess parameters");
+  CU(cudaSetDevice(c->device));
+  if (prec == OFDFT_PREC_FP64) return device_guess<double>(c, g, R, Z, M, guess_sigma, guess_cut, N, (double*)u);
+  return device_guess<float>(c, g, R, Z, M, guess_sigma, guess_cut, N, (float*)u);
+}
+
+int ofdft_poisson(ofdft_ctx* c, const ofdft_grid* g, int fd_order, int prec, const void* rho, const void* u,
+                  const void* b, void* phi, double tol, int max_it, ofdft_cg_stats* st) {
+  if (!c) return OFDFT_EINVAL;
+  c->err.clear();
+  TRY(check_grid(c, g));
+  TRY(check_order(c, fd_order));
+  TRY(check_prec(c, prec));
+  if (!phi || (!rho && (!u || !b))) return fail(c, OFDFT_EINVAL, "need phi and either rho or (u, b)");
+  if (!(tol > 0.0) || max_it < 0) return fail(c, OFDFT_EINVAL, "need tol > 0 and max_it >= 0");
+  CU(cudaSetDevice(c->device));
+  const GridDev gd = gdev(g);
+  ofdft_cg_stats tmp;
+  if (!st) st = &tmp;
+  if (prec == OFDFT_PREC_FP64)
+    return poisson_fp64(c, fd_order / 2, gd, g->h, (const double*)rho, (const double*)u, (const double*)b,
+                        (double*)phi, tol, max_it, st);
+  // mixed: FP64 copies of b and phi live in the context for the call
+  TRY(ensure(c, c->v[V_PHI64], gd.G * sizeof(double)));
+  TRY(ensure(c, c->v[V_B64], gd.G * sizeof(double)));
+  const int pb = pointwise_blocks(c, gd.G);
+  {
+    ProfScope ps_(c, OFDFT_K_VECTOR);
+    convert_kernel<float, double><<<pb, 256, 0, c->stream>>>(gd.G, vec<double>(c, V_PHI64), (const float*)phi);
+  }
+  if (!rho) {
+    ProfScope ps_(c, OFDFT_K_VECTOR);
+    convert_kernel<float, double><<<pb, 256, 0, c->stream>>>(gd.G, vec<double>(c, V_B64), (const float*)b);
+  }
+  CU(cudaGetLastError());
+  ofdft_params dp;
+  ofdft_default_params(&dp);
+  return poisson_mixed(c, fd_order / 2, gd, g->h, (const float*)rho, (const float*)u, vec<double>(c, V_B64),
+                       vec<double>(c, V_PHI64), (float*)phi, tol, max_it, dp.refine_every, st);
+}
+
+int ofdft_energy_grad(ofdft_ctx* c, const ofdft_grid* g, const ofdft_params* p, const void* u, const void* b,
+                      void* phi, double E_self, double eta, double mu, double N, int solve_poisson, void* grad,
+                      void* s, const void* d, const void* s_old, ofdft_energy* out) {
+  if (!c) return OFDFT_EINVAL;
+  c->err.clear();
+  TRY(check_grid(c, g));
+  TRY(check_params(c, p));
+  if (!u || !out || ((p->terms & OFDFT_TERM_ES) && (!b || !phi))) return fail(c, OFDFT_EINVAL, "null pointer");
+  if (!(mu > 0.0) || !isfinite(eta) || !isfinite(N)) return fail(c, OFDFT_EINVAL, "need mu > 0, finite eta and N");
+  CU(cudaSetDevice(c->device));
+  const GridDev gd = gdev(g);
+  const int R = p->fd_order / 2;
+  const bool mixed = p->precision == OFDFT_PREC_MIXED;
+  const bool es = p->terms & OFDFT_TERM_ES;
+  memset(out, 0, sizeof(*out));
+  ofdft_cg_stats cs{0, 0.0};
+  const double* sum_uu = &c->sc->sum_uu;
+  TRY(ensure_cg_vectors(c, gd.G, mixed ? 4 : 8, mixed));
+  if (es) {
+    if (!mixed) {
+      // residual at the incoming phi (and CG if asked): gives r for the energy and sum u^2
+      const int rc = poisson_fp64(c, R, gd, g->h, nullptr, (const double*)u, (const double*)b, (double*)phi,
+                                  p->tol_poisson, solve_poisson ? p->max_cg : 0, &cs);
+      if (rc != OFDFT_OK && !(rc == OFDFT_ENOTCONV && !solve_poisson)) return rc;
+      c->err.clear();
+    } else {
+      TRY(ensure(c, c->v[V_PHI64], gd.G * sizeof(double)));
+      TRY(ensure(c, c->v[V_B64], gd.G * sizeof(double)));
+      const int pb = pointwise_blocks(c, gd.G);
+      {
+        ProfScope ps_(c, OFDFT_K_VECTOR);
+        convert_kernel<float, double><<<pb, 256, 0, c->stream>>>(gd.G, vec<double>(c, V_PHI64), (const float*)phi);
+      }
+      {
+        ProfScope ps_(c, OFDFT_K_VECTOR);
+        convert_kernel<float, double><<<pb, 256, 0, c->stream>>>(gd.G, vec<double>(c, V_B64), (const float*)b);
+      }
+      CU(cudaGetLastError());
+      int rc = poisson_mixed(c, R, gd, g->h, nullptr, (const float*)u, vec<double>(c, V_B64), vec<double>(c, V_PHI64),
+                             (float*)phi, p->tol_poisson, solve_poisson ? p->max_cg : 0, std::max(p->refine_every, 1),
+                             &cs);
+      if (rc != OFDFT_OK && !(rc == OFDFT_ENOTCONV && !solve_poisson)) return rc;
+      c->err.clear();
+      {
+        ProfScope ps_(c, OFDFT_K_VECTOR);
+        convert_kernel<double, float><<<pb, 256, 0, c->stream>>>(gd.G, vec<float>(c, V_R), vec<double>(c, V_R64));
+      }
+      CU(cudaGetLastError());
+    }
+  } else {
+    const int pb = pointwise_blocks(c, gd.G);
+    TRY(ensure_partials(c, pb, 2));
+    if (mixed)
+      {
+        ProfScope ps_(c, OFDFT_K_VECTOR);
+        dot2_kernel<float><<<pb, 256, 0, c->stream>>>(gd.G, (const float*)u, (const float*)u, nullptr, nullptr, c->scal + 16, red(c));
+      }
+    else
+      {
+        ProfScope ps_(c, OFDFT_K_VECTOR);
+        dot2_kernel<double><<<pb, 256, 0, c->stream>>>(gd.G, (const double*)u, (const double*)u, nullptr, nullptr, c->scal + 16, red(c));
+      }
+    CU(cudaGetLastError());
+    sum_uu = c->scal + 16;
+  }
+  EvalOut o;
+  if (!mixed)
+    TRY(functional_pass<double>(c, R, gd, g->h, p, (const double*)u, (const double*)b, (const double*)phi,
+                                es ? vec<double>(c, V_R) : nullptr, eta, mu, N, sum_uu, (double*)grad, (double*)s,
+                                (const double*)d, (const double*)s_old, &o));
+  else
+    TRY(functional_pass<float>(c, R, gd, g->h, p, (const float*)u, (const float*)b, (const float*)phi,
+                               es ? vec<float>(c, V_R) : nullptr, eta, mu, N, sum_uu, (float*)grad, (float*)s,
+                               (const float*)d, (const float*)s_old, &o));
+  fill_energy(o, g->h, p, E_self, 0.0, eta, mu, out);
+  out->poisson = cs;
+  if (!isfinite(out->L)) return fail(c, OFDFT_ENONFINITE, "augmented Lagrangian is not finite");
+  return OFDFT_OK;
+}
+
+int ofdft_forces(ofdft_ctx* c, const ofdft_grid* g, int fd_order, const double* R, const double* Z, int M,
+                 double sigma, double rc, int variant, int prec, const void* phi, double* F) {
+  if (!c) return OFDFT_EINVAL;
+  c->err.clear();
+  TRY(check_grid(c, g));
+  TRY(check_order(c, fd_order));
+  TRY(check_prec(c, prec));
+  TRY(check_atoms(c, R, Z, M));
+  if (!phi || !F) return fail(c, OFDFT_EINVAL, "null pointer");
+  if (variant != OFDFT_FORCE_PAPER && variant != OFDFT_FORCE_EXACT) return fail(c, OFDFT_EINVAL, "bad force variant");
+  CU(cudaSetDevice(c->device));
+  if (prec == OFDFT_PREC_FP64)
+    return device_forces<double>(c, g, fd_order / 2, R, Z, M, sigma, rc, variant, (const double*)phi, F);
+  return device_forces<float>(c, g, fd_order / 2, R, Z, M, sigma, rc, variant, (const float*)phi, F);
+}
+
+int ofdft_solve(ofdft_ctx* c, const ofdft_grid* grid, const double* R, const double* Z, int M, double h,
+                const ofdft_params* p, void* u_out, void* phi_out, double* energy, double* forces,
+                ofdft_solve_stats* st) {
+  if (!c) return OFDFT_EINVAL;
+  c->err.clear();
+  TRY(check_params(c, p));
+  TRY(check_atoms(c, R, Z, M));
+  if (!energy) return fail(c, OFDFT_EINVAL, "energy pointer is NULL");
+  ofdft_solve_stats tmp;
+  if (!st) st = &tmp;
+  memset(st, 0, sizeof(*st));
+  ofdft_grid g;
+  if (grid) {
+    g = *grid;
+  } else {
+    const int rc = ofdft_grid_for_atoms(R, M, h, p->vacuum, p->round_to > 0 ? p->round_to : 1, &g);
+    if (rc != OFDFT_OK) return fail(c, rc, "box rule failed for h=%g vacuum=%g", h, p->vacuum);
+  }
+  TRY(check_grid(c, &g));
+  CU(cudaSetDevice(c->device));
+  if (p->precision == OFDFT_PREC_FP64) return solve_impl<double>(c, &g, R, Z, M, p, u_out, phi_out, energy, forces, st);
+  return solve_impl<float>(c, &g, R, Z, M, p, u_out, phi_out, energy, forces, st);
+}
+
+}  // extern "C"

@@ -1,0 +1,773 @@
+// CUDA kernels of the library (sm_103a).  Every stencil-shaped pass of the
+// method (S2 stencil, S3 CG, S4 fused functional) is one instance of the
+// z-streaming kernel below with its own loader (what the stencil is applied to)
+// and epilogue (what is done with the result at each node).
+#pragma once
+
+#include <math.h>
+
+#include "common.cuh"
+
+namespace ofd {
+
+constexpr int BX = 32;  // threads along x (one warp per row)
+constexpr int BY = 8;   // rows per block
+constexpr int NT = BX * BY;
+
+// ---------------------------------------------------------------------------
+// Device scalars of one CG solve (S3).  Written only by the last block of a
+// reduction, read by every thread of the next kernel.
+struct CgScalars {
+  double rr;      // r.r of the current residual
+  double bb;      // ||4 pi rho||^2
+  double pAp;     // p.(A p)
+  double alpha;   // rr / pAp
+  double beta;    // rr_new / rr
+  double tol2;    // tol^2 (relative, squared)
+  double sum_uu;  // sum u^2 (from the residual pass, for C_h)
+  double rr0;     // rr at the start of the solve
+  int iters;      // CG iterations done
+  int max_it;
+  int done;       // 1 once converged or out of iterations
+  int first;      // 1 until the first search direction is formed
+};
+
+// ---------------------------------------------------------------------------
+// z-streaming radius-R star stencil (Sec. 4, Eq. FD:Laplacian).
+//
+// A block owns a BX x BY column of nodes and a z-range [z0, z1).  It walks the
+// range one plane at a time: the plane (with an R-wide x/y halo) is staged in
+// shared memory, the 2R+1 values of the block's own column along z live in a
+// register queue, so every node's 6R neighbours come from shared memory or
+// registers.  Every index outside the grid reads 0 (zero Dirichlet, Sec. 4).
+//
+// Loader: T value(idx) (pure; used for halo nodes and for nodes of other
+//         z-ranges) and T own(idx) (called once per node of this block's range;
+//         may store a side product, e.g. the new CG direction).
+// Epi:    static constexpr int K (number of FP64 partial sums), bool skip(),
+//         void apply(idx, centre, lap, acc[K]), and fin(sums[K]) run once by
+//         the last block.
+template <typename T, int R, class Loader, class Epi>
+__global__ void __launch_bounds__(NT) zstream_kernel(GridDev g, Weights<T> W, int zchunk,
+                                                     Loader ld, Epi ep, RedBuf red) {
+  if (ep.skip()) return;
+  __shared__ T s[BY + 2 * R][BX + 2 * R];
+  __shared__ double red_smem[(Epi::K > 0 ? Epi::K : 1) * (NT / 32)];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * BX + tx;
+  const int x = blockIdx.x * BX + tx, y = blockIdx.y * BY + ty;
+  const int z0 = blockIdx.z * zchunk;
+  const int z1 = min(z0 + zchunk, g.n3);
+  const bool in_xy = (x < g.n1) && (y < g.n2);
+  const long long col = (long long)x + (long long)g.n1 * y;
+  const long long plane = (long long)g.n1 * g.n2;
+
+  T q[2 * R + 1];
+#pragma unroll
+  for (int i = 0; i < 2 * R; ++i) {
+    const int k = z0 - R + i;
+    q[i] = (in_xy && k >= 0 && k < g.n3) ? ((k >= z0 && k < z1) ? ld.own(col + plane * k)
+                                                                  : ld.value(col + plane * k))
+                                         : T(0);
+  }
+  double acc[Epi::K > 0 ? Epi::K : 1];
+#pragma unroll
+  for (int i = 0; i < (Epi::K > 0 ? Epi::K : 1); ++i) acc[i] = 0.0;
+
+  // halo coordinates of this thread (x-halo for tx < R, y-halo for ty < R)
+  const int xl = blockIdx.x * BX - R + tx, xr = blockIdx.x * BX + BX + tx;
+  const int yb = blockIdx.y * BY - R + ty, yt = blockIdx.y * BY + BY + ty;
+  const bool yok = y < g.n2, xok = x < g.n1;
+
+  for (int k = z0; k < z1; ++k) {
+    const int kf = k + R;
+    q[2 * R] = (in_xy && kf < g.n3) ? ((kf < z1) ? ld.own(col + plane * kf)
+                                                : ld.value(col + plane * kf))
+                                    : T(0);
+    __syncthreads();
+    s[ty + R][tx + R] = q[R];
+    const long long pk = plane * k;
+    if (tx < R) {
+      s[ty + R][tx] = (yok && xl >= 0) ? ld.value(pk + (long long)g.n1 * y + xl) : T(0);
+      s[ty + R][tx + BX + R] = (yok && xr < g.n1) ? ld.value(pk + (long long)g.n1 * y + xr) : T(0);
+    }
+    if (ty < R) {
+      s[ty][tx + R] = (xok && yb >= 0) ? ld.value(pk + (long long)g.n1 * yb + x) : T(0);
+      s[ty + BY + R][tx + R] = (xok && yt < g.n2) ? ld.value(pk + (long long)g.n1 * yt + x) : T(0);
+    }
+    __syncthreads();
+    if (in_xy) {
+      T lap = W.c * q[R];
+#pragma unroll
+      for (int p = 1; p <= R; ++p) {
+        const T sx = s[ty + R][tx + R + p] + s[ty + R][tx + R - p];
+        const T sy = s[ty + R + p][tx + R] + s[ty + R - p][tx + R];
+        const T sz = q[R + p] + q[R - p];
+        lap = fma(W.w[p], (sx + sy) + sz, lap);
+      }
+      ep.apply(col + pk, q[R], lap, acc);
+    }
+#pragma unroll
+    for (int i = 0; i < 2 * R; ++i) q[i] = q[i + 1];
+  }
+  if constexpr (Epi::K > 0) {
+    const int nblocks = gridDim.x * gridDim.y * gridDim.z;
+    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    grid_sum<Epi::K, NT>(acc, red_smem, red, nblocks, bid, tid, ep);
+  }
+}
+
+// ----------------------------------------------------------------- loaders --
+template <typename T>
+struct LoadPlain {
+  const T* f;
+  __device__ __forceinline__ T value(long long i) const { return f[i]; }
+  __device__ __forceinline__ T own(long long i) const { return f[i]; }
+};
+
+// CG search direction p = r + beta p_prev formed on the fly (S3).  p_prev is
+// only read: the new direction goes to a second buffer (other blocks still read
+// p_prev in their halos while this block writes).
+template <typename T>
+struct LoadCgDir {
+  const T* r;
+  const T* p_prev;
+  const CgScalars* sc;
+  __device__ __forceinline__ T value(long long i) const {
+    if (sc->first) return r[i];
+    return fma((T)sc->beta, p_prev[i], r[i]);
+  }
+  __device__ __forceinline__ T own(long long i) const { return value(i); }
+};
+
+// ---------------------------------------------------------------- epilogues --
+// out = lap (S2).
+template <typename T>
+struct EpiStore {
+  static constexpr int K = 0;
+  T* out;
+  __device__ __forceinline__ bool skip() const { return false; }
+  __device__ __forceinline__ void apply(long long i, T, T lap, double*) const { out[i] = lap; }
+  __device__ __forceinline__ void operator()(double*) const {}
+};
+
+// CG step, first half (S3): Ap = (-L_h) p with p formed by LoadCgDir; writes p
+// and Ap, reduces p.Ap, and alpha = rr / pAp.  The weights carry the minus sign.
+template <typename T>
+struct EpiCgA {
+  static constexpr int K = 1;
+  T* p;
+  T* Ap;
+  CgScalars* sc;
+  __device__ __forceinline__ bool skip() const { return sc->done != 0; }
+  __device__ __forceinline__ void apply(long long i, T pc, T ap, double* acc) const {
+    p[i] = pc;
+    Ap[i] = ap;
+    acc[0] += (double)pc * (double)ap;
+  }
+  __device__ __forceinline__ void operator()(double* t) const {
+    sc->pAp = t[0];
+    sc->alpha = (t[0] != 0.0) ? sc->rr / t[0] : 0.0;
+    sc->first = 0;
+  }
+};
+
+// Initial residual of a Poisson solve (S3, S5): rhs = 4 pi rho with
+// rho = rho_in or u^2 + b; r = rhs + L_h phi (= rhs - (-L_h) phi); reduces
+// sum u^2 (for C_h), ||rhs||^2 and ||r||^2 and sets up the CG scalars.
+template <typename T, typename U = T, typename V = U>
+struct EpiResidual {
+  static constexpr int K = 3;
+  const U* rho;
+  const U* u;
+  const V* b;
+  T* r;
+  CgScalars* sc;
+  double tol;
+  int max_it;
+  int want_r;
+  __device__ __forceinline__ bool skip() const { return false; }
+  __device__ __forceinline__ void apply(long long i, T, T lap, double* acc) const {
+    T uu = T(0);
+    if (u) {
+      const T ui = (T)u[i];
+      uu = ui * ui;
+      acc[0] += (double)ui * (double)ui;
+    }
+    if (want_r) {
+      const T rh = (T)(4.0 * kPi) * (rho ? (T)rho[i] : uu + (T)b[i]);
+      const T ri = rh + lap;
+      r[i] = ri;
+      acc[1] += (double)rh * (double)rh;
+      acc[2] += (double)ri * (double)ri;
+    }
+  }
+  __device__ __forceinline__ void operator()(double* t) const {
+    sc->sum_uu = t[0];
+    sc->bb = t[1];
+    sc->rr = t[2];
+    sc->rr0 = t[2];
+    sc->tol2 = tol * tol;
+    sc->iters = 0;
+    sc->max_it = max_it;
+    sc->first = 1;
+    sc->beta = 0.0;
+    const double thr = tol * tol * (t[1] > 0.0 ? t[1] : 1.0);
+    sc->done = (!want_r || t[2] <= thr || max_it <= 0) ? 1 : 0;
+  }
+};
+
+// ------------------------------------------------------------- functional ---
+// LDA exchange-correlation of Sec. 2 / Sec. 3 (Ceperley-Alder form), density
+// floor u^2 < 1e-30 -> 0.
+template <typename T>
+__device__ __forceinline__ void xc_eval(T u, T& eps, T& v) {
+  const T rho = u * u;
+  if (!(rho >= (T)1e-30)) {
+    eps = T(0);
+    v = T(0);
+    return;
+  }
+  const T g1 = (T)-0.1423, b1 = (T)1.0529, b2 = (T)0.3334;
+  const T A1 = (T)0.0311, B1 = (T)-0.048, C1 = (T)0.002, D1 = (T)-0.0116;
+  const T c3pi = (T)0.98474502184269641;  // (3/pi)^{1/3}
+  const T rho13 = cbrt(rho);
+  const T ex = (T)-0.75 * c3pi * rho13;
+  const T vx = -c3pi * rho13;
+  const T rs = (T)0.62035049089940009 / rho13;  // (3/(4 pi))^{1/3} / rho^{1/3}
+  T ec, vc;
+  if (rs >= T(1)) {
+    const T srs = sqrt(rs);
+    const T den = T(1) + b1 * srs + b2 * rs;
+    ec = g1 / den;
+    vc = (g1 + (T)(7.0 / 6.0) * g1 * b1 * srs + (T)(4.0 / 3.0) * g1 * b2 * rs) / (den * den);
+  } else {
+    const T lr = log(rs);
+    ec = A1 * lr + B1 + C1 * rs * lr + D1 * rs;
+    vc = (A1 + (T)(2.0 / 3.0) * C1 * rs) * lr + (B1 - A1 / T(3)) + (T)(1.0 / 3.0) * (T(2) * D1 - C1) * rs;
+  }
+  eps = ex + ec;
+  v = vx + vc;
+}
+
+struct FuncScalars {
+  double h3, N, eta, inv_mu, lambda, CF, kin_vw;
+  int terms;
+};
+
+// Fused energy + gradient pass (S4): lap = L_h u from the stencil, then at each
+// node the TF, vW, XC and electrostatic energy densities, the gradient
+//   G = -lambda L_h u + 2 (V_K + V_xc + phi) u + 2 (-eta + C/mu) u,
+// the Jacobi diagonal and s = -G / diag, and nine FP64 partial sums.
+template <typename T>
+struct EpiFunctional {
+  static constexpr int K = 9;
+  const T* phi;
+  const T* b;
+  const T* rcg;
+  const T* d;
+  const T* s_old;
+  T* G;
+  T* s;
+  const double* sum_uu;  // device sum of u^2 (C_h = h^3 sum_uu - N)
+  FuncScalars f;
+  double* out;  // 9 sums + C
+  __device__ __forceinline__ bool skip() const { return false; }
+  __device__ __forceinline__ void apply(long long i, T uc, T lap, double* acc) const {
+    const double C = f.h3 * *sum_uu - f.N;
+    const T mult = (T)(-f.eta + C * f.inv_mu);
+    const bool tf = f.terms & 1, vw = f.terms & 2, xc = f.terms & 4, es = f.terms & 8;
+    const T ux = fabs(uc);
+    T vk = T(0), vxc = T(0), exc = T(0), ph = T(0);
+    if (tf) {
+      const T c = cbrt(ux);
+      const T u43 = (c * c) * (c * c);
+      vk = (T)(5.0 / 3.0 * f.CF) * u43;
+      acc[0] += f.CF * (double)u43 * (double)ux * (double)ux;
+    }
+    if (vw) acc[1] += (double)uc * (double)lap;
+    if (xc) {
+      xc_eval<T>(ux, exc, vxc);
+      acc[2] += (double)exc * (double)ux * (double)ux;
+    }
+    if (es) {
+      ph = phi[i];
+      const T rho = uc * uc + b[i];
+      acc[3] += (double)rho * (double)ph;
+      if (rcg) acc[4] += (double)ph * (double)rcg[i];
+    }
+    const T gx = (vw ? (T)(-f.lambda) * lap : T(0)) + T(2) * (vk + vxc + ph) * uc + T(2) * mult * uc;
+    const T kin = (vw ? (T)f.kin_vw : T(0)) + (T)(14.0 / 3.0) * vk;
+    T md = kin + T(2) * (vxc + ph + mult);
+    md = fmax(md, (T)0.25 * kin);
+    md = fmax(md, (T)1e-10);
+    const T sx = -gx / md;
+    if (G) G[i] = gx;
+    if (s) s[i] = sx;
+    if (d) acc[5] += (double)gx * (double)d[i];
+    if (s_old) acc[6] += (double)gx * (double)s_old[i];
+    acc[7] += (double)gx * (double)gx / (double)md;
+    acc[8] += (double)gx * (double)gx;
+  }
+  __device__ __forceinline__ void operator()(double* t) const {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) out[k] = t[k];
+    out[9] = f.h3 * *sum_uu - f.N;
+  }
+};
+
+// ------------------------------------------------------- CG second half ---
+// phi += alpha p, r -= alpha Ap, reduces r.r; the last block sets beta, counts
+// the iteration and raises `done` at convergence or at the iteration cap.
+template <typename T>
+__global__ void __launch_bounds__(256) cg_update_kernel(long long G, T* __restrict__ phi,
+                                                        T* __restrict__ r, const T* __restrict__ p,
+                                                        const T* __restrict__ Ap, CgScalars* sc,
+                                                        RedBuf red) {
+  if (sc->done) return;
+  __shared__ double smem[256 / 32];
+  const T alpha = (T)sc->alpha;
+  double acc[1] = {0.0};
+  for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < G; i += (long long)gridDim.x * 256) {
+    const T pi = p[i], api = Ap[i];
+    phi[i] = fma(alpha, pi, phi[i]);
+    const T ri = fma(-alpha, api, r[i]);
+    r[i] = ri;
+    acc[0] += (double)ri * (double)ri;
+  }
+  struct Fin {
+    CgScalars* sc;
+    __device__ void operator()(double* t) const {
+      const double rr_new = t[0];
+      sc->beta = (sc->rr != 0.0) ? rr_new / sc->rr : 0.0;
+      sc->rr = rr_new;
+      sc->iters += 1;
+      const double thr = sc->tol2 * (sc->bb > 0.0 ? sc->bb : 1.0);
+      if (rr_new <= thr || sc->iters >= sc->max_it || !(rr_new == rr_new)) sc->done = 1;
+    }
+  } fin{sc};
+  grid_sum<1, 256>(acc, smem, red, gridDim.x, blockIdx.x, threadIdx.x, fin);
+}
+
+// ----------------------------------------------------------- vector ops ---
+// out = |a + alpha b| (trial point and secant update of Sec. 4, u <- |u|).
+template <typename T>
+__global__ void __launch_bounds__(256) axpy_abs_kernel(long long G, T* out, const T* a, const T* b,
+                                                       double alpha) {
+  const T al = (T)alpha;
+  for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < G; i += (long long)gridDim.x * 256)
+    out[i] = fabs(fma(al, b[i], a[i]));
+}
+
+// d = s + beta d (Polak-Ribiere direction), or d = s when beta == 0.
+template <typename T>
+__global__ void __launch_bounds__(256) direction_kernel(long long G, T* d, const T* s, double beta) {
+  const T be = (T)beta;
+  for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < G; i += (long long)gridDim.x * 256)
+    d[i] = (beta == 0.0) ? s[i] : fma(be, d[i], s[i]);
+}
+
+// out[0] = a.b, out[1] = c.e (FP64 accumulation; c may be NULL).
+template <typename T>
+__global__ void __launch_bounds__(256) dot2_kernel(long long G, const T* a, const T* b, const T* c,
+                                                   const T* e, double* out, RedBuf red) {
+  __shared__ double smem[2 * (256 / 32)];
+  double acc[2] = {0.0, 0.0};
+  for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < G; i += (long long)gridDim.x * 256) {
+    acc[0] += (double)a[i] * (double)b[i];
+    if (c) acc[1] += (double)c[i] * (double)e[i];
+  }
+  struct Fin {
+    double* out;
+    __device__ void operator()(double* t) const {
+      out[0] = t[0];
+      out[1] = t[1];
+    }
+  } fin{out};
+  grid_sum<2, 256>(acc, smem, red, gridDim.x, blockIdx.x, threadIdx.x, fin);
+}
+
+// u *= scale where scale = sqrt(N / (h^3 sum)) from the device sum (initial guess).
+template <typename T>
+__global__ void __launch_bounds__(256) normalise_kernel(long long G, T* u, const double* sum, double h3,
+                                                        double N) {
+  const double sc = (*sum > 0.0) ? sqrt(N / (h3 * *sum)) : 0.0;
+  for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < G; i += (long long)gridDim.x * 256)
+    u[i] = (T)(sc * (double)u[i]);
+}
+
+// Start of an FP32 correction solve A e = r (iterative refinement of a mixed
+// Poisson solve): r32 = (float) r64, e = 0, and CG scalars relative to ||r32||.
+__global__ void __launch_bounds__(256) refine_init_kernel(long long G, float* r32, float* e,
+                                                          const double* r64, CgScalars* sc,
+                                                          double tol, int max_it, RedBuf red) {
+  __shared__ double smem[256 / 32];
+  double acc[1] = {0.0};
+  for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < G; i += (long long)gridDim.x * 256) {
+    const float v = (float)r64[i];
+    r32[i] = v;
+    e[i] = 0.0f;
+    acc[0] += (double)v * (double)v;
+  }
+  struct Fin {
+    CgScalars* sc;
+    double tol;
+    int max_it;
+    __device__ void operator()(double* t) const {
+      sc->rr = t[0];
+      sc->rr0 = t[0];
+      sc->bb = t[0];
+      sc->tol2 = tol * tol;
+      sc->iters = 0;
+      sc->max_it = max_it;
+      sc->first = 1;
+      sc->beta = 0.0;
+      sc->done = (t[0] == 0.0 || max_it <= 0) ? 1 : 0;
+    }
+  } fin{sc, tol, max_it};
+  grid_sum<1, 256>(acc, smem, red, gridDim.x, blockIdx.x, threadIdx.x, fin);
+}
+
+// phi64 += e (apply an FP32 correction to the FP64 potential) and phi32 = (float) phi64.
+__global__ void __launch_bounds__(256) refine_apply_kernel(long long G, double* phi64, float* phi32,
+                                                           const float* e) {
+  for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < G; i += (long long)gridDim.x * 256) {
+    const double v = phi64[i] + (double)e[i];
+    phi64[i] = v;
+    phi32[i] = (float)v;
+  }
+}
+
+template <typename S, typename D>
+__global__ void __launch_bounds__(256) convert_kernel(long long G, D* out, const S* in) {
+  for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < G; i += (long long)gridDim.x * 256)
+    out[i] = (D)in[i];
+}
+
+// ------------------------------------------------------------ atom kernels --
+// Node-to-atom offsets and distances computed with explicitly rounded IEEE
+// operations (no FMA contraction), so that every "is this node inside the
+// ball" decision is taken exactly as plain FP64 arithmetic takes it.
+__device__ __forceinline__ double node_off(double origin, int i, double h, double Ra) {
+  return __dsub_rn(__dadd_rn(origin, __dmul_rn(__dadd_rn((double)i, 0.5), h)), Ra);
+}
+__device__ __forceinline__ double dist3(double x, double y, double z) {
+  return __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z)));
+}
+__device__ __forceinline__ double dist3_sq(double x, double y, double z) {
+  return __dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z));
+}
+
+// Gaussian nucleus V(r) = -Z erf(r/sigma)/r and its r -> 0 limit.
+__device__ __forceinline__ double gauss_v(double Z, double inv_sigma, double r) {
+  if (r < 1e-12 / inv_sigma) return -2.0 * Z * inv_sigma * 0.56418958354775628;  // 1/sqrt(pi)
+  return -Z * erf(r * inv_sigma) / r;
+}
+
+struct AtomArgs {
+  const double* R;  // M x 3
+  const double* Z;  // M
+  int M;
+  double h, ox, oy, oz;  // spacing and origin
+  double sigma, rc;
+};
+
+constexpr int AT = 8;  // atom-kernel tile edge (AT^3 = 512 threads)
+
+// Ordered list (in atom order) of the atoms of [a0, a0+512) whose ball of radius
+// `reach` meets the tile's box; returns the count.  Deterministic order.
+__device__ __forceinline__ int tile_atoms(const AtomArgs& A, int a0, double cx, double cy, double cz,
+                                          double half, double reach, int* list, int* warp_cnt) {
+  const int tid = threadIdx.x + AT * (threadIdx.y + AT * threadIdx.z);
+  const int lane = tid & 31, warp = tid >> 5;
+  const int a = a0 + tid;
+  bool hit = false;
+  if (a < A.M) {
+    const double dx = fmax(fabs(A.R[3 * a] - cx) - half, 0.0);
+    const double dy = fmax(fabs(A.R[3 * a + 1] - cy) - half, 0.0);
+    const double dz = fmax(fabs(A.R[3 * a + 2] - cz) - half, 0.0);
+    hit = dx * dx + dy * dy + dz * dz < reach * reach;
+  }
+  const unsigned m = __ballot_sync(0xffffffffu, hit);
+  if (lane == 0) warp_cnt[warp] = __popc(m);
+  __syncthreads();
+  int off = 0, total = 0;
+  for (int w = 0; w < 16; ++w) {
+    if (w < warp) off += warp_cnt[w];
+    total += warp_cnt[w];
+  }
+  if (hit) list[off + __popc(m & ((1u << lane) - 1u))] = a;
+  __syncthreads();
+  return total;
+}
+
+// b = sum_J -(1/4 pi) L_h V_J inside r_c (Sec. 4) and the self-energy partial
+// sums (1/2) h^3 b_J V_J, gathered per node over the atoms near its tile.
+template <typename T, int R>
+__global__ void __launch_bounds__(512) pseudocharge_kernel(GridDev g, AtomArgs A, Weights<double> W,
+                                                           T* b, double* es_out, RedBuf red) {
+  __shared__ int list[512];
+  __shared__ int warp_cnt[16];
+  __shared__ double smem[512 / 32];
+  const int x = blockIdx.x * AT + threadIdx.x, y = blockIdx.y * AT + threadIdx.y,
+            z = blockIdx.z * AT + threadIdx.z;
+  const int tid = threadIdx.x + AT * (threadIdx.y + AT * threadIdx.z);
+  const bool inside = x < g.n1 && y < g.n2 && z < g.n3;
+  const double half = 0.5 * AT * A.h;
+  const double cx = A.ox + (blockIdx.x * AT) * A.h + half, cy = A.oy + (blockIdx.y * AT) * A.h + half,
+               cz = A.oz + (blockIdx.z * AT) * A.h + half;
+  const double inv_s = 1.0 / A.sigma;
+  double bsum = 0.0, es = 0.0;
+  for (int a0 = 0; a0 < A.M; a0 += 512) {
+    const int cnt = tile_atoms(A, a0, cx, cy, cz, half, A.rc + A.h, list, warp_cnt);
+    if (inside) {
+      for (int t = 0; t < cnt; ++t) {
+        const int J = list[t];
+        const double rx = node_off(A.ox, x, A.h, A.R[3 * J]), ry = node_off(A.oy, y, A.h, A.R[3 * J + 1]),
+                     rz = node_off(A.oz, z, A.h, A.R[3 * J + 2]);
+        const double r = dist3(rx, ry, rz);
+        if (!(r < A.rc)) continue;
+        const double ZJ = A.Z[J];
+        const double vc = gauss_v(ZJ, inv_s, r);
+        double lap = W.c * vc;
+#pragma unroll
+        for (int p = 1; p <= R; ++p) {
+          const double ph = p * A.h;
+          double sum = 0.0;
+          sum += gauss_v(ZJ, inv_s, sqrt((rx + ph) * (rx + ph) + ry * ry + rz * rz));
+          sum += gauss_v(ZJ, inv_s, sqrt((rx - ph) * (rx - ph) + ry * ry + rz * rz));
+          sum += gauss_v(ZJ, inv_s, sqrt(rx * rx + (ry + ph) * (ry + ph) + rz * rz));
+          sum += gauss_v(ZJ, inv_s, sqrt(rx * rx + (ry - ph) * (ry - ph) + rz * rz));
+          sum += gauss_v(ZJ, inv_s, sqrt(rx * rx + ry * ry + (rz + ph) * (rz + ph)));
+          sum += gauss_v(ZJ, inv_s, sqrt(rx * rx + ry * ry + (rz - ph) * (rz - ph)));
+          lap = fma(W.w[p], sum, lap);
+        }
+        const double bj = -lap / (4.0 * kPi);
+        bsum += bj;
+        es += bj * vc;
+      }
+    }
+    __syncthreads();
+  }
+  if (inside) b[lin(g, x, y, z)] = (T)bsum;
+  double acc[1] = {es};
+  struct Fin {
+    double* out;
+    __device__ void operator()(double* t) const { out[0] = t[0]; }
+  } fin{es_out};
+  const int nb = gridDim.x * gridDim.y * gridDim.z;
+  const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  grid_sum<1, 512>(acc, smem, red, nb, bid, tid, fin);
+}
+
+// rho_0 = sum_J Z_J (2 pi s^2)^{-3/2} exp(-r^2/(2 s^2)) (r < cut); writes
+// sqrt(rho_0) and reduces sum rho_0 (starting guess, Sec. 4).
+template <typename T>
+__global__ void __launch_bounds__(512) guess_kernel(GridDev g, AtomArgs A, double gsig, double gcut,
+                                                    T* u, double* sum_out, RedBuf red) {
+  __shared__ int list[512];
+  __shared__ int warp_cnt[16];
+  __shared__ double smem[512 / 32];
+  const int x = blockIdx.x * AT + threadIdx.x, y = blockIdx.y * AT + threadIdx.y,
+            z = blockIdx.z * AT + threadIdx.z;
+  const int tid = threadIdx.x + AT * (threadIdx.y + AT * threadIdx.z);
+  const bool inside = x < g.n1 && y < g.n2 && z < g.n3;
+  const double half = 0.5 * AT * A.h;
+  const double cx = A.ox + (blockIdx.x * AT) * A.h + half, cy = A.oy + (blockIdx.y * AT) * A.h + half,
+               cz = A.oz + (blockIdx.z * AT) * A.h + half;
+  const double norm = pow(2.0 * kPi * gsig * gsig, -1.5);
+  double rho = 0.0;
+  for (int a0 = 0; a0 < A.M; a0 += 512) {
+    const int cnt = tile_atoms(A, a0, cx, cy, cz, half, gcut + A.h, list, warp_cnt);
+    if (inside) {
+      for (int t = 0; t < cnt; ++t) {
+        const int J = list[t];
+        const double rx = node_off(A.ox, x, A.h, A.R[3 * J]), ry = node_off(A.oy, y, A.h, A.R[3 * J + 1]),
+                     rz = node_off(A.oz, z, A.h, A.R[3 * J + 2]);
+        const double r2 = dist3_sq(rx, ry, rz);
+        if (r2 < __dmul_rn(gcut, gcut)) rho += A.Z[J] * norm * exp(-r2 / (2.0 * gsig * gsig));
+      }
+    }
+    __syncthreads();
+  }
+  if (inside) u[lin(g, x, y, z)] = (T)sqrt(rho);
+  double acc[1] = {inside ? rho : 0.0};
+  struct Fin {
+    double* out;
+    __device__ void operator()(double* t) const { out[0] = t[0]; }
+  } fin{sum_out};
+  const int nb = gridDim.x * gridDim.y * gridDim.z;
+  const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  grid_sum<1, 512>(acc, smem, red, nb, bid, tid, fin);
+}
+
+// Per-atom box of lattice nodes [lo, lo + dim) (may extend outside the grid).
+struct AtomBox {
+  int lo[3];
+  int dim[3];
+};
+
+// V_J tabulated on the atom's box grown by 2R (forces, paper form): vbox[a][...].
+__global__ void __launch_bounds__(256) force_vbox_kernel(AtomArgs A, int a0, int na, int vdim, int R,
+                                                         const int* __restrict__ lo, double* vbox) {
+  const long long per = (long long)vdim * vdim * vdim;
+  for (long long t = (long long)blockIdx.x * 256 + threadIdx.x; t < per * na; t += (long long)gridDim.x * 256) {
+    const int a = (int)(t / per);
+    const long long e = t - (long long)a * per;
+    const int i = (int)(e % vdim), j = (int)((e / vdim) % vdim), k = (int)(e / ((long long)vdim * vdim));
+    const int J = a0 + a;
+    const double px = A.ox + (lo[3 * a] - 2 * R + i + 0.5) * A.h - A.R[3 * J];
+    const double py = A.oy + (lo[3 * a + 1] - 2 * R + j + 0.5) * A.h - A.R[3 * J + 1];
+    const double pz = A.oz + (lo[3 * a + 2] - 2 * R + k + 0.5) * A.h - A.R[3 * J + 2];
+    vbox[t] = gauss_v(A.Z[J], 1.0 / A.sigma, sqrt(px * px + py * py + pz * pz));
+  }
+}
+
+// b_J on the atom's box grown by R: -(1/4 pi) L_h V_J inside r_c, 0 outside.
+template <int R>
+__global__ void __launch_bounds__(256) force_bbox_kernel(AtomArgs A, int a0, int na, int vdim, int bdim,
+                                                         const int* __restrict__ lo, Weights<double> W,
+                                                         const double* __restrict__ vbox, double* bbox) {
+  const long long per = (long long)bdim * bdim * bdim;
+  const long long vper = (long long)vdim * vdim * vdim;
+  for (long long t = (long long)blockIdx.x * 256 + threadIdx.x; t < per * na; t += (long long)gridDim.x * 256) {
+    const int a = (int)(t / per);
+    const long long e = t - (long long)a * per;
+    const int i = (int)(e % bdim), j = (int)((e / bdim) % bdim), k = (int)(e / ((long long)bdim * bdim));
+    const int J = a0 + a;
+    const double px = node_off(A.ox, lo[3 * a] - R + i, A.h, A.R[3 * J]);
+    const double py = node_off(A.oy, lo[3 * a + 1] - R + j, A.h, A.R[3 * J + 1]);
+    const double pz = node_off(A.oz, lo[3 * a + 2] - R + k, A.h, A.R[3 * J + 2]);
+    double val = 0.0;
+    if (dist3(px, py, pz) < A.rc) {
+      const double* v = vbox + (long long)a * vper;
+      const long long c = (long long)(i + R) + (long long)vdim * ((j + R) + (long long)vdim * (k + R));
+      const long long sy = vdim, sz = (long long)vdim * vdim;
+      double lap = W.c * v[c];
+#pragma unroll
+      for (int p = 1; p <= R; ++p)
+        lap = fma(W.w[p], ((v[c + p] + v[c - p]) + (v[c + p * sy] + v[c - p * sy])) + (v[c + p * sz] + v[c - p * sz]), lap);
+      val = -lap / (4.0 * kPi);
+    }
+    bbox[t] = val;
+  }
+}
+
+// Force of atom a0+blockIdx.y: h^3 sum over in-grid ball nodes of
+// grad(b_J) (phi - V_J); paper form uses the FD gradient (weights wt) of the
+// tabulated b_J, exact form uses -(1/4 pi) L_h grad V_J (analytic grad V).
+// One block row per atom; partial sums reduced per atom by force_sum_kernel.
+template <typename T, int R>
+__global__ void __launch_bounds__(256) force_ball_kernel(GridDev g, AtomArgs A, int a0, int bdim,
+                                                         int box, const int* __restrict__ lo,
+                                                         Weights<double> W, Weights<double> Wt,
+                                                         const double* __restrict__ bbox,
+                                                         const T* __restrict__ phi, int exact,
+                                                         double* partial) {
+  __shared__ double smem[3 * (256 / 32)];
+  const int a = blockIdx.y;
+  const int J = a0 + a;
+  const long long per = (long long)box * box * box;
+  const long long bper = (long long)bdim * bdim * bdim;
+  const double inv_s = 1.0 / A.sigma;
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (long long t = (long long)blockIdx.x * 256 + threadIdx.x; t < per; t += (long long)gridDim.x * 256) {
+    const int i = (int)(t % box), j = (int)((t / box) % box), k = (int)(t / ((long long)box * box));
+    const int gi = lo[3 * a] + i, gj = lo[3 * a + 1] + j, gk = lo[3 * a + 2] + k;
+    if (gi < 0 || gj < 0 || gk < 0 || gi >= g.n1 || gj >= g.n2 || gk >= g.n3) continue;
+    const double rx = node_off(A.ox, gi, A.h, A.R[3 * J]);
+    const double ry = node_off(A.oy, gj, A.h, A.R[3 * J + 1]);
+    const double rz = node_off(A.oz, gk, A.h, A.R[3 * J + 2]);
+    const double r = dist3(rx, ry, rz);
+    if (!(r < A.rc)) continue;
+    const double pv = (double)phi[lin(g, gi, gj, gk)] - gauss_v(A.Z[J], inv_s, r);
+    double gx = 0.0, gy = 0.0, gz = 0.0;
+    if (!exact) {
+      const double* bb = bbox + (long long)a * bper;
+      const long long c = (long long)(i + R) + (long long)bdim * ((j + R) + (long long)bdim * (k + R));
+      const long long sy = bdim, sz = (long long)bdim * bdim;
+#pragma unroll
+      for (int p = 1; p <= R; ++p) {
+        gx = fma(Wt.w[p], bb[c + p] - bb[c - p], gx);
+        gy = fma(Wt.w[p], bb[c + p * sy] - bb[c - p * sy], gy);
+        gz = fma(Wt.w[p], bb[c + p * sz] - bb[c - p * sz], gz);
+      }
+    } else {
+      // -(1/4 pi) L_h grad V_J with grad V analytic: dV/dr = Z erf(r/s)/r^2 - Z (2/(s sqrt pi)) e^{-r^2/s^2}/r
+      double lx = 0.0, ly = 0.0, lz = 0.0;
+      for (int p = -R; p <= R; ++p) {
+        for (int ax = 0; ax < 3; ++ax) {
+          if (p == 0 && ax > 0) continue;
+          const double ex = rx + (ax == 0 ? p * A.h : 0.0);
+          const double ey = ry + (ax == 1 ? p * A.h : 0.0);
+          const double ez = rz + (ax == 2 ? p * A.h : 0.0);
+          const double rr = sqrt(ex * ex + ey * ey + ez * ez);
+          double gvx = 0.0, gvy = 0.0, gvz = 0.0;
+          if (rr > 1e-12 * A.sigma) {
+            const double x = rr * inv_s;
+            const double dVdr = A.Z[J] * erf(x) / (rr * rr) -
+                                A.Z[J] * 2.0 * inv_s * 0.56418958354775628 * exp(-x * x) / rr;
+            gvx = dVdr * ex / rr;
+            gvy = dVdr * ey / rr;
+            gvz = dVdr * ez / rr;
+          }
+          const double wp = (p == 0) ? W.c : W.w[p < 0 ? -p : p];
+          lx = fma(wp, gvx, lx);
+          ly = fma(wp, gvy, ly);
+          lz = fma(wp, gvz, lz);
+        }
+      }
+      gx = -lx / (4.0 * kPi);
+      gy = -ly / (4.0 * kPi);
+      gz = -lz / (4.0 * kPi);
+    }
+    acc[0] = fma(gx, pv, acc[0]);
+    acc[1] = fma(gy, pv, acc[1]);
+    acc[2] = fma(gz, pv, acc[2]);
+  }
+  block_sum<3, 256>(acc, smem, threadIdx.x);
+  if (threadIdx.x == 0) {
+    const long long o = ((long long)a * gridDim.x + blockIdx.x) * 3;
+    partial[o] = acc[0];
+    partial[o + 1] = acc[1];
+    partial[o + 2] = acc[2];
+  }
+}
+
+// F[J] = h^3 * (sum of the per-block partials of atom J, in block order).
+__global__ void force_sum_kernel(int a0, int na, int nblk, double h3, const double* partial, double* F) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= na) return;
+  double f[3] = {0.0, 0.0, 0.0};
+  for (int b = 0; b < nblk; ++b)
+    for (int d = 0; d < 3; ++d) f[d] += partial[((long long)a * nblk + b) * 3 + d];
+  for (int d = 0; d < 3; ++d) F[3 * (a0 + a) + d] = h3 * f[d];
+}
+
+// Gaussian-overlap repulsion correction (Appendix A in closed form):
+// E_c = sum_{I<J} Z_I Z_J erfc(R_IJ/(sqrt2 sigma))/R_IJ and its forces.  One
+// thread per atom I sums over all J != I (half the pair energy each).
+__global__ void ezz_kernel(AtomArgs A, double* eI, double* F) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= A.M) return;
+  const double a = 0.70710678118654752 / A.sigma;
+  double e = 0.0, f[3] = {0.0, 0.0, 0.0};
+  for (int J = 0; J < A.M; ++J) {
+    if (J == I) continue;
+    const double dx = A.R[3 * I] - A.R[3 * J], dy = A.R[3 * I + 1] - A.R[3 * J + 1],
+                 dz = A.R[3 * I + 2] - A.R[3 * J + 2];
+    const double r2 = dx * dx + dy * dy + dz * dz, r = sqrt(r2);
+    const double zz = A.Z[I] * A.Z[J];
+    e += 0.5 * zz * erfc(a * r) / r;
+    const double dEdr = zz * (-erfc(a * r) / r2 - 2.0 * a * 0.56418958354775628 * exp(-a * a * r2) / r);
+    f[0] -= dEdr * dx / r;
+    f[1] -= dEdr * dy / r;
+    f[2] -= dEdr * dz / r;
+  }
+  eI[I] = e;
+  F[3 * I] = f[0];
+  F[3 * I + 1] = f[1];
+  F[3 * I + 2] = f[2];
+}
+
+}  // namespace ofd

@@ -1,0 +1,71 @@
+"""CPU checks of the C-ABI library: it builds, loads, and exports every entry
+point that include/ofdft.h declares; host-only calls behave (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1405_6456_gb300 import build as B
+from paper_1405_6456_gb300 import ofdft as F
+from paper_1405_6456_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(ofdft_[a-z0-9_]+)\s*\(", txt))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return F.lib()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    declared = _declared()
+    assert len(declared) >= 12
+    for name in sorted(declared):
+        assert hasattr(lib, name), name
+    assert set(F.exported_symbols()) <= declared
+
+
+def test_default_params_follow_the_paper(lib):
+    p = F.default_params()
+    assert p.lam == 0.2  # Sec. 5
+    assert (p.eta0, p.mu0, p.kappa) == (-0.2, 1.0, 0.1)  # Sec. 5.3.1
+    assert p.fd_order == 12 and p.terms == F.TERM_ALL and p.method == F.METHOD_AL
+
+
+def test_box_rule_matches_oracle_box_rule(lib):
+    for c in [W.cluster_c1(), W.cluster_c2(), W.tiny_cluster("dimer")] + W.batch_c4(6):
+        for rt in (1, 2, 16):
+            g = F.ofdft_grid_for_atoms(c.R, c.h, c.vacuum, rt)
+            go = O.grid_for_atoms(c.R, c.h, c.vacuum, rt)
+            assert tuple(g.n) == (go.n1, go.n2, go.n3)
+            np.testing.assert_allclose(list(g.origin), list(go.origin), rtol=0, atol=1e-12)
+
+
+def test_host_argument_checks(lib):
+    g = F.Grid()
+    R = np.zeros(3)
+    assert lib.ofdft_grid_for_atoms(R.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 0, 0.5, 8.0,
+                                    16, ctypes.byref(g)) == F.EINVAL
+    assert lib.ofdft_grid_for_atoms(R.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 1, -0.5, 8.0,
+                                    16, ctypes.byref(g)) == F.EINVAL
+    bad = np.array([0.0, np.nan, 0.0])
+    assert lib.ofdft_grid_for_atoms(bad.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 1, 0.5, 8.0,
+                                    16, ctypes.byref(g)) == F.ENONFINITE
+    assert lib.ofdft_destroy(None) == F.OK
+    assert lib.ofdft_last_error(None) == b"null context"
+    gg = F.make_grid(128, 128, 128, 0.5)
+    assert F.workspace_bytes(gg, 12, F.PREC_FP64) > F.workspace_bytes(gg, 12, F.PREC_MIXED) > 0

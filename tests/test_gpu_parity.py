@@ -1,0 +1,351 @@
+"""GPU parity: the sm_103a library (through its C ABI) against the FP64 CPU oracle
+on the same seeded inputs.  Tolerances are written per test:
+  - FP64 kernels: relative 1e-12 of the natural scale of each quantity (only the
+    summation order differs);
+  - FP64 converged solves: 1e-6 Ha/atom in energy, 1e-5 Ha/bohr in forces (the
+    stated target), checked much tighter where both sides converge tightly;
+  - MIXED (FP32 fields, FP64 sums): 1e-5 Ha/atom in energy.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O
+from paper_1405_6456_gb300 import build as B
+from paper_1405_6456_gb300 import ofdft as F
+from paper_1405_6456_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    B.build()
+    c = F.Context(0)
+    yield c
+    c.close()
+
+
+def _t(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device=DEV)
+
+
+def _h(t):
+    torch.cuda.synchronize()
+    return t.double().cpu().numpy()
+
+
+def _ogrid(g):
+    return O.make_grid(g.n[0], g.n[1], g.n[2], g.h, tuple(g.origin))
+
+
+# ------------------------------------------------------------------ S2 ---
+@pytest.mark.parametrize("dims", [(37, 29, 23), (1, 1, 1), (5, 70, 3), (64, 16, 40), (33, 9, 13)])
+@pytest.mark.parametrize("order", [2, 4, 6, 8, 10, 12])
+def test_stencil_fp64_matches_oracle(ctx, dims, order):
+    rng = np.random.default_rng(sum(dims) * 31 + order)
+    g = F.make_grid(*dims, 0.45)
+    f = rng.standard_normal(g.shape)
+    out = torch.empty(g.shape, dtype=torch.float64, device=DEV)
+    ctx.stencil(g, order, _t(f), out)
+    ref = O.laplacian(_ogrid(g), order // 2, f)
+    scale = np.abs(O.lap_weights(order // 2, g.h)).sum() * 6 * np.abs(f).max()
+    assert np.abs(_h(out) - ref).max() <= 1e-14 * scale
+
+
+@pytest.mark.parametrize("order", [6, 12])
+def test_stencil_fp32_matches_oracle(ctx, order):
+    rng = np.random.default_rng(order)
+    g = F.make_grid(70, 45, 38, 0.5)
+    f = rng.standard_normal(g.shape).astype(np.float32)
+    out = torch.empty(g.shape, dtype=torch.float32, device=DEV)
+    ctx.stencil(g, order, _t(f, torch.float32), out)
+    ref = O.laplacian(_ogrid(g), order // 2, f.astype(np.float64))
+    scale = np.abs(O.lap_weights(order // 2, g.h)).sum() * 6 * np.abs(f).max()
+    assert np.abs(_h(out) - ref).max() <= 2e-6 * scale
+
+
+def test_stencil_full_size_128_cubed_matches_oracle(ctx):
+    """Full C2 grid (128^3, 12th order) in the launch shape the solver uses."""
+    c = W.cluster_c2()
+    g = F.ofdft_grid_for_atoms(c.R, c.h, c.vacuum)
+    rng = np.random.default_rng(11)
+    f = rng.standard_normal(g.shape)
+    out = torch.empty(g.shape, dtype=torch.float64, device=DEV)
+    ctx.stencil(g, 12, _t(f), out)
+    ref = O.laplacian(_ogrid(g), 6, f)
+    scale = np.abs(O.lap_weights(6, g.h)).sum() * 6 * np.abs(f).max()
+    assert np.abs(_h(out) - ref).max() <= 1e-14 * scale
+
+
+# ------------------------------------------------------------------ S1 ---
+@pytest.mark.parametrize("kind,order", [("dimer", 6), ("trimer", 12), ("atom", 2)])
+def test_pseudocharge_and_guess_match_oracle(ctx, kind, order):
+    c = W.tiny_cluster(kind, h=0.7, fd_order=order)
+    g = F.ofdft_grid_for_atoms(c.R, c.h, c.vacuum, 1)
+    b = torch.empty(g.shape, dtype=torch.float64, device=DEV)
+    es = ctx.pseudocharge(g, order, c.R, c.Z, b)
+    b_ref, es_ref = O.pseudocharge(_ogrid(g), order // 2, c.R, c.Z)
+    assert np.abs(_h(b) - b_ref).max() <= 1e-13 * np.abs(b_ref).max()
+    assert es == pytest.approx(es_ref, rel=1e-12)
+    u = torch.empty(g.shape, dtype=torch.float64, device=DEV)
+    ctx.initial_guess(g, c.R, c.Z, u)
+    u_ref = O.initial_guess(_ogrid(g), c.R, c.Z)
+    assert np.abs(_h(u) - u_ref).max() <= 1e-13 * np.abs(u_ref).max()
+
+
+def test_pseudocharge_full_size_c1(ctx):
+    c = W.cluster_c1()
+    g = F.ofdft_grid_for_atoms(c.R, c.h, c.vacuum)
+    b = torch.empty(g.shape, dtype=torch.float64, device=DEV)
+    es = ctx.pseudocharge(g, 12, c.R, c.Z, b)
+    b_ref, es_ref = O.pseudocharge(_ogrid(g), 6, c.R, c.Z)
+    assert np.abs(_h(b) - b_ref).max() <= 1e-13 * np.abs(b_ref).max()
+    assert es == pytest.approx(es_ref, rel=1e-12)
+
+
+# ------------------------------------------------------------------ S3 ---
+@pytest.mark.parametrize("order", [4, 12])
+def test_poisson_fp64_matches_oracle(ctx, order):
+    c = W.tiny_cluster("trimer", h=0.8, fd_order=order)
+    g = F.ofdft_grid_for_atoms(c.R, c.h, c.vacuum, 1)
+    og = _ogrid(g)
+    b_ref, _ = O.pseudocharge(og, order // 2, c.R, c.Z)
+    u_ref = O.initial_guess(og, c.R, c.Z)
+    rho = u_ref**2 + b_ref
+    phi_ref, it_ref, rel_ref = O.poisson(og, order // 2, rho, tol=1e-12)
+    phi = torch.zeros(g.shape, dtype=torch.float64, device=DEV)
+    st = ctx.poisson(g, order, phi, u=_t(u_ref), b=_t(b_ref), tol=1e-12)
+    assert st.rel_residual <= 1e-12
+    assert abs(st.iterations - it_ref) <= max(3, it_ref // 20)
+    assert np.abs(_h(phi) - phi_ref).max() <= 1e-9 * np.abs(phi_ref).max()
+    # explicit rho path and warm start from the solution
+    phi2 = _t(phi_ref)
+    st2 = ctx.poisson(g, order, phi2, rho=_t(rho), tol=1e-11)
+    assert st2.iterations <= 1
+
+
+def test_poisson_mixed_reaches_fp64_tolerance(ctx):
+    c = W.cluster_c1()
+    g = F.ofdft_grid_for_atoms(c.R, c.h, c.vacuum)
+    og = _ogrid(g)
+    b_ref, _ = O.pseudocharge(og, 6, c.R, c.Z)
+    u_ref = O.initial_guess(og, c.R, c.Z)
+    phi_ref, _, _ = O.poisson(og, 6, u_ref**2 + b_ref, tol=1e-12)
+    phi = torch.zeros(g.shape, dtype=torch.float32, device=DEV)
+    st = ctx.poisson(g, 12, phi, u=_t(u_ref, torch.float32), b=_t(b_ref, torch.float32), tol=1e-9)
+    assert st.rel_residual <= 1e-9
+    # the float32 copy of an FP64-accurate phi: relative error at FP32 rounding
+    assert np.abs(_h(phi) - phi_ref).max() <= 2e-6 * np.abs(phi_ref).max()
+
+
+# ------------------------------------------------------------------ S4 ---
+def _random_state(g, order, c, seed):
+    og = _ogrid(g)
+    b, es = O.pseudocharge(og, order // 2, c.R, c.Z)
+    u = O.initial_guess(og, c.R, c.Z)
+    rng = np.random.default_rng(seed)
+    u = np.abs(u * (1 + 0.05 * rng.standard_normal(u.shape)))
+    phi, _, _ = O.poisson(og, order // 2, u**2 + b, tol=1e-12)
+    phi = phi + 1e-3 * rng.standard_normal(phi.shape)  # not the exact solution
+    d = 0.01 * rng.standard_normal(u.shape)
+    s_old = 0.01 * rng.standard_normal(u.shape)
+    return og, b, es, u, phi, d, s_old
+
+
+@pytest.mark.parametrize("terms", [F.TERM_ALL, F.TERM_VW | F.TERM_TF, F.TERM_ES | F.TERM_XC])
+def test_functional_fp64_matches_oracle_at_given_phi(ctx, terms):
+    c = W.tiny_cluster("trimer", h=0.7, fd_order=12)
+    g = F.ofdft_grid_for_atoms(c.R, c.h, c.vacuum, 1)
+    og, b, es, u, phi, d, s_old = _random_state(g, 12, c, 5)
+    p = F.default_params(terms=terms, fd_order=12)
+    po = O.default_params(terms=terms, fd_n=6)
+    eta, mu = -0.15, 0.3
+    G = torch.empty(g.shape, dtype=torch.float64, device=DEV)
+    s = torch.empty_like(G)
+    e = ctx.energy_grad(g, p, _t(u), _t(b), _t(phi), es, eta, mu, c.N, solve_poisson=False,
+                        grad=G, s=s, d=_t(d), s_old=_t(s_old))
+    eo, Go, so = O.functional(og, po, u, b, phi, es, eta, mu, c.N)
+    for k in ("E_tf", "E_vw", "E_xc", "E_es", "E", "C", "L", "gnorm2", "rs"):
+        assert getattr(e, k) == pytest.approx(getattr(eo, k), rel=1e-11, abs=1e-11), k
+    h3 = g.h**3
+    assert e.gd == pytest.approx(h3 * (Go * d).sum(), rel=1e-11, abs=1e-13)
+    assert e.gs_old == pytest.approx(h3 * (Go * s_old).sum(), rel=1e-11, abs=1e-13)
+    assert np.abs(_h(G) - Go).max() <= 1e-12 * np.abs(Go).max()
+    assert np.abs(_h(s) - so).max() <= 1e-12 * np.abs(so).max()
+
+
+def test_energy_grad_with_poisson_matches_oracle(ctx):
+    c = W.tiny_cluster("dimer", h=0.8, fd_order=8)
+    g = F.ofdft_grid_for_atoms(c.R, c.h, c.vacuum, 1)
+    og, b, es, u, phi, d, s_old = _random_state(g, 8, c, 6)
+    p = F.default_params(fd_order=8, tol_poisson=1e-12)
+    po = O.default_params(fd_n=4, tol_poisson=1e-12)
+    phi_d = _t(phi)
+    G = torch.empty(g.shape, dtype=torch.float64, device=DEV)
+    e = ctx.energy_grad(g, p, _t(u), _t(b), phi_d, es, -0.2, 1.0, c.N, grad=G)
+    eo, Go, so, phio = O.energy_grad(og, po, u, b, phi, es, -0.2, 1.0, c.N)
+    assert e.E == pytest.approx(eo.E, abs=1e-10)
+    assert e.L == pytest.approx(eo.L, abs=1e-10)
+    assert np.abs(_h(phi_d) - phio).max() <= 1e-9 * np.abs(phio).max()
+    assert np.abs(_h(G) - Go).max() <= 1e-8 * np.abs(Go).max()
+
+
+def test_functional_full_size_c2_at_given_phi(ctx):
+    """Full 128^3 grid, 666 atoms: the fused pass against the oracle at a fixed phi."""
+    c = W.cluster_c2()
+    g = F.ofdft_grid_for_atoms(c.R, c.h, c.vacuum)
+    og = _ogrid(g)
+    b, es = O.pseudocharge(og, 6, c.R, c.Z)
+    u = O.initial_guess(og, c.R, c.Z)
+    rng = np.random.default_rng(8)
+    phi = -0.5 * np.exp(-((np.arange(g.size) % 97) / 97.0)).reshape(g.shape) + 0.01 * rng.standard_normal(g.shape)
+    p = F.default_params()
+    po = O.default_params()
+    b_d = torch.empty(g.shape, dtype=torch.float64, device=DEV)
+    es_d = ctx.pseudocharge(g, 12, c.R, c.Z, b_d)
+    assert np.abs(_h(b_d) - b).max() <= 1e-13 * np.abs(b).max()
+    assert es_d == pytest.approx(es, rel=1e-12)
+    e = ctx.energy_grad(g, p, _t(u), b_d, _t(phi), es_d, -0.2, 1.0, c.N, solve_poisson=False)
+    eo, _, _ = O.functional(og, po, u, b, phi, es, -0.2, 1.0, c.N, want_grad=False)
+    for k in ("E_tf", "E_vw", "E_xc", "E_es", "E", "L"):
+        assert getattr(e, k) == pytest.approx(getattr(eo, k), rel=1e-11), k
+    # C = h^3 sum u^2 - N cancels ~2e3 to ~0, so the summation order alone moves it by
+    # ~1e-13 N; G carries 2 u C / mu, hence the looser bound on the gradient norms
+    assert abs(e.C - eo.C) <= 1e-12 * c.N
+    for k in ("gnorm2", "rs"):
+        assert getattr(e, k) == pytest.approx(getattr(eo, k), rel=5e-9), k
+
+
+# ------------------------------------------------------------------ S9 ---
+@pytest.mark.parametrize("variant", [F.FORCE_PAPER, F.FORCE_EXACT])
+def test_forces_match_oracle_at_given_phi(ctx, variant):
+    c = W.tiny_cluster("trimer", h=0.6, fd_order=8)
+    g = F.ofdft_grid_for_atoms(c.R, c.h, c.vacuum, 1)
+    og = _ogrid(g)
+    rng = np.random.default_rng(9)
+    X = g.origin[0] + (np.arange(g.n[0]) + 0.5) * g.h
+    phi = np.broadcast_to(0.3 * np.sin(0.2 * X), g.shape) + 0.01 * rng.standard_normal(g.shape)
+    Fd = ctx.forces(g, 8, c.R, c.Z, _t(phi), variant=variant)
+    Fo = O.forces(og, 4, c.R, c.Z, phi, exact=(variant == F.FORCE_EXACT))
+    np.testing.assert_allclose(Fd, Fo, rtol=1e-11, atol=1e-13)
+
+
+# ------------------------------------------------------- full ground state --
+def _parity_params(order, **kw):
+    base = dict(fd_order=order, tol_E=1e-10, tol_inner=1e-13, tol_poisson=1e-12, max_outer=40, max_nlcg=4000)
+    base.update(kw)
+    return F.default_params(**base)
+
+
+def _oracle_solve(c, g, order, **kw):
+    po = O.default_params(fd_n=order // 2, tol_E=1e-10 * c.M, tol_inner=1e-12, tol_poisson=1e-12, max_outer=40,
+                          max_nlcg=4000, **kw)
+    return O.solve(_ogrid(g), po, c.R, c.Z)
+
+
+@pytest.fixture(scope="module")
+def dimer_case(ctx):
+    c = W.tiny_cluster("dimer", h=0.8, fd_order=6)
+    g = F.ofdft_grid_for_atoms(c.R, c.h, c.vacuum, 1)
+    res, u, phi, b = _oracle_solve(c, g, 6)
+    return c, g, res, u, phi
+
+
+def test_solve_fp64_matches_oracle_dimer(ctx, dimer_case):
+    c, g, res, u_ref, phi_ref = dimer_case
+    p = _parity_params(6)
+    u = torch.empty(g.shape, dtype=torch.float64, device=DEV)
+    phi = torch.empty_like(u)
+    E, Fv, st = ctx.solve(c.R, c.Z, c.h, p, grid=g, u_out=u, phi_out=phi)
+    assert st.converged
+    assert E / c.M == pytest.approx(res.E / c.M, abs=1e-9)
+    assert st.eta == pytest.approx(res.eta, abs=1e-6)
+    assert np.abs(_h(u) - u_ref).max() <= 1e-5 * np.abs(u_ref).max()
+    Fo = O.forces(_ogrid(g), 3, c.R, c.Z, phi_ref)
+    np.testing.assert_allclose(Fv, Fo, atol=1e-7)
+
+
+@pytest.fixture(scope="module")
+def c1_case(ctx):
+    c = W.cluster_c1()
+    g = F.ofdft_grid_for_atoms(c.R, c.h, c.vacuum)
+    res, u, phi, b = _oracle_solve(c, g, 12)
+    Fo = O.forces(_ogrid(g), 6, c.R, c.Z, phi)
+    return c, g, res, Fo
+
+
+def test_solve_fp64_matches_oracle_c1(ctx, c1_case):
+    """13-atom cuboctahedron, 32^3, 12th order: the FP64 target is 1e-6 Ha/atom
+    and 1e-5 Ha/bohr; with tight tolerances both sides agree far closer."""
+    c, g, res, Fo = c1_case
+    p = _parity_params(12)
+    E, Fv, st = ctx.solve(c.R, c.Z, c.h, p, grid=g)
+    assert st.converged and res.converged
+    assert abs(E - res.E) / c.M <= 1e-6
+    assert abs(E - res.E) / c.M <= 1e-8
+    assert np.abs(Fv - Fo).max() <= 1e-5
+    assert abs(st.C) <= 1e-8 * c.N
+
+
+def test_solve_mixed_matches_oracle_c1(ctx, c1_case):
+    c, g, res, Fo = c1_case
+    p = _parity_params(12, precision=F.PREC_MIXED, tol_poisson=1e-9, tol_inner=1e-9, tol_E=1e-8)
+    E, Fv, st = ctx.solve(c.R, c.Z, c.h, p, grid=g)
+    assert st.converged
+    assert abs(E - res.E) / c.M <= 1e-5
+    assert np.abs(Fv - Fo).max() <= 1e-4
+
+
+def test_solve_product_tolerance_c1(ctx, c1_case):
+    """Default (product) tolerances: 1e-6 Ha/atom of the tightly converged oracle."""
+    c, g, res, Fo = c1_case
+    p = F.default_params()
+    E, Fv, st = ctx.solve(c.R, c.Z, c.h, p)
+    assert st.converged
+    assert tuple(st.grid.n) == tuple(g.n)
+    assert abs(E - res.E) / c.M <= 1e-6
+    assert np.abs(Fv - Fo).max() <= 1e-5
+
+
+# ------------------------------------------------------------ edge cases --
+def test_invalid_arguments_are_rejected(ctx):
+    g = F.make_grid(8, 8, 8, 0.5)
+    f = torch.zeros(g.shape, dtype=torch.float64, device=DEV)
+    out = torch.zeros_like(f)
+    with pytest.raises(F.OfdftError) as ei:
+        ctx.stencil(g, 14, f, out)
+    assert ei.value.code == F.EINVAL
+    with pytest.raises(F.OfdftError) as ei:
+        ctx.stencil(g, 5, f, out)
+    assert ei.value.code == F.EINVAL
+    with pytest.raises(F.OfdftError) as ei:
+        ctx.stencil(F.make_grid(0, 8, 8, 0.5), 4, f, out)
+    assert ei.value.code == F.EINVAL
+    with pytest.raises(F.OfdftError) as ei:
+        ctx.pseudocharge(g, 4, np.array([[0.0, np.nan, 0.0]]), [3.0], f)
+    assert ei.value.code == F.ENONFINITE
+    with pytest.raises(F.OfdftError) as ei:
+        ctx.solve(np.zeros((1, 3)), [3.0], 0.5, F.default_params(kappa=1.5))
+    assert ei.value.code == F.EINVAL
+    # the context stays usable after errors
+    ctx.stencil(g, 4, f, out)
+
+
+def test_poisson_iteration_cap_reports_notconv(ctx):
+    g = F.make_grid(24, 24, 24, 0.5)
+    rng = np.random.default_rng(1)
+    rho = _t(rng.standard_normal(g.shape))
+    phi = torch.zeros(g.shape, dtype=torch.float64, device=DEV)
+    with pytest.raises(F.OfdftError) as ei:
+        ctx.poisson(g, 6, phi, rho=rho, tol=1e-12, max_it=3)
+    assert ei.value.code == F.ENOTCONV
+    st = ctx.poisson(g, 6, phi, rho=rho, tol=1e-12, max_it=3, allow_notconv=True)
+    assert st.iterations == 3
