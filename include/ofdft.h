@@ -91,6 +91,10 @@ typedef struct {
   double vacuum;      /* box rule of ofdft_grid_for_atoms: vacuum on every side */
   int round_to;       /* box rule: node counts rounded up to a multiple of this */
   int refine_every;   /* MIXED: FP64 residual correction every this many FP32 CG steps */
+  double trial_max_rel; /* cap of the trial step: h^3 |sig d|^2 <= trial_max_rel^2 N (0: no cap) */
+  int max_backtrack;  /* halvings of the secant step while L does not decrease (0: none) */
+  int precond_rank1;  /* 1: the preconditioner also inverts the rank-one term (4h^3/mu) u u^T
+                         of the augmented Lagrangian's Hessian exactly (Sherman-Morrison) */
 } ofdft_params;
 
 typedef struct {
@@ -106,7 +110,8 @@ typedef struct {
   double gd;      /* h^3 G.d when d was given */
   double gs_old;  /* h^3 G.s_old when s_old was given */
   double gnorm2;  /* h^3 G.G */
-  double rs;      /* h^3 r.s, r = -G, s = r / Jacobi diagonal */
+  double rs;      /* h^3 r.s, r = -G, s = r / Jacobi diagonal (NLCG stopping measure) */
+  double rs_pc;   /* h^3 r.s with the preconditioner the solver applies (Polak-Ribiere beta) */
   ofdft_cg_stats poisson;
 } ofdft_energy;
 

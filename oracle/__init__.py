@@ -56,15 +56,16 @@ class Params(C.Structure):
                 ("max_cg", C.c_int), ("max_secant", C.c_int), ("sigma0", C.c_double),
                 ("eps_secant", C.c_double), ("restart_every", C.c_int), ("sigma", C.c_double),
                 ("rc", C.c_double), ("guess_sigma", C.c_double), ("guess_cut", C.c_double),
-                ("ezz_correction", C.c_int)]
+                ("ezz_correction", C.c_int), ("trial_max_rel", C.c_double), ("max_backtrack", C.c_int),
+                ("precond_rank1", C.c_int)]
 
 
 class Energy(C.Structure):
     _fields_ = [("L", C.c_double), ("E", C.c_double), ("E_tf", C.c_double),
                 ("E_vw", C.c_double), ("E_xc", C.c_double), ("E_es", C.c_double),
                 ("E_self", C.c_double), ("E_zz_corr", C.c_double), ("C", C.c_double),
-                ("gnorm2", C.c_double), ("rs", C.c_double), ("cg_iters", C.c_int),
-                ("cg_relres", C.c_double)]
+                ("gnorm2", C.c_double), ("rs", C.c_double), ("rs_pc", C.c_double),
+                ("cg_iters", C.c_int), ("cg_relres", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

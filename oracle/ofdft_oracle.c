@@ -12,9 +12,13 @@
  *   R3 gradient: G = (1/h^3) dL_h/du, which is twice the discrete Euler-Lagrange
  *      expression of Sec. 4 (Eq. EulerLagrangeDiscretized); same zero set;
  *   R4 Jacobi preconditioner: the diagonal of dG/du with the nonlocal Hartree and
- *      the rank-one constraint parts left out, floored to stay positive;
+ *      the rank-one constraint parts left out, floored to stay positive (optionally
+ *      with the rank-one part inverted exactly, Sherman-Morrison);
  *   R5 secant line search and Polak-Ribiere update as in the reference the paper
  *      names for them (Shewchuk 1994), with |u| taken after every update (Sec. 4);
+ *      the trial step is sigma0 along d, capped so that its RMS size is at most
+ *      trial_max_rel times that of u, and a secant step that does not lower L is
+ *      halved up to max_backtrack times;
  *   R6 pseudocharge: Gaussian nuclei V_J = -Z erf(r/sigma)/r (the paper's GNH
  *      parameters are not given), b_J from Eq. b_J of Sec. 4 inside r < r_c;
  *   R7 initial guess: superposed Gaussian atomic densities (isolated-atom
@@ -61,6 +65,9 @@ void orc_default_params(orc_params* p) {
   p->guess_sigma = 2.0;
   p->guess_cut = 8.0;
   p->ezz_correction = 0;
+  p->trial_max_rel = 0.2;
+  p->max_backtrack = 2;
+  p->precond_rank1 = 1;
 }
 
 /* Laplacian weights of Sec. 4, Eq. FD:Laplacian: w_0 = -(1/h^2) sum_{q=1}^n 1/q^2,
@@ -396,7 +403,8 @@ void orc_functional(const orc_grid* g, const orc_params* p, const double* u, con
   const double C = h3 * s_uu - N;
   const double inv_mu = 1.0 / mu;
   const double mult = -eta + C * inv_mu;
-  double g2 = 0.0, rs = 0.0;
+  double g2 = 0.0, rs = 0.0, us = 0.0, uwu = 0.0;
+  double* winv = (p->precond_rank1 && s) ? (double*)malloc(sizeof(double) * NG) : NULL;
   for (long x = 0; x < NG; ++x) {
     const double ux = fabs(u[x]);
     double e_xc = 0.0, v_xc = 0.0;
@@ -418,9 +426,21 @@ void orc_functional(const orc_grid* g, const orc_params* p, const double* u, con
     if (md < 1e-10) md = 1e-10;
     if (G) G[x] = gx;
     if (s) s[x] = -gx / md;
+    if (winv) winv[x] = u[x] / md;
     g2 += gx * gx;
     rs += gx * gx / md;
+    us += u[x] * (-gx / md);
+    uwu += u[x] * u[x] / md;
   }
+  double rs_pc = rs;
+  if (winv && s) {
+    /* rank-one term (4 h^3/mu) u u^T of dG/du inverted exactly (Sherman-Morrison) */
+    const double cpen = 4.0 * h3 * inv_mu;
+    const double gamma = cpen * us / (1.0 + cpen * uwu);
+    for (long x = 0; x < NG; ++x) s[x] -= gamma * winv[x];
+    rs_pc -= gamma * us;
+  }
+  free(winv);
   out->E_tf = h3 * s_tf;
   out->E_vw = -0.5 * p->lambda * h3 * s_vw;
   out->E_xc = h3 * s_xc;
@@ -431,6 +451,7 @@ void orc_functional(const orc_grid* g, const orc_params* p, const double* u, con
   out->L = out->E - eta * C + 0.5 * C * C * inv_mu;
   out->gnorm2 = h3 * g2;
   out->rs = h3 * rs;
+  out->rs_pc = h3 * rs_pc;
   free(Lu);
   free(Lphi);
 }
@@ -497,7 +518,7 @@ static int nlcg(solver* S, double eta, double mu) {
   int converged = 0;
   sv_eval(S, S->u, eta, mu);
   memcpy(d, S->s, sizeof(double) * NG);
-  double delta_new = S->e.rs;
+  double delta_new = S->e.rs_pc;
   int k = 0;
   for (int it = 0; it < p->max_nlcg; ++it) {
     if (S->e.rs < p->tol_inner) {
@@ -514,8 +535,12 @@ static int nlcg(solver* S, double eta, double mu) {
       g0 = h3 * dot(S->G, d, NG);
     }
     const double dd = h3 * dot(d, d, NG);
-    /* trial point at sigma0 along d */
-    for (long x = 0; x < NG; ++x) ut[x] = fabs(S->u[x] + p->sigma0 * d[x]);
+    /* trial point at sig along d: sigma0, capped so that its RMS size is at most
+       trial_max_rel times that of u (R5) */
+    double sig = p->sigma0;
+    if (p->trial_max_rel > 0.0 && dd > 0.0 && p->trial_max_rel * sqrt(S->N / dd) < sig)
+      sig = p->trial_max_rel * sqrt(S->N / dd);
+    for (long x = 0; x < NG; ++x) ut[x] = fabs(S->u[x] + sig * d[x]);
     {
       double* Gs = S->G;
       double* ss = S->s;
@@ -526,17 +551,24 @@ static int nlcg(solver* S, double eta, double mu) {
       S->s = ss;
     }
     double gt = h3 * dot(Gt, d, NG);
-    double alpha = -p->sigma0, gprev = gt, gcur = g0;
+    double alpha = -sig, gprev = gt, gcur = g0;
     if (!((gcur - gprev) / alpha > 0.0)) {
       /* no positive curvature between 0 and sigma0: keep the trial point */
       memcpy(S->u, ut, sizeof(double) * NG);
       memcpy(S->G, Gt, sizeof(double) * NG);
       memcpy(S->s, st, sizeof(double) * NG);
     } else {
+      const double L0 = S->e.L;
       for (int j = 1; j <= p->max_secant; ++j) {
         alpha = alpha * gcur / (gprev - gcur);
-        for (long x = 0; x < NG; ++x) S->u[x] = fabs(S->u[x] + alpha * d[x]);
-        sv_eval(S, S->u, eta, mu);
+        for (long x = 0; x < NG; ++x) ut[x] = fabs(S->u[x] + alpha * d[x]);
+        sv_eval(S, ut, eta, mu);
+        for (int bt = 0; bt < p->max_backtrack && !(S->e.L <= L0); ++bt) {
+          alpha *= 0.5; /* the secant step did not lower L: halve it */
+          for (long x = 0; x < NG; ++x) ut[x] = fabs(S->u[x] + alpha * d[x]);
+          sv_eval(S, ut, eta, mu);
+        }
+        memcpy(S->u, ut, sizeof(double) * NG);
         gprev = gcur;
         gcur = h3 * dot(S->G, d, NG);
         if (j == p->max_secant || alpha * alpha * dd <= p->eps_secant * p->eps_secant * S->N) break;
@@ -546,7 +578,7 @@ static int nlcg(solver* S, double eta, double mu) {
     /* Polak-Ribiere direction update with restarts */
     const double delta_old = delta_new;
     const double delta_mid = -h3 * dot(S->G, s_old, NG);
-    delta_new = S->e.rs;
+    delta_new = S->e.rs_pc;
     const double beta = (delta_new - delta_mid) / delta_old;
     ++k;
     if (k >= p->restart_every || !(beta > 0.0)) {

@@ -53,6 +53,9 @@ typedef struct {
   double sigma, rc;
   double guess_sigma, guess_cut; /* initial guess: Gaussian atoms, width, cutoff */
   int ezz_correction;  /* add the Gaussian-overlap repulsion correction (App. A) */
+  double trial_max_rel; /* trial step capped to h^3 |sig d|^2 <= trial_max_rel^2 N (0: no cap) */
+  int max_backtrack;   /* halvings of the secant step while L does not decrease */
+  int precond_rank1;   /* also invert the rank-one term (4 h^3/mu) u u^T of the Hessian exactly */
 } orc_params;
 
 typedef struct {
@@ -61,7 +64,8 @@ typedef struct {
   double E_tf, E_vw, E_xc, E_es, E_self, E_zz_corr;
   double C;        /* C_h(u) = h^3 sum u^2 - N */
   double gnorm2;   /* h^3 sum G^2 */
-  double rs;       /* h^3 r.s with r = -G, s = r/M (Jacobi) */
+  double rs;       /* h^3 r.s with r = -G, s = r/M (Jacobi diagonal alone): stopping measure */
+  double rs_pc;    /* h^3 r.s with s the preconditioned residual actually used (PR beta) */
   int cg_iters;
   double cg_relres;
 } orc_energy;

@@ -13,7 +13,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libofdft.so")
 SOURCES = ["api.cu"]
-HEADERS = ["common.cuh", "kernels.cuh"]
+HEADERS = ["common.cuh", "kernels.cuh", "host.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

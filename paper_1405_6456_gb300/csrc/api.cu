@@ -1,299 +1,10 @@
-// Host side of the library: the C ABI of include/ofdft.h, device workspaces,
-// kernel launch configuration, and the control flow of the method (Poisson CG
-// loop, secant/Polak-Ribiere nonlinear CG, Algorithm 1).  All arithmetic on
-// fields runs in the kernels of kernels.cuh; the host only moves scalars.
-#include <cuda_runtime.h>
-#include <math.h>
-#include <stdarg.h>
-#include <stdio.h>
-#include <stdlib.h>
-#include <string.h>
+// C ABI of include/ofdft.h for single solves: Poisson CG control, the fused
+// functional pass, the secant/Polak-Ribiere nonlinear CG and Algorithm 1 (host
+// control of device work), atom kernels' launches, and the entry points.
+// All arithmetic on fields runs in the kernels of kernels.cuh.
+#include "host.cuh"
 
-#include <algorithm>
-#include <string>
-#include <vector>
-
-#include "../../include/ofdft.h"
-#include "kernels.cuh"
-
-using namespace ofd;
-
-// ----------------------------------------------------------------- context --
-struct DevBuf {
-  void* p = nullptr;
-  size_t bytes = 0;
-};
-
-struct ofdft_ctx {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  std::string err;
-  int sms = 152;
-  // reduction scratch
-  DevBuf partials;
-  unsigned int* counter = nullptr;
-  // small device scalars: CG scalars (2 sets), functional outputs, dot outputs
-  CgScalars* sc = nullptr;
-  CgScalars* sc32 = nullptr;
-  double* scal = nullptr;  // 64 doubles
-  double* host_scal = nullptr;  // pinned mirror
-  // named vector workspaces
-  DevBuf v[24];
-  // launch counters and optional CUDA-event timing of every launch
-  long long launches = 0;
-  long long kind_launches[OFDFT_K_COUNT] = {0};
-  long long timed_launches[OFDFT_K_COUNT] = {0};
-  double timed_ms[OFDFT_K_COUNT] = {0};
-  int prof = 0;
-  struct Pending {
-    cudaEvent_t a, b;
-    int kind;
-  };
-  std::vector<Pending> pending;
-  std::vector<cudaEvent_t> free_events;
-};
-
-namespace {
-
-enum Vec {
-  V_R = 0, V_P0, V_P1, V_AP,           // CG vectors (prec type)
-  V_R64, V_PHI64, V_B64, V_E32,        // mixed refinement (FP64 r, phi, b; FP32 correction)
-  V_U, V_UT, V_PHI, V_B,               // solve state
-  V_G, V_GT, V_S, V_ST, V_SN, V_D,     // NLCG vectors
-  V_ATOM0, V_ATOM1, V_ATOM2,           // atom scratch
-  V_COUNT
-};
-
-int fail(ofdft_ctx* c, int code, const char* fmt, ...) {
-  char buf[512];
-  va_list ap;
-  va_start(ap, fmt);
-  vsnprintf(buf, sizeof(buf), fmt, ap);
-  va_end(ap);
-  if (c) c->err = buf;
-  return code;
-}
-
-#define CU(call)                                                                   \
-  do {                                                                             \
-    cudaError_t e_ = (call);                                                       \
-    if (e_ != cudaSuccess)                                                         \
-      return fail(c, e_ == cudaErrorMemoryAllocation ? OFDFT_ENOMEM : OFDFT_ECUDA, \
-                  "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
-  } while (0)
-
-#define TRY(expr)            \
-  do {                       \
-    int rc_ = (expr);        \
-    if (rc_ != OFDFT_OK) return rc_; \
-  } while (0)
-
-int ensure(ofdft_ctx* c, DevBuf& b, size_t bytes) {
-  if (b.bytes >= bytes && b.p) return OFDFT_OK;
-  if (b.p) {
-    CU(cudaStreamSynchronize(c->stream));
-    CU(cudaFree(b.p));
-    b.p = nullptr;
-    b.bytes = 0;
-  }
-  const size_t want = std::max<size_t>(bytes, 256);
-  CU(cudaMalloc(&b.p, want));
-  b.bytes = want;
-  return OFDFT_OK;
-}
-
-template <typename T>
-T* vec(ofdft_ctx* c, int which) {
-  return static_cast<T*>(c->v[which].p);
-}
-
-cudaEvent_t take_event(ofdft_ctx* c) {
-  if (!c->free_events.empty()) {
-    cudaEvent_t e = c->free_events.back();
-    c->free_events.pop_back();
-    return e;
-  }
-  cudaEvent_t e = nullptr;
-  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
-  return e;
-}
-
-// Folds the durations of completed timed launches into the totals (call after
-// the stream has been synchronised) and recycles their events.
-void harvest(ofdft_ctx* c) {
-  for (auto& p : c->pending) {
-    float ms = 0.0f;
-    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
-      c->timed_ms[p.kind] += ms;
-      c->timed_launches[p.kind] += 1;
-    }
-    c->free_events.push_back(p.a);
-    c->free_events.push_back(p.b);
-  }
-  c->pending.clear();
-}
-
-// Counts a kernel launch of `kind`; with profiling on, brackets it with events.
-struct ProfScope {
-  ofdft_ctx* c;
-  int kind;
-  cudaEvent_t a = nullptr, b = nullptr;
-  ProfScope(ofdft_ctx* c_, int k) : c(c_), kind(k) {
-    c->launches++;
-    c->kind_launches[k]++;
-    if (c->prof) {
-      a = take_event(c);
-      b = take_event(c);
-      if (a && b) cudaEventRecord(a, c->stream);
-    }
-  }
-  ~ProfScope() {
-    if (a && b) {
-      cudaEventRecord(b, c->stream);
-      c->pending.push_back({a, b, kind});
-      if (c->pending.size() > 4096) {
-        cudaEventSynchronize(b);
-        harvest(c);
-      }
-    }
-  }
-};
-
-RedBuf red(ofdft_ctx* c) { return RedBuf{static_cast<double*>(c->partials.p), c->counter}; }
-
-int ensure_partials(ofdft_ctx* c, long long nblocks, int K) {
-  return ensure(c, c->partials, (size_t)nblocks * K * sizeof(double) + 64);
-}
-
-GridDev gdev(const ofdft_grid* g) {
-  GridDev d;
-  d.n1 = g->n[0];
-  d.n2 = g->n[1];
-  d.n3 = g->n[2];
-  d.G = (long long)d.n1 * d.n2 * d.n3;
-  return d;
-}
-
-int check_grid(ofdft_ctx* c, const ofdft_grid* g) {
-  if (!g) return fail(c, OFDFT_EINVAL, "grid is NULL");
-  for (int d = 0; d < 3; ++d)
-    if (g->n[d] < 1 || g->n[d] > (1 << 16)) return fail(c, OFDFT_EINVAL, "grid dimension %d is %d", d, g->n[d]);
-  if (!(g->h > 0.0) || !isfinite(g->h)) return fail(c, OFDFT_EINVAL, "grid spacing must be positive");
-  return OFDFT_OK;
-}
-
-int check_order(ofdft_ctx* c, int fd_order) {
-  if (fd_order < 2 || fd_order > 2 * kMaxR || (fd_order & 1))
-    return fail(c, OFDFT_EINVAL, "fd_order must be even in [2, %d], got %d", 2 * kMaxR, fd_order);
-  return OFDFT_OK;
-}
-
-int check_prec(ofdft_ctx* c, int prec) {
-  if (prec != OFDFT_PREC_FP64 && prec != OFDFT_PREC_MIXED)
-    return fail(c, OFDFT_EINVAL, "precision must be OFDFT_PREC_FP64 or OFDFT_PREC_MIXED");
-  return OFDFT_OK;
-}
-
-// Laplacian weights of Sec. 4 (Eq. FD:Laplacian) in FP64, scaled by `scale`;
-// c = 6 w_0 (the p = 0 term counts the centre six times).
-Weights<double> lap_weights(int R, double h, double scale) {
-  Weights<double> W;
-  memset(&W, 0, sizeof(W));
-  double s = 0.0;
-  for (int q = 1; q <= R; ++q) s += 1.0 / ((double)q * q);
-  W.c = scale * 6.0 * (-s / (h * h));
-  // (R!)^2 / ((R-p)! (R+p)!) as a running product
-  for (int p = 1; p <= R; ++p) {
-    double ratio = 1.0;
-    for (int i = 1; i <= p; ++i) ratio *= (double)(R - p + i) / (double)(R + i);
-    const double sign = (p & 1) ? 1.0 : -1.0;
-    W.w[p] = scale * 2.0 * sign * ratio / (h * h * (double)p * p);
-  }
-  return W;
-}
-
-// Gradient weights of Sec. 4: w~_p = (-1)^{p+1} (R!)^2 / (h p (R-p)! (R+p)!).
-Weights<double> grad_weights(int R, double h) {
-  Weights<double> W;
-  memset(&W, 0, sizeof(W));
-  for (int p = 1; p <= R; ++p) {
-    double ratio = 1.0;
-    for (int i = 1; i <= p; ++i) ratio *= (double)(R - p + i) / (double)(R + i);
-    const double sign = (p & 1) ? 1.0 : -1.0;
-    W.w[p] = sign * ratio / (h * (double)p);
-  }
-  return W;
-}
-
-template <typename T>
-Weights<T> cast_weights(const Weights<double>& W) {
-  Weights<T> o;
-  o.c = (T)W.c;
-  for (int p = 0; p <= kMaxR; ++p) o.w[p] = (T)W.w[p];
-  return o;
-}
-
-int pointwise_blocks(ofdft_ctx* c, long long G) {
-  long long b = (G + 255) / 256;
-  return (int)std::max<long long>(1, std::min<long long>(b, (long long)c->sms * 8));
-}
-
-// z-streaming launch shape: BX x BY columns, z split so that the grid holds
-// about four blocks per SM, each z-chunk at least 2R planes deep.
-struct ZShape {
-  dim3 grid;
-  int zchunk;
-  long long nblocks;
-};
-
-ZShape zshape(ofdft_ctx* c, const GridDev& g, int R) {
-  ZShape s;
-  const int gx = (g.n1 + BX - 1) / BX, gy = (g.n2 + BY - 1) / BY;
-  const long long tiles = (long long)gx * gy;
-  const long long want = (long long)c->sms * 4;
-  int nz = (int)std::max<long long>(1, (want + tiles - 1) / tiles);
-  nz = std::min(nz, std::max(1, g.n3 / std::max(2 * R, 4)));
-  int zc = (g.n3 + nz - 1) / nz;
-  nz = (g.n3 + zc - 1) / zc;
-  s.grid = dim3(gx, gy, nz);
-  s.zchunk = zc;
-  s.nblocks = (long long)gx * gy * nz;
-  return s;
-}
-
-template <typename T, int R, class L, class E>
-int launch_z(ofdft_ctx* c, const GridDev& g, const Weights<double>& W, L ld, E ep, int kind) {
-  const ZShape s = zshape(c, g, R);
-  if (E::K > 0) TRY(ensure_partials(c, s.nblocks, E::K));
-  {
-    ProfScope ps_(c, kind);
-    zstream_kernel<T, R, L, E><<<s.grid, dim3(BX, BY), 0, c->stream>>>(g, cast_weights<T>(W), s.zchunk, ld, ep,
-                                                                       red(c));
-  }
-  CU(cudaGetLastError());
-  return OFDFT_OK;
-}
-
-// Runtime radius -> template radius.
-template <typename T, class L, class E>
-int launch_z_r(ofdft_ctx* c, int R, const GridDev& g, const Weights<double>& W, L ld, E ep, int kind) {
-  switch (R) {
-    case 1: return launch_z<T, 1>(c, g, W, ld, ep, kind);
-    case 2: return launch_z<T, 2>(c, g, W, ld, ep, kind);
-    case 3: return launch_z<T, 3>(c, g, W, ld, ep, kind);
-    case 4: return launch_z<T, 4>(c, g, W, ld, ep, kind);
-    case 5: return launch_z<T, 5>(c, g, W, ld, ep, kind);
-    case 6: return launch_z<T, 6>(c, g, W, ld, ep, kind);
-  }
-  return fail(c, OFDFT_EINVAL, "stencil radius %d not supported", R);
-}
-
-int sync_scalars(ofdft_ctx* c, const void* dev, size_t bytes, void* host) {
-  CU(cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, c->stream));
-  CU(cudaStreamSynchronize(c->stream));
-  if (!c->pending.empty()) harvest(c);
-  return OFDFT_OK;
-}
+namespace ofd {
 
 // ------------------------------------------------------------ Poisson (S3) --
 // Plain CG iterations on the prepared scalars `sc` (residual r, iterate x),
@@ -302,25 +13,32 @@ template <typename T>
 int cg_iterate(ofdft_ctx* c, int R, const GridDev& g, const Weights<double>& Wneg, T* x, T* r, CgScalars* sc,
                int max_it, CgScalars* host_sc) {
   T* p0 = vec<T>(c, V_P0);
-  T* p1 = vec<T>(c, V_P1);
   T* Ap = vec<T>(c, V_AP);
   const int pb = pointwise_blocks(c, g.G);
   TRY(ensure_partials(c, pb, 1));
   const int chunk = 8;
-  int launched = 0;
+  int launched = 0, chunks = 0;
+  // Chunk k+1 is enqueued before the host waits for chunk k's copy of the
+  // scalars, so the stream never drains; kernels of a converged solve return at
+  // once (device `done` flag), so an extra chunk costs only empty launches.
   while (launched < max_it) {
     for (int i = 0; i < chunk && launched < max_it; ++i, ++launched) {
-      T* pp = (launched & 1) ? p1 : p0;  // previous direction
-      T* pc = (launched & 1) ? p0 : p1;  // new direction
-      TRY(launch_z_r<T>(c, R, g, Wneg, LoadCgDir<T>{r, pp, sc}, EpiCgA<T>{pc, Ap, sc}, OFDFT_K_CG_DIR_STENCIL));
+      // p and q = A p live in p0 and Ap and are updated in place
+      TRY(launch_z_r<T>(c, R, g, Wneg, LoadPlain<T>{r}, EpiCgA<T>{p0, Ap, sc}, OFDFT_K_CG_DIR_STENCIL));
       {
         ProfScope ps_(c, OFDFT_K_CG_UPDATE);
-        cg_update_kernel<T><<<pb, 256, 0, c->stream>>>(g.G, x, r, pc, Ap, sc, red(c));
+        cg_update_kernel<T><<<pb, 256, 0, c->stream>>>(g.G, x, r, p0, Ap, sc, red(c));
       }
       CU(cudaGetLastError());
     }
-    TRY(sync_scalars(c, sc, sizeof(CgScalars), host_sc));
-    if (host_sc->done) break;
+    const int slot = chunks & 1;
+    CU(cudaMemcpyAsync(&c->ring[slot], sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaEventRecord(c->ring_ev[slot], c->stream));
+    if (chunks > 0) {
+      CU(cudaEventSynchronize(c->ring_ev[slot ^ 1]));
+      if (c->ring[slot ^ 1].done) break;
+    }
+    ++chunks;
   }
   TRY(sync_scalars(c, sc, sizeof(CgScalars), host_sc));
   return OFDFT_OK;
@@ -417,13 +135,14 @@ int poisson_mixed(ofdft_ctx* c, int R, const GridDev& g, double h, const float* 
 
 // ------------------------------------------------------ functional (S4) ---
 struct EvalOut {
-  double sums[10];
+  double sums[12];
 };
 
 template <typename T>
 int functional_pass(ofdft_ctx* c, int R, const GridDev& g, double h, const ofdft_params* p, const T* u,
                     const T* b, const T* phi, const T* rcg, double eta, double mu, double N,
-                    const double* sum_uu_dev, T* G, T* s, const T* d, const T* s_old, EvalOut* out) {
+                    const double* sum_uu_dev, T* G, T* s, const T* d, const T* s_old, EvalOut* out,
+                    T* winv = nullptr) {
   const Weights<double> W = lap_weights(R, h, 1.0);
   FuncScalars f;
   f.h3 = h * h * h;
@@ -435,9 +154,9 @@ int functional_pass(ofdft_ctx* c, int R, const GridDev& g, double h, const ofdft
   f.kin_vw = -p->lambda * W.c;  // -lambda 6 w_0 > 0
   f.terms = p->terms;
   const bool es = p->terms & OFDFT_TERM_ES;
-  EpiFunctional<T> ep{es ? phi : nullptr, b, es ? rcg : nullptr, d, s_old, G, s, sum_uu_dev, f, c->scal};
+  EpiFunctional<T> ep{es ? phi : nullptr, b, es ? rcg : nullptr, d, s_old, G, s, winv, sum_uu_dev, f, c->scal};
   TRY(launch_z_r<T>(c, R, g, W, LoadPlain<T>{u}, ep, OFDFT_K_FUNCTIONAL));
-  TRY(sync_scalars(c, c->scal, 10 * sizeof(double), out->sums));
+  TRY(sync_scalars(c, c->scal, 12 * sizeof(double), out->sums));
   return OFDFT_OK;
 }
 
@@ -457,6 +176,7 @@ void fill_energy(const EvalOut& o, double h, const ofdft_params* p, double E_sel
   e->gd = h3 * o.sums[5];
   e->gs_old = h3 * o.sums[6];
   e->rs = h3 * o.sums[7];
+  e->rs_pc = e->rs;
   e->gnorm2 = h3 * o.sums[8];
 }
 
@@ -527,10 +247,22 @@ struct Solver {
       rcg = vec<T>(c, V_R);
     }
     EvalOut o;
-    TRY(functional_pass<T>(c, R, g, h, p, at, b, phi, rcg, eta, mu, N, sum_uu, Gout, sout, dd, s_old, &o));
+    T* winv = (p->precond_rank1 && sout) ? vec<T>(c, V_W) : nullptr;
+    TRY(functional_pass<T>(c, R, g, h, p, at, b, phi, rcg, eta, mu, N, sum_uu, Gout, sout, dd, s_old, &o, winv));
     stats->stencil_apps += 2;
     stats->grad_evals += 1;
     fill_energy(o, h, p, E_self, ezz, eta, mu, out);
+    if (winv) {
+      // exact inverse of diag + (4 h^3/mu) u u^T (Sherman-Morrison) applied to r = -G
+      const double cpen = 4.0 * h * h * h / mu;
+      const double gamma = cpen * o.sums[10] / (1.0 + cpen * o.sums[11]);
+      {
+        ProfScope ps_(c, OFDFT_K_VECTOR);
+        rank1_kernel<T><<<pointwise_blocks(c, g.G), 256, 0, c->stream>>>(g.G, sout, winv, gamma);
+      }
+      CU(cudaGetLastError());
+      out->rs_pc -= h * h * h * gamma * o.sums[10];
+    }
     out->poisson = cs;
     return OFDFT_OK;
   }
@@ -573,7 +305,7 @@ struct Solver {
     const double tol_in = p->tol_inner * M;
     TRY(eval(u, G, s, nullptr, nullptr, eta, mu, &e));
     TRY(direction(0.0));  // d = s
-    double delta_new = e.rs;
+    double delta_new = e.rs_pc;
     int k = 0;
     for (int it = 0; it < p->max_nlcg; ++it) {
       if (e.rs < tol_in) {
@@ -594,11 +326,13 @@ struct Solver {
         g0 = h3 * gdd[0];
         dd = h3 * gdd[1];
       }
-      // trial point at sigma0 along d
-      TRY(axpy_abs(ut, u, d, p->sigma0));
+      // trial point at sig along d (sigma0, capped to an RMS change of trial_max_rel of u)
+      double sig = p->sigma0;
+      if (p->trial_max_rel > 0.0 && dd > 0.0) sig = std::min(sig, p->trial_max_rel * sqrt(N / dd));
+      TRY(axpy_abs(ut, u, d, sig));
       ofdft_energy et;
       TRY(eval(ut, Gt, st, d, s_old, eta, mu, &et));
-      double alpha = -p->sigma0, gprev = et.gd, gcur = g0;
+      double alpha = -sig, gprev = et.gd, gcur = g0;
       if (!((gcur - gprev) / alpha > 0.0)) {
         // no positive curvature between 0 and sigma0: keep the trial point
         std::swap(u, ut);
@@ -607,10 +341,18 @@ struct Solver {
         e = et;
       } else {
         T* snew = sn;
+        const double L0 = e.L;
         for (int j = 1; j <= p->max_secant; ++j) {
           alpha = alpha * gcur / (gprev - gcur);
-          TRY(axpy_abs(u, u, d, alpha));
-          TRY(eval(u, G, snew, d, s_old, eta, mu, &e));
+          // candidate written beside u so that a rejected step can be halved
+          TRY(axpy_abs(ut, u, d, alpha));
+          TRY(eval(ut, G, snew, d, s_old, eta, mu, &e));
+          for (int bt = 0; bt < p->max_backtrack && !(e.L <= L0); ++bt) {
+            alpha *= 0.5;
+            TRY(axpy_abs(ut, u, d, alpha));
+            TRY(eval(ut, G, snew, d, s_old, eta, mu, &e));
+          }
+          std::swap(u, ut);
           gprev = gcur;
           gcur = e.gd;
           if (j == p->max_secant || alpha * alpha * dd <= p->eps_secant * p->eps_secant * N) break;
@@ -622,7 +364,7 @@ struct Solver {
       }
       const double delta_old = delta_new;
       const double delta_mid = -e.gs_old;
-      delta_new = e.rs;
+      delta_new = e.rs_pc;
       const double beta = (delta_new - delta_mid) / delta_old;
       ++k;
       if (k >= p->restart_every || !(beta > 0.0)) {
@@ -637,17 +379,6 @@ struct Solver {
   }
 };
 
-template <typename T>
-int device_pseudocharge(ofdft_ctx* c, const ofdft_grid* gr, int R, const double* R_host, const double* Z_host,
-                        int M, double sigma, double rc, T* b, double* E_self);
-template <typename T>
-int device_guess(ofdft_ctx* c, const ofdft_grid* gr, const double* R_host, const double* Z_host, int M,
-                 double gsig, double gcut, double N, T* u);
-template <typename T>
-int device_forces(ofdft_ctx* c, const ofdft_grid* gr, int R, const double* R_host, const double* Z_host, int M,
-                  double sigma, double rc, int variant, const T* phi, double* F);
-int device_ezz(ofdft_ctx* c, const double* R_host, const double* Z_host, int M, double sigma, double* E,
-               double* F);
 
 // Copies atoms to a device scratch buffer (V_ATOM0): R (3M) then Z (M).
 int upload_atoms(ofdft_ctx* c, const double* R_host, const double* Z_host, int M, AtomArgs* A,
@@ -858,6 +589,7 @@ int solve_impl(ofdft_ctx* c, const ofdft_grid* gr, const double* R_host, const d
   const size_t es = sizeof(T);
   // workspace
   for (int v : {V_U, V_UT, V_PHI, V_B, V_G, V_GT, V_S, V_ST, V_SN, V_D}) TRY(ensure(c, c->v[v], g.G * es));
+  if (p->precond_rank1) TRY(ensure(c, c->v[V_W], g.G * es));
   TRY(ensure_cg_vectors(c, g.G, es, mixed));
   if (mixed) {
     TRY(ensure(c, c->v[V_B64], g.G * sizeof(double)));
@@ -960,7 +692,22 @@ int check_params(ofdft_ctx* c, const ofdft_params* p) {
   return OFDFT_OK;
 }
 
-}  // namespace
+template int device_pseudocharge<double>(ofdft_ctx*, const ofdft_grid*, int, const double*, const double*, int,
+                                         double, double, double*, double*);
+template int device_pseudocharge<float>(ofdft_ctx*, const ofdft_grid*, int, const double*, const double*, int,
+                                        double, double, float*, double*);
+template int device_guess<double>(ofdft_ctx*, const ofdft_grid*, const double*, const double*, int, double, double,
+                                  double, double*);
+template int device_guess<float>(ofdft_ctx*, const ofdft_grid*, const double*, const double*, int, double, double,
+                                 double, float*);
+template int device_forces<double>(ofdft_ctx*, const ofdft_grid*, int, const double*, const double*, int, double,
+                                   double, int, const double*, double*);
+template int device_forces<float>(ofdft_ctx*, const ofdft_grid*, int, const double*, const double*, int, double,
+                                  double, int, const float*, double*);
+
+}  // namespace ofd
+
+using namespace ofd;
 
 // ===================================================================== C ABI
 extern "C" {
@@ -995,6 +742,9 @@ void ofdft_default_params(ofdft_params* p) {
   p->vacuum = 8.0;
   p->round_to = 16;
   p->refine_every = 200;
+  p->trial_max_rel = 0.2;
+  p->max_backtrack = 2;
+  p->precond_rank1 = 1;
 }
 
 int ofdft_create(ofdft_ctx** out, int device, void* stream) {
@@ -1012,7 +762,10 @@ int ofdft_create(ofdft_ctx** out, int device, void* stream) {
   if (cudaMalloc(&c->counter, 64) != cudaSuccess || cudaMemset(c->counter, 0, 64) != cudaSuccess ||
       cudaMalloc(&c->sc, 2 * sizeof(CgScalars)) != cudaSuccess ||
       cudaMalloc(&c->scal, 64 * sizeof(double)) != cudaSuccess ||
-      cudaMallocHost(&c->host_scal, 64 * sizeof(double)) != cudaSuccess) {
+      cudaMallocHost(&c->host_scal, 64 * sizeof(double)) != cudaSuccess ||
+      cudaMallocHost(&c->ring, 2 * sizeof(CgScalars)) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ring_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ring_ev[1], cudaEventDisableTiming) != cudaSuccess) {
     delete c;
     return OFDFT_ENOMEM;
   }
@@ -1037,6 +790,9 @@ int ofdft_destroy(ofdft_ctx* c) {
   cudaFree(c->sc);
   cudaFree(c->scal);
   cudaFreeHost(c->host_scal);
+  cudaFreeHost(c->ring);
+  for (cudaEvent_t e : c->ring_ev)
+    if (e) cudaEventDestroy(e);
   delete c;
   return OFDFT_OK;
 }

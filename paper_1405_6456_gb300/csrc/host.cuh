@@ -1,0 +1,319 @@
+// Host-side infrastructure shared by the translation units of the library:
+// the context (device workspaces, reduction scratch, trace counters), error
+// handling, stencil weights of Sec. 4, and kernel launch configuration.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/ofdft.h"
+#include "kernels.cuh"
+
+
+// ----------------------------------------------------------------- context --
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+using ofd::CgScalars;
+
+struct ofdft_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  int sms = 152;
+  // reduction scratch
+  DevBuf partials;
+  unsigned int* counter = nullptr;
+  // small device scalars: CG scalars (2 sets), functional outputs, dot outputs
+  CgScalars* sc = nullptr;
+  CgScalars* sc32 = nullptr;
+  double* scal = nullptr;  // 64 doubles
+  double* host_scal = nullptr;  // pinned mirror
+  // named vector workspaces
+  DevBuf v[24];
+  // launch counters and optional CUDA-event timing of every launch
+  long long launches = 0;
+  long long kind_launches[OFDFT_K_COUNT] = {0};
+  long long timed_launches[OFDFT_K_COUNT] = {0};
+  double timed_ms[OFDFT_K_COUNT] = {0};
+  int prof = 0;
+  struct Pending {
+    cudaEvent_t a, b;
+    int kind;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> free_events;
+  // pinned double buffer for polling CG flags without draining the stream
+  CgScalars* ring = nullptr;
+  cudaEvent_t ring_ev[2] = {nullptr, nullptr};
+};
+
+namespace ofd {
+
+enum Vec {
+  V_R = 0, V_P0, V_P1, V_AP,           // CG vectors (prec type)
+  V_R64, V_PHI64, V_B64, V_E32,        // mixed refinement (FP64 r, phi, b; FP32 correction)
+  V_U, V_UT, V_PHI, V_B,               // solve state
+  V_G, V_GT, V_S, V_ST, V_SN, V_D,     // NLCG vectors
+  V_ATOM0, V_ATOM1, V_ATOM2,           // atom scratch
+  V_W,                                 // u / Jacobi diagonal (rank-one preconditioner)
+  V_COUNT
+};
+
+inline int fail(ofdft_ctx* c, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return code;
+}
+
+#define CU(call)                                                                   \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess)                                                         \
+      return fail(c, e_ == cudaErrorMemoryAllocation ? OFDFT_ENOMEM : OFDFT_ECUDA, \
+                  "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)
+
+#define TRY(expr)            \
+  do {                       \
+    int rc_ = (expr);        \
+    if (rc_ != OFDFT_OK) return rc_; \
+  } while (0)
+
+inline int ensure(ofdft_ctx* c, DevBuf& b, size_t bytes) {
+  if (b.bytes >= bytes && b.p) return OFDFT_OK;
+  if (b.p) {
+    CU(cudaStreamSynchronize(c->stream));
+    CU(cudaFree(b.p));
+    b.p = nullptr;
+    b.bytes = 0;
+  }
+  const size_t want = std::max<size_t>(bytes, 256);
+  CU(cudaMalloc(&b.p, want));
+  b.bytes = want;
+  return OFDFT_OK;
+}
+
+template <typename T>
+T* vec(ofdft_ctx* c, int which) {
+  return static_cast<T*>(c->v[which].p);
+}
+
+inline cudaEvent_t take_event(ofdft_ctx* c) {
+  if (!c->free_events.empty()) {
+    cudaEvent_t e = c->free_events.back();
+    c->free_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Folds the durations of completed timed launches into the totals (call after
+// the stream has been synchronised) and recycles their events.
+inline void harvest(ofdft_ctx* c) {
+  for (auto& p : c->pending) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      c->timed_ms[p.kind] += ms;
+      c->timed_launches[p.kind] += 1;
+    }
+    c->free_events.push_back(p.a);
+    c->free_events.push_back(p.b);
+  }
+  c->pending.clear();
+}
+
+// Counts a kernel launch of `kind`; with profiling on, brackets it with events.
+struct ProfScope {
+  ofdft_ctx* c;
+  int kind;
+  cudaEvent_t a = nullptr, b = nullptr;
+  ProfScope(ofdft_ctx* c_, int k) : c(c_), kind(k) {
+    c->launches++;
+    c->kind_launches[k]++;
+    if (c->prof) {
+      a = take_event(c);
+      b = take_event(c);
+      if (a && b) cudaEventRecord(a, c->stream);
+    }
+  }
+  ~ProfScope() {
+    if (a && b) {
+      cudaEventRecord(b, c->stream);
+      c->pending.push_back({a, b, kind});
+      if (c->pending.size() > 4096) {
+        cudaEventSynchronize(b);
+        harvest(c);
+      }
+    }
+  }
+};
+
+inline RedBuf red(ofdft_ctx* c) { return RedBuf{static_cast<double*>(c->partials.p), c->counter}; }
+
+inline int ensure_partials(ofdft_ctx* c, long long nblocks, int K) {
+  return ensure(c, c->partials, (size_t)nblocks * K * sizeof(double) + 64);
+}
+
+inline GridDev gdev(const ofdft_grid* g) {
+  GridDev d;
+  d.n1 = g->n[0];
+  d.n2 = g->n[1];
+  d.n3 = g->n[2];
+  d.G = (long long)d.n1 * d.n2 * d.n3;
+  return d;
+}
+
+inline int check_grid(ofdft_ctx* c, const ofdft_grid* g) {
+  if (!g) return fail(c, OFDFT_EINVAL, "grid is NULL");
+  for (int d = 0; d < 3; ++d)
+    if (g->n[d] < 1 || g->n[d] > (1 << 16)) return fail(c, OFDFT_EINVAL, "grid dimension %d is %d", d, g->n[d]);
+  if (!(g->h > 0.0) || !isfinite(g->h)) return fail(c, OFDFT_EINVAL, "grid spacing must be positive");
+  return OFDFT_OK;
+}
+
+inline int check_order(ofdft_ctx* c, int fd_order) {
+  if (fd_order < 2 || fd_order > 2 * kMaxR || (fd_order & 1))
+    return fail(c, OFDFT_EINVAL, "fd_order must be even in [2, %d], got %d", 2 * kMaxR, fd_order);
+  return OFDFT_OK;
+}
+
+inline int check_prec(ofdft_ctx* c, int prec) {
+  if (prec != OFDFT_PREC_FP64 && prec != OFDFT_PREC_MIXED)
+    return fail(c, OFDFT_EINVAL, "precision must be OFDFT_PREC_FP64 or OFDFT_PREC_MIXED");
+  return OFDFT_OK;
+}
+
+// Laplacian weights of Sec. 4 (Eq. FD:Laplacian) in FP64, scaled by `scale`;
+// c = 6 w_0 (the p = 0 term counts the centre six times).
+inline Weights<double> lap_weights(int R, double h, double scale) {
+  Weights<double> W;
+  memset(&W, 0, sizeof(W));
+  double s = 0.0;
+  for (int q = 1; q <= R; ++q) s += 1.0 / ((double)q * q);
+  W.c = scale * 6.0 * (-s / (h * h));
+  // (R!)^2 / ((R-p)! (R+p)!) as a running product
+  for (int p = 1; p <= R; ++p) {
+    double ratio = 1.0;
+    for (int i = 1; i <= p; ++i) ratio *= (double)(R - p + i) / (double)(R + i);
+    const double sign = (p & 1) ? 1.0 : -1.0;
+    W.w[p] = scale * 2.0 * sign * ratio / (h * h * (double)p * p);
+  }
+  return W;
+}
+
+// Gradient weights of Sec. 4: w~_p = (-1)^{p+1} (R!)^2 / (h p (R-p)! (R+p)!).
+inline Weights<double> grad_weights(int R, double h) {
+  Weights<double> W;
+  memset(&W, 0, sizeof(W));
+  for (int p = 1; p <= R; ++p) {
+    double ratio = 1.0;
+    for (int i = 1; i <= p; ++i) ratio *= (double)(R - p + i) / (double)(R + i);
+    const double sign = (p & 1) ? 1.0 : -1.0;
+    W.w[p] = sign * ratio / (h * (double)p);
+  }
+  return W;
+}
+
+template <typename T>
+Weights<T> cast_weights(const Weights<double>& W) {
+  Weights<T> o;
+  o.c = (T)W.c;
+  for (int p = 0; p <= kMaxR; ++p) o.w[p] = (T)W.w[p];
+  return o;
+}
+
+inline int pointwise_blocks(ofdft_ctx* c, long long G) {
+  long long b = (G + 255) / 256;
+  return (int)std::max<long long>(1, std::min<long long>(b, (long long)c->sms * 8));
+}
+
+// z-streaming launch shape: BX x BY columns, z split so that the grid holds
+// about four blocks per SM, each z-chunk at least 2R planes deep.
+struct ZShape {
+  dim3 grid;
+  int zchunk;
+  long long nblocks;
+};
+
+inline ZShape zshape(ofdft_ctx* c, const GridDev& g, int R) {
+  ZShape s;
+  const int gx = (g.n1 + BX - 1) / BX, gy = (g.n2 + BY - 1) / BY;
+  const long long tiles = (long long)gx * gy;
+  const long long want = (long long)c->sms * 4;
+  int nz = (int)std::max<long long>(1, (want + tiles - 1) / tiles);
+  nz = std::min(nz, std::max(1, g.n3 / std::max(2 * R, 4)));
+  int zc = (g.n3 + nz - 1) / nz;
+  nz = (g.n3 + zc - 1) / zc;
+  s.grid = dim3(gx, gy, nz);
+  s.zchunk = zc;
+  s.nblocks = (long long)gx * gy * nz;
+  return s;
+}
+
+template <typename T, int R, class L, class E>
+int launch_z(ofdft_ctx* c, const GridDev& g, const Weights<double>& W, L ld, E ep, int kind) {
+  const ZShape s = zshape(c, g, R);
+  if (E::K > 0) TRY(ensure_partials(c, s.nblocks, E::K));
+  {
+    ProfScope ps_(c, kind);
+    zstream_kernel<T, R, L, E><<<s.grid, dim3(BX, BY), 0, c->stream>>>(g, cast_weights<T>(W), s.zchunk, ld, ep,
+                                                                       red(c));
+  }
+  CU(cudaGetLastError());
+  return OFDFT_OK;
+}
+
+// Runtime radius -> template radius.
+template <typename T, class L, class E>
+int launch_z_r(ofdft_ctx* c, int R, const GridDev& g, const Weights<double>& W, L ld, E ep, int kind) {
+  switch (R) {
+    case 1: return launch_z<T, 1>(c, g, W, ld, ep, kind);
+    case 2: return launch_z<T, 2>(c, g, W, ld, ep, kind);
+    case 3: return launch_z<T, 3>(c, g, W, ld, ep, kind);
+    case 4: return launch_z<T, 4>(c, g, W, ld, ep, kind);
+    case 5: return launch_z<T, 5>(c, g, W, ld, ep, kind);
+    case 6: return launch_z<T, 6>(c, g, W, ld, ep, kind);
+  }
+  return fail(c, OFDFT_EINVAL, "stencil radius %d not supported", R);
+}
+
+
+inline int sync_scalars(ofdft_ctx* c, const void* dev, size_t bytes, void* host) {
+  CU(cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  if (!c->pending.empty()) harvest(c);
+  return OFDFT_OK;
+}
+
+// Routines of api.cu used by the batched engine (instantiated for double and float).
+int check_atoms(ofdft_ctx* c, const double* R, const double* Z, int M);
+int check_params(ofdft_ctx* c, const ofdft_params* p);
+template <typename T>
+int device_pseudocharge(ofdft_ctx* c, const ofdft_grid* gr, int R, const double* R_host, const double* Z_host,
+                        int M, double sigma, double rc, T* b, double* E_self);
+template <typename T>
+int device_guess(ofdft_ctx* c, const ofdft_grid* gr, const double* R_host, const double* Z_host, int M,
+                 double gsig, double gcut, double N, T* u);
+template <typename T>
+int device_forces(ofdft_ctx* c, const ofdft_grid* gr, int R, const double* R_host, const double* Z_host, int M,
+                  double sigma, double rc, int variant, const T* phi, double* F);
+int device_ezz(ofdft_ctx* c, const double* R_host, const double* Z_host, int M, double sigma, double* E,
+               double* F);
+
+}  // namespace ofd

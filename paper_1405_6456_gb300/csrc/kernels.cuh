@@ -62,6 +62,16 @@ __global__ void __launch_bounds__(NT) zstream_kernel(GridDev g, Weights<T> W, in
   const long long col = (long long)x + (long long)g.n1 * y;
   const long long plane = (long long)g.n1 * g.n2;
 
+  // halo nodes this thread stages: x-halo (tx < R) left/right, y-halo (ty < R) below/above
+  const int xl = blockIdx.x * BX - R + tx, xr = blockIdx.x * BX + BX + tx;
+  const int yb = blockIdx.y * BY - R + ty, yt = blockIdx.y * BY + BY + ty;
+  const bool hx = tx < R, hy = ty < R;
+  const bool okl = hx && y < g.n2 && xl >= 0, okr = hx && y < g.n2 && xr < g.n1;
+  const bool okb = hy && x < g.n1 && yb >= 0, okt = hy && x < g.n1 && yt < g.n2;
+  const long long il = (long long)g.n1 * y + xl, ir = (long long)g.n1 * y + xr;
+  const long long ib = (long long)g.n1 * yb + x, it = (long long)g.n1 * yt + x;
+
+  // register queue of the block's own column along z (planes k-R .. k+R)
   T q[2 * R + 1];
 #pragma unroll
   for (int i = 0; i < 2 * R; ++i) {
@@ -70,14 +80,22 @@ __global__ void __launch_bounds__(NT) zstream_kernel(GridDev g, Weights<T> W, in
                                                                   : ld.value(col + plane * k))
                                          : T(0);
   }
+  // halo values prefetched PF planes ahead, so their loads overlap earlier steps
+  constexpr int PF = 4;
+  T hv[PF][4];
+#pragma unroll
+  for (int j = 0; j < PF; ++j) {
+    const int k = z0 + j;
+    const bool kk = k < z1;
+    const long long pk = plane * k;
+    hv[j][0] = (kk && okl) ? ld.value(pk + il) : T(0);
+    hv[j][1] = (kk && okr) ? ld.value(pk + ir) : T(0);
+    hv[j][2] = (kk && okb) ? ld.value(pk + ib) : T(0);
+    hv[j][3] = (kk && okt) ? ld.value(pk + it) : T(0);
+  }
   double acc[Epi::K > 0 ? Epi::K : 1];
 #pragma unroll
   for (int i = 0; i < (Epi::K > 0 ? Epi::K : 1); ++i) acc[i] = 0.0;
-
-  // halo coordinates of this thread (x-halo for tx < R, y-halo for ty < R)
-  const int xl = blockIdx.x * BX - R + tx, xr = blockIdx.x * BX + BX + tx;
-  const int yb = blockIdx.y * BY - R + ty, yt = blockIdx.y * BY + BY + ty;
-  const bool yok = y < g.n2, xok = x < g.n1;
 
   for (int k = z0; k < z1; ++k) {
     const int kf = k + R;
@@ -86,14 +104,27 @@ __global__ void __launch_bounds__(NT) zstream_kernel(GridDev g, Weights<T> W, in
                                     : T(0);
     __syncthreads();
     s[ty + R][tx + R] = q[R];
-    const long long pk = plane * k;
-    if (tx < R) {
-      s[ty + R][tx] = (yok && xl >= 0) ? ld.value(pk + (long long)g.n1 * y + xl) : T(0);
-      s[ty + R][tx + BX + R] = (yok && xr < g.n1) ? ld.value(pk + (long long)g.n1 * y + xr) : T(0);
+    if (hx) {
+      s[ty + R][tx] = hv[0][0];
+      s[ty + R][tx + BX + R] = hv[0][1];
     }
-    if (ty < R) {
-      s[ty][tx + R] = (xok && yb >= 0) ? ld.value(pk + (long long)g.n1 * yb + x) : T(0);
-      s[ty + BY + R][tx + R] = (xok && yt < g.n2) ? ld.value(pk + (long long)g.n1 * yt + x) : T(0);
+    if (hy) {
+      s[ty][tx + R] = hv[0][2];
+      s[ty + BY + R][tx + R] = hv[0][3];
+    }
+#pragma unroll
+    for (int j = 0; j < PF - 1; ++j) {
+#pragma unroll
+      for (int m = 0; m < 4; ++m) hv[j][m] = hv[j + 1][m];
+    }
+    {
+      const int kn = k + PF;
+      const bool kk = kn < z1;
+      const long long pk = plane * kn;
+      hv[PF - 1][0] = (kk && okl) ? ld.value(pk + il) : T(0);
+      hv[PF - 1][1] = (kk && okr) ? ld.value(pk + ir) : T(0);
+      hv[PF - 1][2] = (kk && okb) ? ld.value(pk + ib) : T(0);
+      hv[PF - 1][3] = (kk && okt) ? ld.value(pk + it) : T(0);
     }
     __syncthreads();
     if (in_xy) {
@@ -105,7 +136,7 @@ __global__ void __launch_bounds__(NT) zstream_kernel(GridDev g, Weights<T> W, in
         const T sz = q[R + p] + q[R - p];
         lap = fma(W.w[p], (sx + sy) + sz, lap);
       }
-      ep.apply(col + pk, q[R], lap, acc);
+      ep.apply(col + plane * k, q[R], lap, acc);
     }
 #pragma unroll
     for (int i = 0; i < 2 * R; ++i) q[i] = q[i + 1];
@@ -151,19 +182,31 @@ struct EpiStore {
   __device__ __forceinline__ void operator()(double*) const {}
 };
 
-// CG step, first half (S3): Ap = (-L_h) p with p formed by LoadCgDir; writes p
-// and Ap, reduces p.Ap, and alpha = rr / pAp.  The weights carry the minus sign.
+// CG step, first half (S3).  The stencil is applied to the residual r (a plain
+// array): with p = r + beta p_old and q = A p, linearity gives
+// q = A r + beta q_old, so p and q are updated in place at each node and only r
+// is read with a halo.  Reduces p.q; the last block sets alpha = rr / p.q.  The
+// weights carry the minus sign of A = -L_h.
 template <typename T>
 struct EpiCgA {
   static constexpr int K = 1;
   T* p;
-  T* Ap;
+  T* q;
   CgScalars* sc;
   __device__ __forceinline__ bool skip() const { return sc->done != 0; }
-  __device__ __forceinline__ void apply(long long i, T pc, T ap, double* acc) const {
+  __device__ __forceinline__ void apply(long long i, T rc, T ar, double* acc) const {
+    T pc, qc;
+    if (sc->first) {
+      pc = rc;
+      qc = ar;
+    } else {
+      const T be = (T)sc->beta;
+      pc = fma(be, p[i], rc);
+      qc = fma(be, q[i], ar);
+    }
     p[i] = pc;
-    Ap[i] = ap;
-    acc[0] += (double)pc * (double)ap;
+    q[i] = qc;
+    acc[0] += (double)pc * (double)qc;
   }
   __device__ __forceinline__ void operator()(double* t) const {
     sc->pAp = t[0];
@@ -261,7 +304,7 @@ struct FuncScalars {
 // the Jacobi diagonal and s = -G / diag, and nine FP64 partial sums.
 template <typename T>
 struct EpiFunctional {
-  static constexpr int K = 9;
+  static constexpr int K = 11;
   const T* phi;
   const T* b;
   const T* rcg;
@@ -269,9 +312,10 @@ struct EpiFunctional {
   const T* s_old;
   T* G;
   T* s;
+  T* winv;               // optional: u / diag (rank-one correction of the preconditioner)
   const double* sum_uu;  // device sum of u^2 (C_h = h^3 sum_uu - N)
   FuncScalars f;
-  double* out;  // 9 sums + C
+  double* out;  // 11 sums + C
   __device__ __forceinline__ bool skip() const { return false; }
   __device__ __forceinline__ void apply(long long i, T uc, T lap, double* acc) const {
     const double C = f.h3 * *sum_uu - f.N;
@@ -304,15 +348,20 @@ struct EpiFunctional {
     const T sx = -gx / md;
     if (G) G[i] = gx;
     if (s) s[i] = sx;
+    if (winv) winv[i] = uc / md;
     if (d) acc[5] += (double)gx * (double)d[i];
     if (s_old) acc[6] += (double)gx * (double)s_old[i];
     acc[7] += (double)gx * (double)gx / (double)md;
     acc[8] += (double)gx * (double)gx;
+    acc[9] += (double)uc * (double)sx;
+    acc[10] += (double)uc * (double)uc / (double)md;
   }
   __device__ __forceinline__ void operator()(double* t) const {
 #pragma unroll
     for (int k = 0; k < 9; ++k) out[k] = t[k];
     out[9] = f.h3 * *sum_uu - f.N;
+    out[10] = t[9];
+    out[11] = t[10];
   }
 };
 
@@ -350,6 +399,14 @@ __global__ void __launch_bounds__(256) cg_update_kernel(long long G, T* __restri
 }
 
 // ----------------------------------------------------------- vector ops ---
+// s -= gamma w (rank-one correction of the preconditioned residual).
+template <typename T>
+__global__ void __launch_bounds__(256) rank1_kernel(long long G, T* s, const T* w, double gamma) {
+  const T ga = (T)gamma;
+  for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < G; i += (long long)gridDim.x * 256)
+    s[i] = fma(-ga, w[i], s[i]);
+}
+
 // out = |a + alpha b| (trial point and secant update of Sec. 4, u <- |u|).
 template <typename T>
 __global__ void __launch_bounds__(256) axpy_abs_kernel(long long G, T* out, const T* a, const T* b,

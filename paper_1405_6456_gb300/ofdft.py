@@ -57,7 +57,8 @@ class Params(C.Structure):
                 ("max_secant", C.c_int), ("sigma0", C.c_double), ("eps_secant", C.c_double),
                 ("restart_every", C.c_int), ("force_variant", C.c_int),
                 ("ezz_correction", C.c_int), ("vacuum", C.c_double), ("round_to", C.c_int),
-                ("refine_every", C.c_int)]
+                ("refine_every", C.c_int), ("trial_max_rel", C.c_double), ("max_backtrack", C.c_int),
+                ("precond_rank1", C.c_int)]
 
 
 class CgStats(C.Structure):
@@ -69,7 +70,7 @@ class Energy(C.Structure):
                 ("E_vw", C.c_double), ("E_xc", C.c_double), ("E_es", C.c_double),
                 ("E_self", C.c_double), ("E_zz_corr", C.c_double), ("C", C.c_double),
                 ("gd", C.c_double), ("gs_old", C.c_double), ("gnorm2", C.c_double),
-                ("rs", C.c_double), ("poisson", CgStats)]
+                ("rs", C.c_double), ("rs_pc", C.c_double), ("poisson", CgStats)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "poisson"}

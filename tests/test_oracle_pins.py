@@ -322,7 +322,9 @@ def test_vw_only_ground_state_is_lowest_laplacian_eigenpair(n):
         mu_min += mu_d
     E_exact = 0.5 * lam * N * mu_min
     assert res.converged
-    assert res.E == pytest.approx(E_exact, rel=1e-9)
+    # E = (lambda/2) mu_min h^3 u.u exactly along the eigenvector, and h^3 u.u = N + C
+    assert res.E == pytest.approx(E_exact * (N + res.C) / N, rel=1e-10)
+    assert res.E == pytest.approx(E_exact, rel=1e-8)
     assert res.eta == pytest.approx(E_exact / N, rel=1e-5)  # multiplier: first order in the residual
     assert abs(res.C) < 1e-8 * N
     assert (u >= 0).all()
@@ -339,7 +341,7 @@ def test_tf_only_ground_state_is_uniform_density():
     res, u, _, _ = O.solve(g, p, np.zeros((1, 3)), [N], u0=u0)
     G = g.size
     h3 = g.h**3
-    rho = N / (h3 * G)
+    rho = (N + res.C) / (h3 * G)  # uniform density at the achieved norm h^3 u.u = N + C
     CF = 2.871234000188191
     assert res.E == pytest.approx(CF * h3 * G * rho ** (5 / 3), rel=1e-9)
     assert res.eta == pytest.approx(5 / 3 * CF * rho ** (2 / 3), rel=1e-6)
@@ -388,10 +390,10 @@ def test_al_penalty_and_lagrange_multiplier_agree(dimer_ground_state):
     """Sec. 5.3.2 / Table ComparisonApproaches: the three constraint treatments
     reach the same energy (paper: within 1e-4 eV/atom = 3.7e-6 Ha/atom)."""
     c, g, p0, res0, u0, _, _ = dimer_ground_state
-    # the penalty's small mu makes the direction along u stiff: one secant step
-    # from the sigma0 trial point overshoots, two are enough
+    # the penalty's small mu makes the direction along u stiff (curvature 4N/mu):
+    # the rank-one term of the preconditioner (R4) inverts it exactly
     res_p, _, _, _ = O.solve(g, _solve_params(fd_n=3, method=O.PENALTY, tol_E=1e-9,
-                                              tol_inner=1e-12, max_secant=2), c.R, c.Z)
+                                              tol_inner=1e-12), c.R, c.Z)
     res_l, u_l, _, _ = O.solve(g, _solve_params(fd_n=3, method=O.LM, tol_inner=1e-10), c.R, c.Z)
     assert res_p.converged and res_l.converged
     assert res_p.E / c.M == pytest.approx(res0.E / c.M, abs=1e-8)
