@@ -243,7 +243,7 @@ def run_gpu(args):
     # timed region (device time per step, L2 flushed between steps)
     dom = F.K_CG_DIR_STENCIL
     ctx.reset_counters()
-    ctx.profile(args.profile_timed)
+    ctx.profile((1 << dom) if args.profile_timed else 0)  # events around the dominant kernel only
     lat = []
     stats = []
     barrier(pg)
@@ -298,20 +298,20 @@ def run_gpu(args):
             pass
         if prec == F.PREC_MIXED:
             peak, which = load_peaks()
-            algo = G * 4 * es  # read r, p_prev; write p, Ap
+            algo = G * 5 * es  # read r (stencil), p, q; write p, q
             ach = algo / avg_s / 1e9
             roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                    "traffic": traffic, "kernel": "zstream_kernel<float,6,LoadCgDir,EpiCgA>",
+                    "traffic": traffic, "kernel": "zstream_kernel<float,6,LoadPlain,EpiCgA> (CG: q = A r + beta q, p = r + beta p, p.q)",
                     "launches": tl, "avg_us": avg_s * 1e6, "peak_source": which,
                     "algorithmic_bytes_per_launch": algo}
         else:
-            flops = G * (2 * (6 * n + 1) + 2 + 2)
+            flops = G * (2 * (6 * n + 1) + 2 + 2 + 2)  # stencil, p and q updates, p.q
             ach = flops / avg_s / 1e9
             roof = {"bound": "alu", "achieved": ach, "peak": FP64_ALU_PEAK_GFLOPS, "unit": "GFLOP/s",
                     "frac": ach / FP64_ALU_PEAK_GFLOPS, "traffic": traffic,
-                    "kernel": "zstream_kernel<double,6,LoadCgDir,EpiCgA>", "launches": tl,
+                    "kernel": "zstream_kernel<double,6,LoadPlain,EpiCgA> (CG: q = A r + beta q, p = r + beta p, p.q)", "launches": tl,
                     "avg_us": avg_s * 1e6, "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2070 MHz",
-                    "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": G * 4 * es}
+                    "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": G * 5 * es}
     kinds = {F.KIND_NAMES[k]: {"launches": int(cnt.kind_launches[k]),
                                "ms": round(cnt.timed_ms[k], 3)} for k in range(7) if cnt.kind_launches[k]}
     st = stats[-1]

@@ -189,7 +189,8 @@ int ofdft_poisson(ofdft_ctx* ctx, const ofdft_grid* g, int fd_order, int prec, c
  *   G = -lambda L_h u + 2 (V_K + V_xc + phi) u + 2 (-eta + C/mu) u
  * G is (1/h^3) dL/du, twice the discrete Euler-Lagrange expression of Sec. 4
  * (Eq. EulerLagrangeDiscretized).  Optional device outputs: grad (G) and s (the
- * Jacobi-preconditioned residual -G/diag); optional device inputs d and s_old
+ * preconditioned residual: -G/diag, and with p->precond_rank1 the exact inverse of
+ * diag + (4h^3/mu) u u^T applied to -G); optional device inputs d and s_old
  * give out->gd = h^3 G.d and out->gs_old = h^3 G.s_old.  mu = +inf drops the
  * penalty term.  u, b, phi, grad, s, d, s_old: device arrays of the `prec` type
  * (p->precision).  Synchronises; results in *out. */
@@ -244,13 +245,47 @@ typedef struct {
 } ofdft_counters;
 
 /* Tracing (no counterpart in the paper, which reports wall time and counts of
- * matrix-vector products): with enable != 0 every kernel launch on the context's
- * stream is bracketed by a pair of CUDA events and its duration is summed per
- * kind; with 0 only launches are counted.  Costs two event records per launch. */
-int ofdft_profile(ofdft_ctx* ctx, int enable);
+ * matrix-vector products): every launch is counted per kind; launches of the
+ * kinds whose bit (1 << OFDFT_K_*) is set in kind_mask are also bracketed by a
+ * pair of CUDA events on the context's stream and their durations summed
+ * (kind_mask = -1: all kinds, 0: counting only).  Costs two event records per
+ * timed launch. */
+int ofdft_profile(ofdft_ctx* ctx, int kind_mask);
 /* Copies the counters (synchronises the stream first). */
 int ofdft_get_counters(ofdft_ctx* ctx, ofdft_counters* out);
 int ofdft_reset_counters(ofdft_ctx* ctx);
+
+/* S11/S12 - batched and continuously served ground states.  A batch holds
+ * solve requests (the same inputs as ofdft_solve) and advances every admitted
+ * solve by one evaluation round per ofdft_batch_step: the rounds of all active
+ * solves are packed into shared launches over work lists of tiles of their
+ * (uneven) grids, and a solve whose CG has converged leaves the list.  Requests
+ * are admitted in submission order between rounds while their workspace
+ * (ofdft_batch_bytes) fits in hbm_budget_bytes (a request larger than the budget
+ * is admitted alone).  Every solve keeps u, phi, its CG and NLCG vectors and
+ * (eta, mu) resident on the device between rounds.  All requests of a batch use
+ * `precision`.  Results are identical in method to ofdft_solve: the same
+ * Algorithm 1 and nonlinear CG, only the launches are shared. */
+typedef struct ofdft_batch ofdft_batch;
+int ofdft_batch_create(ofdft_ctx* ctx, int precision, long long hbm_budget_bytes, ofdft_batch** out);
+int ofdft_batch_destroy(ofdft_batch* b);
+/* Queues a solve; R, Z host arrays (copied), grid as in ofdft_solve (may be NULL).
+ * *request_id identifies it in ofdft_batch_poll. */
+int ofdft_batch_submit(ofdft_batch* b, const double* R, const double* Z, int M, double h,
+                       const ofdft_params* p, const ofdft_grid* grid, int* request_id);
+/* One round: admit, advance every active solve to its next evaluation, run the
+ * packed work, retire finished solves (forces computed at retirement).
+ * Outputs the numbers of active and queued solves. */
+int ofdft_batch_step(ofdft_batch* b, int* n_active, int* n_queued);
+/* *done = 1 once request_id finished; then energy, forces (M x 3, may be NULL)
+ * and stats are written and the request is forgotten.  Returns the solve's
+ * status (OFDFT_OK, OFDFT_ENOTCONV, ...). */
+int ofdft_batch_poll(ofdft_batch* b, int request_id, int* done, double* energy, double* forces,
+                     ofdft_solve_stats* st);
+/* Steps until no solve is active or queued. */
+int ofdft_batch_run(ofdft_batch* b);
+/* Device bytes one batched solve of grid g holds while admitted. */
+long long ofdft_batch_bytes(const ofdft_grid* g, int prec);
 
 /* Device bytes a solve of this grid needs in the context workspace (for
  * admission control by callers that pack several solves on one device). */

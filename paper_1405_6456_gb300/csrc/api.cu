@@ -134,9 +134,6 @@ int poisson_mixed(ofdft_ctx* c, int R, const GridDev& g, double h, const float* 
 }
 
 // ------------------------------------------------------ functional (S4) ---
-struct EvalOut {
-  double sums[12];
-};
 
 template <typename T>
 int functional_pass(ofdft_ctx* c, int R, const GridDev& g, double h, const ofdft_params* p, const T* u,
@@ -158,26 +155,6 @@ int functional_pass(ofdft_ctx* c, int R, const GridDev& g, double h, const ofdft
   TRY(launch_z_r<T>(c, R, g, W, LoadPlain<T>{u}, ep, OFDFT_K_FUNCTIONAL));
   TRY(sync_scalars(c, c->scal, 12 * sizeof(double), out->sums));
   return OFDFT_OK;
-}
-
-void fill_energy(const EvalOut& o, double h, const ofdft_params* p, double E_self, double ezz, double eta,
-                 double mu, ofdft_energy* e) {
-  const double h3 = h * h * h;
-  const bool es = p->terms & OFDFT_TERM_ES;
-  e->E_tf = h3 * o.sums[0];
-  e->E_vw = -0.5 * p->lambda * h3 * o.sums[1];
-  e->E_xc = h3 * o.sums[2];
-  e->E_self = es ? E_self : 0.0;
-  e->E_es = es ? h3 * (0.5 * o.sums[3] + o.sums[4] / (8.0 * kPi)) - E_self : 0.0;
-  e->E_zz_corr = ezz;
-  e->E = e->E_tf + e->E_vw + e->E_xc + e->E_es + ezz;
-  e->C = o.sums[9];
-  e->L = e->E - eta * e->C + 0.5 * e->C * e->C / mu;
-  e->gd = h3 * o.sums[5];
-  e->gs_old = h3 * o.sums[6];
-  e->rs = h3 * o.sums[7];
-  e->rs_pc = e->rs;
-  e->gnorm2 = h3 * o.sums[8];
 }
 
 // ------------------------------------------------------------- solve state --
@@ -799,9 +776,9 @@ int ofdft_destroy(ofdft_ctx* c) {
 
 const char* ofdft_last_error(const ofdft_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
-int ofdft_profile(ofdft_ctx* c, int enable) {
+int ofdft_profile(ofdft_ctx* c, int kind_mask) {
   if (!c) return OFDFT_EINVAL;
-  c->prof = enable ? 1 : 0;
+  c->prof = kind_mask;
   return OFDFT_OK;
 }
 
@@ -1013,15 +990,32 @@ int ofdft_energy_grad(ofdft_ctx* c, const ofdft_grid* g, const ofdft_params* p, 
     sum_uu = c->scal + 16;
   }
   EvalOut o;
+  const bool r1 = p->precond_rank1 && s;
+  if (r1) TRY(ensure(c, c->v[V_W], gd.G * (mixed ? 4 : 8)));
   if (!mixed)
     TRY(functional_pass<double>(c, R, gd, g->h, p, (const double*)u, (const double*)b, (const double*)phi,
                                 es ? vec<double>(c, V_R) : nullptr, eta, mu, N, sum_uu, (double*)grad, (double*)s,
-                                (const double*)d, (const double*)s_old, &o));
+                                (const double*)d, (const double*)s_old, &o, r1 ? vec<double>(c, V_W) : nullptr));
   else
     TRY(functional_pass<float>(c, R, gd, g->h, p, (const float*)u, (const float*)b, (const float*)phi,
                                es ? vec<float>(c, V_R) : nullptr, eta, mu, N, sum_uu, (float*)grad, (float*)s,
-                               (const float*)d, (const float*)s_old, &o));
+                               (const float*)d, (const float*)s_old, &o, r1 ? vec<float>(c, V_W) : nullptr));
   fill_energy(o, g->h, p, E_self, 0.0, eta, mu, out);
+  if (r1) {
+    // the preconditioned residual includes the exact inverse of the rank-one term (4 h^3/mu) u u^T
+    const double h3 = g->h * g->h * g->h;
+    const double cpen = 4.0 * h3 / mu;
+    const double gamma = cpen * o.sums[10] / (1.0 + cpen * o.sums[11]);
+    {
+      ProfScope ps_(c, OFDFT_K_VECTOR);
+      if (!mixed)
+        rank1_kernel<double><<<pointwise_blocks(c, gd.G), 256, 0, c->stream>>>(gd.G, (double*)s, vec<double>(c, V_W), gamma);
+      else
+        rank1_kernel<float><<<pointwise_blocks(c, gd.G), 256, 0, c->stream>>>(gd.G, (float*)s, vec<float>(c, V_W), gamma);
+    }
+    CU(cudaGetLastError());
+    out->rs_pc -= h3 * gamma * o.sums[10];
+  }
   out->poisson = cs;
   if (!isfinite(out->L)) return fail(c, OFDFT_ENONFINITE, "augmented Lagrangian is not finite");
   return OFDFT_OK;

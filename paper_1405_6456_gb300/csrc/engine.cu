@@ -1,0 +1,957 @@
+// Batched and continuously served ground states (S11, S12).
+//
+// Every solve ("slot") runs the same method as ofdft_solve: Algorithm 1 around
+// the secant / Polak-Ribiere nonlinear CG with one CG Poisson solve per
+// gradient evaluation.  Its control flow is written as a state machine that
+// yields one request at a time (an evaluation of L and its gradient, or two dot
+// products) after queueing the vector updates that precede it.  The engine
+// advances all active slots in lockstep rounds and packs the work of a round
+// into shared launches: one z-streaming launch per stencil stage over a work
+// list of tiles drawn from every grid (uneven sizes), one pointwise launch per
+// vector operation over segments of every grid, each grid reducing into its
+// own scratch.  A converged CG drops out of the tile list at the next poll.
+// New solves are admitted between rounds when their workspace fits in the
+// HBM budget, so requests that arrive while others run join the mix.
+#include "host.cuh"
+
+#include <deque>
+#include <functional>
+#include <memory>
+
+namespace ofd {
+namespace {
+
+enum SlotState {
+  S_AL_START,      // evaluation at u0 before the first inner solve
+  S_NLCG_START,    // evaluation at u with the current (eta, mu)
+  S_ITER,          // convergence test of the inner loop, then dots G.d, d.d
+  S_DOTS,          // got G.d, d.d
+  S_TRIAL,         // got the evaluation at the trial point
+  S_SECANT,        // got the evaluation at a secant candidate
+  S_AL_UPDATE,     // multiplier update of Algorithm 1
+  S_DONE
+};
+
+enum ReqKind { REQ_NONE = 0, REQ_EVAL = 1, REQ_DOTS = 2 };
+enum VopKind { VOP_AXPY_ABS = 0, VOP_DIRECTION = 1 };
+
+template <typename T>
+struct Vop {
+  int kind;
+  T* out;
+  const T* a;
+  const T* b;
+  double scalar;
+};
+
+template <typename T>
+struct Slot {
+  int id = 0;
+  ofdft_params p;
+  std::vector<double> R, Z;
+  int M = 0;
+  double N = 0.0;
+  ofdft_grid grid;
+  GridDev g;
+  int Rr = 6;
+  double h = 0.5, h3 = 0.125;
+  size_t bytes = 0;
+  void* mem = nullptr;
+  // fields
+  T *u, *ut, *phi, *b, *G, *Gt, *s, *st, *sn, *d, *w, *r, *pv, *qv;
+  double *phi64 = nullptr, *b64 = nullptr, *r64 = nullptr;
+  float* e32 = nullptr;
+  double* partials = nullptr;
+  unsigned int* counter = nullptr;
+  int maxblk = 0;
+  int index = 0;  // position in the engine's device scalar arrays
+  // method state (host scalars)
+  int state = S_AL_START;
+  double eta = 0, mu = 1, E_prev = 0, delta_new = 0, alpha = 0, gprev = 0, gcur = 0, L0 = 0, sig = 0, dd = 0, g0 = 0;
+  int k = 0, it = 0, q = 0, j = 0, bt = 0, inner_ok = 0, redo_dots = 0;
+  T* s_old = nullptr;
+  T* snew = nullptr;
+  ofdft_energy e, et;
+  ofdft_solve_stats stats;
+  double E_self = 0.0, ezz = 0.0;
+  std::vector<double> Fz, forces;
+  int status = OFDFT_OK;
+  std::string err;
+  // pending request
+  int req = REQ_NONE;
+  const T* ev_at = nullptr;
+  T* ev_G = nullptr;
+  T* ev_s = nullptr;
+  const T* ev_d = nullptr;
+  const T* ev_sold = nullptr;
+  double ev_eta = 0, ev_mu = 1;
+  ofdft_energy* ev_out = nullptr;
+  const T* dot_a[4] = {nullptr, nullptr, nullptr, nullptr};
+  std::vector<Vop<T>> vops;
+  // Poisson phase (within a round)
+  int pphase = 0, ptotal = 0;
+  ofdft_cg_stats pstats;
+};
+
+struct DevArena {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+}  // namespace ofd
+
+using namespace ofd;
+
+// The batch engine behind the ofdft_batch_* entry points.
+struct ofdft_batch {
+  ofdft_ctx* c = nullptr;
+  int prec = OFDFT_PREC_MIXED;
+  long long budget = 0, in_use = 0;
+  int next_id = 1;
+  int capacity = 0;           // slots the device scalar arrays hold
+  CgScalars* sc = nullptr;    // per slot: FP64 residual / CG scalars
+  CgScalars* sc32 = nullptr;  // per slot: FP32 correction CG (mixed)
+  double* out = nullptr;      // per slot: 16 doubles
+  std::vector<CgScalars> h_sc, h_sc32;
+  std::vector<double> h_out;
+  DevArena d_tiles, d_desc, d_segs, d_ops;
+  std::vector<int> free_index;
+  long long rounds = 0;
+  // type-erased slot lists (only the engine of the batch precision is used)
+  std::vector<std::unique_ptr<Slot<double>>> s64_active, s64_done;
+  std::vector<std::unique_ptr<Slot<float>>> s32_active, s32_done;
+  std::deque<std::unique_ptr<Slot<double>>> s64_queue;
+  std::deque<std::unique_ptr<Slot<float>>> s32_queue;
+};
+
+namespace ofd {
+namespace {
+
+int grow_arena(ofdft_ctx* c, DevArena& a, size_t bytes) {
+  if (a.bytes >= bytes && a.p) return OFDFT_OK;
+  if (a.p) {
+    CU(cudaStreamSynchronize(c->stream));
+    CU(cudaFree(a.p));
+    a.p = nullptr;
+  }
+  const size_t want = std::max<size_t>(bytes * 2, 4096);
+  CU(cudaMalloc(&a.p, want));
+  a.bytes = want;
+  return OFDFT_OK;
+}
+
+template <typename V>
+int upload(ofdft_ctx* c, DevArena& a, const std::vector<V>& v) {
+  TRY(grow_arena(c, a, v.size() * sizeof(V) + 64));
+  if (!v.empty())
+    CU(cudaMemcpyAsync(a.p, v.data(), v.size() * sizeof(V), cudaMemcpyHostToDevice, c->stream));
+  return OFDFT_OK;
+}
+
+// Workspace of one solve: every field it keeps resident between rounds.
+long long slot_bytes(const ofdft_grid& g, int prec, int* maxblk) {
+  const long long G = (long long)g.n[0] * g.n[1] * g.n[2];
+  const long long es = (prec == OFDFT_PREC_MIXED) ? 4 : 8;
+  long long bytes = G * es * 14;
+  if (prec == OFDFT_PREC_MIXED) bytes += G * (8 * 3 + 4);
+  // reduction scratch: the larger of the tile count and the segment count
+  const long long tiles = (long long)((g.n[0] + BX - 1) / BX) * ((g.n[1] + BY - 1) / BY) * ((g.n[2] + 15) / 16);
+  const long long segs = (G + 16383) / 16384;
+  const long long mb = std::max(tiles, segs) + 1;
+  *maxblk = (int)mb;
+  bytes += mb * 16 * 8 + 256 + 64 * 16;
+  return bytes;
+}
+
+template <typename T>
+int carve(ofdft_ctx* c, Slot<T>* S, int prec) {
+  const long long G = S->g.G;
+  S->bytes = (size_t)slot_bytes(S->grid, prec, &S->maxblk);
+  CU(cudaMalloc(&S->mem, S->bytes));
+  char* p = (char*)S->mem;
+  auto take = [&](size_t n) {
+    char* q = p;
+    p += (n + 255) & ~(size_t)255;
+    return (void*)q;
+  };
+  T** vecs[] = {&S->u, &S->ut, &S->phi, &S->b, &S->G, &S->Gt, &S->s, &S->st, &S->sn, &S->d, &S->w, &S->r, &S->pv, &S->qv};
+  for (T** v : vecs) *v = (T*)take(G * sizeof(T));
+  if (prec == OFDFT_PREC_MIXED) {
+    S->phi64 = (double*)take(G * 8);
+    S->b64 = (double*)take(G * 8);
+    S->r64 = (double*)take(G * 8);
+    S->e32 = (float*)take(G * 4);
+  }
+  S->partials = (double*)take((size_t)S->maxblk * 16 * 8);
+  S->counter = (unsigned int*)take(256);
+  if ((size_t)(p - (char*)S->mem) > S->bytes) return fail(c, OFDFT_EINVAL, "slot workspace carve overflow");
+  CU(cudaMemsetAsync(S->counter, 0, 256, c->stream));
+  return OFDFT_OK;
+}
+
+// Tiles of one grid for the z-streaming batch launch (z chunks of 16 planes).
+void grid_tiles(const GridDev& g, int slot, std::vector<ZTile>& out, int* count) {
+  const int gx = (g.n1 + BX - 1) / BX, gy = (g.n2 + BY - 1) / BY;
+  const int zc = 16;
+  int bid = 0;
+  for (int z0 = 0; z0 < g.n3; z0 += zc)
+    for (int by = 0; by < gy; ++by)
+      for (int bx = 0; bx < gx; ++bx) out.push_back(ZTile{slot, bx, by, z0, std::min(z0 + zc, g.n3), bid++});
+  *count = bid;
+}
+
+void grid_segs(const GridDev& g, int slot, std::vector<PSeg>& out, int* count) {
+  const long long L = 16384;
+  int bid = 0;
+  for (long long b = 0; b < g.G; b += L) out.push_back(PSeg{slot, bid++, b, std::min(b + L, g.G)});
+  *count = bid;
+}
+
+template <typename T>
+struct Engine {
+  ofdft_batch* B;
+  ofdft_ctx* c;
+  std::vector<std::unique_ptr<Slot<T>>>* active;
+  std::vector<std::unique_ptr<Slot<T>>>* done;
+  std::deque<std::unique_ptr<Slot<T>>>* queue;
+  bool mixed;
+
+  RedBuf slot_red(Slot<T>* S) { return RedBuf{S->partials, S->counter}; }
+
+  template <typename TT, int R, class L, class E>
+  int launch_zb(int kind, unsigned nb, const ZTile* dt, const ZSlot<TT, L, E>* ds) {
+    constexpr int smem = zring_bytes<TT, R>();
+    static bool attr = false;
+    if (!attr) {
+      CU(cudaFuncSetAttribute(zbatch_kernel<TT, R, L, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+      attr = true;
+    }
+    {
+      ProfScope ps_(c, kind);
+      zbatch_kernel<TT, R, L, E><<<nb, dim3(BX, BY), smem, c->stream>>>(dt, ds);
+    }
+    CU(cudaGetLastError());
+    return OFDFT_OK;
+  }
+
+  // --- batched launches ---------------------------------------------------
+  // z-streaming pass of kind `kind` over the given slots; make(S) returns the
+  // loader/epilogue descriptor of that slot.  One launch per stencil radius.
+  template <typename TT, class L, class E, class Make>
+  int zpass(const std::vector<Slot<T>*>& slots, int kind, double wscale, Make make) {
+    for (int Rr = 1; Rr <= kMaxR; ++Rr) {
+      std::vector<ZTile> tiles;
+      std::vector<ZSlot<TT, L, E>> desc;
+      for (Slot<T>* S : slots) {
+        if (S->Rr != Rr) continue;
+        int cnt = 0;
+        const int si = (int)desc.size();
+        grid_tiles(S->g, si, tiles, &cnt);
+        ZSlot<TT, L, E> z;
+        z.g = S->g;
+        z.W = cast_weights<TT>(lap_weights(Rr, S->h, wscale));
+        auto le = make(S);
+        z.ld = le.first;
+        z.ep = le.second;
+        z.red = slot_red(S);
+        z.nblocks = cnt;
+        desc.push_back(z);
+      }
+      if (tiles.empty()) continue;
+      TRY(upload(c, B->d_tiles, tiles));
+      TRY(upload(c, B->d_desc, desc));
+      const ZTile* dt = (const ZTile*)B->d_tiles.p;
+      const ZSlot<TT, L, E>* ds = (const ZSlot<TT, L, E>*)B->d_desc.p;
+      switch (Rr) {
+        case 1: TRY((launch_zb<TT, 1, L, E>(kind, (unsigned)tiles.size(), dt, ds))); break;
+        case 2: TRY((launch_zb<TT, 2, L, E>(kind, (unsigned)tiles.size(), dt, ds))); break;
+        case 3: TRY((launch_zb<TT, 3, L, E>(kind, (unsigned)tiles.size(), dt, ds))); break;
+        case 4: TRY((launch_zb<TT, 4, L, E>(kind, (unsigned)tiles.size(), dt, ds))); break;
+        case 5: TRY((launch_zb<TT, 5, L, E>(kind, (unsigned)tiles.size(), dt, ds))); break;
+        case 6: TRY((launch_zb<TT, 6, L, E>(kind, (unsigned)tiles.size(), dt, ds))); break;
+      }
+    }
+    return OFDFT_OK;
+  }
+
+  // pointwise pass over the given slots; make(S, nblocks) returns the op.
+  template <class Op, class Make>
+  int ppass(const std::vector<Slot<T>*>& slots, int kind, Make make) {
+    std::vector<PSeg> segs;
+    std::vector<Op> ops;
+    for (Slot<T>* S : slots) {
+      int cnt = 0;
+      const int si = (int)ops.size();
+      std::vector<PSeg> tmp;
+      grid_segs(S->g, si, tmp, &cnt);
+      segs.insert(segs.end(), tmp.begin(), tmp.end());
+      ops.push_back(make(S, cnt));
+    }
+    if (segs.empty()) return OFDFT_OK;
+    TRY(upload(c, B->d_segs, segs));
+    TRY(upload(c, B->d_ops, ops));
+    {
+      ProfScope ps_(c, kind);
+      pbatch_kernel<Op><<<(unsigned)segs.size(), 256, 0, c->stream>>>((const PSeg*)B->d_segs.p,
+                                                                     (const Op*)B->d_ops.p);
+    }
+    CU(cudaGetLastError());
+    return OFDFT_OK;
+  }
+
+  int read_scalars() {
+    CU(cudaMemcpyAsync(B->h_sc.data(), B->sc, B->capacity * sizeof(CgScalars), cudaMemcpyDeviceToHost, c->stream));
+    if (mixed)
+      CU(cudaMemcpyAsync(B->h_sc32.data(), B->sc32, B->capacity * sizeof(CgScalars), cudaMemcpyDeviceToHost,
+                         c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    if (!c->pending.empty()) harvest(c);
+    return OFDFT_OK;
+  }
+
+  // CG iterations on the given slots until each is done (S3), `x` the iterate,
+  // `r` the residual, `scp` the slot's CG scalars.
+  template <class GetX, class GetR, class GetSc, class HostSc>
+  int cg_loop(std::vector<Slot<T>*> slots, GetX getx, GetR getr, GetSc getsc, HostSc hostsc) {
+    const int chunk = 8;
+    while (!slots.empty()) {
+      for (int i = 0; i < chunk; ++i) {
+        TRY((zpass<T, LoadPlain<T>, EpiCgA<T>>(slots, OFDFT_K_CG_DIR_STENCIL, -1.0, [&](Slot<T>* S) {
+          return std::make_pair(LoadPlain<T>{getr(S)}, EpiCgA<T>{S->pv, S->qv, getsc(S)});
+        })));
+        TRY((ppass<OpCgUpdate<T>>(slots, OFDFT_K_CG_UPDATE, [&](Slot<T>* S, int nb) {
+          return OpCgUpdate<T>{getx(S), getr(S), S->pv, S->qv, getsc(S), slot_red(S), nb};
+        })));
+      }
+      TRY(read_scalars());
+      std::vector<Slot<T>*> still;
+      for (Slot<T>* S : slots)
+        if (!hostsc(S).done) still.push_back(S);
+      slots.swap(still);
+    }
+    return OFDFT_OK;
+  }
+
+  // Batched Poisson solves at each slot's evaluation point.
+  int poisson(const std::vector<Slot<T>*>& ev) {
+    if (ev.empty()) return OFDFT_OK;
+    if (!mixed) {
+      TRY((zpass<T, LoadPlain<T>, EpiResidual<T>>(ev, OFDFT_K_RESIDUAL, 1.0, [&](Slot<T>* S) {
+        return std::make_pair(LoadPlain<T>{S->phi}, EpiResidual<T>{nullptr, S->ev_at, S->b, S->r, B->sc + S->index,
+                                                                  S->p.tol_poisson, S->p.max_cg, 1});
+      })));
+      TRY(read_scalars());
+      std::vector<Slot<T>*> run;
+      for (Slot<T>* S : ev)
+        if (!B->h_sc[S->index].done) run.push_back(S);
+      TRY(cg_loop(
+          run, [](Slot<T>* S) { return S->phi; }, [](Slot<T>* S) { return S->r; },
+          [&](Slot<T>* S) { return B->sc + S->index; }, [&](Slot<T>* S) -> CgScalars& { return B->h_sc[S->index]; }));
+      for (Slot<T>* S : ev) {
+        const CgScalars& h = B->h_sc[S->index];
+        S->pstats.iterations = h.iters;
+        S->pstats.rel_residual = sqrt(h.rr / (h.bb > 0 ? h.bb : 1.0));
+      }
+      return OFDFT_OK;
+    }
+    // mixed: FP64 residual rounds around FP32 correction solves (per slot)
+    for (Slot<T>* S : ev) {
+      S->pphase = 0;
+      S->ptotal = 0;
+    }
+    std::vector<Slot<T>*> resid = ev;
+    for (int round = 0; round < 40 && !resid.empty(); ++round) {
+      TRY((zpass<double, LoadPlain<double>, EpiResidual<double, float, double>>(
+          resid, OFDFT_K_RESIDUAL, 1.0, [&](Slot<T>* S) {
+            return std::make_pair(LoadPlain<double>{S->phi64},
+                                  EpiResidual<double, float, double>{nullptr, (const float*)S->ev_at, S->b64, S->r64,
+                                                                     B->sc + S->index, S->p.tol_poisson, S->p.max_cg,
+                                                                     1});
+          })));
+      TRY(read_scalars());
+      std::vector<Slot<T>*> corr;
+      for (Slot<T>* S : resid) {
+        const CgScalars& h = B->h_sc[S->index];
+        const double bb = h.bb > 0 ? h.bb : 1.0;
+        S->pstats.iterations = S->ptotal;
+        S->pstats.rel_residual = sqrt(h.rr / bb);
+        if (h.rr <= S->p.tol_poisson * S->p.tol_poisson * bb || S->ptotal >= S->p.max_cg || !isfinite(h.rr)) continue;
+        corr.push_back(S);
+      }
+      if (corr.empty()) break;
+      TRY((ppass<OpRefineInit>(corr, OFDFT_K_VECTOR, [&](Slot<T>* S, int nb) {
+        const int budget = std::min(std::max(S->p.refine_every, 1), S->p.max_cg - S->ptotal);
+        return OpRefineInit{(float*)S->r, S->e32, S->r64, B->sc32 + S->index, 1e-5, budget, slot_red(S), nb};
+      })));
+      TRY(read_scalars());
+      std::vector<Slot<T>*> run;
+      for (Slot<T>* S : corr)
+        if (!B->h_sc32[S->index].done) run.push_back(S);
+      TRY(cg_loop(
+          run, [](Slot<T>* S) { return (T*)S->e32; }, [](Slot<T>* S) { return S->r; },
+          [&](Slot<T>* S) { return B->sc32 + S->index; },
+          [&](Slot<T>* S) -> CgScalars& { return B->h_sc32[S->index]; }));
+      for (Slot<T>* S : corr) S->ptotal += std::max(B->h_sc32[S->index].iters, 1);
+      TRY((ppass<OpRefineApply>(corr, OFDFT_K_VECTOR, [&](Slot<T>* S, int) {
+        return OpRefineApply{S->phi64, (float*)S->phi, S->e32};
+      })));
+      resid.swap(corr);
+    }
+    // FP32 copy of the FP64 residual for the phi.r energy term
+    TRY((ppass<OpConvert<double, float>>(ev, OFDFT_K_VECTOR, [&](Slot<T>* S, int) {
+      return OpConvert<double, float>{(float*)S->r, S->r64};
+    })));
+    return OFDFT_OK;
+  }
+
+  int evaluate(const std::vector<Slot<T>*>& ev) {
+    if (ev.empty()) return OFDFT_OK;
+    TRY(poisson(ev));
+    TRY((zpass<T, LoadPlain<T>, EpiFunctional<T>>(ev, OFDFT_K_FUNCTIONAL, 1.0, [&](Slot<T>* S) {
+      const Weights<double> W = lap_weights(S->Rr, S->h, 1.0);
+      FuncScalars f;
+      f.h3 = S->h3;
+      f.N = S->N;
+      f.eta = S->ev_eta;
+      f.inv_mu = 1.0 / S->ev_mu;
+      f.lambda = S->p.lambda;
+      f.CF = 0.3 * pow(3.0 * kPi * kPi, 2.0 / 3.0);
+      f.kin_vw = -S->p.lambda * W.c;
+      f.terms = S->p.terms;
+      const bool es = S->p.terms & OFDFT_TERM_ES;
+      EpiFunctional<T> ep{es ? S->phi : nullptr, S->b, es ? S->r : nullptr, S->ev_d, S->ev_sold, S->ev_G, S->ev_s,
+                          (S->p.precond_rank1 && S->ev_s) ? S->w : nullptr, &B->sc[S->index].sum_uu, f,
+                          B->out + 16 * S->index};
+      return std::make_pair(LoadPlain<T>{S->ev_at}, ep);
+    })));
+    CU(cudaMemcpyAsync(B->h_out.data(), B->out, B->capacity * 16 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    std::vector<Slot<T>*> r1;
+    std::vector<double> gam(B->capacity, 0.0);
+    for (Slot<T>* S : ev) {
+      EvalOut o;
+      memcpy(o.sums, &B->h_out[16 * S->index], 12 * sizeof(double));
+      fill_energy(o, S->h, &S->p, S->E_self, S->ezz, S->ev_eta, S->ev_mu, S->ev_out);
+      S->ev_out->poisson = S->pstats;
+      S->stats.stencil_apps += S->pstats.iterations + 3;
+      S->stats.cg_iters += S->pstats.iterations;
+      S->stats.grad_evals += 1;
+      if (S->p.precond_rank1 && S->ev_s) {
+        const double cpen = 4.0 * S->h3 / S->ev_mu;
+        gam[S->index] = cpen * o.sums[10] / (1.0 + cpen * o.sums[11]);
+        S->ev_out->rs_pc -= S->h3 * gam[S->index] * o.sums[10];
+        r1.push_back(S);
+      }
+    }
+    TRY((ppass<OpRank1<T>>(r1, OFDFT_K_VECTOR, [&](Slot<T>* S, int) {
+      return OpRank1<T>{S->ev_s, S->w, gam[S->index]};
+    })));
+    return OFDFT_OK;
+  }
+
+  int dots(const std::vector<Slot<T>*>& dv) {
+    if (dv.empty()) return OFDFT_OK;
+    TRY((ppass<OpDot2<T>>(dv, OFDFT_K_VECTOR, [&](Slot<T>* S, int nb) {
+      return OpDot2<T>{S->dot_a[0], S->dot_a[1], S->dot_a[2], S->dot_a[3], B->out + 16 * S->index + 12,
+                       slot_red(S), nb};
+    })));
+    CU(cudaMemcpyAsync(B->h_out.data(), B->out, B->capacity * 16 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    return OFDFT_OK;
+  }
+
+  // Runs queued vector updates in lockstep (op i of every slot together).
+  int flush_vops(const std::vector<Slot<T>*>& slots) {
+    size_t depth = 0;
+    for (Slot<T>* S : slots) depth = std::max(depth, S->vops.size());
+    for (size_t i = 0; i < depth; ++i) {
+      std::vector<Slot<T>*> ax, dr;
+      for (Slot<T>* S : slots)
+        if (i < S->vops.size()) (S->vops[i].kind == VOP_AXPY_ABS ? ax : dr).push_back(S);
+      TRY((ppass<OpAxpyAbs<T>>(ax, OFDFT_K_VECTOR, [&](Slot<T>* S, int) {
+        const Vop<T>& v = S->vops[i];
+        return OpAxpyAbs<T>{v.out, v.a, v.b, v.scalar};
+      })));
+      TRY((ppass<OpDirection<T>>(dr, OFDFT_K_VECTOR, [&](Slot<T>* S, int) {
+        const Vop<T>& v = S->vops[i];
+        return OpDirection<T>{v.out, v.a, v.scalar};
+      })));
+    }
+    for (Slot<T>* S : slots) S->vops.clear();
+    return OFDFT_OK;
+  }
+
+  // --- the method as a state machine ---------------------------------------
+  void request_eval(Slot<T>* S, const T* at, T* Gout, T* sout, const T* d, const T* sold, ofdft_energy* out) {
+    S->req = REQ_EVAL;
+    S->ev_at = at;
+    S->ev_G = Gout;
+    S->ev_s = sout;
+    S->ev_d = d;
+    S->ev_sold = sold;
+    S->ev_eta = S->eta;
+    S->ev_mu = S->mu;
+    S->ev_out = out;
+  }
+  void request_dots(Slot<T>* S) {
+    S->req = REQ_DOTS;
+    S->dot_a[0] = S->G;
+    S->dot_a[1] = S->d;
+    S->dot_a[2] = S->d;
+    S->dot_a[3] = S->d;
+  }
+  void vop(Slot<T>* S, int kind, T* out, const T* a, const T* b, double x) { S->vops.push_back(Vop<T>{kind, out, a, b, x}); }
+
+  void finish(Slot<T>* S, int status, const char* msg) {
+    S->status = status;
+    if (msg) S->err = msg;
+    S->state = S_DONE;
+    S->req = REQ_NONE;
+  }
+
+  // Advances S until it issues a request or finishes (mirrors Solver::nlcg and
+  // the Algorithm 1 loop of ofdft_solve step by step).
+  void advance(Slot<T>* S) {
+    const ofdft_params& p = S->p;
+    const double h3 = S->h3;
+    for (;;) {
+      switch (S->state) {
+        case S_AL_START:
+          request_eval(S, S->u, S->G, S->s, nullptr, nullptr, &S->e);
+          S->state = S_NLCG_START;
+          S->inner_ok = -1;  // marks "E_prev not yet recorded"
+          return;
+        case S_NLCG_START:
+          if (S->inner_ok == -1) {
+            S->E_prev = S->e.E;
+            S->inner_ok = 0;
+          }
+          // inner solve on L(., eta, mu) starts with an evaluation at u
+          request_eval(S, S->u, S->G, S->s, nullptr, nullptr, &S->e);
+          S->state = S_ITER;
+          S->it = -1;
+          return;
+        case S_ITER: {
+          if (S->it == -1) {  // first pass after the starting evaluation
+            vop(S, VOP_DIRECTION, S->d, S->s, nullptr, 0.0);
+            S->delta_new = S->e.rs_pc;
+            S->k = 0;
+            S->it = 0;
+          }
+          if (S->e.rs < p.tol_inner * S->M) {
+            S->inner_ok = 1;
+            S->state = S_AL_UPDATE;
+            continue;
+          }
+          if (!isfinite(S->e.L) || !isfinite(S->e.rs)) {
+            finish(S, OFDFT_ENONFINITE, "augmented Lagrangian is not finite");
+            return;
+          }
+          if (S->it >= p.max_nlcg) {
+            S->state = S_AL_UPDATE;
+            continue;
+          }
+          S->stats.nlcg_iters++;
+          S->s_old = S->s;
+          S->redo_dots = 0;
+          request_dots(S);
+          S->state = S_DOTS;
+          return;
+        }
+        case S_DOTS: {
+          const double* o = &B->h_out[16 * S->index + 12];
+          S->g0 = h3 * o[0];
+          S->dd = h3 * o[1];
+          if (!(S->g0 < 0.0) && !S->redo_dots) {  // not a descent direction: restart along s
+            vop(S, VOP_DIRECTION, S->d, S->s, nullptr, 0.0);
+            S->k = 0;
+            S->redo_dots = 1;
+            request_dots(S);
+            return;
+          }
+          S->sig = p.sigma0;
+          if (p.trial_max_rel > 0.0 && S->dd > 0.0) S->sig = std::min(S->sig, p.trial_max_rel * sqrt(S->N / S->dd));
+          vop(S, VOP_AXPY_ABS, S->ut, S->u, S->d, S->sig);
+          request_eval(S, S->ut, S->Gt, S->st, S->d, S->s_old, &S->et);
+          S->state = S_TRIAL;
+          return;
+        }
+        case S_TRIAL: {
+          S->alpha = -S->sig;
+          S->gprev = S->et.gd;
+          S->gcur = S->g0;
+          if (!((S->gcur - S->gprev) / S->alpha > 0.0)) {
+            std::swap(S->u, S->ut);
+            std::swap(S->G, S->Gt);
+            std::swap(S->s, S->st);
+            S->e = S->et;
+            goto direction;
+          }
+          S->snew = S->sn;
+          S->L0 = S->e.L;
+          S->j = 1;
+          S->alpha = S->alpha * S->gcur / (S->gprev - S->gcur);
+          S->bt = 0;
+          vop(S, VOP_AXPY_ABS, S->ut, S->u, S->d, S->alpha);
+          request_eval(S, S->ut, S->G, S->snew, S->d, S->s_old, &S->e);
+          S->state = S_SECANT;
+          return;
+        }
+        case S_SECANT: {
+          if (S->bt < p.max_backtrack && !(S->e.L <= S->L0)) {
+            S->bt++;
+            S->alpha *= 0.5;
+            vop(S, VOP_AXPY_ABS, S->ut, S->u, S->d, S->alpha);
+            request_eval(S, S->ut, S->G, S->snew, S->d, S->s_old, &S->e);
+            return;
+          }
+          std::swap(S->u, S->ut);
+          S->gprev = S->gcur;
+          S->gcur = S->e.gd;
+          const bool stop = (S->j == p.max_secant || S->alpha * S->alpha * S->dd <= p.eps_secant * p.eps_secant * S->N) ||
+                            !((S->gcur - S->gprev) / S->alpha > 0.0);
+          if (!stop) {
+            S->j++;
+            S->alpha = S->alpha * S->gcur / (S->gprev - S->gcur);
+            S->bt = 0;
+            vop(S, VOP_AXPY_ABS, S->ut, S->u, S->d, S->alpha);
+            request_eval(S, S->ut, S->G, S->snew, S->d, S->s_old, &S->e);
+            return;
+          }
+          S->sn = S->s;
+          S->s = S->snew;
+          goto direction;
+        }
+        case S_AL_UPDATE: {
+          S->stats.outer_iters++;
+          const double E = S->e.E, C = S->e.C;
+          if (!isfinite(E) || !isfinite(C)) {
+            finish(S, OFDFT_ENONFINITE, "energy or constraint is not finite");
+            return;
+          }
+          const double eta_eff = S->eta - C / S->mu;
+          S->stats.eta = eta_eff;
+          if (p.method == OFDFT_METHOD_AL) S->eta = eta_eff;
+          S->mu = p.kappa * S->mu;
+          S->q++;
+          if (fabs(E - S->E_prev) < p.tol_E * S->M) {
+            S->stats.converged = 1;
+            finish(S, OFDFT_OK, nullptr);
+            return;
+          }
+          S->E_prev = E;
+          if (S->q >= p.max_outer) {
+            finish(S, OFDFT_ENOTCONV, "Algorithm 1 reached max_outer");
+            return;
+          }
+          S->state = S_NLCG_START;
+          continue;
+        }
+        default:
+          return;
+      }
+    direction : {
+      const double delta_old = S->delta_new;
+      const double delta_mid = -S->e.gs_old;
+      S->delta_new = S->e.rs_pc;
+      const double beta = (S->delta_new - delta_mid) / delta_old;
+      S->k++;
+      if (S->k >= p.restart_every || !(beta > 0.0)) {
+        vop(S, VOP_DIRECTION, S->d, S->s, nullptr, 0.0);
+        S->k = 0;
+      } else {
+        vop(S, VOP_DIRECTION, S->d, S->s, nullptr, beta);
+      }
+      S->it++;
+      S->state = S_ITER;
+      continue;
+    }
+    }
+  }
+
+  // --- admission and completion --------------------------------------------
+  int ensure_capacity(int need) {
+    if (need <= B->capacity) return OFDFT_OK;
+    const int cap = std::max(need, std::max(16, 2 * B->capacity));
+    CU(cudaStreamSynchronize(c->stream));
+    CgScalars *nsc = nullptr, *nsc32 = nullptr;
+    double* nout = nullptr;
+    CU(cudaMalloc(&nsc, cap * sizeof(CgScalars)));
+    CU(cudaMalloc(&nsc32, cap * sizeof(CgScalars)));
+    CU(cudaMalloc(&nout, cap * 16 * sizeof(double)));
+    CU(cudaMemset(nsc, 0, cap * sizeof(CgScalars)));
+    CU(cudaMemset(nsc32, 0, cap * sizeof(CgScalars)));
+    CU(cudaMemset(nout, 0, cap * 16 * sizeof(double)));
+    if (B->capacity > 0) {
+      CU(cudaMemcpy(nsc, B->sc, B->capacity * sizeof(CgScalars), cudaMemcpyDeviceToDevice));
+      CU(cudaMemcpy(nsc32, B->sc32, B->capacity * sizeof(CgScalars), cudaMemcpyDeviceToDevice));
+      CU(cudaMemcpy(nout, B->out, B->capacity * 16 * sizeof(double), cudaMemcpyDeviceToDevice));
+    }
+    cudaFree(B->sc);
+    cudaFree(B->sc32);
+    cudaFree(B->out);
+    B->sc = nsc;
+    B->sc32 = nsc32;
+    B->out = nout;
+    for (int i = B->capacity; i < cap; ++i) B->free_index.push_back(i);
+    B->capacity = cap;
+    B->h_sc.resize(cap);
+    B->h_sc32.resize(cap);
+    B->h_out.resize((size_t)cap * 16);
+    return OFDFT_OK;
+  }
+
+  int admit_one(Slot<T>* S) {
+    TRY(carve(c, S, B->prec));
+    if (B->free_index.empty()) TRY(ensure_capacity(B->capacity + 1));
+    std::sort(B->free_index.begin(), B->free_index.end(), std::greater<int>());
+    S->index = B->free_index.back();
+    B->free_index.pop_back();
+    B->in_use += (long long)S->bytes;
+    const int rr = S->Rr;
+    const ofdft_grid* gr = &S->grid;
+    if (!mixed) {
+      TRY(device_pseudocharge<double>(c, gr, rr, S->R.data(), S->Z.data(), S->M, S->p.sigma, S->p.rc, (double*)S->b,
+                                      &S->E_self));
+    } else {
+      TRY(device_pseudocharge<double>(c, gr, rr, S->R.data(), S->Z.data(), S->M, S->p.sigma, S->p.rc, S->b64,
+                                      &S->E_self));
+      std::vector<Slot<T>*> one{S};
+      TRY((ppass<OpConvert<double, float>>(one, OFDFT_K_VECTOR, [&](Slot<T>* X, int) {
+        return OpConvert<double, float>{(float*)X->b, X->b64};
+      })));
+      CU(cudaMemsetAsync(S->phi64, 0, S->g.G * sizeof(double), c->stream));
+    }
+    TRY(device_guess<T>(c, gr, S->R.data(), S->Z.data(), S->M, S->p.guess_sigma, S->p.guess_cut, S->N, S->u));
+    CU(cudaMemsetAsync(S->phi, 0, S->g.G * sizeof(T), c->stream));
+    S->Fz.assign(3 * (size_t)S->M, 0.0);
+    if (S->p.ezz_correction) TRY(device_ezz(c, S->R.data(), S->Z.data(), S->M, S->p.sigma, &S->ezz, S->Fz.data()));
+    S->eta = (S->p.method == OFDFT_METHOD_PENALTY) ? 0.0 : S->p.eta0;
+    S->mu = S->p.mu0;
+    S->state = S_AL_START;
+    S->stats.grid = S->grid;
+    return OFDFT_OK;
+  }
+
+  int complete(Slot<T>* S) {
+    S->stats.E = S->e.E;
+    S->stats.C = S->e.C;
+    S->stats.parts = S->e;
+    if (S->status == OFDFT_OK || S->status == OFDFT_ENOTCONV) {
+      S->forces.assign(3 * (size_t)S->M, 0.0);
+      TRY(device_forces<T>(c, &S->grid, S->Rr, S->R.data(), S->Z.data(), S->M, S->p.sigma, S->p.rc,
+                           S->p.force_variant, S->phi, S->forces.data()));
+      if (S->p.ezz_correction)
+        for (int i = 0; i < 3 * S->M; ++i) S->forces[i] += S->Fz[i];
+    }
+    CU(cudaStreamSynchronize(c->stream));
+    CU(cudaFree(S->mem));
+    S->mem = nullptr;
+    B->in_use -= (long long)S->bytes;
+    B->free_index.push_back(S->index);
+    return OFDFT_OK;
+  }
+
+  // One round: admit what fits, advance every slot to its next request, run the
+  // packed vector updates, evaluations and dot products, retire finished solves.
+  int step() {
+    while (!queue->empty()) {
+      Slot<T>* S = queue->front().get();
+      int mb = 0;
+      const long long need = slot_bytes(S->grid, B->prec, &mb);
+      if (B->in_use + need > B->budget && !active->empty()) break;
+      TRY(admit_one(S));
+      active->push_back(std::move(queue->front()));
+      queue->pop_front();
+    }
+    std::vector<Slot<T>*> slots;
+    for (auto& u : *active) slots.push_back(u.get());
+    for (Slot<T>* S : slots) {
+      S->req = REQ_NONE;
+      advance(S);
+    }
+    TRY(flush_vops(slots));
+    std::vector<Slot<T>*> ev, dv;
+    for (Slot<T>* S : slots) {
+      if (S->req == REQ_EVAL) ev.push_back(S);
+      if (S->req == REQ_DOTS) dv.push_back(S);
+    }
+    TRY(evaluate(ev));
+    TRY(dots(dv));
+    for (size_t i = 0; i < active->size();) {
+      Slot<T>* S = (*active)[i].get();
+      if (S->state == S_DONE) {
+        TRY(complete(S));
+        done->push_back(std::move((*active)[i]));
+        active->erase(active->begin() + i);
+      } else {
+        ++i;
+      }
+    }
+    B->rounds++;
+    return OFDFT_OK;
+  }
+};
+
+template <typename T>
+Engine<T> engine_of(ofdft_batch* b);
+
+template <>
+Engine<double> engine_of<double>(ofdft_batch* b) {
+  return Engine<double>{b, b->c, &b->s64_active, &b->s64_done, &b->s64_queue, false};
+}
+template <>
+Engine<float> engine_of<float>(ofdft_batch* b) {
+  return Engine<float>{b, b->c, &b->s32_active, &b->s32_done, &b->s32_queue, true};
+}
+
+template <typename T>
+int submit_impl(ofdft_batch* b, const double* R, const double* Z, int M, double h, const ofdft_params* p,
+                const ofdft_grid* grid, int* id) {
+  auto S = std::make_unique<Slot<T>>();
+  S->p = *p;
+  S->R.assign(R, R + 3 * (size_t)M);
+  S->Z.assign(Z, Z + M);
+  S->M = M;
+  for (int i = 0; i < M; ++i) S->N += Z[i];
+  if (grid) {
+    S->grid = *grid;
+  } else {
+    const int rc = ofdft_grid_for_atoms(R, M, h, p->vacuum, p->round_to > 0 ? p->round_to : 1, &S->grid);
+    if (rc != OFDFT_OK) return fail(b->c, rc, "box rule failed");
+  }
+  TRY(check_grid(b->c, &S->grid));
+  S->g = gdev(&S->grid);
+  S->h = S->grid.h;
+  S->h3 = S->h * S->h * S->h;
+  S->Rr = p->fd_order / 2;
+  S->id = b->next_id++;
+  *id = S->id;
+  engine_of<T>(b).queue->push_back(std::move(S));
+  return OFDFT_OK;
+}
+
+template <typename T>
+int poll_impl(ofdft_batch* b, int id, int* done, double* energy, double* forces, ofdft_solve_stats* st) {
+  Engine<T> E = engine_of<T>(b);
+  for (size_t i = 0; i < E.done->size(); ++i) {
+    Slot<T>* S = (*E.done)[i].get();
+    if (S->id != id) continue;
+    *done = 1;
+    if (energy) *energy = S->stats.E;
+    if (forces && !S->forces.empty()) memcpy(forces, S->forces.data(), S->forces.size() * sizeof(double));
+    if (st) *st = S->stats;
+    const int status = S->status;
+    if (status != OFDFT_OK) fail(b->c, status, "%s", S->err.c_str());
+    E.done->erase(E.done->begin() + i);
+    return status;
+  }
+  *done = 0;
+  for (auto& S : *E.active)
+    if (S->id == id) return OFDFT_OK;
+  for (auto& S : *E.queue)
+    if (S->id == id) return OFDFT_OK;
+  return fail(b->c, OFDFT_EINVAL, "unknown request id %d", id);
+}
+
+}  // namespace
+}  // namespace ofd
+
+// ===================================================================== C ABI
+extern "C" {
+
+int ofdft_batch_create(ofdft_ctx* c, int precision, long long hbm_budget_bytes, ofdft_batch** out) {
+  if (!c || !out) return OFDFT_EINVAL;
+  c->err.clear();
+  *out = nullptr;
+  if (precision != OFDFT_PREC_FP64 && precision != OFDFT_PREC_MIXED)
+    return fail(c, OFDFT_EINVAL, "precision must be OFDFT_PREC_FP64 or OFDFT_PREC_MIXED");
+  if (hbm_budget_bytes <= 0) return fail(c, OFDFT_EINVAL, "HBM budget must be positive");
+  CU(cudaSetDevice(c->device));
+  ofdft_batch* b = new ofdft_batch();
+  b->c = c;
+  b->prec = precision;
+  b->budget = hbm_budget_bytes;
+  *out = b;
+  return OFDFT_OK;
+}
+
+int ofdft_batch_destroy(ofdft_batch* b) {
+  if (!b) return OFDFT_OK;
+  ofdft_ctx* c = b->c;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  auto drop = [](auto& v) {
+    for (auto& S : v)
+      if (S->mem) cudaFree(S->mem);
+  };
+  drop(b->s64_active);
+  drop(b->s32_active);
+  drop(b->s64_done);
+  drop(b->s32_done);
+  cudaFree(b->sc);
+  cudaFree(b->sc32);
+  cudaFree(b->out);
+  for (DevArena* a : {&b->d_tiles, &b->d_desc, &b->d_segs, &b->d_ops}) cudaFree(a->p);
+  delete b;
+  return OFDFT_OK;
+}
+
+int ofdft_batch_submit(ofdft_batch* b, const double* R, const double* Z, int M, double h, const ofdft_params* p,
+                       const ofdft_grid* grid, int* request_id) {
+  if (!b || !request_id) return OFDFT_EINVAL;
+  ofdft_ctx* c = b->c;
+  c->err.clear();
+  TRY(check_params(c, p));
+  TRY(check_atoms(c, R, Z, M));
+  if (p->precision != b->prec) return fail(c, OFDFT_EINVAL, "request precision differs from the batch precision");
+  if (b->prec == OFDFT_PREC_FP64) return submit_impl<double>(b, R, Z, M, h, p, grid, request_id);
+  return submit_impl<float>(b, R, Z, M, h, p, grid, request_id);
+}
+
+int ofdft_batch_step(ofdft_batch* b, int* n_active, int* n_queued) {
+  if (!b) return OFDFT_EINVAL;
+  ofdft_ctx* c = b->c;
+  c->err.clear();
+  CU(cudaSetDevice(c->device));
+  int rc;
+  if (b->prec == OFDFT_PREC_FP64) {
+    Engine<double> E = engine_of<double>(b);
+    rc = E.step();
+    if (n_active) *n_active = (int)E.active->size();
+    if (n_queued) *n_queued = (int)E.queue->size();
+  } else {
+    Engine<float> E = engine_of<float>(b);
+    rc = E.step();
+    if (n_active) *n_active = (int)E.active->size();
+    if (n_queued) *n_queued = (int)E.queue->size();
+  }
+  return rc;
+}
+
+int ofdft_batch_poll(ofdft_batch* b, int request_id, int* done, double* energy, double* forces,
+                     ofdft_solve_stats* st) {
+  if (!b || !done) return OFDFT_EINVAL;
+  b->c->err.clear();
+  if (b->prec == OFDFT_PREC_FP64) return poll_impl<double>(b, request_id, done, energy, forces, st);
+  return poll_impl<float>(b, request_id, done, energy, forces, st);
+}
+
+int ofdft_batch_run(ofdft_batch* b) {
+  if (!b) return OFDFT_EINVAL;
+  for (;;) {
+    int na = 0, nq = 0;
+    const int rc = ofdft_batch_step(b, &na, &nq);
+    if (rc != OFDFT_OK) return rc;
+    if (na == 0 && nq == 0) return OFDFT_OK;
+  }
+}
+
+long long ofdft_batch_bytes(const ofdft_grid* g, int prec) {
+  if (!g) return -1;
+  int mb = 0;
+  return slot_bytes(*g, prec, &mb);
+}
+
+}  // extern "C"

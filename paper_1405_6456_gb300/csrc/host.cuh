@@ -146,7 +146,7 @@ struct ProfScope {
   ProfScope(ofdft_ctx* c_, int k) : c(c_), kind(k) {
     c->launches++;
     c->kind_launches[k]++;
-    if (c->prof) {
+    if (c->prof & (1 << k)) {
       a = take_event(c);
       b = take_event(c);
       if (a && b) cudaEventRecord(a, c->stream);
@@ -270,10 +270,16 @@ template <typename T, int R, class L, class E>
 int launch_z(ofdft_ctx* c, const GridDev& g, const Weights<double>& W, L ld, E ep, int kind) {
   const ZShape s = zshape(c, g, R);
   if (E::K > 0) TRY(ensure_partials(c, s.nblocks, E::K));
+  constexpr int smem = zring_bytes<T, R>();
+  static bool attr = false;  // dynamic shared memory above 48 KB needs an opt-in per kernel
+  if (!attr) {
+    CU(cudaFuncSetAttribute(zstream_kernel<T, R, L, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    attr = true;
+  }
   {
     ProfScope ps_(c, kind);
-    zstream_kernel<T, R, L, E><<<s.grid, dim3(BX, BY), 0, c->stream>>>(g, cast_weights<T>(W), s.zchunk, ld, ep,
-                                                                       red(c));
+    zstream_kernel<T, R, L, E><<<s.grid, dim3(BX, BY), smem, c->stream>>>(g, cast_weights<T>(W), s.zchunk, ld, ep,
+                                                                          red(c));
   }
   CU(cudaGetLastError());
   return OFDFT_OK;
@@ -299,6 +305,30 @@ inline int sync_scalars(ofdft_ctx* c, const void* dev, size_t bytes, void* host)
   CU(cudaStreamSynchronize(c->stream));
   if (!c->pending.empty()) harvest(c);
   return OFDFT_OK;
+}
+
+struct EvalOut {
+  double sums[12];
+};
+
+inline void fill_energy(const EvalOut& o, double h, const ofdft_params* p, double E_self, double ezz, double eta,
+                 double mu, ofdft_energy* e) {
+  const double h3 = h * h * h;
+  const bool es = p->terms & OFDFT_TERM_ES;
+  e->E_tf = h3 * o.sums[0];
+  e->E_vw = -0.5 * p->lambda * h3 * o.sums[1];
+  e->E_xc = h3 * o.sums[2];
+  e->E_self = es ? E_self : 0.0;
+  e->E_es = es ? h3 * (0.5 * o.sums[3] + o.sums[4] / (8.0 * kPi)) - E_self : 0.0;
+  e->E_zz_corr = ezz;
+  e->E = e->E_tf + e->E_vw + e->E_xc + e->E_es + ezz;
+  e->C = o.sums[9];
+  e->L = e->E - eta * e->C + 0.5 * e->C * e->C / mu;
+  e->gd = h3 * o.sums[5];
+  e->gs_old = h3 * o.sums[6];
+  e->rs = h3 * o.sums[7];
+  e->rs_pc = e->rs;
+  e->gnorm2 = h3 * o.sums[8];
 }
 
 // Routines of api.cu used by the batched engine (instantiated for double and float).

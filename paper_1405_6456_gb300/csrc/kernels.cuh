@@ -47,92 +47,108 @@ struct CgScalars {
 // Epi:    static constexpr int K (number of FP64 partial sums), bool skip(),
 //         void apply(idx, centre, lap, acc[K]), and fin(sums[K]) run once by
 //         the last block.
-template <typename T, int R, class Loader, class Epi>
-__global__ void __launch_bounds__(NT) zstream_kernel(GridDev g, Weights<T> W, int zchunk,
-                                                     Loader ld, Epi ep, RedBuf red) {
+// Asynchronous 4- or 8-byte global -> shared copy; src_valid == false fills the
+// destination with zeros (the zero Dirichlet value of every out-of-grid node) and
+// reads nothing.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src, bool src_valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const int n = src_valid ? (int)sizeof(T) : 0;
+  if constexpr (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Depth of the plane pipeline and the shared-memory ring of planes it needs.
+constexpr int ZD = 3;
+template <typename T, int R>
+constexpr int zring_bytes() {
+  return (R + ZD) * (BY + 2 * R) * (BX + 2 * R) * (int)sizeof(T);
+}
+
+// One block's share of a z-streaming pass: tile (bx, by) of the BX x BY column
+// grid, planes [z0, z1).  Planes are staged (tile plus an R-wide x/y halo) in a
+// shared-memory ring of R + ZD slots by cp.async, ZD planes ahead of use; the
+// block's own column along z lives in a register queue fed from the ring.  No
+// register ever holds an in-flight load, so global latency overlaps compute.
+// nblocks / bid describe the reduction this block takes part in (the whole grid
+// for a single solve, one grid of a batch otherwise).  f is the stencil input.
+template <typename T, int R, class Epi>
+__device__ __forceinline__ void zstream_tile(const GridDev& g, const Weights<T>& W, int bx, int by, int z0, int z1,
+                                             const T* __restrict__ f, const Epi& ep, const RedBuf& red, int nblocks,
+                                             int bid) {
   if (ep.skip()) return;
-  __shared__ T s[BY + 2 * R][BX + 2 * R];
+  constexpr int NS = R + ZD;
+  constexpr int SY = BY + 2 * R, SX = BX + 2 * R;
+  extern __shared__ __align__(16) unsigned char zsm_raw[];
+  T(*ring)[SY][SX] = reinterpret_cast<T(*)[SY][SX]>(zsm_raw);
   __shared__ double red_smem[(Epi::K > 0 ? Epi::K : 1) * (NT / 32)];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * BX + tx;
-  const int x = blockIdx.x * BX + tx, y = blockIdx.y * BY + ty;
-  const int z0 = blockIdx.z * zchunk;
-  const int z1 = min(z0 + zchunk, g.n3);
+  const int x = bx * BX + tx, y = by * BY + ty;
   const bool in_xy = (x < g.n1) && (y < g.n2);
   const long long col = (long long)x + (long long)g.n1 * y;
   const long long plane = (long long)g.n1 * g.n2;
 
   // halo nodes this thread stages: x-halo (tx < R) left/right, y-halo (ty < R) below/above
-  const int xl = blockIdx.x * BX - R + tx, xr = blockIdx.x * BX + BX + tx;
-  const int yb = blockIdx.y * BY - R + ty, yt = blockIdx.y * BY + BY + ty;
+  const int xl = bx * BX - R + tx, xr = bx * BX + BX + tx;
+  const int yb = by * BY - R + ty, yt = by * BY + BY + ty;
   const bool hx = tx < R, hy = ty < R;
   const bool okl = hx && y < g.n2 && xl >= 0, okr = hx && y < g.n2 && xr < g.n1;
   const bool okb = hy && x < g.n1 && yb >= 0, okt = hy && x < g.n1 && yt < g.n2;
   const long long il = (long long)g.n1 * y + xl, ir = (long long)g.n1 * y + xr;
   const long long ib = (long long)g.n1 * yb + x, it = (long long)g.n1 * yt + x;
 
-  // register queue of the block's own column along z (planes k-R .. k+R)
+  // stage plane p into its ring slot (every thread commits one group per plane)
+  auto stage = [&](int p) {
+    const int sl = ((p % NS) + NS) % NS;
+    const bool pv = (p >= 0) && (p < g.n3);
+    const long long pb = plane * (long long)(pv ? p : 0);
+    cp_async_elem(&ring[sl][ty + R][tx + R], f + (pv && in_xy ? pb + col : 0), pv && in_xy);
+    if (hx) {
+      cp_async_elem(&ring[sl][ty + R][tx], f + (pv && okl ? pb + il : 0), pv && okl);
+      cp_async_elem(&ring[sl][ty + R][tx + BX + R], f + (pv && okr ? pb + ir : 0), pv && okr);
+    }
+    if (hy) {
+      cp_async_elem(&ring[sl][ty][tx + R], f + (pv && okb ? pb + ib : 0), pv && okb);
+      cp_async_elem(&ring[sl][ty + BY + R][tx + R], f + (pv && okt ? pb + it : 0), pv && okt);
+    }
+    cp_async_commit();
+  };
+
+  // register queue of the own column along z (planes k-R .. k+R); the planes
+  // below the chunk and the first R of it come from plain loads
   T q[2 * R + 1];
 #pragma unroll
   for (int i = 0; i < 2 * R; ++i) {
     const int k = z0 - R + i;
-    q[i] = (in_xy && k >= 0 && k < g.n3) ? ((k >= z0 && k < z1) ? ld.own(col + plane * k)
-                                                                  : ld.value(col + plane * k))
-                                         : T(0);
+    q[i] = (in_xy && k >= 0 && k < g.n3) ? f[col + plane * k] : T(0);
   }
-  // halo values prefetched PF planes ahead, so their loads overlap earlier steps
-  constexpr int PF = 4;
-  T hv[PF][4];
-#pragma unroll
-  for (int j = 0; j < PF; ++j) {
-    const int k = z0 + j;
-    const bool kk = k < z1;
-    const long long pk = plane * k;
-    hv[j][0] = (kk && okl) ? ld.value(pk + il) : T(0);
-    hv[j][1] = (kk && okr) ? ld.value(pk + ir) : T(0);
-    hv[j][2] = (kk && okb) ? ld.value(pk + ib) : T(0);
-    hv[j][3] = (kk && okt) ? ld.value(pk + it) : T(0);
-  }
+  for (int p = z0; p < z0 + R + ZD - 1; ++p) stage(p);
+
   double acc[Epi::K > 0 ? Epi::K : 1];
 #pragma unroll
   for (int i = 0; i < (Epi::K > 0 ? Epi::K : 1); ++i) acc[i] = 0.0;
 
   for (int k = z0; k < z1; ++k) {
-    const int kf = k + R;
-    q[2 * R] = (in_xy && kf < g.n3) ? ((kf < z1) ? ld.own(col + plane * kf)
-                                                : ld.value(col + plane * kf))
-                                    : T(0);
-    __syncthreads();
-    s[ty + R][tx + R] = q[R];
-    if (hx) {
-      s[ty + R][tx] = hv[0][0];
-      s[ty + R][tx + BX + R] = hv[0][1];
-    }
-    if (hy) {
-      s[ty][tx + R] = hv[0][2];
-      s[ty + BY + R][tx + R] = hv[0][3];
-    }
-#pragma unroll
-    for (int j = 0; j < PF - 1; ++j) {
-#pragma unroll
-      for (int m = 0; m < 4; ++m) hv[j][m] = hv[j + 1][m];
-    }
-    {
-      const int kn = k + PF;
-      const bool kk = kn < z1;
-      const long long pk = plane * kn;
-      hv[PF - 1][0] = (kk && okl) ? ld.value(pk + il) : T(0);
-      hv[PF - 1][1] = (kk && okr) ? ld.value(pk + ir) : T(0);
-      hv[PF - 1][2] = (kk && okb) ? ld.value(pk + ib) : T(0);
-      hv[PF - 1][3] = (kk && okt) ? ld.value(pk + it) : T(0);
-    }
-    __syncthreads();
+    __syncthreads();         // every thread is done with plane k-1's slot
+    stage(k + R + ZD - 1);   // refills that slot
+    cp_async_wait<ZD - 1>();  // planes <= k + R have landed (this thread's copies)
+    __syncthreads();         // ... and every other thread's
+    const int sk = k % NS, sf = (k + R) % NS;
+    q[2 * R] = ring[sf][ty + R][tx + R];
     if (in_xy) {
       T lap = W.c * q[R];
 #pragma unroll
       for (int p = 1; p <= R; ++p) {
-        const T sx = s[ty + R][tx + R + p] + s[ty + R][tx + R - p];
-        const T sy = s[ty + R + p][tx + R] + s[ty + R - p][tx + R];
+        const T sx = ring[sk][ty + R][tx + R + p] + ring[sk][ty + R][tx + R - p];
+        const T sy = ring[sk][ty + R + p][tx + R] + ring[sk][ty + R - p][tx + R];
         const T sz = q[R + p] + q[R - p];
         lap = fma(W.w[p], (sx + sy) + sz, lap);
       }
@@ -141,10 +157,73 @@ __global__ void __launch_bounds__(NT) zstream_kernel(GridDev g, Weights<T> W, in
 #pragma unroll
     for (int i = 0; i < 2 * R; ++i) q[i] = q[i + 1];
   }
+  cp_async_wait<0>();
   if constexpr (Epi::K > 0) {
-    const int nblocks = gridDim.x * gridDim.y * gridDim.z;
-    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-    grid_sum<Epi::K, NT>(acc, red_smem, red, nblocks, bid, tid, ep);
+    Epi fin = ep;
+    grid_sum<Epi::K, NT>(acc, red_smem, red, nblocks, bid, tid, fin);
+  }
+}
+
+// Single grid: blocks tile (x, y) and split z into chunks of `zchunk` planes.
+template <typename T, int R, class Loader, class Epi>
+__global__ void __launch_bounds__(NT) zstream_kernel(GridDev g, Weights<T> W, int zchunk,
+                                                     Loader ld, Epi ep, RedBuf red) {
+  const int z0 = blockIdx.z * zchunk;
+  const int z1 = min(z0 + zchunk, g.n3);
+  const int nblocks = gridDim.x * gridDim.y * gridDim.z;
+  const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  zstream_tile<T, R>(g, W, blockIdx.x, blockIdx.y, z0, z1, ld.f, ep, red, nblocks, bid);
+}
+
+// Batched: uneven grids packed into one launch (S11).  Block b works on
+// tiles[b] of grid slots[tiles[b].slot]; each grid reduces into its own scratch.
+struct ZTile {
+  int slot, bx, by, z0, z1, bid;
+};
+
+template <typename T, class Loader, class Epi>
+struct ZSlot {
+  GridDev g;
+  Weights<T> W;
+  Loader ld;
+  Epi ep;
+  RedBuf red;
+  int nblocks;
+};
+
+template <typename T, int R, class Loader, class Epi>
+__global__ void __launch_bounds__(NT) zbatch_kernel(const ZTile* __restrict__ tiles,
+                                                    const ZSlot<T, Loader, Epi>* __restrict__ slots) {
+  const ZTile t = tiles[blockIdx.x];
+  const ZSlot<T, Loader, Epi>* S = slots + t.slot;
+  const GridDev g = S->g;
+  const Weights<T> W = S->W;
+  const Epi ep = S->ep;
+  const RedBuf red = S->red;
+  zstream_tile<T, R>(g, W, t.bx, t.by, t.z0, t.z1, S->ld.f, ep, red, S->nblocks, t.bid);
+}
+
+// Batched pointwise pass: block b works on elements [begin, end) of grid
+// segs[b].slot with that grid's operation; per-grid deterministic reductions.
+struct PSeg {
+  int slot;
+  int bid;
+  long long begin, end;
+};
+
+template <class Op>
+__global__ void __launch_bounds__(256) pbatch_kernel(const PSeg* __restrict__ segs, const Op* __restrict__ ops) {
+  const PSeg sg = segs[blockIdx.x];
+  const Op op = ops[sg.slot];
+  if (op.skip()) return;
+  __shared__ double smem[(Op::K > 0 ? Op::K : 1) * (256 / 32)];
+  double acc[Op::K > 0 ? Op::K : 1];
+#pragma unroll
+  for (int i = 0; i < (Op::K > 0 ? Op::K : 1); ++i) acc[i] = 0.0;
+  for (long long i = sg.begin + threadIdx.x; i < sg.end; i += 256) op.apply(i, acc);
+  if constexpr (Op::K > 0) {
+    Op fin = op;
+    grid_sum<Op::K, 256>(acc, smem, op.red, op.nblocks, sg.bid, threadIdx.x, fin);
   }
 }
 
@@ -154,21 +233,6 @@ struct LoadPlain {
   const T* f;
   __device__ __forceinline__ T value(long long i) const { return f[i]; }
   __device__ __forceinline__ T own(long long i) const { return f[i]; }
-};
-
-// CG search direction p = r + beta p_prev formed on the fly (S3).  p_prev is
-// only read: the new direction goes to a second buffer (other blocks still read
-// p_prev in their halos while this block writes).
-template <typename T>
-struct LoadCgDir {
-  const T* r;
-  const T* p_prev;
-  const CgScalars* sc;
-  __device__ __forceinline__ T value(long long i) const {
-    if (sc->first) return r[i];
-    return fma((T)sc->beta, p_prev[i], r[i]);
-  }
-  __device__ __forceinline__ T own(long long i) const { return value(i); }
 };
 
 // ---------------------------------------------------------------- epilogues --
@@ -455,7 +519,7 @@ __global__ void __launch_bounds__(256) normalise_kernel(long long G, T* u, const
 
 // Start of an FP32 correction solve A e = r (iterative refinement of a mixed
 // Poisson solve): r32 = (float) r64, e = 0, and CG scalars relative to ||r32||.
-__global__ void __launch_bounds__(256) refine_init_kernel(long long G, float* r32, float* e,
+static __global__ void __launch_bounds__(256) refine_init_kernel(long long G, float* r32, float* e,
                                                           const double* r64, CgScalars* sc,
                                                           double tol, int max_it, RedBuf red) {
   __shared__ double smem[256 / 32];
@@ -486,7 +550,7 @@ __global__ void __launch_bounds__(256) refine_init_kernel(long long G, float* r3
 }
 
 // phi64 += e (apply an FP32 correction to the FP64 potential) and phi32 = (float) phi64.
-__global__ void __launch_bounds__(256) refine_apply_kernel(long long G, double* phi64, float* phi32,
+static __global__ void __launch_bounds__(256) refine_apply_kernel(long long G, double* phi64, float* phi32,
                                                            const float* e) {
   for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < G; i += (long long)gridDim.x * 256) {
     const double v = phi64[i] + (double)e[i];
@@ -500,6 +564,153 @@ __global__ void __launch_bounds__(256) convert_kernel(long long G, D* out, const
   for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < G; i += (long long)gridDim.x * 256)
     out[i] = (D)in[i];
 }
+
+// ------------------------------------------------- batched pointwise ops ---
+// CG second half on one grid of a batch (same arithmetic as cg_update_kernel).
+template <typename T>
+struct OpCgUpdate {
+  static constexpr int K = 1;
+  T* x;
+  T* r;
+  const T* p;
+  const T* q;
+  CgScalars* sc;
+  RedBuf red;
+  int nblocks;
+  __device__ __forceinline__ bool skip() const { return sc->done != 0; }
+  __device__ __forceinline__ void apply(long long i, double* acc) const {
+    const T al = (T)sc->alpha;
+    x[i] = fma(al, p[i], x[i]);
+    const T ri = fma(-al, q[i], r[i]);
+    r[i] = ri;
+    acc[0] += (double)ri * (double)ri;
+  }
+  __device__ __forceinline__ void operator()(double* t) const {
+    const double rr_new = t[0];
+    sc->beta = (sc->rr != 0.0) ? rr_new / sc->rr : 0.0;
+    sc->rr = rr_new;
+    sc->iters += 1;
+    const double thr = sc->tol2 * (sc->bb > 0.0 ? sc->bb : 1.0);
+    if (rr_new <= thr || sc->iters >= sc->max_it || !(rr_new == rr_new)) sc->done = 1;
+  }
+};
+
+// out = |a + alpha b| (trial point / secant update, u <- |u|).
+template <typename T>
+struct OpAxpyAbs {
+  static constexpr int K = 0;
+  T* out;
+  const T* a;
+  const T* b;
+  double alpha;
+  __device__ __forceinline__ bool skip() const { return false; }
+  __device__ __forceinline__ void apply(long long i, double*) const { out[i] = fabs(fma((T)alpha, b[i], a[i])); }
+  __device__ __forceinline__ void operator()(double*) const {}
+};
+
+// d = s + beta d (Polak-Ribiere), d = s when beta == 0.
+template <typename T>
+struct OpDirection {
+  static constexpr int K = 0;
+  T* d;
+  const T* s;
+  double beta;
+  __device__ __forceinline__ bool skip() const { return false; }
+  __device__ __forceinline__ void apply(long long i, double*) const {
+    d[i] = (beta == 0.0) ? s[i] : fma((T)beta, d[i], s[i]);
+  }
+  __device__ __forceinline__ void operator()(double*) const {}
+};
+
+// out[0] = a.b, out[1] = c.e (FP64 accumulation).
+template <typename T>
+struct OpDot2 {
+  static constexpr int K = 2;
+  const T* a;
+  const T* b;
+  const T* c;
+  const T* e;
+  double* out;
+  RedBuf red;
+  int nblocks;
+  __device__ __forceinline__ bool skip() const { return false; }
+  __device__ __forceinline__ void apply(long long i, double* acc) const {
+    acc[0] += (double)a[i] * (double)b[i];
+    acc[1] += (double)c[i] * (double)e[i];
+  }
+  __device__ __forceinline__ void operator()(double* t) const {
+    out[0] = t[0];
+    out[1] = t[1];
+  }
+};
+
+// s -= gamma w (rank-one correction of the preconditioner).
+template <typename T>
+struct OpRank1 {
+  static constexpr int K = 0;
+  T* s;
+  const T* w;
+  double gamma;
+  __device__ __forceinline__ bool skip() const { return false; }
+  __device__ __forceinline__ void apply(long long i, double*) const { s[i] = fma(-(T)gamma, w[i], s[i]); }
+  __device__ __forceinline__ void operator()(double*) const {}
+};
+
+// Start of an FP32 correction solve (mixed Poisson): r32 = (float) r64, e = 0.
+struct OpRefineInit {
+  static constexpr int K = 1;
+  float* r32;
+  float* e;
+  const double* r64;
+  CgScalars* sc;
+  double tol;
+  int max_it;
+  RedBuf red;
+  int nblocks;
+  __device__ __forceinline__ bool skip() const { return false; }
+  __device__ __forceinline__ void apply(long long i, double* acc) const {
+    const float v = (float)r64[i];
+    r32[i] = v;
+    e[i] = 0.0f;
+    acc[0] += (double)v * (double)v;
+  }
+  __device__ __forceinline__ void operator()(double* t) const {
+    sc->rr = t[0];
+    sc->rr0 = t[0];
+    sc->bb = t[0];
+    sc->tol2 = tol * tol;
+    sc->iters = 0;
+    sc->max_it = max_it;
+    sc->first = 1;
+    sc->beta = 0.0;
+    sc->done = (t[0] == 0.0 || max_it <= 0) ? 1 : 0;
+  }
+};
+
+// phi64 += e, phi32 = (float) phi64.
+struct OpRefineApply {
+  static constexpr int K = 0;
+  double* phi64;
+  float* phi32;
+  const float* e;
+  __device__ __forceinline__ bool skip() const { return false; }
+  __device__ __forceinline__ void apply(long long i, double*) const {
+    const double v = phi64[i] + (double)e[i];
+    phi64[i] = v;
+    phi32[i] = (float)v;
+  }
+  __device__ __forceinline__ void operator()(double*) const {}
+};
+
+template <typename S, typename D>
+struct OpConvert {
+  static constexpr int K = 0;
+  D* out;
+  const S* in;
+  __device__ __forceinline__ bool skip() const { return false; }
+  __device__ __forceinline__ void apply(long long i, double*) const { out[i] = (D)in[i]; }
+  __device__ __forceinline__ void operator()(double*) const {}
+};
 
 // ------------------------------------------------------------ atom kernels --
 // Node-to-atom offsets and distances computed with explicitly rounded IEEE
@@ -665,7 +876,7 @@ struct AtomBox {
 };
 
 // V_J tabulated on the atom's box grown by 2R (forces, paper form): vbox[a][...].
-__global__ void __launch_bounds__(256) force_vbox_kernel(AtomArgs A, int a0, int na, int vdim, int R,
+static __global__ void __launch_bounds__(256) force_vbox_kernel(AtomArgs A, int a0, int na, int vdim, int R,
                                                          const int* __restrict__ lo, double* vbox) {
   const long long per = (long long)vdim * vdim * vdim;
   for (long long t = (long long)blockIdx.x * 256 + threadIdx.x; t < per * na; t += (long long)gridDim.x * 256) {
@@ -792,7 +1003,7 @@ __global__ void __launch_bounds__(256) force_ball_kernel(GridDev g, AtomArgs A, 
 }
 
 // F[J] = h^3 * (sum of the per-block partials of atom J, in block order).
-__global__ void force_sum_kernel(int a0, int na, int nblk, double h3, const double* partial, double* F) {
+static __global__ void force_sum_kernel(int a0, int na, int nblk, double h3, const double* partial, double* F) {
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= na) return;
   double f[3] = {0.0, 0.0, 0.0};
@@ -804,7 +1015,7 @@ __global__ void force_sum_kernel(int a0, int na, int nblk, double h3, const doub
 // Gaussian-overlap repulsion correction (Appendix A in closed form):
 // E_c = sum_{I<J} Z_I Z_J erfc(R_IJ/(sqrt2 sigma))/R_IJ and its forces.  One
 // thread per atom I sums over all J != I (half the pair energy each).
-__global__ void ezz_kernel(AtomArgs A, double* eI, double* F) {
+static __global__ void ezz_kernel(AtomArgs A, double* eI, double* F) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= A.M) return;
   const double a = 0.70710678118654752 / A.sigma;

@@ -132,6 +132,15 @@ def lib():
     L.ofdft_profile.argtypes = [vp, ip]
     L.ofdft_get_counters.argtypes = [vp, C.POINTER(Counters)]
     L.ofdft_reset_counters.argtypes = [vp]
+    L.ofdft_batch_create.argtypes = [vp, ip, C.c_longlong, C.POINTER(vp)]
+    L.ofdft_batch_destroy.argtypes = [vp]
+    L.ofdft_batch_submit.argtypes = [vp, dp, dp, ip, C.c_double, C.POINTER(Params), C.POINTER(Grid),
+                                     C.POINTER(C.c_int)]
+    L.ofdft_batch_step.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.ofdft_batch_poll.argtypes = [vp, ip, C.POINTER(C.c_int), dp, dp, C.POINTER(SolveStats)]
+    L.ofdft_batch_run.argtypes = [vp]
+    L.ofdft_batch_bytes.argtypes = [C.POINTER(Grid), ip]
+    L.ofdft_batch_bytes.restype = C.c_longlong
     L.ofdft_workspace_bytes.argtypes = [C.POINTER(Grid), ip, ip]
     L.ofdft_workspace_bytes.restype = C.c_longlong
     _lib = L
@@ -227,8 +236,10 @@ class Context:
         return rc
 
     # tracing
-    def profile(self, enable: bool):
-        return self._check(self._lib.ofdft_profile(self.h, 1 if enable else 0), "ofdft_profile")
+    def profile(self, kinds=-1):
+        """Time launches of the given kinds (bitmask of 1 << K_*; True/-1: all; False/0: none)."""
+        mask = -1 if kinds is True else (0 if kinds is False else int(kinds))
+        return self._check(self._lib.ofdft_profile(self.h, mask), "ofdft_profile")
 
     def counters(self) -> Counters:
         c = Counters()
@@ -301,6 +312,62 @@ class Context:
         return E.value, F, st
 
 
+class Batch:
+    """A batch of ground-state solves advanced together (ofdft_batch_*)."""
+
+    def __init__(self, ctx: Context, precision: int, hbm_budget_bytes: int):
+        self.ctx = ctx
+        self.h = C.c_void_p()
+        ctx._check(ctx._lib.ofdft_batch_create(ctx.h, precision, int(hbm_budget_bytes), C.byref(self.h)),
+                   "ofdft_batch_create")
+        self.M = {}
+
+    def close(self):
+        if self.h:
+            self.ctx._lib.ofdft_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, R, Z, h, p: Params, grid: Grid | None = None) -> int:
+        R, Z = _host_f64(R).reshape(-1, 3), _host_f64(Z)
+        rid = C.c_int()
+        self.ctx._check(self.ctx._lib.ofdft_batch_submit(self.h, _dp(R), _dp(Z), R.shape[0], h, C.byref(p),
+                                                         C.byref(grid) if grid is not None else None,
+                                                         C.byref(rid)), "ofdft_batch_submit")
+        self.M[rid.value] = R.shape[0]
+        return rid.value
+
+    def step(self):
+        na, nq = C.c_int(), C.c_int()
+        self.ctx._check(self.ctx._lib.ofdft_batch_step(self.h, C.byref(na), C.byref(nq)), "ofdft_batch_step")
+        return na.value, nq.value
+
+    def poll(self, rid: int, allow_notconv=False):
+        """None while running; (energy, forces, SolveStats) once finished."""
+        done = C.c_int()
+        E = C.c_double()
+        F = np.zeros((self.M[rid], 3))
+        st = SolveStats()
+        rc = self.ctx._lib.ofdft_batch_poll(self.h, rid, C.byref(done), C.byref(E), _dp(F), C.byref(st))
+        if not done.value:
+            self.ctx._check(rc, "ofdft_batch_poll")
+            return None
+        self.ctx._check(rc, "ofdft_batch_poll", allow=(ENOTCONV,) if allow_notconv else ())
+        return E.value, F, st
+
+    def run(self):
+        self.ctx._check(self.ctx._lib.ofdft_batch_run(self.h), "ofdft_batch_run")
+
+
+def batch_bytes(g: Grid, prec: int) -> int:
+    return int(lib().ofdft_batch_bytes(C.byref(g), prec))
+
+
 def workspace_bytes(g: Grid, fd_order: int, prec: int) -> int:
     return int(lib().ofdft_workspace_bytes(C.byref(g), fd_order, prec))
 
@@ -310,5 +377,7 @@ def exported_symbols():
     return ["ofdft_default_params", "ofdft_create", "ofdft_destroy", "ofdft_last_error",
             "ofdft_grid_for_atoms", "ofdft_stencil", "ofdft_pseudocharge", "ofdft_initial_guess",
             "ofdft_poisson", "ofdft_energy_grad", "ofdft_forces", "ofdft_solve",
-            "ofdft_workspace_bytes", "ofdft_profile", "ofdft_get_counters", "ofdft_reset_counters"]
+            "ofdft_workspace_bytes", "ofdft_profile", "ofdft_get_counters", "ofdft_reset_counters",
+            "ofdft_batch_create", "ofdft_batch_destroy", "ofdft_batch_submit", "ofdft_batch_step",
+            "ofdft_batch_poll", "ofdft_batch_run", "ofdft_batch_bytes"]
 
