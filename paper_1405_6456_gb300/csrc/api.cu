@@ -9,27 +9,90 @@ namespace ofd {
 // ------------------------------------------------------------ Poisson (S3) --
 // Plain CG iterations on the prepared scalars `sc` (residual r, iterate x),
 // checking the device `done` flag every `chunk` iterations.
+// Launches one CG iteration (S3): the stencil pass on r with the p/q update and
+// p.q, then the x/r update with r.r; both kernels read and write the CG scalars
+// on the device and return at once when the solve is done.
 template <typename T>
-int cg_iterate(ofdft_ctx* c, int R, const GridDev& g, const Weights<double>& Wneg, T* x, T* r, CgScalars* sc,
-               int max_it, CgScalars* host_sc) {
-  T* p0 = vec<T>(c, V_P0);
-  T* Ap = vec<T>(c, V_AP);
+int cg_step(ofdft_ctx* c, int R, const GridDev& g, const Weights<double>& Wneg, T* x, T* r, T* pv, T* qv,
+            CgScalars* sc, int pb) {
+  TRY(launch_z_r<T>(c, R, g, Wneg, LoadPlain<T>{r}, EpiCgA<T>{pv, qv, sc}, OFDFT_K_CG_DIR_STENCIL));
+  {
+    ProfScope ps_(c, OFDFT_K_CG_UPDATE);
+    cg_update_kernel<T><<<pb, 256, 0, c->stream>>>(g.G, x, r, pv, qv, sc, red(c));
+  }
+  CU(cudaGetLastError());
+  return OFDFT_OK;
+}
+
+constexpr int kChunk = 8;  // CG iterations between convergence polls
+
+// The graph of one chunk of CG iterations for this buffer set, captured on
+// first use (the launches bake in pointers, sizes and weights).
+template <typename T>
+int cg_graph(ofdft_ctx* c, int R, const GridDev& g, double h, const Weights<double>& Wneg, T* x, T* r, T* pv, T* qv,
+             CgScalars* sc, int pb, cudaGraphExec_t* out) {
+  const std::vector<long long> key = {(long long)sizeof(T), R, g.n1, g.n2, g.n3, (long long)x, (long long)r,
+                                      (long long)pv, (long long)qv, (long long)sc, pb,
+                                      (long long)c->partials.p, (long long)(h * 1e12)};
+  for (auto& e : c->graphs)
+    if (e.key == key) {
+      *out = e.exec;
+      return OFDFT_OK;
+    }
+  // the launches must not allocate or time themselves while being captured
+  const int prof = c->prof;
+  c->prof = 0;
+  const long long launches = c->launches;
+  long long kinds[OFDFT_K_COUNT];
+  memcpy(kinds, c->kind_launches, sizeof(kinds));
+  TRY(cg_step<T>(c, R, g, Wneg, x, r, pv, qv, sc, pb));  // sets kernel attributes outside capture
+  CU(cudaStreamSynchronize(c->stream));
+  cudaGraph_t graph = nullptr;
+  CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  int rc = OFDFT_OK;
+  for (int i = 0; i < kChunk && rc == OFDFT_OK; ++i) rc = cg_step<T>(c, R, g, Wneg, x, r, pv, qv, sc, pb);
+  const cudaError_t ec = cudaStreamEndCapture(c->stream, &graph);
+  c->prof = prof;
+  c->launches = launches;
+  memcpy(c->kind_launches, kinds, sizeof(kinds));
+  if (rc != OFDFT_OK) return rc;
+  if (ec != cudaSuccess) return fail(c, OFDFT_ECUDA, "CG graph capture: %s", cudaGetErrorString(ec));
+  cudaGraphExec_t exec = nullptr;
+  CU(cudaGraphInstantiate(&exec, graph, 0));
+  cudaGraphDestroy(graph);
+  c->graphs.push_back({key, exec});
+  *out = exec;
+  return OFDFT_OK;
+}
+
+// Plain CG iterations on the prepared scalars `sc` (residual r, iterate x),
+// checking the device `done` flag every kChunk iterations.  Chunk k+1 is
+// enqueued before the host waits for chunk k's copy of the scalars, so the
+// stream never drains; kernels of a converged solve return at once, so an extra
+// chunk costs only empty launches.  Without per-launch timing a chunk is one
+// CUDA graph launch.
+template <typename T>
+int cg_iterate(ofdft_ctx* c, int R, const GridDev& g, double h, const Weights<double>& Wneg, T* x, T* r,
+               CgScalars* sc, int max_it, CgScalars* host_sc) {
+  T* pv = vec<T>(c, V_P0);
+  T* qv = vec<T>(c, V_AP);
   const int pb = pointwise_blocks(c, g.G);
   TRY(ensure_partials(c, pb, 1));
-  const int chunk = 8;
+  TRY(ensure_partials(c, zshape(c, g, R).nblocks, 1));
+  const bool timed = (c->prof & ((1 << OFDFT_K_CG_DIR_STENCIL) | (1 << OFDFT_K_CG_UPDATE))) != 0;
+  cudaGraphExec_t exec = nullptr;
+  if (c->use_graphs && !timed && max_it >= kChunk) TRY(cg_graph<T>(c, R, g, h, Wneg, x, r, pv, qv, sc, pb, &exec));
   int launched = 0, chunks = 0;
-  // Chunk k+1 is enqueued before the host waits for chunk k's copy of the
-  // scalars, so the stream never drains; kernels of a converged solve return at
-  // once (device `done` flag), so an extra chunk costs only empty launches.
   while (launched < max_it) {
-    for (int i = 0; i < chunk && launched < max_it; ++i, ++launched) {
-      // p and q = A p live in p0 and Ap and are updated in place
-      TRY(launch_z_r<T>(c, R, g, Wneg, LoadPlain<T>{r}, EpiCgA<T>{p0, Ap, sc}, OFDFT_K_CG_DIR_STENCIL));
-      {
-        ProfScope ps_(c, OFDFT_K_CG_UPDATE);
-        cg_update_kernel<T><<<pb, 256, 0, c->stream>>>(g.G, x, r, p0, Ap, sc, red(c));
-      }
-      CU(cudaGetLastError());
+    if (exec && launched + kChunk <= max_it) {
+      CU(cudaGraphLaunch(exec, c->stream));
+      launched += kChunk;
+      c->launches += 2 * kChunk;
+      c->kind_launches[OFDFT_K_CG_DIR_STENCIL] += kChunk;
+      c->kind_launches[OFDFT_K_CG_UPDATE] += kChunk;
+    } else {
+      for (int i = 0; i < kChunk && launched < max_it; ++i, ++launched)
+        TRY(cg_step<T>(c, R, g, Wneg, x, r, pv, qv, sc, pb));
     }
     const int slot = chunks & 1;
     CU(cudaMemcpyAsync(&c->ring[slot], sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, c->stream));
@@ -68,7 +131,7 @@ int poisson_fp64(ofdft_ctx* c, int R, const GridDev& g, double h, const double* 
                          EpiResidual<double>{rho, u, b, r, c->sc, tol, max_it, 1}, OFDFT_K_RESIDUAL));
   CgScalars hs;
   TRY(sync_scalars(c, c->sc, sizeof(CgScalars), &hs));
-  if (!hs.done) TRY(cg_iterate<double>(c, R, g, Wneg, phi, r, c->sc, max_it, &hs));
+  if (!hs.done) TRY(cg_iterate<double>(c, R, g, h, Wneg, phi, r, c->sc, max_it, &hs));
   if (st) {
     st->iterations = hs.iters;
     st->rel_residual = sqrt(hs.rr / (hs.bb > 0 ? hs.bb : 1.0));
@@ -122,7 +185,7 @@ int poisson_mixed(ofdft_ctx* c, int R, const GridDev& g, double h, const float* 
       refine_init_kernel<<<pb, 256, 0, c->stream>>>(g.G, r32, e32, r64, c->sc32, 1e-5, budget, red(c));
     }
     CU(cudaGetLastError());
-    TRY(cg_iterate<float>(c, R, g, Wneg, e32, r32, c->sc32, budget, &hs32));
+    TRY(cg_iterate<float>(c, R, g, h, Wneg, e32, r32, c->sc32, budget, &hs32));
     total += std::max(hs32.iters, 1);
     {
       ProfScope ps_(c, OFDFT_K_VECTOR);
@@ -760,6 +823,7 @@ int ofdft_destroy(ofdft_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   cudaDeviceSynchronize();
   harvest(c);
+  for (auto& e : c->graphs) cudaGraphExecDestroy(e.exec);
   for (cudaEvent_t e : c->free_events) cudaEventDestroy(e);
   cudaFree(c->partials.p);
   for (auto& b : c->v) cudaFree(b.p);

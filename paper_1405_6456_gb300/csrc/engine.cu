@@ -153,14 +153,15 @@ int upload(ofdft_ctx* c, DevArena& a, const std::vector<V>& v) {
 long long slot_bytes(const ofdft_grid& g, int prec, int* maxblk) {
   const long long G = (long long)g.n[0] * g.n[1] * g.n[2];
   const long long es = (prec == OFDFT_PREC_MIXED) ? 4 : 8;
-  long long bytes = G * es * 14;
-  if (prec == OFDFT_PREC_MIXED) bytes += G * (8 * 3 + 4);
+  auto chunk = [](long long n) { return (n + 255) & ~255LL; };  // carve() rounds every piece to 256 B
+  long long bytes = 14 * chunk(G * es);
+  if (prec == OFDFT_PREC_MIXED) bytes += 3 * chunk(G * 8) + chunk(G * 4);
   // reduction scratch: the larger of the tile count and the segment count
   const long long tiles = (long long)((g.n[0] + BX - 1) / BX) * ((g.n[1] + BY - 1) / BY) * ((g.n[2] + 15) / 16);
   const long long segs = (G + 16383) / 16384;
   const long long mb = std::max(tiles, segs) + 1;
   *maxblk = (int)mb;
-  bytes += mb * 16 * 8 + 256 + 64 * 16;
+  bytes += chunk(mb * 16 * 8) + chunk(256);
   return bytes;
 }
 
@@ -221,7 +222,7 @@ struct Engine {
 
   template <typename TT, int R, class L, class E>
   int launch_zb(int kind, unsigned nb, const ZTile* dt, const ZSlot<TT, L, E>* ds) {
-    constexpr int smem = zring_bytes<TT, R>();
+    constexpr int smem = zsmem_bytes<TT, R, E>();
     static bool attr = false;
     if (!attr) {
       CU(cudaFuncSetAttribute(zbatch_kernel<TT, R, L, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));

@@ -55,6 +55,13 @@ struct ofdft_ctx {
   // pinned double buffer for polling CG flags without draining the stream
   CgScalars* ring = nullptr;
   cudaEvent_t ring_ev[2] = {nullptr, nullptr};
+  // CUDA graphs of a chunk of CG iterations, keyed by everything they bake in
+  struct GraphEntry {
+    std::vector<long long> key;
+    cudaGraphExec_t exec = nullptr;
+  };
+  std::vector<GraphEntry> graphs;
+  int use_graphs = 1;
 };
 
 namespace ofd {
@@ -239,8 +246,8 @@ Weights<T> cast_weights(const Weights<double>& W) {
 }
 
 inline int pointwise_blocks(ofdft_ctx* c, long long G) {
-  long long b = (G + 255) / 256;
-  return (int)std::max<long long>(1, std::min<long long>(b, (long long)c->sms * 8));
+  long long b = (G + 1023) / 1024;
+  return (int)std::max<long long>(1, std::min<long long>(b, (long long)c->sms * 4));
 }
 
 // z-streaming launch shape: BX x BY columns, z split so that the grid holds
@@ -270,7 +277,7 @@ template <typename T, int R, class L, class E>
 int launch_z(ofdft_ctx* c, const GridDev& g, const Weights<double>& W, L ld, E ep, int kind) {
   const ZShape s = zshape(c, g, R);
   if (E::K > 0) TRY(ensure_partials(c, s.nblocks, E::K));
-  constexpr int smem = zring_bytes<T, R>();
+  constexpr int smem = zsmem_bytes<T, R, E>();
   static bool attr = false;  // dynamic shared memory above 48 KB needs an opt-in per kernel
   if (!attr) {
     CU(cudaFuncSetAttribute(zstream_kernel<T, R, L, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));

@@ -71,6 +71,12 @@ template <typename T, int R>
 constexpr int zring_bytes() {
   return (R + ZD) * (BY + 2 * R) * (BX + 2 * R) * (int)sizeof(T);
 }
+// Dynamic shared memory of a z-streaming pass: the stencil-input ring plus a
+// ring of ZD planes for each pointwise input the epilogue declares (NIN).
+template <typename T, int R, class Epi>
+constexpr int zsmem_bytes() {
+  return zring_bytes<T, R>() + ZD * Epi::NIN * BY * BX * (int)sizeof(T);
+}
 
 // One block's share of a z-streaming pass: tile (bx, by) of the BX x BY column
 // grid, planes [z0, z1).  Planes are staged (tile plus an R-wide x/y halo) in a
@@ -79,6 +85,8 @@ constexpr int zring_bytes() {
 // register ever holds an in-flight load, so global latency overlaps compute.
 // nblocks / bid describe the reduction this block takes part in (the whole grid
 // for a single solve, one grid of a batch otherwise).  f is the stencil input.
+// The epilogue's NIN pointwise inputs (ep.input(j)) at the block's own nodes
+// travel in the same pipeline, so the epilogue never waits on a global load.
 template <typename T, int R, class Epi>
 __device__ __forceinline__ void zstream_tile(const GridDev& g, const Weights<T>& W, int bx, int by, int z0, int z1,
                                              const T* __restrict__ f, const Epi& ep, const RedBuf& red, int nblocks,
@@ -86,8 +94,11 @@ __device__ __forceinline__ void zstream_tile(const GridDev& g, const Weights<T>&
   if (ep.skip()) return;
   constexpr int NS = R + ZD;
   constexpr int SY = BY + 2 * R, SX = BX + 2 * R;
+  constexpr int NIN = Epi::NIN;
   extern __shared__ __align__(16) unsigned char zsm_raw[];
   T(*ring)[SY][SX] = reinterpret_cast<T(*)[SY][SX]>(zsm_raw);
+  T(*pin)[NIN > 0 ? NIN : 1][BY][BX] =
+      reinterpret_cast<T(*)[NIN > 0 ? NIN : 1][BY][BX]>(zsm_raw + zring_bytes<T, R>());
   __shared__ double red_smem[(Epi::K > 0 ? Epi::K : 1) * (NT / 32)];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * BX + tx;
@@ -118,6 +129,19 @@ __device__ __forceinline__ void zstream_tile(const GridDev& g, const Weights<T>&
     if (hy) {
       cp_async_elem(&ring[sl][ty][tx + R], f + (pv && okb ? pb + ib : 0), pv && okb);
       cp_async_elem(&ring[sl][ty + BY + R][tx + R], f + (pv && okt ? pb + it : 0), pv && okt);
+    }
+    if constexpr (NIN > 0) {
+      // pointwise inputs of plane p - R, needed at the same step as stencil plane p
+      const int pp = p - R;
+      if (pp >= z0 && pp < z1) {
+        const long long o = plane * (long long)pp + col;
+#pragma unroll
+        for (int j = 0; j < NIN; ++j) {
+          const T* src = ep.input(j);
+          const bool v = in_xy && src != nullptr;
+          cp_async_elem(&pin[pp % ZD][j][ty][tx], v ? src + o : f, v);
+        }
+      }
     }
     cp_async_commit();
   };
@@ -152,7 +176,10 @@ __device__ __forceinline__ void zstream_tile(const GridDev& g, const Weights<T>&
         const T sz = q[R + p] + q[R - p];
         lap = fma(W.w[p], (sx + sy) + sz, lap);
       }
-      ep.apply(col + plane * k, q[R], lap, acc);
+      T vin[NIN > 0 ? NIN : 1];
+#pragma unroll
+      for (int j = 0; j < NIN; ++j) vin[j] = pin[k % ZD][j][ty][tx];
+      ep.apply(col + plane * k, q[R], lap, vin, acc);
     }
 #pragma unroll
     for (int i = 0; i < 2 * R; ++i) q[i] = q[i + 1];
@@ -240,9 +267,11 @@ struct LoadPlain {
 template <typename T>
 struct EpiStore {
   static constexpr int K = 0;
+  static constexpr int NIN = 0;
   T* out;
   __device__ __forceinline__ bool skip() const { return false; }
-  __device__ __forceinline__ void apply(long long i, T, T lap, double*) const { out[i] = lap; }
+  __device__ __forceinline__ const T* input(int) const { return nullptr; }
+  __device__ __forceinline__ void apply(long long i, T, T lap, const T*, double*) const { out[i] = lap; }
   __device__ __forceinline__ void operator()(double*) const {}
 };
 
@@ -254,19 +283,21 @@ struct EpiStore {
 template <typename T>
 struct EpiCgA {
   static constexpr int K = 1;
+  static constexpr int NIN = 2;  // p_old, q_old at the node, staged by the pipeline
   T* p;
   T* q;
   CgScalars* sc;
   __device__ __forceinline__ bool skip() const { return sc->done != 0; }
-  __device__ __forceinline__ void apply(long long i, T rc, T ar, double* acc) const {
+  __device__ __forceinline__ const T* input(int j) const { return j == 0 ? p : q; }
+  __device__ __forceinline__ void apply(long long i, T rc, T ar, const T* vin, double* acc) const {
     T pc, qc;
     if (sc->first) {
       pc = rc;
       qc = ar;
     } else {
       const T be = (T)sc->beta;
-      pc = fma(be, p[i], rc);
-      qc = fma(be, q[i], ar);
+      pc = fma(be, vin[0], rc);
+      qc = fma(be, vin[1], ar);
     }
     p[i] = pc;
     q[i] = qc;
@@ -285,6 +316,7 @@ struct EpiCgA {
 template <typename T, typename U = T, typename V = U>
 struct EpiResidual {
   static constexpr int K = 3;
+  static constexpr int NIN = 0;
   const U* rho;
   const U* u;
   const V* b;
@@ -294,7 +326,8 @@ struct EpiResidual {
   int max_it;
   int want_r;
   __device__ __forceinline__ bool skip() const { return false; }
-  __device__ __forceinline__ void apply(long long i, T, T lap, double* acc) const {
+  __device__ __forceinline__ const T* input(int) const { return nullptr; }
+  __device__ __forceinline__ void apply(long long i, T, T lap, const T*, double* acc) const {
     T uu = T(0);
     if (u) {
       const T ui = (T)u[i];
@@ -369,6 +402,7 @@ struct FuncScalars {
 template <typename T>
 struct EpiFunctional {
   static constexpr int K = 11;
+  static constexpr int NIN = 0;
   const T* phi;
   const T* b;
   const T* rcg;
@@ -381,7 +415,8 @@ struct EpiFunctional {
   FuncScalars f;
   double* out;  // 11 sums + C
   __device__ __forceinline__ bool skip() const { return false; }
-  __device__ __forceinline__ void apply(long long i, T uc, T lap, double* acc) const {
+  __device__ __forceinline__ const T* input(int) const { return nullptr; }
+  __device__ __forceinline__ void apply(long long i, T uc, T lap, const T*, double* acc) const {
     const double C = f.h3 * *sum_uu - f.N;
     const T mult = (T)(-f.eta + C * f.inv_mu);
     const bool tf = f.terms & 1, vw = f.terms & 2, xc = f.terms & 4, es = f.terms & 8;
@@ -441,12 +476,30 @@ __global__ void __launch_bounds__(256) cg_update_kernel(long long G, T* __restri
   __shared__ double smem[256 / 32];
   const T alpha = (T)sc->alpha;
   double acc[1] = {0.0};
-  for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < G; i += (long long)gridDim.x * 256) {
-    const T pi = p[i], api = Ap[i];
-    phi[i] = fma(alpha, pi, phi[i]);
-    const T ri = fma(-alpha, api, r[i]);
-    r[i] = ri;
-    acc[0] += (double)ri * (double)ri;
+  // four independent elements per thread and pass keep several loads in flight
+  const long long stride = (long long)gridDim.x * 1024;
+  for (long long i0 = (long long)blockIdx.x * 1024 + threadIdx.x; i0 < G; i0 += stride) {
+    T pv[4], av[4], xv[4], rv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const long long i = i0 + 256 * u;
+      if (i < G) {
+        pv[u] = p[i];
+        av[u] = Ap[i];
+        xv[u] = phi[i];
+        rv[u] = r[i];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const long long i = i0 + 256 * u;
+      if (i < G) {
+        phi[i] = fma(alpha, pv[u], xv[u]);
+        const T ri = fma(-alpha, av[u], rv[u]);
+        r[i] = ri;
+        acc[0] += (double)ri * (double)ri;
+      }
+    }
   }
   struct Fin {
     CgScalars* sc;

@@ -11,6 +11,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import weakref
 
 import numpy as np
 
@@ -218,9 +219,12 @@ class Context:
         if rc != OK:
             raise OfdftError(rc, "ofdft_create failed")
         self.h = h
+        self._batches = weakref.WeakSet()
 
     def close(self):
         if self.h:
+            for bt in list(self._batches):  # a batch must not outlive its context
+                bt.close()
             self._lib.ofdft_destroy(self.h)
             self.h = None
 
@@ -321,10 +325,12 @@ class Batch:
         ctx._check(ctx._lib.ofdft_batch_create(ctx.h, precision, int(hbm_budget_bytes), C.byref(self.h)),
                    "ofdft_batch_create")
         self.M = {}
+        ctx._batches.add(self)
 
     def close(self):
         if self.h:
-            self.ctx._lib.ofdft_batch_destroy(self.h)
+            if self.ctx.h:  # the context frees the batch's device memory only through it
+                self.ctx._lib.ofdft_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):
