@@ -287,6 +287,25 @@ int ofdft_batch_run(ofdft_batch* b);
 /* Device bytes one batched solve of grid g holds while admitted. */
 long long ofdft_batch_bytes(const ofdft_grid* g, int prec);
 
+/* Allocation-free variant of ofdft_poisson (FP64), for callers that cannot
+ * allocate device memory: an application whose framework owns every device
+ * allocation, or code that must not call cudaMalloc on a latency-critical path.
+ * The paper has no counterpart; this is an interface of this library only.
+ * It needs no context.  Its CG vectors, reduction scratch and CG scalars live
+ * in one file-scope device array of about 6.1 MB that every GPU which loads the
+ * library holds until the process exits, so it accepts grids of at most
+ * 262144 nodes (64^3) and returns OFDFT_EINVAL beyond that.  The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress), so make
+ * that first call before any stream capture.  All calls share the array and
+ * it keeps the last call's contents (the reduction counter is cleared at the
+ * start of each call): calls that overlap on the GPU, on any stream or from any
+ * thread, race and must be serialised by the caller.  rho, phi: device arrays
+ * (double) of the grid's node count; phi in: guess, out: solution of
+ * (-L_h) phi = 4 pi rho with zero Dirichlet values, as ofdft_poisson.  Work is
+ * enqueued on cuda_stream and the call synchronises it. */
+int ofdft_poisson_noalloc(const ofdft_grid* g, int fd_order, const double* rho, double* phi,
+                          double tol, int max_it, void* cuda_stream, ofdft_cg_stats* st);
+
 /* Device bytes a solve of this grid needs in the context workspace (for
  * admission control by callers that pack several solves on one device). */
 long long ofdft_workspace_bytes(const ofdft_grid* g, int fd_order, int prec);

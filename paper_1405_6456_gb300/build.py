@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libofdft.so")
-SOURCES = ["api.cu", "engine.cu"]
+SOURCES = ["api.cu", "engine.cu", "noalloc.cu"]
 HEADERS = ["common.cuh", "kernels.cuh", "host.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

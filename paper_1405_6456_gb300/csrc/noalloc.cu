@@ -1,0 +1,144 @@
+// ofdft_poisson_noalloc: the FP64 Poisson CG of ofdft_poisson for callers that
+// cannot allocate device memory (a framework that owns every allocation of the
+// process, code that must not call cudaMalloc on a latency-critical path).  It
+// needs no context: its CG vectors, reduction scratch and CG scalars live in
+// one file-scope device array of fixed size, so no call allocates anything.
+#include "host.cuh"
+
+#include <mutex>
+
+namespace {
+
+using namespace ofd;
+
+// Largest grid the array holds: 64^3 nodes (three FP64 CG vectors of 2 MiB).
+constexpr long long kMaxPoints = 64LL * 64 * 64;
+constexpr long long kPartialsBytes = 64 * 1024;  // per-block partial sums of the reductions
+constexpr long long kVecBytes = kMaxPoints * (long long)sizeof(double);
+constexpr long long kScratchBytes = 3 * kVecBytes + kPartialsBytes + 256 + 256;
+
+// One array per device that loads the library, held until the process exits.
+// In host code this name is only a host-side stand-in: kernels get the device
+// address that cudaGetSymbolAddress returns.
+static __device__ __align__(256) unsigned char noalloc_scratch[kScratchBytes];
+
+std::mutex g_mutex;
+void* g_addr[256] = {nullptr};
+
+int fail_na(const char* msg) {
+  fprintf(stderr, "[ofdft_poisson_noalloc] %s\n", msg);
+  return OFDFT_EINVAL;
+}
+
+// Device address of the array on the current device (set up once per device).
+int scratch_address(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return OFDFT_ECUDA;
+  std::lock_guard<std::mutex> lock(g_mutex);
+  if (!g_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, noalloc_scratch);
+    if (e != cudaSuccess || !p) return OFDFT_ECUDA;
+    g_addr[dev] = p;
+  }
+  *out = g_addr[dev];
+  return OFDFT_OK;
+}
+
+template <int R>
+cudaError_t launch_stencil_pass(dim3 grid, int zchunk, const GridDev& g, const Weights<double>& W,
+                                const double* f, EpiResidual<double> ep, RedBuf red, cudaStream_t s) {
+  constexpr int smem = zsmem_bytes<double, R, EpiResidual<double>>();
+  cudaFuncSetAttribute(zstream_kernel<double, R, LoadPlain<double>, EpiResidual<double>>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  zstream_kernel<double, R, LoadPlain<double>, EpiResidual<double>>
+      <<<grid, dim3(BX, BY), smem, s>>>(g, W, zchunk, LoadPlain<double>{f}, ep, red);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" int ofdft_poisson_noalloc(const ofdft_grid* gr, int fd_order, const double* rho, double* phi,
+                                     double tol, int max_it, void* cuda_stream, ofdft_cg_stats* st) {
+  if (!gr || !rho || !phi) return fail_na("null grid, rho or phi");
+  for (int d = 0; d < 3; ++d)
+    if (gr->n[d] < 1) return fail_na("grid dimensions must be positive");
+  const long long G = (long long)gr->n[0] * gr->n[1] * gr->n[2];
+  if (G > kMaxPoints) return fail_na("grid exceeds the fixed scratch (at most 262144 = 64^3 nodes)");
+  if (fd_order < 2 || fd_order > 2 * kMaxR || (fd_order & 1)) return fail_na("fd_order must be even in [2, 12]");
+  if (!(tol > 0.0) || max_it < 0 || !(gr->h > 0.0)) return fail_na("need tol > 0, max_it >= 0, h > 0");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  void* base = nullptr;
+  int rc = scratch_address(&base);
+  if (rc != OFDFT_OK) return rc;
+  char* p = static_cast<char*>(base);
+  double* r = reinterpret_cast<double*>(p);
+  double* pv = reinterpret_cast<double*>(p + kVecBytes);
+  double* qv = reinterpret_cast<double*>(p + 2 * kVecBytes);
+  double* partials = reinterpret_cast<double*>(p + 3 * kVecBytes);
+  unsigned int* counter = reinterpret_cast<unsigned int*>(p + 3 * kVecBytes + kPartialsBytes);
+  CgScalars* sc = reinterpret_cast<CgScalars*>(p + 3 * kVecBytes + kPartialsBytes + 256);
+  // the array keeps the previous call's contents: the reduction counter must start at zero
+  if (cudaMemsetAsync(counter, 0, sizeof(unsigned int), s) != cudaSuccess) return OFDFT_ECUDA;
+  const RedBuf red{partials, counter};
+  const GridDev g{gr->n[0], gr->n[1], gr->n[2], G};
+  const int R = fd_order / 2;
+  const Weights<double> W = lap_weights(R, gr->h, 1.0), Wneg = lap_weights(R, gr->h, -1.0);
+  // launch shape of the library's single-grid passes (152 SMs assumed for the split)
+  const int gx = (g.n1 + BX - 1) / BX, gy = (g.n2 + BY - 1) / BY;
+  int nz = std::max(1, (608 + gx * gy - 1) / (gx * gy));
+  nz = std::min(nz, std::max(1, g.n3 / std::max(2 * R, 4)));
+  const int zc = (g.n3 + nz - 1) / nz;
+  nz = (g.n3 + zc - 1) / zc;
+  const dim3 zgrid(gx, gy, nz);
+  if ((long long)gx * gy * nz * 3 * 8 > kPartialsBytes) return fail_na("launch needs more partial sums than fit");
+  const int pb = (int)std::min<long long>(std::max<long long>(1, (G + 255) / 256), 1024);
+  cudaError_t e = cudaSuccess;
+  // r = 4 pi rho + L phi, CG scalars initialised by the last block
+  EpiResidual<double> res{rho, nullptr, nullptr, r, sc, tol, max_it, 1};
+  switch (R) {
+    case 1: e = launch_stencil_pass<1>(zgrid, zc, g, W, phi, res, red, s); break;
+    case 2: e = launch_stencil_pass<2>(zgrid, zc, g, W, phi, res, red, s); break;
+    case 3: e = launch_stencil_pass<3>(zgrid, zc, g, W, phi, res, red, s); break;
+    case 4: e = launch_stencil_pass<4>(zgrid, zc, g, W, phi, res, red, s); break;
+    case 5: e = launch_stencil_pass<5>(zgrid, zc, g, W, phi, res, red, s); break;
+    case 6: e = launch_stencil_pass<6>(zgrid, zc, g, W, phi, res, red, s); break;
+  }
+  if (e != cudaSuccess) return OFDFT_ECUDA;
+  CgScalars hs;
+  int launched = 0;
+  for (;;) {
+    if (cudaMemcpyAsync(&hs, sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s) != cudaSuccess) return OFDFT_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return OFDFT_ECUDA;
+    if (hs.done || launched >= max_it) break;
+    for (int i = 0; i < 8 && launched < max_it; ++i, ++launched) {
+      switch (R) {
+#define NA_CG(RR)                                                                                                \
+  case RR: {                                                                                                     \
+    constexpr int smem = zsmem_bytes<double, RR, EpiCgA<double>>();                                                              \
+    cudaFuncSetAttribute(zstream_kernel<double, RR, LoadPlain<double>, EpiCgA<double>>,                        \
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);                                     \
+    zstream_kernel<double, RR, LoadPlain<double>, EpiCgA<double>>                                                \
+        <<<zgrid, dim3(BX, BY), smem, s>>>(g, cast_weights<double>(Wneg), zc, LoadPlain<double>{r},             \
+                                          EpiCgA<double>{pv, qv, sc}, red);                                      \
+  } break;
+        NA_CG(1)
+        NA_CG(2)
+        NA_CG(3)
+        NA_CG(4)
+        NA_CG(5)
+        NA_CG(6)
+#undef NA_CG
+      }
+      cg_update_kernel<double><<<pb, 256, 0, s>>>(G, phi, r, pv, qv, sc, red);
+      if (cudaGetLastError() != cudaSuccess) return OFDFT_ECUDA;
+    }
+  }
+  const double bb = hs.bb > 0 ? hs.bb : 1.0;
+  if (st) {
+    st->iterations = hs.iters;
+    st->rel_residual = sqrt(hs.rr / bb);
+  }
+  if (!isfinite(hs.rr)) return OFDFT_ENONFINITE;
+  return hs.rr <= tol * tol * bb ? OFDFT_OK : OFDFT_ENOTCONV;
+}
