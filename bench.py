@@ -368,6 +368,74 @@ def run_gpu(args):
     return 0
 
 
+# ------------------------------------------------------ batch / serving modes --
+def run_batch(args):
+    """C4: count FCC cubes (m uniform in 1..5, h = 0.5, 12th order, 8 bohr vacuum,
+    48^3..112^3 grids) solved together by the batch engine (MIXED)."""
+    import torch
+    from paper_1405_6456_gb300 import build as B
+    from paper_1405_6456_gb300 import ofdft as F
+    from paper_1405_6456_gb300 import workloads as W
+    B.build()
+    ctx = F.Context(0)
+    cl = W.batch_c4(args.batch_count)
+    p = F.default_params(precision=F.PREC_MIXED, vacuum=8.0, round_to=16)
+    grids = [F.ofdft_grid_for_atoms(c.R, c.h, c.vacuum, 16) for c in cl]
+    out = {"metric": METRIC, "mode": "batch", "unit": UNIT, "requests": len(cl),
+           "grids": sorted({g.n[0] for g in grids}), "dtype": "f32+f64acc", "data": "synthetic"}
+    for rep in range(2):  # warm-up pass, then the timed pass
+        bt = F.Batch(ctx, F.PREC_MIXED, 200 << 30)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ids = [bt.submit(c.R, c.Z, c.h, p) for c in cl]
+        done_t = {}
+        rounds = 0
+        while len(done_t) < len(ids):
+            bt.step()
+            rounds += 1
+            for rid in ids:
+                if rid not in done_t and bt.poll(rid, allow_notconv=True) is not None:
+                    done_t[rid] = time.perf_counter() - t0
+        wall = time.perf_counter() - t0
+        bt.close()
+    lat = np.array(sorted(done_t.values()))
+    out.update({"value": len(cl) / wall, "wall_s": wall, "rounds": rounds,
+                "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))}})
+    # the same requests one at a time through ofdft_solve (the plain form)
+    t0 = time.perf_counter()
+    for c in cl[: args.batch_solo]:
+        ctx.solve(c.R, c.Z, c.h, p, want_forces=True, allow_notconv=True)
+    solo = (time.perf_counter() - t0) / max(args.batch_solo, 1)
+    out["one_at_a_time"] = {"value": 1.0 / solo, "unit": UNIT, "sample": f"first {args.batch_solo} requests"}
+    ctx.close()
+    print(json.dumps(out))
+    return 0
+
+
+def run_serve(args):
+    """C5: Poisson arrivals of FCC cubes (m log-uniform in 1..8, h in {0.45, 0.5, 0.6},
+    order in {8, 12}, 8 bohr vacuum) served with continuous batching (MIXED)."""
+    from paper_1405_6456_gb300 import build as B
+    from paper_1405_6456_gb300 import ofdft as F
+    from paper_1405_6456_gb300 import serving as S
+    from paper_1405_6456_gb300 import workloads as W
+    B.build()
+    ctx = F.Context(0)
+    rates = [float(x) for x in args.rates.split(",")]
+    res = []
+    for rate in rates:
+        reqs = W.serving_requests_c5(rate, args.requests, max_m=args.max_m)
+        prm = lambda c: F.default_params(precision=F.PREC_MIXED, fd_order=c.fd_order, vacuum=c.vacuum, round_to=16)
+        rep = S.serve(ctx, reqs, prm, precision=F.PREC_MIXED, hbm_budget_bytes=args.hbm_gb << 30)
+        s = rep.summary()
+        s["rate_per_s"] = rate
+        res.append(s)
+    ctx.close()
+    print(json.dumps({"metric": METRIC, "mode": "serve", "unit": UNIT, "dtype": "f32+f64acc",
+                      "data": "synthetic", "max_m": args.max_m, "rates": res}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -379,9 +447,20 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--write-counts", action="store_true")
     ap.add_argument("--profile-timed", type=int, default=1)
+    ap.add_argument("--mode", default="solve", choices=["solve", "batch", "serve"])
+    ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--batch-solo", type=int, default=4)
+    ap.add_argument("--rates", default="1,5,20")
+    ap.add_argument("--requests", type=int, default=24)
+    ap.add_argument("--max-m", type=int, default=8)
+    ap.add_argument("--hbm-gb", type=int, default=200)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "batch":
+        return run_batch(args)
+    if args.mode == "serve":
+        return run_serve(args)
     return run_gpu(args)
 
 

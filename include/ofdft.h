@@ -130,7 +130,12 @@ void ofdft_default_params(ofdft_params* p);
 
 /* Creates a context on CUDA device `device` whose work goes to `cuda_stream`
  * (a cudaStream_t; NULL means the legacy default stream).  The context owns its
- * device workspaces; they grow on demand and are freed by ofdft_destroy. */
+ * device workspaces; they grow on demand and are freed by ofdft_destroy.
+ * The first Poisson solve on a new grid times a few launch shapes of the CG
+ * stencil pass and keeps the fastest for the context's lifetime (the shape sets
+ * the order of the reductions' partial sums, so two contexts may differ in the
+ * last bits); environment variable OFDFT_AUTOTUNE=0 at creation turns this off
+ * and keeps the fixed one-wave shape. */
 int ofdft_create(ofdft_ctx** ctx, int device, void* cuda_stream);
 int ofdft_destroy(ofdft_ctx* ctx);
 /* Message describing the last failure on ctx (never NULL; "" after success). */

@@ -12,13 +12,13 @@ namespace ofd {
 // Launches one CG iteration (S3): the stencil pass on r with the p/q update and
 // p.q, then the x/r update with r.r; both kernels read and write the CG scalars
 // on the device and return at once when the solve is done.
-template <typename T>
-int cg_step(ofdft_ctx* c, int R, const GridDev& g, const Weights<double>& Wneg, T* x, T* r, T* pv, T* qv,
+template <typename T, typename X>
+int cg_step(ofdft_ctx* c, int R, const GridDev& g, const Weights<double>& Wneg, X* x, T* r, T* pv, T* qv,
             CgScalars* sc, int pb) {
   TRY(launch_z_r<T>(c, R, g, Wneg, LoadPlain<T>{r}, EpiCgA<T>{pv, qv, sc}, OFDFT_K_CG_DIR_STENCIL));
   {
     ProfScope ps_(c, OFDFT_K_CG_UPDATE);
-    cg_update_kernel<T><<<pb, 256, 0, c->stream>>>(g.G, x, r, pv, qv, sc, red(c));
+    cg_update_kernel<T, X><<<pb, 256, 0, c->stream>>>(g.G, x, r, pv, qv, sc, red(c));
   }
   CU(cudaGetLastError());
   return OFDFT_OK;
@@ -26,12 +26,79 @@ int cg_step(ofdft_ctx* c, int R, const GridDev& g, const Weights<double>& Wneg, 
 
 constexpr int kChunk = 8;  // CG iterations between convergence polls
 
+// Autotuner (S11): picks the number of z chunks of the CG stencil pass for one
+// (kernel, grid) by timing candidate splits on scratch vectors (a private CG
+// scalar block keeps the solve's state untouched) and caches the choice in the
+// context.  The split changes the blocks' partial sums, so it is fixed before
+// the solve's first CG pass and the reduction order stays the same afterwards.
+template <typename T>
+int tune_cg_split(ofdft_ctx* c, int R, const GridDev& g, const Weights<double>& Wneg, const T* r) {
+  if (!c->autotune) return OFDFT_OK;
+  const std::vector<long long> key = ztune_key(zkernel_ptr<T, LoadPlain<T>, EpiCgA<T>>(R), g);
+  for (auto& t : c->ztune)
+    if (t.first == key) return OFDFT_OK;
+  const std::vector<int> cand = {0, 1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64};
+  TRY(ensure_partials(c, zshape(c, g, R, 1, 64).nblocks, 1));  // largest candidate
+  T* scratch = nullptr;
+  CU(cudaMalloc(&scratch, 2 * g.G * sizeof(T)));
+  CgScalars* sc = c->sc + 2;
+  CgScalars init;
+  memset(&init, 0, sizeof(init));
+  init.first = 1;
+  init.max_it = 1 << 30;
+  const int prof = c->prof;
+  const long long launches = c->launches;
+  long long kinds[OFDFT_K_COUNT];
+  memcpy(kinds, c->kind_launches, sizeof(kinds));
+  c->prof = 0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int best = 0, rc = OFDFT_OK;
+  float best_ms = 1e30f;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    rc = fail(c, OFDFT_ECUDA, "autotune: event creation failed");
+  for (int nz : cand) {
+    if (rc != OFDFT_OK || nz > g.n3) break;
+    c->ztune.push_back({key, nz});
+    float ms = 0.0f;
+    for (int rep = 0; rep < 4 && rc == OFDFT_OK; ++rep) {
+      if (cudaMemcpyAsync(sc, &init, sizeof(init), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+          cudaEventRecord(e0, c->stream) != cudaSuccess) {
+        rc = fail(c, OFDFT_ECUDA, "autotune: enqueue failed");
+        break;
+      }
+      rc = launch_z_r<T>(c, R, g, Wneg, LoadPlain<T>{r}, EpiCgA<T>{scratch, scratch + g.G, sc},
+                         OFDFT_K_CG_DIR_STENCIL);
+      float t = 0.0f;
+      if (rc == OFDFT_OK && (cudaEventRecord(e1, c->stream) != cudaSuccess ||
+                             cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess))
+        rc = fail(c, OFDFT_ECUDA, "autotune: timing failed");
+      if (rep > 0) ms += t;  // the first launch of each split warms up
+    }
+    c->ztune.pop_back();
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = nz;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamSynchronize(c->stream);
+  cudaFree(scratch);
+  c->prof = prof;
+  c->launches = launches;  // tuning launches are not part of the caller's work
+  memcpy(c->kind_launches, kinds, sizeof(kinds));
+  if (rc != OFDFT_OK) return rc;
+  c->ztune.push_back({key, best});
+  return OFDFT_OK;
+}
+
 // The graph of one chunk of CG iterations for this buffer set, captured on
 // first use (the launches bake in pointers, sizes and weights).
-template <typename T>
-int cg_graph(ofdft_ctx* c, int R, const GridDev& g, double h, const Weights<double>& Wneg, T* x, T* r, T* pv, T* qv,
+template <typename T, typename X>
+int cg_graph(ofdft_ctx* c, int R, const GridDev& g, double h, const Weights<double>& Wneg, X* x, T* r, T* pv, T* qv,
              CgScalars* sc, int pb, cudaGraphExec_t* out) {
-  const std::vector<long long> key = {(long long)sizeof(T), R, g.n1, g.n2, g.n3, (long long)x, (long long)r,
+  const std::vector<long long> key = {(long long)sizeof(T), (long long)sizeof(X), R, g.n1, g.n2, g.n3, (long long)x,
+                                      (long long)r,
                                       (long long)pv, (long long)qv, (long long)sc, pb,
                                       (long long)c->partials.p, (long long)(h * 1e12)};
   for (auto& e : c->graphs)
@@ -45,13 +112,19 @@ int cg_graph(ofdft_ctx* c, int R, const GridDev& g, double h, const Weights<doub
   const long long launches = c->launches;
   long long kinds[OFDFT_K_COUNT];
   memcpy(kinds, c->kind_launches, sizeof(kinds));
-  TRY(cg_step<T>(c, R, g, Wneg, x, r, pv, qv, sc, pb));  // sets kernel attributes outside capture
+  TRY((cg_step<T, X>(c, R, g, Wneg, x, r, pv, qv, sc, pb)));  // sets kernel attributes outside capture
   CU(cudaStreamSynchronize(c->stream));
+  // capture on the context's private stream (the caller's stream may be the
+  // legacy default stream, which cannot be captured); replay on the caller's
   cudaGraph_t graph = nullptr;
-  CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  cudaStream_t user = c->stream;
+  c->stream = c->gstream;
+  cudaError_t eb = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
   int rc = OFDFT_OK;
-  for (int i = 0; i < kChunk && rc == OFDFT_OK; ++i) rc = cg_step<T>(c, R, g, Wneg, x, r, pv, qv, sc, pb);
-  const cudaError_t ec = cudaStreamEndCapture(c->stream, &graph);
+  if (eb == cudaSuccess)
+    for (int i = 0; i < kChunk && rc == OFDFT_OK; ++i) rc = cg_step<T, X>(c, R, g, Wneg, x, r, pv, qv, sc, pb);
+  const cudaError_t ec = (eb == cudaSuccess) ? cudaStreamEndCapture(c->stream, &graph) : eb;
+  c->stream = user;
   c->prof = prof;
   c->launches = launches;
   memcpy(c->kind_launches, kinds, sizeof(kinds));
@@ -71,17 +144,18 @@ int cg_graph(ofdft_ctx* c, int R, const GridDev& g, double h, const Weights<doub
 // stream never drains; kernels of a converged solve return at once, so an extra
 // chunk costs only empty launches.  Without per-launch timing a chunk is one
 // CUDA graph launch.
-template <typename T>
-int cg_iterate(ofdft_ctx* c, int R, const GridDev& g, double h, const Weights<double>& Wneg, T* x, T* r,
+template <typename T, typename X = T>
+int cg_iterate(ofdft_ctx* c, int R, const GridDev& g, double h, const Weights<double>& Wneg, X* x, T* r,
                CgScalars* sc, int max_it, CgScalars* host_sc) {
   T* pv = vec<T>(c, V_P0);
   T* qv = vec<T>(c, V_AP);
   const int pb = pointwise_blocks(c, g.G);
   TRY(ensure_partials(c, pb, 1));
-  TRY(ensure_partials(c, zshape(c, g, R).nblocks, 1));
+  TRY(ensure_partials(c, zshape(c, g, R, 32).nblocks, 1));
+  TRY(tune_cg_split<T>(c, R, g, Wneg, r));
   const bool timed = (c->prof & ((1 << OFDFT_K_CG_DIR_STENCIL) | (1 << OFDFT_K_CG_UPDATE))) != 0;
   cudaGraphExec_t exec = nullptr;
-  if (c->use_graphs && !timed && max_it >= kChunk) TRY(cg_graph<T>(c, R, g, h, Wneg, x, r, pv, qv, sc, pb, &exec));
+  if (c->use_graphs && !timed && max_it >= kChunk) TRY((cg_graph<T, X>(c, R, g, h, Wneg, x, r, pv, qv, sc, pb, &exec)));
   int launched = 0, chunks = 0;
   while (launched < max_it) {
     if (exec && launched + kChunk <= max_it) {
@@ -92,7 +166,7 @@ int cg_iterate(ofdft_ctx* c, int R, const GridDev& g, double h, const Weights<do
       c->kind_launches[OFDFT_K_CG_UPDATE] += kChunk;
     } else {
       for (int i = 0; i < kChunk && launched < max_it; ++i, ++launched)
-        TRY(cg_step<T>(c, R, g, Wneg, x, r, pv, qv, sc, pb));
+        TRY((cg_step<T, X>(c, R, g, Wneg, x, r, pv, qv, sc, pb)));
     }
     const int slot = chunks & 1;
     CU(cudaMemcpyAsync(&c->ring[slot], sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, c->stream));
@@ -143,30 +217,40 @@ int poisson_fp64(ofdft_ctx* c, int R, const GridDev& g, double h, const double* 
   return OFDFT_OK;
 }
 
-// Mixed Poisson solve (S3 + S10): phi64 is the FP64 iterate; each round computes
-// the FP64 residual r64 = 4 pi (u^2 + b64) + L_h phi64 with the FP64 stencil,
-// then solves A e = r64 by FP32 CG (relative tolerance 1e-5 or refine_every
-// steps) and sets phi64 += e, phi32 = (float) phi64.  Ends when the FP64
-// residual meets tol.  rho32 (optional) replaces u^2 + b.
+// Mixed Poisson solve (S3 + S10): FP32 CG with residual replacement.  The
+// potential phi64 stays FP64; r, p, q = A p and the correction e of the current
+// round are FP32.  Each round folds e into phi64 and computes the FP64 true
+// residual r64 = 4 pi (u^2 + b64) + L_h phi64 with the FP64 stencil; the solve
+// ends when it meets tol.  Otherwise r64 replaces the FP32 residual (the search
+// direction is kept after the first round, so no Krylov information is lost)
+// and FP32 iterations run until the FP32 residual falls by 1e-4 or refine_every
+// steps.  At the end phi32 = (float) phi64.  rho32 (optional) replaces u^2 + b.
 int poisson_mixed(ofdft_ctx* c, int R, const GridDev& g, double h, const float* rho32, const float* u,
-                  const double* b64, double* phi64, float* phi32, double tol, int max_it,
-                  int refine_every, ofdft_cg_stats* st) {
+                  const double* b64, double* phi64, float* phi32, double tol, int max_it, int refine_every,
+                  ofdft_cg_stats* st) {
   TRY(ensure_cg_vectors(c, g.G, sizeof(float), true));
   const Weights<double> W = lap_weights(R, h, 1.0), Wneg = lap_weights(R, h, -1.0);
   double* r64 = vec<double>(c, V_R64);
   float* r32 = vec<float>(c, V_R);
   float* e32 = vec<float>(c, V_E32);
   const int pb = pointwise_blocks(c, g.G);
-  int total = 0;
+  int total = 0, rc = OFDFT_OK;
   CgScalars hs, hs32;
-  const int max_rounds = 40;
+  const int max_rounds = 60;
+  CU(cudaMemsetAsync(e32, 0, g.G * sizeof(float), c->stream));
   for (int round = 0; round <= max_rounds; ++round) {
+    if (round > 0) {
+      ProfScope ps_(c, OFDFT_K_VECTOR);
+      fold_kernel<<<pb, 256, 0, c->stream>>>(g.G, phi64, e32);
+    }
     if (rho32)
       TRY(launch_z_r<double>(c, R, g, W, LoadPlain<double>{phi64},
-                             EpiResidual<double, float, double>{rho32, nullptr, nullptr, r64, c->sc, tol, max_it, 1}, OFDFT_K_RESIDUAL));
+                             EpiResidual<double, float, double>{rho32, nullptr, nullptr, r64, c->sc, tol, max_it, 1},
+                             OFDFT_K_RESIDUAL));
     else
       TRY(launch_z_r<double>(c, R, g, W, LoadPlain<double>{phi64},
-                             EpiResidual<double, float, double>{nullptr, u, b64, r64, c->sc, tol, max_it, 1}, OFDFT_K_RESIDUAL));
+                             EpiResidual<double, float, double>{nullptr, u, b64, r64, c->sc, tol, max_it, 1},
+                             OFDFT_K_RESIDUAL));
     TRY(sync_scalars(c, c->sc, sizeof(CgScalars), &hs));
     const double bb = hs.bb > 0 ? hs.bb : 1.0;
     if (st) {
@@ -174,26 +258,32 @@ int poisson_mixed(ofdft_ctx* c, int R, const GridDev& g, double h, const float* 
       st->rel_residual = sqrt(hs.rr / bb);
     }
     if (!isfinite(hs.rr)) return fail(c, OFDFT_ENONFINITE, "Poisson residual is not finite");
-    if (hs.rr <= tol * tol * bb) return OFDFT_OK;
-    if (total >= max_it || round == max_rounds)
-      return fail(c, OFDFT_ENOTCONV, "mixed Poisson reached %d FP32 iterations at relative residual %.3e", total,
-                  sqrt(hs.rr / bb));
+    if (hs.rr <= tol * tol * bb) break;
+    if (total >= max_it || round == max_rounds) {
+      rc = fail(c, OFDFT_ENOTCONV, "mixed Poisson reached %d FP32 iterations at relative residual %.3e", total,
+                sqrt(hs.rr / bb));
+      break;
+    }
     const int budget = std::min(refine_every, max_it - total);
     TRY(ensure_partials(c, pb, 1));
     {
       ProfScope ps_(c, OFDFT_K_VECTOR);
-      refine_init_kernel<<<pb, 256, 0, c->stream>>>(g.G, r32, e32, r64, c->sc32, 1e-5, budget, red(c));
+      refine_replace_kernel<<<pb, 256, 0, c->stream>>>(g.G, r32, r64, c->sc32, 1e-4, budget, round == 0 ? 1 : 0,
+                                                       red(c));
     }
     CU(cudaGetLastError());
-    TRY(cg_iterate<float>(c, R, g, h, Wneg, e32, r32, c->sc32, budget, &hs32));
-    total += std::max(hs32.iters, 1);
-    {
-      ProfScope ps_(c, OFDFT_K_VECTOR);
-      refine_apply_kernel<<<pb, 256, 0, c->stream>>>(g.G, phi64, phi32, e32);
-    }
-    CU(cudaGetLastError());
+    TRY(sync_scalars(c, c->sc32, sizeof(CgScalars), &hs32));
+    const int before = hs32.iters;
+    if (!hs32.done) TRY((cg_iterate<float, float>(c, R, g, h, Wneg, e32, r32, c->sc32, budget, &hs32)));
+    total += std::max(hs32.iters - before, 1);
   }
-  return OFDFT_OK;
+  {
+    ProfScope ps_(c, OFDFT_K_VECTOR);
+    convert_kernel<double, float><<<pb, 256, 0, c->stream>>>(g.G, phi32, phi64);
+  }
+  CU(cudaGetLastError());
+  if (st) st->iterations = total;
+  return rc;
 }
 
 // ------------------------------------------------------ functional (S4) ---
@@ -769,7 +859,7 @@ void ofdft_default_params(ofdft_params* p) {
   p->guess_cut = 8.0;
   p->tol_E = 1e-6;
   p->tol_inner = 1e-8;
-  p->tol_poisson = 1e-10;
+  p->tol_poisson = 1e-8;
   p->max_outer = 30;
   p->max_nlcg = 2000;
   p->max_cg = 20000;
@@ -800,7 +890,7 @@ int ofdft_create(ofdft_ctx** out, int device, void* stream) {
   }
   cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
   if (cudaMalloc(&c->counter, 64) != cudaSuccess || cudaMemset(c->counter, 0, 64) != cudaSuccess ||
-      cudaMalloc(&c->sc, 2 * sizeof(CgScalars)) != cudaSuccess ||
+      cudaMalloc(&c->sc, 3 * sizeof(CgScalars)) != cudaSuccess ||
       cudaMalloc(&c->scal, 64 * sizeof(double)) != cudaSuccess ||
       cudaMallocHost(&c->host_scal, 64 * sizeof(double)) != cudaSuccess ||
       cudaMallocHost(&c->ring, 2 * sizeof(CgScalars)) != cudaSuccess ||
@@ -810,7 +900,10 @@ int ofdft_create(ofdft_ctx** out, int device, void* stream) {
     return OFDFT_ENOMEM;
   }
   c->sc32 = c->sc + 1;
-  cudaMemset(c->sc, 0, 2 * sizeof(CgScalars));
+  if (cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking) != cudaSuccess) c->use_graphs = 0;
+  const char* at = getenv("OFDFT_AUTOTUNE");
+  c->autotune = !(at && at[0] == '0');
+  cudaMemset(c->sc, 0, 3 * sizeof(CgScalars));
   cudaMemset(c->scal, 0, 64 * sizeof(double));
   cudaDeviceSynchronize();
   *out = c;
@@ -824,6 +917,7 @@ int ofdft_destroy(ofdft_ctx* c) {
   cudaDeviceSynchronize();
   harvest(c);
   for (auto& e : c->graphs) cudaGraphExecDestroy(e.exec);
+  if (c->gstream) cudaStreamDestroy(c->gstream);
   for (cudaEvent_t e : c->free_events) cudaEventDestroy(e);
   cudaFree(c->partials.p);
   for (auto& b : c->v) cudaFree(b.p);

@@ -34,6 +34,34 @@ struct RedBuf {
   unsigned int* counter;
 };
 
+// Per-thread accumulator of a dot product.  FP64 fields accumulate with FP64
+// FMAs.  FP32 fields accumulate as an unevaluated pair hi + lo of floats with
+// error-free transformations (the product's rounding error from an FMA, the
+// sum's from TwoSum), so the per-thread partial carries FP64-level accuracy
+// without any FP64 instruction per element (FP64 issues at 1/64 of the FP32
+// rate on this GPU); the pair is converted to FP64 once, for the cross-thread
+// FP64 reduction.
+template <typename T>
+struct DotAcc {
+  double s = 0.0;
+  __device__ __forceinline__ void add(T a, T b) { s = fma((double)a, (double)b, s); }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct DotAcc<float> {
+  float hi = 0.0f, lo = 0.0f;
+  __device__ __forceinline__ void add(float a, float b) {
+    const float p = a * b;
+    const float pe = fmaf(a, b, -p);  // exact rounding error of the product
+    const float t = hi + p;           // TwoSum(hi, p)
+    const float bp = t - hi;
+    const float se = (hi - (t - bp)) + (p - bp);
+    hi = t;
+    lo += se + pe;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 // Sum K per-thread doubles over the block; the result is valid in thread 0.
 // NT is the block size (a multiple of 32); smem holds K * NT/32 doubles.
 template <int K, int NT>

@@ -17,6 +17,7 @@
 #include <deque>
 #include <functional>
 #include <memory>
+#include <type_traits>
 
 namespace ofd {
 namespace {
@@ -321,8 +322,9 @@ struct Engine {
         TRY((zpass<T, LoadPlain<T>, EpiCgA<T>>(slots, OFDFT_K_CG_DIR_STENCIL, -1.0, [&](Slot<T>* S) {
           return std::make_pair(LoadPlain<T>{getr(S)}, EpiCgA<T>{S->pv, S->qv, getsc(S)});
         })));
-        TRY((ppass<OpCgUpdate<T>>(slots, OFDFT_K_CG_UPDATE, [&](Slot<T>* S, int nb) {
-          return OpCgUpdate<T>{getx(S), getr(S), S->pv, S->qv, getsc(S), slot_red(S), nb};
+        using X = std::remove_pointer_t<decltype(getx(slots[0]))>;
+        TRY((ppass<OpCgUpdate<T, X>>(slots, OFDFT_K_CG_UPDATE, [&](Slot<T>* S, int nb) {
+          return OpCgUpdate<T, X>{getx(S), getr(S), S->pv, S->qv, getsc(S), slot_red(S), nb};
         })));
       }
       TRY(read_scalars());
@@ -356,13 +358,16 @@ struct Engine {
       }
       return OFDFT_OK;
     }
-    // mixed: FP64 residual rounds around FP32 correction solves (per slot)
+    // mixed: FP32 CG with residual replacement (per slot), as poisson_mixed
     for (Slot<T>* S : ev) {
-      S->pphase = 0;
       S->ptotal = 0;
+      S->pphase = 1;  // 1: the next replacement restarts the FP32 CG
     }
     std::vector<Slot<T>*> resid = ev;
-    for (int round = 0; round < 40 && !resid.empty(); ++round) {
+    for (Slot<T>* S : ev) CU(cudaMemsetAsync(S->e32, 0, S->g.G * sizeof(float), c->stream));
+    for (int round = 0; round <= 60 && !resid.empty(); ++round) {
+      if (round > 0)
+        TRY((ppass<OpFold>(resid, OFDFT_K_VECTOR, [&](Slot<T>* S, int) { return OpFold{S->phi64, S->e32}; })));
       TRY((zpass<double, LoadPlain<double>, EpiResidual<double, float, double>>(
           resid, OFDFT_K_RESIDUAL, 1.0, [&](Slot<T>* S) {
             return std::make_pair(LoadPlain<double>{S->phi64},
@@ -381,25 +386,29 @@ struct Engine {
         corr.push_back(S);
       }
       if (corr.empty()) break;
-      TRY((ppass<OpRefineInit>(corr, OFDFT_K_VECTOR, [&](Slot<T>* S, int nb) {
+      TRY((ppass<OpRefineReplace>(corr, OFDFT_K_VECTOR, [&](Slot<T>* S, int nb) {
         const int budget = std::min(std::max(S->p.refine_every, 1), S->p.max_cg - S->ptotal);
-        return OpRefineInit{(float*)S->r, S->e32, S->r64, B->sc32 + S->index, 1e-5, budget, slot_red(S), nb};
+        return OpRefineReplace{(float*)S->r, S->r64, B->sc32 + S->index, 1e-4, budget, S->pphase, slot_red(S), nb};
       })));
       TRY(read_scalars());
+      std::vector<int> before(B->capacity, 0);
       std::vector<Slot<T>*> run;
-      for (Slot<T>* S : corr)
+      for (Slot<T>* S : corr) {
+        S->pphase = 0;
+        before[S->index] = B->h_sc32[S->index].iters;
         if (!B->h_sc32[S->index].done) run.push_back(S);
+      }
       TRY(cg_loop(
           run, [](Slot<T>* S) { return (T*)S->e32; }, [](Slot<T>* S) { return S->r; },
           [&](Slot<T>* S) { return B->sc32 + S->index; },
           [&](Slot<T>* S) -> CgScalars& { return B->h_sc32[S->index]; }));
-      for (Slot<T>* S : corr) S->ptotal += std::max(B->h_sc32[S->index].iters, 1);
-      TRY((ppass<OpRefineApply>(corr, OFDFT_K_VECTOR, [&](Slot<T>* S, int) {
-        return OpRefineApply{S->phi64, (float*)S->phi, S->e32};
-      })));
+      for (Slot<T>* S : corr) S->ptotal += std::max(B->h_sc32[S->index].iters - before[S->index], 1);
       resid.swap(corr);
     }
-    // FP32 copy of the FP64 residual for the phi.r energy term
+    // FP32 potential for the functional and FP32 copy of the FP64 residual (phi.r term)
+    TRY((ppass<OpConvert<double, float>>(ev, OFDFT_K_VECTOR, [&](Slot<T>* S, int) {
+      return OpConvert<double, float>{(float*)S->phi, S->phi64};
+    })));
     TRY((ppass<OpConvert<double, float>>(ev, OFDFT_K_VECTOR, [&](Slot<T>* S, int) {
       return OpConvert<double, float>{(float*)S->r, S->r64};
     })));

@@ -62,6 +62,10 @@ struct ofdft_ctx {
   };
   std::vector<GraphEntry> graphs;
   int use_graphs = 1;
+  cudaStream_t gstream = nullptr;  // private stream used only to capture graphs
+  // autotuned z-splits of the z-streaming passes: key -> number of z chunks
+  std::vector<std::pair<std::vector<long long>, int>> ztune;
+  int autotune = 1;
 };
 
 namespace ofd {
@@ -250,21 +254,24 @@ inline int pointwise_blocks(ofdft_ctx* c, long long G) {
   return (int)std::max<long long>(1, std::min<long long>(b, (long long)c->sms * 4));
 }
 
-// z-streaming launch shape: BX x BY columns, z split so that the grid holds
-// about four blocks per SM, each z-chunk at least 2R planes deep.
+// z-streaming launch shape: BX x BY columns; z split so that the grid fills
+// the resident block slots (SMs x blocks per SM) in whole waves: a grid just
+// above a wave would leave a nearly empty second wave.  z-chunks are at least
+// 2R planes deep unless the grid is too small to fill the GPU at all.
 struct ZShape {
   dim3 grid;
   int zchunk;
   long long nblocks;
 };
 
-inline ZShape zshape(ofdft_ctx* c, const GridDev& g, int R) {
+inline ZShape zshape(ofdft_ctx* c, const GridDev& g, int R, int blocks_per_sm = 4, int force_nz = 0) {
   ZShape s;
   const int gx = (g.n1 + BX - 1) / BX, gy = (g.n2 + BY - 1) / BY;
   const long long tiles = (long long)gx * gy;
-  const long long want = (long long)c->sms * 4;
-  int nz = (int)std::max<long long>(1, (want + tiles - 1) / tiles);
+  const long long slots = (long long)c->sms * std::max(blocks_per_sm, 1);
+  int nz = (int)std::max<long long>(1, slots / tiles);  // one wave when tiles <= slots
   nz = std::min(nz, std::max(1, g.n3 / std::max(2 * R, 4)));
+  if (force_nz > 0) nz = std::min(force_nz, g.n3);
   int zc = (g.n3 + nz - 1) / nz;
   nz = (g.n3 + zc - 1) / zc;
   s.grid = dim3(gx, gy, nz);
@@ -273,16 +280,44 @@ inline ZShape zshape(ofdft_ctx* c, const GridDev& g, int R) {
   return s;
 }
 
+// Key of an autotuned z-split: the kernel instantiation and the grid.
+inline std::vector<long long> ztune_key(const void* fn, const GridDev& g) {
+  return {(long long)(uintptr_t)fn, g.n1, g.n2, g.n3};
+}
+
+template <typename T, class L, class E>
+const void* zkernel_ptr(int R) {
+  switch (R) {
+    case 1: return (const void*)zstream_kernel<T, 1, L, E>;
+    case 2: return (const void*)zstream_kernel<T, 2, L, E>;
+    case 3: return (const void*)zstream_kernel<T, 3, L, E>;
+    case 4: return (const void*)zstream_kernel<T, 4, L, E>;
+    case 5: return (const void*)zstream_kernel<T, 5, L, E>;
+    default: return (const void*)zstream_kernel<T, 6, L, E>;
+  }
+}
+
 template <typename T, int R, class L, class E>
 int launch_z(ofdft_ctx* c, const GridDev& g, const Weights<double>& W, L ld, E ep, int kind) {
-  const ZShape s = zshape(c, g, R);
-  if (E::K > 0) TRY(ensure_partials(c, s.nblocks, E::K));
   constexpr int smem = zsmem_bytes<T, R, E>();
-  static bool attr = false;  // dynamic shared memory above 48 KB needs an opt-in per kernel
-  if (!attr) {
+  static int per_sm = 0;  // resident blocks per SM of this kernel (dynamic smem above 48 KB needs an opt-in)
+  if (!per_sm) {
     CU(cudaFuncSetAttribute(zstream_kernel<T, R, L, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    attr = true;
+    int nb = 0;
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, zstream_kernel<T, R, L, E>, NT, smem));
+    per_sm = std::max(nb, 1);
   }
+  int nz = 0;
+  if (!c->ztune.empty()) {
+    const std::vector<long long> key = ztune_key((const void*)zstream_kernel<T, R, L, E>, g);
+    for (auto& t : c->ztune)
+      if (t.first == key) {
+        nz = t.second;
+        break;
+      }
+  }
+  const ZShape s = zshape(c, g, R, per_sm, nz);
+  if (E::K > 0) TRY(ensure_partials(c, s.nblocks, E::K));
   {
     ProfScope ps_(c, kind);
     zstream_kernel<T, R, L, E><<<s.grid, dim3(BX, BY), smem, c->stream>>>(g, cast_weights<T>(W), s.zchunk, ld, ep,

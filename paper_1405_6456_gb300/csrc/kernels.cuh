@@ -25,7 +25,8 @@ struct CgScalars {
   double beta;    // rr_new / rr
   double tol2;    // tol^2 (relative, squared)
   double sum_uu;  // sum u^2 (from the residual pass, for C_h)
-  double rr0;     // rr at the start of the solve
+  double rr0;     // rr at the start of the solve (or at the last residual replacement)
+  double rr_prev; // r.r of the previous iteration (beta after a residual replacement)
   int iters;      // CG iterations done
   int max_it;
   int done;       // 1 once converged or out of iterations
@@ -47,6 +48,11 @@ struct CgScalars {
 // Epi:    static constexpr int K (number of FP64 partial sums), bool skip(),
 //         void apply(idx, centre, lap, acc[K]), and fin(sums[K]) run once by
 //         the last block.
+// Epilogue accumulators: plain doubles, or DotAcc (compensated for FP32).
+__device__ __forceinline__ double to_double(double v) { return v; }
+template <typename T>
+__device__ __forceinline__ double to_double(const DotAcc<T>& a) { return a.value(); }
+
 // Asynchronous 4- or 8-byte global -> shared copy; src_valid == false fills the
 // destination with zeros (the zero Dirichlet value of every out-of-grid node) and
 // reads nothing.
@@ -116,22 +122,21 @@ __device__ __forceinline__ void zstream_tile(const GridDev& g, const Weights<T>&
   const long long il = (long long)g.n1 * y + xl, ir = (long long)g.n1 * y + xr;
   const long long ib = (long long)g.n1 * yb + x, it = (long long)g.n1 * yt + x;
 
-  // stage plane p into its ring slot (every thread commits one group per plane)
-  auto stage = [&](int p) {
-    const int sl = ((p % NS) + NS) % NS;
+  // stage plane p into ring slot sl and (for p - R inside the chunk) the
+  // epilogue inputs of plane p - R into input slot il_; one commit group per call
+  auto stage = [&](int p, int sl, int isl) {
     const bool pv = (p >= 0) && (p < g.n3);
-    const long long pb = plane * (long long)(pv ? p : 0);
-    cp_async_elem(&ring[sl][ty + R][tx + R], f + (pv && in_xy ? pb + col : 0), pv && in_xy);
+    const T* fp = f + plane * (long long)(pv ? p : 0);
+    cp_async_elem(&ring[sl][ty + R][tx + R], pv && in_xy ? fp + col : f, pv && in_xy);
     if (hx) {
-      cp_async_elem(&ring[sl][ty + R][tx], f + (pv && okl ? pb + il : 0), pv && okl);
-      cp_async_elem(&ring[sl][ty + R][tx + BX + R], f + (pv && okr ? pb + ir : 0), pv && okr);
+      cp_async_elem(&ring[sl][ty + R][tx], pv && okl ? fp + il : f, pv && okl);
+      cp_async_elem(&ring[sl][ty + R][tx + BX + R], pv && okr ? fp + ir : f, pv && okr);
     }
     if (hy) {
-      cp_async_elem(&ring[sl][ty][tx + R], f + (pv && okb ? pb + ib : 0), pv && okb);
-      cp_async_elem(&ring[sl][ty + BY + R][tx + R], f + (pv && okt ? pb + it : 0), pv && okt);
+      cp_async_elem(&ring[sl][ty][tx + R], pv && okb ? fp + ib : f, pv && okb);
+      cp_async_elem(&ring[sl][ty + BY + R][tx + R], pv && okt ? fp + it : f, pv && okt);
     }
     if constexpr (NIN > 0) {
-      // pointwise inputs of plane p - R, needed at the same step as stencil plane p
       const int pp = p - R;
       if (pp >= z0 && pp < z1) {
         const long long o = plane * (long long)pp + col;
@@ -139,7 +144,7 @@ __device__ __forceinline__ void zstream_tile(const GridDev& g, const Weights<T>&
         for (int j = 0; j < NIN; ++j) {
           const T* src = ep.input(j);
           const bool v = in_xy && src != nullptr;
-          cp_async_elem(&pin[pp % ZD][j][ty][tx], v ? src + o : f, v);
+          cp_async_elem(&pin[isl][j][ty][tx], v ? src + o : f, v);
         }
       }
     }
@@ -154,18 +159,28 @@ __device__ __forceinline__ void zstream_tile(const GridDev& g, const Weights<T>&
     const int k = z0 - R + i;
     q[i] = (in_xy && k >= 0 && k < g.n3) ? f[col + plane * k] : T(0);
   }
-  for (int p = z0; p < z0 + R + ZD - 1; ++p) stage(p);
+  // ring slots advance by one per plane (no integer division in the loop):
+  // stencil plane p lives in slot (p - z0) mod NS, input plane p in (p - z0) mod ZD
+  int s_stage = 0, i_stage = (ZD - R % ZD) % ZD;
+  auto bump = [](int v, int n) { return v + 1 == n ? 0 : v + 1; };
+  for (int p = z0; p < z0 + R + ZD - 1; ++p) {
+    stage(p, s_stage, i_stage);
+    s_stage = bump(s_stage, NS);
+    i_stage = bump(i_stage, ZD);
+  }
 
-  double acc[Epi::K > 0 ? Epi::K : 1];
+  typename Epi::Acc acc[Epi::K > 0 ? Epi::K : 1];
 #pragma unroll
-  for (int i = 0; i < (Epi::K > 0 ? Epi::K : 1); ++i) acc[i] = 0.0;
+  for (int i = 0; i < (Epi::K > 0 ? Epi::K : 1); ++i) acc[i] = typename Epi::Acc();
 
+  int sk = 0, sf = R % NS, ik = 0;  // slots of plane k, plane k + R, inputs of plane k
   for (int k = z0; k < z1; ++k) {
-    __syncthreads();         // every thread is done with plane k-1's slot
-    stage(k + R + ZD - 1);   // refills that slot
+    __syncthreads();                        // every thread is done with plane k-1's slot
+    stage(k + R + ZD - 1, s_stage, i_stage);  // refills that slot
+    s_stage = bump(s_stage, NS);
+    i_stage = bump(i_stage, ZD);
     cp_async_wait<ZD - 1>();  // planes <= k + R have landed (this thread's copies)
-    __syncthreads();         // ... and every other thread's
-    const int sk = k % NS, sf = (k + R) % NS;
+    __syncthreads();          // ... and every other thread's
     q[2 * R] = ring[sf][ty + R][tx + R];
     if (in_xy) {
       T lap = W.c * q[R];
@@ -178,16 +193,22 @@ __device__ __forceinline__ void zstream_tile(const GridDev& g, const Weights<T>&
       }
       T vin[NIN > 0 ? NIN : 1];
 #pragma unroll
-      for (int j = 0; j < NIN; ++j) vin[j] = pin[k % ZD][j][ty][tx];
+      for (int j = 0; j < NIN; ++j) vin[j] = pin[ik][j][ty][tx];
       ep.apply(col + plane * k, q[R], lap, vin, acc);
     }
 #pragma unroll
     for (int i = 0; i < 2 * R; ++i) q[i] = q[i + 1];
+    sk = bump(sk, NS);
+    sf = bump(sf, NS);
+    ik = bump(ik, ZD);
   }
   cp_async_wait<0>();
   if constexpr (Epi::K > 0) {
+    double accd[Epi::K];
+#pragma unroll
+    for (int i = 0; i < Epi::K; ++i) accd[i] = to_double(acc[i]);
     Epi fin = ep;
-    grid_sum<Epi::K, NT>(acc, red_smem, red, nblocks, bid, tid, fin);
+    grid_sum<Epi::K, NT>(accd, red_smem, red, nblocks, bid, tid, fin);
   }
 }
 
@@ -268,10 +289,11 @@ template <typename T>
 struct EpiStore {
   static constexpr int K = 0;
   static constexpr int NIN = 0;
+  using Acc = double;
   T* out;
   __device__ __forceinline__ bool skip() const { return false; }
   __device__ __forceinline__ const T* input(int) const { return nullptr; }
-  __device__ __forceinline__ void apply(long long i, T, T lap, const T*, double*) const { out[i] = lap; }
+  __device__ __forceinline__ void apply(long long i, T, T lap, const T*, Acc*) const { out[i] = lap; }
   __device__ __forceinline__ void operator()(double*) const {}
 };
 
@@ -284,12 +306,13 @@ template <typename T>
 struct EpiCgA {
   static constexpr int K = 1;
   static constexpr int NIN = 2;  // p_old, q_old at the node, staged by the pipeline
+  using Acc = DotAcc<T>;
   T* p;
   T* q;
   CgScalars* sc;
   __device__ __forceinline__ bool skip() const { return sc->done != 0; }
   __device__ __forceinline__ const T* input(int j) const { return j == 0 ? p : q; }
-  __device__ __forceinline__ void apply(long long i, T rc, T ar, const T* vin, double* acc) const {
+  __device__ __forceinline__ void apply(long long i, T rc, T ar, const T* vin, Acc* acc) const {
     T pc, qc;
     if (sc->first) {
       pc = rc;
@@ -301,7 +324,7 @@ struct EpiCgA {
     }
     p[i] = pc;
     q[i] = qc;
-    acc[0] += (double)pc * (double)qc;
+    acc[0].add(pc, qc);
   }
   __device__ __forceinline__ void operator()(double* t) const {
     sc->pAp = t[0];
@@ -317,6 +340,7 @@ template <typename T, typename U = T, typename V = U>
 struct EpiResidual {
   static constexpr int K = 3;
   static constexpr int NIN = 0;
+  using Acc = double;
   const U* rho;
   const U* u;
   const V* b;
@@ -403,6 +427,7 @@ template <typename T>
 struct EpiFunctional {
   static constexpr int K = 11;
   static constexpr int NIN = 0;
+  using Acc = double;
   const T* phi;
   const T* b;
   const T* rcg;
@@ -465,21 +490,24 @@ struct EpiFunctional {
 };
 
 // ------------------------------------------------------- CG second half ---
-// phi += alpha p, r -= alpha Ap, reduces r.r; the last block sets beta, counts
-// the iteration and raises `done` at convergence or at the iteration cap.
-template <typename T>
-__global__ void __launch_bounds__(256) cg_update_kernel(long long G, T* __restrict__ phi,
+// x += alpha p, r -= alpha q, reduces r.r; the last block sets beta, counts the
+// iteration and raises `done` at convergence or at the iteration cap.  X is the
+// iterate's type: T, or double for the mixed CG (FP32 r, p, q, FP64 iterate).
+template <typename T, typename X = T>
+__global__ void __launch_bounds__(256) cg_update_kernel(long long G, X* __restrict__ phi,
                                                         T* __restrict__ r, const T* __restrict__ p,
                                                         const T* __restrict__ Ap, CgScalars* sc,
                                                         RedBuf red) {
   if (sc->done) return;
   __shared__ double smem[256 / 32];
   const T alpha = (T)sc->alpha;
-  double acc[1] = {0.0};
+  const X alpha_x = (X)sc->alpha;
+  DotAcc<T> dacc;
   // four independent elements per thread and pass keep several loads in flight
   const long long stride = (long long)gridDim.x * 1024;
   for (long long i0 = (long long)blockIdx.x * 1024 + threadIdx.x; i0 < G; i0 += stride) {
-    T pv[4], av[4], xv[4], rv[4];
+    T pv[4], av[4], rv[4];
+    X xv[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const long long i = i0 + 256 * u;
@@ -494,24 +522,63 @@ __global__ void __launch_bounds__(256) cg_update_kernel(long long G, T* __restri
     for (int u = 0; u < 4; ++u) {
       const long long i = i0 + 256 * u;
       if (i < G) {
-        phi[i] = fma(alpha, pv[u], xv[u]);
+        phi[i] = fma(alpha_x, (X)pv[u], xv[u]);
         const T ri = fma(-alpha, av[u], rv[u]);
         r[i] = ri;
-        acc[0] += (double)ri * (double)ri;
+        dacc.add(ri, ri);
       }
     }
   }
+  double acc[1] = {dacc.value()};
   struct Fin {
     CgScalars* sc;
     __device__ void operator()(double* t) const {
       const double rr_new = t[0];
       sc->beta = (sc->rr != 0.0) ? rr_new / sc->rr : 0.0;
+      sc->rr_prev = sc->rr;
       sc->rr = rr_new;
       sc->iters += 1;
       const double thr = sc->tol2 * (sc->bb > 0.0 ? sc->bb : 1.0);
       if (rr_new <= thr || sc->iters >= sc->max_it || !(rr_new == rr_new)) sc->done = 1;
     }
   } fin{sc};
+  grid_sum<1, 256>(acc, smem, red, gridDim.x, blockIdx.x, threadIdx.x, fin);
+}
+
+// Residual replacement of the mixed CG: r32 = (float) r64 (the FP64 true
+// residual).  On the first round the CG starts from scratch (p = r); later
+// rounds keep the search direction and rescale beta to the replaced residual.
+// The FP32 iterations of a round stop when r.r falls by inner_tol^2.
+static __global__ void __launch_bounds__(256) refine_replace_kernel(long long G, float* r32, const double* r64,
+                                                                    CgScalars* sc, double inner_tol, int budget,
+                                                                    int restart, RedBuf red) {
+  __shared__ double smem[256 / 32];
+  double acc[1] = {0.0};
+  for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < G; i += (long long)gridDim.x * 256) {
+    const float v = (float)r64[i];
+    r32[i] = v;
+    acc[0] += (double)v * (double)v;
+  }
+  struct Fin {
+    CgScalars* sc;
+    double tol;
+    int budget, restart;
+    __device__ void operator()(double* t) const {
+      if (restart) {
+        sc->first = 1;
+        sc->beta = 0.0;
+        sc->iters = 0;
+      } else {
+        sc->beta = (sc->rr_prev != 0.0) ? t[0] / sc->rr_prev : 0.0;
+      }
+      sc->rr = t[0];
+      sc->rr0 = t[0];
+      sc->bb = t[0];
+      sc->tol2 = tol * tol;
+      sc->max_it = sc->iters + budget;
+      sc->done = (t[0] == 0.0 || budget <= 0) ? 1 : 0;
+    }
+  } fin{sc, inner_tol, budget, restart};
   grid_sum<1, 256>(acc, smem, red, gridDim.x, blockIdx.x, threadIdx.x, fin);
 }
 
@@ -570,45 +637,11 @@ __global__ void __launch_bounds__(256) normalise_kernel(long long G, T* u, const
     u[i] = (T)(sc * (double)u[i]);
 }
 
-// Start of an FP32 correction solve A e = r (iterative refinement of a mixed
-// Poisson solve): r32 = (float) r64, e = 0, and CG scalars relative to ||r32||.
-static __global__ void __launch_bounds__(256) refine_init_kernel(long long G, float* r32, float* e,
-                                                          const double* r64, CgScalars* sc,
-                                                          double tol, int max_it, RedBuf red) {
-  __shared__ double smem[256 / 32];
-  double acc[1] = {0.0};
+// phi64 += e; e = 0 (folds a round's FP32 correction into the FP64 potential).
+static __global__ void __launch_bounds__(256) fold_kernel(long long G, double* phi64, float* e) {
   for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < G; i += (long long)gridDim.x * 256) {
-    const float v = (float)r64[i];
-    r32[i] = v;
+    phi64[i] += (double)e[i];
     e[i] = 0.0f;
-    acc[0] += (double)v * (double)v;
-  }
-  struct Fin {
-    CgScalars* sc;
-    double tol;
-    int max_it;
-    __device__ void operator()(double* t) const {
-      sc->rr = t[0];
-      sc->rr0 = t[0];
-      sc->bb = t[0];
-      sc->tol2 = tol * tol;
-      sc->iters = 0;
-      sc->max_it = max_it;
-      sc->first = 1;
-      sc->beta = 0.0;
-      sc->done = (t[0] == 0.0 || max_it <= 0) ? 1 : 0;
-    }
-  } fin{sc, tol, max_it};
-  grid_sum<1, 256>(acc, smem, red, gridDim.x, blockIdx.x, threadIdx.x, fin);
-}
-
-// phi64 += e (apply an FP32 correction to the FP64 potential) and phi32 = (float) phi64.
-static __global__ void __launch_bounds__(256) refine_apply_kernel(long long G, double* phi64, float* phi32,
-                                                           const float* e) {
-  for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < G; i += (long long)gridDim.x * 256) {
-    const double v = phi64[i] + (double)e[i];
-    phi64[i] = v;
-    phi32[i] = (float)v;
   }
 }
 
@@ -620,10 +653,10 @@ __global__ void __launch_bounds__(256) convert_kernel(long long G, D* out, const
 
 // ------------------------------------------------- batched pointwise ops ---
 // CG second half on one grid of a batch (same arithmetic as cg_update_kernel).
-template <typename T>
+template <typename T, typename X = T>
 struct OpCgUpdate {
   static constexpr int K = 1;
-  T* x;
+  X* x;
   T* r;
   const T* p;
   const T* q;
@@ -633,7 +666,7 @@ struct OpCgUpdate {
   __device__ __forceinline__ bool skip() const { return sc->done != 0; }
   __device__ __forceinline__ void apply(long long i, double* acc) const {
     const T al = (T)sc->alpha;
-    x[i] = fma(al, p[i], x[i]);
+    x[i] = fma((X)sc->alpha, (X)p[i], x[i]);
     const T ri = fma(-al, q[i], r[i]);
     r[i] = ri;
     acc[0] += (double)ri * (double)ri;
@@ -641,6 +674,7 @@ struct OpCgUpdate {
   __device__ __forceinline__ void operator()(double* t) const {
     const double rr_new = t[0];
     sc->beta = (sc->rr != 0.0) ? rr_new / sc->rr : 0.0;
+    sc->rr_prev = sc->rr;
     sc->rr = rr_new;
     sc->iters += 1;
     const double thr = sc->tol2 * (sc->bb > 0.0 ? sc->bb : 1.0);
@@ -709,48 +743,48 @@ struct OpRank1 {
   __device__ __forceinline__ void operator()(double*) const {}
 };
 
-// Start of an FP32 correction solve (mixed Poisson): r32 = (float) r64, e = 0.
-struct OpRefineInit {
+// Residual replacement of the mixed CG on one grid (see refine_replace_kernel).
+struct OpRefineReplace {
   static constexpr int K = 1;
   float* r32;
-  float* e;
   const double* r64;
   CgScalars* sc;
   double tol;
-  int max_it;
+  int budget, restart;
   RedBuf red;
   int nblocks;
   __device__ __forceinline__ bool skip() const { return false; }
   __device__ __forceinline__ void apply(long long i, double* acc) const {
     const float v = (float)r64[i];
     r32[i] = v;
-    e[i] = 0.0f;
     acc[0] += (double)v * (double)v;
   }
   __device__ __forceinline__ void operator()(double* t) const {
+    if (restart) {
+      sc->first = 1;
+      sc->beta = 0.0;
+      sc->iters = 0;
+    } else {
+      sc->beta = (sc->rr_prev != 0.0) ? t[0] / sc->rr_prev : 0.0;
+    }
     sc->rr = t[0];
     sc->rr0 = t[0];
     sc->bb = t[0];
     sc->tol2 = tol * tol;
-    sc->iters = 0;
-    sc->max_it = max_it;
-    sc->first = 1;
-    sc->beta = 0.0;
-    sc->done = (t[0] == 0.0 || max_it <= 0) ? 1 : 0;
+    sc->max_it = sc->iters + budget;
+    sc->done = (t[0] == 0.0 || budget <= 0) ? 1 : 0;
   }
 };
 
-// phi64 += e, phi32 = (float) phi64.
-struct OpRefineApply {
+// phi64 += e; e = 0 on one grid of a batch.
+struct OpFold {
   static constexpr int K = 0;
   double* phi64;
-  float* phi32;
-  const float* e;
+  float* e;
   __device__ __forceinline__ bool skip() const { return false; }
   __device__ __forceinline__ void apply(long long i, double*) const {
-    const double v = phi64[i] + (double)e[i];
-    phi64[i] = v;
-    phi32[i] = (float)v;
+    phi64[i] += (double)e[i];
+    e[i] = 0.0f;
   }
   __device__ __forceinline__ void operator()(double*) const {}
 };

@@ -111,3 +111,28 @@ def test_admission_by_hbm_budget_queues_and_completes(ctx):
     n = len(cases) // 2
     np.testing.assert_array_equal(Es[:n], Es[n:])  # same request, same result, whatever the queueing
     bt.close()
+
+
+def test_serving_loop_results_match_solo_and_report_latency(ctx):
+    """Requests arriving while others run join the mix (continuous batching) and
+    finish with the result they have alone (bit-identical), each with a latency."""
+    from paper_1405_6456_gb300 import serving as S
+    cases = _mix()[:3]
+    prm = lambda c: _params(c.fd_order, F.PREC_MIXED, tol_E=1e-7, tol_inner=1e-8, tol_poisson=1e-8)
+    solo = []
+    for c in cases:
+        bt = F.Batch(ctx, F.PREC_MIXED, 8 * GB)
+        rid = bt.submit(c.R, c.Z, c.h, prm(c), grid=_grid(c))
+        bt.run()
+        solo.append(bt.poll(rid)[0])
+        bt.close()
+    reqs = [(0.0, cases[0]), (0.05, cases[1]), (0.1, cases[2])]
+    rep = S.serve(ctx, reqs, prm, precision=F.PREC_MIXED, hbm_budget_bytes=8 * GB, grid_for=_grid)
+    assert len(rep.results) == 3
+    by_name = {r.name: r for r in rep.results}
+    for c, Es in zip(cases, solo):
+        r = by_name[c.name]
+        assert r.energy == Es
+        assert r.latency_s > 0 and r.finish_s >= r.admit_s >= r.arrival_s - 1e-9
+    s = rep.summary()
+    assert s["latency_p99_s"] >= s["latency_p50_s"] > 0
