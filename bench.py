@@ -303,6 +303,8 @@ def run_gpu(args):
             roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                     "traffic": traffic, "kernel": "zstream_kernel<float,6,LoadPlain,EpiCgA> (CG: q = A r + beta q, p = r + beta p, p.q)",
                     "launches": tl, "avg_us": avg_s * 1e6, "peak_source": which,
+                    "timing": "CUDA events on the solve's stream around one stencil launch in 8 (recorded "
+                              "inside the CG graphs), over the whole timed region",
                     "algorithmic_bytes_per_launch": algo}
         else:
             flops = G * (2 * (6 * n + 1) + 2 + 2 + 2)  # stencil, p and q updates, p.q

@@ -90,7 +90,9 @@ typedef struct {
   int ezz_correction; /* 1: add the Gaussian-overlap repulsion correction (App. A) */
   double vacuum;      /* box rule of ofdft_grid_for_atoms: vacuum on every side */
   int round_to;       /* box rule: node counts rounded up to a multiple of this */
-  int refine_every;   /* MIXED: FP64 residual correction every this many FP32 CG steps */
+  int refine_every;   /* MIXED: FP64 residual correction after at most this many FP32 CG steps
+                         (sooner once the FP32 residual fell by 1e-4 or to half the tolerance);
+                         default 200: much longer FP32 runs let the q = A p recurrence drift */
   double trial_max_rel; /* cap of the trial step: h^3 |sig d|^2 <= trial_max_rel^2 N (0: no cap) */
   int max_backtrack;  /* halvings of the secant step while L does not decrease (0: none) */
   int precond_rank1;  /* 1: the preconditioner also inverts the rank-one term (4h^3/mu) u u^T

@@ -7,8 +7,22 @@
 namespace ofd {
 
 // ------------------------------------------------------------ Poisson (S3) --
-// Plain CG iterations on the prepared scalars `sc` (residual r, iterate x),
-// checking the device `done` flag every `chunk` iterations.
+// The x/r update of one CG iteration with r.r (second kernel of cg_step).
+template <typename T, typename X>
+int cg_update(ofdft_ctx* c, const GridDev& g, X* x, T* r, T* pv, T* qv, CgScalars* sc, int pb) {
+  {
+    ProfScope ps_(c, OFDFT_K_CG_UPDATE);
+    auto aligned = [](const void* q) { return ((uintptr_t)q & 15u) == 0; };
+    if (sizeof(X) == sizeof(T) && g.G % (16 / (long long)sizeof(T)) == 0 && aligned(x) && aligned(r) &&
+        aligned(pv) && aligned(qv))
+      cg_update_kernel<T, X, sizeof(X) == sizeof(T)><<<pb, 256, 0, c->stream>>>(g.G, x, r, pv, qv, sc, red(c));
+    else
+      cg_update_kernel<T, X><<<pb, 256, 0, c->stream>>>(g.G, x, r, pv, qv, sc, red(c));
+  }
+  CU(cudaGetLastError());
+  return OFDFT_OK;
+}
+
 // Launches one CG iteration (S3): the stencil pass on r with the p/q update and
 // p.q, then the x/r update with r.r; both kernels read and write the CG scalars
 // on the device and return at once when the solve is done.
@@ -16,12 +30,7 @@ template <typename T, typename X>
 int cg_step(ofdft_ctx* c, int R, const GridDev& g, const Weights<double>& Wneg, X* x, T* r, T* pv, T* qv,
             CgScalars* sc, int pb) {
   TRY(launch_z_r<T>(c, R, g, Wneg, LoadPlain<T>{r}, EpiCgA<T>{pv, qv, sc}, OFDFT_K_CG_DIR_STENCIL));
-  {
-    ProfScope ps_(c, OFDFT_K_CG_UPDATE);
-    cg_update_kernel<T, X><<<pb, 256, 0, c->stream>>>(g.G, x, r, pv, qv, sc, red(c));
-  }
-  CU(cudaGetLastError());
-  return OFDFT_OK;
+  return cg_update<T, X>(c, g, x, r, pv, qv, sc, pb);
 }
 
 constexpr int kChunk = 8;  // CG iterations between convergence polls
@@ -34,13 +43,18 @@ constexpr int kChunk = 8;  // CG iterations between convergence polls
 template <typename T>
 int tune_cg_split(ofdft_ctx* c, int R, const GridDev& g, const Weights<double>& Wneg, const T* r) {
   if (!c->autotune) return OFDFT_OK;
-  const std::vector<long long> key = ztune_key(zkernel_ptr<T, LoadPlain<T>, EpiCgA<T>>(R), g);
-  for (auto& t : c->ztune)
-    if (t.first == key) return OFDFT_OK;
+  T *pv = nullptr, *qv = nullptr;  // scratch p and q (separate allocations, aligned like the solver's)
+  const long long vec16 = zvec_ok<T>(g, LoadPlain<T>{r}, EpiCgA<T>{vec<T>(c, V_P0), vec<T>(c, V_AP), nullptr});
+  const std::vector<long long> tkey = {(long long)sizeof(T), R, g.n1, g.n2, g.n3, vec16};
+  for (auto& t : c->ztuned)
+    if (t == tkey) return OFDFT_OK;
   const std::vector<int> cand = {0, 1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64};
-  TRY(ensure_partials(c, zshape(c, g, R, 1, 64).nblocks, 1));  // largest candidate
-  T* scratch = nullptr;
-  CU(cudaMalloc(&scratch, 2 * g.G * sizeof(T)));
+  TRY(ensure_partials(c, zshape<T>(c, g, R, 1, 64).nblocks, 1));  // largest candidate
+  CU(cudaMalloc(&pv, g.G * sizeof(T)));
+  if (cudaMalloc(&qv, g.G * sizeof(T)) != cudaSuccess) {
+    cudaFree(pv);
+    return fail(c, OFDFT_ENOMEM, "autotune: no room for scratch vectors");
+  }
   CgScalars* sc = c->sc + 2;
   CgScalars init;
   memset(&init, 0, sizeof(init));
@@ -54,11 +68,12 @@ int tune_cg_split(ofdft_ctx* c, int R, const GridDev& g, const Weights<double>& 
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   int best = 0, rc = OFDFT_OK;
   float best_ms = 1e30f;
+  std::vector<long long> key;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     rc = fail(c, OFDFT_ECUDA, "autotune: event creation failed");
   for (int nz : cand) {
     if (rc != OFDFT_OK || nz > g.n3) break;
-    c->ztune.push_back({key, nz});
+    c->force_nz = nz;
     float ms = 0.0f;
     for (int rep = 0; rep < 4 && rc == OFDFT_OK; ++rep) {
       if (cudaMemcpyAsync(sc, &init, sizeof(init), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
@@ -66,41 +81,50 @@ int tune_cg_split(ofdft_ctx* c, int R, const GridDev& g, const Weights<double>& 
         rc = fail(c, OFDFT_ECUDA, "autotune: enqueue failed");
         break;
       }
-      rc = launch_z_r<T>(c, R, g, Wneg, LoadPlain<T>{r}, EpiCgA<T>{scratch, scratch + g.G, sc},
-                         OFDFT_K_CG_DIR_STENCIL);
+      rc = launch_z_r<T>(c, R, g, Wneg, LoadPlain<T>{r}, EpiCgA<T>{pv, qv, sc}, OFDFT_K_CG_DIR_STENCIL);
+      key = c->last_zkey;
       float t = 0.0f;
       if (rc == OFDFT_OK && (cudaEventRecord(e1, c->stream) != cudaSuccess ||
                              cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess))
         rc = fail(c, OFDFT_ECUDA, "autotune: timing failed");
       if (rep > 0) ms += t;  // the first launch of each split warms up
     }
-    c->ztune.pop_back();
     if (ms < best_ms) {
       best_ms = ms;
       best = nz;
     }
   }
+  c->force_nz = -1;
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   cudaStreamSynchronize(c->stream);
-  cudaFree(scratch);
+  cudaFree(pv);
+  cudaFree(qv);
   c->prof = prof;
   c->launches = launches;  // tuning launches are not part of the caller's work
   memcpy(c->kind_launches, kinds, sizeof(kinds));
   if (rc != OFDFT_OK) return rc;
   c->ztune.push_back({key, best});
+  c->ztuned.push_back(tkey);
   return OFDFT_OK;
 }
 
 // The graph of one chunk of CG iterations for this buffer set, captured on
 // first use (the launches bake in pointers, sizes and weights).
+// With sample_set = 0 or 1 the graph also records the context's timing events
+// gev[sample_set] around the stencil pass of its middle iteration, so that a
+// timed run keeps its graphs and times one stencil launch in kChunk.
 template <typename T, typename X>
 int cg_graph(ofdft_ctx* c, int R, const GridDev& g, double h, const Weights<double>& Wneg, X* x, T* r, T* pv, T* qv,
-             CgScalars* sc, int pb, cudaGraphExec_t* out) {
+             CgScalars* sc, int pb, int sample_set, cudaGraphExec_t* out) {
   const std::vector<long long> key = {(long long)sizeof(T), (long long)sizeof(X), R, g.n1, g.n2, g.n3, (long long)x,
                                       (long long)r,
                                       (long long)pv, (long long)qv, (long long)sc, pb,
-                                      (long long)c->partials.p, (long long)(h * 1e12)};
+                                      (long long)c->partials.p, (long long)(h * 1e12), sample_set};
+  if (sample_set >= 0 && !c->gev[sample_set][0]) {
+    CU(cudaEventCreate(&c->gev[sample_set][0]));
+    CU(cudaEventCreate(&c->gev[sample_set][1]));
+  }
   for (auto& e : c->graphs)
     if (e.key == key) {
       *out = e.exec;
@@ -122,7 +146,16 @@ int cg_graph(ofdft_ctx* c, int R, const GridDev& g, double h, const Weights<doub
   cudaError_t eb = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
   int rc = OFDFT_OK;
   if (eb == cudaSuccess)
-    for (int i = 0; i < kChunk && rc == OFDFT_OK; ++i) rc = cg_step<T, X>(c, R, g, Wneg, x, r, pv, qv, sc, pb);
+    for (int i = 0; i < kChunk && rc == OFDFT_OK; ++i) {
+      if (sample_set >= 0 && i == kChunk / 2) {
+        cudaEventRecordWithFlags(c->gev[sample_set][0], c->stream, cudaEventRecordExternal);
+        rc = launch_z_r<T>(c, R, g, Wneg, LoadPlain<T>{r}, EpiCgA<T>{pv, qv, sc}, OFDFT_K_CG_DIR_STENCIL);
+        cudaEventRecordWithFlags(c->gev[sample_set][1], c->stream, cudaEventRecordExternal);
+        if (rc == OFDFT_OK) rc = cg_update<T, X>(c, g, x, r, pv, qv, sc, pb);
+      } else {
+        rc = cg_step<T, X>(c, R, g, Wneg, x, r, pv, qv, sc, pb);
+      }
+    }
   const cudaError_t ec = (eb == cudaSuccess) ? cudaStreamEndCapture(c->stream, &graph) : eb;
   c->stream = user;
   c->prof = prof;
@@ -142,8 +175,10 @@ int cg_graph(ofdft_ctx* c, int R, const GridDev& g, double h, const Weights<doub
 // checking the device `done` flag every kChunk iterations.  Chunk k+1 is
 // enqueued before the host waits for chunk k's copy of the scalars, so the
 // stream never drains; kernels of a converged solve return at once, so an extra
-// chunk costs only empty launches.  Without per-launch timing a chunk is one
-// CUDA graph launch.
+// chunk costs only empty launches.  A chunk is one CUDA graph launch unless the
+// CG update is being timed (then every launch is bracketed by events); when
+// only the stencil pass is timed, the graphs of alternate chunks carry the two
+// sets of sampling events and the host reads chunk k's set while chunk k+1 runs.
 template <typename T, typename X = T>
 int cg_iterate(ofdft_ctx* c, int R, const GridDev& g, double h, const Weights<double>& Wneg, X* x, T* r,
                CgScalars* sc, int max_it, CgScalars* host_sc) {
@@ -151,15 +186,31 @@ int cg_iterate(ofdft_ctx* c, int R, const GridDev& g, double h, const Weights<do
   T* qv = vec<T>(c, V_AP);
   const int pb = pointwise_blocks(c, g.G);
   TRY(ensure_partials(c, pb, 1));
-  TRY(ensure_partials(c, zshape(c, g, R, 32).nblocks, 1));
+  TRY(ensure_partials(c, zshape<T>(c, g, R, 32).nblocks, 1));
   TRY(tune_cg_split<T>(c, R, g, Wneg, r));
-  const bool timed = (c->prof & ((1 << OFDFT_K_CG_DIR_STENCIL) | (1 << OFDFT_K_CG_UPDATE))) != 0;
-  cudaGraphExec_t exec = nullptr;
-  if (c->use_graphs && !timed && max_it >= kChunk) TRY((cg_graph<T, X>(c, R, g, h, Wneg, x, r, pv, qv, sc, pb, &exec)));
+  const bool full_timed = (c->prof & (1 << OFDFT_K_CG_UPDATE)) != 0;
+  const bool sampled = !full_timed && (c->prof & (1 << OFDFT_K_CG_DIR_STENCIL)) != 0;
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  if (c->use_graphs && !full_timed && max_it >= kChunk) {
+    TRY((cg_graph<T, X>(c, R, g, h, Wneg, x, r, pv, qv, sc, pb, sampled ? 0 : -1, &exec[0])));
+    exec[1] = exec[0];
+    if (sampled) TRY((cg_graph<T, X>(c, R, g, h, Wneg, x, r, pv, qv, sc, pb, 1, &exec[1])));
+  }
+  bool pending[2] = {false, false};
+  auto read_sample = [&](int set) {
+    float ms = 0.0f;
+    if (pending[set] && cudaEventElapsedTime(&ms, c->gev[set][0], c->gev[set][1]) == cudaSuccess) {
+      c->timed_ms[OFDFT_K_CG_DIR_STENCIL] += ms;
+      c->timed_launches[OFDFT_K_CG_DIR_STENCIL] += 1;
+    }
+    pending[set] = false;
+  };
   int launched = 0, chunks = 0;
   while (launched < max_it) {
-    if (exec && launched + kChunk <= max_it) {
-      CU(cudaGraphLaunch(exec, c->stream));
+    const int slot = chunks & 1;
+    if (exec[0] && launched + kChunk <= max_it) {
+      CU(cudaGraphLaunch(exec[slot], c->stream));
+      pending[slot] = sampled;
       launched += kChunk;
       c->launches += 2 * kChunk;
       c->kind_launches[OFDFT_K_CG_DIR_STENCIL] += kChunk;
@@ -168,16 +219,18 @@ int cg_iterate(ofdft_ctx* c, int R, const GridDev& g, double h, const Weights<do
       for (int i = 0; i < kChunk && launched < max_it; ++i, ++launched)
         TRY((cg_step<T, X>(c, R, g, Wneg, x, r, pv, qv, sc, pb)));
     }
-    const int slot = chunks & 1;
     CU(cudaMemcpyAsync(&c->ring[slot], sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, c->stream));
     CU(cudaEventRecord(c->ring_ev[slot], c->stream));
     if (chunks > 0) {
       CU(cudaEventSynchronize(c->ring_ev[slot ^ 1]));
+      read_sample(slot ^ 1);  // chunk k-1 has finished; chunk k+1 will reuse its events
       if (c->ring[slot ^ 1].done) break;
     }
     ++chunks;
   }
   TRY(sync_scalars(c, sc, sizeof(CgScalars), host_sc));
+  read_sample(0);
+  read_sample(1);
   return OFDFT_OK;
 }
 
@@ -223,8 +276,9 @@ int poisson_fp64(ofdft_ctx* c, int R, const GridDev& g, double h, const double* 
 // residual r64 = 4 pi (u^2 + b64) + L_h phi64 with the FP64 stencil; the solve
 // ends when it meets tol.  Otherwise r64 replaces the FP32 residual (the search
 // direction is kept after the first round, so no Krylov information is lost)
-// and FP32 iterations run until the FP32 residual falls by 1e-4 or refine_every
-// steps.  At the end phi32 = (float) phi64.  rho32 (optional) replaces u^2 + b.
+// and FP32 iterations run until the FP32 residual falls by mixed_inner_tol (1e-4,
+// or less when the FP64 test needs less) or refine_every steps.  At the end
+// phi32 = (float) phi64.  rho32 (optional) replaces u^2 + b.
 int poisson_mixed(ofdft_ctx* c, int R, const GridDev& g, double h, const float* rho32, const float* u,
                   const double* b64, double* phi64, float* phi32, double tol, int max_it, int refine_every,
                   ofdft_cg_stats* st) {
@@ -268,8 +322,8 @@ int poisson_mixed(ofdft_ctx* c, int R, const GridDev& g, double h, const float* 
     TRY(ensure_partials(c, pb, 1));
     {
       ProfScope ps_(c, OFDFT_K_VECTOR);
-      refine_replace_kernel<<<pb, 256, 0, c->stream>>>(g.G, r32, r64, c->sc32, 1e-4, budget, round == 0 ? 1 : 0,
-                                                       red(c));
+      refine_replace_kernel<<<pb, 256, 0, c->stream>>>(g.G, r32, r64, c->sc32, mixed_inner_tol(hs.rr, bb, tol),
+                                                       budget, round == 0 ? 1 : 0, red(c));
     }
     CU(cudaGetLastError());
     TRY(sync_scalars(c, c->sc32, sizeof(CgScalars), &hs32));
@@ -324,6 +378,8 @@ struct Solver {
   T *u, *ut, *phi, *b, *G, *Gt, *s, *st, *sn, *d;
   double* b64;    // mixed: FP64 pseudocharge
   double* phi64;  // mixed: FP64 potential
+  double* phi0;   // FP64 potential at the origin of the current line search
+  double line_l = 0.0;  // position along d of the last Poisson solve (0: none yet)
   ofdft_solve_stats* stats;
   ofdft_energy e;  // at the current point
   int trace = 0;   // OFDFT_TRACE=1: one line per evaluation on stderr
@@ -397,6 +453,26 @@ struct Solver {
     return OFDFT_OK;
   }
 
+  // Warm start of the Poisson solves of a line search: phi(u + a d) is close to
+  // phi0 + (a / l) (phi_l - phi0) (rho = u^2 + b is smooth in a), a better start
+  // than phi_l alone.  line_start records phi0 at the origin; line_guess(a)
+  // rewrites the FP64 potential (phi_l, from the solve at position l) in place.
+  double* master() { return mixed ? phi64 : reinterpret_cast<double*>(phi); }
+  int line_start() {
+    CU(cudaMemcpyAsync(phi0, master(), g.G * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    line_l = 0.0;
+    return OFDFT_OK;
+  }
+  int line_guess(double a) {
+    if (line_l != 0.0 && (p->terms & OFDFT_TERM_ES)) {
+      ProfScope ps_(c, OFDFT_K_VECTOR);
+      extrap_kernel<<<pointwise_blocks(c, g.G), 256, 0, c->stream>>>(g.G, master(), phi0, a / line_l - 1.0);
+    }
+    CU(cudaGetLastError());
+    line_l = a;
+    return OFDFT_OK;
+  }
+
   int dots(const T* a, const T* bb, const T* cc, const T* ee, double* r2) {
     const int pb = pointwise_blocks(c, g.G);
     TRY(ensure_partials(c, pb, 2));
@@ -459,6 +535,8 @@ struct Solver {
       // trial point at sig along d (sigma0, capped to an RMS change of trial_max_rel of u)
       double sig = p->sigma0;
       if (p->trial_max_rel > 0.0 && dd > 0.0) sig = std::min(sig, p->trial_max_rel * sqrt(N / dd));
+      TRY(line_start());
+      TRY(line_guess(sig));
       TRY(axpy_abs(ut, u, d, sig));
       ofdft_energy et;
       TRY(eval(ut, Gt, st, d, s_old, eta, mu, &et));
@@ -472,17 +550,21 @@ struct Solver {
       } else {
         T* snew = sn;
         const double L0 = e.L;
+        double pos = 0.0;  // position of u along d
         for (int j = 1; j <= p->max_secant; ++j) {
           alpha = alpha * gcur / (gprev - gcur);
           // candidate written beside u so that a rejected step can be halved
+          TRY(line_guess(pos + alpha));
           TRY(axpy_abs(ut, u, d, alpha));
           TRY(eval(ut, G, snew, d, s_old, eta, mu, &e));
           for (int bt = 0; bt < p->max_backtrack && !(e.L <= L0); ++bt) {
             alpha *= 0.5;
+            TRY(line_guess(pos + alpha));
             TRY(axpy_abs(ut, u, d, alpha));
             TRY(eval(ut, G, snew, d, s_old, eta, mu, &e));
           }
           std::swap(u, ut);
+          pos += alpha;
           gprev = gcur;
           gcur = e.gd;
           if (j == p->max_secant || alpha * alpha * dd <= p->eps_secant * p->eps_secant * N) break;
@@ -750,6 +832,8 @@ int solve_impl(ofdft_ctx* c, const ofdft_grid* gr, const double* R_host, const d
   S.d = vec<T>(c, V_D);
   S.b64 = mixed ? vec<double>(c, V_B64) : nullptr;
   S.phi64 = mixed ? vec<double>(c, V_PHI64) : nullptr;
+  TRY(ensure(c, c->v[V_PHI0], g.G * sizeof(double)));
+  S.phi0 = vec<double>(c, V_PHI0);
   // S1: pseudocharge (FP64 for the mixed path too), starting guess, phi = 0
   if (!mixed) {
     TRY(device_pseudocharge<double>(c, gr, R, R_host, Z_host, M, p->sigma, p->rc, (double*)S.b, &S.E_self));
@@ -918,6 +1002,9 @@ int ofdft_destroy(ofdft_ctx* c) {
   harvest(c);
   for (auto& e : c->graphs) cudaGraphExecDestroy(e.exec);
   if (c->gstream) cudaStreamDestroy(c->gstream);
+  for (auto& s : c->gev)
+    for (auto& e : s)
+      if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : c->free_events) cudaEventDestroy(e);
   cudaFree(c->partials.p);
   for (auto& b : c->v) cudaFree(b.p);
@@ -997,6 +1084,7 @@ long long ofdft_workspace_bytes(const ofdft_grid* g, int fd_order, int prec) {
   const long long es = (prec == OFDFT_PREC_MIXED) ? 4 : 8;
   long long bytes = G * es * 14;                 // solve state, NLCG and CG vectors
   if (prec == OFDFT_PREC_MIXED) bytes += G * 8 * 3 + G * 4;  // r64, phi64, b64, e32
+  bytes += G * 8;                                // potential at the line-search origin
   (void)fd_order;
   return bytes;
 }

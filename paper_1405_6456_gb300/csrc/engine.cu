@@ -61,6 +61,7 @@ struct Slot {
   // fields
   T *u, *ut, *phi, *b, *G, *Gt, *s, *st, *sn, *d, *w, *r, *pv, *qv;
   double *phi64 = nullptr, *b64 = nullptr, *r64 = nullptr;
+  double* phi0 = nullptr;  // FP64 potential at the origin of the current line search
   float* e32 = nullptr;
   double* partials = nullptr;
   unsigned int* counter = nullptr;
@@ -89,6 +90,8 @@ struct Slot {
   ofdft_energy* ev_out = nullptr;
   const T* dot_a[4] = {nullptr, nullptr, nullptr, nullptr};
   std::vector<Vop<T>> vops;
+  std::vector<double> line_ops;  // OpLine parameters, applied before the next evaluation
+  double line_l = 0.0, pos = 0.0;  // last solve's position along d; position of u along d
   // Poisson phase (within a round)
   int pphase = 0, ptotal = 0;
   ofdft_cg_stats pstats;
@@ -155,7 +158,7 @@ long long slot_bytes(const ofdft_grid& g, int prec, int* maxblk) {
   const long long G = (long long)g.n[0] * g.n[1] * g.n[2];
   const long long es = (prec == OFDFT_PREC_MIXED) ? 4 : 8;
   auto chunk = [](long long n) { return (n + 255) & ~255LL; };  // carve() rounds every piece to 256 B
-  long long bytes = 14 * chunk(G * es);
+  long long bytes = 14 * chunk(G * es) + chunk(G * 8);
   if (prec == OFDFT_PREC_MIXED) bytes += 3 * chunk(G * 8) + chunk(G * 4);
   // reduction scratch: the larger of the tile count and the segment count
   const long long tiles = (long long)((g.n[0] + BX - 1) / BX) * ((g.n[1] + BY - 1) / BY) * ((g.n[2] + 15) / 16);
@@ -179,6 +182,7 @@ int carve(ofdft_ctx* c, Slot<T>* S, int prec) {
   };
   T** vecs[] = {&S->u, &S->ut, &S->phi, &S->b, &S->G, &S->Gt, &S->s, &S->st, &S->sn, &S->d, &S->w, &S->r, &S->pv, &S->qv};
   for (T** v : vecs) *v = (T*)take(G * sizeof(T));
+  S->phi0 = (double*)take(G * 8);
   if (prec == OFDFT_PREC_MIXED) {
     S->phi64 = (double*)take(G * 8);
     S->b64 = (double*)take(G * 8);
@@ -192,9 +196,10 @@ int carve(ofdft_ctx* c, Slot<T>* S, int prec) {
   return OFDFT_OK;
 }
 
-// Tiles of one grid for the z-streaming batch launch (z chunks of 16 planes).
-void grid_tiles(const GridDev& g, int slot, std::vector<ZTile>& out, int* count) {
-  const int gx = (g.n1 + BX - 1) / BX, gy = (g.n2 + BY - 1) / BY;
+// Tiles of one grid for the z-streaming batch launch (BX x rows columns, z chunks
+// of 16 planes).
+void grid_tiles(const GridDev& g, int slot, int rows, std::vector<ZTile>& out, int* count) {
+  const int gx = (g.n1 + BX - 1) / BX, gy = (g.n2 + rows - 1) / rows;
   const int zc = 16;
   int bid = 0;
   for (int z0 = 0; z0 < g.n3; z0 += zc)
@@ -221,17 +226,17 @@ struct Engine {
 
   RedBuf slot_red(Slot<T>* S) { return RedBuf{S->partials, S->counter}; }
 
-  template <typename TT, int R, class L, class E>
+  template <typename TT, int R, int V, class L, class E>
   int launch_zb(int kind, unsigned nb, const ZTile* dt, const ZSlot<TT, L, E>* ds) {
-    constexpr int smem = zsmem_bytes<TT, R, E>();
+    constexpr int smem = zsmem_bytes<TT, R, V, E>();
     static bool attr = false;
     if (!attr) {
-      CU(cudaFuncSetAttribute(zbatch_kernel<TT, R, L, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+      CU(cudaFuncSetAttribute(zbatch_kernel<TT, R, V, L, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
       attr = true;
     }
     {
       ProfScope ps_(c, kind);
-      zbatch_kernel<TT, R, L, E><<<nb, dim3(BX, BY), smem, c->stream>>>(dt, ds);
+      zbatch_kernel<TT, R, V, L, E><<<nb, dim3(BX, BY), smem, c->stream>>>(dt, ds);
     }
     CU(cudaGetLastError());
     return OFDFT_OK;
@@ -242,38 +247,48 @@ struct Engine {
   // loader/epilogue descriptor of that slot.  One launch per stencil radius.
   template <typename TT, class L, class E, class Make>
   int zpass(const std::vector<Slot<T>*>& slots, int kind, double wscale, Make make) {
-    for (int Rr = 1; Rr <= kMaxR; ++Rr) {
-      std::vector<ZTile> tiles;
-      std::vector<ZSlot<TT, L, E>> desc;
-      for (Slot<T>* S : slots) {
-        if (S->Rr != Rr) continue;
-        int cnt = 0;
-        const int si = (int)desc.size();
-        grid_tiles(S->g, si, tiles, &cnt);
-        ZSlot<TT, L, E> z;
-        z.g = S->g;
-        z.W = cast_weights<TT>(lap_weights(Rr, S->h, wscale));
-        auto le = make(S);
-        z.ld = le.first;
-        z.ep = le.second;
-        z.red = slot_red(S);
-        z.nblocks = cnt;
-        desc.push_back(z);
+    // one launch per stencil radius and staging width (16-byte copies where the
+    // grid's rows allow them, element copies otherwise)
+    for (int Rr = 1; Rr <= kMaxR; ++Rr)
+      for (int wide = 1; wide >= 0; --wide) {
+        std::vector<ZTile> tiles;
+        std::vector<ZSlot<TT, L, E>> desc;
+        for (Slot<T>* S : slots) {
+          if (S->Rr != Rr) continue;
+          auto le = make(S);
+          if ((int)zvec_ok<TT>(S->g, le.first, le.second) != wide) continue;
+          int cnt = 0;
+          const int si = (int)desc.size();
+          grid_tiles(S->g, si, ZCfg<TT>::TY, tiles, &cnt);
+          ZSlot<TT, L, E> z;
+          z.g = S->g;
+          z.W = cast_weights<TT>(lap_weights(Rr, S->h, wscale));
+          z.ld = le.first;
+          z.ep = le.second;
+          z.red = slot_red(S);
+          z.nblocks = cnt;
+          desc.push_back(z);
+        }
+        if (tiles.empty()) continue;
+        TRY(upload(c, B->d_tiles, tiles));
+        TRY(upload(c, B->d_desc, desc));
+        const ZTile* dt = (const ZTile*)B->d_tiles.p;
+        const ZSlot<TT, L, E>* ds = (const ZSlot<TT, L, E>*)B->d_desc.p;
+        const unsigned nb = (unsigned)tiles.size();
+        constexpr int VW = 16 / (int)sizeof(TT);
+        switch (Rr * 2 + wide) {
+#define ZB_CASE(RR)                                                             \
+  case RR * 2 + 1: TRY((launch_zb<TT, RR, VW, L, E>(kind, nb, dt, ds))); break; \
+  case RR * 2: TRY((launch_zb<TT, RR, 1, L, E>(kind, nb, dt, ds))); break;
+          ZB_CASE(1)
+          ZB_CASE(2)
+          ZB_CASE(3)
+          ZB_CASE(4)
+          ZB_CASE(5)
+          ZB_CASE(6)
+#undef ZB_CASE
+        }
       }
-      if (tiles.empty()) continue;
-      TRY(upload(c, B->d_tiles, tiles));
-      TRY(upload(c, B->d_desc, desc));
-      const ZTile* dt = (const ZTile*)B->d_tiles.p;
-      const ZSlot<TT, L, E>* ds = (const ZSlot<TT, L, E>*)B->d_desc.p;
-      switch (Rr) {
-        case 1: TRY((launch_zb<TT, 1, L, E>(kind, (unsigned)tiles.size(), dt, ds))); break;
-        case 2: TRY((launch_zb<TT, 2, L, E>(kind, (unsigned)tiles.size(), dt, ds))); break;
-        case 3: TRY((launch_zb<TT, 3, L, E>(kind, (unsigned)tiles.size(), dt, ds))); break;
-        case 4: TRY((launch_zb<TT, 4, L, E>(kind, (unsigned)tiles.size(), dt, ds))); break;
-        case 5: TRY((launch_zb<TT, 5, L, E>(kind, (unsigned)tiles.size(), dt, ds))); break;
-        case 6: TRY((launch_zb<TT, 6, L, E>(kind, (unsigned)tiles.size(), dt, ds))); break;
-      }
-    }
     return OFDFT_OK;
   }
 
@@ -388,7 +403,9 @@ struct Engine {
       if (corr.empty()) break;
       TRY((ppass<OpRefineReplace>(corr, OFDFT_K_VECTOR, [&](Slot<T>* S, int nb) {
         const int budget = std::min(std::max(S->p.refine_every, 1), S->p.max_cg - S->ptotal);
-        return OpRefineReplace{(float*)S->r, S->r64, B->sc32 + S->index, 1e-4, budget, S->pphase, slot_red(S), nb};
+        const CgScalars& h = B->h_sc[S->index];
+        const double itol = mixed_inner_tol(h.rr, h.bb > 0 ? h.bb : 1.0, S->p.tol_poisson);
+        return OpRefineReplace{(float*)S->r, S->r64, B->sc32 + S->index, itol, budget, S->pphase, slot_red(S), nb};
       })));
       TRY(read_scalars());
       std::vector<int> before(B->capacity, 0);
@@ -489,6 +506,17 @@ struct Engine {
       })));
     }
     for (Slot<T>* S : slots) S->vops.clear();
+    size_t ldepth = 0;
+    for (Slot<T>* S : slots) ldepth = std::max(ldepth, S->line_ops.size());
+    for (size_t i = 0; i < ldepth; ++i) {
+      std::vector<Slot<T>*> ls;
+      for (Slot<T>* S : slots)
+        if (i < S->line_ops.size()) ls.push_back(S);
+      TRY((ppass<OpLine>(ls, OFDFT_K_VECTOR, [&](Slot<T>* S, int) {
+        return OpLine{mixed ? S->phi64 : reinterpret_cast<double*>(S->phi), S->phi0, S->line_ops[i]};
+      })));
+    }
+    for (Slot<T>* S : slots) S->line_ops.clear();
     return OFDFT_OK;
   }
 
@@ -512,6 +540,21 @@ struct Engine {
     S->dot_a[3] = S->d;
   }
   void vop(Slot<T>* S, int kind, T* out, const T* a, const T* b, double x) { S->vops.push_back(Vop<T>{kind, out, a, b, x}); }
+  // Warm start of the line search's Poisson solves (as Solver::line_start and
+  // line_guess of the single-solve path): record phi0, then extrapolate
+  // phi0 -> phi_l linearly to the next position a.
+  void line_start(Slot<T>* S) {
+    if (S->p.terms & OFDFT_TERM_ES) S->line_ops.push_back(0.0);
+    S->line_l = 0.0;
+    S->pos = 0.0;
+  }
+  void line_guess(Slot<T>* S, double a) {
+    if (S->line_l != 0.0 && (S->p.terms & OFDFT_TERM_ES)) {
+      const double t = a / S->line_l - 1.0;
+      if (t != 0.0) S->line_ops.push_back(t);
+    }
+    S->line_l = a;
+  }
 
   void finish(Slot<T>* S, int status, const char* msg) {
     S->status = status;
@@ -582,6 +625,8 @@ struct Engine {
           }
           S->sig = p.sigma0;
           if (p.trial_max_rel > 0.0 && S->dd > 0.0) S->sig = std::min(S->sig, p.trial_max_rel * sqrt(S->N / S->dd));
+          line_start(S);
+          line_guess(S, S->sig);
           vop(S, VOP_AXPY_ABS, S->ut, S->u, S->d, S->sig);
           request_eval(S, S->ut, S->Gt, S->st, S->d, S->s_old, &S->et);
           S->state = S_TRIAL;
@@ -603,6 +648,7 @@ struct Engine {
           S->j = 1;
           S->alpha = S->alpha * S->gcur / (S->gprev - S->gcur);
           S->bt = 0;
+          line_guess(S, S->pos + S->alpha);
           vop(S, VOP_AXPY_ABS, S->ut, S->u, S->d, S->alpha);
           request_eval(S, S->ut, S->G, S->snew, S->d, S->s_old, &S->e);
           S->state = S_SECANT;
@@ -612,11 +658,13 @@ struct Engine {
           if (S->bt < p.max_backtrack && !(S->e.L <= S->L0)) {
             S->bt++;
             S->alpha *= 0.5;
+            line_guess(S, S->pos + S->alpha);
             vop(S, VOP_AXPY_ABS, S->ut, S->u, S->d, S->alpha);
             request_eval(S, S->ut, S->G, S->snew, S->d, S->s_old, &S->e);
             return;
           }
           std::swap(S->u, S->ut);
+          S->pos += S->alpha;
           S->gprev = S->gcur;
           S->gcur = S->e.gd;
           const bool stop = (S->j == p.max_secant || S->alpha * S->alpha * S->dd <= p.eps_secant * p.eps_secant * S->N) ||
@@ -625,6 +673,7 @@ struct Engine {
             S->j++;
             S->alpha = S->alpha * S->gcur / (S->gprev - S->gcur);
             S->bt = 0;
+            line_guess(S, S->pos + S->alpha);
             vop(S, VOP_AXPY_ABS, S->ut, S->u, S->d, S->alpha);
             request_eval(S, S->ut, S->G, S->snew, S->d, S->s_old, &S->e);
             return;

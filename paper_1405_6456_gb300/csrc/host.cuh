@@ -63,8 +63,12 @@ struct ofdft_ctx {
   std::vector<GraphEntry> graphs;
   int use_graphs = 1;
   cudaStream_t gstream = nullptr;  // private stream used only to capture graphs
+  cudaEvent_t gev[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // sampling events recorded by CG graphs
   // autotuned z-splits of the z-streaming passes: key -> number of z chunks
   std::vector<std::pair<std::vector<long long>, int>> ztune;
+  std::vector<std::vector<long long>> ztuned;  // (type, radius, grid, 16-byte staging) already tuned
+  std::vector<long long> last_zkey;            // key of the last z-streaming launch
+  int force_nz = -1;                           // >= 0: z-split of the next launches (autotuner)
   int autotune = 1;
 };
 
@@ -77,6 +81,7 @@ enum Vec {
   V_G, V_GT, V_S, V_ST, V_SN, V_D,     // NLCG vectors
   V_ATOM0, V_ATOM1, V_ATOM2,           // atom scratch
   V_W,                                 // u / Jacobi diagonal (rank-one preconditioner)
+  V_PHI0,                              // FP64 potential at the origin of the current line search
   V_COUNT
 };
 
@@ -195,6 +200,9 @@ inline int check_grid(ofdft_ctx* c, const ofdft_grid* g) {
   for (int d = 0; d < 3; ++d)
     if (g->n[d] < 1 || g->n[d] > (1 << 16)) return fail(c, OFDFT_EINVAL, "grid dimension %d is %d", d, g->n[d]);
   if (!(g->h > 0.0) || !isfinite(g->h)) return fail(c, OFDFT_EINVAL, "grid spacing must be positive");
+  // the stencil kernels hold in-plane offsets in 32 bits
+  if ((long long)g->n[0] * (g->n[1] + 2 * kMaxR) >= (1LL << 31))
+    return fail(c, OFDFT_EINVAL, "grid plane of %d x %d nodes is too large", g->n[0], g->n[1]);
   return OFDFT_OK;
 }
 
@@ -258,15 +266,25 @@ inline int pointwise_blocks(ofdft_ctx* c, long long G) {
 // the resident block slots (SMs x blocks per SM) in whole waves: a grid just
 // above a wave would leave a nearly empty second wave.  z-chunks are at least
 // 2R planes deep unless the grid is too small to fill the GPU at all.
+// Relative tolerance of one FP32 round of the mixed Poisson CG: cut the FP32
+// residual by 1e-4 (the reduction FP32 recurrences track faithfully), but not
+// below half of what the FP64 stopping test still asks for (||r|| <= tol ||b||),
+// so that the last round does not over-solve.  rr = ||r64||^2, bb = ||b||^2.
+inline double mixed_inner_tol(double rr, double bb, double tol) {
+  const double want = (rr > 0.0) ? 0.5 * tol * sqrt(bb / rr) : 1e-4;
+  return std::max(1e-4, std::min(want, 0.5));
+}
+
 struct ZShape {
   dim3 grid;
   int zchunk;
   long long nblocks;
 };
 
-inline ZShape zshape(ofdft_ctx* c, const GridDev& g, int R, int blocks_per_sm = 4, int force_nz = 0) {
+template <typename T>
+ZShape zshape(ofdft_ctx* c, const GridDev& g, int R, int blocks_per_sm = 4, int force_nz = 0) {
   ZShape s;
-  const int gx = (g.n1 + BX - 1) / BX, gy = (g.n2 + BY - 1) / BY;
+  const int gx = (g.n1 + BX - 1) / BX, gy = (g.n2 + ZCfg<T>::TY - 1) / ZCfg<T>::TY;
   const long long tiles = (long long)gx * gy;
   const long long slots = (long long)c->sms * std::max(blocks_per_sm, 1);
   int nz = (int)std::max<long long>(1, slots / tiles);  // one wave when tiles <= slots
@@ -285,46 +303,55 @@ inline std::vector<long long> ztune_key(const void* fn, const GridDev& g) {
   return {(long long)(uintptr_t)fn, g.n1, g.n2, g.n3};
 }
 
+// True when a pass can stage 16-byte copies: rows of a whole number of copies
+// (n1 % (16 / sizeof(T)) == 0) and 16-byte aligned stencil and epilogue inputs.
 template <typename T, class L, class E>
-const void* zkernel_ptr(int R) {
-  switch (R) {
-    case 1: return (const void*)zstream_kernel<T, 1, L, E>;
-    case 2: return (const void*)zstream_kernel<T, 2, L, E>;
-    case 3: return (const void*)zstream_kernel<T, 3, L, E>;
-    case 4: return (const void*)zstream_kernel<T, 4, L, E>;
-    case 5: return (const void*)zstream_kernel<T, 5, L, E>;
-    default: return (const void*)zstream_kernel<T, 6, L, E>;
-  }
+bool zvec_ok(const GridDev& g, const L& ld, const E& ep) {
+  if (g.n1 % (16 / (int)sizeof(T))) return false;
+  auto aligned = [](const void* p) { return ((uintptr_t)p & 15u) == 0; };
+  if (!aligned(ld.f)) return false;
+  for (int j = 0; j < E::NIN; ++j)
+    if (ep.input(j) && !aligned(ep.input(j))) return false;
+  return true;
 }
 
-template <typename T, int R, class L, class E>
-int launch_z(ofdft_ctx* c, const GridDev& g, const Weights<double>& W, L ld, E ep, int kind) {
-  constexpr int smem = zsmem_bytes<T, R, E>();
+template <typename T, int R, int V, class L, class E>
+int launch_zv(ofdft_ctx* c, const GridDev& g, const Weights<double>& W, L ld, E ep, int kind) {
+  constexpr int smem = zsmem_bytes<T, R, V, E>();
   static int per_sm = 0;  // resident blocks per SM of this kernel (dynamic smem above 48 KB needs an opt-in)
   if (!per_sm) {
-    CU(cudaFuncSetAttribute(zstream_kernel<T, R, L, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CU(cudaFuncSetAttribute(zstream_kernel<T, R, V, L, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int nb = 0;
-    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, zstream_kernel<T, R, L, E>, NT, smem));
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, zstream_kernel<T, R, V, L, E>, NT, smem));
     per_sm = std::max(nb, 1);
   }
+  const std::vector<long long> key = ztune_key((const void*)zstream_kernel<T, R, V, L, E>, g);
   int nz = 0;
-  if (!c->ztune.empty()) {
-    const std::vector<long long> key = ztune_key((const void*)zstream_kernel<T, R, L, E>, g);
+  if (c->force_nz >= 0) {
+    nz = c->force_nz;
+  } else {
     for (auto& t : c->ztune)
       if (t.first == key) {
         nz = t.second;
         break;
       }
   }
-  const ZShape s = zshape(c, g, R, per_sm, nz);
+  c->last_zkey = key;
+  const ZShape s = zshape<T>(c, g, R, per_sm, nz);
   if (E::K > 0) TRY(ensure_partials(c, s.nblocks, E::K));
   {
     ProfScope ps_(c, kind);
-    zstream_kernel<T, R, L, E><<<s.grid, dim3(BX, BY), smem, c->stream>>>(g, cast_weights<T>(W), s.zchunk, ld, ep,
-                                                                          red(c));
+    zstream_kernel<T, R, V, L, E><<<s.grid, dim3(BX, BY), smem, c->stream>>>(g, cast_weights<T>(W), s.zchunk, ld,
+                                                                             ep, red(c));
   }
   CU(cudaGetLastError());
   return OFDFT_OK;
+}
+
+template <typename T, int R, class L, class E>
+int launch_z(ofdft_ctx* c, const GridDev& g, const Weights<double>& W, L ld, E ep, int kind) {
+  if (zvec_ok<T>(g, ld, ep)) return launch_zv<T, R, 16 / (int)sizeof(T)>(c, g, W, ld, ep, kind);
+  return launch_zv<T, R, 1>(c, g, W, ld, ep, kind);
 }
 
 // Runtime radius -> template radius.

@@ -11,8 +11,20 @@
 namespace ofd {
 
 constexpr int BX = 32;  // threads along x (one warp per row)
-constexpr int BY = 8;   // rows per block
+constexpr int BY = 8;   // thread rows per block
 constexpr int NT = BX * BY;
+
+// Tile shape of the z-streaming passes per element type: each thread computes
+// RY consecutive rows (register blocking: the y-neighbours of its own rows come
+// from its registers, and the staging and synchronisation of a plane are shared
+// by RY outputs), so a block covers BX x TY nodes.  ZD = planes staged ahead of
+// use.  FP64 takes fewer rows and a shallower pipeline to keep two blocks per SM.
+template <typename T>
+struct ZCfg {
+  static constexpr int RY = sizeof(T) == 4 ? 4 : 2;
+  static constexpr int TY = BY * RY;
+  static constexpr int ZD = sizeof(T) == 4 ? 3 : 2;
+};
 
 // ---------------------------------------------------------------------------
 // Device scalars of one CG solve (S3).  Written only by the last block of a
@@ -36,7 +48,7 @@ struct CgScalars {
 // ---------------------------------------------------------------------------
 // z-streaming radius-R star stencil (Sec. 4, Eq. FD:Laplacian).
 //
-// A block owns a BX x BY column of nodes and a z-range [z0, z1).  It walks the
+// A block owns a BX x TY column of nodes and a z-range [z0, z1).  It walks the
 // range one plane at a time: the plane (with an R-wide x/y halo) is staged in
 // shared memory, the 2R+1 values of the block's own column along z live in a
 // register queue, so every node's 6R neighbours come from shared memory or
@@ -53,17 +65,20 @@ __device__ __forceinline__ double to_double(double v) { return v; }
 template <typename T>
 __device__ __forceinline__ double to_double(const DotAcc<T>& a) { return a.value(); }
 
-// Asynchronous 4- or 8-byte global -> shared copy; src_valid == false fills the
-// destination with zeros (the zero Dirichlet value of every out-of-grid node) and
-// reads nothing.
-template <typename T>
-__device__ __forceinline__ void cp_async_elem(T* dst, const T* src, bool src_valid) {
+// Asynchronous global -> shared copy of BYTES = 4, 8 or 16 bytes (16: both
+// addresses 16-byte aligned; bypasses L1).  src_valid == false fills the
+// destination with zeros (the zero Dirichlet value of every out-of-grid node)
+// and reads nothing.
+template <int BYTES>
+__device__ __forceinline__ void cp_async_bytes(void* dst, const void* src, bool src_valid) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  const int n = src_valid ? (int)sizeof(T) : 0;
-  if constexpr (sizeof(T) == 4)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
-  else
+  const int n = src_valid ? BYTES : 0;
+  if constexpr (BYTES == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+  else if constexpr (BYTES == 8)
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
@@ -71,94 +86,143 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// Depth of the plane pipeline and the shared-memory ring of planes it needs.
-constexpr int ZD = 3;
-template <typename T, int R>
+// Staging granularity V (elements per copy): 1, or 16 / sizeof(T) when the
+// grid's rows and the arrays are 16-byte aligned (zvec_width).  The x-halo is
+// staged RA = R rounded up to a multiple of V wide, so a staged row is
+// BX + 2 RA elements and every copy stays aligned.
+template <int R, int V>
+constexpr int zhalo_x() {
+  return ((R + V - 1) / V) * V;
+}
+// Shared-memory ring of R + ZD stencil planes (tile plus x/y halo).
+template <typename T, int R, int V>
 constexpr int zring_bytes() {
-  return (R + ZD) * (BY + 2 * R) * (BX + 2 * R) * (int)sizeof(T);
+  return (R + ZCfg<T>::ZD) * (ZCfg<T>::TY + 2 * R) * (BX + 2 * zhalo_x<R, V>()) * (int)sizeof(T);
 }
 // Dynamic shared memory of a z-streaming pass: the stencil-input ring plus a
 // ring of ZD planes for each pointwise input the epilogue declares (NIN).
-template <typename T, int R, class Epi>
+template <typename T, int R, int V, class Epi>
 constexpr int zsmem_bytes() {
-  return zring_bytes<T, R>() + ZD * Epi::NIN * BY * BX * (int)sizeof(T);
+  return zring_bytes<T, R, V>() + ZCfg<T>::ZD * Epi::NIN * ZCfg<T>::TY * BX * (int)sizeof(T);
 }
 
-// One block's share of a z-streaming pass: tile (bx, by) of the BX x BY column
-// grid, planes [z0, z1).  Planes are staged (tile plus an R-wide x/y halo) in a
-// shared-memory ring of R + ZD slots by cp.async, ZD planes ahead of use; the
-// block's own column along z lives in a register queue fed from the ring.  No
+// One block's share of a z-streaming pass: tile (bx, by) of BX x TY columns,
+// planes [z0, z1).  Planes are staged (tile plus an R-wide x/y halo) in a
+// shared-memory ring of R + ZD slots by cp.async, ZD planes ahead of use; each
+// thread's RY columns along z live in register queues fed from the ring.  No
 // register ever holds an in-flight load, so global latency overlaps compute.
-// nblocks / bid describe the reduction this block takes part in (the whole grid
-// for a single solve, one grid of a batch otherwise).  f is the stencil input.
-// The epilogue's NIN pointwise inputs (ep.input(j)) at the block's own nodes
-// travel in the same pipeline, so the epilogue never waits on a global load.
-template <typename T, int R, class Epi>
+// The staging work is a flat list over the (TY+2R) x (BX+2R) plane whose
+// in-plane offsets and validity each thread computes once; per plane only the
+// plane offset changes.  nblocks / bid describe the reduction this block takes
+// part in (the whole grid for a single solve, one grid of a batch otherwise).
+// f is the stencil input.  The epilogue's NIN pointwise inputs (ep.input(j)) at
+// the block's own nodes travel in the same pipeline, so the epilogue never
+// waits on a global load.  In-plane offsets are 32-bit (n1 * n2 < 2^31).
+template <typename T, int R, int V, class Epi>
 __device__ __forceinline__ void zstream_tile(const GridDev& g, const Weights<T>& W, int bx, int by, int z0, int z1,
-                                             const T* __restrict__ f, const Epi& ep, const RedBuf& red, int nblocks,
-                                             int bid) {
-  if (ep.skip()) return;
+                                             const T* __restrict__ f, const Epi& ep_in, const RedBuf& red,
+                                             int nblocks, int bid) {
+  if (ep_in.skip()) return;
+  Epi ep = ep_in;  // block-local copy: load() caches the epilogue's device scalars in registers
+  ep.load();
+  constexpr int RY = ZCfg<T>::RY, TY = ZCfg<T>::TY, ZD = ZCfg<T>::ZD;
   constexpr int NS = R + ZD;
-  constexpr int SY = BY + 2 * R, SX = BX + 2 * R;
+  constexpr int RA = zhalo_x<R, V>();
+  constexpr int SY = TY + 2 * R, SX = BX + 2 * RA, SP = SY * SX;
+  constexpr int CH = SX / V;                 // copies per staged row
+  constexpr int NE = (SY * CH + NT - 1) / NT;  // stencil copies per thread and plane
+  constexpr int ICH = TY * BX / V;           // copies per input plane
+  constexpr int NI = ICH / NT;               // input copies per thread, input and plane
   constexpr int NIN = Epi::NIN;
+  static_assert(NE <= 32 && NI * (NIN > 0 ? NIN : 1) <= 32, "staging masks hold 32 entries");
+  static_assert(ICH % NT == 0, "input planes split evenly over the threads");
   extern __shared__ __align__(16) unsigned char zsm_raw[];
-  T(*ring)[SY][SX] = reinterpret_cast<T(*)[SY][SX]>(zsm_raw);
-  T(*pin)[NIN > 0 ? NIN : 1][BY][BX] =
-      reinterpret_cast<T(*)[NIN > 0 ? NIN : 1][BY][BX]>(zsm_raw + zring_bytes<T, R>());
+  T(*ring)[SP] = reinterpret_cast<T(*)[SP]>(zsm_raw);
+  T(*pin)[NIN > 0 ? NIN : 1][TY * BX] =
+      reinterpret_cast<T(*)[NIN > 0 ? NIN : 1][TY * BX]>(zsm_raw + zring_bytes<T, R, V>());
   __shared__ double red_smem[(Epi::K > 0 ? Epi::K : 1) * (NT / 32)];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * BX + tx;
-  const int x = bx * BX + tx, y = by * BY + ty;
-  const bool in_xy = (x < g.n1) && (y < g.n2);
-  const long long col = (long long)x + (long long)g.n1 * y;
+  const int x = bx * BX + tx, y0 = by * TY + ty * RY;  // this thread's column x, rows y0 .. y0+RY-1
+  const bool in_x = x < g.n1;
   const long long plane = (long long)g.n1 * g.n2;
+  unsigned rows_ok = 0;  // bit i: node (x, y0 + i) is inside the grid
+#pragma unroll
+  for (int i = 0; i < RY; ++i)
+    if (in_x && y0 + i < g.n2) rows_ok |= 1u << i;
 
-  // halo nodes this thread stages: x-halo (tx < R) left/right, y-halo (ty < R) below/above
-  const int xl = bx * BX - R + tx, xr = bx * BX + BX + tx;
-  const int yb = by * BY - R + ty, yt = by * BY + BY + ty;
-  const bool hx = tx < R, hy = ty < R;
-  const bool okl = hx && y < g.n2 && xl >= 0, okr = hx && y < g.n2 && xr < g.n1;
-  const bool okb = hy && x < g.n1 && yb >= 0, okt = hy && x < g.n1 && yt < g.n2;
-  const long long il = (long long)g.n1 * y + xl, ir = (long long)g.n1 * y + xr;
-  const long long ib = (long long)g.n1 * yb + x, it = (long long)g.n1 * yt + x;
+  // this thread's share of a staged plane: copies e = tid + j NT of V
+  // elements, row e / CH and column V (e % CH) of the SY x SX tile-with-halo
+  // (shared offset V e), at in-plane offset soff[j] when inside the grid.  A
+  // copy lies wholly inside or wholly outside the grid (n1 % V == 0).
+  int soff[NE];
+  unsigned smask = 0;
+#pragma unroll
+  for (int j = 0; j < NE; ++j) {
+    const int e = tid + j * NT;
+    const int sy = e / CH, cx = e - sy * CH;
+    const int gx = bx * BX - RA + cx * V, gy = by * TY - R + sy;
+    const bool ok = e < SY * CH && gx >= 0 && gx + V <= g.n1 && gy >= 0 && gy < g.n2;
+    soff[j] = ok ? gy * g.n1 + gx : 0;
+    if (ok) smask |= 1u << j;
+  }
+  // and of each epilogue input plane: copies e = tid + m NT of the TY x BX tile
+  int ioff[NI > 0 ? NI : 1];
+  unsigned imask = 0;
+#pragma unroll
+  for (int m = 0; m < NI; ++m) {
+    const int e = tid + m * NT;
+    const int row = e / (BX / V), cx = e - row * (BX / V);
+    const int gx = bx * BX + cx * V, gy = by * TY + row;
+    const bool ok = gx + V <= g.n1 && gy < g.n2;
+    ioff[m] = ok ? gy * g.n1 + gx : 0;
+    if (ok) imask |= 1u << m;
+  }
 
   // stage plane p into ring slot sl and (for p - R inside the chunk) the
-  // epilogue inputs of plane p - R into input slot il_; one commit group per call
+  // epilogue inputs of plane p - R into input slot isl; one commit group per call
   auto stage = [&](int p, int sl, int isl) {
     const bool pv = (p >= 0) && (p < g.n3);
     const T* fp = f + plane * (long long)(pv ? p : 0);
-    cp_async_elem(&ring[sl][ty + R][tx + R], pv && in_xy ? fp + col : f, pv && in_xy);
-    if (hx) {
-      cp_async_elem(&ring[sl][ty + R][tx], pv && okl ? fp + il : f, pv && okl);
-      cp_async_elem(&ring[sl][ty + R][tx + BX + R], pv && okr ? fp + ir : f, pv && okr);
-    }
-    if (hy) {
-      cp_async_elem(&ring[sl][ty][tx + R], pv && okb ? fp + ib : f, pv && okb);
-      cp_async_elem(&ring[sl][ty + BY + R][tx + R], pv && okt ? fp + it : f, pv && okt);
+    T* dst = ring[sl];
+#pragma unroll
+    for (int j = 0; j < NE; ++j) {
+      const int e = tid + j * NT;
+      if (j < NE - 1 || e < SY * CH) {
+        const bool ok = pv && ((smask >> j) & 1u);
+        cp_async_bytes<V * (int)sizeof(T)>(dst + V * e, ok ? fp + soff[j] : f, ok);
+      }
     }
     if constexpr (NIN > 0) {
       const int pp = p - R;
       if (pp >= z0 && pp < z1) {
-        const long long o = plane * (long long)pp + col;
+        const long long o = plane * (long long)pp;
 #pragma unroll
         for (int j = 0; j < NIN; ++j) {
           const T* src = ep.input(j);
-          const bool v = in_xy && src != nullptr;
-          cp_async_elem(&pin[isl][j][ty][tx], v ? src + o : f, v);
+#pragma unroll
+          for (int m = 0; m < NI; ++m) {
+            const bool v = ((imask >> m) & 1u) && src != nullptr;
+            cp_async_bytes<V * (int)sizeof(T)>(&pin[isl][j][V * (tid + m * NT)], v ? src + o + ioff[m] : f, v);
+          }
         }
       }
     }
     cp_async_commit();
   };
 
-  // register queue of the own column along z (planes k-R .. k+R); the planes
+  // register queues of the own columns along z (planes k-R .. k+R); the planes
   // below the chunk and the first R of it come from plain loads
-  T q[2 * R + 1];
+  T q[RY][2 * R + 1];
 #pragma unroll
-  for (int i = 0; i < 2 * R; ++i) {
-    const int k = z0 - R + i;
-    q[i] = (in_xy && k >= 0 && k < g.n3) ? f[col + plane * k] : T(0);
-  }
+  for (int i = 0; i < RY; ++i)
+#pragma unroll
+    for (int m = 0; m < 2 * R; ++m) {
+      const int kk = z0 - R + m;
+      q[i][m] = (((rows_ok >> i) & 1u) && kk >= 0 && kk < g.n3)
+                    ? f[(long long)g.n1 * (y0 + i) + x + plane * kk]
+                    : T(0);
+    }
   // ring slots advance by one per plane (no integer division in the loop):
   // stencil plane p lives in slot (p - z0) mod NS, input plane p in (p - z0) mod ZD
   int s_stage = 0, i_stage = (ZD - R % ZD) % ZD;
@@ -173,31 +237,56 @@ __device__ __forceinline__ void zstream_tile(const GridDev& g, const Weights<T>&
 #pragma unroll
   for (int i = 0; i < (Epi::K > 0 ? Epi::K : 1); ++i) acc[i] = typename Epi::Acc();
 
-  int sk = 0, sf = R % NS, ik = 0;  // slots of plane k, plane k + R, inputs of plane k
+  const int cb = ty * RY * SX + tx + RA;  // ring offset of this thread's column in its lowest y-halo row
+  int sk = 0, sf = R % NS, ik = 0;       // slots of plane k, plane k + R, inputs of plane k
   for (int k = z0; k < z1; ++k) {
-    __syncthreads();                        // every thread is done with plane k-1's slot
+    __syncthreads();                          // every thread is done with plane k-1's slot
     stage(k + R + ZD - 1, s_stage, i_stage);  // refills that slot
     s_stage = bump(s_stage, NS);
     i_stage = bump(i_stage, ZD);
     cp_async_wait<ZD - 1>();  // planes <= k + R have landed (this thread's copies)
     __syncthreads();          // ... and every other thread's
-    q[2 * R] = ring[sf][ty + R][tx + R];
-    if (in_xy) {
-      T lap = W.c * q[R];
+    const T* pk = ring[sk] + cb;  // (row offset m, column 0) of plane k at pk[m * SX]
 #pragma unroll
-      for (int p = 1; p <= R; ++p) {
-        const T sx = ring[sk][ty + R][tx + R + p] + ring[sk][ty + R][tx + R - p];
-        const T sy = ring[sk][ty + R + p][tx + R] + ring[sk][ty + R - p][tx + R];
-        const T sz = q[R + p] + q[R - p];
-        lap = fma(W.w[p], (sx + sy) + sz, lap);
+    for (int i = 0; i < RY; ++i) q[i][2 * R] = ring[sf][cb + (i + R) * SX];
+    // the y-halo of the own rows in plane k (rows ty*RY - R .. ty*RY - 1 and
+    // ty*RY + RY .. ty*RY + RY + R - 1); the own rows' values are q[i][R]
+    T yl[R], yh[R];
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+      yl[m] = pk[m * SX];
+      yh[m] = pk[(RY + R + m) * SX];
+    }
+    auto ycol = [&](int m) -> T { return m < R ? yl[m] : (m >= RY + R ? yh[m - RY - R] : q[m - R][R]); };
+    // the RY rows' sums advance together (independent FMA chains); rows outside
+    // the grid read zeros and are computed but not applied
+    T lap[RY];
+#pragma unroll
+    for (int i = 0; i < RY; ++i) lap[i] = W.c * q[i][R];
+#pragma unroll
+    for (int p = 1; p <= R; ++p)
+#pragma unroll
+      for (int i = 0; i < RY; ++i) {
+        const T* row = pk + (i + R) * SX;
+        const T sx = row[p] + row[-p];
+        const T sy = ycol(i + R + p) + ycol(i + R - p);
+        const T sz = q[i][R + p] + q[i][R - p];
+        lap[i] = fma(W.w[p], (sx + sy) + sz, lap[i]);
       }
-      T vin[NIN > 0 ? NIN : 1];
+    const long long base = plane * k + (long long)g.n1 * y0 + x;
 #pragma unroll
-      for (int j = 0; j < NIN; ++j) vin[j] = pin[ik][j][ty][tx];
-      ep.apply(col + plane * k, q[R], lap, vin, acc);
+    for (int i = 0; i < RY; ++i) {
+      if ((rows_ok >> i) & 1u) {
+        T vin[NIN > 0 ? NIN : 1];
+#pragma unroll
+        for (int j = 0; j < NIN; ++j) vin[j] = pin[ik][j][(ty * RY + i) * BX + tx];
+        ep.apply(base + (long long)g.n1 * i, q[i][R], lap[i], vin, acc);
+      }
     }
 #pragma unroll
-    for (int i = 0; i < 2 * R; ++i) q[i] = q[i + 1];
+    for (int i = 0; i < RY; ++i)
+#pragma unroll
+      for (int m = 0; m < 2 * R; ++m) q[i][m] = q[i][m + 1];
     sk = bump(sk, NS);
     sf = bump(sf, NS);
     ik = bump(ik, ZD);
@@ -213,14 +302,14 @@ __device__ __forceinline__ void zstream_tile(const GridDev& g, const Weights<T>&
 }
 
 // Single grid: blocks tile (x, y) and split z into chunks of `zchunk` planes.
-template <typename T, int R, class Loader, class Epi>
-__global__ void __launch_bounds__(NT) zstream_kernel(GridDev g, Weights<T> W, int zchunk,
+template <typename T, int R, int V, class Loader, class Epi>
+__global__ void __launch_bounds__(NT, 2) zstream_kernel(GridDev g, Weights<T> W, int zchunk,
                                                      Loader ld, Epi ep, RedBuf red) {
   const int z0 = blockIdx.z * zchunk;
   const int z1 = min(z0 + zchunk, g.n3);
   const int nblocks = gridDim.x * gridDim.y * gridDim.z;
   const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-  zstream_tile<T, R>(g, W, blockIdx.x, blockIdx.y, z0, z1, ld.f, ep, red, nblocks, bid);
+  zstream_tile<T, R, V>(g, W, blockIdx.x, blockIdx.y, z0, z1, ld.f, ep, red, nblocks, bid);
 }
 
 // Batched: uneven grids packed into one launch (S11).  Block b works on
@@ -239,8 +328,8 @@ struct ZSlot {
   int nblocks;
 };
 
-template <typename T, int R, class Loader, class Epi>
-__global__ void __launch_bounds__(NT) zbatch_kernel(const ZTile* __restrict__ tiles,
+template <typename T, int R, int V, class Loader, class Epi>
+__global__ void __launch_bounds__(NT, 2) zbatch_kernel(const ZTile* __restrict__ tiles,
                                                     const ZSlot<T, Loader, Epi>* __restrict__ slots) {
   const ZTile t = tiles[blockIdx.x];
   const ZSlot<T, Loader, Epi>* S = slots + t.slot;
@@ -248,7 +337,7 @@ __global__ void __launch_bounds__(NT) zbatch_kernel(const ZTile* __restrict__ ti
   const Weights<T> W = S->W;
   const Epi ep = S->ep;
   const RedBuf red = S->red;
-  zstream_tile<T, R>(g, W, t.bx, t.by, t.z0, t.z1, S->ld.f, ep, red, S->nblocks, t.bid);
+  zstream_tile<T, R, V>(g, W, t.bx, t.by, t.z0, t.z1, S->ld.f, ep, red, S->nblocks, t.bid);
 }
 
 // Batched pointwise pass: block b works on elements [begin, end) of grid
@@ -262,16 +351,20 @@ struct PSeg {
 template <class Op>
 __global__ void __launch_bounds__(256) pbatch_kernel(const PSeg* __restrict__ segs, const Op* __restrict__ ops) {
   const PSeg sg = segs[blockIdx.x];
-  const Op op = ops[sg.slot];
+  Op op = ops[sg.slot];
   if (op.skip()) return;
+  op.load();  // the op's device scalars, once per block
   __shared__ double smem[(Op::K > 0 ? Op::K : 1) * (256 / 32)];
-  double acc[Op::K > 0 ? Op::K : 1];
+  typename Op::Acc acc[Op::K > 0 ? Op::K : 1];
 #pragma unroll
-  for (int i = 0; i < (Op::K > 0 ? Op::K : 1); ++i) acc[i] = 0.0;
+  for (int i = 0; i < (Op::K > 0 ? Op::K : 1); ++i) acc[i] = typename Op::Acc();
   for (long long i = sg.begin + threadIdx.x; i < sg.end; i += 256) op.apply(i, acc);
   if constexpr (Op::K > 0) {
+    double accd[Op::K];
+#pragma unroll
+    for (int i = 0; i < Op::K; ++i) accd[i] = to_double(acc[i]);
     Op fin = op;
-    grid_sum<Op::K, 256>(acc, smem, op.red, op.nblocks, sg.bid, threadIdx.x, fin);
+    grid_sum<Op::K, 256>(accd, smem, op.red, op.nblocks, sg.bid, threadIdx.x, fin);
   }
 }
 
@@ -292,7 +385,8 @@ struct EpiStore {
   using Acc = double;
   T* out;
   __device__ __forceinline__ bool skip() const { return false; }
-  __device__ __forceinline__ const T* input(int) const { return nullptr; }
+  __device__ __forceinline__ void load() {}
+  __host__ __device__ __forceinline__ const T* input(int) const { return nullptr; }
   __device__ __forceinline__ void apply(long long i, T, T lap, const T*, Acc*) const { out[i] = lap; }
   __device__ __forceinline__ void operator()(double*) const {}
 };
@@ -310,17 +404,22 @@ struct EpiCgA {
   T* p;
   T* q;
   CgScalars* sc;
+  int first_ = 0;  // copies of the CG scalars, read once per block by load()
+  T beta_ = T(0);
   __device__ __forceinline__ bool skip() const { return sc->done != 0; }
-  __device__ __forceinline__ const T* input(int j) const { return j == 0 ? p : q; }
+  __device__ __forceinline__ void load() {
+    first_ = sc->first;
+    beta_ = (T)sc->beta;
+  }
+  __host__ __device__ __forceinline__ const T* input(int j) const { return j == 0 ? p : q; }
   __device__ __forceinline__ void apply(long long i, T rc, T ar, const T* vin, Acc* acc) const {
     T pc, qc;
-    if (sc->first) {
+    if (first_) {
       pc = rc;
       qc = ar;
     } else {
-      const T be = (T)sc->beta;
-      pc = fma(be, vin[0], rc);
-      qc = fma(be, vin[1], ar);
+      pc = fma(beta_, vin[0], rc);
+      qc = fma(beta_, vin[1], ar);
     }
     p[i] = pc;
     q[i] = qc;
@@ -350,7 +449,8 @@ struct EpiResidual {
   int max_it;
   int want_r;
   __device__ __forceinline__ bool skip() const { return false; }
-  __device__ __forceinline__ const T* input(int) const { return nullptr; }
+  __device__ __forceinline__ void load() {}
+  __host__ __device__ __forceinline__ const T* input(int) const { return nullptr; }
   __device__ __forceinline__ void apply(long long i, T, T lap, const T*, double* acc) const {
     T uu = T(0);
     if (u) {
@@ -439,11 +539,15 @@ struct EpiFunctional {
   const double* sum_uu;  // device sum of u^2 (C_h = h^3 sum_uu - N)
   FuncScalars f;
   double* out;  // 11 sums + C
+  T mult_ = T(0);  // -eta + C/mu, from the device sum of u^2 (load())
   __device__ __forceinline__ bool skip() const { return false; }
-  __device__ __forceinline__ const T* input(int) const { return nullptr; }
-  __device__ __forceinline__ void apply(long long i, T uc, T lap, const T*, double* acc) const {
+  __device__ __forceinline__ void load() {
     const double C = f.h3 * *sum_uu - f.N;
-    const T mult = (T)(-f.eta + C * f.inv_mu);
+    mult_ = (T)(-f.eta + C * f.inv_mu);
+  }
+  __host__ __device__ __forceinline__ const T* input(int) const { return nullptr; }
+  __device__ __forceinline__ void apply(long long i, T uc, T lap, const T*, double* acc) const {
+    const T mult = mult_;
     const bool tf = f.terms & 1, vw = f.terms & 2, xc = f.terms & 4, es = f.terms & 8;
     const T ux = fabs(uc);
     T vk = T(0), vxc = T(0), exc = T(0), ph = T(0);
@@ -493,7 +597,25 @@ struct EpiFunctional {
 // x += alpha p, r -= alpha q, reduces r.r; the last block sets beta, counts the
 // iteration and raises `done` at convergence or at the iteration cap.  X is the
 // iterate's type: T, or double for the mixed CG (FP32 r, p, q, FP64 iterate).
-template <typename T, typename X = T>
+// 16-byte vector of T (the wide path of the pointwise CG update).
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using type = float4;
+  __device__ static void get(const type& v, float* o) { o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w; }
+  __device__ static type make(const float* o) { return make_float4(o[0], o[1], o[2], o[3]); }
+};
+template <>
+struct Vec16<double> {
+  using type = double2;
+  __device__ static void get(const type& v, double* o) { o[0] = v.x; o[1] = v.y; }
+  __device__ static type make(const double* o) { return make_double2(o[0], o[1]); }
+};
+
+// WIDE: every array 16-byte aligned, G a multiple of 16 / sizeof(T) and X == T;
+// each thread then moves whole 16-byte vectors (two per pass).
+template <typename T, typename X = T, bool WIDE = false>
 __global__ void __launch_bounds__(256) cg_update_kernel(long long G, X* __restrict__ phi,
                                                         T* __restrict__ r, const T* __restrict__ p,
                                                         const T* __restrict__ Ap, CgScalars* sc,
@@ -503,29 +625,73 @@ __global__ void __launch_bounds__(256) cg_update_kernel(long long G, X* __restri
   const T alpha = (T)sc->alpha;
   const X alpha_x = (X)sc->alpha;
   DotAcc<T> dacc;
-  // four independent elements per thread and pass keep several loads in flight
-  const long long stride = (long long)gridDim.x * 1024;
-  for (long long i0 = (long long)blockIdx.x * 1024 + threadIdx.x; i0 < G; i0 += stride) {
-    T pv[4], av[4], rv[4];
-    X xv[4];
+  if constexpr (WIDE) {
+    static_assert(sizeof(X) == sizeof(T), "the wide update needs X == T");
+    using VT = typename Vec16<T>::type;
+    constexpr int VW = 16 / (int)sizeof(T);
+    const long long nv = G / VW;
+    const VT* p4 = reinterpret_cast<const VT*>(p);
+    const VT* a4 = reinterpret_cast<const VT*>(Ap);
+    VT* x4 = reinterpret_cast<VT*>(phi);
+    VT* r4 = reinterpret_cast<VT*>(r);
+    const long long stride = (long long)gridDim.x * 512;
+    for (long long v0 = (long long)blockIdx.x * 512 + threadIdx.x; v0 < nv; v0 += stride) {
+      VT pv[2], av[2], xv[2], rv[2];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const long long i = i0 + 256 * u;
-      if (i < G) {
-        pv[u] = p[i];
-        av[u] = Ap[i];
-        xv[u] = phi[i];
-        rv[u] = r[i];
+      for (int u = 0; u < 2; ++u) {
+        const long long v = v0 + 256 * u;
+        if (v < nv) {
+          pv[u] = p4[v];
+          av[u] = a4[v];
+          xv[u] = x4[v];
+          rv[u] = r4[v];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const long long v = v0 + 256 * u;
+        if (v < nv) {
+          T pe[VW], ae[VW], xe[VW], re[VW];
+          Vec16<T>::get(pv[u], pe);
+          Vec16<T>::get(av[u], ae);
+          Vec16<T>::get(xv[u], xe);
+          Vec16<T>::get(rv[u], re);
+#pragma unroll
+          for (int l = 0; l < VW; ++l) {
+            xe[l] = fma(alpha, pe[l], xe[l]);
+            re[l] = fma(-alpha, ae[l], re[l]);
+            dacc.add(re[l], re[l]);
+          }
+          x4[v] = Vec16<T>::make(xe);
+          r4[v] = Vec16<T>::make(re);
+        }
       }
     }
+  } else {
+    // four independent elements per thread and pass keep several loads in flight
+    const long long stride = (long long)gridDim.x * 1024;
+    for (long long i0 = (long long)blockIdx.x * 1024 + threadIdx.x; i0 < G; i0 += stride) {
+      T pv[4], av[4], rv[4];
+      X xv[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const long long i = i0 + 256 * u;
-      if (i < G) {
-        phi[i] = fma(alpha_x, (X)pv[u], xv[u]);
-        const T ri = fma(-alpha, av[u], rv[u]);
-        r[i] = ri;
-        dacc.add(ri, ri);
+      for (int u = 0; u < 4; ++u) {
+        const long long i = i0 + 256 * u;
+        if (i < G) {
+          pv[u] = p[i];
+          av[u] = Ap[i];
+          xv[u] = phi[i];
+          rv[u] = r[i];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const long long i = i0 + 256 * u;
+        if (i < G) {
+          phi[i] = fma(alpha_x, (X)pv[u], xv[u]);
+          const T ri = fma(-alpha, av[u], rv[u]);
+          r[i] = ri;
+          dacc.add(ri, ri);
+        }
       }
     }
   }
@@ -645,6 +811,13 @@ static __global__ void __launch_bounds__(256) fold_kernel(long long G, double* p
   }
 }
 
+// phi += t (phi - phi0): linear extrapolation of the potential along a line
+// search (warm start of the next Poisson solve).
+static __global__ void __launch_bounds__(256) extrap_kernel(long long G, double* phi, const double* phi0, double t) {
+  for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < G; i += (long long)gridDim.x * 256)
+    phi[i] = fma(t, phi[i] - phi0[i], phi[i]);
+}
+
 template <typename S, typename D>
 __global__ void __launch_bounds__(256) convert_kernel(long long G, D* out, const S* in) {
   for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < G; i += (long long)gridDim.x * 256)
@@ -663,13 +836,19 @@ struct OpCgUpdate {
   CgScalars* sc;
   RedBuf red;
   int nblocks;
+  using Acc = DotAcc<T>;
+  T al_ = T(0);
+  X alx_ = X(0);
   __device__ __forceinline__ bool skip() const { return sc->done != 0; }
-  __device__ __forceinline__ void apply(long long i, double* acc) const {
-    const T al = (T)sc->alpha;
-    x[i] = fma((X)sc->alpha, (X)p[i], x[i]);
-    const T ri = fma(-al, q[i], r[i]);
+  __device__ __forceinline__ void load() {
+    al_ = (T)sc->alpha;
+    alx_ = (X)sc->alpha;
+  }
+  __device__ __forceinline__ void apply(long long i, Acc* acc) const {
+    x[i] = fma(alx_, (X)p[i], x[i]);
+    const T ri = fma(-al_, q[i], r[i]);
     r[i] = ri;
-    acc[0] += (double)ri * (double)ri;
+    acc[0].add(ri, ri);
   }
   __device__ __forceinline__ void operator()(double* t) const {
     const double rr_new = t[0];
@@ -690,6 +869,8 @@ struct OpAxpyAbs {
   const T* a;
   const T* b;
   double alpha;
+  using Acc = double;
+  __device__ __forceinline__ void load() {}
   __device__ __forceinline__ bool skip() const { return false; }
   __device__ __forceinline__ void apply(long long i, double*) const { out[i] = fabs(fma((T)alpha, b[i], a[i])); }
   __device__ __forceinline__ void operator()(double*) const {}
@@ -702,6 +883,8 @@ struct OpDirection {
   T* d;
   const T* s;
   double beta;
+  using Acc = double;
+  __device__ __forceinline__ void load() {}
   __device__ __forceinline__ bool skip() const { return false; }
   __device__ __forceinline__ void apply(long long i, double*) const {
     d[i] = (beta == 0.0) ? s[i] : fma((T)beta, d[i], s[i]);
@@ -720,6 +903,8 @@ struct OpDot2 {
   double* out;
   RedBuf red;
   int nblocks;
+  using Acc = double;
+  __device__ __forceinline__ void load() {}
   __device__ __forceinline__ bool skip() const { return false; }
   __device__ __forceinline__ void apply(long long i, double* acc) const {
     acc[0] += (double)a[i] * (double)b[i];
@@ -738,6 +923,8 @@ struct OpRank1 {
   T* s;
   const T* w;
   double gamma;
+  using Acc = double;
+  __device__ __forceinline__ void load() {}
   __device__ __forceinline__ bool skip() const { return false; }
   __device__ __forceinline__ void apply(long long i, double*) const { s[i] = fma(-(T)gamma, w[i], s[i]); }
   __device__ __forceinline__ void operator()(double*) const {}
@@ -753,6 +940,8 @@ struct OpRefineReplace {
   int budget, restart;
   RedBuf red;
   int nblocks;
+  using Acc = double;
+  __device__ __forceinline__ void load() {}
   __device__ __forceinline__ bool skip() const { return false; }
   __device__ __forceinline__ void apply(long long i, double* acc) const {
     const float v = (float)r64[i];
@@ -781,10 +970,31 @@ struct OpFold {
   static constexpr int K = 0;
   double* phi64;
   float* e;
+  using Acc = double;
+  __device__ __forceinline__ void load() {}
   __device__ __forceinline__ bool skip() const { return false; }
   __device__ __forceinline__ void apply(long long i, double*) const {
     phi64[i] += (double)e[i];
     e[i] = 0.0f;
+  }
+  __device__ __forceinline__ void operator()(double*) const {}
+};
+
+// Warm start of a line search's Poisson solves on one grid: t == 0 records
+// phi0 = phi (the origin), otherwise phi += t (phi - phi0) (as extrap_kernel).
+struct OpLine {
+  static constexpr int K = 0;
+  double* phi;
+  double* phi0;
+  double t;
+  using Acc = double;
+  __device__ __forceinline__ void load() {}
+  __device__ __forceinline__ bool skip() const { return false; }
+  __device__ __forceinline__ void apply(long long i, double*) const {
+    if (t == 0.0)
+      phi0[i] = phi[i];
+    else
+      phi[i] = fma(t, phi[i] - phi0[i], phi[i]);
   }
   __device__ __forceinline__ void operator()(double*) const {}
 };
@@ -794,6 +1004,8 @@ struct OpConvert {
   static constexpr int K = 0;
   D* out;
   const S* in;
+  using Acc = double;
+  __device__ __forceinline__ void load() {}
   __device__ __forceinline__ bool skip() const { return false; }
   __device__ __forceinline__ void apply(long long i, double*) const { out[i] = (D)in[i]; }
   __device__ __forceinline__ void operator()(double*) const {}

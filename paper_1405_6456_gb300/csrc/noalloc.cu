@@ -48,10 +48,10 @@ int scratch_address(void** out) {
 template <int R>
 cudaError_t launch_stencil_pass(dim3 grid, int zchunk, const GridDev& g, const Weights<double>& W,
                                 const double* f, EpiResidual<double> ep, RedBuf red, cudaStream_t s) {
-  constexpr int smem = zsmem_bytes<double, R, EpiResidual<double>>();
-  cudaFuncSetAttribute(zstream_kernel<double, R, LoadPlain<double>, EpiResidual<double>>,
+  constexpr int smem = zsmem_bytes<double, R, 1, EpiResidual<double>>();
+  cudaFuncSetAttribute(zstream_kernel<double, R, 1, LoadPlain<double>, EpiResidual<double>>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  zstream_kernel<double, R, LoadPlain<double>, EpiResidual<double>>
+  zstream_kernel<double, R, 1, LoadPlain<double>, EpiResidual<double>>
       <<<grid, dim3(BX, BY), smem, s>>>(g, W, zchunk, LoadPlain<double>{f}, ep, red);
   return cudaGetLastError();
 }
@@ -85,7 +85,7 @@ extern "C" int ofdft_poisson_noalloc(const ofdft_grid* gr, int fd_order, const d
   const int R = fd_order / 2;
   const Weights<double> W = lap_weights(R, gr->h, 1.0), Wneg = lap_weights(R, gr->h, -1.0);
   // launch shape of the library's single-grid passes (152 SMs assumed for the split)
-  const int gx = (g.n1 + BX - 1) / BX, gy = (g.n2 + BY - 1) / BY;
+  const int gx = (g.n1 + BX - 1) / BX, gy = (g.n2 + ZCfg<double>::TY - 1) / ZCfg<double>::TY;
   int nz = std::max(1, (608 + gx * gy - 1) / (gx * gy));
   nz = std::min(nz, std::max(1, g.n3 / std::max(2 * R, 4)));
   const int zc = (g.n3 + nz - 1) / nz;
@@ -115,10 +115,10 @@ extern "C" int ofdft_poisson_noalloc(const ofdft_grid* gr, int fd_order, const d
       switch (R) {
 #define NA_CG(RR)                                                                                                \
   case RR: {                                                                                                     \
-    constexpr int smem = zsmem_bytes<double, RR, EpiCgA<double>>();                                                              \
-    cudaFuncSetAttribute(zstream_kernel<double, RR, LoadPlain<double>, EpiCgA<double>>,                        \
+    constexpr int smem = zsmem_bytes<double, RR, 1, EpiCgA<double>>();                                         \
+    cudaFuncSetAttribute(zstream_kernel<double, RR, 1, LoadPlain<double>, EpiCgA<double>>,                     \
                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);                                     \
-    zstream_kernel<double, RR, LoadPlain<double>, EpiCgA<double>>                                                \
+    zstream_kernel<double, RR, 1, LoadPlain<double>, EpiCgA<double>>                                             \
         <<<zgrid, dim3(BX, BY), smem, s>>>(g, cast_weights<double>(Wneg), zc, LoadPlain<double>{r},             \
                                           EpiCgA<double>{pv, qv, sc}, red);                                      \
   } break;
