@@ -55,8 +55,12 @@ enum { OFDFT_PREC_FP64 = 0, OFDFT_PREC_MIXED = 1 };
 enum { OFDFT_TERM_TF = 1, OFDFT_TERM_VW = 2, OFDFT_TERM_XC = 4, OFDFT_TERM_ES = 8,
        OFDFT_TERM_ALL = 15 };
 
-/* constraint treatment: Algorithm 1, or the penalty method (eta_q = 0, Sec. 5.3.2) */
-enum { OFDFT_METHOD_AL = 0, OFDFT_METHOD_PENALTY = 1 };
+/* constraint treatment (Sec. 5.3.2): Algorithm 1 (augmented Lagrangian), the
+ * penalty method (Algorithm 1 with eta_q = 0), or the Lagrange-multiplier method
+ * (PR nonlinear CG on the sphere h^3 sum u^2 = N with the gradient projected
+ * orthogonal to u, eta = G_E.u / (2 u.u), Brent's line search on the angle of
+ * the norm-preserving rotation; single solves only: the batch engine rejects it) */
+enum { OFDFT_METHOD_AL = 0, OFDFT_METHOD_PENALTY = 1, OFDFT_METHOD_LM = 2 };
 
 /* force expression: Eq. Force:Nuclei with the FD gradient of Sec. 4 (paper), or
  * the exact derivative of the discrete energy at fixed grid (exact). */
@@ -97,6 +101,10 @@ typedef struct {
   int max_backtrack;  /* halvings of the secant step while L does not decrease (0: none) */
   int precond_rank1;  /* 1: the preconditioner also inverts the rank-one term (4h^3/mu) u u^T
                          of the augmented Lagrangian's Hessian exactly (Sherman-Morrison) */
+  double poisson_adapt; /* c > 0: inside a solve's NLCG, Poisson solves stop at
+                           min(1e-4, max(tol_poisson, c tol_poisson sqrt(rs / (tol_inner M)))),
+                           rs = h^3 r.s at the current point: loose while the gradient is
+                           large, tol_poisson as the NLCG converges; 0: always tol_poisson */
 } ofdft_params;
 
 typedef struct {
@@ -121,6 +129,7 @@ typedef struct {
   double E, eta, C;   /* E*, eta* (Algorithm 1 output), C_h(u*) */
   ofdft_energy parts; /* terms at u* */
   int outer_iters, nlcg_iters, grad_evals, cg_iters;
+  int energy_evals;       /* energy-only evaluations (line searches of OFDFT_METHOD_LM) */
   long long stencil_apps; /* "matrix-vector products" counted as in Sec. 5.3 */
   int converged;
   ofdft_grid grid;    /* grid the solve used */
@@ -316,6 +325,12 @@ int ofdft_poisson_noalloc(const ofdft_grid* g, int fd_order, const double* rho, 
 /* Device bytes a solve of this grid needs in the context workspace (for
  * admission control by callers that pack several solves on one device). */
 long long ofdft_workspace_bytes(const ofdft_grid* g, int fd_order, int prec);
+
+/* sizeof of the named ABI struct ("ofdft_grid", "ofdft_params", "ofdft_cg_stats",
+ * "ofdft_energy", "ofdft_solve_stats", "ofdft_counters"), or -1 for any other
+ * name: lets a binding check its struct layouts against the library's.  Host
+ * only, no context needed. */
+long long ofdft_struct_bytes(const char* name);
 
 #ifdef __cplusplus
 }

@@ -48,7 +48,7 @@ int tune_cg_split(ofdft_ctx* c, int R, const GridDev& g, const Weights<double>& 
   const std::vector<long long> tkey = {(long long)sizeof(T), R, g.n1, g.n2, g.n3, vec16};
   for (auto& t : c->ztuned)
     if (t == tkey) return OFDFT_OK;
-  const std::vector<int> cand = {0, 1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64};
+  const std::vector<int> cand = {0, 1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 14, 16, 20, 24, 32, 48, 64};
   TRY(ensure_partials(c, zshape<T>(c, g, R, 1, 64).nblocks, 1));  // largest candidate
   CU(cudaMalloc(&pv, g.G * sizeof(T)));
   if (cudaMalloc(&qv, g.G * sizeof(T)) != cudaSuccess) {
@@ -346,7 +346,8 @@ template <typename T>
 int functional_pass(ofdft_ctx* c, int R, const GridDev& g, double h, const ofdft_params* p, const T* u,
                     const T* b, const T* phi, const T* rcg, double eta, double mu, double N,
                     const double* sum_uu_dev, T* G, T* s, const T* d, const T* s_old, EvalOut* out,
-                    T* winv = nullptr) {
+                    T* winv = nullptr, const double* phi64 = nullptr, const double* b64 = nullptr,
+                    const double* r64 = nullptr) {
   const Weights<double> W = lap_weights(R, h, 1.0);
   FuncScalars f;
   f.h3 = h * h * h;
@@ -359,8 +360,86 @@ int functional_pass(ofdft_ctx* c, int R, const GridDev& g, double h, const ofdft
   f.terms = p->terms;
   const bool es = p->terms & OFDFT_TERM_ES;
   EpiFunctional<T> ep{es ? phi : nullptr, b, es ? rcg : nullptr, d, s_old, G, s, winv, sum_uu_dev, f, c->scal};
+  if (es && phi64) {
+    ep.phi64 = phi64;
+    ep.b64 = b64;
+    ep.r64 = r64;
+  }
   TRY(launch_z_r<T>(c, R, g, W, LoadPlain<T>{u}, ep, OFDFT_K_FUNCTIONAL));
   TRY(sync_scalars(c, c->scal, 12 * sizeof(double), out->sums));
+  return OFDFT_OK;
+}
+
+#define TRY_PLAIN(expr)       \
+  do {                        \
+    const int rc_ = (expr);   \
+    if (rc_ != OFDFT_OK) return rc_; \
+  } while (0)
+
+// Brent's minimiser (1973): parabolic steps through the three best points,
+// golden-section steps when a parabola is not trusted, on a bracket a < x < b
+// (or b < x < a) with f(x) below both ends.  f(t, &value) returns a status;
+// rel_tol bounds the final bracket relative to |x|.  Returns the status and
+// leaves the best abscissa/value in *xmin / *fmin.
+template <class F>
+int brent_minimise(F&& f, double a, double x, double b, double fx, double rel_tol, int max_it, double* xmin,
+                   double* fmin) {
+  constexpr double kGold = 0.38196601125010515;  // (3 - sqrt 5) / 2
+  double lo = std::min(a, b), hi = std::max(a, b);
+  double second = x, third = x, f2 = fx, f3 = fx;  // second- and third-best points
+  double last_step = 0.0, step = 0.0;
+  for (int it = 0; it < max_it; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    const double tol1 = rel_tol * fabs(x) + 1e-12, tol2 = 2.0 * tol1;
+    if (fabs(x - mid) <= tol2 - 0.5 * (hi - lo)) break;
+    bool parabolic = false;
+    if (fabs(last_step) > tol1) {
+      const double r = (x - second) * (fx - f3);
+      double q = (x - third) * (fx - f2);
+      double num = (x - third) * q - (x - second) * r;
+      q = 2.0 * (q - r);
+      if (q > 0.0) num = -num;
+      q = fabs(q);
+      const double older = last_step;
+      last_step = step;
+      // accept the parabola's minimum if it lies inside the bracket and the
+      // step is less than half of the step before last
+      if (fabs(num) < fabs(0.5 * q * older) && num > q * (lo - x) && num < q * (hi - x)) {
+        step = num / q;
+        if ((x + step) - lo < tol2 || hi - (x + step) < tol2) step = (x < mid) ? tol1 : -tol1;
+        parabolic = true;
+      }
+    }
+    if (!parabolic) {
+      last_step = (x >= mid) ? lo - x : hi - x;
+      step = kGold * last_step;
+    }
+    const double t = (fabs(step) >= tol1) ? x + step : x + (step > 0.0 ? tol1 : -tol1);
+    double ft = 0.0;
+    TRY_PLAIN(f(t, &ft));
+    if (ft <= fx) {
+      (t >= x ? lo : hi) = x;
+      third = second;
+      f3 = f2;
+      second = x;
+      f2 = fx;
+      x = t;
+      fx = ft;
+    } else {
+      (t < x ? lo : hi) = t;
+      if (ft <= f2 || second == x) {
+        third = second;
+        f3 = f2;
+        second = t;
+        f2 = ft;
+      } else if (ft <= f3 || third == x || third == second) {
+        third = t;
+        f3 = ft;
+      }
+    }
+  }
+  *xmin = x;
+  *fmin = fx;
   return OFDFT_OK;
 }
 
@@ -380,6 +459,7 @@ struct Solver {
   double* phi64;  // mixed: FP64 potential
   double* phi0;   // FP64 potential at the origin of the current line search
   double line_l = 0.0;  // position along d of the last Poisson solve (0: none yet)
+  double tol_p = 0.0;   // Poisson tolerance of the next evaluations (adaptive_poisson_tol)
   ofdft_solve_stats* stats;
   ofdft_energy e;  // at the current point
   int trace = 0;   // OFDFT_TRACE=1: one line per evaluation on stderr
@@ -401,11 +481,11 @@ struct Solver {
     if (es) {
       int rc;
       if (!mixed)
-        rc = poisson_fp64(c, R, g, h, nullptr, (const double*)at, (const double*)b, (double*)phi, p->tol_poisson,
-                          p->max_cg, &cs);
+        rc = poisson_fp64(c, R, g, h, nullptr, (const double*)at, (const double*)b, (double*)phi, tol_p, p->max_cg,
+                          &cs);
       else
-        rc = poisson_mixed(c, R, g, h, nullptr, (const float*)at, b64, phi64, (float*)phi, p->tol_poisson,
-                           p->max_cg, std::max(p->refine_every, 1), &cs);
+        rc = poisson_mixed(c, R, g, h, nullptr, (const float*)at, b64, phi64, (float*)phi, tol_p, p->max_cg,
+                           std::max(p->refine_every, 1), &cs);
       if (rc != OFDFT_OK) return rc;
       stats->stencil_apps += cs.iterations + 1;
       stats->cg_iters += cs.iterations;
@@ -419,22 +499,12 @@ struct Solver {
       CU(cudaGetLastError());
       sum_uu = c->scal + 16;
     }
-    const T* rcg = nullptr;
-    if (es) {
-      if (mixed) {
-        // FP32 copy of the FP64 residual for the phi.r energy term
-        const int pb = pointwise_blocks(c, g.G);
-        {
-          ProfScope ps_(c, OFDFT_K_VECTOR);
-          convert_kernel<double, float><<<pb, 256, 0, c->stream>>>(g.G, vec<float>(c, V_R), vec<double>(c, V_R64));
-        }
-        CU(cudaGetLastError());
-      }
-      rcg = vec<T>(c, V_R);
-    }
+    // the phi.r energy term uses the Poisson solve's residual (FP64 in MIXED)
+    const T* rcg = (es && !mixed) ? vec<T>(c, V_R) : nullptr;
     EvalOut o;
     T* winv = (p->precond_rank1 && sout) ? vec<T>(c, V_W) : nullptr;
-    TRY(functional_pass<T>(c, R, g, h, p, at, b, phi, rcg, eta, mu, N, sum_uu, Gout, sout, dd, s_old, &o, winv));
+    TRY(functional_pass<T>(c, R, g, h, p, at, b, phi, rcg, eta, mu, N, sum_uu, Gout, sout, dd, s_old, &o, winv,
+                           mixed ? phi64 : nullptr, mixed ? b64 : nullptr, mixed ? vec<double>(c, V_R64) : nullptr));
     stats->stencil_apps += 2;
     stats->grad_evals += 1;
     fill_energy(o, h, p, E_self, ezz, eta, mu, out);
@@ -518,6 +588,7 @@ struct Solver {
         *converged = 1;
         break;
       }
+      tol_p = adaptive_poisson_tol(p, e.rs, M);
       if (!isfinite(e.L) || !isfinite(e.rs)) return fail(c, OFDFT_ENONFINITE, "augmented Lagrangian is not finite");
       stats->nlcg_iters++;
       T* s_old = s;
@@ -549,7 +620,7 @@ struct Solver {
         e = et;
       } else {
         T* snew = sn;
-        const double L0 = e.L;
+        const double L0 = e.L + l_resolution(e, mixed);
         double pos = 0.0;  // position of u along d
         for (int j = 1; j <= p->max_secant; ++j) {
           alpha = alpha * gcur / (gprev - gcur);
@@ -587,6 +658,150 @@ struct Solver {
       }
     }
     if (!*converged && e.rs < tol_in) *converged = 1;
+    return OFDFT_OK;
+  }
+
+  // ---- Lagrange-multiplier method (Sec. 5.3.2) --------------------------------
+  int lincomb(T* out, const T* a, double ca, const T* bb, double cb, int take_abs) {
+    {
+      ProfScope ps_(c, OFDFT_K_VECTOR);
+      lincomb_kernel<T><<<pointwise_blocks(c, g.G), 256, 0, c->stream>>>(g.G, out, a, ca, bb, cb, take_abs);
+    }
+    CU(cudaGetLastError());
+    return OFDFT_OK;
+  }
+
+  // Energy E_h at `at` (no gradient); L = E with eta = 0 and 1/mu = 0.
+  int energy_at(const T* at, ofdft_energy* out) {
+    TRY(eval(at, nullptr, nullptr, nullptr, nullptr, 0.0, INFINITY, out));
+    stats->energy_evals++;
+    stats->grad_evals--;  // counted as an energy evaluation
+    return OFDFT_OK;
+  }
+
+  // PR nonlinear CG on the sphere h^3 sum u^2 = N: the energy gradient G_E at u,
+  // eta = G_E.u / (2 u.u), g = G_E - 2 eta u, s = -g / diag projected orthogonal
+  // to u, the Polak-Ribiere direction projected the same way, and a Brent line
+  // search on the angle t of u(t) = |cos t u + sin t d^|, d^ = d sqrt(N) / |d|,
+  // which keeps the norm.  Buffers: G holds g, s the direction of steepest
+  // preconditioned descent, sn the previous s, st the scaled direction d^, Gt
+  // the line's origin u0, ut the trial point.
+  int lm_stall = 0;  // 1: the LM line search found no lower energy along a descent direction
+
+  int lm(double* eta_out, int* converged) {
+    *converged = 0;
+    const double h3 = h * h * h;
+    const double tol_in = p->tol_inner * M;
+    const int pb = pointwise_blocks(c, g.G);
+    TRY(ensure_partials(c, pb, 2));
+    double r2[2];
+    // start on the sphere
+    TRY(dots(u, u, nullptr, nullptr, r2));
+    TRY(lincomb(u, u, sqrt(N / (h3 * r2[0])), nullptr, 0.0, 0));
+    CU(cudaMemsetAsync(sn, 0, g.G * sizeof(T), c->stream));
+    FuncScalars f;
+    const Weights<double> W = lap_weights(R, h, 1.0);
+    f.h3 = h3;
+    f.N = N;
+    f.inv_mu = 0.0;
+    f.lambda = p->lambda;
+    f.CF = 0.3 * pow(3.0 * kPi * kPi, 2.0 / 3.0);
+    f.kin_vw = -p->lambda * W.c;
+    f.terms = p->terms;
+    const bool es = p->terms & OFDFT_TERM_ES;
+    double eta = 0.0, delta = 0.0;
+    int k = 0;
+    T* u0 = Gt;
+    T* dh = st;
+    for (int it = 0; it <= p->max_nlcg; ++it) {
+      // G_E at u and G_E.u (the functional pass's <G, d> with d = u)
+      TRY(eval(u, G, nullptr, u, nullptr, 0.0, INFINITY, &e));
+      if (!isfinite(e.E)) return fail(c, OFDFT_ENONFINITE, "energy is not finite");
+      const double uu_h3 = e.C + N;  // h^3 u.u
+      eta = e.gd / (2.0 * uu_h3);
+      f.eta = eta;
+      {
+        ProfScope ps_(c, OFDFT_K_VECTOR);
+        lm_precond_kernel<T><<<pb, 256, 0, c->stream>>>(g.G, G, s, u, es ? phi : nullptr, f, c->scal + 16, red(c));
+      }
+      CU(cudaGetLastError());
+      TRY(sync_scalars(c, c->scal + 16, 2 * sizeof(double), r2));
+      const double uu = r2[1];
+      TRY(lincomb(s, s, 1.0, u, -r2[0] / uu, 0));  // s orthogonal to u
+      TRY(dots(G, s, G, sn, r2));
+      const double rs = -h3 * r2[0], rs_mid = -h3 * r2[1];
+      e.rs = rs;
+      e.rs_pc = rs;
+      if (trace) fprintf(stderr, "[ofdft] lm it %d E=%.12g eta=%.9f rs=%.4e\n", it, e.E, eta, rs);
+      if (rs < tol_in) {
+        if (tol_p > p->tol_poisson) {  // confirm at the full Poisson tolerance
+          tol_p = p->tol_poisson;
+          continue;
+        }
+        *converged = 1;
+        break;
+      }
+      if (it == p->max_nlcg) break;
+      tol_p = adaptive_poisson_tol(p, rs, M);
+      stats->nlcg_iters++;
+      const double beta = (it == 0) ? 0.0 : (rs - rs_mid) / delta;
+      delta = rs;
+      ++k;
+      const bool restart = (it == 0 || k >= p->restart_every || !(beta > 0.0));
+      if (restart) k = 0;
+      TRY(direction(restart ? 0.0 : beta));
+      TRY(dots(d, u, nullptr, nullptr, r2));
+      TRY(lincomb(d, d, 1.0, u, -r2[0] / uu, 0));  // d orthogonal to u
+      TRY(dots(G, d, d, d, r2));
+      double gdot = r2[0], dd = r2[1];
+      if (!(gdot < 0.0)) {  // not a descent direction: restart along s
+        TRY(direction(0.0));
+        k = 0;
+        TRY(dots(d, d, nullptr, nullptr, r2));
+        dd = r2[0];
+      }
+      std::swap(s, sn);  // this s is the next iteration's s_old
+      const double dnorm = sqrt(h3 * dd);
+      if (!(dnorm > 0.0)) break;
+      TRY(lincomb(dh, d, sqrt(N) / dnorm, nullptr, 0.0, 0));
+      CU(cudaMemcpyAsync(u0, u, g.G * sizeof(T), cudaMemcpyDeviceToDevice, c->stream));
+      auto E_at = [&](double t, double* val) -> int {
+        TRY(lincomb(ut, u0, cos(t), dh, sin(t), 1));
+        ofdft_energy et;
+        TRY(energy_at(ut, &et));
+        if (!isfinite(et.E)) return fail(c, OFDFT_ENONFINITE, "energy is not finite on the line search");
+        *val = et.E;
+        return OFDFT_OK;
+      };
+      // bracket the minimum along t, then Brent
+      double ta = 0.0, fa = e.E;
+      double tb = std::min(dnorm / sqrt(N), 0.3), fb = 0.0;
+      TRY(E_at(tb, &fb));
+      for (int sh = 0; sh < 30 && fb >= fa; ++sh) {
+        tb *= 0.25;
+        TRY(E_at(tb, &fb));
+      }
+      if (fb >= fa) {  // no decrease along d: stop where we are (phi back at u for the forces)
+        TRY(eval(u, G, nullptr, u, nullptr, 0.0, INFINITY, &e));
+        e.rs = rs;
+        lm_stall = 1;
+        break;
+      }
+      double tc = 2.0 * tb, fc = 0.0;
+      TRY(E_at(tc, &fc));
+      for (int gr = 0; gr < 40 && fc < fb; ++gr) {
+        ta = tb;
+        fa = fb;
+        tb = tc;
+        fb = fc;
+        tc = 1.618034 * tb;
+        TRY(E_at(tc, &fc));
+      }
+      double tmin = tb, fmin = fb;
+      TRY(brent_minimise(E_at, ta, tb, tc, fb, 1e-4, 60, &tmin, &fmin));
+      TRY(lincomb(u, u0, cos(tmin), dh, sin(tmin), 1));
+    }
+    *eta_out = eta;
     return OFDFT_OK;
   }
 };
@@ -791,6 +1006,29 @@ int device_ezz(ofdft_ctx* c, const double* R_host, const double* Z_host, int M, 
   return OFDFT_OK;
 }
 
+// Results of a solve at its final state: energy, stats, forces at phi* (S9).
+template <typename T>
+int finish_solve(ofdft_ctx* c, Solver<T>& S, const ofdft_grid* gr, int R, const double* R_host, const double* Z_host,
+                 int M, const ofdft_params* p, void* u_out, void* phi_out, double* energy, double* forces,
+                 ofdft_solve_stats* st, int converged, const double* Fz, const char* notconv) {
+  const size_t es = sizeof(T);
+  st->E = S.e.E;
+  st->C = S.e.C;
+  st->parts = S.e;
+  st->converged = converged;
+  st->grid = *gr;
+  *energy = S.e.E;
+  if (forces) {
+    TRY(device_forces<T>(c, gr, R, R_host, Z_host, M, p->sigma, p->rc, p->force_variant, S.phi, forces));
+    if (p->ezz_correction)
+      for (int i = 0; i < 3 * M; ++i) forces[i] += Fz[i];
+  }
+  if (u_out) CU(cudaMemcpyAsync(u_out, S.u, S.g.G * es, cudaMemcpyDeviceToDevice, c->stream));
+  if (phi_out) CU(cudaMemcpyAsync(phi_out, S.phi, S.g.G * es, cudaMemcpyDeviceToDevice, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return converged ? OFDFT_OK : fail(c, OFDFT_ENOTCONV, "%s", notconv);
+}
+
 template <typename T>
 int solve_impl(ofdft_ctx* c, const ofdft_grid* gr, const double* R_host, const double* Z_host, int M,
                const ofdft_params* p, void* u_out, void* phi_out, double* energy, double* forces,
@@ -834,6 +1072,7 @@ int solve_impl(ofdft_ctx* c, const ofdft_grid* gr, const double* R_host, const d
   S.phi64 = mixed ? vec<double>(c, V_PHI64) : nullptr;
   TRY(ensure(c, c->v[V_PHI0], g.G * sizeof(double)));
   S.phi0 = vec<double>(c, V_PHI0);
+  S.tol_p = (p->poisson_adapt > 0.0) ? std::max(p->tol_poisson, 1e-4) : p->tol_poisson;  // first solve from phi = 0
   // S1: pseudocharge (FP64 for the mixed path too), starting guess, phi = 0
   if (!mixed) {
     TRY(device_pseudocharge<double>(c, gr, R, R_host, Z_host, M, p->sigma, p->rc, (double*)S.b, &S.E_self));
@@ -851,12 +1090,23 @@ int solve_impl(ofdft_ctx* c, const ofdft_grid* gr, const double* R_host, const d
   S.ezz = 0.0;
   std::vector<double> Fz(3 * (size_t)M, 0.0);
   if (p->ezz_correction) TRY(device_ezz(c, R_host, Z_host, M, p->sigma, &S.ezz, Fz.data()));
+  int converged = 0;
+  if (p->method == OFDFT_METHOD_LM) {
+    double eta_lm = 0.0;
+    TRY(S.lm(&eta_lm, &converged));
+    st->eta = eta_lm;
+    st->outer_iters = 1;
+    return finish_solve(c, S, gr, R, R_host, Z_host, M, p, u_out, phi_out, energy, forces, st, converged,
+                        Fz.data(),
+                        S.lm_stall ? "the Lagrange-multiplier line search found no lower energy before h^3 r.s "
+                                     "reached tol_inner (energy resolution of the precision)"
+                                   : "the Lagrange-multiplier method reached max_nlcg");
+  }
   // Algorithm 1
   double eta = (p->method == OFDFT_METHOD_PENALTY) ? 0.0 : p->eta0;
   double mu = p->mu0;
   TRY(S.eval(S.u, S.G, S.s, nullptr, nullptr, eta, mu, &S.e));
   double E_prev = S.e.E;
-  int converged = 0;
   const double tolE = p->tol_E * M;
   for (int q = 0; q < p->max_outer; ++q) {
     int inner_ok = 0;
@@ -874,32 +1124,25 @@ int solve_impl(ofdft_ctx* c, const ofdft_grid* gr, const double* R_host, const d
     }
     E_prev = E;
   }
-  st->E = S.e.E;
-  st->C = S.e.C;
-  st->parts = S.e;
-  st->converged = converged;
-  st->grid = *gr;
-  *energy = S.e.E;
-  // S9: forces at phi*
-  if (forces) {
-    TRY(device_forces<T>(c, gr, R, R_host, Z_host, M, p->sigma, p->rc, p->force_variant, S.phi, forces));
-    if (p->ezz_correction)
-      for (int i = 0; i < 3 * M; ++i) forces[i] += Fz[i];
+  if (S.tol_p > p->tol_poisson) {
+    // the last potential may come from a loose solve (poisson_adapt): the
+    // reported energy and the forces use one solved to tol_poisson
+    S.tol_p = p->tol_poisson;
+    TRY(S.eval(S.u, nullptr, nullptr, nullptr, nullptr, eta, mu, &S.e));
   }
-  if (u_out) CU(cudaMemcpyAsync(u_out, S.u, g.G * es, cudaMemcpyDeviceToDevice, c->stream));
-  if (phi_out) CU(cudaMemcpyAsync(phi_out, S.phi, g.G * es, cudaMemcpyDeviceToDevice, c->stream));
-  CU(cudaStreamSynchronize(c->stream));
-  return converged ? OFDFT_OK : fail(c, OFDFT_ENOTCONV, "Algorithm 1 reached %d outer iterations", p->max_outer);
+  return finish_solve(c, S, gr, R, R_host, Z_host, M, p, u_out, phi_out, energy, forces, st, converged, Fz.data(),
+                      "Algorithm 1 reached max_outer");
 }
 
 int check_params(ofdft_ctx* c, const ofdft_params* p) {
   if (!p) return fail(c, OFDFT_EINVAL, "params is NULL");
   TRY(check_order(c, p->fd_order));
   TRY(check_prec(c, p->precision));
-  if (p->method != OFDFT_METHOD_AL && p->method != OFDFT_METHOD_PENALTY)
-    return fail(c, OFDFT_EINVAL, "method must be OFDFT_METHOD_AL or OFDFT_METHOD_PENALTY");
+  if (p->method != OFDFT_METHOD_AL && p->method != OFDFT_METHOD_PENALTY && p->method != OFDFT_METHOD_LM)
+    return fail(c, OFDFT_EINVAL, "method must be OFDFT_METHOD_AL, OFDFT_METHOD_PENALTY or OFDFT_METHOD_LM");
   if (!(p->mu0 > 0.0) || !(p->kappa > 0.0 && p->kappa < 1.0))
     return fail(c, OFDFT_EINVAL, "Algorithm 1 needs mu0 > 0 and 0 < kappa < 1");
+  if (!(p->poisson_adapt >= 0.0)) return fail(c, OFDFT_EINVAL, "poisson_adapt must be >= 0");
   if (!(p->tol_poisson > 0.0) || p->max_cg < 1 || p->max_nlcg < 0 || p->max_outer < 1 || p->max_secant < 1)
     return fail(c, OFDFT_EINVAL, "tolerances must be positive and iteration caps >= 1");
   if (!(p->sigma > 0.0) || !(p->rc > 0.0)) return fail(c, OFDFT_EINVAL, "sigma and rc must be positive");
@@ -959,6 +1202,7 @@ void ofdft_default_params(ofdft_params* p) {
   p->trial_max_rel = 0.2;
   p->max_backtrack = 2;
   p->precond_rank1 = 1;
+  p->poisson_adapt = 1.0;
 }
 
 int ofdft_create(ofdft_ctx** out, int device, void* stream) {
@@ -1076,6 +1320,18 @@ int ofdft_grid_for_atoms(const double* R, int M, double h, double vacuum, int ro
   }
   g->h = h;
   return OFDFT_OK;
+}
+
+long long ofdft_struct_bytes(const char* name) {
+  if (!name) return -1;
+  const std::string n(name);
+  if (n == "ofdft_grid") return (long long)sizeof(ofdft_grid);
+  if (n == "ofdft_params") return (long long)sizeof(ofdft_params);
+  if (n == "ofdft_cg_stats") return (long long)sizeof(ofdft_cg_stats);
+  if (n == "ofdft_energy") return (long long)sizeof(ofdft_energy);
+  if (n == "ofdft_solve_stats") return (long long)sizeof(ofdft_solve_stats);
+  if (n == "ofdft_counters") return (long long)sizeof(ofdft_counters);
+  return -1;
 }
 
 long long ofdft_workspace_bytes(const ofdft_grid* g, int fd_order, int prec) {
@@ -1213,11 +1469,6 @@ int ofdft_energy_grad(ofdft_ctx* c, const ofdft_grid* g, const ofdft_params* p, 
                              &cs);
       if (rc != OFDFT_OK && !(rc == OFDFT_ENOTCONV && !solve_poisson)) return rc;
       c->err.clear();
-      {
-        ProfScope ps_(c, OFDFT_K_VECTOR);
-        convert_kernel<double, float><<<pb, 256, 0, c->stream>>>(gd.G, vec<float>(c, V_R), vec<double>(c, V_R64));
-      }
-      CU(cudaGetLastError());
     }
   } else {
     const int pb = pointwise_blocks(c, gd.G);
@@ -1243,9 +1494,10 @@ int ofdft_energy_grad(ofdft_ctx* c, const ofdft_grid* g, const ofdft_params* p, 
                                 es ? vec<double>(c, V_R) : nullptr, eta, mu, N, sum_uu, (double*)grad, (double*)s,
                                 (const double*)d, (const double*)s_old, &o, r1 ? vec<double>(c, V_W) : nullptr));
   else
-    TRY(functional_pass<float>(c, R, gd, g->h, p, (const float*)u, (const float*)b, (const float*)phi,
-                               es ? vec<float>(c, V_R) : nullptr, eta, mu, N, sum_uu, (float*)grad, (float*)s,
-                               (const float*)d, (const float*)s_old, &o, r1 ? vec<float>(c, V_W) : nullptr));
+    TRY(functional_pass<float>(c, R, gd, g->h, p, (const float*)u, (const float*)b, (const float*)phi, nullptr, eta,
+                               mu, N, sum_uu, (float*)grad, (float*)s, (const float*)d, (const float*)s_old, &o,
+                               r1 ? vec<float>(c, V_W) : nullptr, es ? vec<double>(c, V_PHI64) : nullptr,
+                               es ? vec<double>(c, V_B64) : nullptr, es ? vec<double>(c, V_R64) : nullptr));
   fill_energy(o, g->h, p, E_self, 0.0, eta, mu, out);
   if (r1) {
     // the preconditioned residual includes the exact inverse of the rank-one term (4 h^3/mu) u u^T

@@ -30,6 +30,7 @@ enum SlotState {
   S_TRIAL,         // got the evaluation at the trial point
   S_SECANT,        // got the evaluation at a secant candidate
   S_AL_UPDATE,     // multiplier update of Algorithm 1
+  S_FINAL,         // got the final evaluation at tol_poisson (after loose adaptive solves)
   S_DONE
 };
 
@@ -92,6 +93,7 @@ struct Slot {
   std::vector<Vop<T>> vops;
   std::vector<double> line_ops;  // OpLine parameters, applied before the next evaluation
   double line_l = 0.0, pos = 0.0;  // last solve's position along d; position of u along d
+  double tol_p = 0.0;              // Poisson tolerance of the next evaluations (adaptive_poisson_tol)
   // Poisson phase (within a round)
   int pphase = 0, ptotal = 0;
   ofdft_cg_stats pstats;
@@ -357,7 +359,7 @@ struct Engine {
     if (!mixed) {
       TRY((zpass<T, LoadPlain<T>, EpiResidual<T>>(ev, OFDFT_K_RESIDUAL, 1.0, [&](Slot<T>* S) {
         return std::make_pair(LoadPlain<T>{S->phi}, EpiResidual<T>{nullptr, S->ev_at, S->b, S->r, B->sc + S->index,
-                                                                  S->p.tol_poisson, S->p.max_cg, 1});
+                                                                  S->tol_p, S->p.max_cg, 1});
       })));
       TRY(read_scalars());
       std::vector<Slot<T>*> run;
@@ -387,7 +389,7 @@ struct Engine {
           resid, OFDFT_K_RESIDUAL, 1.0, [&](Slot<T>* S) {
             return std::make_pair(LoadPlain<double>{S->phi64},
                                   EpiResidual<double, float, double>{nullptr, (const float*)S->ev_at, S->b64, S->r64,
-                                                                     B->sc + S->index, S->p.tol_poisson, S->p.max_cg,
+                                                                     B->sc + S->index, S->tol_p, S->p.max_cg,
                                                                      1});
           })));
       TRY(read_scalars());
@@ -397,14 +399,14 @@ struct Engine {
         const double bb = h.bb > 0 ? h.bb : 1.0;
         S->pstats.iterations = S->ptotal;
         S->pstats.rel_residual = sqrt(h.rr / bb);
-        if (h.rr <= S->p.tol_poisson * S->p.tol_poisson * bb || S->ptotal >= S->p.max_cg || !isfinite(h.rr)) continue;
+        if (h.rr <= S->tol_p * S->tol_p * bb || S->ptotal >= S->p.max_cg || !isfinite(h.rr)) continue;
         corr.push_back(S);
       }
       if (corr.empty()) break;
       TRY((ppass<OpRefineReplace>(corr, OFDFT_K_VECTOR, [&](Slot<T>* S, int nb) {
         const int budget = std::min(std::max(S->p.refine_every, 1), S->p.max_cg - S->ptotal);
         const CgScalars& h = B->h_sc[S->index];
-        const double itol = mixed_inner_tol(h.rr, h.bb > 0 ? h.bb : 1.0, S->p.tol_poisson);
+        const double itol = mixed_inner_tol(h.rr, h.bb > 0 ? h.bb : 1.0, S->tol_p);
         return OpRefineReplace{(float*)S->r, S->r64, B->sc32 + S->index, itol, budget, S->pphase, slot_red(S), nb};
       })));
       TRY(read_scalars());
@@ -422,12 +424,9 @@ struct Engine {
       for (Slot<T>* S : corr) S->ptotal += std::max(B->h_sc32[S->index].iters - before[S->index], 1);
       resid.swap(corr);
     }
-    // FP32 potential for the functional and FP32 copy of the FP64 residual (phi.r term)
+    // FP32 potential (the gradient and the forces take it)
     TRY((ppass<OpConvert<double, float>>(ev, OFDFT_K_VECTOR, [&](Slot<T>* S, int) {
       return OpConvert<double, float>{(float*)S->phi, S->phi64};
-    })));
-    TRY((ppass<OpConvert<double, float>>(ev, OFDFT_K_VECTOR, [&](Slot<T>* S, int) {
-      return OpConvert<double, float>{(float*)S->r, S->r64};
     })));
     return OFDFT_OK;
   }
@@ -447,9 +446,14 @@ struct Engine {
       f.kin_vw = -S->p.lambda * W.c;
       f.terms = S->p.terms;
       const bool es = S->p.terms & OFDFT_TERM_ES;
-      EpiFunctional<T> ep{es ? S->phi : nullptr, S->b, es ? S->r : nullptr, S->ev_d, S->ev_sold, S->ev_G, S->ev_s,
-                          (S->p.precond_rank1 && S->ev_s) ? S->w : nullptr, &B->sc[S->index].sum_uu, f,
-                          B->out + 16 * S->index};
+      EpiFunctional<T> ep{es ? S->phi : nullptr, S->b, (es && !mixed) ? S->r : nullptr, S->ev_d, S->ev_sold,
+                          S->ev_G, S->ev_s, (S->p.precond_rank1 && S->ev_s) ? S->w : nullptr,
+                          &B->sc[S->index].sum_uu, f, B->out + 16 * S->index};
+      if (es && mixed) {  // FP64 potential, pseudocharge and residual (as the single-solve path)
+        ep.phi64 = S->phi64;
+        ep.b64 = S->b64;
+        ep.r64 = S->r64;
+      }
       return std::make_pair(LoadPlain<T>{S->ev_at}, ep);
     })));
     CU(cudaMemcpyAsync(B->h_out.data(), B->out, B->capacity * 16 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -605,6 +609,7 @@ struct Engine {
             S->state = S_AL_UPDATE;
             continue;
           }
+          S->tol_p = adaptive_poisson_tol(&p, S->e.rs, S->M);
           S->stats.nlcg_iters++;
           S->s_old = S->s;
           S->redo_dots = 0;
@@ -644,7 +649,7 @@ struct Engine {
             goto direction;
           }
           S->snew = S->sn;
-          S->L0 = S->e.L;
+          S->L0 = S->e.L + l_resolution(S->e, mixed);
           S->j = 1;
           S->alpha = S->alpha * S->gcur / (S->gprev - S->gcur);
           S->bt = 0;
@@ -694,19 +699,30 @@ struct Engine {
           if (p.method == OFDFT_METHOD_AL) S->eta = eta_eff;
           S->mu = p.kappa * S->mu;
           S->q++;
-          if (fabs(E - S->E_prev) < p.tol_E * S->M) {
-            S->stats.converged = 1;
-            finish(S, OFDFT_OK, nullptr);
-            return;
-          }
+          const bool conv = fabs(E - S->E_prev) < p.tol_E * S->M;
           S->E_prev = E;
-          if (S->q >= p.max_outer) {
-            finish(S, OFDFT_ENOTCONV, "Algorithm 1 reached max_outer");
-            return;
+          if (conv || S->q >= p.max_outer) {
+            S->stats.converged = conv ? 1 : 0;
+            if (S->tol_p > p.tol_poisson) {
+              // as ofdft_solve: the reported energy and the forces use a
+              // potential solved to tol_poisson
+              S->tol_p = p.tol_poisson;
+              request_eval(S, S->u, nullptr, nullptr, nullptr, nullptr, &S->e);
+              S->state = S_FINAL;
+              return;
+            }
+            S->state = S_FINAL;
+            continue;
           }
           S->state = S_NLCG_START;
           continue;
         }
+        case S_FINAL:
+          if (S->stats.converged)
+            finish(S, OFDFT_OK, nullptr);
+          else
+            finish(S, OFDFT_ENOTCONV, "Algorithm 1 reached max_outer");
+          return;
         default:
           return;
       }
@@ -788,6 +804,7 @@ struct Engine {
     if (S->p.ezz_correction) TRY(device_ezz(c, S->R.data(), S->Z.data(), S->M, S->p.sigma, &S->ezz, S->Fz.data()));
     S->eta = (S->p.method == OFDFT_METHOD_PENALTY) ? 0.0 : S->p.eta0;
     S->mu = S->p.mu0;
+    S->tol_p = (S->p.poisson_adapt > 0.0) ? std::max(S->p.tol_poisson, 1e-4) : S->p.tol_poisson;
     S->state = S_AL_START;
     S->stats.grid = S->grid;
     return OFDFT_OK;
@@ -963,6 +980,8 @@ int ofdft_batch_submit(ofdft_batch* b, const double* R, const double* Z, int M, 
   ofdft_ctx* c = b->c;
   c->err.clear();
   TRY(check_params(c, p));
+  if (p->method == OFDFT_METHOD_LM)
+    return fail(c, OFDFT_EINVAL, "the batch engine runs Algorithm 1 (AL or penalty); use ofdft_solve for LM");
   TRY(check_atoms(c, R, Z, M));
   if (p->precision != b->prec) return fail(c, OFDFT_EINVAL, "request precision differs from the batch precision");
   if (b->prec == OFDFT_PREC_FP64) return submit_impl<double>(b, R, Z, M, h, p, grid, request_id);

@@ -266,6 +266,25 @@ inline int pointwise_blocks(ofdft_ctx* c, long long G) {
 // the resident block slots (SMs x blocks per SM) in whole waves: a grid just
 // above a wave would leave a nearly empty second wave.  z-chunks are at least
 // 2R planes deep unless the grid is too small to fill the GPU at all.
+// Poisson tolerance inside a solve's NLCG at a point with h^3 r.s = rs (see
+// ofdft_params.poisson_adapt): the gradient's error from an inexact potential
+// only has to stay small against the gradient itself.
+inline double adaptive_poisson_tol(const ofdft_params* p, double rs, int M) {
+  if (!(p->poisson_adapt > 0.0) || !(rs > 0.0) || !isfinite(rs)) return p->tol_poisson;
+  const double t = p->poisson_adapt * p->tol_poisson * sqrt(rs / (p->tol_inner * M));
+  return std::max(p->tol_poisson, std::min(1e-4, t));
+}
+
+// Resolution of L in a MIXED evaluation: the FP32 energy densities (TF, vW
+// with the FP32 stencil, XC) carry rounding noise that measured about 1e-9 of the
+// summed magnitudes of the energy terms on the 666-atom cluster; a secant step
+// whose L rises by less than that is not a rise the evaluation can resolve.
+// FP64 evaluations resolve far below any step the NLCG takes: 0.
+inline double l_resolution(const ofdft_energy& e, bool mixed) {
+  if (!mixed) return 0.0;
+  return 1e-9 * (fabs(e.E_tf) + fabs(e.E_vw) + fabs(e.E_xc) + fabs(e.E_es));
+}
+
 // Relative tolerance of one FP32 round of the mixed Poisson CG: cut the FP32
 // residual by 1e-4 (the reduction FP32 recurrences track faithfully), but not
 // below half of what the FP64 stopping test still asks for (||r|| <= tol ||b||),

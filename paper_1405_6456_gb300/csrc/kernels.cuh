@@ -21,9 +21,37 @@ constexpr int NT = BX * BY;
 // use.  FP64 takes fewer rows and a shallower pipeline to keep two blocks per SM.
 template <typename T>
 struct ZCfg {
-  static constexpr int RY = sizeof(T) == 4 ? 4 : 2;
-  static constexpr int TY = BY * RY;
+  static constexpr int CX = sizeof(T) == 4 ? 2 : 1;  // adjacent columns per thread (packed FP32 pairs)
+  static constexpr int RY = 2;                       // rows per thread
+  static constexpr int THX = BX / CX;                // threads along a tile row
+  static constexpr int TY = (NT / THX) * RY;         // rows per tile
   static constexpr int ZD = sizeof(T) == 4 ? 3 : 2;
+};
+
+// Arithmetic on a thread's CX adjacent columns: one FP64 value, or an FP32 pair
+// computed with the packed FP32x2 instructions (each lane rounds as the scalar
+// operation does, so results equal the one-column code's bit for bit).
+template <typename T, int CX>
+struct Lanes;
+template <typename T>
+struct Lanes<T, 1> {
+  using V = T;
+  __device__ static V ld(const T* p) { return *p; }
+  __device__ static V add(V a, V b) { return a + b; }
+  __device__ static V mul(T w, V a) { return w * a; }
+  __device__ static V fma(T w, V a, V c) { return ::fma(w, a, c); }
+  __device__ static V make(const T* v) { return v[0]; }
+  __device__ static T lane(V v, int) { return v; }
+};
+template <>
+struct Lanes<float, 2> {
+  using V = float2;
+  __device__ static V ld(const float* p) { return *reinterpret_cast<const float2*>(p); }
+  __device__ static V add(V a, V b) { return __fadd2_rn(a, b); }
+  __device__ static V mul(float w, V a) { return __fmul2_rn(make_float2(w, w), a); }
+  __device__ static V fma(float w, V a, V c) { return __ffma2_rn(make_float2(w, w), a, c); }
+  __device__ static V make(const float* v) { return make_float2(v[0], v[1]); }
+  __device__ static float lane(V v, int l) { return l == 0 ? v.x : v.y; }
 };
 
 // ---------------------------------------------------------------------------
@@ -87,17 +115,19 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 // Staging granularity V (elements per copy): 1, or 16 / sizeof(T) when the
-// grid's rows and the arrays are 16-byte aligned (zvec_width).  The x-halo is
-// staged RA = R rounded up to a multiple of V wide, so a staged row is
-// BX + 2 RA elements and every copy stays aligned.
-template <int R, int V>
+// grid's rows and the arrays are 16-byte aligned (zvec_ok).  The x-halo is
+// staged RA = R rounded up to a multiple of V and of CX wide, so a staged row is
+// BX + 2 RA elements, every copy stays aligned and a thread's column pair starts
+// on an even element.
+template <typename T, int R, int V>
 constexpr int zhalo_x() {
-  return ((R + V - 1) / V) * V;
+  constexpr int m = V > ZCfg<T>::CX ? V : ZCfg<T>::CX;
+  return ((R + m - 1) / m) * m;
 }
 // Shared-memory ring of R + ZD stencil planes (tile plus x/y halo).
 template <typename T, int R, int V>
 constexpr int zring_bytes() {
-  return (R + ZCfg<T>::ZD) * (ZCfg<T>::TY + 2 * R) * (BX + 2 * zhalo_x<R, V>()) * (int)sizeof(T);
+  return (R + ZCfg<T>::ZD) * (ZCfg<T>::TY + 2 * R) * (BX + 2 * zhalo_x<T, R, V>()) * (int)sizeof(T);
 }
 // Dynamic shared memory of a z-streaming pass: the stencil-input ring plus a
 // ring of ZD planes for each pointwise input the epilogue declares (NIN).
@@ -109,47 +139,52 @@ constexpr int zsmem_bytes() {
 // One block's share of a z-streaming pass: tile (bx, by) of BX x TY columns,
 // planes [z0, z1).  Planes are staged (tile plus an R-wide x/y halo) in a
 // shared-memory ring of R + ZD slots by cp.async, ZD planes ahead of use; each
-// thread's RY columns along z live in register queues fed from the ring.  No
-// register ever holds an in-flight load, so global latency overlaps compute.
-// The staging work is a flat list over the (TY+2R) x (BX+2R) plane whose
-// in-plane offsets and validity each thread computes once; per plane only the
-// plane offset changes.  nblocks / bid describe the reduction this block takes
-// part in (the whole grid for a single solve, one grid of a batch otherwise).
-// f is the stencil input.  The epilogue's NIN pointwise inputs (ep.input(j)) at
-// the block's own nodes travel in the same pipeline, so the epilogue never
-// waits on a global load.  In-plane offsets are 32-bit (n1 * n2 < 2^31).
+// thread owns CX adjacent columns times RY rows, whose values along z live in
+// register queues fed from the ring.  No register ever holds an in-flight load,
+// so global latency overlaps compute.  The staging work is a flat list over the
+// staged plane whose in-plane offsets and validity each thread computes once;
+// per plane only the plane offset changes.  nblocks / bid describe the reduction
+// this block takes part in (the whole grid for a single solve, one grid of a
+// batch otherwise).  f is the stencil input.  The epilogue's NIN pointwise
+// inputs (ep.input(j)) at the block's own nodes travel in the same pipeline, so
+// the epilogue never waits on a global load.  In-plane offsets are 32-bit
+// (n1 * n2 < 2^31).
 template <typename T, int R, int V, class Epi>
 __device__ __forceinline__ void zstream_tile(const GridDev& g, const Weights<T>& W, int bx, int by, int z0, int z1,
                                              const T* __restrict__ f, const Epi& ep_in, const RedBuf& red,
                                              int nblocks, int bid) {
-  if (ep_in.skip()) return;
   Epi ep = ep_in;  // block-local copy: load() caches the epilogue's device scalars in registers
-  ep.load();
-  constexpr int RY = ZCfg<T>::RY, TY = ZCfg<T>::TY, ZD = ZCfg<T>::ZD;
+  constexpr int CX = ZCfg<T>::CX, RY = ZCfg<T>::RY, THX = ZCfg<T>::THX, TY = ZCfg<T>::TY, ZD = ZCfg<T>::ZD;
+  using L = Lanes<T, CX>;
+  using VT = typename L::V;
   constexpr int NS = R + ZD;
-  constexpr int RA = zhalo_x<R, V>();
+  constexpr int RA = zhalo_x<T, R, V>();
   constexpr int SY = TY + 2 * R, SX = BX + 2 * RA, SP = SY * SX;
   constexpr int CH = SX / V;                 // copies per staged row
   constexpr int NE = (SY * CH + NT - 1) / NT;  // stencil copies per thread and plane
   constexpr int ICH = TY * BX / V;           // copies per input plane
   constexpr int NI = ICH / NT;               // input copies per thread, input and plane
   constexpr int NIN = Epi::NIN;
+  constexpr int RE = ((R + CX - 1) / CX) * CX;  // x-window half width (a multiple of CX)
+  constexpr int NWIN = 2 * RE + CX;             // x-window of a row: columns x0 - RE .. x0 + CX - 1 + RE
   static_assert(NE <= 32 && NI * (NIN > 0 ? NIN : 1) <= 32, "staging masks hold 32 entries");
   static_assert(ICH % NT == 0, "input planes split evenly over the threads");
+  static_assert(RE <= RA, "the x-window stays inside the staged halo");
   extern __shared__ __align__(16) unsigned char zsm_raw[];
   T(*ring)[SP] = reinterpret_cast<T(*)[SP]>(zsm_raw);
   T(*pin)[NIN > 0 ? NIN : 1][TY * BX] =
       reinterpret_cast<T(*)[NIN > 0 ? NIN : 1][TY * BX]>(zsm_raw + zring_bytes<T, R, V>());
   __shared__ double red_smem[(Epi::K > 0 ? Epi::K : 1) * (NT / 32)];
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int tid = ty * BX + tx;
-  const int x = bx * BX + tx, y0 = by * TY + ty * RY;  // this thread's column x, rows y0 .. y0+RY-1
-  const bool in_x = x < g.n1;
+  const int tid = threadIdx.y * BX + threadIdx.x;
+  const int tx = tid % THX, ty = tid / THX;  // column group and row group of this thread
+  const int x0 = bx * BX + CX * tx, y0 = by * TY + ty * RY;  // first column and first row
   const long long plane = (long long)g.n1 * g.n2;
-  unsigned rows_ok = 0;  // bit i: node (x, y0 + i) is inside the grid
+  unsigned node_ok = 0;  // bit i * CX + l: node (x0 + l, y0 + i) is inside the grid
 #pragma unroll
   for (int i = 0; i < RY; ++i)
-    if (in_x && y0 + i < g.n2) rows_ok |= 1u << i;
+#pragma unroll
+    for (int l = 0; l < CX; ++l)
+      if (x0 + l < g.n1 && y0 + i < g.n2) node_ok |= 1u << (i * CX + l);
 
   // this thread's share of a staged plane: copies e = tid + j NT of V
   // elements, row e / CH and column V (e % CH) of the SY x SX tile-with-halo
@@ -211,17 +246,21 @@ __device__ __forceinline__ void zstream_tile(const GridDev& g, const Weights<T>&
     cp_async_commit();
   };
 
-  // register queues of the own columns along z (planes k-R .. k+R); the planes
+  // register queues of the own nodes along z (planes k-R .. k+R); the planes
   // below the chunk and the first R of it come from plain loads
-  T q[RY][2 * R + 1];
+  VT q[RY][2 * R + 1];
 #pragma unroll
   for (int i = 0; i < RY; ++i)
 #pragma unroll
     for (int m = 0; m < 2 * R; ++m) {
       const int kk = z0 - R + m;
-      q[i][m] = (((rows_ok >> i) & 1u) && kk >= 0 && kk < g.n3)
-                    ? f[(long long)g.n1 * (y0 + i) + x + plane * kk]
-                    : T(0);
+      T v[CX];
+#pragma unroll
+      for (int l = 0; l < CX; ++l)
+        v[l] = (((node_ok >> (i * CX + l)) & 1u) && kk >= 0 && kk < g.n3)
+                   ? f[(long long)g.n1 * (y0 + i) + x0 + l + plane * kk]
+                   : T(0);
+      q[i][m] = L::make(v);
     }
   // ring slots advance by one per plane (no integer division in the loop):
   // stencil plane p lives in slot (p - z0) mod NS, input plane p in (p - z0) mod ZD
@@ -233,12 +272,20 @@ __device__ __forceinline__ void zstream_tile(const GridDev& g, const Weights<T>&
     i_stage = bump(i_stage, ZD);
   }
 
+  // the epilogue's device scalars (and whether the pass has anything to do)
+  // are read while the first planes are in flight
+  if (ep.skip()) {
+    cp_async_wait<0>();  // no copy may land in shared memory after the block exits
+    return;
+  }
+  ep.load();
+
   typename Epi::Acc acc[Epi::K > 0 ? Epi::K : 1];
 #pragma unroll
   for (int i = 0; i < (Epi::K > 0 ? Epi::K : 1); ++i) acc[i] = typename Epi::Acc();
 
-  const int cb = ty * RY * SX + tx + RA;  // ring offset of this thread's column in its lowest y-halo row
-  int sk = 0, sf = R % NS, ik = 0;       // slots of plane k, plane k + R, inputs of plane k
+  const int cb = ty * RY * SX + CX * tx + RA;  // ring offset of this thread's first column, lowest y-halo row
+  int sk = 0, sf = R % NS, ik = 0;            // slots of plane k, plane k + R, inputs of plane k
   for (int k = z0; k < z1; ++k) {
     __syncthreads();                          // every thread is done with plane k-1's slot
     stage(k + R + ZD - 1, s_stage, i_stage);  // refills that slot
@@ -246,43 +293,52 @@ __device__ __forceinline__ void zstream_tile(const GridDev& g, const Weights<T>&
     i_stage = bump(i_stage, ZD);
     cp_async_wait<ZD - 1>();  // planes <= k + R have landed (this thread's copies)
     __syncthreads();          // ... and every other thread's
-    const T* pk = ring[sk] + cb;  // (row offset m, column 0) of plane k at pk[m * SX]
+    const T* pk = ring[sk] + cb;  // (row offset m, first column) of plane k at pk[m * SX]
 #pragma unroll
-    for (int i = 0; i < RY; ++i) q[i][2 * R] = ring[sf][cb + (i + R) * SX];
-    // the y-halo of the own rows in plane k (rows ty*RY - R .. ty*RY - 1 and
-    // ty*RY + RY .. ty*RY + RY + R - 1); the own rows' values are q[i][R]
-    T yl[R], yh[R];
+    for (int i = 0; i < RY; ++i) q[i][2 * R] = L::ld(ring[sf] + cb + (i + R) * SX);
+    // y-neighbours: the R rows below and above the own rows in plane k; the own
+    // rows' values are q[i][R]
+    auto ycol = [&](int m) -> VT { return (m >= R && m < RY + R) ? q[m - R][R] : L::ld(pk + m * SX); };
+    // nodes outside the grid read zeros and are computed but not applied
+    VT lap[RY];
 #pragma unroll
-    for (int m = 0; m < R; ++m) {
-      yl[m] = pk[m * SX];
-      yh[m] = pk[(RY + R + m) * SX];
-    }
-    auto ycol = [&](int m) -> T { return m < R ? yl[m] : (m >= RY + R ? yh[m - RY - R] : q[m - R][R]); };
-    // the RY rows' sums advance together (independent FMA chains); rows outside
-    // the grid read zeros and are computed but not applied
-    T lap[RY];
-#pragma unroll
-    for (int i = 0; i < RY; ++i) lap[i] = W.c * q[i][R];
-#pragma unroll
-    for (int p = 1; p <= R; ++p)
-#pragma unroll
-      for (int i = 0; i < RY; ++i) {
-        const T* row = pk + (i + R) * SX;
-        const T sx = row[p] + row[-p];
-        const T sy = ycol(i + R + p) + ycol(i + R - p);
-        const T sz = q[i][R + p] + q[i][R - p];
-        lap[i] = fma(W.w[p], (sx + sy) + sz, lap[i]);
-      }
-    const long long base = plane * k + (long long)g.n1 * y0 + x;
+    for (int i = 0; i < RY; ++i) lap[i] = L::mul(W.c, q[i][R]);
 #pragma unroll
     for (int i = 0; i < RY; ++i) {
-      if ((rows_ok >> i) & 1u) {
-        T vin[NIN > 0 ? NIN : 1];
+      // x-window of row i: columns x0 - RE .. x0 + CX - 1 + RE (the centre is q[i][R])
+      const T* row = pk + (i + R) * SX;
+      T win[NWIN];
 #pragma unroll
-        for (int j = 0; j < NIN; ++j) vin[j] = pin[ik][j][(ty * RY + i) * BX + tx];
-        ep.apply(base + (long long)g.n1 * i, q[i][R], lap[i], vin, acc);
+      for (int c = 0; c < NWIN; c += CX) {
+        if (CX == 1 && c == RE) continue;
+        const VT t = L::ld(row + c - RE);
+#pragma unroll
+        for (int l = 0; l < CX; ++l) win[c + l] = L::lane(t, l);
       }
+      // one weighted sum per axis: three independent FMA chains per row
+      VT ax = L::mul(W.w[1], L::add(L::make(win + RE + 1), L::make(win + RE - 1)));
+      VT ay = L::mul(W.w[1], L::add(ycol(i + R + 1), ycol(i + R - 1)));
+      VT az = L::mul(W.w[1], L::add(q[i][R + 1], q[i][R - 1]));
+#pragma unroll
+      for (int p = 2; p <= R; ++p) {
+        ax = L::fma(W.w[p], L::add(L::make(win + RE + p), L::make(win + RE - p)), ax);
+        ay = L::fma(W.w[p], L::add(ycol(i + R + p), ycol(i + R - p)), ay);
+        az = L::fma(W.w[p], L::add(q[i][R + p], q[i][R - p]), az);
+      }
+      lap[i] = L::add(L::add(L::add(lap[i], ax), ay), az);
     }
+    const long long base = plane * k + (long long)g.n1 * y0 + x0;
+#pragma unroll
+    for (int i = 0; i < RY; ++i)
+#pragma unroll
+      for (int l = 0; l < CX; ++l) {
+        if ((node_ok >> (i * CX + l)) & 1u) {
+          T vin[NIN > 0 ? NIN : 1];
+#pragma unroll
+          for (int j = 0; j < NIN; ++j) vin[j] = pin[ik][j][(ty * RY + i) * BX + CX * tx + l];
+          ep.apply(base + (long long)g.n1 * i + l, L::lane(q[i][R], l), L::lane(lap[i], l), vin, acc);
+        }
+      }
 #pragma unroll
     for (int i = 0; i < RY; ++i)
 #pragma unroll
@@ -540,6 +596,13 @@ struct EpiFunctional {
   FuncScalars f;
   double* out;  // 11 sums + C
   T mult_ = T(0);  // -eta + C/mu, from the device sum of u^2 (load())
+  // MIXED: the FP64 potential, pseudocharge and Poisson residual.  With them the
+  // electrostatic energy sums use the same FP64 phi and rho = u^2 + b as the FP64
+  // residual of the Poisson solve (no FP32 rounding of phi in the variational
+  // form); the gradient still takes (float) phi.
+  const double* phi64 = nullptr;
+  const double* b64 = nullptr;
+  const double* r64 = nullptr;
   __device__ __forceinline__ bool skip() const { return false; }
   __device__ __forceinline__ void load() {
     const double C = f.h3 * *sum_uu - f.N;
@@ -563,10 +626,17 @@ struct EpiFunctional {
       acc[2] += (double)exc * (double)ux * (double)ux;
     }
     if (es) {
-      ph = phi[i];
-      const T rho = uc * uc + b[i];
-      acc[3] += (double)rho * (double)ph;
-      if (rcg) acc[4] += (double)ph * (double)rcg[i];
+      if (phi64) {
+        const double phd = phi64[i];
+        ph = (T)phd;
+        acc[3] += ((double)uc * (double)uc + b64[i]) * phd;
+        if (r64) acc[4] += phd * r64[i];
+      } else {
+        ph = phi[i];
+        const T rho = uc * uc + b[i];
+        acc[3] += (double)rho * (double)ph;
+        if (rcg) acc[4] += (double)ph * (double)rcg[i];
+      }
     }
     const T gx = (vw ? (T)(-f.lambda) * lap : T(0)) + T(2) * (vk + vxc + ph) * uc + T(2) * mult * uc;
     const T kin = (vw ? (T)f.kin_vw : T(0)) + (T)(14.0 / 3.0) * vk;
@@ -620,10 +690,7 @@ __global__ void __launch_bounds__(256) cg_update_kernel(long long G, X* __restri
                                                         T* __restrict__ r, const T* __restrict__ p,
                                                         const T* __restrict__ Ap, CgScalars* sc,
                                                         RedBuf red) {
-  if (sc->done) return;
   __shared__ double smem[256 / 32];
-  const T alpha = (T)sc->alpha;
-  const X alpha_x = (X)sc->alpha;
   DotAcc<T> dacc;
   if constexpr (WIDE) {
     static_assert(sizeof(X) == sizeof(T), "the wide update needs X == T");
@@ -635,6 +702,11 @@ __global__ void __launch_bounds__(256) cg_update_kernel(long long G, X* __restri
     VT* x4 = reinterpret_cast<VT*>(phi);
     VT* r4 = reinterpret_cast<VT*>(r);
     const long long stride = (long long)gridDim.x * 512;
+    // the first pass's loads are issued together with the loads of the CG
+    // scalars (reading is harmless when the solve is already done)
+    bool first = true;
+    int done = 0;
+    T alpha = T(0);
     for (long long v0 = (long long)blockIdx.x * 512 + threadIdx.x; v0 < nv; v0 += stride) {
       VT pv[2], av[2], xv[2], rv[2];
 #pragma unroll
@@ -646,6 +718,12 @@ __global__ void __launch_bounds__(256) cg_update_kernel(long long G, X* __restri
           xv[u] = x4[v];
           rv[u] = r4[v];
         }
+      }
+      if (first) {
+        done = sc->done;
+        alpha = (T)sc->alpha;
+        first = false;
+        if (done) return;
       }
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
@@ -667,7 +745,11 @@ __global__ void __launch_bounds__(256) cg_update_kernel(long long G, X* __restri
         }
       }
     }
+    if (first && sc->done) return;  // threads without elements take the same exit
   } else {
+    if (sc->done) return;
+    const T alpha = (T)sc->alpha;
+    const X alpha_x = (X)sc->alpha;
     // four independent elements per thread and pass keep several loads in flight
     const long long stride = (long long)gridDim.x * 1024;
     for (long long i0 = (long long)blockIdx.x * 1024 + threadIdx.x; i0 < G; i0 += stride) {
@@ -783,6 +865,61 @@ __global__ void __launch_bounds__(256) dot2_kernel(long long G, const T* a, cons
   for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < G; i += (long long)gridDim.x * 256) {
     acc[0] += (double)a[i] * (double)b[i];
     if (c) acc[1] += (double)c[i] * (double)e[i];
+  }
+  struct Fin {
+    double* out;
+    __device__ void operator()(double* t) const {
+      out[0] = t[0];
+      out[1] = t[1];
+    }
+  } fin{out};
+  grid_sum<2, 256>(acc, smem, red, gridDim.x, blockIdx.x, threadIdx.x, fin);
+}
+
+// out = ca a + cb b (b may be NULL), |.| when take_abs: the projections,
+// scalings and the norm-preserving rotation |cos t u0 + sin t dh| of the
+// Lagrange-multiplier method.  out may alias a or b.
+template <typename T>
+__global__ void __launch_bounds__(256) lincomb_kernel(long long G, T* out, const T* a, double ca, const T* b,
+                                                      double cb, int take_abs) {
+  const T xa = (T)ca, xb = (T)cb;
+  for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < G; i += (long long)gridDim.x * 256) {
+    T v = xa * a[i];
+    if (b) v = fma(xb, b[i], v);
+    out[i] = take_abs ? fabs(v) : v;
+  }
+}
+
+// Preconditioned projected gradient of the Lagrange-multiplier method (Sec. 5.3.2)
+// from the energy gradient G_E at u: g = G_E - 2 eta u (written over G), the
+// Jacobi diagonal of the functional pass with multiplier term -eta, s = -g / diag.
+// out[0] = s.u, out[1] = u.u (the caller projects s orthogonal to u).
+template <typename T>
+__global__ void __launch_bounds__(256) lm_precond_kernel(long long G, T* g, T* s, const T* u, const T* phi,
+                                                         FuncScalars f, double* out, RedBuf red) {
+  __shared__ double smem[2 * (256 / 32)];
+  double acc[2] = {0.0, 0.0};
+  const bool tf = f.terms & 1, vw = f.terms & 2, xc = f.terms & 4, es = f.terms & 8;
+  const T eta = (T)f.eta;
+  for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < G; i += (long long)gridDim.x * 256) {
+    const T uc = u[i], ux = fabs(uc);
+    T vk = T(0), vxc = T(0), exc = T(0);
+    if (tf) {
+      const T c = cbrt(ux);
+      vk = (T)(5.0 / 3.0 * f.CF) * ((c * c) * (c * c));
+    }
+    if (xc) xc_eval<T>(ux, exc, vxc);
+    const T ph = es ? phi[i] : T(0);
+    const T gi = fma(T(-2) * eta, uc, g[i]);
+    const T kin = (vw ? (T)f.kin_vw : T(0)) + (T)(14.0 / 3.0) * vk;
+    T md = kin + T(2) * (vxc + ph - eta);
+    md = fmax(md, (T)0.25 * kin);
+    md = fmax(md, (T)1e-10);
+    const T si = -gi / md;
+    g[i] = gi;
+    s[i] = si;
+    acc[0] += (double)si * (double)uc;
+    acc[1] += (double)uc * (double)uc;
   }
   struct Fin {
     double* out;

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libofdft.so")
 OK, EINVAL, ENOMEM, ENOTCONV, ENONFINITE, ETIMEOUT, ECUDA = range(7)
 PREC_FP64, PREC_MIXED = 0, 1
 TERM_TF, TERM_VW, TERM_XC, TERM_ES, TERM_ALL = 1, 2, 4, 8, 15
-METHOD_AL, METHOD_PENALTY = 0, 1
+METHOD_AL, METHOD_PENALTY, METHOD_LM = 0, 1, 2
 FORCE_PAPER, FORCE_EXACT = 0, 1
 _STATUS = {0: "OFDFT_OK", 1: "OFDFT_EINVAL", 2: "OFDFT_ENOMEM", 3: "OFDFT_ENOTCONV",
            4: "OFDFT_ENONFINITE", 5: "OFDFT_ETIMEOUT", 6: "OFDFT_ECUDA"}
@@ -59,7 +59,7 @@ class Params(C.Structure):
                 ("restart_every", C.c_int), ("force_variant", C.c_int),
                 ("ezz_correction", C.c_int), ("vacuum", C.c_double), ("round_to", C.c_int),
                 ("refine_every", C.c_int), ("trial_max_rel", C.c_double), ("max_backtrack", C.c_int),
-                ("precond_rank1", C.c_int)]
+                ("precond_rank1", C.c_int), ("poisson_adapt", C.c_double)]
 
 
 class CgStats(C.Structure):
@@ -93,7 +93,8 @@ class Counters(C.Structure):
 class SolveStats(C.Structure):
     _fields_ = [("E", C.c_double), ("eta", C.c_double), ("C", C.c_double), ("parts", Energy),
                 ("outer_iters", C.c_int), ("nlcg_iters", C.c_int), ("grad_evals", C.c_int),
-                ("cg_iters", C.c_int), ("stencil_apps", C.c_longlong), ("converged", C.c_int),
+                ("cg_iters", C.c_int), ("energy_evals", C.c_int), ("stencil_apps", C.c_longlong),
+                ("converged", C.c_int),
                 ("grid", Grid)]
 
 

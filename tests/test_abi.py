@@ -46,6 +46,18 @@ def test_default_params_follow_the_paper(lib):
     assert p.fd_order == 12 and p.terms == F.TERM_ALL and p.method == F.METHOD_AL
 
 
+def test_binding_struct_layouts_match_the_library(lib):
+    lib.ofdft_struct_bytes.restype = ctypes.c_longlong
+    lib.ofdft_struct_bytes.argtypes = [ctypes.c_char_p]
+    for name, cls in [("ofdft_grid", F.Grid), ("ofdft_params", F.Params), ("ofdft_cg_stats", F.CgStats),
+                      ("ofdft_energy", F.Energy), ("ofdft_solve_stats", F.SolveStats),
+                      ("ofdft_counters", F.Counters)]:
+        assert lib.ofdft_struct_bytes(name.encode()) == ctypes.sizeof(cls), name
+    assert lib.ofdft_struct_bytes(b"nothing") == -1
+    p = F.default_params()
+    assert p.poisson_adapt == 1.0 and p.refine_every == 200 and p.tol_poisson == 1e-8
+
+
 def test_box_rule_matches_oracle_box_rule(lib):
     for c in [W.cluster_c1(), W.cluster_c2(), W.tiny_cluster("dimer")] + W.batch_c4(6):
         for rt in (1, 2, 16):

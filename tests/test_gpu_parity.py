@@ -315,6 +315,73 @@ def test_solve_product_tolerance_c1(ctx, c1_case):
     assert np.abs(Fv - Fo).max() <= 1e-5
 
 
+def test_adaptive_poisson_tolerance_reaches_the_same_ground_state(ctx, c1_case):
+    """Loose Poisson solves while the gradient is large (poisson_adapt) and a final
+    confirmation at tol_poisson give the ground state of fixed-tolerance solves."""
+    c, g, res, Fo = c1_case
+    for prec, tight, tolE, tolF in ((F.PREC_FP64, dict(tol_E=1e-10, tol_inner=1e-11), 1e-9, 1e-6),
+                                    (F.PREC_MIXED, dict(tol_E=1e-8, tol_inner=1e-9), 1e-6, 1e-4)):
+        fixed = F.default_params(precision=prec, poisson_adapt=0.0, **tight)
+        adapt = F.default_params(precision=prec, **tight)
+        E0, F0, s0 = ctx.solve(c.R, c.Z, c.h, fixed, grid=g)
+        E1, F1, s1 = ctx.solve(c.R, c.Z, c.h, adapt, grid=g)
+        assert s0.converged and s1.converged
+        assert abs(E1 - E0) / c.M <= tolE
+        assert np.abs(F1 - F0).max() <= tolF
+        assert s1.cg_iters < s0.cg_iters
+
+
+# ------------------------------------------- Lagrange-multiplier method --
+@pytest.fixture(scope="module")
+def dimer_lm_case(ctx):
+    c = W.tiny_cluster("dimer", h=0.8, fd_order=6)
+    g = F.ofdft_grid_for_atoms(c.R, c.h, c.vacuum, 1)
+    po = O.default_params(fd_n=3, method=O.LM, tol_inner=1e-10, tol_poisson=1e-12, max_nlcg=4000)
+    res, u, phi, b = O.solve(_ogrid(g), po, c.R, c.Z)
+    return c, g, res, u, phi
+
+
+def test_solve_lm_fp64_matches_oracle_lm(ctx, dimer_lm_case):
+    """Sec. 5.3.2's Lagrange-multiplier method on the GPU against the oracle's:
+    the same constrained minimum, eta = G_E.u / (2 u.u), norm exactly N."""
+    c, g, res, u_ref, phi_ref = dimer_lm_case
+    assert res.converged
+    p = _parity_params(6, method=F.METHOD_LM, tol_inner=1e-10)
+    u = torch.empty(g.shape, dtype=torch.float64, device=DEV)
+    E, Fv, st = ctx.solve(c.R, c.Z, c.h, p, grid=g, u_out=u)
+    assert st.converged
+    assert E / c.M == pytest.approx(res.E / c.M, abs=1e-8)
+    assert st.eta == pytest.approx(res.eta, abs=1e-5)
+    assert abs(st.C) <= 1e-9 * c.N  # the rotation keeps h^3 sum u^2 = N
+    assert st.energy_evals > 0 and st.nlcg_iters > 0
+    assert np.abs(_h(u) - u_ref).max() <= 1e-4 * np.abs(u_ref).max()
+    Fo = O.forces(_ogrid(g), 3, c.R, c.Z, phi_ref)
+    np.testing.assert_allclose(Fv, Fo, atol=1e-6)
+
+
+def test_solve_lm_agrees_with_al_and_mixed(ctx, dimer_lm_case):
+    c, g, res, _, _ = dimer_lm_case
+    E_al, F_al, st_al = ctx.solve(c.R, c.Z, c.h, _parity_params(6), grid=g)
+    E_lm, F_lm, st_lm = ctx.solve(c.R, c.Z, c.h, _parity_params(6, method=F.METHOD_LM, tol_inner=1e-10), grid=g)
+    assert abs(E_al - E_lm) / c.M <= 1e-7
+    assert st_lm.eta == pytest.approx(st_al.eta, abs=1e-4)
+    np.testing.assert_allclose(F_lm, F_al, atol=1e-5)
+    # MIXED: the line search compares FP32-evaluated energies (resolution ~1e-7 relative),
+    # so the NLCG tolerance sits above that floor
+    pm = _parity_params(6, method=F.METHOD_LM, precision=F.PREC_MIXED, tol_inner=2e-6, tol_poisson=1e-9)
+    E_m, _, st_m = ctx.solve(c.R, c.Z, c.h, pm, grid=g)
+    assert st_m.converged
+    assert abs(E_m - E_lm) / c.M <= 1e-5
+
+
+def test_batch_rejects_lm(ctx):
+    c = W.tiny_cluster("dimer", h=0.8, fd_order=6)
+    bt = F.Batch(ctx, F.PREC_FP64, 1 << 30)
+    with pytest.raises(F.OfdftError):
+        bt.submit(c.R, c.Z, c.h, F.default_params(method=F.METHOD_LM, fd_order=6))
+    bt.close()
+
+
 # ------------------------------------------------------------ edge cases --
 def test_invalid_arguments_are_rejected(ctx):
     g = F.make_grid(8, 8, 8, 0.5)
