@@ -105,6 +105,9 @@ typedef struct {
                            min(1e-4, max(tol_poisson, c tol_poisson sqrt(rs / (tol_inner M)))),
                            rs = h^3 r.s at the current point: loose while the gradient is
                            large, tol_poisson as the NLCG converges; 0: always tol_poisson */
+  double trial_poisson_loosen; /* >= 1: the Poisson solve at a secant trial point (whose gradient only
+                                  sets the secant step) stops at this multiple of the current
+                                  tolerance, at most 1e-4; 1: the same tolerance as every other solve */
 } ofdft_params;
 
 typedef struct {

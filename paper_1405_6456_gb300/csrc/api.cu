@@ -610,7 +610,10 @@ struct Solver {
       TRY(line_guess(sig));
       TRY(axpy_abs(ut, u, d, sig));
       ofdft_energy et;
+      const double tol_keep = tol_p;
+      tol_p = trial_poisson_tol(p, tol_p);
       TRY(eval(ut, Gt, st, d, s_old, eta, mu, &et));
+      tol_p = tol_keep;
       double alpha = -sig, gprev = et.gd, gcur = g0;
       if (!((gcur - gprev) / alpha > 0.0)) {
         // no positive curvature between 0 and sigma0: keep the trial point
@@ -1143,6 +1146,7 @@ int check_params(ofdft_ctx* c, const ofdft_params* p) {
   if (!(p->mu0 > 0.0) || !(p->kappa > 0.0 && p->kappa < 1.0))
     return fail(c, OFDFT_EINVAL, "Algorithm 1 needs mu0 > 0 and 0 < kappa < 1");
   if (!(p->poisson_adapt >= 0.0)) return fail(c, OFDFT_EINVAL, "poisson_adapt must be >= 0");
+  if (!(p->trial_poisson_loosen >= 1.0)) return fail(c, OFDFT_EINVAL, "trial_poisson_loosen must be >= 1");
   if (!(p->tol_poisson > 0.0) || p->max_cg < 1 || p->max_nlcg < 0 || p->max_outer < 1 || p->max_secant < 1)
     return fail(c, OFDFT_EINVAL, "tolerances must be positive and iteration caps >= 1");
   if (!(p->sigma > 0.0) || !(p->rc > 0.0)) return fail(c, OFDFT_EINVAL, "sigma and rc must be positive");
@@ -1203,6 +1207,7 @@ void ofdft_default_params(ofdft_params* p) {
   p->max_backtrack = 2;
   p->precond_rank1 = 1;
   p->poisson_adapt = 1.0;
+  p->trial_poisson_loosen = 1.0;
 }
 
 int ofdft_create(ofdft_ctx** out, int device, void* stream) {

@@ -94,6 +94,7 @@ struct Slot {
   std::vector<double> line_ops;  // OpLine parameters, applied before the next evaluation
   double line_l = 0.0, pos = 0.0;  // last solve's position along d; position of u along d
   double tol_p = 0.0;              // Poisson tolerance of the next evaluations (adaptive_poisson_tol)
+  double ev_tol = 0.0;             // Poisson tolerance of the pending evaluation
   // Poisson phase (within a round)
   int pphase = 0, ptotal = 0;
   ofdft_cg_stats pstats;
@@ -359,7 +360,7 @@ struct Engine {
     if (!mixed) {
       TRY((zpass<T, LoadPlain<T>, EpiResidual<T>>(ev, OFDFT_K_RESIDUAL, 1.0, [&](Slot<T>* S) {
         return std::make_pair(LoadPlain<T>{S->phi}, EpiResidual<T>{nullptr, S->ev_at, S->b, S->r, B->sc + S->index,
-                                                                  S->tol_p, S->p.max_cg, 1});
+                                                                  S->ev_tol, S->p.max_cg, 1});
       })));
       TRY(read_scalars());
       std::vector<Slot<T>*> run;
@@ -389,7 +390,7 @@ struct Engine {
           resid, OFDFT_K_RESIDUAL, 1.0, [&](Slot<T>* S) {
             return std::make_pair(LoadPlain<double>{S->phi64},
                                   EpiResidual<double, float, double>{nullptr, (const float*)S->ev_at, S->b64, S->r64,
-                                                                     B->sc + S->index, S->tol_p, S->p.max_cg,
+                                                                     B->sc + S->index, S->ev_tol, S->p.max_cg,
                                                                      1});
           })));
       TRY(read_scalars());
@@ -399,14 +400,14 @@ struct Engine {
         const double bb = h.bb > 0 ? h.bb : 1.0;
         S->pstats.iterations = S->ptotal;
         S->pstats.rel_residual = sqrt(h.rr / bb);
-        if (h.rr <= S->tol_p * S->tol_p * bb || S->ptotal >= S->p.max_cg || !isfinite(h.rr)) continue;
+        if (h.rr <= S->ev_tol * S->ev_tol * bb || S->ptotal >= S->p.max_cg || !isfinite(h.rr)) continue;
         corr.push_back(S);
       }
       if (corr.empty()) break;
       TRY((ppass<OpRefineReplace>(corr, OFDFT_K_VECTOR, [&](Slot<T>* S, int nb) {
         const int budget = std::min(std::max(S->p.refine_every, 1), S->p.max_cg - S->ptotal);
         const CgScalars& h = B->h_sc[S->index];
-        const double itol = mixed_inner_tol(h.rr, h.bb > 0 ? h.bb : 1.0, S->tol_p);
+        const double itol = mixed_inner_tol(h.rr, h.bb > 0 ? h.bb : 1.0, S->ev_tol);
         return OpRefineReplace{(float*)S->r, S->r64, B->sc32 + S->index, itol, budget, S->pphase, slot_red(S), nb};
       })));
       TRY(read_scalars());
@@ -535,6 +536,7 @@ struct Engine {
     S->ev_eta = S->eta;
     S->ev_mu = S->mu;
     S->ev_out = out;
+    S->ev_tol = S->tol_p;
   }
   void request_dots(Slot<T>* S) {
     S->req = REQ_DOTS;
@@ -634,6 +636,7 @@ struct Engine {
           line_guess(S, S->sig);
           vop(S, VOP_AXPY_ABS, S->ut, S->u, S->d, S->sig);
           request_eval(S, S->ut, S->Gt, S->st, S->d, S->s_old, &S->et);
+          S->ev_tol = trial_poisson_tol(&p, S->tol_p);
           S->state = S_TRIAL;
           return;
         }

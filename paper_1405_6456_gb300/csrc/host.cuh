@@ -275,6 +275,12 @@ inline double adaptive_poisson_tol(const ofdft_params* p, double rs, int M) {
   return std::max(p->tol_poisson, std::min(1e-4, t));
 }
 
+// Poisson tolerance of a secant trial point (ofdft_params.trial_poisson_loosen).
+inline double trial_poisson_tol(const ofdft_params* p, double tol) {
+  if (!(p->trial_poisson_loosen > 1.0)) return tol;
+  return std::max(tol, std::min(1e-4, tol * p->trial_poisson_loosen));
+}
+
 // Resolution of L in a MIXED evaluation: the FP32 energy densities (TF, vW
 // with the FP32 stencil, XC) carry rounding noise that measured about 1e-9 of the
 // summed magnitudes of the energy terms on the 666-atom cluster; a secant step

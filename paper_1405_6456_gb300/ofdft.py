@@ -59,7 +59,8 @@ class Params(C.Structure):
                 ("restart_every", C.c_int), ("force_variant", C.c_int),
                 ("ezz_correction", C.c_int), ("vacuum", C.c_double), ("round_to", C.c_int),
                 ("refine_every", C.c_int), ("trial_max_rel", C.c_double), ("max_backtrack", C.c_int),
-                ("precond_rank1", C.c_int), ("poisson_adapt", C.c_double)]
+                ("precond_rank1", C.c_int), ("poisson_adapt", C.c_double),
+                ("trial_poisson_loosen", C.c_double)]
 
 
 class CgStats(C.Structure):
