@@ -244,6 +244,39 @@ int ofdft_solve(ofdft_ctx* ctx, const ofdft_grid* grid, const double* R, const d
                 double h, const ofdft_params* p, void* u_out, void* phi_out, double* energy,
                 double* forces, ofdft_solve_stats* st);
 
+/* Warm-started ground state: as ofdft_solve, with the NLCG starting from u_in
+ * (device array of p->precision type on `grid`, rescaled to h^3 sum u^2 = N)
+ * instead of the Gaussian guess, and the Poisson solves from phi_in instead of
+ * zero.  Either may be NULL; grid must be given when either is.  u_in and
+ * phi_in may be the same arrays as u_out and phi_out.  Algorithm 1 starts from
+ * p->eta0 and p->mu0: to resume from a previous ground state pass its eta* and
+ * the last penalty weight (mu0 kappa^(outer_iters - 1)), as ofdft_relax does. */
+int ofdft_solve_from(ofdft_ctx* ctx, const ofdft_grid* grid, const double* R, const double* Z, int M, double h,
+                     const ofdft_params* p, const void* u_in, const void* phi_in, void* u_out, void* phi_out,
+                     double* energy, double* forces, ofdft_solve_stats* st);
+
+typedef struct {
+  int steps;          /* geometry steps taken */
+  int solves;         /* ground states computed (two or three per step) */
+  long long cg_iters; /* Poisson CG iterations over all of them */
+  double max_force;   /* largest atomic force norm at the final geometry (Ha/bohr) */
+  double energy;      /* E* at the final geometry */
+  int converged;      /* 1 once max_force < f_tol */
+} ofdft_relax_stats;
+
+/* Geometry relaxation (Sec. 3, the nuclei at the minimum of E over R with the
+ * forces of Eq. Force:Nuclei): Polak-Ribiere CG over the 3M coordinates with a
+ * secant step on F.d between the current geometry and a trial geometry whose
+ * largest atomic move is max_move (bohr), each ground state warm-started from
+ * the previous one (ofdft_solve_from) on one fixed grid (the caller's, or the
+ * box rule at the starting geometry).  R (host, M x 3) is updated in place;
+ * energy and forces (host, M x 3) are those of the final geometry.  Stops when
+ * the largest atomic force norm is below f_tol or after max_steps steps
+ * (OFDFT_ENOTCONV). */
+int ofdft_relax(ofdft_ctx* ctx, const ofdft_grid* grid, double* R, const double* Z, int M, double h,
+                const ofdft_params* p, int max_steps, double f_tol, double max_move, double* energy,
+                double* forces, ofdft_relax_stats* st);
+
 /* Kernel kinds counted by the context (trace counters). */
 enum {
   OFDFT_K_STENCIL = 0,          /* S2 plain stencil */
@@ -330,7 +363,7 @@ int ofdft_poisson_noalloc(const ofdft_grid* g, int fd_order, const double* rho, 
 long long ofdft_workspace_bytes(const ofdft_grid* g, int fd_order, int prec);
 
 /* sizeof of the named ABI struct ("ofdft_grid", "ofdft_params", "ofdft_cg_stats",
- * "ofdft_energy", "ofdft_solve_stats", "ofdft_counters"), or -1 for any other
+ * "ofdft_energy", "ofdft_solve_stats", "ofdft_counters", "ofdft_relax_stats"), or -1 for any other
  * name: lets a binding check its struct layouts against the library's.  Host
  * only, no context needed. */
 long long ofdft_struct_bytes(const char* name);

@@ -14,10 +14,11 @@ int cg_update(ofdft_ctx* c, const GridDev& g, X* x, T* r, T* pv, T* qv, CgScalar
     ProfScope ps_(c, OFDFT_K_CG_UPDATE);
     auto aligned = [](const void* q) { return ((uintptr_t)q & 15u) == 0; };
     if (sizeof(X) == sizeof(T) && g.G % (16 / (long long)sizeof(T)) == 0 && aligned(x) && aligned(r) &&
-        aligned(pv) && aligned(qv))
+        aligned(pv) && aligned(qv)) {
       cg_update_kernel<T, X, sizeof(X) == sizeof(T)><<<pb, 256, 0, c->stream>>>(g.G, x, r, pv, qv, sc, red(c));
-    else
+    } else {
       cg_update_kernel<T, X><<<pb, 256, 0, c->stream>>>(g.G, x, r, pv, qv, sc, red(c));
+    }
   }
   CU(cudaGetLastError());
   return OFDFT_OK;
@@ -1035,7 +1036,7 @@ int finish_solve(ofdft_ctx* c, Solver<T>& S, const ofdft_grid* gr, int R, const 
 template <typename T>
 int solve_impl(ofdft_ctx* c, const ofdft_grid* gr, const double* R_host, const double* Z_host, int M,
                const ofdft_params* p, void* u_out, void* phi_out, double* energy, double* forces,
-               ofdft_solve_stats* st) {
+               ofdft_solve_stats* st, const void* u_in = nullptr, const void* phi_in = nullptr) {
   const bool mixed = (p->precision == OFDFT_PREC_MIXED);
   const GridDev g = gdev(gr);
   const int R = p->fd_order / 2;
@@ -1088,8 +1089,35 @@ int solve_impl(ofdft_ctx* c, const ofdft_grid* gr, const double* R_host, const d
     CU(cudaGetLastError());
     CU(cudaMemsetAsync(S.phi64, 0, g.G * sizeof(double), c->stream));
   }
-  TRY(device_guess<T>(c, gr, R_host, Z_host, M, p->guess_sigma, p->guess_cut, N, S.u));
-  CU(cudaMemsetAsync(S.phi, 0, g.G * es, c->stream));
+  if (u_in) {
+    // warm start: the given density amplitude, rescaled to h^3 sum u^2 = N
+    CU(cudaMemcpyAsync(S.u, u_in, g.G * es, cudaMemcpyDeviceToDevice, c->stream));
+    const int pb = pointwise_blocks(c, g.G);
+    TRY(ensure_partials(c, pb, 2));
+    {
+      ProfScope ps_(c, OFDFT_K_VECTOR);
+      dot2_kernel<T><<<pb, 256, 0, c->stream>>>(g.G, S.u, S.u, nullptr, nullptr, c->scal + 16, red(c));
+    }
+    {
+      ProfScope ps_(c, OFDFT_K_VECTOR);
+      normalise_kernel<T><<<pb, 256, 0, c->stream>>>(g.G, S.u, c->scal + 16, gr->h * gr->h * gr->h, N);
+    }
+    CU(cudaGetLastError());
+  } else {
+    TRY(device_guess<T>(c, gr, R_host, Z_host, M, p->guess_sigma, p->guess_cut, N, S.u));
+  }
+  if (phi_in) {
+    // warm start of the Poisson solves
+    CU(cudaMemcpyAsync(S.phi, phi_in, g.G * es, cudaMemcpyDeviceToDevice, c->stream));
+    if (mixed) {
+      ProfScope ps_(c, OFDFT_K_VECTOR);
+      convert_kernel<float, double><<<pointwise_blocks(c, g.G), 256, 0, c->stream>>>(g.G, S.phi64,
+                                                                                      (const float*)phi_in);
+    }
+    CU(cudaGetLastError());
+  } else {
+    CU(cudaMemsetAsync(S.phi, 0, g.G * es, c->stream));
+  }
   S.ezz = 0.0;
   std::vector<double> Fz(3 * (size_t)M, 0.0);
   if (p->ezz_correction) TRY(device_ezz(c, R_host, Z_host, M, p->sigma, &S.ezz, Fz.data()));
@@ -1336,6 +1364,7 @@ long long ofdft_struct_bytes(const char* name) {
   if (n == "ofdft_energy") return (long long)sizeof(ofdft_energy);
   if (n == "ofdft_solve_stats") return (long long)sizeof(ofdft_solve_stats);
   if (n == "ofdft_counters") return (long long)sizeof(ofdft_counters);
+  if (n == "ofdft_relax_stats") return (long long)sizeof(ofdft_relax_stats);
   return -1;
 }
 
@@ -1540,6 +1569,32 @@ int ofdft_forces(ofdft_ctx* c, const ofdft_grid* g, int fd_order, const double* 
   return device_forces<float>(c, g, fd_order / 2, R, Z, M, sigma, rc, variant, (const float*)phi, F);
 }
 
+int ofdft_solve_from(ofdft_ctx* c, const ofdft_grid* grid, const double* R, const double* Z, int M, double h,
+                     const ofdft_params* p, const void* u_in, const void* phi_in, void* u_out, void* phi_out,
+                     double* energy, double* forces, ofdft_solve_stats* st) {
+  if (!c) return OFDFT_EINVAL;
+  c->err.clear();
+  if ((u_in || phi_in) && !grid) return fail(c, OFDFT_EINVAL, "a warm start needs the grid it was computed on");
+  TRY(check_params(c, p));
+  TRY(check_atoms(c, R, Z, M));
+  if (!energy) return fail(c, OFDFT_EINVAL, "energy pointer is NULL");
+  ofdft_solve_stats tmp;
+  if (!st) st = &tmp;
+  memset(st, 0, sizeof(*st));
+  ofdft_grid g;
+  if (grid) {
+    g = *grid;
+  } else {
+    const int rc = ofdft_grid_for_atoms(R, M, h, p->vacuum, p->round_to > 0 ? p->round_to : 1, &g);
+    if (rc != OFDFT_OK) return fail(c, rc, "box rule failed for h=%g vacuum=%g", h, p->vacuum);
+  }
+  TRY(check_grid(c, &g));
+  CU(cudaSetDevice(c->device));
+  if (p->precision == OFDFT_PREC_FP64)
+    return solve_impl<double>(c, &g, R, Z, M, p, u_out, phi_out, energy, forces, st, u_in, phi_in);
+  return solve_impl<float>(c, &g, R, Z, M, p, u_out, phi_out, energy, forces, st, u_in, phi_in);
+}
+
 int ofdft_solve(ofdft_ctx* c, const ofdft_grid* grid, const double* R, const double* Z, int M, double h,
                 const ofdft_params* p, void* u_out, void* phi_out, double* energy, double* forces,
                 ofdft_solve_stats* st) {
@@ -1562,6 +1617,130 @@ int ofdft_solve(ofdft_ctx* c, const ofdft_grid* grid, const double* R, const dou
   CU(cudaSetDevice(c->device));
   if (p->precision == OFDFT_PREC_FP64) return solve_impl<double>(c, &g, R, Z, M, p, u_out, phi_out, energy, forces, st);
   return solve_impl<float>(c, &g, R, Z, M, p, u_out, phi_out, energy, forces, st);
+}
+
+int ofdft_relax(ofdft_ctx* c, const ofdft_grid* grid, double* R, const double* Z, int M, double h,
+                const ofdft_params* p, int max_steps, double f_tol, double max_move, double* energy,
+                double* forces, ofdft_relax_stats* rst) {
+  if (!c) return OFDFT_EINVAL;
+  c->err.clear();
+  TRY(check_params(c, p));
+  TRY(check_atoms(c, R, Z, M));
+  if (!energy || !forces) return fail(c, OFDFT_EINVAL, "energy and forces are required");
+  if (max_steps < 0 || !(f_tol > 0.0) || !(max_move > 0.0))
+    return fail(c, OFDFT_EINVAL, "need max_steps >= 0, f_tol > 0 and max_move > 0");
+  ofdft_relax_stats tmp;
+  if (!rst) rst = &tmp;
+  memset(rst, 0, sizeof(*rst));
+  // one grid for the whole relaxation: the caller's, or the box rule at the start
+  ofdft_grid g;
+  if (grid) {
+    g = *grid;
+  } else {
+    const int rc = ofdft_grid_for_atoms(R, M, h, p->vacuum, p->round_to > 0 ? p->round_to : 1, &g);
+    if (rc != OFDFT_OK) return fail(c, rc, "box rule failed for h=%g vacuum=%g", h, p->vacuum);
+  }
+  TRY(check_grid(c, &g));
+  CU(cudaSetDevice(c->device));
+  const size_t es = (p->precision == OFDFT_PREC_FP64) ? 8 : 4;
+  const long long G = (long long)g.n[0] * g.n[1] * g.n[2];
+  // u* and phi* of the last ground state: the warm start of the next one
+  DevBuf bu, bphi;
+  TRY(ensure(c, bu, G * es));
+  TRY(ensure(c, bphi, G * es));
+  struct Free {
+    DevBuf *a, *b;
+    ~Free() {
+      cudaFree(a->p);
+      cudaFree(b->p);
+    }
+  } free_bufs{&bu, &bphi};
+  const int n = 3 * M;
+  std::vector<double> F(n), Ft(n), Rt(n), d(n, 0.0), gold(n, 0.0);
+  // a warm start also resumes Algorithm 1 where the previous ground state ended:
+  // eta0 = its eta*, mu0 = the last penalty weight it used
+  ofdft_params pw = *p;
+  auto ground = [&](const double* Rx, double* Ex, double* Fx, bool warm) -> int {
+    ofdft_solve_stats st;
+    const int rc = ofdft_solve_from(c, &g, Rx, Z, M, h, warm ? &pw : p, warm ? bu.p : nullptr,
+                                    warm ? bphi.p : nullptr, bu.p, bphi.p, Ex, Fx, &st);
+    rst->solves++;
+    rst->cg_iters += st.cg_iters;
+    if (rc == OFDFT_OK && p->method == OFDFT_METHOD_AL) {
+      pw.eta0 = st.eta;
+      pw.mu0 = p->mu0 * pow(p->kappa, std::max(st.outer_iters - 1, 0));
+    }
+    return rc;
+  };
+  auto fmax_of = [&](const std::vector<double>& Fx) {
+    double m = 0.0;
+    for (int J = 0; J < M; ++J)
+      m = std::max(m, sqrt(Fx[3 * J] * Fx[3 * J] + Fx[3 * J + 1] * Fx[3 * J + 1] + Fx[3 * J + 2] * Fx[3 * J + 2]));
+    return m;
+  };
+  double E = 0.0;
+  TRY(ground(R, &E, F.data(), false));
+  double gg_old = 0.0;
+  // Polak-Ribiere CG on E(R) with g = -F, a secant step on the directional
+  // derivative -F.d between R and a trial geometry whose largest atomic move is
+  // max_move, and a halved step when the energy rises
+  for (int step = 0; step < max_steps; ++step) {
+    rst->max_force = fmax_of(F);
+    if (rst->max_force < f_tol) {
+      rst->converged = 1;
+      break;
+    }
+    double gg = 0.0, gdg = 0.0;
+    for (int i = 0; i < n; ++i) {
+      gg += F[i] * F[i];
+      gdg += -F[i] * (-F[i] - gold[i]);
+    }
+    double beta = (step == 0 || gg_old <= 0.0) ? 0.0 : std::max(0.0, gdg / gg_old);
+    double dg = 0.0;
+    for (int i = 0; i < n; ++i) {
+      d[i] = F[i] + beta * d[i];
+      dg += -F[i] * d[i];
+    }
+    if (!(dg < 0.0)) {  // not a descent direction: steepest descent
+      for (int i = 0; i < n; ++i) d[i] = F[i];
+      dg = -gg;
+    }
+    for (int i = 0; i < n; ++i) gold[i] = -F[i];
+    gg_old = gg;
+    double dmax = 0.0;
+    for (int J = 0; J < M; ++J)
+      dmax = std::max(dmax, sqrt(d[3 * J] * d[3 * J] + d[3 * J + 1] * d[3 * J + 1] + d[3 * J + 2] * d[3 * J + 2]));
+    if (!(dmax > 0.0)) break;
+    const double a0 = max_move / dmax;
+    for (int i = 0; i < n; ++i) Rt[i] = R[i] + a0 * d[i];
+    double Et = 0.0;
+    TRY(ground(Rt.data(), &Et, Ft.data(), true));
+    double g1 = 0.0;
+    for (int i = 0; i < n; ++i) g1 += -Ft[i] * d[i];
+    // secant on the directional derivative: dg at 0, g1 at a0
+    double a = (g1 > dg) ? a0 * dg / (dg - g1) : 2.0 * a0;
+    a = std::min(std::max(a, 0.1 * a0), 4.0 * a0);
+    for (int i = 0; i < n; ++i) Rt[i] = R[i] + a * d[i];
+    double En = 0.0;
+    TRY(ground(Rt.data(), &En, Ft.data(), true));
+    if (En > E && Et < E) {  // the secant overshot: take the trial geometry instead
+      for (int i = 0; i < n; ++i) Rt[i] = R[i] + a0 * d[i];
+      TRY(ground(Rt.data(), &En, Ft.data(), true));
+    }
+    for (int i = 0; i < n; ++i) {
+      R[i] = Rt[i];
+      F[i] = Ft[i];
+    }
+    E = En;
+    rst->steps++;
+  }
+  rst->max_force = fmax_of(F);
+  if (rst->max_force < f_tol) rst->converged = 1;
+  rst->energy = E;
+  *energy = E;
+  for (int i = 0; i < n; ++i) forces[i] = F[i];
+  return rst->converged ? OFDFT_OK : fail(c, OFDFT_ENOTCONV, "relaxation reached %d steps (max force %.3e)",
+                                          max_steps, rst->max_force);
 }
 
 }  // extern "C"

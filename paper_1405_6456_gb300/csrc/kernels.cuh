@@ -701,16 +701,17 @@ __global__ void __launch_bounds__(256) cg_update_kernel(long long G, X* __restri
     const VT* a4 = reinterpret_cast<const VT*>(Ap);
     VT* x4 = reinterpret_cast<VT*>(phi);
     VT* r4 = reinterpret_cast<VT*>(r);
-    const long long stride = (long long)gridDim.x * 512;
+    constexpr int UV = 2;  // vectors per thread and pass: all loads of a pass in flight together
+    const long long stride = (long long)gridDim.x * 256 * UV;
     // the first pass's loads are issued together with the loads of the CG
     // scalars (reading is harmless when the solve is already done)
     bool first = true;
     int done = 0;
     T alpha = T(0);
-    for (long long v0 = (long long)blockIdx.x * 512 + threadIdx.x; v0 < nv; v0 += stride) {
-      VT pv[2], av[2], xv[2], rv[2];
+    for (long long v0 = (long long)blockIdx.x * 256 * UV + threadIdx.x; v0 < nv; v0 += stride) {
+      VT pv[UV], av[UV], xv[UV], rv[UV];
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
+      for (int u = 0; u < UV; ++u) {
         const long long v = v0 + 256 * u;
         if (v < nv) {
           pv[u] = p4[v];
@@ -726,7 +727,7 @@ __global__ void __launch_bounds__(256) cg_update_kernel(long long G, X* __restri
         if (done) return;
       }
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
+      for (int u = 0; u < UV; ++u) {
         const long long v = v0 + 256 * u;
         if (v < nv) {
           T pe[VW], ae[VW], xe[VW], re[VW];

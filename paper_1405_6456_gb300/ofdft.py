@@ -99,6 +99,11 @@ class SolveStats(C.Structure):
                 ("grid", Grid)]
 
 
+class RelaxStats(C.Structure):
+    _fields_ = [("steps", C.c_int), ("solves", C.c_int), ("cg_iters", C.c_longlong), ("max_force", C.c_double),
+                ("energy", C.c_double), ("converged", C.c_int)]
+
+
 _lib = None
 
 
@@ -132,6 +137,12 @@ def lib():
                                vp, dp]
     L.ofdft_solve.argtypes = [vp, C.POINTER(Grid), dp, dp, ip, C.c_double, C.POINTER(Params), vp,
                               vp, dp, dp, C.POINTER(SolveStats)]
+    L.ofdft_solve_from.argtypes = [vp, C.POINTER(Grid), dp, dp, ip, C.c_double, C.POINTER(Params), vp, vp,
+                                   vp, vp, dp, dp, C.POINTER(SolveStats)]
+    L.ofdft_relax.argtypes = [vp, C.POINTER(Grid), dp, dp, ip, C.c_double, C.POINTER(Params), ip, C.c_double,
+                              C.c_double, dp, dp, C.POINTER(RelaxStats)]
+    L.ofdft_struct_bytes.argtypes = [C.c_char_p]
+    L.ofdft_struct_bytes.restype = C.c_longlong
     L.ofdft_profile.argtypes = [vp, ip]
     L.ofdft_get_counters.argtypes = [vp, C.POINTER(Counters)]
     L.ofdft_reset_counters.argtypes = [vp]
@@ -316,6 +327,33 @@ class Context:
                                    _dp(F) if F is not None else None, C.byref(st))
         self._check(rc, "ofdft_solve", allow=(ENOTCONV,) if allow_notconv else ())
         return E.value, F, st
+
+    def solve_from(self, R, Z, h, p: Params, grid: Grid, u_in=None, phi_in=None, u_out=None, phi_out=None,
+                   want_forces=True, allow_notconv=False):
+        """Warm-started ground state (ofdft_solve_from); returns (energy, forces or None, SolveStats)."""
+        R, Z = _host_f64(R).reshape(-1, 3), _host_f64(Z)
+        E = C.c_double()
+        F = np.zeros((R.shape[0], 3)) if want_forces else None
+        st = SolveStats()
+        rc = self._lib.ofdft_solve_from(self.h, C.byref(grid), _dp(R), _dp(Z), R.shape[0], h, C.byref(p),
+                                        _ptr(u_in), _ptr(phi_in), _ptr(u_out), _ptr(phi_out), C.byref(E),
+                                        _dp(F) if F is not None else None, C.byref(st))
+        self._check(rc, "ofdft_solve_from", allow=(ENOTCONV,) if allow_notconv else ())
+        return E.value, F, st
+
+    def relax(self, R, Z, h, p: Params, grid: Grid | None = None, max_steps=50, f_tol=1e-3, max_move=0.05,
+              allow_notconv=False):
+        """Geometry relaxation (ofdft_relax); returns (R*, energy, forces, RelaxStats)."""
+        R = np.array(_host_f64(R).reshape(-1, 3), copy=True)
+        Z = _host_f64(Z)
+        E = C.c_double()
+        F = np.zeros_like(R)
+        st = RelaxStats()
+        rc = self._lib.ofdft_relax(self.h, C.byref(grid) if grid is not None else None, _dp(R), _dp(Z),
+                                   R.shape[0], h, C.byref(p), int(max_steps), float(f_tol), float(max_move),
+                                   C.byref(E), _dp(F), C.byref(st))
+        self._check(rc, "ofdft_relax", allow=(ENOTCONV,) if allow_notconv else ())
+        return R, E.value, F, st
 
 
 class Batch:
