@@ -1264,6 +1264,8 @@ int ofdft_create(ofdft_ctx** out, int device, void* stream) {
   if (cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking) != cudaSuccess) c->use_graphs = 0;
   const char* at = getenv("OFDFT_AUTOTUNE");
   c->autotune = !(at && at[0] == '0');
+  const char* pw = getenv("OFDFT_POINTWISE_BLOCKS_PER_SM");  // launch-shape experiments (default 4)
+  if (pw && atoi(pw) >= 1 && atoi(pw) <= 16) c->pw_per_sm = atoi(pw);
   cudaMemset(c->sc, 0, 3 * sizeof(CgScalars));
   cudaMemset(c->scal, 0, 64 * sizeof(double));
   cudaDeviceSynchronize();

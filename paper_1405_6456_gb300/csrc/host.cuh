@@ -69,6 +69,7 @@ struct ofdft_ctx {
   std::vector<std::vector<long long>> ztuned;  // (type, radius, grid, 16-byte staging) already tuned
   std::vector<long long> last_zkey;            // key of the last z-streaming launch
   int force_nz = -1;                           // >= 0: z-split of the next launches (autotuner)
+  int pw_per_sm = 4;                           // blocks per SM of the pointwise passes
   int autotune = 1;
 };
 
@@ -259,7 +260,7 @@ Weights<T> cast_weights(const Weights<double>& W) {
 
 inline int pointwise_blocks(ofdft_ctx* c, long long G) {
   long long b = (G + 1023) / 1024;
-  return (int)std::max<long long>(1, std::min<long long>(b, (long long)c->sms * 4));
+  return (int)std::max<long long>(1, std::min<long long>(b, (long long)c->sms * c->pw_per_sm));
 }
 
 // z-streaming launch shape: BX x BY columns; z split so that the grid fills
