@@ -7,31 +7,77 @@
 namespace ofd {
 
 // ------------------------------------------------------------ Poisson (S3) --
-// The x/r update of one CG iteration with r.r (second kernel of cg_step).
-template <typename T, typename X>
-int cg_update(ofdft_ctx* c, const GridDev& g, X* x, T* r, T* pv, T* qv, CgScalars* sc, int pb) {
+// The r update of one CG iteration with r.r (second kernel of cg_step); the
+// iterate update x += alpha p is folded into the next stencil pass (EpiCgAX).
+// Without folding (fold == false) the update also applies x += alpha p itself.
+template <typename T>
+int cg_update(ofdft_ctx* c, const GridDev& g, T* x, T* r, T* pv, T* qv, CgScalars* sc, int pb, bool fold) {
   {
     ProfScope ps_(c, OFDFT_K_CG_UPDATE);
     auto aligned = [](const void* q) { return ((uintptr_t)q & 15u) == 0; };
-    if (sizeof(X) == sizeof(T) && g.G % (16 / (long long)sizeof(T)) == 0 && aligned(x) && aligned(r) &&
-        aligned(pv) && aligned(qv)) {
-      cg_update_kernel<T, X, sizeof(X) == sizeof(T)><<<pb, 256, 0, c->stream>>>(g.G, x, r, pv, qv, sc, red(c));
+    const bool wide = g.G % (16 / (long long)sizeof(T)) == 0 && aligned(r) && aligned(qv) && aligned(x) &&
+                      aligned(pv);
+    if (fold) {
+      if (wide)
+        cg_update_r_kernel<T, true><<<pb, 256, 0, c->stream>>>(g.G, r, qv, sc, red(c));
+      else
+        cg_update_r_kernel<T, false><<<pb, 256, 0, c->stream>>>(g.G, r, qv, sc, red(c));
     } else {
-      cg_update_kernel<T, X><<<pb, 256, 0, c->stream>>>(g.G, x, r, pv, qv, sc, red(c));
+      if (wide)
+        cg_update_kernel<T, T, true><<<pb, 256, 0, c->stream>>>(g.G, x, r, pv, qv, sc, red(c));
+      else
+        cg_update_kernel<T, T><<<pb, 256, 0, c->stream>>>(g.G, x, r, pv, qv, sc, red(c));
     }
   }
   CU(cudaGetLastError());
   return OFDFT_OK;
 }
 
+// Whether a CG solve folds the iterate update into the stencil pass: it saves
+// 8 bytes per node and iteration, which pays when the CG vectors stream from
+// DRAM; when they stay in the 129 MB L2 the update kernel is bound by its fixed
+// costs and the heavier stencil epilogue does not pay (measured at 128^3).
+template <typename T>
+bool cg_fold(const GridDev& g) {
+  return 5.0 * (double)g.G * sizeof(T) > 96.0 * (1 << 20);
+}
+
+// The stencil pass of one CG iteration: q = A r + beta q, p = r + beta p, p.q,
+// and the previous iteration's x += alpha p when it is pending.
+template <typename T>
+int cg_stencil(ofdft_ctx* c, int R, const GridDev& g, const Weights<double>& Wneg, T* x, const T* r, T* pv, T* qv,
+               CgScalars* sc, bool fold) {
+  if (fold)
+    return launch_z_r<T>(c, R, g, Wneg, LoadPlain<T>{r}, EpiCgAX<T>{pv, qv, x, sc}, OFDFT_K_CG_DIR_STENCIL);
+  return launch_z_r<T>(c, R, g, Wneg, LoadPlain<T>{r}, EpiCgA<T>{pv, qv, sc}, OFDFT_K_CG_DIR_STENCIL);
+}
+
+// Applies the last iteration's pending x += alpha p (after the CG loop of a call).
+template <typename T>
+int cg_flush(ofdft_ctx* c, const GridDev& g, T* x, const T* pv, CgScalars* sc) {
+  {
+    ProfScope ps_(c, OFDFT_K_VECTOR);
+    cg_xflush_kernel<T><<<pointwise_blocks(c, g.G), 256, 0, c->stream>>>(g.G, x, pv, sc);
+  }
+  {
+    ProfScope ps_(c, OFDFT_K_VECTOR);
+    cg_xclear_kernel<<<1, 1, 0, c->stream>>>(sc);
+  }
+  CU(cudaGetLastError());
+  return OFDFT_OK;
+}
+
 // Launches one CG iteration (S3): the stencil pass on r with the p/q update and
-// p.q, then the x/r update with r.r; both kernels read and write the CG scalars
-// on the device and return at once when the solve is done.
+// p.q (and the previous x update), then the r update with r.r; both kernels
+// read and write the CG scalars on the device and return at once when the
+// solve is done.
 template <typename T, typename X>
 int cg_step(ofdft_ctx* c, int R, const GridDev& g, const Weights<double>& Wneg, X* x, T* r, T* pv, T* qv,
             CgScalars* sc, int pb) {
-  TRY(launch_z_r<T>(c, R, g, Wneg, LoadPlain<T>{r}, EpiCgA<T>{pv, qv, sc}, OFDFT_K_CG_DIR_STENCIL));
-  return cg_update<T, X>(c, g, x, r, pv, qv, sc, pb);
+  static_assert(sizeof(X) == sizeof(T), "the iterate has the CG vectors' type");
+  const bool fold = cg_fold<T>(g);
+  TRY(cg_stencil<T>(c, R, g, Wneg, reinterpret_cast<T*>(x), r, pv, qv, sc, fold));
+  return cg_update<T>(c, g, reinterpret_cast<T*>(x), r, pv, qv, sc, pb, fold);
 }
 
 constexpr int kChunk = 8;  // CG iterations between convergence polls
@@ -42,11 +88,12 @@ constexpr int kChunk = 8;  // CG iterations between convergence polls
 // context.  The split changes the blocks' partial sums, so it is fixed before
 // the solve's first CG pass and the reduction order stays the same afterwards.
 template <typename T>
-int tune_cg_split(ofdft_ctx* c, int R, const GridDev& g, const Weights<double>& Wneg, const T* r) {
+int tune_cg_split(ofdft_ctx* c, int R, const GridDev& g, const Weights<double>& Wneg, const T* r, T* x) {
   if (!c->autotune) return OFDFT_OK;
   T *pv = nullptr, *qv = nullptr;  // scratch p and q (separate allocations, aligned like the solver's)
-  const long long vec16 = zvec_ok<T>(g, LoadPlain<T>{r}, EpiCgA<T>{vec<T>(c, V_P0), vec<T>(c, V_AP), nullptr});
-  const std::vector<long long> tkey = {(long long)sizeof(T), R, g.n1, g.n2, g.n3, vec16};
+  const bool fold = cg_fold<T>(g);
+  const long long vec16 = zvec_ok<T>(g, LoadPlain<T>{r}, EpiCgAX<T>{vec<T>(c, V_P0), vec<T>(c, V_AP), x, nullptr});
+  const std::vector<long long> tkey = {(long long)sizeof(T), R, g.n1, g.n2, g.n3, vec16, fold ? 1 : 0};
   for (auto& t : c->ztuned)
     if (t == tkey) return OFDFT_OK;
   const std::vector<int> cand = {0, 1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 14, 16, 20, 24, 32, 48, 64};
@@ -82,7 +129,7 @@ int tune_cg_split(ofdft_ctx* c, int R, const GridDev& g, const Weights<double>& 
         rc = fail(c, OFDFT_ECUDA, "autotune: enqueue failed");
         break;
       }
-      rc = launch_z_r<T>(c, R, g, Wneg, LoadPlain<T>{r}, EpiCgA<T>{pv, qv, sc}, OFDFT_K_CG_DIR_STENCIL);
+      rc = cg_stencil<T>(c, R, g, Wneg, x, r, pv, qv, sc, fold);
       key = c->last_zkey;
       float t = 0.0f;
       if (rc == OFDFT_OK && (cudaEventRecord(e1, c->stream) != cudaSuccess ||
@@ -150,9 +197,10 @@ int cg_graph(ofdft_ctx* c, int R, const GridDev& g, double h, const Weights<doub
     for (int i = 0; i < kChunk && rc == OFDFT_OK; ++i) {
       if (sample_set >= 0 && i == kChunk / 2) {
         cudaEventRecordWithFlags(c->gev[sample_set][0], c->stream, cudaEventRecordExternal);
-        rc = launch_z_r<T>(c, R, g, Wneg, LoadPlain<T>{r}, EpiCgA<T>{pv, qv, sc}, OFDFT_K_CG_DIR_STENCIL);
+        const bool fold = cg_fold<T>(g);
+        rc = cg_stencil<T>(c, R, g, Wneg, reinterpret_cast<T*>(x), r, pv, qv, sc, fold);
         cudaEventRecordWithFlags(c->gev[sample_set][1], c->stream, cudaEventRecordExternal);
-        if (rc == OFDFT_OK) rc = cg_update<T, X>(c, g, x, r, pv, qv, sc, pb);
+        if (rc == OFDFT_OK) rc = cg_update<T>(c, g, reinterpret_cast<T*>(x), r, pv, qv, sc, pb, fold);
       } else {
         rc = cg_step<T, X>(c, R, g, Wneg, x, r, pv, qv, sc, pb);
       }
@@ -188,7 +236,7 @@ int cg_iterate(ofdft_ctx* c, int R, const GridDev& g, double h, const Weights<do
   const int pb = pointwise_blocks(c, g.G);
   TRY(ensure_partials(c, pb, 1));
   TRY(ensure_partials(c, zshape<T>(c, g, R, 32).nblocks, 1));
-  TRY(tune_cg_split<T>(c, R, g, Wneg, r));
+  TRY(tune_cg_split<T>(c, R, g, Wneg, r, reinterpret_cast<T*>(x)));
   const bool full_timed = (c->prof & (1 << OFDFT_K_CG_UPDATE)) != 0;
   const bool sampled = !full_timed && (c->prof & (1 << OFDFT_K_CG_DIR_STENCIL)) != 0;
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
@@ -229,6 +277,7 @@ int cg_iterate(ofdft_ctx* c, int R, const GridDev& g, double h, const Weights<do
     }
     ++chunks;
   }
+  if (cg_fold<T>(g)) TRY(cg_flush<T>(c, g, reinterpret_cast<T*>(x), pv, sc));
   TRY(sync_scalars(c, sc, sizeof(CgScalars), host_sc));
   read_sample(0);
   read_sample(1);

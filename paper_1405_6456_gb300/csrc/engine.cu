@@ -335,15 +335,31 @@ struct Engine {
   template <class GetX, class GetR, class GetSc, class HostSc>
   int cg_loop(std::vector<Slot<T>*> slots, GetX getx, GetR getr, GetSc getsc, HostSc hostsc) {
     const int chunk = 8;
+    const std::vector<Slot<T>*> all = slots;
+    // as ofdft_solve: when the batch's CG vectors do not fit in L2 the iterate
+    // update of an iteration is folded into the next stencil pass (EpiCgAX), the
+    // update only moves r, and a last flush applies the final pending x += alpha p
+    double bytes = 0.0;
+    for (Slot<T>* S : slots) bytes += 5.0 * (double)S->g.G * sizeof(T);
+    const bool fold = bytes > 96.0 * (1 << 20);
     while (!slots.empty()) {
       for (int i = 0; i < chunk; ++i) {
-        TRY((zpass<T, LoadPlain<T>, EpiCgA<T>>(slots, OFDFT_K_CG_DIR_STENCIL, -1.0, [&](Slot<T>* S) {
-          return std::make_pair(LoadPlain<T>{getr(S)}, EpiCgA<T>{S->pv, S->qv, getsc(S)});
-        })));
-        using X = std::remove_pointer_t<decltype(getx(slots[0]))>;
-        TRY((ppass<OpCgUpdate<T, X>>(slots, OFDFT_K_CG_UPDATE, [&](Slot<T>* S, int nb) {
-          return OpCgUpdate<T, X>{getx(S), getr(S), S->pv, S->qv, getsc(S), slot_red(S), nb};
-        })));
+        if (fold) {
+          TRY((zpass<T, LoadPlain<T>, EpiCgAX<T>>(slots, OFDFT_K_CG_DIR_STENCIL, -1.0, [&](Slot<T>* S) {
+            return std::make_pair(LoadPlain<T>{getr(S)}, EpiCgAX<T>{S->pv, S->qv, (T*)getx(S), getsc(S)});
+          })));
+          TRY((ppass<OpCgUpdateR<T>>(slots, OFDFT_K_CG_UPDATE, [&](Slot<T>* S, int nb) {
+            return OpCgUpdateR<T>{getr(S), S->qv, getsc(S), slot_red(S), nb};
+          })));
+        } else {
+          TRY((zpass<T, LoadPlain<T>, EpiCgA<T>>(slots, OFDFT_K_CG_DIR_STENCIL, -1.0, [&](Slot<T>* S) {
+            return std::make_pair(LoadPlain<T>{getr(S)}, EpiCgA<T>{S->pv, S->qv, getsc(S)});
+          })));
+          using X = std::remove_pointer_t<decltype(getx(slots[0]))>;
+          TRY((ppass<OpCgUpdate<T, X>>(slots, OFDFT_K_CG_UPDATE, [&](Slot<T>* S, int nb) {
+            return OpCgUpdate<T, X>{getx(S), getr(S), S->pv, S->qv, getsc(S), slot_red(S), nb};
+          })));
+        }
       }
       TRY(read_scalars());
       std::vector<Slot<T>*> still;
@@ -351,6 +367,10 @@ struct Engine {
         if (!hostsc(S).done) still.push_back(S);
       slots.swap(still);
     }
+    if (fold)
+      TRY((ppass<OpXFlush<T>>(all, OFDFT_K_VECTOR, [&](Slot<T>* S, int nb) {
+        return OpXFlush<T>{(T*)getx(S), S->pv, getsc(S), slot_red(S), nb};
+      })));
     return OFDFT_OK;
   }
 

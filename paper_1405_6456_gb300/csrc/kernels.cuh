@@ -71,6 +71,7 @@ struct CgScalars {
   int max_it;
   int done;       // 1 once converged or out of iterations
   int first;      // 1 until the first search direction is formed
+  int xdefer;     // 1 while x += alpha p of the last iteration is still to be applied
 };
 
 // ---------------------------------------------------------------------------
@@ -488,6 +489,52 @@ struct EpiCgA {
   }
 };
 
+// EpiCgA with the iterate update folded in: x += alpha p of the previous
+// iteration (p = the staged p_old, alpha = the previous alpha) is applied here,
+// at the nodes this pass already visits, instead of in the update kernel, which
+// then only moves r and q (cg_update_r_kernel).  xdefer says whether an update
+// is pending; the last block clears it.  NIN = 3: p_old, q_old, x.
+template <typename T>
+struct EpiCgAX {
+  static constexpr int K = 1;
+  static constexpr int NIN = 3;
+  using Acc = DotAcc<T>;
+  T* p;
+  T* q;
+  T* x;
+  CgScalars* sc;
+  int first_ = 0, xd_ = 0;
+  T beta_ = T(0), alpha_ = T(0);
+  __device__ __forceinline__ bool skip() const { return sc->done != 0; }
+  __device__ __forceinline__ void load() {
+    first_ = sc->first;
+    xd_ = sc->xdefer;
+    beta_ = (T)sc->beta;
+    alpha_ = (T)sc->alpha;
+  }
+  __host__ __device__ __forceinline__ const T* input(int j) const { return j == 0 ? p : (j == 1 ? q : x); }
+  __device__ __forceinline__ void apply(long long i, T rc, T ar, const T* vin, Acc* acc) const {
+    if (xd_) x[i] = fma(alpha_, vin[0], vin[2]);
+    T pc, qc;
+    if (first_) {
+      pc = rc;
+      qc = ar;
+    } else {
+      pc = fma(beta_, vin[0], rc);
+      qc = fma(beta_, vin[1], ar);
+    }
+    p[i] = pc;
+    q[i] = qc;
+    acc[0].add(pc, qc);
+  }
+  __device__ __forceinline__ void operator()(double* t) const {
+    sc->pAp = t[0];
+    sc->alpha = (t[0] != 0.0) ? sc->rr / t[0] : 0.0;
+    sc->first = 0;
+    sc->xdefer = 0;
+  }
+};
+
 // Initial residual of a Poisson solve (S3, S5): rhs = 4 pi rho with
 // rho = rho_in or u^2 + b; r = rhs + L_h phi (= rhs - (-L_h) phi); reduces
 // sum u^2 (for C_h), ||rhs||^2 and ||r||^2 and sets up the CG scalars.
@@ -532,6 +579,7 @@ struct EpiResidual {
     sc->max_it = max_it;
     sc->first = 1;
     sc->beta = 0.0;
+    sc->xdefer = 0;
     const double thr = tol * tol * (t[1] > 0.0 ? t[1] : 1.0);
     sc->done = (!want_r || t[2] <= thr || max_it <= 0) ? 1 : 0;
   }
@@ -794,6 +842,110 @@ __global__ void __launch_bounds__(256) cg_update_kernel(long long G, X* __restri
   grid_sum<1, 256>(acc, smem, red, gridDim.x, blockIdx.x, threadIdx.x, fin);
 }
 
+// CG second half when the iterate update is folded into the next stencil pass
+// (EpiCgAX): r -= alpha q and r.r only; the last block sets beta, counts the
+// iteration, raises `done` and marks x += alpha p as pending (xdefer).
+template <typename T, bool WIDE = false>
+__global__ void __launch_bounds__(256) cg_update_r_kernel(long long G, T* __restrict__ r, const T* __restrict__ Ap,
+                                                          CgScalars* sc, RedBuf red) {
+  __shared__ double smem[256 / 32];
+  DotAcc<T> dacc;
+  if constexpr (WIDE) {
+    using VT = typename Vec16<T>::type;
+    constexpr int VW = 16 / (int)sizeof(T);
+    constexpr int UV = 4;  // vectors per thread and pass
+    const long long nv = G / VW;
+    const VT* a4 = reinterpret_cast<const VT*>(Ap);
+    VT* r4 = reinterpret_cast<VT*>(r);
+    const long long stride = (long long)gridDim.x * 256 * UV;
+    bool first = true;
+    T alpha = T(0);
+    for (long long v0 = (long long)blockIdx.x * 256 * UV + threadIdx.x; v0 < nv; v0 += stride) {
+      VT av[UV], rv[UV];
+#pragma unroll
+      for (int u = 0; u < UV; ++u) {
+        const long long v = v0 + 256 * u;
+        if (v < nv) {
+          av[u] = a4[v];
+          rv[u] = r4[v];
+        }
+      }
+      if (first) {  // the CG scalars arrive with the first loads
+        const int done = sc->done;
+        alpha = (T)sc->alpha;
+        first = false;
+        if (done) return;
+      }
+#pragma unroll
+      for (int u = 0; u < UV; ++u) {
+        const long long v = v0 + 256 * u;
+        if (v < nv) {
+          T ae[VW], re[VW];
+          Vec16<T>::get(av[u], ae);
+          Vec16<T>::get(rv[u], re);
+#pragma unroll
+          for (int l = 0; l < VW; ++l) {
+            re[l] = fma(-alpha, ae[l], re[l]);
+            dacc.add(re[l], re[l]);
+          }
+          r4[v] = Vec16<T>::make(re);
+        }
+      }
+    }
+    if (first && sc->done) return;  // threads without elements take the same exit
+  } else {
+    if (sc->done) return;
+    const T alpha = (T)sc->alpha;
+    const long long stride = (long long)gridDim.x * 1024;
+    for (long long i0 = (long long)blockIdx.x * 1024 + threadIdx.x; i0 < G; i0 += stride) {
+      T av[4], rv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const long long i = i0 + 256 * u;
+        if (i < G) {
+          av[u] = Ap[i];
+          rv[u] = r[i];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const long long i = i0 + 256 * u;
+        if (i < G) {
+          const T ri = fma(-alpha, av[u], rv[u]);
+          r[i] = ri;
+          dacc.add(ri, ri);
+        }
+      }
+    }
+  }
+  double acc[1] = {dacc.value()};
+  struct Fin {
+    CgScalars* sc;
+    __device__ void operator()(double* t) const {
+      const double rr_new = t[0];
+      sc->beta = (sc->rr != 0.0) ? rr_new / sc->rr : 0.0;
+      sc->rr_prev = sc->rr;
+      sc->rr = rr_new;
+      sc->iters += 1;
+      sc->xdefer = 1;
+      const double thr = sc->tol2 * (sc->bb > 0.0 ? sc->bb : 1.0);
+      if (rr_new <= thr || sc->iters >= sc->max_it || !(rr_new == rr_new)) sc->done = 1;
+    }
+  } fin{sc};
+  grid_sum<1, 256>(acc, smem, red, gridDim.x, blockIdx.x, threadIdx.x, fin);
+}
+
+// Applies a pending x += alpha p (xdefer) after the last CG iteration of a call.
+template <typename T>
+__global__ void __launch_bounds__(256) cg_xflush_kernel(long long G, T* __restrict__ x, const T* __restrict__ p,
+                                                        const CgScalars* sc) {
+  if (!sc->xdefer) return;
+  const T alpha = (T)sc->alpha;
+  for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < G; i += (long long)gridDim.x * 256)
+    x[i] = fma(alpha, p[i], x[i]);
+}
+static __global__ void cg_xclear_kernel(CgScalars* sc) { sc->xdefer = 0; }
+
 // Residual replacement of the mixed CG: r32 = (float) r64 (the FP64 true
 // residual).  On the first round the CG starts from scratch (p = r); later
 // rounds keep the search direction and rescale beta to the replaced residual.
@@ -823,6 +975,7 @@ static __global__ void __launch_bounds__(256) refine_replace_kernel(long long G,
       sc->rr = t[0];
       sc->rr0 = t[0];
       sc->bb = t[0];
+      sc->xdefer = 0;
       sc->tol2 = tol * tol;
       sc->max_it = sc->iters + budget;
       sc->done = (t[0] == 0.0 || budget <= 0) ? 1 : 0;
@@ -964,6 +1117,61 @@ __global__ void __launch_bounds__(256) convert_kernel(long long G, D* out, const
 
 // ------------------------------------------------- batched pointwise ops ---
 // CG second half on one grid of a batch (same arithmetic as cg_update_kernel).
+// CG second half with the iterate update folded into the next stencil pass
+// (same arithmetic as cg_update_r_kernel).
+template <typename T>
+struct OpCgUpdateR {
+  static constexpr int K = 1;
+  T* r;
+  const T* q;
+  CgScalars* sc;
+  RedBuf red;
+  int nblocks;
+  using Acc = DotAcc<T>;
+  T al_ = T(0);
+  __device__ __forceinline__ bool skip() const { return sc->done != 0; }
+  __device__ __forceinline__ void load() { al_ = (T)sc->alpha; }
+  __device__ __forceinline__ void apply(long long i, Acc* acc) const {
+    const T ri = fma(-al_, q[i], r[i]);
+    r[i] = ri;
+    acc[0].add(ri, ri);
+  }
+  __device__ __forceinline__ void operator()(double* t) const {
+    const double rr_new = t[0];
+    sc->beta = (sc->rr != 0.0) ? rr_new / sc->rr : 0.0;
+    sc->rr_prev = sc->rr;
+    sc->rr = rr_new;
+    sc->iters += 1;
+    sc->xdefer = 1;
+    const double thr = sc->tol2 * (sc->bb > 0.0 ? sc->bb : 1.0);
+    if (rr_new <= thr || sc->iters >= sc->max_it || !(rr_new == rr_new)) sc->done = 1;
+  }
+};
+
+// Pending x += alpha p of one grid after its CG loop (as cg_xflush_kernel); the
+// last block clears xdefer.
+template <typename T>
+struct OpXFlush {
+  static constexpr int K = 1;
+  T* x;
+  const T* p;
+  CgScalars* sc;
+  RedBuf red;
+  int nblocks;
+  using Acc = double;
+  int on_ = 0;
+  T al_ = T(0);
+  __device__ __forceinline__ bool skip() const { return false; }
+  __device__ __forceinline__ void load() {
+    on_ = sc->xdefer;
+    al_ = (T)sc->alpha;
+  }
+  __device__ __forceinline__ void apply(long long i, Acc*) const {
+    if (on_) x[i] = fma(al_, p[i], x[i]);
+  }
+  __device__ __forceinline__ void operator()(double*) const { sc->xdefer = 0; }
+};
+
 template <typename T, typename X = T>
 struct OpCgUpdate {
   static constexpr int K = 1;
@@ -1097,6 +1305,7 @@ struct OpRefineReplace {
     sc->rr = t[0];
     sc->rr0 = t[0];
     sc->bb = t[0];
+    sc->xdefer = 0;
     sc->tol2 = tol * tol;
     sc->max_it = sc->iters + budget;
     sc->done = (t[0] == 0.0 || budget <= 0) ? 1 : 0;

@@ -47,8 +47,14 @@ def main():
         ctx.profile(False)
     es = 4 if args.prec == "fp32" else 8
     G = g.size
-    out = {"grid": args.n, "order": args.order, "prec": args.prec, "cg_iterations": st.iterations}
-    for k, name, acc in [(F.K_CG_DIR_STENCIL, "cg_dir_stencil", 5), (F.K_CG_UPDATE, "cg_update", 6)]:
+    out = {"grid": args.n, "order": args.order, "prec": args.prec, "cg_iterations": st.iterations,
+           "folded_update": bool(5 * g.size * es > 96 * (1 << 20))}
+    # per node: the stencil pass reads r, p, q and writes p, q; the update reads x, r, p, q and writes
+    # x, r -- or, when the five vectors exceed 96 MB, the stencil pass also moves x (folded update)
+    # and the update only reads r, q and writes r
+    fold = 5 * G * es > 96 * (1 << 20)
+    for k, name, acc in [(F.K_CG_DIR_STENCIL, "cg_dir_stencil", 7 if fold else 5),
+                         (F.K_CG_UPDATE, "cg_update", 3 if fold else 6)]:
         n = cnt.timed_launches[k]
         if n:
             us = cnt.timed_ms[k] / n * 1e3
