@@ -94,6 +94,32 @@ __device__ __forceinline__ double to_double(double v) { return v; }
 template <typename T>
 __device__ __forceinline__ double to_double(const DotAcc<T>& a) { return a.value(); }
 
+// Accumulator of the functional pass's sums: plain FP64 for FP64 fields; for
+// FP32 fields the compensated FP32 pair of DotAcc (no FP64 arithmetic per node),
+// with add_d for the terms formed in FP64 (the electrostatic sums of MIXED).
+template <typename T>
+struct FAcc;
+template <>
+struct FAcc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double a, double b) { s += a * b; }
+  __device__ __forceinline__ void add_d(double v) { s += v; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct FAcc<float> {
+  DotAcc<float> a;
+  __device__ __forceinline__ void add(float x, float y) { a.add(x, y); }
+  __device__ __forceinline__ void add_d(double v) {
+    const float hi = (float)v;
+    a.add(hi, 1.0f);
+    a.add((float)(v - (double)hi), 1.0f);
+  }
+  __device__ __forceinline__ double value() const { return a.value(); }
+};
+template <typename T>
+__device__ __forceinline__ double to_double(const FAcc<T>& a) { return a.value(); }
+
 // Asynchronous global -> shared copy of BYTES = 4, 8 or 16 bytes (16: both
 // addresses 16-byte aligned; bypasses L1).  src_valid == false fills the
 // destination with zeros (the zero Dirichlet value of every out-of-grid node)
@@ -631,7 +657,7 @@ template <typename T>
 struct EpiFunctional {
   static constexpr int K = 11;
   static constexpr int NIN = 0;
-  using Acc = double;
+  using Acc = FAcc<T>;
   const T* phi;
   const T* b;
   const T* rcg;
@@ -644,6 +670,7 @@ struct EpiFunctional {
   FuncScalars f;
   double* out;  // 11 sums + C
   T mult_ = T(0);  // -eta + C/mu, from the device sum of u^2 (load())
+  T cf_ = T(0), vk_ = T(0), lam_ = T(0), kvw_ = T(0);  // FuncScalars in the field type (load())
   // MIXED: the FP64 potential, pseudocharge and Poisson residual.  With them the
   // electrostatic energy sums use the same FP64 phi and rho = u^2 + b as the FP64
   // residual of the Poisson solve (no FP32 rounding of phi in the variational
@@ -655,9 +682,13 @@ struct EpiFunctional {
   __device__ __forceinline__ void load() {
     const double C = f.h3 * *sum_uu - f.N;
     mult_ = (T)(-f.eta + C * f.inv_mu);
+    cf_ = (T)f.CF;
+    vk_ = (T)(5.0 / 3.0 * f.CF);
+    lam_ = (T)(-f.lambda);
+    kvw_ = (T)f.kin_vw;
   }
   __host__ __device__ __forceinline__ const T* input(int) const { return nullptr; }
-  __device__ __forceinline__ void apply(long long i, T uc, T lap, const T*, double* acc) const {
+  __device__ __forceinline__ void apply(long long i, T uc, T lap, const T*, Acc* acc) const {
     const T mult = mult_;
     const bool tf = f.terms & 1, vw = f.terms & 2, xc = f.terms & 4, es = f.terms & 8;
     const T ux = fabs(uc);
@@ -665,42 +696,43 @@ struct EpiFunctional {
     if (tf) {
       const T c = cbrt(ux);
       const T u43 = (c * c) * (c * c);
-      vk = (T)(5.0 / 3.0 * f.CF) * u43;
-      acc[0] += f.CF * (double)u43 * (double)ux * (double)ux;
+      vk = vk_ * u43;
+      acc[0].add(cf_ * u43, ux * ux);
     }
-    if (vw) acc[1] += (double)uc * (double)lap;
+    if (vw) acc[1].add(uc, lap);
     if (xc) {
       xc_eval<T>(ux, exc, vxc);
-      acc[2] += (double)exc * (double)ux * (double)ux;
+      acc[2].add(exc, ux * ux);
     }
     if (es) {
       if (phi64) {
         const double phd = phi64[i];
         ph = (T)phd;
-        acc[3] += ((double)uc * (double)uc + b64[i]) * phd;
-        if (r64) acc[4] += phd * r64[i];
+        acc[3].add_d(((double)uc * (double)uc + b64[i]) * phd);
+        if (r64) acc[4].add_d(phd * r64[i]);
       } else {
         ph = phi[i];
         const T rho = uc * uc + b[i];
-        acc[3] += (double)rho * (double)ph;
-        if (rcg) acc[4] += (double)ph * (double)rcg[i];
+        acc[3].add(rho, ph);
+        if (rcg) acc[4].add(ph, rcg[i]);
       }
     }
-    const T gx = (vw ? (T)(-f.lambda) * lap : T(0)) + T(2) * (vk + vxc + ph) * uc + T(2) * mult * uc;
-    const T kin = (vw ? (T)f.kin_vw : T(0)) + (T)(14.0 / 3.0) * vk;
+    const T gx = (vw ? lam_ * lap : T(0)) + T(2) * (vk + vxc + ph) * uc + T(2) * mult * uc;
+    const T kin = (vw ? kvw_ : T(0)) + (T)(14.0 / 3.0) * vk;
     T md = kin + T(2) * (vxc + ph + mult);
     md = fmax(md, (T)0.25 * kin);
     md = fmax(md, (T)1e-10);
     const T sx = -gx / md;
+    const T wv = uc / md;
     if (G) G[i] = gx;
     if (s) s[i] = sx;
-    if (winv) winv[i] = uc / md;
-    if (d) acc[5] += (double)gx * (double)d[i];
-    if (s_old) acc[6] += (double)gx * (double)s_old[i];
-    acc[7] += (double)gx * (double)gx / (double)md;
-    acc[8] += (double)gx * (double)gx;
-    acc[9] += (double)uc * (double)sx;
-    acc[10] += (double)uc * (double)uc / (double)md;
+    if (winv) winv[i] = wv;
+    if (d) acc[5].add(gx, d[i]);
+    if (s_old) acc[6].add(gx, s_old[i]);
+    acc[7].add(gx, -sx);  // g^2 / diag
+    acc[8].add(gx, gx);
+    acc[9].add(uc, sx);
+    acc[10].add(uc, wv);  // u^2 / diag
   }
   __device__ __forceinline__ void operator()(double* t) const {
 #pragma unroll
