@@ -257,7 +257,9 @@ def run_gpu(args):
     # timed region (device time per step, L2 flushed between steps)
     dom = F.K_CG_DIR_STENCIL
     ctx.reset_counters()
-    ctx.profile((1 << dom) if args.profile_timed else 0)  # events around the dominant kernel only
+    # events around the dominant kernel only: the persistent CG launches, else
+    # one CG stencil pass in eight
+    ctx.profile(((1 << dom) | (1 << F.K_CG_PERSISTENT)) if args.profile_timed else 0)
     lat = []
     stats = []
     barrier(pg)
@@ -292,13 +294,49 @@ def run_gpu(args):
     e2e_val, e2e_max = job_rate(pg, ws, args.steps, sum(e2e_t), dev)
     h2d = c.R.nbytes + c.Z.nbytes
     d2h = 8 + 3 * c.M * 8
-    # roofline of the dominant kernel (the CG direction + stencil pass)
-    tl, tms = cnt.timed_launches[dom], cnt.timed_ms[dom]
+    # roofline of the dominant kernel: the persistent CG kernel where the
+    # library ran it, else the CG direction + stencil pass
     es = 4 if prec == F.PREC_MIXED else 8
     roof = None
-    if tl > 0:
+    n = c.fd_order // 2
+    pk = F.K_CG_PERSISTENT
+    if cnt.timed_launches[pk] > 0 and cnt.persistent_cg_iters > 0:
+        tl, tms, its = cnt.timed_launches[pk], cnt.timed_ms[pk], cnt.persistent_cg_iters
         avg_s = tms / tl / 1e3
-        n = c.fd_order // 2
+        traffic = None
+        try:
+            with open(TRAFFIC_FILE) as f:
+                tr = json.load(f)
+            key = f"cg_persistent_{args.precision}"
+            if tr.get("src_hash") == src_hash() and key in tr:
+                traffic = tr[key]["bytes_per_iteration_full"] * its / tl
+        except Exception:
+            pass
+        # per CG iteration: stencil half reads r, p, q and writes p, q; update
+        # half reads x, p, q, r and writes x, r
+        algo_it = 11 * G * es
+        kname = "cg_coop_kernel<%s,%d,%d> (whole CG iterations: q = A r + beta q, p = r + beta p, p.q | " \
+                "x += alpha p, r -= alpha q, r.r)" % ("float" if es == 4 else "double", n, 16 // es)
+        common = {"traffic": traffic, "kernel": kname, "launches": tl, "avg_us": avg_s * 1e6,
+                  "cg_iters_per_launch": its / tl,
+                  "timing": "CUDA events on the solve's stream around every persistent CG launch, over the "
+                            "whole timed region",
+                  "algorithmic_bytes_per_launch": algo_it * its / tl}
+        if prec == F.PREC_MIXED:
+            peak, which = load_peaks()
+            ach = algo_it * its / (tms / 1e3) / 1e9
+            roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                    "peak_source": which, **common}
+        else:
+            flops_it = G * (2 * (6 * n + 1) + 12)  # stencil, p, q, x, r updates, p.q, r.r
+            ach = flops_it * its / (tms / 1e3) / 1e9
+            roof = {"bound": "alu", "achieved": ach, "peak": FP64_ALU_PEAK_GFLOPS, "unit": "GFLOP/s",
+                    "frac": ach / FP64_ALU_PEAK_GFLOPS,
+                    "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2070 MHz",
+                    "algorithmic_flops_per_launch": flops_it * its / tl, **common}
+    tl, tms = cnt.timed_launches[dom], cnt.timed_ms[dom]
+    if roof is None and tl > 0:
+        avg_s = tms / tl / 1e3
         traffic = None
         try:
             with open(TRAFFIC_FILE) as f:
@@ -329,7 +367,7 @@ def run_gpu(args):
                     "avg_us": avg_s * 1e6, "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2070 MHz",
                     "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": G * (7 if fold else 5) * es}
     kinds = {F.KIND_NAMES[k]: {"launches": int(cnt.kind_launches[k]),
-                               "ms": round(cnt.timed_ms[k], 3)} for k in range(7) if cnt.kind_launches[k]}
+                               "ms": round(cnt.timed_ms[k], 3)} for k in range(F.K_COUNT) if cnt.kind_launches[k]}
     st = stats[-1]
     lat_sorted = sorted(lat)
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

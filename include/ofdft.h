@@ -286,6 +286,7 @@ enum {
   OFDFT_K_FUNCTIONAL = 4,       /* S4 fused energy + gradient */
   OFDFT_K_VECTOR = 5,           /* S6/S7 dots, NLCG updates, conversions */
   OFDFT_K_ATOMS = 6,            /* S1/S9 pseudocharge, guess, forces */
+  OFDFT_K_CG_PERSISTENT = 7,    /* S3 CG: whole iterations (both halves) in one cooperative launch */
   OFDFT_K_COUNT = 8
 };
 
@@ -294,6 +295,7 @@ typedef struct {
   long long kind_launches[OFDFT_K_COUNT];  /* per OFDFT_K_* kind */
   long long timed_launches[OFDFT_K_COUNT]; /* launches bracketed by CUDA events */
   double timed_ms[OFDFT_K_COUNT];          /* summed event durations (ms) */
+  long long persistent_cg_iters;           /* CG iterations run by OFDFT_K_CG_PERSISTENT launches */
 } ofdft_counters;
 
 /* Tracing (no counterpart in the paper, which reports wall time and counts of

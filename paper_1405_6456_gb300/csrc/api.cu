@@ -17,19 +17,21 @@ int cg_update(ofdft_ctx* c, const GridDev& g, T* x, T* r, T* pv, T* qv, CgScalar
     auto aligned = [](const void* q) { return ((uintptr_t)q & 15u) == 0; };
     const bool wide = g.G % (16 / (long long)sizeof(T)) == 0 && aligned(r) && aligned(qv) && aligned(x) &&
                       aligned(pv);
+    const dim3 gr(pb), bl(256);
+    const T* cqv = qv;
     if (fold) {
       if (wide)
-        cg_update_r_kernel<T, true><<<pb, 256, 0, c->stream>>>(g.G, r, qv, sc, red(c));
+        CU(launch_k(c, cg_update_r_kernel<T, true>, gr, bl, 0, g.G, r, cqv, sc, red(c)));
       else
-        cg_update_r_kernel<T, false><<<pb, 256, 0, c->stream>>>(g.G, r, qv, sc, red(c));
+        CU(launch_k(c, cg_update_r_kernel<T, false>, gr, bl, 0, g.G, r, cqv, sc, red(c)));
     } else {
+      const T* cpv = pv;
       if (wide)
-        cg_update_kernel<T, T, true><<<pb, 256, 0, c->stream>>>(g.G, x, r, pv, qv, sc, red(c));
+        CU(launch_k(c, cg_update_kernel<T, T, true>, gr, bl, 0, g.G, x, r, cpv, cqv, sc, red(c)));
       else
-        cg_update_kernel<T, T><<<pb, 256, 0, c->stream>>>(g.G, x, r, pv, qv, sc, red(c));
+        CU(launch_k(c, cg_update_kernel<T, T, false>, gr, bl, 0, g.G, x, r, cpv, cqv, sc, red(c)));
     }
   }
-  CU(cudaGetLastError());
   return OFDFT_OK;
 }
 
@@ -220,6 +222,91 @@ int cg_graph(ofdft_ctx* c, int R, const GridDev& g, double h, const Weights<doub
   return OFDFT_OK;
 }
 
+// Persistent CG: one cooperative launch of cg_coop_kernel runs up to kChunk
+// iterations (both halves of each, with grid-wide sums between them), so an
+// iteration costs no launch gaps and no separate update kernel.  Needs 16-byte
+// staging (the kernel's loads bypass L1: other blocks write r within the launch)
+// and a grid whose blocks are all co-resident; *used = false otherwise, and the
+// caller runs the two-kernel iteration.
+template <typename T, int R>
+int cg_coop_r(ofdft_ctx* c, const GridDev& g, const Weights<double>& Wneg, T* x, T* r, T* pv, T* qv, CgScalars* sc,
+              int max_it, CgScalars* host_sc, bool* used) {
+  constexpr int VW = 16 / (int)sizeof(T);
+  *used = false;
+  // grids whose CG vectors overflow L2 run faster as two kernels with the
+  // folded iterate update (at 256^3: 160 against 250 us per iteration)
+  if (cg_fold<T>(g)) return OFDFT_OK;
+  if (!zvec_ok<T>(g, LoadPlain<T>{r}, EpiCgAv<T>{pv, qv, 0, T(0)})) return OFDFT_OK;
+  auto* kern = cg_coop_kernel<T, R, VW>;
+  constexpr int smem = zsmem_bytes<T, R, VW, EpiCgAv<T>>();
+  static int per_sm = 0;
+  if (!per_sm) {
+    CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    int nb = 0;
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, NT, smem));
+    per_sm = std::max(nb, 0) + 1;  // +1: cached even when 0
+  }
+  const long long maxb = (long long)(per_sm - 1) * c->sms;
+  const int gx = (g.n1 + BX - 1) / BX, gy = (g.n2 + ZCfg<T>::TY - 1) / ZCfg<T>::TY;
+  const long long tiles = (long long)gx * gy;
+  if (maxb < 1 || tiles > maxb) return OFDFT_OK;
+  // z-split: as many chunks as co-resident blocks allow (at 128^3, FP32: 4 x 4
+  // tiles x 19 chunks of 7 planes, 304 blocks, 2 per SM), at least 2 planes each
+  int nz = (int)std::min<long long>(maxb / tiles, std::max(1, g.n3 / 2));
+  if (c->coop_nz > 0) nz = (int)std::min<long long>(maxb / tiles, c->coop_nz);
+  nz = std::max(nz, 1);
+  const int zc = (g.n3 + nz - 1) / nz;
+  nz = (g.n3 + zc - 1) / zc;
+  const int nblocks = (int)(tiles * nz);
+  TRY(ensure_partials(c, 2LL * nblocks, 1));
+  if (!c->coop_bar) CU(cudaMalloc(&c->coop_bar, 256));
+  CU(cudaMemsetAsync(c->coop_bar, 0, sizeof(unsigned int), c->stream));
+  *used = true;
+  GridDev gg = g;
+  Weights<T> W = cast_weights<T>(Wneg);
+  int zchunk = zc;
+  double* partials = static_cast<double*>(c->partials.p);
+  unsigned int* bar = c->coop_bar;
+  const dim3 grid(gx, gy, nz), block(BX, BY);
+  int launched = 0, chunks = 0;
+  while (launched < max_it) {
+    int niter = std::min(kChunk, max_it - launched);
+    void* args[] = {&gg, &W, &zchunk, &x, &r, &pv, &qv, &sc, &partials, &bar, &niter};
+    {
+      ProfScope ps_(c, OFDFT_K_CG_PERSISTENT);
+      CU(cudaLaunchCooperativeKernel((const void*)kern, grid, block, args, smem, c->stream));
+    }
+    launched += niter;
+    const int slot = chunks & 1;
+    CU(cudaMemcpyAsync(&c->ring[slot], sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaEventRecord(c->ring_ev[slot], c->stream));
+    if (chunks > 0) {
+      CU(cudaEventSynchronize(c->ring_ev[slot ^ 1]));
+      if (c->ring[slot ^ 1].err) return fail(c, OFDFT_ETIMEOUT, "persistent CG: a grid barrier timed out");
+      if (c->ring[slot ^ 1].done) break;
+    }
+    ++chunks;
+  }
+  const int it0 = host_sc->iters;
+  TRY(sync_scalars(c, sc, sizeof(CgScalars), host_sc));
+  if (host_sc->err) return fail(c, OFDFT_ETIMEOUT, "persistent CG: a grid barrier timed out");
+  c->coop_iters += host_sc->iters - it0;
+  return OFDFT_OK;
+}
+
+template <typename T>
+int cg_coop(ofdft_ctx* c, int R, const GridDev& g, const Weights<double>& Wneg, T* x, T* r, T* pv, T* qv,
+            CgScalars* sc, int max_it, CgScalars* host_sc, bool* used) {
+  switch (R) {
+    case 1: return cg_coop_r<T, 1>(c, g, Wneg, x, r, pv, qv, sc, max_it, host_sc, used);
+    case 2: return cg_coop_r<T, 2>(c, g, Wneg, x, r, pv, qv, sc, max_it, host_sc, used);
+    case 3: return cg_coop_r<T, 3>(c, g, Wneg, x, r, pv, qv, sc, max_it, host_sc, used);
+    case 4: return cg_coop_r<T, 4>(c, g, Wneg, x, r, pv, qv, sc, max_it, host_sc, used);
+    case 5: return cg_coop_r<T, 5>(c, g, Wneg, x, r, pv, qv, sc, max_it, host_sc, used);
+    default: return cg_coop_r<T, 6>(c, g, Wneg, x, r, pv, qv, sc, max_it, host_sc, used);
+  }
+}
+
 // Plain CG iterations on the prepared scalars `sc` (residual r, iterate x),
 // checking the device `done` flag every kChunk iterations.  Chunk k+1 is
 // enqueued before the host waits for chunk k's copy of the scalars, so the
@@ -233,6 +320,12 @@ int cg_iterate(ofdft_ctx* c, int R, const GridDev& g, double h, const Weights<do
                CgScalars* sc, int max_it, CgScalars* host_sc) {
   T* pv = vec<T>(c, V_P0);
   T* qv = vec<T>(c, V_AP);
+  const bool per_launch = (c->prof & (1 << OFDFT_K_CG_UPDATE)) != 0;  // per-kernel timing asked for
+  if (c->coop && !per_launch) {
+    bool used = false;
+    TRY(cg_coop<T>(c, R, g, Wneg, reinterpret_cast<T*>(x), r, pv, qv, sc, max_it, host_sc, &used));
+    if (used) return OFDFT_OK;
+  }
   const int pb = pointwise_blocks(c, g.G);
   TRY(ensure_partials(c, pb, 1));
   TRY(ensure_partials(c, zshape<T>(c, g, R, 32).nblocks, 1));
@@ -1313,6 +1406,10 @@ int ofdft_create(ofdft_ctx** out, int device, void* stream) {
   if (cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking) != cudaSuccess) c->use_graphs = 0;
   const char* at = getenv("OFDFT_AUTOTUNE");
   c->autotune = !(at && at[0] == '0');
+  const char* co = getenv("OFDFT_COOP");  // 1: persistent cooperative CG iterations where they apply
+  c->coop = (co && co[0] == '1') ? 1 : 0;
+  const char* cz = getenv("OFDFT_COOP_NZ");  // launch-shape experiments: z-chunks of the persistent CG grid
+  c->coop_nz = cz ? atoi(cz) : 0;
   const char* pw = getenv("OFDFT_POINTWISE_BLOCKS_PER_SM");  // launch-shape experiments (default 4)
   if (pw && atoi(pw) >= 1 && atoi(pw) <= 16) c->pw_per_sm = atoi(pw);
   cudaMemset(c->sc, 0, 3 * sizeof(CgScalars));
@@ -1330,6 +1427,7 @@ int ofdft_destroy(ofdft_ctx* c) {
   harvest(c);
   for (auto& e : c->graphs) cudaGraphExecDestroy(e.exec);
   if (c->gstream) cudaStreamDestroy(c->gstream);
+  if (c->coop_bar) cudaFree(c->coop_bar);
   for (auto& s : c->gev)
     for (auto& e : s)
       if (e) cudaEventDestroy(e);
@@ -1366,6 +1464,7 @@ int ofdft_get_counters(ofdft_ctx* c, ofdft_counters* out) {
     out->timed_launches[k] = c->timed_launches[k];
     out->timed_ms[k] = c->timed_ms[k];
   }
+  out->persistent_cg_iters = c->coop_iters;
   return OFDFT_OK;
 }
 
@@ -1380,6 +1479,7 @@ int ofdft_reset_counters(ofdft_ctx* c) {
     c->timed_launches[k] = 0;
     c->timed_ms[k] = 0.0;
   }
+  c->coop_iters = 0;
   return OFDFT_OK;
 }
 

@@ -70,6 +70,10 @@ struct ofdft_ctx {
   std::vector<long long> last_zkey;            // key of the last z-streaming launch
   int force_nz = -1;                           // >= 0: z-split of the next launches (autotuner)
   int pw_per_sm = 4;                           // blocks per SM of the pointwise passes
+  int coop = 0;                                // persistent cooperative CG iterations (opt-in)
+  unsigned int* coop_bar = nullptr;            // arrival counter of its grid barriers
+  long long coop_iters = 0;                    // CG iterations run by it (trace counter)
+  int coop_nz = 0;                             // z-chunks of its grid (0: the default rule)
   int autotune = 1;
 };
 
@@ -341,6 +345,13 @@ bool zvec_ok(const GridDev& g, const L& ld, const E& ep) {
   return true;
 }
 
+// Launches kern on the context's stream.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(ofdft_ctx* c, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, Args... args) {
+  kern<<<grid, block, smem, c->stream>>>(args...);
+  return cudaGetLastError();
+}
+
 template <typename T, int R, int V, class L, class E>
 int launch_zv(ofdft_ctx* c, const GridDev& g, const Weights<double>& W, L ld, E ep, int kind) {
   constexpr int smem = zsmem_bytes<T, R, V, E>();
@@ -367,10 +378,9 @@ int launch_zv(ofdft_ctx* c, const GridDev& g, const Weights<double>& W, L ld, E 
   if (E::K > 0) TRY(ensure_partials(c, s.nblocks, E::K));
   {
     ProfScope ps_(c, kind);
-    zstream_kernel<T, R, V, L, E><<<s.grid, dim3(BX, BY), smem, c->stream>>>(g, cast_weights<T>(W), s.zchunk, ld,
-                                                                             ep, red(c));
+    CU(launch_k(c, zstream_kernel<T, R, V, L, E>, s.grid, dim3(BX, BY), smem, g, cast_weights<T>(W), s.zchunk, ld,
+                ep, red(c)));
   }
-  CU(cudaGetLastError());
   return OFDFT_OK;
 }
 

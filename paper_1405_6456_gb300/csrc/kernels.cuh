@@ -72,6 +72,7 @@ struct CgScalars {
   int done;       // 1 once converged or out of iterations
   int first;      // 1 until the first search direction is formed
   int xdefer;     // 1 while x += alpha p of the last iteration is still to be applied
+  int err;        // 1 when a grid barrier of the persistent CG kernel timed out
 };
 
 // ---------------------------------------------------------------------------
@@ -179,7 +180,7 @@ constexpr int zsmem_bytes() {
 template <typename T, int R, int V, class Epi>
 __device__ __forceinline__ void zstream_tile(const GridDev& g, const Weights<T>& W, int bx, int by, int z0, int z1,
                                              const T* __restrict__ f, const Epi& ep_in, const RedBuf& red,
-                                             int nblocks, int bid) {
+                                             int nblocks, int bid, double* block_out = nullptr) {
   Epi ep = ep_in;  // block-local copy: load() caches the epilogue's device scalars in registers
   constexpr int CX = ZCfg<T>::CX, RY = ZCfg<T>::RY, THX = ZCfg<T>::THX, TY = ZCfg<T>::TY, ZD = ZCfg<T>::ZD;
   using L = Lanes<T, CX>;
@@ -285,7 +286,7 @@ __device__ __forceinline__ void zstream_tile(const GridDev& g, const Weights<T>&
 #pragma unroll
       for (int l = 0; l < CX; ++l)
         v[l] = (((node_ok >> (i * CX + l)) & 1u) && kk >= 0 && kk < g.n3)
-                   ? f[(long long)g.n1 * (y0 + i) + x0 + l + plane * kk]
+                   ? __ldcg(&f[(long long)g.n1 * (y0 + i) + x0 + l + plane * kk])  // L2: other blocks may have written it
                    : T(0);
       q[i][m] = L::make(v);
     }
@@ -379,8 +380,179 @@ __device__ __forceinline__ void zstream_tile(const GridDev& g, const Weights<T>&
     double accd[Epi::K];
 #pragma unroll
     for (int i = 0; i < Epi::K; ++i) accd[i] = to_double(acc[i]);
+    if (block_out) {  // the block's sums only (valid in thread 0); the caller combines blocks
+      block_sum<Epi::K, NT>(accd, red_smem, tid);
+      if (tid == 0)
+#pragma unroll
+        for (int i = 0; i < Epi::K; ++i) block_out[i] = accd[i];
+      return;
+    }
     Epi fin = ep;
     grid_sum<Epi::K, NT>(accd, red_smem, red, nblocks, bid, tid, fin);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Persistent CG (S3) for one grid: a cooperative launch whose blocks (all
+// co-resident) run up to niter CG iterations, each the z-streaming pass on r
+// (q = A r + beta q, p = r + beta p, p.q) and the x / r update of the block's
+// own nodes (r.r), with a grid-wide sum after each half.  Every block sums the
+// blocks' partials in the same order, so all blocks hold identical alpha, beta
+// and convergence decisions without a second pass; block 0 publishes the CG
+// scalars for the host.  Saves the launch gaps and the separate update kernel
+// of the two-kernel iteration.
+
+// CG epilogue with beta and `first` given as values (no device scalars).
+template <typename T>
+struct EpiCgAv {
+  static constexpr int K = 1;
+  static constexpr int NIN = 2;
+  using Acc = DotAcc<T>;
+  T* p;
+  T* q;
+  int first_;
+  T beta_;
+  __device__ __forceinline__ bool skip() const { return false; }
+  __device__ __forceinline__ void load() {}
+  __host__ __device__ __forceinline__ const T* input(int j) const { return j == 0 ? p : q; }
+  __device__ __forceinline__ void apply(long long i, T rc, T ar, const T* vin, Acc* acc) const {
+    T pc, qc;
+    if (first_) {
+      pc = rc;
+      qc = ar;
+    } else {
+      pc = fma(beta_, vin[0], rc);
+      qc = fma(beta_, vin[1], ar);
+    }
+    p[i] = pc;
+    q[i] = qc;
+    acc[0].add(pc, qc);
+  }
+  __device__ __forceinline__ void operator()(double*) const {}
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide sum over co-resident blocks: each block's thread 0 publishes the
+// block total `v` (valid in thread 0), arrives at a counting barrier and waits
+// (at most ~2 s, then raises *err); afterwards every block sums all partials in
+// block order.  Returns the total in every thread; false after a timeout.
+// `bar` counts arrivals over the whole solve (reset by the host before it), so
+// the target of this barrier is the next multiple of nblocks.
+template <int NT>
+__device__ __forceinline__ bool coop_sum(double& v, double* smem, double* partials, unsigned int* bar, int* err,
+                                         int nblocks, int bid, int tid) {
+  __shared__ int ok_s;
+  __shared__ double tot_s;
+  if (tid == 0) {
+    partials[bid] = v;
+    __threadfence();
+    const unsigned int t = atomicAdd(bar, 1u);
+    const unsigned int target = (t / (unsigned)nblocks + 1u) * (unsigned)nblocks;
+    const unsigned long long t0 = global_ns();
+    int ok = 1;
+    while ((int)(*(volatile unsigned int*)bar - target) < 0) {
+      if (*(volatile int*)err || global_ns() - t0 > 2000000000ull) {
+        atomicExch(err, 1);
+        ok = 0;
+        break;
+      }
+      __nanosleep(32);
+    }
+    __threadfence();
+    ok_s = ok;
+  }
+  __syncthreads();
+  double t[1] = {0.0};
+  for (int b = tid; b < nblocks; b += NT) t[0] += __ldcg(&partials[b]);
+  block_sum<1, NT>(t, smem, tid);
+  if (tid == 0) tot_s = t[0];
+  __syncthreads();
+  v = tot_s;
+  const bool ok = ok_s != 0;
+  __syncthreads();
+  return ok;
+}
+
+template <typename T, int R, int V>
+__global__ void __launch_bounds__(NT, 2) cg_coop_kernel(GridDev g, Weights<T> W, int zchunk, T* __restrict__ x,
+                                                        T* __restrict__ r, T* __restrict__ p, T* __restrict__ q,
+                                                        CgScalars* sc, double* partials, unsigned int* bar,
+                                                        int niter) {
+  constexpr int CX = ZCfg<T>::CX, RY = ZCfg<T>::RY, THX = ZCfg<T>::THX, TY = ZCfg<T>::TY;
+  __shared__ double smem[NT / 32];
+  const int nblocks = gridDim.x * gridDim.y * gridDim.z;
+  const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  const int tid = threadIdx.y * BX + threadIdx.x;
+  const int z0 = blockIdx.z * zchunk, z1 = min(z0 + zchunk, g.n3);
+  // the CG state, identical in every block (all read it before any block writes)
+  double rr = sc->rr, beta = sc->beta, tol2 = sc->tol2, bb = sc->bb, alpha = sc->alpha, pAp = sc->pAp;
+  int first = sc->first, iters = sc->iters, max_it = sc->max_it, done = sc->done;
+  const double thr = tol2 * (bb > 0.0 ? bb : 1.0);
+  __syncthreads();
+  int* err = &sc->err;
+  double* partA = partials;            // p.q of the blocks
+  double* partB = partials + nblocks;  // r.r of the blocks
+  const int tx = tid % THX, ty = tid / THX;
+  const int x0 = blockIdx.x * BX + CX * tx, y0 = blockIdx.y * TY + ty * RY;
+  const long long plane = (long long)g.n1 * g.n2;
+  bool ok = true;
+  for (int it = 0; it < niter && !done && ok; ++it) {
+    // first half: the stencil pass
+    double v = 0.0;
+    zstream_tile<T, R, V>(g, W, blockIdx.x, blockIdx.y, z0, z1, r, EpiCgAv<T>{p, q, first, (T)beta}, RedBuf{},
+                          nblocks, bid, &v);
+    ok = coop_sum<NT>(v, smem, partA, bar, err, nblocks, bid, tid);
+    if (!ok) break;
+    pAp = v;
+    alpha = (pAp != 0.0) ? rr / pAp : 0.0;
+    first = 0;
+    // second half: x += alpha p, r -= alpha q on this block's own nodes
+    const T al = (T)alpha;
+    DotAcc<T> dacc;
+    for (int k = z0; k < z1; ++k)
+#pragma unroll
+      for (int i = 0; i < RY; ++i) {
+        const int y = y0 + i;
+        if (y >= g.n2) continue;
+        const long long o = plane * k + (long long)g.n1 * y;
+#pragma unroll
+        for (int l = 0; l < CX; ++l) {
+          const int xx = x0 + l;
+          if (xx < g.n1) {
+            const T xi = fma(al, p[o + xx], x[o + xx]);
+            const T ri = fma(-al, q[o + xx], r[o + xx]);
+            x[o + xx] = xi;
+            r[o + xx] = ri;
+            dacc.add(ri, ri);
+          }
+        }
+      }
+    double w[1] = {dacc.value()};
+    block_sum<1, NT>(w, smem, tid);
+    v = w[0];
+    ok = coop_sum<NT>(v, smem, partB, bar, err, nblocks, bid, tid);
+    if (!ok) break;
+    const double rr_new = v;
+    beta = (rr != 0.0) ? rr_new / rr : 0.0;
+    const double rr_prev = rr;
+    rr = rr_new;
+    iters += 1;
+    if (rr_new <= thr || iters >= max_it || !(rr_new == rr_new)) done = 1;
+    if (bid == 0 && tid == 0) {
+      sc->pAp = pAp;
+      sc->alpha = alpha;
+      sc->first = 0;
+      sc->beta = beta;
+      sc->rr_prev = rr_prev;
+      sc->rr = rr;
+      sc->iters = iters;
+      sc->done = done;
+    }
   }
 }
 
@@ -606,6 +778,7 @@ struct EpiResidual {
     sc->first = 1;
     sc->beta = 0.0;
     sc->xdefer = 0;
+    sc->err = 0;
     const double thr = tol * tol * (t[1] > 0.0 ? t[1] : 1.0);
     sc->done = (!want_r || t[2] <= thr || max_it <= 0) ? 1 : 0;
   }
@@ -1008,6 +1181,7 @@ static __global__ void __launch_bounds__(256) refine_replace_kernel(long long G,
       sc->rr0 = t[0];
       sc->bb = t[0];
       sc->xdefer = 0;
+      sc->err = 0;
       sc->tol2 = tol * tol;
       sc->max_it = sc->iters + budget;
       sc->done = (t[0] == 0.0 || budget <= 0) ? 1 : 0;
@@ -1338,6 +1512,7 @@ struct OpRefineReplace {
     sc->rr0 = t[0];
     sc->bb = t[0];
     sc->xdefer = 0;
+    sc->err = 0;
     sc->tol2 = tol * tol;
     sc->max_it = sc->iters + budget;
     sc->done = (t[0] == 0.0 || budget <= 0) ? 1 : 0;

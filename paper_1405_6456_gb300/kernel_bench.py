@@ -12,6 +12,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import os
 
 import numpy as np
 
@@ -38,6 +39,9 @@ def main():
     # warm-up, then the timed solve (FP32 fields go through the mixed path's FP32 CG
     # only when called with float tensors: here a plain FP32 CG is not exposed, so
     # the FP32 case times the mixed solve's FP32 correction iterations)
+    # the default two-kernel iteration, then (a context created with
+    # OFDFT_COOP=1) the persistent cooperative kernel where the grid's blocks fit
+    # on the GPU at once
     for rep in range(2):
         phi = torch.zeros(g.shape, dtype=dt, device="cuda:0")
         ctx.reset_counters()
@@ -45,6 +49,16 @@ def main():
         st = ctx.poisson(g, args.order, phi, rho=rho, tol=1e-300, max_it=args.iters, allow_notconv=True)
         cnt = ctx.counters()
         ctx.profile(False)
+    os.environ["OFDFT_COOP"] = "1"
+    ctxp = F.Context(0)
+    for rep in range(2):
+        phi = torch.zeros(g.shape, dtype=dt, device="cuda:0")
+        ctxp.reset_counters()
+        ctxp.profile(1 << F.K_CG_PERSISTENT)
+        ctxp.poisson(g, args.order, phi, rho=rho, tol=1e-300, max_it=args.iters, allow_notconv=True)
+        cntp = ctxp.counters()
+        ctxp.profile(False)
+    ctxp.close()
     es = 4 if args.prec == "fp32" else 8
     G = g.size
     out = {"grid": args.n, "order": args.order, "prec": args.prec, "cg_iterations": st.iterations,
@@ -60,6 +74,12 @@ def main():
             us = cnt.timed_ms[k] / n * 1e3
             out[name] = {"launches": n, "avg_us": us, "algorithmic_bytes": G * acc * es,
                          "GBps": G * acc * es / (us * 1e-6) / 1e9}
+    its = cntp.persistent_cg_iters
+    if cntp.timed_launches[F.K_CG_PERSISTENT] and its:
+        us_it = cntp.timed_ms[F.K_CG_PERSISTENT] / its * 1e3
+        out["cg_persistent"] = {"launches": cntp.timed_launches[F.K_CG_PERSISTENT], "iterations": its,
+                                "avg_us_per_iteration": us_it, "algorithmic_bytes_per_iteration": G * 11 * es,
+                                "GBps": G * 11 * es / (us_it * 1e-6) / 1e9}
     print(json.dumps(out))
     ctx.close()
 

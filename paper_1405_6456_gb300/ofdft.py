@@ -81,14 +81,16 @@ class Energy(C.Structure):
         return d
 
 
-K_STENCIL, K_CG_DIR_STENCIL, K_CG_UPDATE, K_RESIDUAL, K_FUNCTIONAL, K_VECTOR, K_ATOMS = range(7)
+K_STENCIL, K_CG_DIR_STENCIL, K_CG_UPDATE, K_RESIDUAL, K_FUNCTIONAL, K_VECTOR, K_ATOMS, K_CG_PERSISTENT = range(8)
 K_COUNT = 8
-KIND_NAMES = ["stencil", "cg_dir_stencil", "cg_update", "residual", "functional", "vector", "atoms", "-"]
+KIND_NAMES = ["stencil", "cg_dir_stencil", "cg_update", "residual", "functional", "vector", "atoms",
+              "cg_persistent"]
 
 
 class Counters(C.Structure):
     _fields_ = [("launches", C.c_longlong), ("kind_launches", C.c_longlong * K_COUNT),
-                ("timed_launches", C.c_longlong * K_COUNT), ("timed_ms", C.c_double * K_COUNT)]
+                ("timed_launches", C.c_longlong * K_COUNT), ("timed_ms", C.c_double * K_COUNT),
+                ("persistent_cg_iters", C.c_longlong)]
 
 
 class SolveStats(C.Structure):

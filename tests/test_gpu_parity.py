@@ -146,6 +146,71 @@ def test_poisson_mixed_reaches_fp64_tolerance(ctx):
     assert np.abs(_h(phi) - phi_ref).max() <= 2e-6 * np.abs(phi_ref).max()
 
 
+@pytest.fixture(scope="module")
+def ctx_coop(ctx):
+    """A context created with OFDFT_COOP=1 (read at creation): the persistent
+    cooperative CG kernel where it applies."""
+    import os
+    old = os.environ.get("OFDFT_COOP")
+    os.environ["OFDFT_COOP"] = "1"
+    try:
+        c = F.Context(0)
+    finally:
+        if old is None:
+            del os.environ["OFDFT_COOP"]
+        else:
+            os.environ["OFDFT_COOP"] = old
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("dims,order", [((48, 40, 36), 12), ((64, 20, 70), 6)])
+def test_persistent_cg_matches_two_kernel_cg_and_oracle(ctx, ctx_coop, dtype, dims, order):
+    """The persistent cooperative CG kernel (whole iterations in one launch,
+    grid-wide sums between the halves) against the default two-kernel
+    iteration and, in FP64, the oracle: same iteration count (summation order
+    aside), same phi.  n1 % 4 == 0 so the persistent kernel's 16-byte staging
+    applies; the other extents are ragged against the tiles."""
+    g = F.make_grid(*dims, 0.6)
+    rng = np.random.default_rng(11)
+    rho_h = rng.standard_normal(g.shape)
+    rho = _t(rho_h, dtype)
+    tol = 1e-10 if dtype == torch.float64 else 1e-9
+    out = {}
+    for mode, cx in (("persistent", ctx_coop), ("two_kernel", ctx)):
+        phi = torch.zeros(g.shape, dtype=dtype, device=DEV)
+        cx.reset_counters()
+        st = cx.poisson(g, order, phi, rho=rho, tol=tol)
+        out[mode] = (st, _h(phi), cx.counters())
+    sp, php, cp = out["persistent"]
+    s2, ph2, c2 = out["two_kernel"]
+    assert cp.persistent_cg_iters > 0 and cp.kind_launches[F.K_CG_PERSISTENT] > 0
+    assert c2.persistent_cg_iters == 0 and c2.kind_launches[F.K_CG_PERSISTENT] == 0
+    assert sp.rel_residual <= tol and s2.rel_residual <= tol
+    slack = max(2, s2.iterations // 50) if dtype == torch.float64 else max(4, s2.iterations // 20)
+    assert abs(sp.iterations - s2.iterations) <= slack
+    scale = np.abs(ph2).max()
+    assert np.abs(php - ph2).max() <= (1e-8 if dtype == torch.float64 else 2e-6) * scale
+    if dtype == torch.float64:
+        phi_ref, it_ref, _ = O.poisson(_ogrid(g), order // 2, rho_h, tol=tol)
+        assert abs(sp.iterations - it_ref) <= max(3, it_ref // 20)
+        assert np.abs(php - phi_ref).max() <= 1e-8 * np.abs(phi_ref).max()
+
+
+def test_persistent_cg_solve_matches_oracle(ctx_coop, c1_case):
+    """A whole MIXED ground state with the persistent CG kernel against the
+    FP64 oracle, at the MIXED tolerances of the default path's test."""
+    c, g, res, Fo = c1_case
+    p = _parity_params(12, precision=F.PREC_MIXED, tol_poisson=1e-9, tol_inner=1e-9, tol_E=1e-8)
+    ctx_coop.reset_counters()
+    E, Fv, st = ctx_coop.solve(c.R, c.Z, c.h, p, grid=g)
+    assert ctx_coop.counters().persistent_cg_iters > 0
+    assert st.converged
+    assert abs(E - res.E) / c.M <= 1e-5
+    assert np.abs(Fv - Fo).max() <= 1e-4
+
+
 # ------------------------------------------------------------------ S4 ---
 def _random_state(g, order, c, seed):
     og = _ogrid(g)
