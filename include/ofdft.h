@@ -152,6 +152,22 @@ void ofdft_default_params(ofdft_params* p);
  * and keeps the fixed one-wave shape. */
 int ofdft_create(ofdft_ctx** ctx, int device, void* cuda_stream);
 int ofdft_destroy(ofdft_ctx* ctx);
+
+/* Preconditioner of the Poisson CG (S3) for every later solve on ctx
+ * (ofdft_poisson, ofdft_energy_grad, ofdft_solve and the calls built on them;
+ * not the batch engine, which keeps plain CG).  The paper's Krylov solve has
+ * none; the choice changes the iteration count, not the solution (phi to the
+ * same relative residual).
+ *   OFDFT_PRECOND_NONE: plain CG (the oracle's iteration, iteration for
+ *     iteration up to rounding).
+ *   OFDFT_PRECOND_MG (default): z = M r with M one symmetric V(1,1)-cycle of the
+ *     second-order 7-point Laplacian (damped Jacobi, full weighting, trilinear
+ *     prolongation, coarse node I on fine node 2I+1, zero Dirichlet values);
+ *     grids whose coarsest level would keep more than 4096 nodes (an extent
+ *     below 4 with the others large) fall back to plain CG.
+ * Returns OFDFT_EINVAL for an unknown kind. */
+enum { OFDFT_PRECOND_NONE = 0, OFDFT_PRECOND_MG = 1 };
+int ofdft_set_poisson_precond(ofdft_ctx* ctx, int kind);
 /* Message describing the last failure on ctx (never NULL; "" after success). */
 const char* ofdft_last_error(const ofdft_ctx* ctx);
 
@@ -287,7 +303,8 @@ enum {
   OFDFT_K_VECTOR = 5,           /* S6/S7 dots, NLCG updates, conversions */
   OFDFT_K_ATOMS = 6,            /* S1/S9 pseudocharge, guess, forces */
   OFDFT_K_CG_PERSISTENT = 7,    /* S3 CG: whole iterations (both halves) in one cooperative launch */
-  OFDFT_K_COUNT = 8
+  OFDFT_K_MG = 8,               /* S3 multigrid preconditioner passes */
+  OFDFT_K_COUNT = 9
 };
 
 typedef struct {

@@ -69,16 +69,144 @@ int cg_flush(ofdft_ctx* c, const GridDev& g, T* x, const T* pv, CgScalars* sc) {
   return OFDFT_OK;
 }
 
+// Multigrid preconditioner (S3): the level plan of a grid and one V-cycle
+// z = M r (kernels and the cycle's steps: mg_* in kernels.cuh).
+constexpr int kMgCoarseNodes = 4096;  // levels from this size down run in one block
+constexpr int kMgSweeps = 20;         // Jacobi sweeps from zero on the bottom level
+constexpr double kMgOmega = 0.8;      // Jacobi weight (the cycle is SPD for 0 < omega < 1)
+
+struct MgPlan {
+  int nlev = 0;  // levels from the grid itself down to the bottom (smallest extent below 4)
+  int lc = -1;   // first level handled by the one-block kernel
+  MgLevel d[kMgMaxLevels];
+  long long off[kMgMaxLevels] = {0};  // element offset of level l's r, z, t (l = 1 .. lc) in mgbuf
+  long long elems = 0;                // mgbuf elements
+  size_t smem = 0;                    // shared memory of the one-block kernel
+  double s0 = 0.0;                    // omega h^2 / 6 of the finest level
+  bool ok = false;
+};
+
+inline long long mg_nodes(const MgLevel& d) { return (long long)d.n1 * d.n2 * d.n3; }
+
+template <typename T>
+MgPlan mg_plan(const GridDev& g, double h) {
+  MgPlan P;
+  MgLevel d{g.n1, g.n2, g.n3};
+  P.d[0] = d;
+  P.nlev = 1;
+  while (std::min(d.n1, std::min(d.n2, d.n3)) >= 4 && P.nlev < kMgMaxLevels) {
+    d = MgLevel{d.n1 / 2, d.n2 / 2, d.n3 / 2};
+    P.d[P.nlev++] = d;
+  }
+  for (int l = 0; l < P.nlev; ++l)
+    if (mg_nodes(P.d[l]) <= kMgCoarseNodes) {
+      P.lc = l;
+      break;
+    }
+  if (P.lc < 0) return P;  // the bottom level is too large for one block: plain CG
+  long long e = 0;
+  for (int l = 1; l <= P.lc; ++l) {
+    P.off[l] = e;
+    e += 3 * mg_nodes(P.d[l]);
+  }
+  P.elems = e;
+  size_t sm = 0;
+  for (int l = P.lc; l < P.nlev; ++l) sm += 3 * (size_t)mg_nodes(P.d[l]) * sizeof(T);
+  P.smem = sm;
+  P.s0 = kMgOmega * h * h / 6.0;
+  P.ok = sm <= 200 * 1024;
+  return P;
+}
+
+// Whether the CG on this grid runs preconditioned; allocates what the cycle needs.
+template <typename T>
+int mg_prepare(ofdft_ctx* c, const GridDev& g, double h, MgPlan* P) {
+  *P = MgPlan{};
+  if (c->precond != OFDFT_PRECOND_MG) return OFDFT_OK;
+  *P = mg_plan<T>(g, h);
+  if (!P->ok) return OFDFT_OK;
+  TRY(ensure(c, c->v[V_Z], g.G * sizeof(T)));
+  TRY(ensure(c, c->v[V_T], g.G * sizeof(T)));
+  TRY(ensure(c, c->mgbuf, std::max<long long>(P->elems, 1) * sizeof(T)));
+  TRY(ensure_partials(c, pointwise_blocks(c, g.G), 1));
+  static bool attr = false;  // per element type
+  if (!attr) {
+    CU(cudaFuncSetAttribute(mg_coarse_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    CU(cudaFuncSetAttribute(mg_coarse_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr = true;
+  }
+  return OFDFT_OK;
+}
+
+// z = M r (one V-cycle); the finest level's last pass also forms r.z and the
+// PCG scalars (beta, rz).  Every kernel returns at once when the solve is done.
+template <typename T>
+int mg_vcycle(ofdft_ctx* c, const MgPlan& P, const T* r, T* z, CgScalars* sc) {
+  T* cb = static_cast<T*>(c->mgbuf.p);
+  T* t0 = vec<T>(c, V_T);
+  auto rl = [&](int l) -> T* { return l == 0 ? const_cast<T*>(r) : cb + P.off[l]; };
+  auto zl = [&](int l) -> T* { return l == 0 ? z : cb + P.off[l] + mg_nodes(P.d[l]); };
+  auto tl = [&](int l) -> T* { return l == 0 ? t0 : cb + P.off[l] + 2 * mg_nodes(P.d[l]); };
+  auto blocks = [&](long long G) { return (int)std::min<long long>((G + 255) / 256, (long long)c->sms * 8); };
+  const T om = (T)kMgOmega;
+  for (int l = 0; l < P.lc; ++l) {
+    {
+      ProfScope ps_(c, OFDFT_K_MG);
+      CU(launch_k(c, mg_down_kernel<T>, dim3(blocks(mg_nodes(P.d[l]))), dim3(256), 0, P.d[l], (const T*)rl(l), tl(l),
+                  om, (const CgScalars*)sc));
+    }
+    {
+      ProfScope ps_(c, OFDFT_K_MG);
+      CU(launch_k(c, mg_restrict_kernel<T>, dim3(blocks(mg_nodes(P.d[l + 1]))), dim3(256), 0, P.d[l], P.d[l + 1],
+                  (const T*)tl(l), rl(l + 1), (const CgScalars*)sc));
+    }
+  }
+  double s = P.s0;
+  for (int l = 0; l < P.lc; ++l) s *= 4.0;
+  {
+    ProfScope ps_(c, OFDFT_K_MG);
+    const int nl = P.nlev - P.lc;
+    if (P.lc == 0)
+      CU(launch_k(c, mg_coarse_kernel<T, true>, dim3(1), dim3(1024), P.smem, P.d[P.lc], nl, (const T*)rl(P.lc),
+                  zl(P.lc), om, (T)s, kMgSweeps, sc));
+    else
+      CU(launch_k(c, mg_coarse_kernel<T, false>, dim3(1), dim3(1024), P.smem, P.d[P.lc], nl, (const T*)rl(P.lc),
+                  zl(P.lc), om, (T)s, kMgSweeps, sc));
+  }
+  for (int l = P.lc - 1; l >= 0; --l) {
+    s *= 0.25;
+    {
+      ProfScope ps_(c, OFDFT_K_MG);
+      CU(launch_k(c, mg_prolong_kernel<T>, dim3(blocks(mg_nodes(P.d[l]))), dim3(256), 0, P.d[l], P.d[l + 1],
+                  (const T*)rl(l), (const T*)zl(l + 1), tl(l), (T)s, (const CgScalars*)sc));
+    }
+    ProfScope ps_(c, OFDFT_K_MG);
+    if (l == 0)
+      CU(launch_k(c, mg_up_kernel<T, true>, dim3(pointwise_blocks(c, mg_nodes(P.d[0]))), dim3(256), 0, P.d[0],
+                  (const T*)r, (const T*)t0, z, om, (T)s, sc, red(c)));
+    else
+      CU(launch_k(c, mg_up_kernel<T, false>, dim3(blocks(mg_nodes(P.d[l]))), dim3(256), 0, P.d[l], (const T*)rl(l),
+                  (const T*)tl(l), zl(l), om, (T)s, sc, red(c)));
+  }
+  return OFDFT_OK;
+}
+
 // Launches one CG iteration (S3): the stencil pass on r with the p/q update and
 // p.q (and the previous x update), then the r update with r.r; both kernels
 // read and write the CG scalars on the device and return at once when the
 // solve is done.
 template <typename T, typename X>
 int cg_step(ofdft_ctx* c, int R, const GridDev& g, const Weights<double>& Wneg, X* x, T* r, T* pv, T* qv,
-            CgScalars* sc, int pb) {
+            CgScalars* sc, int pb, const MgPlan* mg = nullptr) {
   static_assert(sizeof(X) == sizeof(T), "the iterate has the CG vectors' type");
   const bool fold = cg_fold<T>(g);
-  TRY(cg_stencil<T>(c, R, g, Wneg, reinterpret_cast<T*>(x), r, pv, qv, sc, fold));
+  const T* dir = r;  // the stencil pass forms p and q from r, or from z = M r (PCG)
+  if (mg && mg->ok) {
+    T* z = vec<T>(c, V_Z);
+    TRY(mg_vcycle<T>(c, *mg, r, z, sc));
+    dir = z;
+  }
+  TRY(cg_stencil<T>(c, R, g, Wneg, reinterpret_cast<T*>(x), dir, pv, qv, sc, fold));
   return cg_update<T>(c, g, reinterpret_cast<T*>(x), r, pv, qv, sc, pb, fold);
 }
 
@@ -166,11 +294,14 @@ int tune_cg_split(ofdft_ctx* c, int R, const GridDev& g, const Weights<double>& 
 // timed run keeps its graphs and times one stencil launch in kChunk.
 template <typename T, typename X>
 int cg_graph(ofdft_ctx* c, int R, const GridDev& g, double h, const Weights<double>& Wneg, X* x, T* r, T* pv, T* qv,
-             CgScalars* sc, int pb, int sample_set, cudaGraphExec_t* out) {
+             CgScalars* sc, int pb, int sample_set, cudaGraphExec_t* out, const MgPlan* mg) {
+  const bool pcg = mg && mg->ok;
   const std::vector<long long> key = {(long long)sizeof(T), (long long)sizeof(X), R, g.n1, g.n2, g.n3, (long long)x,
                                       (long long)r,
                                       (long long)pv, (long long)qv, (long long)sc, pb,
-                                      (long long)c->partials.p, (long long)(h * 1e12), sample_set};
+                                      (long long)c->partials.p, (long long)(h * 1e12), sample_set, pcg ? 1 : 0,
+                                      pcg ? (long long)c->mgbuf.p : 0, pcg ? (long long)c->v[V_Z].p : 0,
+                                      pcg ? (long long)c->v[V_T].p : 0};
   if (sample_set >= 0 && !c->gev[sample_set][0]) {
     CU(cudaEventCreate(&c->gev[sample_set][0]));
     CU(cudaEventCreate(&c->gev[sample_set][1]));
@@ -186,7 +317,7 @@ int cg_graph(ofdft_ctx* c, int R, const GridDev& g, double h, const Weights<doub
   const long long launches = c->launches;
   long long kinds[OFDFT_K_COUNT];
   memcpy(kinds, c->kind_launches, sizeof(kinds));
-  TRY((cg_step<T, X>(c, R, g, Wneg, x, r, pv, qv, sc, pb)));  // sets kernel attributes outside capture
+  TRY((cg_step<T, X>(c, R, g, Wneg, x, r, pv, qv, sc, pb, mg)));  // sets kernel attributes outside capture
   CU(cudaStreamSynchronize(c->stream));
   // capture on the context's private stream (the caller's stream may be the
   // legacy default stream, which cannot be captured); replay on the caller's
@@ -198,13 +329,18 @@ int cg_graph(ofdft_ctx* c, int R, const GridDev& g, double h, const Weights<doub
   if (eb == cudaSuccess)
     for (int i = 0; i < kChunk && rc == OFDFT_OK; ++i) {
       if (sample_set >= 0 && i == kChunk / 2) {
+        const T* dir = r;
+        if (pcg) {
+          rc = mg_vcycle<T>(c, *mg, r, vec<T>(c, V_Z), sc);
+          dir = vec<T>(c, V_Z);
+        }
         cudaEventRecordWithFlags(c->gev[sample_set][0], c->stream, cudaEventRecordExternal);
         const bool fold = cg_fold<T>(g);
-        rc = cg_stencil<T>(c, R, g, Wneg, reinterpret_cast<T*>(x), r, pv, qv, sc, fold);
+        if (rc == OFDFT_OK) rc = cg_stencil<T>(c, R, g, Wneg, reinterpret_cast<T*>(x), dir, pv, qv, sc, fold);
         cudaEventRecordWithFlags(c->gev[sample_set][1], c->stream, cudaEventRecordExternal);
         if (rc == OFDFT_OK) rc = cg_update<T>(c, g, reinterpret_cast<T*>(x), r, pv, qv, sc, pb, fold);
       } else {
-        rc = cg_step<T, X>(c, R, g, Wneg, x, r, pv, qv, sc, pb);
+        rc = cg_step<T, X>(c, R, g, Wneg, x, r, pv, qv, sc, pb, mg);
       }
     }
   const cudaError_t ec = (eb == cudaSuccess) ? cudaStreamEndCapture(c->stream, &graph) : eb;
@@ -321,7 +457,9 @@ int cg_iterate(ofdft_ctx* c, int R, const GridDev& g, double h, const Weights<do
   T* pv = vec<T>(c, V_P0);
   T* qv = vec<T>(c, V_AP);
   const bool per_launch = (c->prof & (1 << OFDFT_K_CG_UPDATE)) != 0;  // per-kernel timing asked for
-  if (c->coop && !per_launch) {
+  MgPlan mg;
+  TRY(mg_prepare<T>(c, g, h, &mg));
+  if (c->coop && !per_launch && !mg.ok) {
     bool used = false;
     TRY(cg_coop<T>(c, R, g, Wneg, reinterpret_cast<T*>(x), r, pv, qv, sc, max_it, host_sc, &used));
     if (used) return OFDFT_OK;
@@ -334,9 +472,9 @@ int cg_iterate(ofdft_ctx* c, int R, const GridDev& g, double h, const Weights<do
   const bool sampled = !full_timed && (c->prof & (1 << OFDFT_K_CG_DIR_STENCIL)) != 0;
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
   if (c->use_graphs && !full_timed && max_it >= kChunk) {
-    TRY((cg_graph<T, X>(c, R, g, h, Wneg, x, r, pv, qv, sc, pb, sampled ? 0 : -1, &exec[0])));
+    TRY((cg_graph<T, X>(c, R, g, h, Wneg, x, r, pv, qv, sc, pb, sampled ? 0 : -1, &exec[0], &mg)));
     exec[1] = exec[0];
-    if (sampled) TRY((cg_graph<T, X>(c, R, g, h, Wneg, x, r, pv, qv, sc, pb, 1, &exec[1])));
+    if (sampled) TRY((cg_graph<T, X>(c, R, g, h, Wneg, x, r, pv, qv, sc, pb, 1, &exec[1], &mg)));
   }
   bool pending[2] = {false, false};
   auto read_sample = [&](int set) {
@@ -354,12 +492,14 @@ int cg_iterate(ofdft_ctx* c, int R, const GridDev& g, double h, const Weights<do
       CU(cudaGraphLaunch(exec[slot], c->stream));
       pending[slot] = sampled;
       launched += kChunk;
-      c->launches += 2 * kChunk;
+      const int nmg = mg.ok ? 4 * mg.lc + 1 : 0;  // V-cycle launches per iteration
+      c->launches += (2 + nmg) * kChunk;
       c->kind_launches[OFDFT_K_CG_DIR_STENCIL] += kChunk;
       c->kind_launches[OFDFT_K_CG_UPDATE] += kChunk;
+      c->kind_launches[OFDFT_K_MG] += nmg * kChunk;
     } else {
       for (int i = 0; i < kChunk && launched < max_it; ++i, ++launched)
-        TRY((cg_step<T, X>(c, R, g, Wneg, x, r, pv, qv, sc, pb)));
+        TRY((cg_step<T, X>(c, R, g, Wneg, x, r, pv, qv, sc, pb, &mg)));
     }
     CU(cudaMemcpyAsync(&c->ring[slot], sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, c->stream));
     CU(cudaEventRecord(c->ring_ev[slot], c->stream));
@@ -397,8 +537,10 @@ int poisson_fp64(ofdft_ctx* c, int R, const GridDev& g, double h, const double* 
   TRY(ensure_cg_vectors(c, g.G, sizeof(double), false));
   const Weights<double> W = lap_weights(R, h, 1.0), Wneg = lap_weights(R, h, -1.0);
   double* r = vec<double>(c, V_R);
+  MgPlan mg;
+  TRY(mg_prepare<double>(c, g, h, &mg));
   TRY(launch_z_r<double>(c, R, g, W, LoadPlain<double>{phi},
-                         EpiResidual<double>{rho, u, b, r, c->sc, tol, max_it, 1}, OFDFT_K_RESIDUAL));
+                         EpiResidual<double>{rho, u, b, r, c->sc, tol, max_it, 1, mg.ok ? 1 : 0}, OFDFT_K_RESIDUAL));
   CgScalars hs;
   TRY(sync_scalars(c, c->sc, sizeof(CgScalars), &hs));
   if (!hs.done) TRY(cg_iterate<double>(c, R, g, h, Wneg, phi, r, c->sc, max_it, &hs));
@@ -431,6 +573,8 @@ int poisson_mixed(ofdft_ctx* c, int R, const GridDev& g, double h, const float* 
   float* r32 = vec<float>(c, V_R);
   float* e32 = vec<float>(c, V_E32);
   const int pb = pointwise_blocks(c, g.G);
+  MgPlan mg;
+  TRY(mg_prepare<float>(c, g, h, &mg));
   int total = 0, rc = OFDFT_OK;
   CgScalars hs, hs32;
   const int max_rounds = 60;
@@ -466,7 +610,7 @@ int poisson_mixed(ofdft_ctx* c, int R, const GridDev& g, double h, const float* 
     {
       ProfScope ps_(c, OFDFT_K_VECTOR);
       refine_replace_kernel<<<pb, 256, 0, c->stream>>>(g.G, r32, r64, c->sc32, mixed_inner_tol(hs.rr, bb, tol),
-                                                       budget, round == 0 ? 1 : 0, red(c));
+                                                       budget, round == 0 ? 1 : 0, mg.ok ? 1 : 0, red(c));
     }
     CU(cudaGetLastError());
     TRY(sync_scalars(c, c->sc32, sizeof(CgScalars), &hs32));
@@ -1408,6 +1552,8 @@ int ofdft_create(ofdft_ctx** out, int device, void* stream) {
   c->autotune = !(at && at[0] == '0');
   const char* co = getenv("OFDFT_COOP");  // 1: persistent cooperative CG iterations where they apply
   c->coop = (co && co[0] == '1') ? 1 : 0;
+  const char* pcn = getenv("OFDFT_PRECOND");  // 0: plain Poisson CG (ofdft_set_poisson_precond)
+  c->precond = (pcn && pcn[0] == '0') ? OFDFT_PRECOND_NONE : OFDFT_PRECOND_MG;
   const char* cz = getenv("OFDFT_COOP_NZ");  // launch-shape experiments: z-chunks of the persistent CG grid
   c->coop_nz = cz ? atoi(cz) : 0;
   const char* pw = getenv("OFDFT_POINTWISE_BLOCKS_PER_SM");  // launch-shape experiments (default 4)
@@ -1434,6 +1580,7 @@ int ofdft_destroy(ofdft_ctx* c) {
   for (cudaEvent_t e : c->free_events) cudaEventDestroy(e);
   cudaFree(c->partials.p);
   for (auto& b : c->v) cudaFree(b.p);
+  cudaFree(c->mgbuf.p);
   cudaFree(c->counter);
   cudaFree(c->sc);
   cudaFree(c->scal);
@@ -1446,6 +1593,14 @@ int ofdft_destroy(ofdft_ctx* c) {
 }
 
 const char* ofdft_last_error(const ofdft_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int ofdft_set_poisson_precond(ofdft_ctx* c, int kind) {
+  if (!c) return OFDFT_EINVAL;
+  if (kind != OFDFT_PRECOND_NONE && kind != OFDFT_PRECOND_MG)
+    return fail(c, OFDFT_EINVAL, "unknown Poisson preconditioner %d", kind);
+  c->precond = kind;
+  return OFDFT_OK;
+}
 
 int ofdft_profile(ofdft_ctx* c, int kind_mask) {
   if (!c) return OFDFT_EINVAL;
@@ -1526,6 +1681,7 @@ long long ofdft_workspace_bytes(const ofdft_grid* g, int fd_order, int prec) {
   long long bytes = G * es * 14;                 // solve state, NLCG and CG vectors
   if (prec == OFDFT_PREC_MIXED) bytes += G * 8 * 3 + G * 4;  // r64, phi64, b64, e32
   bytes += G * 8;                                // potential at the line-search origin
+  bytes += G * es * 3;                           // multigrid: z, finest scratch, coarser levels (3/7 G)
   (void)fd_order;
   return bytes;
 }

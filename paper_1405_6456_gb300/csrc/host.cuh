@@ -39,7 +39,7 @@ struct ofdft_ctx {
   double* scal = nullptr;  // 64 doubles
   double* host_scal = nullptr;  // pinned mirror
   // named vector workspaces
-  DevBuf v[24];
+  DevBuf v[32];
   // launch counters and optional CUDA-event timing of every launch
   long long launches = 0;
   long long kind_launches[OFDFT_K_COUNT] = {0};
@@ -74,6 +74,8 @@ struct ofdft_ctx {
   unsigned int* coop_bar = nullptr;            // arrival counter of its grid barriers
   long long coop_iters = 0;                    // CG iterations run by it (trace counter)
   int coop_nz = 0;                             // z-chunks of its grid (0: the default rule)
+  int precond = 1;                             // Poisson CG preconditioner (OFDFT_PRECOND_*)
+  DevBuf mgbuf;                                // multigrid levels below the finest
   int autotune = 1;
 };
 
@@ -87,6 +89,7 @@ enum Vec {
   V_ATOM0, V_ATOM1, V_ATOM2,           // atom scratch
   V_W,                                 // u / Jacobi diagonal (rank-one preconditioner)
   V_PHI0,                              // FP64 potential at the origin of the current line search
+  V_Z, V_T,                            // PCG: z = M r and the multigrid's finest-level scratch
   V_COUNT
 };
 

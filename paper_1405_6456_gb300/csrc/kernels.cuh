@@ -73,6 +73,8 @@ struct CgScalars {
   int first;      // 1 until the first search direction is formed
   int xdefer;     // 1 while x += alpha p of the last iteration is still to be applied
   int err;        // 1 when a grid barrier of the persistent CG kernel timed out
+  int pc;         // 1: preconditioned CG (alpha = rz / pAp, beta from the preconditioner pass)
+  double rz;      // r.z of the preconditioned residual z = M r (PCG)
 };
 
 // ---------------------------------------------------------------------------
@@ -682,7 +684,7 @@ struct EpiCgA {
   }
   __device__ __forceinline__ void operator()(double* t) const {
     sc->pAp = t[0];
-    sc->alpha = (t[0] != 0.0) ? sc->rr / t[0] : 0.0;
+    sc->alpha = (t[0] != 0.0) ? (sc->pc ? sc->rz : sc->rr) / t[0] : 0.0;
     sc->first = 0;
   }
 };
@@ -727,7 +729,7 @@ struct EpiCgAX {
   }
   __device__ __forceinline__ void operator()(double* t) const {
     sc->pAp = t[0];
-    sc->alpha = (t[0] != 0.0) ? sc->rr / t[0] : 0.0;
+    sc->alpha = (t[0] != 0.0) ? (sc->pc ? sc->rz : sc->rr) / t[0] : 0.0;
     sc->first = 0;
     sc->xdefer = 0;
   }
@@ -749,6 +751,7 @@ struct EpiResidual {
   double tol;
   int max_it;
   int want_r;
+  int pc = 0;  // the CG that follows is preconditioned
   __device__ __forceinline__ bool skip() const { return false; }
   __device__ __forceinline__ void load() {}
   __host__ __device__ __forceinline__ const T* input(int) const { return nullptr; }
@@ -779,6 +782,7 @@ struct EpiResidual {
     sc->beta = 0.0;
     sc->xdefer = 0;
     sc->err = 0;
+    sc->pc = pc;
     const double thr = tol * tol * (t[1] > 0.0 ? t[1] : 1.0);
     sc->done = (!want_r || t[2] <= thr || max_it <= 0) ? 1 : 0;
   }
@@ -1036,7 +1040,7 @@ __global__ void __launch_bounds__(256) cg_update_kernel(long long G, X* __restri
     CgScalars* sc;
     __device__ void operator()(double* t) const {
       const double rr_new = t[0];
-      sc->beta = (sc->rr != 0.0) ? rr_new / sc->rr : 0.0;
+      if (!sc->pc) sc->beta = (sc->rr != 0.0) ? rr_new / sc->rr : 0.0;
       sc->rr_prev = sc->rr;
       sc->rr = rr_new;
       sc->iters += 1;
@@ -1128,7 +1132,7 @@ __global__ void __launch_bounds__(256) cg_update_r_kernel(long long G, T* __rest
     CgScalars* sc;
     __device__ void operator()(double* t) const {
       const double rr_new = t[0];
-      sc->beta = (sc->rr != 0.0) ? rr_new / sc->rr : 0.0;
+      if (!sc->pc) sc->beta = (sc->rr != 0.0) ? rr_new / sc->rr : 0.0;
       sc->rr_prev = sc->rr;
       sc->rr = rr_new;
       sc->iters += 1;
@@ -1157,7 +1161,7 @@ static __global__ void cg_xclear_kernel(CgScalars* sc) { sc->xdefer = 0; }
 // The FP32 iterations of a round stop when r.r falls by inner_tol^2.
 static __global__ void __launch_bounds__(256) refine_replace_kernel(long long G, float* r32, const double* r64,
                                                                     CgScalars* sc, double inner_tol, int budget,
-                                                                    int restart, RedBuf red) {
+                                                                    int restart, int pc, RedBuf red) {
   __shared__ double smem[256 / 32];
   double acc[1] = {0.0};
   for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < G; i += (long long)gridDim.x * 256) {
@@ -1168,8 +1172,9 @@ static __global__ void __launch_bounds__(256) refine_replace_kernel(long long G,
   struct Fin {
     CgScalars* sc;
     double tol;
-    int budget, restart;
+    int budget, restart, pc;
     __device__ void operator()(double* t) const {
+      sc->pc = pc;  // with a preconditioner the next pass forms beta from r.z
       if (restart) {
         sc->first = 1;
         sc->beta = 0.0;
@@ -1186,8 +1191,307 @@ static __global__ void __launch_bounds__(256) refine_replace_kernel(long long G,
       sc->max_it = sc->iters + budget;
       sc->done = (t[0] == 0.0 || budget <= 0) ? 1 : 0;
     }
-  } fin{sc, inner_tol, budget, restart};
+  } fin{sc, inner_tol, budget, restart, pc};
   grid_sum<1, 256>(acc, smem, red, gridDim.x, blockIdx.x, threadIdx.x, fin);
+}
+
+// ------------------------------------------------- multigrid preconditioner ---
+// Preconditioner of the Poisson CG (S3).  The paper's Poisson solver is a
+// Krylov method without a stated preconditioner; the multigrid cycle here is a
+// solver choice of this implementation and leaves the solution (phi to the
+// same residual tolerance) unchanged.  M is one V(1,1)-cycle for the
+// second-order 7-point operator A7 f = (6 f - sum of the 6 neighbours) / H^2
+// with zero Dirichlet values: coarse node I of a level sits on fine node
+// 2I + 1 (n_c = floor(n / 2) per axis, H doubles), damped Jacobi smoothing
+// with weight omega (diagonal 6 / H^2), full-weighting restriction R = P^T / 8
+// and trilinear prolongation P (1D weights 1/2, 1, 1/2; zero outside), and on
+// the bottom level (smallest extent below 4) a fixed number of Jacobi sweeps
+// from zero.  The same smoother before and after the coarse correction makes
+// M a fixed symmetric positive definite operator, so CG with z = M r stays
+// CG; A7 is spectrally equivalent to the high-order stencil (equal at low
+// frequency, within a factor 2.5 at the grid's highest), so the iteration
+// count stays nearly flat as the grid grows.
+//
+// With s = omega H^2 / 6 the cycle's steps on one level are
+//   down:   z1 = s r,  t = r - A7 z1 = (1 - omega) r + (omega / 6) sum_nb r
+//   coarse: r_c = R t
+//   up:     y = z1 + P e_c,  z = y + (omega / D)(r - A7 y)
+//             = (1 - omega) y + s r + (omega / 6) sum_nb y
+// and on the bottom level  z <- (1 - omega) z + s r + (omega / 6) sum_nb z.
+struct MgLevel {
+  int n1, n2, n3;
+};
+constexpr int kMgMaxLevels = 24;
+
+template <typename T>
+__device__ __forceinline__ T mg_nb_sum(const T* f, int i, int j, int k, const MgLevel& d, long long idx,
+                                       long long plane) {
+  T s = T(0);
+  if (i > 0) s += f[idx - 1];
+  if (i + 1 < d.n1) s += f[idx + 1];
+  if (j > 0) s += f[idx - d.n1];
+  if (j + 1 < d.n2) s += f[idx + d.n1];
+  if (k > 0) s += f[idx - plane];
+  if (k + 1 < d.n3) s += f[idx + plane];
+  return s;
+}
+
+__device__ __forceinline__ void mg_ijk(long long idx, const MgLevel& d, int& i, int& j, int& k) {
+  const long long jk = idx / d.n1;
+  i = (int)(idx - jk * d.n1);
+  k = (int)(jk / d.n2);
+  j = (int)(jk - (long long)k * d.n2);
+}
+
+// Coarse node c = I of one axis: full-weighting sum over fine 2I, 2I+1, 2I+2.
+template <typename T>
+__device__ __forceinline__ T mg_restrict_at(const T* t, const MgLevel& f, int I, int J, int K) {
+  const long long fplane = (long long)f.n1 * f.n2;
+  T acc = T(0);
+#pragma unroll
+  for (int dk = 0; dk < 3; ++dk) {
+    const int kk = 2 * K + dk;
+    if (kk >= f.n3) continue;
+    const T wz = dk == 1 ? T(0.5) : T(0.25);
+#pragma unroll
+    for (int dj = 0; dj < 3; ++dj) {
+      const int jj = 2 * J + dj;
+      if (jj >= f.n2) continue;
+      const T wy = dj == 1 ? T(0.5) : T(0.25);
+      const T* row = t + fplane * kk + (long long)f.n1 * jj;
+      const int ii = 2 * I;
+      T sx = T(0.25) * row[ii] + T(0.5) * row[ii + 1];
+      if (ii + 2 < f.n1) sx += T(0.25) * row[ii + 2];
+      acc += wz * wy * sx;
+    }
+  }
+  return acc;
+}
+
+// Trilinear prolongation of the coarse field e (dims c) at fine node (i, j, k):
+// per axis, odd q takes coarse (q - 1) / 2 with weight 1, even q the mean of
+// coarse q / 2 - 1 and q / 2 (zero outside).  Missing terms get weight 0 at a
+// clamped (valid) index, so the 8 loads need no branches.
+template <typename T>
+__device__ __forceinline__ void mg_axis(int q, int n, int& c0, int& c1, T& w0, T& w1) {
+  if (q & 1) {
+    c0 = c1 = (q - 1) >> 1;
+    w0 = T(1);
+    w1 = T(0);
+  } else {
+    const int lo = (q >> 1) - 1, hi = q >> 1;
+    c0 = lo >= 0 ? lo : 0;
+    w0 = lo >= 0 ? T(0.5) : T(0);
+    c1 = hi < n ? hi : n - 1;
+    w1 = hi < n ? T(0.5) : T(0);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T mg_prolong_at(const T* e, const MgLevel& c, int i, int j, int k) {
+  int x0, x1, y0, y1, z0, z1;
+  T wx0, wx1, wy0, wy1, wz0, wz1;
+  mg_axis(i, c.n1, x0, x1, wx0, wx1);
+  mg_axis(j, c.n2, y0, y1, wy0, wy1);
+  mg_axis(k, c.n3, z0, z1, wz0, wz1);
+  const long long cplane = (long long)c.n1 * c.n2;
+  const T* r00 = e + cplane * z0 + (long long)c.n1 * y0;
+  const T* r01 = e + cplane * z0 + (long long)c.n1 * y1;
+  const T* r10 = e + cplane * z1 + (long long)c.n1 * y0;
+  const T* r11 = e + cplane * z1 + (long long)c.n1 * y1;
+  const T a00 = wx0 * r00[x0] + wx1 * r00[x1];
+  const T a01 = wx0 * r01[x0] + wx1 * r01[x1];
+  const T a10 = wx0 * r10[x0] + wx1 * r10[x1];
+  const T a11 = wx0 * r11[x0] + wx1 * r11[x1];
+  return wz0 * (wy0 * a00 + wy1 * a01) + wz1 * (wy0 * a10 + wy1 * a11);
+}
+
+// down: t = (1 - omega) r + (omega / 6) sum_nb r on one level.
+template <typename T>
+__global__ void __launch_bounds__(256) mg_down_kernel(MgLevel d, const T* __restrict__ r, T* __restrict__ t,
+                                                      T omega, const CgScalars* sc) {
+  if (sc->done) return;
+  const long long plane = (long long)d.n1 * d.n2, G = plane * d.n3;
+  const T a = T(1) - omega, b = omega / T(6);
+  for (long long idx = (long long)blockIdx.x * 256 + threadIdx.x; idx < G; idx += (long long)gridDim.x * 256) {
+    int i, j, k;
+    mg_ijk(idx, d, i, j, k);
+    t[idx] = a * r[idx] + b * mg_nb_sum(r, i, j, k, d, idx, plane);
+  }
+}
+
+// coarse: r_c = R t.
+template <typename T>
+__global__ void __launch_bounds__(256) mg_restrict_kernel(MgLevel f, MgLevel c, const T* __restrict__ t,
+                                                          T* __restrict__ rc, const CgScalars* sc) {
+  if (sc->done) return;
+  const long long Gc = (long long)c.n1 * c.n2 * c.n3;
+  for (long long idx = (long long)blockIdx.x * 256 + threadIdx.x; idx < Gc; idx += (long long)gridDim.x * 256) {
+    int I, J, K;
+    mg_ijk(idx, c, I, J, K);
+    rc[idx] = mg_restrict_at(t, f, I, J, K);
+  }
+}
+
+// up, first half: y = s r + P e_c.
+template <typename T>
+__global__ void __launch_bounds__(256) mg_prolong_kernel(MgLevel f, MgLevel c, const T* __restrict__ r,
+                                                         const T* __restrict__ ec, T* __restrict__ y, T s,
+                                                         const CgScalars* sc) {
+  if (sc->done) return;
+  const long long G = (long long)f.n1 * f.n2 * f.n3;
+  for (long long idx = (long long)blockIdx.x * 256 + threadIdx.x; idx < G; idx += (long long)gridDim.x * 256) {
+    int i, j, k;
+    mg_ijk(idx, f, i, j, k);
+    y[idx] = s * r[idx] + mg_prolong_at(ec, c, i, j, k);
+  }
+}
+
+// The PCG scalars after z = M r: beta = (r.z) / (r.z of the previous
+// iteration), unless the next direction is the first.
+struct MgFin {
+  CgScalars* sc;
+  __device__ void operator()(double* t) const {
+    const double rz = t[0];
+    sc->beta = (sc->first || sc->rz == 0.0) ? 0.0 : rz / sc->rz;
+    sc->rz = rz;
+  }
+};
+
+// up, second half: z = (1 - omega) y + s r + (omega / 6) sum_nb y; on the
+// finest level (DOT) also r.z and the PCG scalars.
+template <typename T, bool DOT>
+__global__ void __launch_bounds__(256) mg_up_kernel(MgLevel d, const T* __restrict__ r, const T* __restrict__ y,
+                                                    T* __restrict__ z, T omega, T s, CgScalars* sc, RedBuf red) {
+  __shared__ double smem[256 / 32];
+  if (sc->done) return;
+  const long long plane = (long long)d.n1 * d.n2, G = plane * d.n3;
+  const T a = T(1) - omega, b = omega / T(6);
+  DotAcc<T> acc;
+  for (long long idx = (long long)blockIdx.x * 256 + threadIdx.x; idx < G; idx += (long long)gridDim.x * 256) {
+    int i, j, k;
+    mg_ijk(idx, d, i, j, k);
+    const T ri = r[idx];
+    const T zi = a * y[idx] + s * ri + b * mg_nb_sum(y, i, j, k, d, idx, plane);
+    z[idx] = zi;
+    if constexpr (DOT) acc.add(ri, zi);
+  }
+  if constexpr (DOT) {
+    double v[1] = {acc.value()};
+    MgFin fin{sc};
+    grid_sum<1, 256>(v, smem, red, gridDim.x, blockIdx.x, threadIdx.x, fin);
+  }
+}
+
+// The coarse end of the cycle in one block, every level in shared memory:
+// from level d0 (r in global memory) down to the bottom level, `sweeps`
+// Jacobi sweeps there, and back up to z of level d0 (global memory).  nlev
+// counts d0 and the levels below it.  With DOT (the whole grid is this small)
+// the block also forms r.z and the PCG scalars.
+template <typename T, bool DOT>
+__global__ void __launch_bounds__(1024) mg_coarse_kernel(MgLevel d0, int nlev, const T* __restrict__ r,
+                                                         T* __restrict__ z, T omega, T s0, int sweeps,
+                                                         CgScalars* sc) {
+  extern __shared__ __align__(16) unsigned char mg_sm[];
+  __shared__ double red_sm[1024 / 32];
+  if (sc->done) return;
+  const int tid = threadIdx.x;
+  constexpr int NTH = 1024;
+  MgLevel d[kMgMaxLevels];
+  T* Rl[kMgMaxLevels];
+  T* Zl[kMgMaxLevels];
+  T* Wl[kMgMaxLevels];
+  T* p = reinterpret_cast<T*>(mg_sm);
+  d[0] = d0;
+  for (int l = 0; l < nlev; ++l) {
+    if (l > 0) d[l] = MgLevel{d[l - 1].n1 / 2, d[l - 1].n2 / 2, d[l - 1].n3 / 2};
+    const int G = d[l].n1 * d[l].n2 * d[l].n3;
+    Rl[l] = p;
+    Zl[l] = p + G;
+    Wl[l] = p + 2 * G;
+    p += 3 * G;
+  }
+  const T a = T(1) - omega, b = omega / T(6);
+  {
+    const int G = d0.n1 * d0.n2 * d0.n3;
+    for (int q = tid; q < G; q += NTH) Rl[0][q] = r[q];
+  }
+  __syncthreads();
+  T s = s0;
+  for (int l = 0; l + 1 < nlev; ++l, s *= T(4)) {
+    const MgLevel& dl = d[l];
+    const long long plane = (long long)dl.n1 * dl.n2;
+    const int G = dl.n1 * dl.n2 * dl.n3;
+    for (int q = tid; q < G; q += NTH) {
+      int i, j, k;
+      mg_ijk(q, dl, i, j, k);
+      Wl[l][q] = a * Rl[l][q] + b * mg_nb_sum(Rl[l], i, j, k, dl, q, plane);
+    }
+    __syncthreads();
+    const MgLevel& dc = d[l + 1];
+    const int Gc = dc.n1 * dc.n2 * dc.n3;
+    for (int q = tid; q < Gc; q += NTH) {
+      int I, J, K;
+      mg_ijk(q, dc, I, J, K);
+      Rl[l + 1][q] = mg_restrict_at(Wl[l], dl, I, J, K);
+    }
+    __syncthreads();
+  }
+  {  // bottom: Jacobi sweeps from zero, alternating between Z and W
+    const int l = nlev - 1;
+    const MgLevel& dl = d[l];
+    const long long plane = (long long)dl.n1 * dl.n2;
+    const int G = dl.n1 * dl.n2 * dl.n3;
+    T* cur = Zl[l];
+    T* nxt = Wl[l];
+    for (int q = tid; q < G; q += NTH) cur[q] = s * Rl[l][q];
+    __syncthreads();
+    for (int it = 1; it < sweeps; ++it) {
+      for (int q = tid; q < G; q += NTH) {
+        int i, j, k;
+        mg_ijk(q, dl, i, j, k);
+        nxt[q] = a * cur[q] + s * Rl[l][q] + b * mg_nb_sum(cur, i, j, k, dl, q, plane);
+      }
+      __syncthreads();
+      T* tmp = cur;
+      cur = nxt;
+      nxt = tmp;
+    }
+    if (cur != Zl[l]) {
+      for (int q = tid; q < G; q += NTH) Zl[l][q] = cur[q];
+      __syncthreads();
+    }
+  }
+  for (int l = nlev - 2; l >= 0; --l) {
+    s *= T(0.25);
+    const MgLevel& dl = d[l];
+    const long long plane = (long long)dl.n1 * dl.n2;
+    const int G = dl.n1 * dl.n2 * dl.n3;
+    for (int q = tid; q < G; q += NTH) {
+      int i, j, k;
+      mg_ijk(q, dl, i, j, k);
+      Wl[l][q] = s * Rl[l][q] + mg_prolong_at(Zl[l + 1], d[l + 1], i, j, k);
+    }
+    __syncthreads();
+    for (int q = tid; q < G; q += NTH) {
+      int i, j, k;
+      mg_ijk(q, dl, i, j, k);
+      Zl[l][q] = a * Wl[l][q] + s * Rl[l][q] + b * mg_nb_sum(Wl[l], i, j, k, dl, q, plane);
+    }
+    __syncthreads();
+  }
+  const int G0 = d0.n1 * d0.n2 * d0.n3;
+  DotAcc<T> acc;
+  for (int q = tid; q < G0; q += NTH) {
+    const T zq = Zl[0][q];
+    z[q] = zq;
+    if constexpr (DOT) acc.add(Rl[0][q], zq);
+  }
+  if constexpr (DOT) {
+    double v[1] = {acc.value()};
+    block_sum<1, NTH>(v, red_sm, tid);
+    if (tid == 0) MgFin{sc}(v);
+  }
 }
 
 // ----------------------------------------------------------- vector ops ---

@@ -81,10 +81,11 @@ class Energy(C.Structure):
         return d
 
 
-K_STENCIL, K_CG_DIR_STENCIL, K_CG_UPDATE, K_RESIDUAL, K_FUNCTIONAL, K_VECTOR, K_ATOMS, K_CG_PERSISTENT = range(8)
-K_COUNT = 8
+K_STENCIL, K_CG_DIR_STENCIL, K_CG_UPDATE, K_RESIDUAL, K_FUNCTIONAL, K_VECTOR, K_ATOMS, K_CG_PERSISTENT, K_MG = range(9)
+K_COUNT = 9
 KIND_NAMES = ["stencil", "cg_dir_stencil", "cg_update", "residual", "functional", "vector", "atoms",
-              "cg_persistent"]
+              "cg_persistent", "mg"]
+PRECOND_NONE, PRECOND_MG = 0, 1
 
 
 class Counters(C.Structure):
@@ -146,6 +147,7 @@ def lib():
     L.ofdft_struct_bytes.argtypes = [C.c_char_p]
     L.ofdft_struct_bytes.restype = C.c_longlong
     L.ofdft_profile.argtypes = [vp, ip]
+    L.ofdft_set_poisson_precond.argtypes = [vp, ip]
     L.ofdft_get_counters.argtypes = [vp, C.POINTER(Counters)]
     L.ofdft_reset_counters.argtypes = [vp]
     L.ofdft_batch_create.argtypes = [vp, ip, C.c_longlong, C.POINTER(vp)]
@@ -255,6 +257,10 @@ class Context:
         return rc
 
     # tracing
+    def set_poisson_precond(self, kind: int):
+        """PRECOND_MG (default) or PRECOND_NONE for the Poisson CG of later calls."""
+        return self._check(self._lib.ofdft_set_poisson_precond(self.h, int(kind)), "ofdft_set_poisson_precond")
+
     def profile(self, kinds=-1):
         """Time launches of the given kinds (bitmask of 1 << K_*; True/-1: all; False/0: none)."""
         mask = -1 if kinds is True else (0 if kinds is False else int(kinds))
@@ -426,6 +432,7 @@ def exported_symbols():
             "ofdft_grid_for_atoms", "ofdft_stencil", "ofdft_pseudocharge", "ofdft_initial_guess",
             "ofdft_poisson", "ofdft_energy_grad", "ofdft_forces", "ofdft_solve",
             "ofdft_workspace_bytes", "ofdft_profile", "ofdft_get_counters", "ofdft_reset_counters",
+            "ofdft_set_poisson_precond",
             "ofdft_batch_create", "ofdft_batch_destroy", "ofdft_batch_submit", "ofdft_batch_step",
             "ofdft_batch_poll", "ofdft_batch_run", "ofdft_batch_bytes"]
 

@@ -58,7 +58,9 @@ def test_warm_start_reaches_the_same_ground_state_faster(ctx, prec):
     tolE = 1e-9 if prec == F.PREC_FP64 else 1e-6
     assert abs(E1 - E0) / c.M <= tolE
     np.testing.assert_allclose(F1, F0, atol=1e-6 if prec == F.PREC_FP64 else 1e-4)
-    assert s1.cg_iters < s0.cg_iters / 2
+    # (with the multigrid-preconditioned Poisson CG a cold solve already needs
+    # few iterations per evaluation, so the saving is smaller than with plain CG)
+    assert s1.cg_iters < 0.6 * s0.cg_iters
     # a warm start needs the grid it was computed on
     with pytest.raises(F.OfdftError):
         ctx._check(ctx._lib.ofdft_solve_from(ctx.h, None, F._dp(np.ascontiguousarray(c.R)),

@@ -112,8 +112,18 @@ def test_pseudocharge_full_size_c1(ctx):
 
 
 # ------------------------------------------------------------------ S3 ---
+@pytest.fixture
+def plain_cg(ctx):
+    """Plain (unpreconditioned) Poisson CG on ctx for one test: the oracle's
+    iteration, so iteration counts can be compared."""
+    ctx.set_poisson_precond(F.PRECOND_NONE)
+    yield ctx
+    ctx.set_poisson_precond(F.PRECOND_MG)
+
+
 @pytest.mark.parametrize("order", [4, 12])
-def test_poisson_fp64_matches_oracle(ctx, order):
+def test_poisson_fp64_matches_oracle(plain_cg, order):
+    ctx = plain_cg
     c = W.tiny_cluster("trimer", h=0.8, fd_order=order)
     g = F.ofdft_grid_for_atoms(c.R, c.h, c.vacuum, 1)
     og = _ogrid(g)
@@ -130,6 +140,41 @@ def test_poisson_fp64_matches_oracle(ctx, order):
     phi2 = _t(phi_ref)
     st2 = ctx.poisson(g, order, phi2, rho=_t(rho), tol=1e-11)
     assert st2.iterations <= 1
+
+
+@pytest.mark.parametrize("dims,order", [((48, 40, 36), 12), ((37, 29, 23), 6), ((64, 64, 64), 12),
+                                        ((5, 70, 9), 4), ((3, 40, 40), 6)])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_poisson_multigrid_pcg_matches_oracle(ctx, dims, order, dtype):
+    """The multigrid-preconditioned CG (the default) reaches the oracle's phi
+    at the same relative residual in far fewer iterations; grids whose
+    coarsest level stays large ((3, 40, 40): an extent below 4) fall back to
+    plain CG and match the oracle's iteration count."""
+    g = F.make_grid(*dims, 0.5)
+    rng = np.random.default_rng(5)
+    rho_h = rng.standard_normal(g.shape)
+    tol = 1e-10 if dtype == torch.float64 else 1e-9
+    phi_ref, it_ref, _ = O.poisson(_ogrid(g), order // 2, rho_h, tol=1e-12)
+    ctx.reset_counters()
+    phi = torch.zeros(g.shape, dtype=dtype, device=DEV)
+    st = ctx.poisson(g, order, phi, rho=_t(rho_h, dtype), tol=tol)
+    cnt = ctx.counters()
+    assert st.rel_residual <= tol
+    # ||phi - phi*|| <= ||A^-1|| ||r||: with the residual at tol the error is a
+    # few tol of the solution's scale (FP32 fields add their rounding)
+    err = np.abs(_h(phi) - phi_ref).max() / np.abs(phi_ref).max()
+    assert err <= (1e-8 if dtype == torch.float64 else 2e-6)
+    if min(dims) >= 4:
+        assert cnt.kind_launches[F.K_MG] > 0
+        if max(dims) <= 2 * min(dims):
+            assert st.iterations <= max(30, it_ref // 4)
+        else:  # strongly anisotropic: 20 bottom sweeps leave the long axis' low modes to CG
+            assert st.iterations < it_ref
+    else:
+        assert cnt.kind_launches[F.K_MG] == 0
+        if dtype == torch.float64:
+            _, it_tol, _ = O.poisson(_ogrid(g), order // 2, rho_h, tol=tol)
+            assert abs(st.iterations - it_tol) <= max(3, it_tol // 20)
 
 
 def test_poisson_mixed_reaches_fp64_tolerance(ctx):
@@ -160,18 +205,20 @@ def ctx_coop(ctx):
             del os.environ["OFDFT_COOP"]
         else:
             os.environ["OFDFT_COOP"] = old
+    c.set_poisson_precond(F.PRECOND_NONE)  # the persistent kernel runs plain CG
     yield c
     c.close()
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 @pytest.mark.parametrize("dims,order", [((48, 40, 36), 12), ((64, 20, 70), 6)])
-def test_persistent_cg_matches_two_kernel_cg_and_oracle(ctx, ctx_coop, dtype, dims, order):
+def test_persistent_cg_matches_two_kernel_cg_and_oracle(plain_cg, ctx_coop, dtype, dims, order):
     """The persistent cooperative CG kernel (whole iterations in one launch,
     grid-wide sums between the halves) against the default two-kernel
     iteration and, in FP64, the oracle: same iteration count (summation order
     aside), same phi.  n1 % 4 == 0 so the persistent kernel's 16-byte staging
     applies; the other extents are ragged against the tiles."""
+    ctx = plain_cg
     g = F.make_grid(*dims, 0.6)
     rng = np.random.default_rng(11)
     rho_h = rng.standard_normal(g.shape)
