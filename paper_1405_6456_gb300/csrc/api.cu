@@ -69,61 +69,15 @@ int cg_flush(ofdft_ctx* c, const GridDev& g, T* x, const T* pv, CgScalars* sc) {
   return OFDFT_OK;
 }
 
-// Multigrid preconditioner (S3): the level plan of a grid and one V-cycle
-// z = M r (kernels and the cycle's steps: mg_* in kernels.cuh).
-constexpr int kMgCoarseNodes = 4096;  // levels from this size down run in one block
-constexpr int kMgSweeps = 20;         // Jacobi sweeps from zero on the bottom level
-constexpr double kMgOmega = 0.8;      // Jacobi weight (the cycle is SPD for 0 < omega < 1)
-
-struct MgPlan {
-  int nlev = 0;  // levels from the grid itself down to the bottom (smallest extent below 4)
-  int lc = -1;   // first level handled by the one-block kernel
-  MgLevel d[kMgMaxLevels];
-  long long off[kMgMaxLevels] = {0};  // element offset of level l's r, z, t (l = 1 .. lc) in mgbuf
-  long long elems = 0;                // mgbuf elements
-  size_t smem = 0;                    // shared memory of the one-block kernel
-  double s0 = 0.0;                    // omega h^2 / 6 of the finest level
-  bool ok = false;
-};
-
-inline long long mg_nodes(const MgLevel& d) { return (long long)d.n1 * d.n2 * d.n3; }
-
-template <typename T>
-MgPlan mg_plan(const GridDev& g, double h) {
-  MgPlan P;
-  MgLevel d{g.n1, g.n2, g.n3};
-  P.d[0] = d;
-  P.nlev = 1;
-  while (std::min(d.n1, std::min(d.n2, d.n3)) >= 4 && P.nlev < kMgMaxLevels) {
-    d = MgLevel{d.n1 / 2, d.n2 / 2, d.n3 / 2};
-    P.d[P.nlev++] = d;
-  }
-  for (int l = 0; l < P.nlev; ++l)
-    if (mg_nodes(P.d[l]) <= kMgCoarseNodes) {
-      P.lc = l;
-      break;
-    }
-  if (P.lc < 0) return P;  // the bottom level is too large for one block: plain CG
-  long long e = 0;
-  for (int l = 1; l <= P.lc; ++l) {
-    P.off[l] = e;
-    e += 3 * mg_nodes(P.d[l]);
-  }
-  P.elems = e;
-  size_t sm = 0;
-  for (int l = P.lc; l < P.nlev; ++l) sm += 3 * (size_t)mg_nodes(P.d[l]) * sizeof(T);
-  P.smem = sm;
-  P.s0 = kMgOmega * h * h / 6.0;
-  P.ok = sm <= 200 * 1024;
-  return P;
-}
+// One V-cycle z = M r of the multigrid preconditioner (plan: mg_plan in host.cuh;
+// kernels and the cycle's steps: mg_* in kernels.cuh).
 
 // Whether the CG on this grid runs preconditioned; allocates what the cycle needs.
 template <typename T>
 int mg_prepare(ofdft_ctx* c, const GridDev& g, double h, MgPlan* P) {
   *P = MgPlan{};
   if (c->precond != OFDFT_PRECOND_MG) return OFDFT_OK;
-  *P = mg_plan<T>(g, h);
+  *P = mg_plan(g, h, sizeof(T));
   if (!P->ok) return OFDFT_OK;
   TRY(ensure(c, c->v[V_Z], g.G * sizeof(T)));
   TRY(ensure(c, c->v[V_T], g.G * sizeof(T)));
@@ -559,9 +513,9 @@ int poisson_fp64(ofdft_ctx* c, int R, const GridDev& g, double h, const double* 
 // potential phi64 stays FP64; r, p, q = A p and the correction e of the current
 // round are FP32.  Each round folds e into phi64 and computes the FP64 true
 // residual r64 = 4 pi (u^2 + b64) + L_h phi64 with the FP64 stencil; the solve
-// ends when it meets tol.  Otherwise r64 replaces the FP32 residual (the search
-// direction is kept after the first round, so no Krylov information is lost)
-// and FP32 iterations run until the FP32 residual falls by mixed_inner_tol (1e-4,
+// ends when it meets tol.  Otherwise r64 replaces the FP32 residual (plain CG
+// keeps the search direction after the first round, so no Krylov information is
+// lost; preconditioned CG restarts from p = z) and FP32 iterations run until the FP32 residual falls by mixed_inner_tol (1e-4,
 // or less when the FP64 test needs less) or refine_every steps.  At the end
 // phi32 = (float) phi64.  rho32 (optional) replaces u^2 + b.
 int poisson_mixed(ofdft_ctx* c, int R, const GridDev& g, double h, const float* rho32, const float* u,
@@ -609,13 +563,21 @@ int poisson_mixed(ofdft_ctx* c, int R, const GridDev& g, double h, const float* 
     TRY(ensure_partials(c, pb, 1));
     {
       ProfScope ps_(c, OFDFT_K_VECTOR);
+      // later rounds keep the search direction (plain CG); preconditioned CG
+      // restarts from p = z: the replaced residual is not orthogonal to the old
+      // directions, and keeping them let the FP32 PCG diverge on some states
       refine_replace_kernel<<<pb, 256, 0, c->stream>>>(g.G, r32, r64, c->sc32, mixed_inner_tol(hs.rr, bb, tol),
-                                                       budget, round == 0 ? 1 : 0, mg.ok ? 1 : 0, red(c));
+                                                       budget, (round == 0 || mg.ok) ? 1 : 0, mg.ok ? 1 : 0,
+                                                       red(c));
     }
     CU(cudaGetLastError());
     TRY(sync_scalars(c, c->sc32, sizeof(CgScalars), &hs32));
     const int before = hs32.iters;
     if (!hs32.done) TRY((cg_iterate<float, float>(c, R, g, h, Wneg, e32, r32, c->sc32, budget, &hs32)));
+    if (c->trace)
+      fprintf(stderr, "[ofdft] mixed round %d rel64=%.3e its=%d rr32=%.3e rz=%.3e pAp=%.3e alpha=%.3e beta=%.3e pc=%d\n",
+              round, sqrt(hs.rr / bb), hs32.iters - before, hs32.rr, hs32.rz, hs32.pAp, hs32.alpha, hs32.beta,
+              hs32.pc);
     total += std::max(hs32.iters - before, 1);
   }
   {
@@ -891,8 +853,11 @@ struct Solver {
         dd = h3 * gdd[1];
       }
       // trial point at sig along d (sigma0, capped to an RMS change of trial_max_rel of u)
+      if (!std::isfinite(g0) || !std::isfinite(dd))
+        return fail(c, OFDFT_ENONFINITE, "search direction is not finite (g.d = %g, d.d = %g)", g0, dd);
       double sig = p->sigma0;
       if (p->trial_max_rel > 0.0 && dd > 0.0) sig = std::min(sig, p->trial_max_rel * sqrt(N / dd));
+      if (trace) fprintf(stderr, "[ofdft] nlcg it %d g0=%.6e dd=%.6e sig=%.6e\n", it, g0, dd, sig);
       TRY(line_start());
       TRY(line_guess(sig));
       TRY(axpy_abs(ut, u, d, sig));
@@ -940,7 +905,9 @@ struct Solver {
       delta_new = e.rs_pc;
       const double beta = (delta_new - delta_mid) / delta_old;
       ++k;
-      if (k >= p->restart_every || !(beta > 0.0)) {
+      if (trace) fprintf(stderr, "[ofdft] nlcg beta=%.6e delta_old=%.6e delta_new=%.6e delta_mid=%.6e\n", beta,
+                         delta_old, delta_new, delta_mid);
+      if (k >= p->restart_every || !(beta > 0.0) || !std::isfinite(beta)) {
         TRY(direction(0.0));
         k = 0;
       } else {
@@ -1554,6 +1521,7 @@ int ofdft_create(ofdft_ctx** out, int device, void* stream) {
   c->coop = (co && co[0] == '1') ? 1 : 0;
   const char* pcn = getenv("OFDFT_PRECOND");  // 0: plain Poisson CG (ofdft_set_poisson_precond)
   c->precond = (pcn && pcn[0] == '0') ? OFDFT_PRECOND_NONE : OFDFT_PRECOND_MG;
+  c->trace = getenv("OFDFT_TRACE") && getenv("OFDFT_TRACE")[0] == '1';  // per-round lines of the mixed Poisson
   const char* cz = getenv("OFDFT_COOP_NZ");  // launch-shape experiments: z-chunks of the persistent CG grid
   c->coop_nz = cz ? atoi(cz) : 0;
   const char* pw = getenv("OFDFT_POINTWISE_BLOCKS_PER_SM");  // launch-shape experiments (default 4)

@@ -67,6 +67,10 @@ struct Slot {
   double* partials = nullptr;
   unsigned int* counter = nullptr;
   int maxblk = 0;
+  // multigrid preconditioner of the Poisson CG: z, finest scratch, coarser levels
+  T *mz = nullptr, *mt = nullptr, *mgc = nullptr;
+  MgPlan mg;
+  int pc = 0;  // this solve's CG is preconditioned
   int index = 0;  // position in the engine's device scalar arrays
   // method state (host scalars)
   int state = S_AL_START;
@@ -163,6 +167,9 @@ long long slot_bytes(const ofdft_grid& g, int prec, int* maxblk) {
   auto chunk = [](long long n) { return (n + 255) & ~255LL; };  // carve() rounds every piece to 256 B
   long long bytes = 14 * chunk(G * es) + chunk(G * 8);
   if (prec == OFDFT_PREC_MIXED) bytes += 3 * chunk(G * 8) + chunk(G * 4);
+  // multigrid preconditioner: z, the finest level's scratch, the coarser levels
+  const MgPlan mg = mg_plan(gdev(&g), g.h, (size_t)es);
+  if (mg.ok) bytes += 2 * chunk(G * es) + chunk(std::max<long long>(mg.elems, 1) * es);
   // reduction scratch: the larger of the tile count and the segment count
   const long long tiles = (long long)((g.n[0] + BX - 1) / BX) * ((g.n[1] + BY - 1) / BY) * ((g.n[2] + 15) / 16);
   const long long segs = (G + 16383) / 16384;
@@ -194,6 +201,13 @@ int carve(ofdft_ctx* c, Slot<T>* S, int prec) {
   }
   S->partials = (double*)take((size_t)S->maxblk * 16 * 8);
   S->counter = (unsigned int*)take(256);
+  S->mg = mg_plan(S->g, S->h, sizeof(T));
+  if (S->mg.ok) {
+    S->mz = (T*)take(G * sizeof(T));
+    S->mt = (T*)take(G * sizeof(T));
+    S->mgc = (T*)take(std::max<long long>(S->mg.elems, 1) * sizeof(T));
+  }
+  S->pc = (S->mg.ok && c->precond == OFDFT_PRECOND_MG) ? 1 : 0;
   if ((size_t)(p - (char*)S->mem) > S->bytes) return fail(c, OFDFT_EINVAL, "slot workspace carve overflow");
   CU(cudaMemsetAsync(S->counter, 0, 256, c->stream));
   return OFDFT_OK;
@@ -215,6 +229,13 @@ void grid_segs(const GridDev& g, int slot, std::vector<PSeg>& out, int* count) {
   const long long L = 16384;
   int bid = 0;
   for (long long b = 0; b < g.G; b += L) out.push_back(PSeg{slot, bid++, b, std::min(b + L, g.G)});
+  *count = bid;
+}
+
+void count_segs(long long n, int slot, std::vector<PSeg>& out, int* count) {
+  const long long L = 16384;
+  int bid = 0;
+  for (long long b = 0; b < n; b += L) out.push_back(PSeg{slot, bid++, b, std::min(b + L, n)});
   *count = bid;
 }
 
@@ -320,6 +341,111 @@ struct Engine {
     return OFDFT_OK;
   }
 
+  // pointwise pass over n(S) elements of each slot (a multigrid level).
+  template <class Op, class Count, class Make>
+  int ppass_n(const std::vector<Slot<T>*>& slots, int kind, Count n, Make make) {
+    std::vector<PSeg> segs;
+    std::vector<Op> ops;
+    for (Slot<T>* S : slots) {
+      int cnt = 0;
+      const int si = (int)ops.size();
+      count_segs(n(S), si, segs, &cnt);
+      ops.push_back(make(S, cnt));
+    }
+    if (segs.empty()) return OFDFT_OK;
+    TRY(upload(c, B->d_segs, segs));
+    TRY(upload(c, B->d_ops, ops));
+    {
+      ProfScope ps_(c, kind);
+      pbatch_kernel<Op><<<(unsigned)segs.size(), 256, 0, c->stream>>>((const PSeg*)B->d_segs.p,
+                                                                     (const Op*)B->d_ops.p);
+    }
+    CU(cudaGetLastError());
+    return OFDFT_OK;
+  }
+
+  // z = M r for every preconditioned slot: one V-cycle per grid, each pass of
+  // the cycle shared by the grids that have that level (S3 + S11).
+  template <class GetR, class GetSc>
+  int mg_cycle(const std::vector<Slot<T>*>& slots, GetR getr, GetSc getsc) {
+    std::vector<Slot<T>*> pcs;
+    int maxlc = 0;
+    for (Slot<T>* S : slots)
+      if (S->pc) {
+        pcs.push_back(S);
+        maxlc = std::max(maxlc, S->mg.lc);
+      }
+    if (pcs.empty()) return OFDFT_OK;
+    const T om = (T)kMgOmega;
+    auto nodes = [](Slot<T>* S, int l) { return mg_nodes(S->mg.d[l]); };
+    auto rl = [&](Slot<T>* S, int l) -> T* { return l == 0 ? (T*)getr(S) : S->mgc + S->mg.off[l]; };
+    auto zl = [&](Slot<T>* S, int l) -> T* { return l == 0 ? S->mz : S->mgc + S->mg.off[l] + nodes(S, l); };
+    auto tl = [&](Slot<T>* S, int l) -> T* { return l == 0 ? S->mt : S->mgc + S->mg.off[l] + 2 * nodes(S, l); };
+    auto sl = [&](Slot<T>* S, int l) { return (T)(S->mg.s0 * pow(4.0, l)); };
+    auto having = [&](int l) {
+      std::vector<Slot<T>*> v;
+      for (Slot<T>* S : pcs)
+        if (S->mg.lc > l) v.push_back(S);
+      return v;
+    };
+    for (int l = 0; l < maxlc; ++l) {
+      const std::vector<Slot<T>*> v = having(l);
+      TRY((ppass_n<OpMgDown<T>>(v, OFDFT_K_MG, [&](Slot<T>* S) { return nodes(S, l); }, [&](Slot<T>* S, int nb) {
+        return OpMgDown<T>{S->mg.d[l], rl(S, l), tl(S, l), om, getsc(S), slot_red(S), nb};
+      })));
+      TRY((ppass_n<OpMgRestrict<T>>(v, OFDFT_K_MG, [&](Slot<T>* S) { return nodes(S, l + 1); },
+                                    [&](Slot<T>* S, int nb) {
+                                      return OpMgRestrict<T>{S->mg.d[l], S->mg.d[l + 1], tl(S, l), rl(S, l + 1),
+                                                             getsc(S), slot_red(S), nb};
+                                    })));
+    }
+    for (int dot = 0; dot < 2; ++dot) {  // the coarse ends: whole grids (lc = 0) form r.z themselves
+      std::vector<MgCoarseJob<T>> jobs;
+      size_t smem = 0;
+      for (Slot<T>* S : pcs)
+        if ((S->mg.lc == 0) == (dot == 1)) {
+          const int lc = S->mg.lc;
+          jobs.push_back(MgCoarseJob<T>{S->mg.d[lc], S->mg.nlev - lc, rl(S, lc), zl(S, lc), sl(S, lc), getsc(S)});
+          smem = std::max(smem, S->mg.smem);
+        }
+      if (jobs.empty()) continue;
+      TRY(upload(c, B->d_ops, jobs));
+      ProfScope ps_(c, OFDFT_K_MG);
+      static bool attr = false;  // per element type
+      if (!attr) {
+        CU(cudaFuncSetAttribute(mg_coarse_batch_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                200 * 1024));
+        CU(cudaFuncSetAttribute(mg_coarse_batch_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                200 * 1024));
+        attr = true;
+      }
+      if (dot) {
+        mg_coarse_batch_kernel<T, true><<<(unsigned)jobs.size(), 1024, smem, c->stream>>>(
+            (const MgCoarseJob<T>*)B->d_ops.p, om, kMgSweeps);
+      } else {
+        mg_coarse_batch_kernel<T, false><<<(unsigned)jobs.size(), 1024, smem, c->stream>>>(
+            (const MgCoarseJob<T>*)B->d_ops.p, om, kMgSweeps);
+      }
+      CU(cudaGetLastError());
+    }
+    for (int l = maxlc - 1; l >= 0; --l) {
+      const std::vector<Slot<T>*> v = having(l);
+      TRY((ppass_n<OpMgProlong<T>>(v, OFDFT_K_MG, [&](Slot<T>* S) { return nodes(S, l); }, [&](Slot<T>* S, int nb) {
+        return OpMgProlong<T>{S->mg.d[l], S->mg.d[l + 1], rl(S, l), zl(S, l + 1), tl(S, l), sl(S, l), getsc(S),
+                              slot_red(S), nb};
+      })));
+      if (l == 0)
+        TRY((ppass_n<OpMgUp<T, true>>(v, OFDFT_K_MG, [&](Slot<T>* S) { return nodes(S, 0); }, [&](Slot<T>* S, int nb) {
+          return OpMgUp<T, true>{S->mg.d[0], rl(S, 0), tl(S, 0), S->mz, om, sl(S, 0), getsc(S), slot_red(S), nb};
+        })));
+      else
+        TRY((ppass_n<OpMgUp<T, false>>(v, OFDFT_K_MG, [&](Slot<T>* S) { return nodes(S, l); }, [&](Slot<T>* S, int nb) {
+          return OpMgUp<T, false>{S->mg.d[l], rl(S, l), tl(S, l), zl(S, l), om, sl(S, l), getsc(S), slot_red(S), nb};
+        })));
+    }
+    return OFDFT_OK;
+  }
+
   int read_scalars() {
     CU(cudaMemcpyAsync(B->h_sc.data(), B->sc, B->capacity * sizeof(CgScalars), cudaMemcpyDeviceToHost, c->stream));
     if (mixed)
@@ -344,16 +470,19 @@ struct Engine {
     const bool fold = bytes > 96.0 * (1 << 20);
     while (!slots.empty()) {
       for (int i = 0; i < chunk; ++i) {
+        // the stencil pass forms p and q from z = M r (preconditioned slots) or r
+        TRY(mg_cycle(slots, getr, getsc));
+        auto dir = [&](Slot<T>* S) -> const T* { return S->pc ? S->mz : getr(S); };
         if (fold) {
           TRY((zpass<T, LoadPlain<T>, EpiCgAX<T>>(slots, OFDFT_K_CG_DIR_STENCIL, -1.0, [&](Slot<T>* S) {
-            return std::make_pair(LoadPlain<T>{getr(S)}, EpiCgAX<T>{S->pv, S->qv, (T*)getx(S), getsc(S)});
+            return std::make_pair(LoadPlain<T>{dir(S)}, EpiCgAX<T>{S->pv, S->qv, (T*)getx(S), getsc(S)});
           })));
           TRY((ppass<OpCgUpdateR<T>>(slots, OFDFT_K_CG_UPDATE, [&](Slot<T>* S, int nb) {
             return OpCgUpdateR<T>{getr(S), S->qv, getsc(S), slot_red(S), nb};
           })));
         } else {
           TRY((zpass<T, LoadPlain<T>, EpiCgA<T>>(slots, OFDFT_K_CG_DIR_STENCIL, -1.0, [&](Slot<T>* S) {
-            return std::make_pair(LoadPlain<T>{getr(S)}, EpiCgA<T>{S->pv, S->qv, getsc(S)});
+            return std::make_pair(LoadPlain<T>{dir(S)}, EpiCgA<T>{S->pv, S->qv, getsc(S)});
           })));
           using X = std::remove_pointer_t<decltype(getx(slots[0]))>;
           TRY((ppass<OpCgUpdate<T, X>>(slots, OFDFT_K_CG_UPDATE, [&](Slot<T>* S, int nb) {
@@ -380,7 +509,7 @@ struct Engine {
     if (!mixed) {
       TRY((zpass<T, LoadPlain<T>, EpiResidual<T>>(ev, OFDFT_K_RESIDUAL, 1.0, [&](Slot<T>* S) {
         return std::make_pair(LoadPlain<T>{S->phi}, EpiResidual<T>{nullptr, S->ev_at, S->b, S->r, B->sc + S->index,
-                                                                  S->ev_tol, S->p.max_cg, 1});
+                                                                  S->ev_tol, S->p.max_cg, 1, S->pc});
       })));
       TRY(read_scalars());
       std::vector<Slot<T>*> run;
@@ -428,7 +557,9 @@ struct Engine {
         const int budget = std::min(std::max(S->p.refine_every, 1), S->p.max_cg - S->ptotal);
         const CgScalars& h = B->h_sc[S->index];
         const double itol = mixed_inner_tol(h.rr, h.bb > 0 ? h.bb : 1.0, S->ev_tol);
-        return OpRefineReplace{(float*)S->r, S->r64, B->sc32 + S->index, itol, budget, S->pphase, slot_red(S), nb};
+        // preconditioned CG restarts every round (as poisson_mixed)
+        return OpRefineReplace{(float*)S->r, S->r64, B->sc32 + S->index, itol, budget, S->pphase || S->pc ? 1 : 0,
+                               slot_red(S), nb, S->pc};
       })));
       TRY(read_scalars());
       std::vector<int> before(B->capacity, 0);
@@ -755,7 +886,7 @@ struct Engine {
       S->delta_new = S->e.rs_pc;
       const double beta = (S->delta_new - delta_mid) / delta_old;
       S->k++;
-      if (S->k >= p.restart_every || !(beta > 0.0)) {
+      if (S->k >= p.restart_every || !(beta > 0.0) || !std::isfinite(beta)) {
         vop(S, VOP_DIRECTION, S->d, S->s, nullptr, 0.0);
         S->k = 0;
       } else {

@@ -75,6 +75,7 @@ struct ofdft_ctx {
   long long coop_iters = 0;                    // CG iterations run by it (trace counter)
   int coop_nz = 0;                             // z-chunks of its grid (0: the default rule)
   int precond = 1;                             // Poisson CG preconditioner (OFDFT_PRECOND_*)
+  int trace = 0;                               // OFDFT_TRACE=1: diagnostic lines on stderr
   DevBuf mgbuf;                                // multigrid levels below the finest
   int autotune = 1;
 };
@@ -346,6 +347,54 @@ bool zvec_ok(const GridDev& g, const L& ld, const E& ep) {
   for (int j = 0; j < E::NIN; ++j)
     if (ep.input(j) && !aligned(ep.input(j))) return false;
   return true;
+}
+
+// Multigrid preconditioner of the Poisson CG (S3): the levels of a grid (kernels
+// and the cycle's steps: mg_* in kernels.cuh).
+constexpr int kMgCoarseNodes = 4096;  // levels from this size down run in one block
+constexpr int kMgSweeps = 20;         // Jacobi sweeps from zero on the bottom level
+constexpr double kMgOmega = 0.8;      // Jacobi weight (the cycle is SPD for 0 < omega < 1)
+
+struct MgPlan {
+  int nlev = 0;  // levels from the grid itself down to the bottom (smallest extent below 4)
+  int lc = -1;   // first level handled by the one-block kernel
+  MgLevel d[kMgMaxLevels];
+  long long off[kMgMaxLevels] = {0};  // element offset of level l's r, z, t (l = 1 .. lc) in mgbuf
+  long long elems = 0;                // mgbuf elements
+  size_t smem = 0;                    // shared memory of the one-block kernel
+  double s0 = 0.0;                    // omega h^2 / 6 of the finest level
+  bool ok = false;
+};
+
+inline long long mg_nodes(const MgLevel& d) { return (long long)d.n1 * d.n2 * d.n3; }
+
+inline MgPlan mg_plan(const GridDev& g, double h, size_t es) {
+  MgPlan P;
+  MgLevel d{g.n1, g.n2, g.n3};
+  P.d[0] = d;
+  P.nlev = 1;
+  while (std::min(d.n1, std::min(d.n2, d.n3)) >= 4 && P.nlev < kMgMaxLevels) {
+    d = MgLevel{d.n1 / 2, d.n2 / 2, d.n3 / 2};
+    P.d[P.nlev++] = d;
+  }
+  for (int l = 0; l < P.nlev; ++l)
+    if (mg_nodes(P.d[l]) <= kMgCoarseNodes) {
+      P.lc = l;
+      break;
+    }
+  if (P.lc < 0) return P;  // the bottom level is too large for one block: plain CG
+  long long e = 0;
+  for (int l = 1; l <= P.lc; ++l) {
+    P.off[l] = e;
+    e += 3 * mg_nodes(P.d[l]);
+  }
+  P.elems = e;
+  size_t sm = 0;
+  for (int l = P.lc; l < P.nlev; ++l) sm += 3 * (size_t)mg_nodes(P.d[l]) * es;
+  P.smem = sm;
+  P.s0 = kMgOmega * h * h / 6.0;
+  P.ok = sm <= 200 * 1024;
+  return P;
 }
 
 // Launches kern on the context's stream.

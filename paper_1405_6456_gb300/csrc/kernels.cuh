@@ -1333,6 +1333,17 @@ __global__ void __launch_bounds__(256) mg_restrict_kernel(MgLevel f, MgLevel c, 
   }
 }
 
+// The PCG scalars after z = M r: beta = (r.z) / (r.z of the previous
+// iteration), unless the next direction is the first.
+struct MgFin {
+  CgScalars* sc;
+  __device__ void operator()(double* t) const {
+    const double rz = t[0];
+    sc->beta = (sc->first || sc->rz == 0.0) ? 0.0 : rz / sc->rz;
+    sc->rz = rz;
+  }
+};
+
 // up, first half: y = s r + P e_c.
 template <typename T>
 __global__ void __launch_bounds__(256) mg_prolong_kernel(MgLevel f, MgLevel c, const T* __restrict__ r,
@@ -1346,17 +1357,6 @@ __global__ void __launch_bounds__(256) mg_prolong_kernel(MgLevel f, MgLevel c, c
     y[idx] = s * r[idx] + mg_prolong_at(ec, c, i, j, k);
   }
 }
-
-// The PCG scalars after z = M r: beta = (r.z) / (r.z of the previous
-// iteration), unless the next direction is the first.
-struct MgFin {
-  CgScalars* sc;
-  __device__ void operator()(double* t) const {
-    const double rz = t[0];
-    sc->beta = (sc->first || sc->rz == 0.0) ? 0.0 : rz / sc->rz;
-    sc->rz = rz;
-  }
-};
 
 // up, second half: z = (1 - omega) y + s r + (omega / 6) sum_nb y; on the
 // finest level (DOT) also r.z and the PCG scalars.
@@ -1389,9 +1389,8 @@ __global__ void __launch_bounds__(256) mg_up_kernel(MgLevel d, const T* __restri
 // counts d0 and the levels below it.  With DOT (the whole grid is this small)
 // the block also forms r.z and the PCG scalars.
 template <typename T, bool DOT>
-__global__ void __launch_bounds__(1024) mg_coarse_kernel(MgLevel d0, int nlev, const T* __restrict__ r,
-                                                         T* __restrict__ z, T omega, T s0, int sweeps,
-                                                         CgScalars* sc) {
+__device__ __forceinline__ void mg_coarse_body(MgLevel d0, int nlev, const T* __restrict__ r, T* __restrict__ z,
+                                               T omega, T s0, int sweeps, CgScalars* sc) {
   extern __shared__ __align__(16) unsigned char mg_sm[];
   __shared__ double red_sm[1024 / 32];
   if (sc->done) return;
@@ -1492,6 +1491,31 @@ __global__ void __launch_bounds__(1024) mg_coarse_kernel(MgLevel d0, int nlev, c
     block_sum<1, NTH>(v, red_sm, tid);
     if (tid == 0) MgFin{sc}(v);
   }
+}
+
+template <typename T, bool DOT>
+__global__ void __launch_bounds__(1024) mg_coarse_kernel(MgLevel d0, int nlev, const T* __restrict__ r,
+                                                         T* __restrict__ z, T omega, T s0, int sweeps,
+                                                         CgScalars* sc) {
+  mg_coarse_body<T, DOT>(d0, nlev, r, z, omega, s0, sweeps, sc);
+}
+
+// The coarse end for several grids of a batch (S11): block b takes job b.
+template <typename T>
+struct MgCoarseJob {
+  MgLevel d0;
+  int nlev;
+  const T* r;
+  T* z;
+  T s0;
+  CgScalars* sc;
+};
+
+template <typename T, bool DOT>
+__global__ void __launch_bounds__(1024) mg_coarse_batch_kernel(const MgCoarseJob<T>* __restrict__ jobs, T omega,
+                                                               int sweeps) {
+  const MgCoarseJob<T> j = jobs[blockIdx.x];
+  mg_coarse_body<T, DOT>(j.d0, j.nlev, j.r, j.z, omega, j.s0, sweeps, j.sc);
 }
 
 // ----------------------------------------------------------- vector ops ---
@@ -1717,6 +1741,100 @@ struct OpCgUpdate {
   }
 };
 
+// Multigrid passes of one grid of a batch (S11), element i a node of the
+// op's level; same arithmetic as mg_down/restrict/prolong/up_kernel.
+template <typename T>
+struct OpMgDown {
+  static constexpr int K = 0;
+  using Acc = double;
+  MgLevel d;
+  const T* r;
+  T* t;
+  T om;
+  const CgScalars* sc;
+  RedBuf red;
+  int nblocks;
+  __device__ __forceinline__ bool skip() const { return sc->done != 0; }
+  __device__ __forceinline__ void load() {}
+  __device__ __forceinline__ void apply(long long idx, Acc*) const {
+    int i, j, k;
+    mg_ijk(idx, d, i, j, k);
+    const long long plane = (long long)d.n1 * d.n2;
+    t[idx] = (T(1) - om) * r[idx] + (om / T(6)) * mg_nb_sum(r, i, j, k, d, idx, plane);
+  }
+  __device__ __forceinline__ void operator()(double*) const {}
+};
+
+template <typename T>
+struct OpMgRestrict {
+  static constexpr int K = 0;
+  using Acc = double;
+  MgLevel f, c;
+  const T* t;
+  T* rc;
+  const CgScalars* sc;
+  RedBuf red;
+  int nblocks;
+  __device__ __forceinline__ bool skip() const { return sc->done != 0; }
+  __device__ __forceinline__ void load() {}
+  __device__ __forceinline__ void apply(long long idx, Acc*) const {
+    int I, J, K3;
+    mg_ijk(idx, c, I, J, K3);
+    rc[idx] = mg_restrict_at(t, f, I, J, K3);
+  }
+  __device__ __forceinline__ void operator()(double*) const {}
+};
+
+template <typename T>
+struct OpMgProlong {
+  static constexpr int K = 0;
+  using Acc = double;
+  MgLevel f, c;
+  const T* r;
+  const T* ec;
+  T* y;
+  T s;
+  const CgScalars* sc;
+  RedBuf red;
+  int nblocks;
+  __device__ __forceinline__ bool skip() const { return sc->done != 0; }
+  __device__ __forceinline__ void load() {}
+  __device__ __forceinline__ void apply(long long idx, Acc*) const {
+    int i, j, k;
+    mg_ijk(idx, f, i, j, k);
+    y[idx] = s * r[idx] + mg_prolong_at(ec, c, i, j, k);
+  }
+  __device__ __forceinline__ void operator()(double*) const {}
+};
+
+template <typename T, bool DOT>
+struct OpMgUp {
+  static constexpr int K = DOT ? 1 : 0;
+  using Acc = DotAcc<T>;
+  MgLevel d;
+  const T* r;
+  const T* y;
+  T* z;
+  T om, s;
+  CgScalars* sc;
+  RedBuf red;
+  int nblocks;
+  __device__ __forceinline__ bool skip() const { return sc->done != 0; }
+  __device__ __forceinline__ void load() {}
+  __device__ __forceinline__ void apply(long long idx, Acc* acc) const {
+    int i, j, k;
+    mg_ijk(idx, d, i, j, k);
+    const long long plane = (long long)d.n1 * d.n2;
+    const T ri = r[idx];
+    const T zi = (T(1) - om) * y[idx] + s * ri + (om / T(6)) * mg_nb_sum(y, i, j, k, d, idx, plane);
+    z[idx] = zi;
+    if constexpr (DOT) acc[0].add(ri, zi);
+  }
+  __device__ __forceinline__ void operator()(double* t) const {
+    if constexpr (DOT) MgFin{sc}(t);
+  }
+};
+
 // out = |a + alpha b| (trial point / secant update, u <- |u|).
 template <typename T>
 struct OpAxpyAbs {
@@ -1796,6 +1914,7 @@ struct OpRefineReplace {
   int budget, restart;
   RedBuf red;
   int nblocks;
+  int pc = 0;  // the FP32 CG is preconditioned
   using Acc = double;
   __device__ __forceinline__ void load() {}
   __device__ __forceinline__ bool skip() const { return false; }
@@ -1805,6 +1924,7 @@ struct OpRefineReplace {
     acc[0] += (double)v * (double)v;
   }
   __device__ __forceinline__ void operator()(double* t) const {
+    sc->pc = pc;
     if (restart) {
       sc->first = 1;
       sc->beta = 0.0;

@@ -4,9 +4,10 @@
 
 Solves (-L_h) phi = 4 pi rho for a seeded random rho with a fixed iteration
 count (tolerance 0), through the C ABI, and reports the average duration of the
-CG stencil pass (CUDA events around each launch) and of the CG update, with the
-algorithmic bytes moved.  Grids above 200^3 in FP32 exceed the 129 MB L2, which
-makes the DRAM counters of a profiler meaningful.
+CG stencil pass (CUDA events around each launch), of the CG update and of the
+multigrid preconditioner's V-cycle, with the algorithmic bytes moved.  Grids
+above 200^3 in FP32 exceed the 129 MB L2, which makes the DRAM counters of a
+profiler meaningful.
 """
 from __future__ import annotations
 
@@ -45,12 +46,13 @@ def main():
     for rep in range(2):
         phi = torch.zeros(g.shape, dtype=dt, device="cuda:0")
         ctx.reset_counters()
-        ctx.profile((1 << F.K_CG_DIR_STENCIL) | (1 << F.K_CG_UPDATE))
+        ctx.profile((1 << F.K_CG_DIR_STENCIL) | (1 << F.K_CG_UPDATE) | (1 << F.K_MG))
         st = ctx.poisson(g, args.order, phi, rho=rho, tol=1e-300, max_it=args.iters, allow_notconv=True)
         cnt = ctx.counters()
         ctx.profile(False)
     os.environ["OFDFT_COOP"] = "1"
     ctxp = F.Context(0)
+    ctxp.set_poisson_precond(F.PRECOND_NONE)  # the persistent kernel runs plain CG
     for rep in range(2):
         phi = torch.zeros(g.shape, dtype=dt, device="cuda:0")
         ctxp.reset_counters()
@@ -74,6 +76,11 @@ def main():
             us = cnt.timed_ms[k] / n * 1e3
             out[name] = {"launches": n, "avg_us": us, "algorithmic_bytes": G * acc * es,
                          "GBps": G * acc * es / (us * 1e-6) / 1e9}
+    if cnt.timed_launches[F.K_MG]:
+        # the multigrid preconditioner's passes (one V-cycle per CG iteration)
+        out["mg_vcycle"] = {"launches": cnt.timed_launches[F.K_MG],
+                            "launches_per_iteration": cnt.timed_launches[F.K_MG] / st.iterations,
+                            "us_per_iteration": cnt.timed_ms[F.K_MG] * 1e3 / st.iterations}
     its = cntp.persistent_cg_iters
     if cntp.timed_launches[F.K_CG_PERSISTENT] and its:
         us_it = cntp.timed_ms[F.K_CG_PERSISTENT] / its * 1e3
