@@ -379,8 +379,17 @@ def run_gpu(args):
         avg_r = cnt.timed_ms[kr] / cnt.timed_launches[kr] / 1e3
         flops_r = G * (2 * (6 * n + 1) + 10)
         ach_r = flops_r / avg_r / 1e9
+        traffic_r = None
+        try:
+            with open(TRAFFIC_FILE) as f:
+                tr = json.load(f)
+            key = f"residual_fp64_{args.precision}"
+            if tr.get("src_hash") == src_hash() and key in tr:
+                traffic_r = tr[key]["bytes_per_launch_full"]
+        except Exception:
+            pass
         roof_res = {"bound": "alu", "achieved": ach_r, "peak": FP64_ALU_PEAK_GFLOPS, "unit": "GFLOP/s",
-                    "frac": ach_r / FP64_ALU_PEAK_GFLOPS, "traffic": None,
+                    "frac": ach_r / FP64_ALU_PEAK_GFLOPS, "traffic": traffic_r,
                     "kernel": "zstream_kernel<double,%d,2,LoadPlain,EpiResidual> (FP64 residual "
                               "4 pi (u^2 + b) + L_h phi of each Poisson round, with r.r, b.b, u.u)" % n,
                     "launches": int(cnt.timed_launches[kr]), "avg_us": avg_r * 1e6,
