@@ -77,7 +77,7 @@ template <typename T>
 int mg_prepare(ofdft_ctx* c, const GridDev& g, double h, MgPlan* P) {
   *P = MgPlan{};
   if (c->precond != OFDFT_PRECOND_MG) return OFDFT_OK;
-  *P = mg_plan(g, h, sizeof(T));
+  *P = mg_plan(g, h, sizeof(T), c->mg_omega);
   if (!P->ok) return OFDFT_OK;
   TRY(ensure(c, c->v[V_Z], g.G * sizeof(T)));
   TRY(ensure(c, c->v[V_T], g.G * sizeof(T)));
@@ -102,7 +102,7 @@ int mg_vcycle(ofdft_ctx* c, const MgPlan& P, const T* r, T* z, CgScalars* sc) {
   auto zl = [&](int l) -> T* { return l == 0 ? z : cb + P.off[l] + mg_nodes(P.d[l]); };
   auto tl = [&](int l) -> T* { return l == 0 ? t0 : cb + P.off[l] + 2 * mg_nodes(P.d[l]); };
   auto blocks = [&](long long G) { return (int)std::min<long long>((G + 255) / 256, (long long)c->sms * 8); };
-  const T om = (T)kMgOmega;
+  const T om = (T)c->mg_omega;
   for (int l = 0; l < P.lc; ++l) {
     {
       ProfScope ps_(c, OFDFT_K_MG);
@@ -122,10 +122,10 @@ int mg_vcycle(ofdft_ctx* c, const MgPlan& P, const T* r, T* z, CgScalars* sc) {
     const int nl = P.nlev - P.lc;
     if (P.lc == 0)
       CU(launch_k(c, mg_coarse_kernel<T, true>, dim3(1), dim3(1024), P.smem, P.d[P.lc], nl, (const T*)rl(P.lc),
-                  zl(P.lc), om, (T)s, kMgSweeps, sc));
+                  zl(P.lc), om, (T)s, c->mg_sweeps, sc));
     else
       CU(launch_k(c, mg_coarse_kernel<T, false>, dim3(1), dim3(1024), P.smem, P.d[P.lc], nl, (const T*)rl(P.lc),
-                  zl(P.lc), om, (T)s, kMgSweeps, sc));
+                  zl(P.lc), om, (T)s, c->mg_sweeps, sc));
   }
   for (int l = P.lc - 1; l >= 0; --l) {
     s *= 0.25;
@@ -1522,6 +1522,12 @@ int ofdft_create(ofdft_ctx** out, int device, void* stream) {
   const char* pcn = getenv("OFDFT_PRECOND");  // 0: plain Poisson CG (ofdft_set_poisson_precond)
   c->precond = (pcn && pcn[0] == '0') ? OFDFT_PRECOND_NONE : OFDFT_PRECOND_MG;
   c->trace = getenv("OFDFT_TRACE") && getenv("OFDFT_TRACE")[0] == '1';  // per-round lines of the mixed Poisson
+  c->mg_omega = kMgOmega;
+  c->mg_sweeps = kMgSweeps;
+  const char* mo = getenv("OFDFT_MG_OMEGA");  // multigrid experiments: Jacobi weight, bottom sweeps
+  if (mo && atof(mo) > 0.0 && atof(mo) < 1.0) c->mg_omega = atof(mo);
+  const char* ms = getenv("OFDFT_MG_SWEEPS");
+  if (ms && atoi(ms) >= 1) c->mg_sweeps = atoi(ms);
   const char* cz = getenv("OFDFT_COOP_NZ");  // launch-shape experiments: z-chunks of the persistent CG grid
   c->coop_nz = cz ? atoi(cz) : 0;
   const char* pw = getenv("OFDFT_POINTWISE_BLOCKS_PER_SM");  // launch-shape experiments (default 4)

@@ -201,7 +201,7 @@ int carve(ofdft_ctx* c, Slot<T>* S, int prec) {
   }
   S->partials = (double*)take((size_t)S->maxblk * 16 * 8);
   S->counter = (unsigned int*)take(256);
-  S->mg = mg_plan(S->g, S->h, sizeof(T));
+  S->mg = mg_plan(S->g, S->h, sizeof(T), c->mg_omega);
   if (S->mg.ok) {
     S->mz = (T*)take(G * sizeof(T));
     S->mt = (T*)take(G * sizeof(T));
@@ -376,7 +376,7 @@ struct Engine {
         maxlc = std::max(maxlc, S->mg.lc);
       }
     if (pcs.empty()) return OFDFT_OK;
-    const T om = (T)kMgOmega;
+    const T om = (T)c->mg_omega;
     auto nodes = [](Slot<T>* S, int l) { return mg_nodes(S->mg.d[l]); };
     auto rl = [&](Slot<T>* S, int l) -> T* { return l == 0 ? (T*)getr(S) : S->mgc + S->mg.off[l]; };
     auto zl = [&](Slot<T>* S, int l) -> T* { return l == 0 ? S->mz : S->mgc + S->mg.off[l] + nodes(S, l); };
@@ -421,10 +421,10 @@ struct Engine {
       }
       if (dot) {
         mg_coarse_batch_kernel<T, true><<<(unsigned)jobs.size(), 1024, smem, c->stream>>>(
-            (const MgCoarseJob<T>*)B->d_ops.p, om, kMgSweeps);
+            (const MgCoarseJob<T>*)B->d_ops.p, om, c->mg_sweeps);
       } else {
         mg_coarse_batch_kernel<T, false><<<(unsigned)jobs.size(), 1024, smem, c->stream>>>(
-            (const MgCoarseJob<T>*)B->d_ops.p, om, kMgSweeps);
+            (const MgCoarseJob<T>*)B->d_ops.p, om, c->mg_sweeps);
       }
       CU(cudaGetLastError());
     }

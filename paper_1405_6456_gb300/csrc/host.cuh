@@ -76,6 +76,8 @@ struct ofdft_ctx {
   int coop_nz = 0;                             // z-chunks of its grid (0: the default rule)
   int precond = 1;                             // Poisson CG preconditioner (OFDFT_PRECOND_*)
   int trace = 0;                               // OFDFT_TRACE=1: diagnostic lines on stderr
+  double mg_omega = 0.9;                       // multigrid Jacobi weight (0 < omega < 1)
+  int mg_sweeps = 20;                          // Jacobi sweeps on the multigrid bottom level
   DevBuf mgbuf;                                // multigrid levels below the finest
   int autotune = 1;
 };
@@ -353,7 +355,7 @@ bool zvec_ok(const GridDev& g, const L& ld, const E& ep) {
 // and the cycle's steps: mg_* in kernels.cuh).
 constexpr int kMgCoarseNodes = 4096;  // levels from this size down run in one block
 constexpr int kMgSweeps = 20;         // Jacobi sweeps from zero on the bottom level
-constexpr double kMgOmega = 0.8;      // Jacobi weight (the cycle is SPD for 0 < omega < 1)
+constexpr double kMgOmega = 0.9;      // Jacobi weight (the cycle is SPD for 0 < omega < 1)
 
 struct MgPlan {
   int nlev = 0;  // levels from the grid itself down to the bottom (smallest extent below 4)
@@ -368,7 +370,7 @@ struct MgPlan {
 
 inline long long mg_nodes(const MgLevel& d) { return (long long)d.n1 * d.n2 * d.n3; }
 
-inline MgPlan mg_plan(const GridDev& g, double h, size_t es) {
+inline MgPlan mg_plan(const GridDev& g, double h, size_t es, double omega = kMgOmega) {
   MgPlan P;
   MgLevel d{g.n1, g.n2, g.n3};
   P.d[0] = d;
@@ -392,7 +394,7 @@ inline MgPlan mg_plan(const GridDev& g, double h, size_t es) {
   size_t sm = 0;
   for (int l = P.lc; l < P.nlev; ++l) sm += 3 * (size_t)mg_nodes(P.d[l]) * es;
   P.smem = sm;
-  P.s0 = kMgOmega * h * h / 6.0;
+  P.s0 = omega * h * h / 6.0;
   P.ok = sm <= 200 * 1024;
   return P;
 }

@@ -79,5 +79,6 @@ def test_host_argument_checks(lib):
                                     16, ctypes.byref(g)) == F.ENONFINITE
     assert lib.ofdft_destroy(None) == F.OK
     assert lib.ofdft_last_error(None) == b"null context"
+    assert lib.ofdft_set_poisson_precond(None, F.PRECOND_MG) == F.EINVAL
     gg = F.make_grid(128, 128, 128, 0.5)
     assert F.workspace_bytes(gg, 12, F.PREC_FP64) > F.workspace_bytes(gg, 12, F.PREC_MIXED) > 0

@@ -514,6 +514,9 @@ def test_invalid_arguments_are_rejected(ctx):
     with pytest.raises(F.OfdftError) as ei:
         ctx.solve(np.zeros((1, 3)), [3.0], 0.5, F.default_params(kappa=1.5))
     assert ei.value.code == F.EINVAL
+    with pytest.raises(F.OfdftError) as ei:
+        ctx.set_poisson_precond(7)
+    assert ei.value.code == F.EINVAL
     # the context stays usable after errors
     ctx.stencil(g, 4, f, out)
 
