@@ -381,6 +381,18 @@ int ofdft_poisson_noalloc(const ofdft_grid* g, int fd_order, const double* rho, 
  * admission control by callers that pack several solves on one device). */
 long long ofdft_workspace_bytes(const ofdft_grid* g, int fd_order, int prec);
 
+/* Host only (no device work): the multigrid levels the Poisson preconditioner
+ * (OFDFT_PRECOND_MG) builds for grid g in precision prec.  *levels = number of
+ * levels from g itself down to the bottom (each level halves every extent,
+ * n_c = floor(n / 2); coarsening stops once an extent is below 4);
+ * dims (nullable, 3 * 24 ints) receives the extents of each level.
+ * *coarse_level = first level handled by the one-block coarse kernel (the first
+ * with at most 4096 nodes), or -1 when even the bottom level is larger: the CG
+ * then runs without preconditioner.  *bytes (nullable) = device bytes of the
+ * preconditioner's vectors (0 when it does not apply).  OFDFT_EINVAL for a NULL
+ * or empty grid. */
+int ofdft_mg_plan(const ofdft_grid* g, int prec, int* levels, int* coarse_level, int* dims, long long* bytes);
+
 /* sizeof of the named ABI struct ("ofdft_grid", "ofdft_params", "ofdft_cg_stats",
  * "ofdft_energy", "ofdft_solve_stats", "ofdft_counters", "ofdft_relax_stats"), or -1 for any other
  * name: lets a binding check its struct layouts against the library's.  Host

@@ -1648,6 +1648,24 @@ long long ofdft_struct_bytes(const char* name) {
   return -1;
 }
 
+int ofdft_mg_plan(const ofdft_grid* g, int prec, int* levels, int* coarse_level, int* dims, long long* bytes) {
+  if (!g || !levels || !coarse_level) return OFDFT_EINVAL;
+  if (g->n[0] < 1 || g->n[1] < 1 || g->n[2] < 1 || !(g->h > 0.0)) return OFDFT_EINVAL;
+  const size_t es = (prec == OFDFT_PREC_MIXED) ? 4 : 8;
+  const GridDev gd = gdev(g);
+  const MgPlan P = mg_plan(gd, g->h, es);
+  *levels = P.nlev;
+  *coarse_level = P.ok ? P.lc : -1;
+  if (dims)
+    for (int l = 0; l < P.nlev; ++l) {
+      dims[3 * l] = P.d[l].n1;
+      dims[3 * l + 1] = P.d[l].n2;
+      dims[3 * l + 2] = P.d[l].n3;
+    }
+  if (bytes) *bytes = P.ok ? (long long)((2 * gd.G + P.elems) * (long long)es) : 0;
+  return OFDFT_OK;
+}
+
 long long ofdft_workspace_bytes(const ofdft_grid* g, int fd_order, int prec) {
   if (!g) return -1;
   const long long G = (long long)g->n[0] * g->n[1] * g->n[2];

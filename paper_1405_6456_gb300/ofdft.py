@@ -159,6 +159,8 @@ def lib():
     L.ofdft_batch_run.argtypes = [vp]
     L.ofdft_batch_bytes.argtypes = [C.POINTER(Grid), ip]
     L.ofdft_batch_bytes.restype = C.c_longlong
+    L.ofdft_mg_plan.argtypes = [C.POINTER(Grid), ip, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                C.POINTER(C.c_int), C.POINTER(C.c_longlong)]
     L.ofdft_workspace_bytes.argtypes = [C.POINTER(Grid), ip, ip]
     L.ofdft_workspace_bytes.restype = C.c_longlong
     _lib = L
@@ -422,6 +424,19 @@ def batch_bytes(g: Grid, prec: int) -> int:
     return int(lib().ofdft_batch_bytes(C.byref(g), prec))
 
 
+def mg_plan(g: Grid, prec: int = PREC_MIXED) -> dict:
+    """Levels of the multigrid Poisson preconditioner for grid g (host only):
+    {"levels": [(n1, n2, n3), ...], "coarse_level": int (-1: plain CG), "bytes": int}."""
+    nl, lc = C.c_int(), C.c_int()
+    dims = (C.c_int * (3 * 24))()
+    nb = C.c_longlong()
+    rc = lib().ofdft_mg_plan(C.byref(g), prec, C.byref(nl), C.byref(lc), dims, C.byref(nb))
+    if rc != OK:
+        raise OfdftError(rc, "ofdft_mg_plan: invalid grid")
+    return {"levels": [tuple(dims[3 * l:3 * l + 3]) for l in range(nl.value)], "coarse_level": lc.value,
+            "bytes": nb.value}
+
+
 def workspace_bytes(g: Grid, fd_order: int, prec: int) -> int:
     return int(lib().ofdft_workspace_bytes(C.byref(g), fd_order, prec))
 
@@ -432,7 +447,7 @@ def exported_symbols():
             "ofdft_grid_for_atoms", "ofdft_stencil", "ofdft_pseudocharge", "ofdft_initial_guess",
             "ofdft_poisson", "ofdft_energy_grad", "ofdft_forces", "ofdft_solve",
             "ofdft_workspace_bytes", "ofdft_profile", "ofdft_get_counters", "ofdft_reset_counters",
-            "ofdft_set_poisson_precond",
+            "ofdft_set_poisson_precond", "ofdft_mg_plan",
             "ofdft_batch_create", "ofdft_batch_destroy", "ofdft_batch_submit", "ofdft_batch_step",
             "ofdft_batch_poll", "ofdft_batch_run", "ofdft_batch_bytes"]
 

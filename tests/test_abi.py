@@ -82,3 +82,45 @@ def test_host_argument_checks(lib):
     assert lib.ofdft_set_poisson_precond(None, F.PRECOND_MG) == F.EINVAL
     gg = F.make_grid(128, 128, 128, 0.5)
     assert F.workspace_bytes(gg, 12, F.PREC_FP64) > F.workspace_bytes(gg, 12, F.PREC_MIXED) > 0
+
+
+def _levels_by_rule(dims):
+    """The coarsening rule written out: halve every extent (floor) while every
+    extent is at least 4."""
+    out = [tuple(dims)]
+    while min(out[-1]) >= 4:
+        out.append(tuple(n // 2 for n in out[-1]))
+    return out
+
+
+@pytest.mark.parametrize("dims", [(128, 128, 128), (192, 192, 192), (37, 29, 23), (48, 40, 36), (5, 70, 9),
+                                  (3, 40, 40), (80, 80, 80), (1, 1, 1), (4, 4, 4), (400, 4, 400)])
+@pytest.mark.parametrize("prec", [F.PREC_FP64, F.PREC_MIXED])
+def test_multigrid_level_plan(lib, dims, prec):
+    g = F.make_grid(*dims, 0.5)
+    plan = F.mg_plan(g, prec)
+    levels = _levels_by_rule(dims)
+    assert plan["levels"] == levels
+    nodes = [a * b * c for a, b, c in levels]
+    small = [l for l, n in enumerate(nodes) if n <= 4096]
+    es = 4 if prec == F.PREC_MIXED else 8
+    if small:
+        lc = small[0]
+        assert plan["coarse_level"] == lc
+        # z and one scratch vector at the finest level, r, z, t of levels 1..lc
+        assert plan["bytes"] == (2 * nodes[0] + 3 * sum(nodes[1:lc + 1])) * es
+        # the one-block coarse end keeps r, z, t of its levels in shared memory
+        assert 3 * sum(nodes[lc:]) * es <= 200 * 1024
+    else:
+        assert plan["coarse_level"] == -1 and plan["bytes"] == 0
+    if dims == (128, 128, 128):
+        assert plan["coarse_level"] == 3 and len(levels) == 7  # 128 .. 2, the block from 16^3
+    if dims == (3, 40, 40):
+        assert plan["coarse_level"] == -1  # an extent below 4, 4800 nodes: plain CG
+
+
+def test_multigrid_plan_rejects_bad_grids(lib):
+    with pytest.raises(F.OfdftError):
+        F.mg_plan(F.make_grid(0, 8, 8, 0.5))
+    with pytest.raises(F.OfdftError):
+        F.mg_plan(F.make_grid(8, 8, 8, -0.5))
