@@ -149,7 +149,12 @@ void ofdft_default_params(ofdft_params* p);
  * stencil pass and keeps the fastest for the context's lifetime (the shape sets
  * the order of the reductions' partial sums, so two contexts may differ in the
  * last bits); environment variable OFDFT_AUTOTUNE=0 at creation turns this off
- * and keeps the fixed one-wave shape. */
+ * and keeps the fixed one-wave shape.  Other variables read at creation:
+ * OFDFT_PRECOND=0 (plain Poisson CG, as ofdft_set_poisson_precond), OFDFT_MG_OMEGA
+ * (multigrid Jacobi weight in (0, 1), default 0.9), OFDFT_MG_SWEEPS (bottom-level
+ * sweeps, default 20), OFDFT_COOP=1 (plain CG iterations in one persistent
+ * cooperative launch per eight iterations where the grid's blocks fit on the
+ * device at once), OFDFT_TRACE=1 (one stderr line per evaluation). */
 int ofdft_create(ofdft_ctx** ctx, int device, void* cuda_stream);
 int ofdft_destroy(ofdft_ctx* ctx);
 
