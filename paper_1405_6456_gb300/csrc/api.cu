@@ -329,14 +329,14 @@ int cg_coop_r(ofdft_ctx* c, const GridDev& g, const Weights<double>& Wneg, T* x,
   if (!zvec_ok<T>(g, LoadPlain<T>{r}, EpiCgAv<T>{pv, qv, 0, T(0)})) return OFDFT_OK;
   auto* kern = cg_coop_kernel<T, R, VW>;
   constexpr int smem = zsmem_bytes<T, R, VW, EpiCgAv<T>>();
-  static int per_sm = 0;
-  if (!per_sm) {
+  static int per_sm = -1;  // co-resident blocks per SM of this instantiation (-1: not yet queried)
+  if (per_sm < 0) {
     CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int nb = 0;
     CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, NT, smem));
-    per_sm = std::max(nb, 0) + 1;  // +1: cached even when 0
+    per_sm = std::max(nb, 0);
   }
-  const long long maxb = (long long)(per_sm - 1) * c->sms;
+  const long long maxb = (long long)per_sm * c->sms;
   const int gx = (g.n1 + BX - 1) / BX, gy = (g.n2 + ZCfg<T>::TY - 1) / ZCfg<T>::TY;
   const long long tiles = (long long)gx * gy;
   if (maxb < 1 || tiles > maxb) return OFDFT_OK;
