@@ -45,7 +45,8 @@ def workload():
 def workload_config(c, g, precision, extra=None):
     cfg = {"workload": f"{c.name}: {c.M} atoms, FCC 5x5x5 cells a=7.6 bohr, Z=3, seeded +-0.1 bohr, "
                        f"h={c.h} bohr, {c.fd_order}th-order FD, {c.vacuum} bohr vacuum, grid "
-                       f"{g[0]}x{g[1]}x{g[2]}, AL+PR-NLCG+multigrid-preconditioned CG Poisson to 1e-6 Ha/atom, forces",
+                       f"{g[0]}x{g[1]}x{g[2]}, AL+PR-NLCG ground state with a Poisson solve per evaluation, to 1e-6 "
+                       f"Ha/atom, forces",
            "atoms": c.M, "grid": list(g), "fd_order": c.fd_order, "precision": precision,
            "l2": "flushed between steps (256 MB write); the 128^3 CG working set itself fits in L2"}
     if extra:
