@@ -86,7 +86,8 @@ def build(force: bool = False) -> str:
                                               os.path.getmtime(__file__)))
         if force or stale:
             tmp = _LIB + f".tmp{os.getpid()}"
-            cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+            cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-o", tmp,
+                   _SRC, "-lm"]
             subprocess.run(cmd, check=True, cwd=_HERE)
             os.replace(tmp, _LIB)
     return _LIB
@@ -99,6 +100,8 @@ def lib():
         L = C.CDLL(_LIB)
         dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
         L.orc_default_params.argtypes = [C.POINTER(Params)]
+        L.orc_set_threads.argtypes = [C.c_int]
+        L.orc_get_threads.restype = C.c_int
         L.orc_lap_weights.argtypes = [C.c_int, C.c_double, dp]
         L.orc_grad_weights.argtypes = [C.c_int, C.c_double, dp]
         L.orc_laplacian.argtypes = [C.POINTER(Grid), C.c_int, dp, dp]
@@ -125,8 +128,21 @@ def lib():
                                  C.c_double, dp, C.c_int, dp]
         L.orc_ezz_correction.argtypes = [dp, dp, C.c_int, C.c_double, C.c_void_p]
         L.orc_ezz_correction.restype = C.c_double
+        # one thread unless a caller asks for more (set_threads): the tests run
+        # many small grids, where threads only add overhead
+        L.orc_set_threads(1)
         _lib = L
     return _lib
+
+
+def set_threads(n: int) -> None:
+    """Number of OpenMP threads of the grid-sized loops (sums are independent of it)."""
+    lib().orc_set_threads(int(n))
+
+
+def threads() -> int:
+    """Threads the grid-sized loops use."""
+    return int(lib().orc_get_threads())
 
 
 def _f64(a):

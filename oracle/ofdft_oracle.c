@@ -30,10 +30,37 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #ifndef M_PI
 #define M_PI 3.14159265358979323846
 #endif
+
+/* Threads: the grid-sized loops below are split over OpenMP threads when the
+ * library is built with OpenMP.  Every sum over the grid is taken in ORC_NCH
+ * fixed contiguous chunks whose partial sums are added in chunk order, so
+ * results do not depend on the number of threads. */
+#define ORC_NCH 256
+
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
+int orc_get_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+static long chunk_lo(long G, int c) { return G * c / ORC_NCH; }
 
 static double fact(int k) {
   double f = 1.0;
@@ -106,11 +133,13 @@ void orc_laplacian(const orc_grid* g, int n, const double* f, double* out) {
   const int n1 = g->n1, n2 = g->n2, n3 = g->n3;
   const long P1 = n1 + 2 * n, P2 = n2 + 2 * n, P3 = n3 + 2 * n;
   double* fp = (double*)calloc((size_t)(P1 * P2 * P3), sizeof(double));
+#pragma omp parallel for schedule(static)
   for (int k = 0; k < n3; ++k)
     for (int j = 0; j < n2; ++j)
       for (int i = 0; i < n1; ++i)
         fp[(i + n) + P1 * ((j + n) + P2 * (long)(k + n))] = f[i + (long)n1 * (j + (long)n2 * k)];
   const long sy = P1, sz = P1 * P2;
+#pragma omp parallel for schedule(static)
   for (int k = 0; k < n3; ++k)
     for (int j = 0; j < n2; ++j)
       for (int i = 0; i < n1; ++i) {
@@ -325,8 +354,15 @@ void orc_initial_guess(const orc_grid* g, const double* R, const double* Z, int 
 }
 
 static double dot(const double* a, const double* b, long G) {
+  double part[ORC_NCH];
+#pragma omp parallel for schedule(static)
+  for (int c = 0; c < ORC_NCH; ++c) {
+    double s = 0.0;
+    for (long x = chunk_lo(G, c); x < chunk_lo(G, c + 1); ++x) s += a[x] * b[x];
+    part[c] = s;
+  }
   double s = 0.0;
-  for (long x = 0; x < G; ++x) s += a[x] * b[x];
+  for (int c = 0; c < ORC_NCH; ++c) s += part[c];
   return s;
 }
 
@@ -342,27 +378,37 @@ int orc_poisson(const orc_grid* g, int n, const double* rho, double* phi, double
   double* p = (double*)malloc(sizeof(double) * G);
   double* Ap = (double*)malloc(sizeof(double) * G);
   orc_laplacian(g, n, phi, Ap);
-  double bb = 0.0;
-  for (long x = 0; x < G; ++x) {
-    const double rhs = 4.0 * M_PI * rho[x];
-    r[x] = rhs + Ap[x]; /* rhs - (-L phi) */
-    p[x] = r[x];
-    bb += rhs * rhs;
+  double part[ORC_NCH];
+#pragma omp parallel for schedule(static)
+  for (int c = 0; c < ORC_NCH; ++c) {
+    double s = 0.0;
+    for (long x = chunk_lo(G, c); x < chunk_lo(G, c + 1); ++x) {
+      const double rhs = 4.0 * M_PI * rho[x];
+      r[x] = rhs + Ap[x]; /* rhs - (-L phi) */
+      p[x] = r[x];
+      s += rhs * rhs;
+    }
+    part[c] = s;
   }
+  double bb = 0.0;
+  for (int c = 0; c < ORC_NCH; ++c) bb += part[c];
   const double bnorm = sqrt(bb) > 0.0 ? sqrt(bb) : 1.0;
   double rr = dot(r, r, G);
   int it = 0;
   while (it < max_it && sqrt(rr) > tol * bnorm) {
     orc_laplacian(g, n, p, Ap);
+#pragma omp parallel for schedule(static)
     for (long x = 0; x < G; ++x) Ap[x] = -Ap[x];
     const double pAp = dot(p, Ap, G);
     const double alpha = rr / pAp;
+#pragma omp parallel for schedule(static)
     for (long x = 0; x < G; ++x) {
       phi[x] += alpha * p[x];
       r[x] -= alpha * Ap[x];
     }
     const double rr_new = dot(r, r, G);
     const double beta = rr_new / rr;
+#pragma omp parallel for schedule(static)
     for (long x = 0; x < G; ++x) p[x] = r[x] + beta * p[x];
     rr = rr_new;
     ++it;
@@ -398,45 +444,71 @@ void orc_functional(const orc_grid* g, const orc_params* p, const double* u, con
   double* Lphi = (double*)malloc(sizeof(double) * NG);
   orc_laplacian(g, p->fd_n, u, Lu);
   if (es) orc_laplacian(g, p->fd_n, phi, Lphi);
-  double s_tf = 0, s_vw = 0, s_xc = 0, s_es = 0, s_uu = 0;
-  for (long x = 0; x < NG; ++x) s_uu += u[x] * u[x];
+  /* per-chunk partial sums, added in chunk order below:
+     tf, vw, xc, es, G.G, G.G/diag, u.s, u.u/diag */
+  enum { NS = 8 };
+  double part[ORC_NCH][NS];
+  const double s_uu = dot(u, u, NG);
   const double C = h3 * s_uu - N;
   const double inv_mu = 1.0 / mu;
   const double mult = -eta + C * inv_mu;
-  double g2 = 0.0, rs = 0.0, us = 0.0, uwu = 0.0;
   double* winv = (p->precond_rank1 && s) ? (double*)malloc(sizeof(double) * NG) : NULL;
-  for (long x = 0; x < NG; ++x) {
-    const double ux = fabs(u[x]);
-    double e_xc = 0.0, v_xc = 0.0;
-    if (xc) orc_xc(ux, &e_xc, &v_xc);
-    const double u43 = pow(ux, 4.0 / 3.0);
-    const double vk = tf ? (5.0 / 3.0) * CF * u43 : 0.0;
-    if (tf) s_tf += CF * u43 * ux * ux;
-    if (vw) s_vw += u[x] * Lu[x];
-    if (xc) s_xc += e_xc * ux * ux;
-    double ph = 0.0;
-    if (es) {
-      ph = phi[x];
-      s_es += ph * Lphi[x] / (8.0 * M_PI) + (u[x] * u[x] + b[x]) * ph;
+#pragma omp parallel for schedule(static)
+  for (int c = 0; c < ORC_NCH; ++c) {
+    double s_tf = 0, s_vw = 0, s_xc = 0, s_es = 0, g2 = 0.0, rs = 0.0, us = 0.0, uwu = 0.0;
+    for (long x = chunk_lo(NG, c); x < chunk_lo(NG, c + 1); ++x) {
+      const double ux = fabs(u[x]);
+      double e_xc = 0.0, v_xc = 0.0;
+      if (xc) orc_xc(ux, &e_xc, &v_xc);
+      const double u43 = pow(ux, 4.0 / 3.0);
+      const double vk = tf ? (5.0 / 3.0) * CF * u43 : 0.0;
+      if (tf) s_tf += CF * u43 * ux * ux;
+      if (vw) s_vw += u[x] * Lu[x];
+      if (xc) s_xc += e_xc * ux * ux;
+      double ph = 0.0;
+      if (es) {
+        ph = phi[x];
+        s_es += ph * Lphi[x] / (8.0 * M_PI) + (u[x] * u[x] + b[x]) * ph;
+      }
+      const double gx = (vw ? -p->lambda * Lu[x] : 0.0) + 2.0 * (vk + v_xc + ph) * u[x] + 2.0 * mult * u[x];
+      const double kin = (vw ? -6.0 * p->lambda * w[0] : 0.0) + (14.0 / 3.0) * vk;
+      double md = kin + 2.0 * (v_xc + ph + mult);
+      if (md < 0.25 * kin) md = 0.25 * kin;
+      if (md < 1e-10) md = 1e-10;
+      if (G) G[x] = gx;
+      if (s) s[x] = -gx / md;
+      if (winv) winv[x] = u[x] / md;
+      g2 += gx * gx;
+      rs += gx * gx / md;
+      us += u[x] * (-gx / md);
+      uwu += u[x] * u[x] / md;
     }
-    const double gx = (vw ? -p->lambda * Lu[x] : 0.0) + 2.0 * (vk + v_xc + ph) * u[x] + 2.0 * mult * u[x];
-    const double kin = (vw ? -6.0 * p->lambda * w[0] : 0.0) + (14.0 / 3.0) * vk;
-    double md = kin + 2.0 * (v_xc + ph + mult);
-    if (md < 0.25 * kin) md = 0.25 * kin;
-    if (md < 1e-10) md = 1e-10;
-    if (G) G[x] = gx;
-    if (s) s[x] = -gx / md;
-    if (winv) winv[x] = u[x] / md;
-    g2 += gx * gx;
-    rs += gx * gx / md;
-    us += u[x] * (-gx / md);
-    uwu += u[x] * u[x] / md;
+    part[c][0] = s_tf;
+    part[c][1] = s_vw;
+    part[c][2] = s_xc;
+    part[c][3] = s_es;
+    part[c][4] = g2;
+    part[c][5] = rs;
+    part[c][6] = us;
+    part[c][7] = uwu;
+  }
+  double s_tf = 0, s_vw = 0, s_xc = 0, s_es = 0, g2 = 0.0, rs = 0.0, us = 0.0, uwu = 0.0;
+  for (int c = 0; c < ORC_NCH; ++c) {
+    s_tf += part[c][0];
+    s_vw += part[c][1];
+    s_xc += part[c][2];
+    s_es += part[c][3];
+    g2 += part[c][4];
+    rs += part[c][5];
+    us += part[c][6];
+    uwu += part[c][7];
   }
   double rs_pc = rs;
   if (winv && s) {
     /* rank-one term (4 h^3/mu) u u^T of dG/du inverted exactly (Sherman-Morrison) */
     const double cpen = 4.0 * h3 * inv_mu;
     const double gamma = cpen * us / (1.0 + cpen * uwu);
+#pragma omp parallel for schedule(static)
     for (long x = 0; x < NG; ++x) s[x] -= gamma * winv[x];
     rs_pc -= gamma * us;
   }
@@ -468,6 +540,7 @@ int orc_energy_grad(const orc_grid* g, const orc_params* p, const double* u, con
   double ezz = out->E_zz_corr;
   if (p->terms & ORC_ES) {
     double* rho = (double*)malloc(sizeof(double) * NG);
+#pragma omp parallel for schedule(static)
     for (long x = 0; x < NG; ++x) rho[x] = u[x] * u[x] + b[x];
     it = orc_poisson(g, p->fd_n, rho, phi, p->tol_poisson, p->max_cg, &rel);
     free(rho);
@@ -540,6 +613,7 @@ static int nlcg(solver* S, double eta, double mu) {
     double sig = p->sigma0;
     if (p->trial_max_rel > 0.0 && dd > 0.0 && p->trial_max_rel * sqrt(S->N / dd) < sig)
       sig = p->trial_max_rel * sqrt(S->N / dd);
+#pragma omp parallel for schedule(static)
     for (long x = 0; x < NG; ++x) ut[x] = fabs(S->u[x] + sig * d[x]);
     {
       double* Gs = S->G;
@@ -561,10 +635,12 @@ static int nlcg(solver* S, double eta, double mu) {
       const double L0 = S->e.L;
       for (int j = 1; j <= p->max_secant; ++j) {
         alpha = alpha * gcur / (gprev - gcur);
+#pragma omp parallel for schedule(static)
         for (long x = 0; x < NG; ++x) ut[x] = fabs(S->u[x] + alpha * d[x]);
         sv_eval(S, ut, eta, mu);
         for (int bt = 0; bt < p->max_backtrack && !(S->e.L <= L0); ++bt) {
           alpha *= 0.5; /* the secant step did not lower L: halve it */
+#pragma omp parallel for schedule(static)
           for (long x = 0; x < NG; ++x) ut[x] = fabs(S->u[x] + alpha * d[x]);
           sv_eval(S, ut, eta, mu);
         }
@@ -585,6 +661,7 @@ static int nlcg(solver* S, double eta, double mu) {
       memcpy(d, S->s, sizeof(double) * NG);
       k = 0;
     } else {
+#pragma omp parallel for schedule(static)
       for (long x = 0; x < NG; ++x) d[x] = S->s[x] + beta * d[x];
     }
   }

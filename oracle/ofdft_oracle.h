@@ -78,6 +78,9 @@ typedef struct {
   int converged;
 } orc_result;
 
+/* OpenMP threads used by the grid-sized loops (no effect without OpenMP). */
+void orc_set_threads(int n);
+int orc_get_threads(void);
 void orc_default_params(orc_params* p);
 int orc_lap_weights(int n, double h, double* w);
 int orc_grad_weights(int n, double h, double* wt);

@@ -184,6 +184,61 @@ def test_poisson_warm_start_from_solution_takes_no_iterations():
     assert it2 == 0 and rel2 <= 1e-11
 
 
+# ---------------------------------------------------------- initial guess ---
+def _guess_density(g, R, Z, s=2.0, cut=8.0):
+    """Superposed atomic densities Z_J (2 pi s^2)^(-3/2) exp(-r^2/(2 s^2)) inside
+    r < cut, written out here from the stated Gaussian (reading R7)."""
+    X, Y, Zc = _coords(g)
+    rho = np.zeros(g.shape)
+    for J in range(len(Z)):
+        r2 = (X - R[J][0]) ** 2 + (Y - R[J][1]) ** 2 + (Zc - R[J][2]) ** 2
+        rho += np.where(r2 < cut * cut, Z[J] * (2 * math.pi * s * s) ** -1.5 * np.exp(-r2 / (2 * s * s)), 0.0)
+    return rho
+
+
+def test_initial_guess_normalisation_shape_and_cut():
+    """u_0 = sqrt(rho_0) scaled to h^3 sum u_0^2 = N (Sec. 4 starting guess, R7):
+    the norm holds to rounding, u_0^2 is one constant times the Gaussian density
+    at every node inside the cut and zero outside, and that constant is the
+    inverse of the density's discrete mass, close to the continuous mass of a
+    Gaussian truncated at 4 widths."""
+    from scipy.special import erf
+    h = 0.45
+    m = 44
+    g = O.make_grid(m, m, m, h, origin=(-m * h / 2,) * 3)
+    R = np.array([[0.111, -0.053, 0.027]])  # no node on the atom or on the cut sphere
+    u = O.initial_guess(g, R, [3.0], 2.0, 8.0, N=3.0)
+    assert h**3 * (u * u).sum() == pytest.approx(3.0, rel=1e-12)
+    rho = _guess_density(g, R, [3.0])
+    inside = rho > 0
+    ratio = (u * u)[inside] / rho[inside]
+    assert np.ptp(ratio) <= 1e-12 * ratio.mean()
+    assert np.all(u[~inside] == 0.0) and np.all(u >= 0.0)
+    a = 8.0 / 2.0  # cut over width
+    mass = erf(a / math.sqrt(2)) - math.sqrt(2 / math.pi) * a * math.exp(-a * a / 2)
+    assert 1.0 / ratio.mean() == pytest.approx(mass, rel=3e-3)
+
+
+def test_initial_guess_superposes_atoms_weighted_by_charge():
+    """Two atoms of charges 3 and 1, 6 bohr apart (their 8-bohr spheres overlap):
+    u_0^2 is proportional to the sum of the two Gaussian densities, each
+    weighted by its charge, and the total still integrates to N = 4."""
+    h = 0.5
+    g = O.make_grid(48, 40, 40, h, origin=(-12.0, -10.0, -10.0))
+    R = np.array([[-3.02, 0.04, -0.03], [2.97, -0.06, 0.05]])
+    Z = [3.0, 1.0]
+    u = O.initial_guess(g, R, Z, 2.0, 8.0, N=4.0)
+    assert h**3 * (u * u).sum() == pytest.approx(4.0, rel=1e-12)
+    rho = _guess_density(g, R, Z)
+    inside = rho > 0
+    ratio = (u * u)[inside] / rho[inside]
+    assert np.ptp(ratio) <= 1e-12 * ratio.mean()
+    assert np.all(u[~inside] == 0.0)
+    # a single atom's guess is not the same as the pair's restricted to it
+    u1 = O.initial_guess(g, R[:1], Z[:1], 2.0, 8.0, N=3.0)
+    assert np.abs(u1 * u1 - u * u).max() > 1e-3
+
+
 # ----------------------------------------------------------- pseudocharge ---
 def test_pseudocharge_total_charge_and_self_energy_converge():
     """sum h^3 b_J -> -Z_J, and E_self -> Z^2/(sigma sqrt(2 pi)) (Gaussian self
@@ -272,6 +327,82 @@ def test_xc_branches_meet_at_rs_one_and_limits():
     assert O.xc(_u_of_rs(rs))[0] * rs == pytest.approx(-0.4581652932831429, rel=1e-5)
     # density floor: no NaN at u = 0
     assert O.xc(0.0) == (0.0, 0.0)
+
+
+def _eps_c(rs):
+    """Correlation part of the oracle's eps_xc: eps_xc minus the closed-form
+    exchange energy of the uniform gas, -(3/4)(9/(4 pi^2))^(1/3) / r_s."""
+    ex = -0.75 * (9.0 / (4.0 * math.pi**2)) ** (1.0 / 3.0) / rs
+    return O.xc(_u_of_rs(rs))[0] - ex
+
+
+def _pz_constants():
+    out = {}
+    for line in open(os.path.join(GOLDEN, "pz_correlation_constants.txt")):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            k, v = line.split()
+            out[k] = float(v)
+    return out
+
+
+def test_correlation_constants_recovered_from_oracle_match_paper():
+    """Both branches of eps_c are linear in their constants once rearranged:
+    1/eps_c = 1/gamma_1 + (beta_1/gamma_1) sqrt(r_s) + (beta_2/gamma_1) r_s on
+    r_s >= 1, and eps_c = A_1 ln r_s + B_1 + C_1 r_s ln r_s + D_1 r_s on r_s < 1.
+    Solving those systems from the oracle's own values at several r_s recovers
+    the constants it uses, which must be the ones printed in Sec. 2 (a fixture
+    under tests/golden/).  A single mistyped digit moves a recovered constant by
+    far more than the 1e-9 allowed here."""
+    k = _pz_constants()
+    rs_hi = np.array([1.0, 1.7, 2.5, 4.0, 7.0, 12.0, 30.0])
+    A = np.stack([np.ones_like(rs_hi), np.sqrt(rs_hi), rs_hi], axis=1)
+    y = np.array([1.0 / _eps_c(r) for r in rs_hi])
+    c, *_ = np.linalg.lstsq(A, y, rcond=None)
+    gamma = 1.0 / c[0]
+    assert gamma == pytest.approx(k["gamma_1"], rel=1e-9)
+    assert c[1] * gamma == pytest.approx(k["beta_1"], rel=1e-9)
+    assert c[2] * gamma == pytest.approx(k["beta_2"], rel=1e-9)
+    rs_lo = np.array([0.003, 0.02, 0.08, 0.2, 0.45, 0.7, 0.95])
+    lr = np.log(rs_lo)
+    A = np.stack([lr, np.ones_like(rs_lo), rs_lo * lr, rs_lo], axis=1)
+    y = np.array([_eps_c(r) for r in rs_lo])
+    c, *_ = np.linalg.lstsq(A, y, rcond=None)
+    assert c[0] == pytest.approx(k["A_1"], rel=1e-9)
+    assert c[1] == pytest.approx(k["B_1"], rel=1e-9)
+    assert c[2] == pytest.approx(k["C_1"], rel=1e-8)
+    assert c[3] == pytest.approx(k["D_1"], rel=1e-9)
+
+
+def test_correlation_high_density_slope_is_gell_mann_brueckner():
+    """As r_s -> 0 the correlation energy of the uniform gas goes as
+    ((1 - ln 2) / pi^2) ln r_s (Gell-Mann and Brueckner 1957, random-phase
+    approximation, exact in that limit); the Ceperley-Alder fit keeps that slope
+    rounded to three figures."""
+    slope = (_eps_c(1e-6) - _eps_c(1e-8)) / (math.log(1e-6) - math.log(1e-8))
+    assert slope == pytest.approx((1.0 - math.log(2.0)) / math.pi**2, abs=2e-5)
+
+
+def _vwn_eps_c(rs):
+    """Vosko, Wilk and Nusair (Can. J. Phys. 58, 1200 (1980)), their Pade fit of
+    the same Ceperley-Alder quantum Monte Carlo data, paramagnetic case, in
+    hartree: an independent parametrisation to compare the curve's shape with."""
+    A, b, c, x0 = 0.0310907, 3.72744, 12.9352, -0.10498
+    x = math.sqrt(rs)
+    X = lambda t: t * t + b * t + c  # noqa: E731
+    Q = math.sqrt(4.0 * c - b * b)
+    at = math.atan(Q / (2.0 * x + b))
+    return A * (math.log(x * x / X(x)) + 2.0 * b / Q * at
+                - b * x0 / X(x0) * (math.log((x - x0) ** 2 / X(x)) + 2.0 * (b + 2.0 * x0) / Q * at))
+
+
+@pytest.mark.parametrize("rs", [0.1, 0.3, 0.5, 0.8, 1.0, 1.5, 2.0, 3.0, 5.0, 10.0, 20.0, 50.0])
+def test_correlation_energy_agrees_with_independent_fit(rs):
+    """The oracle's eps_c lies within 2% of the Vosko-Wilk-Nusair fit of the same
+    data on both branches (the two fits differ by at most 1.3%, about 1 mHa, near
+    r_s = 0.5 and by under 1% from r_s = 1 on); a wrong sign, factor or branch
+    would not."""
+    assert _eps_c(rs) == pytest.approx(_vwn_eps_c(rs), rel=2e-2)
 
 
 # -------------------------------------------------------------- grid rule ---
