@@ -1,15 +1,18 @@
 #!/usr/bin/env python
 """Ground-state throughput of the Augmented Lagrangian OF-DFT solver on GB300.
 
-One step = one complete ground state of the 5x5x5-cell FCC cluster (666 atoms,
-Z = 3, a = 7.6 bohr, seeded +-0.1 bohr displacements, 10 bohr vacuum, h = 0.5
-bohr -> 128^3 grid, 12th-order FD): pseudocharge and starting guess,
-Algorithm 1 around PR nonlinear CG with one CG Poisson solve per gradient
-evaluation, then the forces.  Synthetic input (the paper's aluminium clusters
-with Gaussian nuclei standing in for its pseudopotential).
+One step = one complete ground state of the 8x8x8-cell FCC cluster (2457 atoms,
+Z = 3, a = 7.6 bohr, seeded +-0.1 bohr displacements, 10 bohr vacuum, h = 0.45
+bohr -> 192^3 grid, 12th-order FD) in the mixed-precision form:
+pseudocharge and starting guess, Algorithm 1 around PR nonlinear CG with one
+Poisson solve per gradient evaluation, then the forces.  The plain FP64 form
+of the same ground state is timed beside it.  Synthetic input (the paper's
+aluminium clusters with Gaussian nuclei standing in for its pseudopotential).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
+                  [--workload fcc8|fcc5]
   python bench.py --impl reference ...   (the FP64 CPU oracle, bounded samples)
+  python bench.py --mode batch|serve     (64-cluster batch / Poisson-arrival serving)
 
 Prints one JSON line on rank 0.
 """
@@ -33,25 +36,38 @@ sys.path.insert(0, ROOT)
 METRIC = "ground states/s + p50/p99 latency at 1e-5 Ha/atom; stencil HBM GB/s vs peak"
 UNIT = "ground states/s"
 FP64_ALU_PEAK_GFLOPS = 152 * 2 * 2 * 2.070  # SMs x DFMA/clk/SM x 2 flop x GHz (sm_103a, 2070 MHz)
-COUNTS_FILE = os.path.join(ROOT, "profiles", "c2_solve_counts.json")
+GOLDEN = os.path.join(ROOT, "tests", "golden")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+CELLS = {"fcc8": 8, "fcc5": 5}
 
 
-def workload():
+def workload(name="fcc8", seed=None):
     from paper_1405_6456_gb300 import workloads as W
-    return W.cluster_c2()
+    f = W.cluster_c3 if name == "fcc8" else W.cluster_c2
+    return f() if seed is None else f(seed=seed)
 
 
-def workload_config(c, g, precision, extra=None):
-    cfg = {"workload": f"{c.name}: {c.M} atoms, FCC 5x5x5 cells a=7.6 bohr, Z=3, seeded +-0.1 bohr, "
+def workload_config(c, g, precision, name, extra=None):
+    m = CELLS[name]
+    cfg = {"workload": f"{c.name}: {c.M} atoms, FCC {m}x{m}x{m} cells a=7.6 bohr, Z=3, seeded +-0.1 bohr, "
                        f"h={c.h} bohr, {c.fd_order}th-order FD, {c.vacuum} bohr vacuum, grid "
                        f"{g[0]}x{g[1]}x{g[2]}, AL+PR-NLCG ground state with a Poisson solve per evaluation, to 1e-6 "
                        f"Ha/atom, forces",
            "atoms": c.M, "grid": list(g), "fd_order": c.fd_order, "precision": precision,
-           "l2": "flushed between steps (256 MB write); the 128^3 CG working set itself fits in L2"}
+           "l2": "flushed between steps (256 MB write)"}
     if extra:
         cfg.update(extra)
     return cfg
+
+
+def golden(c, tol):
+    """The oracle's ground state of cluster c (tests/golden/, written by
+    tests/golden/make_ground_states.py), or None."""
+    try:
+        with open(os.path.join(GOLDEN, f"ground_state_{c.name}_{tol}.json")) as f:
+            return json.load(f)
+    except Exception:
+        return None
 
 
 def load_peaks():
@@ -135,11 +151,12 @@ def dist_setup(backend=None):
     return ws, rank, local, pg
 
 
-def replica_cluster(rank, ws):
+def replica_cluster(name, rank, ws):
     """The cluster rank `rank` of `ws` solves: replicas only, every rank its own
-    independent seeded 666-atom cluster (no data-path collective)."""
-    from paper_1405_6456_gb300 import workloads as W
-    return W.cluster_c2(seed=2 + rank) if ws > 1 else W.cluster_c2()
+    independent seeded cluster of the workload (no data-path collective)."""
+    if ws == 1:
+        return workload(name)
+    return workload(name, seed=(3 if name == "fcc8" else 2) + rank)
 
 
 def job_rate(pg, ws, units_per_rank, local_seconds, device):
@@ -163,74 +180,177 @@ def allreduce_max(pg, x, device):
 
 
 # ----------------------------------------------------------- CPU oracle arm --
-def oracle_sample(c, n_cg=4):
-    """Time the FP64 CPU oracle on a bounded sample of the workload: n_cg CG
-    iterations of the 128^3 Poisson problem and one functional evaluation.
-    Returns (seconds per CG iteration, seconds per functional evaluation)."""
-    import oracle as O
-    O.build()
-    g = O.grid_for_atoms(c.R, c.h, c.vacuum, 16)
-    n = c.fd_order // 2
-    b, es = O.pseudocharge(g, n, c.R, c.Z)
-    u = O.initial_guess(g, c.R, c.Z)
-    rho = u**2 + b
-    t0 = time.perf_counter()
-    O.poisson(g, n, rho, tol=1e-300, max_it=n_cg)
-    t1 = time.perf_counter()
-    O.poisson(g, n, rho, tol=1e-300, max_it=0)
-    t2 = time.perf_counter()
-    t_cg = ((t1 - t0) - (t2 - t1)) / n_cg
-    p = O.default_params()
-    phi = np.zeros(g.shape)
-    t3 = time.perf_counter()
-    O.functional(g, p, u, b, phi, es, -0.2, 1.0, c.N)
-    t_fun = time.perf_counter() - t3
-    return t_cg, t_fun
-
-
-def read_counts():
+def cpu_model():
     try:
-        with open(COUNTS_FILE) as f:
-            return json.load(f)
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
     except Exception:
+        pass
+    return "unknown"
+
+
+class OracleSampler:
+    """Times the FP64 CPU oracle on a bounded sample of a workload: n_cg CG
+    iterations of its Poisson problem and one functional evaluation (the
+    pseudocharge and starting guess are set up once, untimed).  The oracle's
+    whole ground state is then scaled from its own counts of CG iterations and
+    gradient evaluations (tests/golden/, at the benchmark's tolerances)."""
+
+    def __init__(self, c):
+        import oracle as O
+        O.build()
+        self.O = O
+        self.c = c
+        self.g = O.grid_for_atoms(c.R, c.h, c.vacuum, 16)
+        self.n = c.fd_order // 2
+        O.set_threads(os.cpu_count() or 1)
+        self.b, self.es = O.pseudocharge(self.g, self.n, c.R, c.Z)
+        self.u = O.initial_guess(self.g, c.R, c.Z)
+        self.rho = self.u**2 + self.b
+        self.p = O.default_params(fd_n=self.n)
+
+    def sample(self, threads, n_cg=3):
+        """(seconds per CG iteration, seconds per functional evaluation, threads used)."""
+        O = self.O
+        O.set_threads(threads)
+        used = O.threads()
+        t0 = time.perf_counter()
+        O.poisson(self.g, self.n, self.rho, tol=1e-300, max_it=n_cg)
+        t1 = time.perf_counter()
+        O.poisson(self.g, self.n, self.rho, tol=1e-300, max_it=0)
+        t2 = time.perf_counter()
+        t_cg = max((t1 - t0) - (t2 - t1), 0.0) / n_cg
+        phi = np.zeros(self.g.shape)
+        t3 = time.perf_counter()
+        O.functional(self.g, self.p, self.u, self.b, phi, self.es, -0.2, 1.0, self.c.N)
+        t_fun = time.perf_counter() - t3
+        return t_cg, t_fun, used
+
+
+def oracle_counts(c):
+    """The oracle's own work per ground state at the benchmark's tolerances."""
+    gd = golden(c, "product")
+    if gd is None:
         return None
+    return gd["counts"]["cg_iters"], gd["counts"]["grad_evals"]
 
 
 def run_reference(args):
-    ws, rank, local, pg = dist_setup()
+    ws, rank, local, pg = dist_setup("gloo")
     if rank != 0:
         return 0
-    c = workload()
-    counts = read_counts()
+    c = workload(args.workload)
+    counts = oracle_counts(c)
     if counts is None:
-        print(json.dumps({"impl": "reference", "unavailable": "profiles/c2_solve_counts.json missing: the "
-                          "oracle cannot finish this ground state in minutes and needs the counts to scale"}))
+        print(json.dumps({"impl": "reference", "unavailable": f"tests/golden/ground_state_{c.name}_product.json "
+                          "missing: the oracle's own iteration counts scale its timed sample"}))
         return 0
-    cg_per, ev_per = counts["cg_iters"], counts["grad_evals"]
+    cg_per, ev_per = counts
+    smp = OracleSampler(c)
+    threads = os.cpu_count() or 1
     for _ in range(args.warmup):
-        oracle_sample(c, n_cg=2)
+        smp.sample(threads, n_cg=1)
     times = []
+    used = threads
     for _ in range(args.steps):
-        t_cg, t_fun = oracle_sample(c, n_cg=3)
+        t_cg, t_fun, used = smp.sample(threads, n_cg=3)
         times.append(t_cg * cg_per + t_fun * ev_per)
     sec = statistics.mean(times)
     val = 1.0 / sec
-    g = counts.get("grid", [128, 128, 128])
+    g = [smp.g.n1, smp.g.n2, smp.g.n3]
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(c, g, "fp64"),
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"per step: oracle pseudocharge + 3 CG iterations + 1 functional at 128^3, "
-                                       f"scaled to {cg_per} CG iterations and {ev_per} gradient evaluations "
-                                       f"per ground state (counts of the plain-CG FP64 GPU solve of this "
-                                       f"workload, the oracle's own iteration)"},
+            "config": workload_config(c, g, args.precision, args.workload),
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": used, "kind": "oracle",
+                             "cpu_model": cpu_model(), "nproc": os.cpu_count(),
+                             "sample": f"per step: 3 oracle CG iterations + 1 functional evaluation on the "
+                                       f"{g[0]}x{g[1]}x{g[2]} grid ({used} threads), scaled to the oracle's own "
+                                       f"{cg_per} CG iterations and {ev_per} gradient evaluations per ground "
+                                       f"state at the benchmark's tolerances (tests/golden/)"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
 
 # ------------------------------------------------------------------ GPU arm --
+def _traffic(key):
+    """Per-launch DRAM bytes from the committed ncu summary, if it was measured on
+    the current kernel sources."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            tr = json.load(f)
+        if tr.get("src_hash") == src_hash() and key in tr:
+            return tr[key]["bytes_per_launch_full"]
+    except Exception:
+        pass
+    return None
+
+
+def roofline_entries(cnt, sampled, G, n, prec_name, es, fold):
+    """Rooflines of the hot kernels from CUDA-event durations of a profiled
+    ground state: one entry per kernel with its algorithmic bytes (or flops) per
+    launch over its mean launch duration, and its total time."""
+    from paper_1405_6456_gb300 import ofdft as F
+    peak_hbm, which = load_peaks()
+    out = []
+    # CG stencil pass (one launch in eight timed inside the CG graphs)
+    k = F.K_CG_DIR_STENCIL
+    if sampled.timed_launches[k] > 0:
+        avg = sampled.timed_ms[k] / sampled.timed_launches[k] / 1e3
+        algo = G * (7 if fold else 5) * es  # read r (stencil), p, q (, x); write p, q (, x)
+        e = {"kernel": "zstream_kernel<%s,%d,LoadPlain,EpiCgA%s> (CG: q = A z + beta q, p = z + beta p, p.q%s)"
+                       % ("float" if es == 4 else "double", n, "X" if fold else "", ", x += alpha p_old" if fold else ""),
+             "launches_timed": int(sampled.timed_launches[k]), "avg_us": avg * 1e6,
+             "total_ms": avg * 1e3 * cnt.kind_launches[k],
+             "algorithmic_bytes_per_launch": algo, "traffic": _traffic(f"cg_dir_stencil_{prec_name}"),
+             "timing": "CUDA events inside the CG graphs around one stencil launch in eight"}
+        if es == 4:
+            ach = algo / avg / 1e9
+            e.update({"bound": "hbm", "achieved": ach, "peak": peak_hbm, "unit": "GB/s", "frac": ach / peak_hbm,
+                      "peak_source": which})
+        else:
+            fl = G * (2 * (6 * n + 1) + 6 + (2 if fold else 0))
+            ach = fl / avg / 1e9
+            e.update({"bound": "alu", "achieved": ach, "peak": FP64_ALU_PEAK_GFLOPS, "unit": "GFLOP/s",
+                      "frac": ach / FP64_ALU_PEAK_GFLOPS, "algorithmic_flops_per_launch": fl,
+                      "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2070 MHz"})
+        out.append(e)
+    # FP64 residual pass of each Poisson round (every launch timed)
+    k = F.K_RESIDUAL
+    if sampled.timed_launches[k] > 0:
+        avg = sampled.timed_ms[k] / sampled.timed_launches[k] / 1e3
+        fl = G * (2 * (6 * n + 1) + 10)
+        ach = fl / avg / 1e9
+        out.append({"kernel": "zstream_kernel<double,%d,LoadPlain,EpiResidual> (FP64 residual 4 pi (u^2 + b) + "
+                              "L_h phi of each Poisson round, with r.r, b.b, u.u)" % n,
+                    "bound": "alu", "achieved": ach, "peak": FP64_ALU_PEAK_GFLOPS, "unit": "GFLOP/s",
+                    "frac": ach / FP64_ALU_PEAK_GFLOPS, "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2070 MHz",
+                    "launches_timed": int(sampled.timed_launches[k]), "avg_us": avg * 1e6,
+                    "total_ms": sampled.timed_ms[k], "algorithmic_flops_per_launch": fl,
+                    "algorithmic_bytes_per_launch": G * 28, "traffic": _traffic(f"residual_fp64_{prec_name}"),
+                    "timing": "CUDA events around every residual launch"})
+    # fused functional + gradient pass (every launch timed)
+    k = F.K_FUNCTIONAL
+    if sampled.timed_launches[k] > 0:
+        avg = sampled.timed_ms[k] / sampled.timed_launches[k] / 1e3
+        algo = G * 5 * es  # read u (stencil), phi, b, d; write G
+        ach = algo / avg / 1e9
+        out.append({"kernel": "zstream_kernel<%s,%d,LoadPlain,EpiFunctional> (fused TF + vW + XC + electrostatic "
+                              "energy, gradient, preconditioner, 11 sums)" % ("float" if es == 4 else "double", n),
+                    "bound": "hbm", "achieved": ach, "peak": peak_hbm, "unit": "GB/s", "frac": ach / peak_hbm,
+                    "peak_source": which, "launches_timed": int(sampled.timed_launches[k]), "avg_us": avg * 1e6,
+                    "total_ms": sampled.timed_ms[k], "algorithmic_bytes_per_launch": algo,
+                    "traffic": _traffic(f"functional_{prec_name}"),
+                    "timing": "CUDA events around every functional launch"})
+    return out
+
+
 def run_gpu(args):
     import torch
     from paper_1405_6456_gb300 import build as B
@@ -239,34 +359,30 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     B.build()
-    from paper_1405_6456_gb300 import workloads as W
-    base = workload()
     # replicas only: every rank solves its own independent cluster
-    c = replica_cluster(rank, ws)
+    c = replica_cluster(args.workload, rank, ws)
     prec = F.PREC_MIXED if args.precision == "mixed" else F.PREC_FP64
-    p = F.default_params(precision=prec, tol_E=1e-6, vacuum=c.vacuum, round_to=16)
+    over = {}
+    for kv in args.param:  # solver-parameter experiments: --param name=value
+        k, v = kv.split("=", 1)
+        over[k] = type(getattr(F.default_params(), "lam" if k == "lambda" else k))(float(v))
+    p = F.default_params(precision=prec, tol_E=1e-6, vacuum=c.vacuum, round_to=16, **over)
     ctx = F.Context(local)
-    if args.write_counts:  # the counts scale the oracle, which runs plain CG
-        ctx.set_poisson_precond(F.PRECOND_NONE)
     stream = ctx.stream
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def one_solve():
-        return ctx.solve(c.R, c.Z, c.h, p)
+    def one_solve(pp):
+        return ctx.solve(c.R, c.Z, c.h, pp, allow_notconv=False)
 
+    g = tuple(F.ofdft_grid_for_atoms(c.R, c.h, c.vacuum, 16).n)
     for _ in range(args.warmup):
-        E, Fv, st = one_solve()
-    g = tuple(st.grid.n)
+        one_solve(p)
     G = g[0] * g[1] * g[2]
-    # timed region (device time per step, L2 flushed between steps)
-    dom = F.K_CG_DIR_STENCIL
+    # timed region: device time per step, L2 flushed between steps, no event
+    # instrumentation of the library's own (that runs in a separate pass below)
+    ctx.profile(False)
     ctx.reset_counters()
-    # events around the candidates for the dominant kernel only: the FP64
-    # residual passes of the Poisson rounds, the persistent CG launches, else one
-    # CG stencil pass in eight (inside the CG graphs)
-    ctx.profile(((1 << dom) | (1 << F.K_CG_PERSISTENT) | (1 << F.K_RESIDUAL)) if args.profile_timed else 0)
-    lat = []
-    stats = []
+    lat, stats = [], []
     barrier(pg)
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
@@ -275,7 +391,7 @@ def run_gpu(args):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            E, Fv, st = one_solve()
+            E, Fv, st = one_solve(p)
             e1.record(stream)
             e1.synchronize()
             lat.append(e0.elapsed_time(e1) / 1e3)
@@ -283,189 +399,134 @@ def run_gpu(args):
     torch.cuda.synchronize()
     barrier(pg)
     cnt = ctx.counters()
-    ctx.profile(False)
     total = sum(lat)
     value, total_max = job_rate(pg, ws, args.steps, total, dev)
-    # e2e: the public C-ABI call with host buffers (atoms in, energy+forces out)
-    ctx.reset_counters()
+    # e2e: the public C-ABI call with host buffers (atoms in, energy + forces out)
     barrier(pg)
     e2e_t = []
     for _ in range(args.steps):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        E2, F2, st2 = one_solve()
+        E2, F2, st2 = one_solve(p)
         e2e_t.append(time.perf_counter() - t0)
     e2e_val, e2e_max = job_rate(pg, ws, args.steps, sum(e2e_t), dev)
     h2d = c.R.nbytes + c.Z.nbytes
     d2h = 8 + 3 * c.M * 8
-    # roofline of the dominant kernel: the persistent CG kernel where the
-    # library ran it, else the CG direction + stencil pass
-    es = 4 if prec == F.PREC_MIXED else 8
-    roof = None
-    n = c.fd_order // 2
-    pk = F.K_CG_PERSISTENT
-    if cnt.timed_launches[pk] > 0 and cnt.persistent_cg_iters > 0:
-        tl, tms, its = cnt.timed_launches[pk], cnt.timed_ms[pk], cnt.persistent_cg_iters
-        avg_s = tms / tl / 1e3
-        traffic = None
-        try:
-            with open(TRAFFIC_FILE) as f:
-                tr = json.load(f)
-            key = f"cg_persistent_{args.precision}"
-            if tr.get("src_hash") == src_hash() and key in tr:
-                traffic = tr[key]["bytes_per_iteration_full"] * its / tl
-        except Exception:
-            pass
-        # per CG iteration: stencil half reads r, p, q and writes p, q; update
-        # half reads x, p, q, r and writes x, r
-        algo_it = 11 * G * es
-        kname = "cg_coop_kernel<%s,%d,%d> (whole CG iterations: q = A r + beta q, p = r + beta p, p.q | " \
-                "x += alpha p, r -= alpha q, r.r)" % ("float" if es == 4 else "double", n, 16 // es)
-        common = {"traffic": traffic, "kernel": kname, "launches": tl, "avg_us": avg_s * 1e6,
-                  "cg_iters_per_launch": its / tl,
-                  "timing": "CUDA events on the solve's stream around every persistent CG launch, over the "
-                            "whole timed region",
-                  "algorithmic_bytes_per_launch": algo_it * its / tl}
-        if prec == F.PREC_MIXED:
-            peak, which = load_peaks()
-            ach = algo_it * its / (tms / 1e3) / 1e9
-            roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                    "peak_source": which, **common}
-        else:
-            flops_it = G * (2 * (6 * n + 1) + 12)  # stencil, p, q, x, r updates, p.q, r.r
-            ach = flops_it * its / (tms / 1e3) / 1e9
-            roof = {"bound": "alu", "achieved": ach, "peak": FP64_ALU_PEAK_GFLOPS, "unit": "GFLOP/s",
-                    "frac": ach / FP64_ALU_PEAK_GFLOPS,
-                    "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2070 MHz",
-                    "algorithmic_flops_per_launch": flops_it * its / tl, **common}
-    tl, tms = cnt.timed_launches[dom], cnt.timed_ms[dom]
-    if roof is None and tl > 0:
-        avg_s = tms / tl / 1e3
-        traffic = None
-        try:
-            with open(TRAFFIC_FILE) as f:
-                tr = json.load(f)
-            key = f"cg_dir_stencil_{args.precision}"
-            if tr.get("src_hash") == src_hash() and key in tr:
-                traffic = tr[key]["bytes_per_launch_full"]
-        except Exception:
-            pass
-        if prec == F.PREC_MIXED:
-            peak, which = load_peaks()
-            fold = 5 * G * es > 96 * (1 << 20)  # the library folds the x update into this pass
-            algo = G * (7 if fold else 5) * es  # read r (stencil), p, q (, x); write p, q (, x)
-            ach = algo / avg_s / 1e9
-            roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                    "traffic": traffic, "kernel": "zstream_kernel<float,6,LoadPlain,EpiCgA%s> (CG: q = A r + beta q, p = r + beta p, p.q%s)" % (("X", ", x += alpha p_old") if fold else ("", "")),
-                    "launches": tl, "avg_us": avg_s * 1e6, "peak_source": which,
-                    "timing": "CUDA events on the solve's stream around one stencil launch in 8 (recorded "
-                              "inside the CG graphs), over the whole timed region",
-                    "algorithmic_bytes_per_launch": algo}
-        else:
-            fold = 5 * G * es > 96 * (1 << 20)
-            flops = G * (2 * (6 * n + 1) + 2 + 2 + 2 + (2 if fold else 0))  # stencil, p, q (, x) updates, p.q
-            ach = flops / avg_s / 1e9
-            roof = {"bound": "alu", "achieved": ach, "peak": FP64_ALU_PEAK_GFLOPS, "unit": "GFLOP/s",
-                    "frac": ach / FP64_ALU_PEAK_GFLOPS, "traffic": traffic,
-                    "kernel": "zstream_kernel<double,6,LoadPlain,EpiCgA%s> (CG: q = A r + beta q, p = r + beta p, p.q%s)" % (("X", ", x += alpha p_old") if fold else ("", "")), "launches": tl,
-                    "avg_us": avg_s * 1e6, "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2070 MHz",
-                    "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": G * (7 if fold else 5) * es}
-    # the FP64 residual pass r = 4 pi rho + L_h phi of every Poisson round
-    # (FP64 ALU-bound): 2(6n+1) stencil flops + u^2, 4 pi (u^2 + b), r and
-    # three dot products per node
-    roof_res = None
-    kr = F.K_RESIDUAL
-    if cnt.timed_launches[kr] > 0:
-        avg_r = cnt.timed_ms[kr] / cnt.timed_launches[kr] / 1e3
-        flops_r = G * (2 * (6 * n + 1) + 10)
-        ach_r = flops_r / avg_r / 1e9
-        traffic_r = None
-        try:
-            with open(TRAFFIC_FILE) as f:
-                tr = json.load(f)
-            key = f"residual_fp64_{args.precision}"
-            if tr.get("src_hash") == src_hash() and key in tr:
-                traffic_r = tr[key]["bytes_per_launch_full"]
-        except Exception:
-            pass
-        roof_res = {"bound": "alu", "achieved": ach_r, "peak": FP64_ALU_PEAK_GFLOPS, "unit": "GFLOP/s",
-                    "frac": ach_r / FP64_ALU_PEAK_GFLOPS, "traffic": traffic_r,
-                    "kernel": "zstream_kernel<double,%d,2,LoadPlain,EpiResidual> (FP64 residual "
-                              "4 pi (u^2 + b) + L_h phi of each Poisson round, with r.r, b.b, u.u)" % n,
-                    "launches": int(cnt.timed_launches[kr]), "avg_us": avg_r * 1e6,
-                    "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2070 MHz",
-                    "timing": "CUDA events on the solve's stream around every residual launch, over the whole "
-                              "timed region",
-                    "algorithmic_flops_per_launch": flops_r, "algorithmic_bytes_per_launch": G * 8 * 3,
-                    "total_ms": cnt.timed_ms[kr]}
-    if roof is not None and "launches" in roof and cnt.timed_launches[F.K_CG_PERSISTENT] == 0:
-        # the stencil pass's total: its mean duration times the CG iterations run
-        roof["total_ms_estimate"] = roof["avg_us"] / 1e3 * sum(s.cg_iters for s in stats)
-    roof_other = None
-    if roof_res is not None and (roof is None or roof_res["total_ms"] > roof.get("total_ms_estimate", 0.0)):
-        roof, roof_other = roof_res, roof
-    elif roof_res is not None:
-        roof_other = roof_res
-    kinds = {F.KIND_NAMES[k]: {"launches": int(cnt.kind_launches[k]),
-                               "ms": round(cnt.timed_ms[k], 3)} for k in range(F.K_COUNT) if cnt.kind_launches[k]}
     st = stats[-1]
     lat_sorted = sorted(lat)
+    es = 4 if prec == F.PREC_MIXED else 8
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * total_max / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
            "dtype": "f32+f64acc" if prec == F.PREC_MIXED else "f64", "data": "synthetic",
-           "config": workload_config(c, g, args.precision, {"parallelism": f"replicas x{ws}"}),
+           "config": workload_config(c, g, args.precision, args.workload,
+                                     {"parallelism": f"replicas x{ws}", **({"params": over} if over else {})}),
            "latency_s": {"p50": float(np.percentile(lat_sorted, 50)), "p99": float(np.percentile(lat_sorted, 99))},
-           "energy_per_atom": E / c.M, "eta": st.eta,
+           "energy_per_atom": E / c.M, "eta": st.eta, "converged": all(s.converged for s in stats),
            "per_solve": {"cg_iters": st.cg_iters, "grad_evals": st.grad_evals, "nlcg_iters": st.nlcg_iters,
                          "outer_iters": st.outer_iters, "stencil_apps": st.stencil_apps},
-           "gpu_launches": int(cnt.launches), "kernels": kinds,
-           "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-           "roofline": roof, "roofline_next": roof_other}
-    # plain FP64 form for comparison (the chosen form is MIXED)
+           "gpu_launches": int(cnt.launches),
+           "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}}
+    # the plain FP64 form of the same ground state (the chosen form is MIXED)
+    E64 = F64 = None
     if prec == F.PREC_MIXED and args.plain_steps > 0:
         p64 = F.default_params(precision=F.PREC_FP64, tol_E=1e-6, vacuum=c.vacuum, round_to=16)
+        one_solve(p64)  # warm-up: workspace, autotuner, graphs of the FP64 kernels
         t64 = []
         for _ in range(args.plain_steps):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            E64, F64, st64 = ctx.solve(c.R, c.Z, c.h, p64)
+            E64, F64, st64 = one_solve(p64)
             e1.record(stream)
             e1.synchronize()
             t64.append(e0.elapsed_time(e1) / 1e3)
-        out["plain_fp64"] = {"value": 1.0 / statistics.mean(t64), "unit": UNIT, "steps": args.plain_steps,
-                             "ms_per_step": 1e3 * statistics.mean(t64), "energy_per_atom": E64 / c.M,
+        med = statistics.median(t64)
+        out["plain_fp64"] = {"value": 1.0 / med, "unit": UNIT, "steps": args.plain_steps, "warmup": 1,
+                             "ms_per_step_median": 1e3 * med, "ms_per_step": [round(1e3 * t, 2) for t in t64],
+                             "energy_per_atom": E64 / c.M,
                              "mixed_minus_fp64_Ha_per_atom": (E - E64) / c.M,
                              "max_force_diff_Ha_per_bohr": float(np.abs(Fv - F64).max()),
-                             "cg_iters": st64.cg_iters, "grad_evals": st64.grad_evals}
-    if prec == F.PREC_FP64 and rank == 0 and args.write_counts:
-        os.makedirs(os.path.dirname(COUNTS_FILE), exist_ok=True)
-        with open(COUNTS_FILE, "w") as f:
-            json.dump({"workload": c.name, "grid": list(g), "cg_iters": st.cg_iters, "grad_evals": st.grad_evals,
-                       "stencil_apps": st.stencil_apps, "precision": "fp64"}, f, indent=1)
+                             "cg_iters": st64.cg_iters, "grad_evals": st64.grad_evals,
+                             "converged": bool(st64.converged)}
+    # error against the FP64 oracle's ground state of the same cluster (tests/golden/)
+    gd = golden(c, "tight") if ws == 1 else None
+    if gd is not None:
+        Fo = np.array(gd["forces_paper"])
+        vs = {"source": f"tests/golden/ground_state_{c.name}_tight.json", "E_per_atom": gd["E_per_atom"],
+              args.precision: {"dE_Ha_per_atom": (E - gd["E"]) / c.M,
+                               "max_dF_Ha_per_bohr": float(np.abs(Fv - Fo).max())}}
+        if E64 is not None:
+            vs["fp64"] = {"dE_Ha_per_atom": (E64 - gd["E"]) / c.M, "max_dF_Ha_per_bohr": float(np.abs(F64 - Fo).max())}
+        out["vs_oracle"] = vs
+    # profiled pass, after the timed region: (a) one ground state with CUDA
+    # events around the residual and functional launches and one CG stencil
+    # pass in eight (inside the CG graphs); (b) one with every launch timed
+    # (no graphs) for the per-kind breakdown
+    if args.profile_steps > 0:
+        ctx.reset_counters()
+        ctx.profile((1 << F.K_CG_DIR_STENCIL) | (1 << F.K_RESIDUAL) | (1 << F.K_FUNCTIONAL))
+        for _ in range(args.profile_steps):
+            flush.zero_()
+            one_solve(p)
+        sampled = ctx.counters()
+        ctx.reset_counters()
+        ctx.profile(True)
+        for _ in range(args.profile_steps):
+            flush.zero_()
+            one_solve(p)
+        allk = ctx.counters()
+        ctx.profile(False)
+        fold = 5 * G * es > 96 * (1 << 20)
+        ents = roofline_entries(sampled, sampled, G, c.fd_order // 2, args.precision, es, fold)
+        ents.sort(key=lambda e: -e["total_ms"])
+        if ents:
+            out["roofline"] = ents[0]
+            out["roofline_others"] = ents[1:]
+        tot = sum(allk.timed_ms[k] for k in range(F.K_COUNT))
+        out["kernels"] = {F.KIND_NAMES[k]: {"launches": int(allk.kind_launches[k] // args.profile_steps),
+                                            "ms": round(allk.timed_ms[k] / args.profile_steps, 3),
+                                            "share": round(allk.timed_ms[k] / tot, 4) if tot > 0 else None}
+                          for k in range(F.K_COUNT) if allk.kind_launches[k]}
+        out["kernels_note"] = ("per ground state, every launch bracketed by CUDA events (no CUDA graphs) in a "
+                               "profiled pass after the timed region; events add a few us per launch")
     ctx.close()
     out["clocks"] = clk.summary()
     if rank == 0 and ws == 1 and not args.no_cpu:
-        t_cg, t_fun = oracle_sample(base, n_cg=4)
-        # the oracle runs plain CG: scale by the plain-CG counts of this
-        # workload (profiles/c2_solve_counts.json), not by the PCG iterations
-        counts = read_counts()
-        cg_n, ev_n, src = ((counts["cg_iters"], counts["grad_evals"], "the plain-CG FP64 solve of this workload")
-                           if counts else (st.cg_iters, st.grad_evals, "this solve"))
-        sec = t_cg * cg_n + t_fun * ev_n
-        out["cpu_baseline"] = {"value": 1.0 / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
-                               "sample": f"oracle pseudocharge + 4 CG iterations + 1 functional evaluation at "
-                                         f"{g[0]}^3, scaled to {cg_n} CG iterations and {ev_n} gradient "
-                                         f"evaluations per ground state (counts of {src}; {t_cg:.3f} s/CG "
-                                         f"iteration, {t_fun:.3f} s/evaluation)"}
+        out["cpu_baseline"] = cpu_baseline(c)
     if rank == 0:
         print(json.dumps(out))
     if pg is not None:
         pg.destroy_process_group()
     return 0
+
+
+def cpu_baseline(c):
+    """The oracle timed on this machine's host cores at 1 thread and at all
+    cores, scaled by its own work per ground state."""
+    counts = oracle_counts(c)
+    smp = OracleSampler(c)
+    nproc = os.cpu_count() or 1
+    res = {}
+    for th in sorted({1, nproc}):
+        t_cg, t_fun, used = smp.sample(th, n_cg=2 if th == 1 else 4)
+        res[th] = (t_cg, t_fun, used)
+    if counts is None:
+        return {"value": None, "unit": UNIT, "cores": nproc, "kind": "oracle",
+                "sample": "oracle counts for this workload missing from tests/golden/",
+                "per_cg_iteration_s": {str(k): v[0] for k, v in res.items()}}
+    cg_n, ev_n = counts
+    sec = {th: v[0] * cg_n + v[1] * ev_n for th, v in res.items()}
+    gg = smp.g
+    return {"value": 1.0 / sec[nproc], "unit": UNIT, "cores": res[nproc][2], "kind": "oracle",
+            "value_1_thread": 1.0 / sec[1], "nproc": nproc, "cpu_model": cpu_model(),
+            "sample": f"oracle CG iterations (2 at 1 thread, 4 at {nproc}) + 1 functional evaluation on the "
+                      f"{gg.n1}x{gg.n2}x{gg.n3} grid, scaled to the oracle's own {cg_n} CG iterations and {ev_n} "
+                      f"gradient evaluations per ground state at the benchmark's tolerances (tests/golden/); "
+                      f"s per CG iteration: {res[1][0]:.3f} (1 thread), {res[nproc][0]:.3f} ({nproc}); "
+                      f"s per functional: {res[1][1]:.3f}, {res[nproc][1]:.3f}"}
 
 
 # ------------------------------------------------------ batch / serving modes --
@@ -489,17 +550,25 @@ def run_batch(args):
         t0 = time.perf_counter()
         ids = [bt.submit(c.R, c.Z, c.h, p) for c in cl]
         done_t = {}
+        unconv = set()
         rounds = 0
         while len(done_t) < len(ids):
             bt.step()
             rounds += 1
             for rid in ids:
-                if rid not in done_t and bt.poll(rid, allow_notconv=True) is not None:
+                if rid in done_t:
+                    continue
+                res = bt.poll(rid, allow_notconv=True)
+                if res is not None:
                     done_t[rid] = time.perf_counter() - t0
+                    if not res[2].converged:
+                        unconv.add(rid)
         wall = time.perf_counter() - t0
+        binfo = bt.info()
         bt.close()
-    lat = np.array(sorted(done_t.values()))
-    out.update({"value": len(cl) / wall, "wall_s": wall, "rounds": rounds,
+    lat = np.array(sorted(t for rid, t in done_t.items() if rid not in unconv))
+    out.update({"value": (len(cl) - len(unconv)) / wall, "wall_s": wall, "rounds": rounds,
+                "unconverged": len(unconv), "batch_launch_stats": binfo,
                 "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))}})
     # the same requests one at a time through ofdft_solve (the plain form)
     t0 = time.perf_counter()
@@ -536,18 +605,104 @@ def run_serve(args):
     return 0
 
 
+def run_kernels(args):
+    """Kernel microbenchmark on one n^3 grid (seeded random fields, through the
+    C ABI): a Poisson solve with a fixed iteration count times the CG stencil
+    pass, the CG update, the multigrid V-cycle and the residual pass; repeated
+    functional evaluations at a fixed potential time the fused functional pass.
+    Reports mean launch durations (CUDA events around each launch) with the
+    algorithmic bytes each pass moves.  Grids of 256^3 in FP32 exceed the 129 MB
+    L2, which makes a profiler's DRAM counters meaningful."""
+    import torch
+    from paper_1405_6456_gb300 import build as B
+    from paper_1405_6456_gb300 import ofdft as F
+    B.build()
+    dt = torch.float64 if args.kprec == "fp64" else torch.float32
+    es = 8 if args.kprec == "fp64" else 4
+    prec = F.PREC_FP64 if args.kprec == "fp64" else F.PREC_MIXED
+    ctx = F.Context(0)
+    n = args.n
+    g = F.make_grid(n, n, n, 0.5)
+    G = g.size
+    rng = np.random.default_rng(0)
+    dev = "cuda:0"
+    rho = torch.as_tensor(rng.standard_normal(g.shape), dtype=dt, device=dev)
+    fold = 5 * G * es > 96 * (1 << 20)
+    out = {"mode": "kernels", "grid": n, "order": args.order, "prec": args.kprec, "folded_update": fold}
+    peak, which = load_peaks()
+    out["hbm_peak_GBps"] = {"value": peak, "source": which}
+    if args.which in ("all", "cg"):
+        for _ in range(2):  # warm-up (autotuner, graphs), then the timed solve
+            phi = torch.zeros(g.shape, dtype=dt, device=dev)
+            ctx.reset_counters()
+            ctx.profile((1 << F.K_CG_DIR_STENCIL) | (1 << F.K_CG_UPDATE) | (1 << F.K_MG) | (1 << F.K_RESIDUAL))
+            st = ctx.poisson(g, args.order, phi, rho=rho, tol=1e-300, max_it=args.iters, allow_notconv=True)
+            cnt = ctx.counters()
+            ctx.profile(False)
+        out["cg_iterations"] = st.iterations
+        # per node: the stencil pass reads r, p, q and writes p, q (and moves x when folded); the update
+        # reads x, r, p, q and writes x, r (folded: reads r, q, writes r)
+        for k, name, acc in [(F.K_CG_DIR_STENCIL, "cg_dir_stencil", 7 if fold else 5),
+                             (F.K_CG_UPDATE, "cg_update", 3 if fold else 6)]:
+            nl = cnt.timed_launches[k]
+            if nl:
+                us = cnt.timed_ms[k] / nl * 1e3
+                out[name] = {"launches": nl, "avg_us": us, "algorithmic_bytes": G * acc * es,
+                             "GBps": G * acc * es / (us * 1e-6) / 1e9,
+                             "frac_hbm": G * acc * es / (us * 1e-6) / 1e9 / peak}
+        if cnt.timed_launches[F.K_MG]:
+            out["mg_vcycle"] = {"launches": cnt.timed_launches[F.K_MG],
+                                "launches_per_iteration": cnt.timed_launches[F.K_MG] / max(st.iterations, 1),
+                                "us_per_iteration": cnt.timed_ms[F.K_MG] * 1e3 / max(st.iterations, 1)}
+        if cnt.timed_launches[F.K_RESIDUAL]:
+            nl = cnt.timed_launches[F.K_RESIDUAL]
+            us = cnt.timed_ms[F.K_RESIDUAL] / nl * 1e3
+            out["residual"] = {"launches": nl, "avg_us": us}
+    if args.which in ("all", "functional"):
+        u = torch.as_tensor(0.1 * np.abs(rng.standard_normal(g.shape)), dtype=dt, device=dev)
+        b = torch.as_tensor(-0.1 * np.abs(rng.standard_normal(g.shape)), dtype=dt, device=dev)
+        phi = torch.as_tensor(rng.standard_normal(g.shape), dtype=dt, device=dev)
+        grad = torch.empty_like(u)
+        sv = torch.empty_like(u)
+        d = torch.as_tensor(rng.standard_normal(g.shape), dtype=dt, device=dev)
+        pp = F.default_params(fd_order=args.order, precision=prec)
+        for rep in range(2):
+            ctx.reset_counters()
+            ctx.profile(1 << F.K_FUNCTIONAL)
+            for _ in range(args.iters):
+                ctx.energy_grad(g, pp, u, b, phi, 0.0, -0.2, 1.0, 1.0, solve_poisson=False, grad=grad, s=sv,
+                                d=d)
+            cnt = ctx.counters()
+            ctx.profile(False)
+        nl = cnt.timed_launches[F.K_FUNCTIONAL]
+        if nl:
+            us = cnt.timed_ms[F.K_FUNCTIONAL] / nl * 1e3
+            algo = G * 5 * es  # read u (stencil), phi, b, d; write G
+            out["functional"] = {"launches": nl, "avg_us": us, "algorithmic_bytes": algo,
+                                 "GBps": algo / (us * 1e-6) / 1e9, "frac_hbm": algo / (us * 1e-6) / 1e9 / peak}
+    ctx.close()
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--plain-steps", type=int, default=1)
+    ap.add_argument("--workload", default="fcc8", choices=sorted(CELLS))
+    ap.add_argument("--plain-steps", type=int, default=5)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--write-counts", action="store_true")
-    ap.add_argument("--profile-timed", type=int, default=1)
-    ap.add_argument("--mode", default="solve", choices=["solve", "batch", "serve"])
+    ap.add_argument("--profile-steps", type=int, default=1)
+    ap.add_argument("--param", action="append", default=[])
+    ap.add_argument("--mode", default="solve", choices=["solve", "batch", "serve", "kernels"])
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--order", type=int, default=12)
+    ap.add_argument("--kprec", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--iters", type=int, default=20)
+    ap.add_argument("--which", default="all", choices=["all", "cg", "functional"])
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--batch-solo", type=int, default=4)
     ap.add_argument("--rates", default="1,5,20")
@@ -561,6 +716,8 @@ def main():
         return run_batch(args)
     if args.mode == "serve":
         return run_serve(args)
+    if args.mode == "kernels":
+        return run_kernels(args)
     return run_gpu(args)
 
 

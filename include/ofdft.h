@@ -154,7 +154,9 @@ void ofdft_default_params(ofdft_params* p);
  * (multigrid Jacobi weight in (0, 1), default 0.9), OFDFT_MG_SWEEPS (bottom-level
  * sweeps, default 20), OFDFT_COOP=1 (plain CG iterations in one persistent
  * cooperative launch per eight iterations where the grid's blocks fit on the
- * device at once), OFDFT_TRACE=1 (one stderr line per evaluation). */
+ * device at once), OFDFT_CG_FOLD_BYTES (bytes of the five CG vectors above which
+ * a CG folds its iterate update into the next stencil pass; default 96 MiB),
+ * OFDFT_TRACE=1 (one stderr line per evaluation). */
 int ofdft_create(ofdft_ctx** ctx, int device, void* cuda_stream);
 int ofdft_destroy(ofdft_ctx* ctx);
 
@@ -363,6 +365,30 @@ int ofdft_batch_run(ofdft_batch* b);
 /* Device bytes one batched solve of grid g holds while admitted. */
 long long ofdft_batch_bytes(const ofdft_grid* g, int prec);
 
+/* Launch statistics of a batch (no counterpart in the paper).  The CG loop of
+ * each Poisson round runs as one CUDA graph launch: a device-side WHILE loop
+ * over one iteration of every solve in the round (V-cycles, stencil pass,
+ * update, all solves packed into shared launches), captured the first time a
+ * set of solves meets and replayed while the set stays the same (it changes on
+ * admission and retirement).  Before the first capture on a new set of grids
+ * the autotuner times the batched CG stencil pass at 8, 16, 32 and 64 planes
+ * per CTA (z-tile depth) and keeps the fastest for the batch; the CTA shape
+ * itself (32 x 8 threads, 2 rows x 2 columns per thread in FP32, 2 x 1 in FP64)
+ * is fixed by the register-blocked kernel. */
+typedef struct {
+  long long rounds;            /* ofdft_batch_step calls that ran a round */
+  long long graph_captures;    /* CG loop graphs captured */
+  long long graph_replays;     /* CG loops run as one graph launch */
+  long long graph_iterations;  /* CG iterations run inside those graphs (largest per loop, summed) */
+  long long eager_iterations;  /* CG iterations launched one by one (one ahead of each graph launch) */
+  int z_depth;                 /* planes per CTA of the batched z-streaming passes */
+  int z_tuned;                 /* 1 once the autotuner has chosen z_depth */
+  int tune_candidates;         /* entries of tune_depth / tune_us from the last tuning */
+  int tune_depth[8];
+  double tune_us[8];           /* mean duration of the batched CG stencil pass at that depth */
+} ofdft_batch_stats;
+int ofdft_batch_info(const ofdft_batch* b, ofdft_batch_stats* out);
+
 /* Allocation-free variant of ofdft_poisson (FP64), for callers that cannot
  * allocate device memory: an application whose framework owns every device
  * allocation, or code that must not call cudaMalloc on a latency-critical path.
@@ -371,7 +397,8 @@ long long ofdft_batch_bytes(const ofdft_grid* g, int prec);
  * in one file-scope device array of about 6.1 MB that every GPU which loads the
  * library holds until the process exits, so it accepts grids of at most
  * 262144 nodes (64^3) and returns OFDFT_EINVAL beyond that.  The first call on
- * a device looks up the array's device address (cudaGetSymbolAddress), so make
+ * a device sets that device up (the array's device address through
+ * cudaGetSymbolAddress, the SM count, the kernels' shared-memory limits), so make
  * that first call before any stream capture.  All calls share the array and
  * it keeps the last call's contents (the reduction counter is cleared at the
  * start of each call): calls that overlap on the GPU, on any stream or from any
@@ -399,7 +426,8 @@ long long ofdft_workspace_bytes(const ofdft_grid* g, int fd_order, int prec);
 int ofdft_mg_plan(const ofdft_grid* g, int prec, int* levels, int* coarse_level, int* dims, long long* bytes);
 
 /* sizeof of the named ABI struct ("ofdft_grid", "ofdft_params", "ofdft_cg_stats",
- * "ofdft_energy", "ofdft_solve_stats", "ofdft_counters", "ofdft_relax_stats"), or -1 for any other
+ * "ofdft_energy", "ofdft_solve_stats", "ofdft_counters", "ofdft_relax_stats",
+ * "ofdft_batch_stats"), or -1 for any other
  * name: lets a binding check its struct layouts against the library's.  Host
  * only, no context needed. */
 long long ofdft_struct_bytes(const char* name);

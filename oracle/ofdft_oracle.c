@@ -305,20 +305,28 @@ void orc_pseudocharge(const orc_grid* g, int n, const double* R, const double* Z
   const double h3 = g->h * g->h * g->h;
   memset(b, 0, sizeof(double) * G);
   double es = 0.0;
-  for (int J = 0; J < M; ++J) {
-    atom_box ab;
-    atom_box_build(g, n, R + 3 * J, Z[J], sigma, rc, 0, &ab);
-    for (long c = 0; c < ab.dim[2]; ++c)
-      for (long bb = 0; bb < ab.dim[1]; ++bb)
-        for (long a = 0; a < ab.dim[0]; ++a) {
-          const long i = ab.lo[0] + a, j = ab.lo[1] + bb, k = ab.lo[2] + c;
-          if (i < 0 || j < 0 || k < 0 || i >= g->n1 || j >= g->n2 || k >= g->n3) continue;
-          const double bj = ab_b(&ab, i, j, k);
-          if (bj == 0.0) continue;
-          b[i + (long)g->n1 * (j + (long)g->n2 * k)] += bj;
-          es += 0.5 * h3 * bj * ab_v(&ab, i, j, k);
-        }
-    atom_box_free(&ab);
+  /* the atoms' tables are built in parallel in groups; their contributions are
+     added to b in atom order */
+  enum { GROUP = 32 };
+  atom_box boxes[GROUP];
+  for (int J0 = 0; J0 < M; J0 += GROUP) {
+    const int nj = (M - J0 < GROUP) ? M - J0 : GROUP;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int t = 0; t < nj; ++t) atom_box_build(g, n, R + 3 * (J0 + t), Z[J0 + t], sigma, rc, 0, &boxes[t]);
+    for (int t = 0; t < nj; ++t) {
+      atom_box* ab = &boxes[t];
+      for (long c = 0; c < ab->dim[2]; ++c)
+        for (long bb = 0; bb < ab->dim[1]; ++bb)
+          for (long a = 0; a < ab->dim[0]; ++a) {
+            const long i = ab->lo[0] + a, j = ab->lo[1] + bb, k = ab->lo[2] + c;
+            if (i < 0 || j < 0 || k < 0 || i >= g->n1 || j >= g->n2 || k >= g->n3) continue;
+            const double bj = ab_b(ab, i, j, k);
+            if (bj == 0.0) continue;
+            b[i + (long)g->n1 * (j + (long)g->n2 * k)] += bj;
+            es += 0.5 * h3 * bj * ab_v(ab, i, j, k);
+          }
+      atom_box_free(ab);
+    }
   }
   *E_self = es;
 }
@@ -994,6 +1002,7 @@ void orc_forces(const orc_grid* g, int n, const double* R, const double* Z, int 
   double wt[ORC_MAX_N + 1], w[ORC_MAX_N + 1];
   orc_grad_weights(n, g->h, wt);
   orc_lap_weights(n, g->h, w);
+#pragma omp parallel for schedule(dynamic, 1)
   for (int J = 0; J < M; ++J) {
     atom_box ab;
     atom_box_build(g, n, R + 3 * J, Z[J], sigma, rc, n, &ab);

@@ -6,6 +6,20 @@
 
 namespace ofd {
 
+// Reads (and clears) the flag a z-streaming pass raises when a TMA copy it
+// waited for never arrived (its waits are bounded); OFDFT_ETIMEOUT if raised.
+int zstream_fault_check(ofdft_ctx* c) {
+  if (!c->tma) return OFDFT_OK;
+  int v = 0;
+  CU(cudaMemcpyFromSymbolAsync(&v, zstream_fault, sizeof(int), 0, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  if (!v) return OFDFT_OK;
+  const int zero = 0;
+  CU(cudaMemcpyToSymbolAsync(zstream_fault, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return fail(c, OFDFT_ETIMEOUT, "a TMA copy of a z-streaming pass did not arrive (bounded wait ran out)");
+}
+
 // ------------------------------------------------------------ Poisson (S3) --
 // The r update of one CG iteration with r.r (second kernel of cg_step); the
 // iterate update x += alpha p is folded into the next stencil pass (EpiCgAX).
@@ -38,10 +52,12 @@ int cg_update(ofdft_ctx* c, const GridDev& g, T* x, T* r, T* pv, T* qv, CgScalar
 // Whether a CG solve folds the iterate update into the stencil pass: it saves
 // 8 bytes per node and iteration, which pays when the CG vectors stream from
 // DRAM; when they stay in the 129 MB L2 the update kernel is bound by its fixed
-// costs and the heavier stencil epilogue does not pay (measured at 128^3).
+// costs and the heavier stencil epilogue does not pay (measured at 128^3).  The
+// threshold on the five CG vectors' bytes is 96 MiB unless OFDFT_CG_FOLD_BYTES
+// set another at context creation.
 template <typename T>
-bool cg_fold(const GridDev& g) {
-  return 5.0 * (double)g.G * sizeof(T) > 96.0 * (1 << 20);
+bool cg_fold(const ofdft_ctx* c, const GridDev& g) {
+  return 5.0 * (double)g.G * sizeof(T) > c->cg_fold_bytes;
 }
 
 // The stencil pass of one CG iteration: q = A r + beta q, p = r + beta p, p.q,
@@ -83,11 +99,18 @@ int mg_prepare(ofdft_ctx* c, const GridDev& g, double h, MgPlan* P) {
   TRY(ensure(c, c->v[V_T], g.G * sizeof(T)));
   TRY(ensure(c, c->mgbuf, std::max<long long>(P->elems, 1) * sizeof(T)));
   TRY(ensure_partials(c, pointwise_blocks(c, g.G), 1));
-  static bool attr = false;  // per element type
-  if (!attr) {
+  {
+    using D = MgPU<T>;
+    const long long nb = (long long)((g.n1 + D::FX - 1) / D::FX) * ((g.n2 + D::FY - 1) / D::FY) *
+                         ((g.n3 + D::FZ - 1) / D::FZ);
+    TRY(ensure_partials(c, nb, 1));
+  }
+  static bool attr_dev[64] = {false};  // per element type and device (a per-device setting)
+  if (c->device < 0 || c->device >= 64) return fail(c, OFDFT_EINVAL, "device index out of range");
+  if (!attr_dev[c->device]) {
     CU(cudaFuncSetAttribute(mg_coarse_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     CU(cudaFuncSetAttribute(mg_coarse_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr = true;
+    attr_dev[c->device] = true;
   }
   return OFDFT_OK;
 }
@@ -101,17 +124,32 @@ int mg_vcycle(ofdft_ctx* c, const MgPlan& P, const T* r, T* z, CgScalars* sc) {
   auto rl = [&](int l) -> T* { return l == 0 ? const_cast<T*>(r) : cb + P.off[l]; };
   auto zl = [&](int l) -> T* { return l == 0 ? z : cb + P.off[l] + mg_nodes(P.d[l]); };
   auto tl = [&](int l) -> T* { return l == 0 ? t0 : cb + P.off[l] + 2 * mg_nodes(P.d[l]); };
-  auto blocks = [&](long long G) { return (int)std::min<long long>((G + 255) / 256, (long long)c->sms * 8); };
+  // the plain passes take a warp per x-row: enough blocks for every row, at most 8 per SM
+  auto rows_blocks = [&](const MgLevel& d) {
+    return (int)std::max<long long>(1, std::min<long long>(((long long)d.n2 * d.n3 + 7) / 8, (long long)c->sms * 8));
+  };
+  // levels with at least mg_fuse_nodes nodes take the two fused passes (shared-memory
+  // tiles), smaller ones the four plain passes (more blocks for little work)
+  auto fused = [&](int l) { return c->mg_fuse_nodes >= 0 && mg_nodes(P.d[l]) >= c->mg_fuse_nodes; };
   const T om = (T)c->mg_omega;
   for (int l = 0; l < P.lc; ++l) {
+    if (fused(l)) {
+      using D = MgDR<T>;
+      const MgLevel& dc = P.d[l + 1];
+      const dim3 gr((dc.n1 + D::CX - 1) / D::CX, (dc.n2 + D::CY - 1) / D::CY, (dc.n3 + D::CZ - 1) / D::CZ);
+      ProfScope ps_(c, OFDFT_K_MG);
+      CU(launch_k(c, mg_down_restrict_kernel<T>, gr, dim3(256), 0, P.d[l], dc, (const T*)rl(l), rl(l + 1), om,
+                  (const CgScalars*)sc));
+      continue;
+    }
     {
       ProfScope ps_(c, OFDFT_K_MG);
-      CU(launch_k(c, mg_down_kernel<T>, dim3(blocks(mg_nodes(P.d[l]))), dim3(256), 0, P.d[l], (const T*)rl(l), tl(l),
+      CU(launch_k(c, mg_down_kernel<T>, dim3(rows_blocks(P.d[l])), dim3(256), 0, P.d[l], (const T*)rl(l), tl(l),
                   om, (const CgScalars*)sc));
     }
     {
       ProfScope ps_(c, OFDFT_K_MG);
-      CU(launch_k(c, mg_restrict_kernel<T>, dim3(blocks(mg_nodes(P.d[l + 1]))), dim3(256), 0, P.d[l], P.d[l + 1],
+      CU(launch_k(c, mg_restrict_kernel<T>, dim3(rows_blocks(P.d[l + 1])), dim3(256), 0, P.d[l], P.d[l + 1],
                   (const T*)tl(l), rl(l + 1), (const CgScalars*)sc));
     }
   }
@@ -129,9 +167,22 @@ int mg_vcycle(ofdft_ctx* c, const MgPlan& P, const T* r, T* z, CgScalars* sc) {
   }
   for (int l = P.lc - 1; l >= 0; --l) {
     s *= 0.25;
+    if (fused(l)) {
+      using D = MgPU<T>;
+      const MgLevel& df = P.d[l];
+      const dim3 gr((df.n1 + D::FX - 1) / D::FX, (df.n2 + D::FY - 1) / D::FY, (df.n3 + D::FZ - 1) / D::FZ);
+      ProfScope ps_(c, OFDFT_K_MG);
+      if (l == 0)
+        CU(launch_k(c, mg_prolong_up_kernel<T, true>, gr, dim3(256), 0, df, P.d[1], (const T*)r, (const T*)zl(1), z,
+                    om, (T)s, sc, red(c)));
+      else
+        CU(launch_k(c, mg_prolong_up_kernel<T, false>, gr, dim3(256), 0, df, P.d[l + 1], (const T*)rl(l),
+                    (const T*)zl(l + 1), zl(l), om, (T)s, sc, red(c)));
+      continue;
+    }
     {
       ProfScope ps_(c, OFDFT_K_MG);
-      CU(launch_k(c, mg_prolong_kernel<T>, dim3(blocks(mg_nodes(P.d[l]))), dim3(256), 0, P.d[l], P.d[l + 1],
+      CU(launch_k(c, mg_prolong_kernel<T>, dim3(rows_blocks(P.d[l])), dim3(256), 0, P.d[l], P.d[l + 1],
                   (const T*)rl(l), (const T*)zl(l + 1), tl(l), (T)s, (const CgScalars*)sc));
     }
     ProfScope ps_(c, OFDFT_K_MG);
@@ -139,10 +190,18 @@ int mg_vcycle(ofdft_ctx* c, const MgPlan& P, const T* r, T* z, CgScalars* sc) {
       CU(launch_k(c, mg_up_kernel<T, true>, dim3(pointwise_blocks(c, mg_nodes(P.d[0]))), dim3(256), 0, P.d[0],
                   (const T*)r, (const T*)t0, z, om, (T)s, sc, red(c)));
     else
-      CU(launch_k(c, mg_up_kernel<T, false>, dim3(blocks(mg_nodes(P.d[l]))), dim3(256), 0, P.d[l], (const T*)rl(l),
+      CU(launch_k(c, mg_up_kernel<T, false>, dim3(rows_blocks(P.d[l])), dim3(256), 0, P.d[l], (const T*)rl(l),
                   (const T*)tl(l), zl(l), om, (T)s, sc, red(c)));
   }
   return OFDFT_OK;
+}
+
+// V-cycle launches per CG iteration.
+inline int mg_launches(const ofdft_ctx* c, const MgPlan& P) {
+  if (!P.ok) return 0;
+  int n = 1;
+  for (int l = 0; l < P.lc; ++l) n += (c->mg_fuse_nodes >= 0 && mg_nodes(P.d[l]) >= c->mg_fuse_nodes) ? 2 : 4;
+  return n;
 }
 
 // Launches one CG iteration (S3): the stencil pass on r with the p/q update and
@@ -153,7 +212,7 @@ template <typename T, typename X>
 int cg_step(ofdft_ctx* c, int R, const GridDev& g, const Weights<double>& Wneg, X* x, T* r, T* pv, T* qv,
             CgScalars* sc, int pb, const MgPlan* mg = nullptr) {
   static_assert(sizeof(X) == sizeof(T), "the iterate has the CG vectors' type");
-  const bool fold = cg_fold<T>(g);
+  const bool fold = cg_fold<T>(c, g);
   const T* dir = r;  // the stencil pass forms p and q from r, or from z = M r (PCG)
   if (mg && mg->ok) {
     T* z = vec<T>(c, V_Z);
@@ -175,7 +234,7 @@ template <typename T>
 int tune_cg_split(ofdft_ctx* c, int R, const GridDev& g, const Weights<double>& Wneg, const T* r, T* x) {
   if (!c->autotune) return OFDFT_OK;
   T *pv = nullptr, *qv = nullptr;  // scratch p and q (separate allocations, aligned like the solver's)
-  const bool fold = cg_fold<T>(g);
+  const bool fold = cg_fold<T>(c, g);
   const long long vec16 = zvec_ok<T>(g, LoadPlain<T>{r}, EpiCgAX<T>{vec<T>(c, V_P0), vec<T>(c, V_AP), x, nullptr});
   const std::vector<long long> tkey = {(long long)sizeof(T), R, g.n1, g.n2, g.n3, vec16, fold ? 1 : 0};
   for (auto& t : c->ztuned)
@@ -289,7 +348,7 @@ int cg_graph(ofdft_ctx* c, int R, const GridDev& g, double h, const Weights<doub
           dir = vec<T>(c, V_Z);
         }
         cudaEventRecordWithFlags(c->gev[sample_set][0], c->stream, cudaEventRecordExternal);
-        const bool fold = cg_fold<T>(g);
+        const bool fold = cg_fold<T>(c, g);
         if (rc == OFDFT_OK) rc = cg_stencil<T>(c, R, g, Wneg, reinterpret_cast<T*>(x), dir, pv, qv, sc, fold);
         cudaEventRecordWithFlags(c->gev[sample_set][1], c->stream, cudaEventRecordExternal);
         if (rc == OFDFT_OK) rc = cg_update<T>(c, g, reinterpret_cast<T*>(x), r, pv, qv, sc, pb, fold);
@@ -312,6 +371,88 @@ int cg_graph(ofdft_ctx* c, int R, const GridDev& g, double h, const Weights<doub
   return OFDFT_OK;
 }
 
+// The whole CG loop of a solve as one CUDA graph: a WHILE node whose body is
+// one iteration (V-cycle, stencil pass, update) followed by cg_cond_kernel, so
+// the device iterates until the solve's own `done` flag rises, with no host
+// polling and no launches past convergence.  A kernel ahead of the node sets
+// the condition from `done` at entry.  Captured once per buffer set (the
+// launches bake in pointers, sizes and weights).
+template <typename T, typename X>
+int cg_while_graph(ofdft_ctx* c, int R, const GridDev& g, double h, const Weights<double>& Wneg, X* x, T* r, T* pv,
+                   T* qv, CgScalars* sc, int pb, cudaGraphExec_t* out, const MgPlan* mg) {
+  const bool pcg = mg && mg->ok;
+  const std::vector<long long> key = {-1, (long long)sizeof(T), (long long)sizeof(X), R, g.n1, g.n2, g.n3,
+                                      (long long)x, (long long)r, (long long)pv, (long long)qv, (long long)sc, pb,
+                                      (long long)c->partials.p, (long long)(h * 1e12), pcg ? 1 : 0,
+                                      pcg ? (long long)c->mgbuf.p : 0, pcg ? (long long)c->v[V_Z].p : 0,
+                                      pcg ? (long long)c->v[V_T].p : 0};
+  for (auto& e : c->graphs)
+    if (e.key == key) {
+      *out = e.exec;
+      return OFDFT_OK;
+    }
+  cudaGraph_t graph = nullptr;
+  CU(cudaGraphCreate(&graph, 0));
+  cudaGraphConditionalHandle handle;
+  int rc = OFDFT_OK;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&handle, graph, 0, cudaGraphCondAssignDefault);
+  cudaGraphNode_t init = nullptr, loop = nullptr;
+  if (e == cudaSuccess) {
+    cudaKernelNodeParams kp = {};
+    const CgScalars* csc = sc;
+    void* args[] = {&handle, &csc};
+    kp.func = (void*)cg_cond_kernel;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(1);
+    kp.kernelParams = args;
+    e = cudaGraphAddKernelNode(&init, graph, nullptr, 0, &kp);
+  }
+  cudaGraphNodeParams cp = {};
+  if (e == cudaSuccess) {
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = handle;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    e = cudaGraphAddNode(&loop, graph, &init, nullptr, 1, &cp);
+  }
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return fail(c, OFDFT_ECUDA, "CG loop graph: %s", cudaGetErrorString(e));
+  }
+  // the body: one iteration and the condition update, captured on the private stream
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  const int prof = c->prof;
+  c->prof = 0;
+  const long long launches = c->launches;
+  long long kinds[OFDFT_K_COUNT];
+  memcpy(kinds, c->kind_launches, sizeof(kinds));
+  cudaStream_t user = c->stream;
+  c->stream = c->gstream;
+  e = cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    rc = cg_step<T, X>(c, R, g, Wneg, x, r, pv, qv, sc, pb, mg);
+    if (rc == OFDFT_OK) {
+      cg_cond_kernel<<<1, 1, 0, c->stream>>>(handle, sc);
+      if (cudaGetLastError() != cudaSuccess) rc = fail(c, OFDFT_ECUDA, "CG loop graph: condition launch failed");
+    }
+    cudaGraph_t got = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(c->stream, &got);
+    if (rc == OFDFT_OK && ee != cudaSuccess) e = ee;
+  }
+  c->stream = user;
+  c->prof = prof;
+  c->launches = launches;
+  memcpy(c->kind_launches, kinds, sizeof(kinds));
+  cudaGraphExec_t exec = nullptr;
+  if (rc == OFDFT_OK && e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (rc != OFDFT_OK) return rc;
+  if (e != cudaSuccess) return fail(c, OFDFT_ECUDA, "CG loop graph: %s", cudaGetErrorString(e));
+  c->graphs.push_back({key, exec});
+  *out = exec;
+  return OFDFT_OK;
+}
+
 // Persistent CG: one cooperative launch of cg_coop_kernel runs up to kChunk
 // iterations (both halves of each, with grid-wide sums between them), so an
 // iteration costs no launch gaps and no separate update kernel.  Needs 16-byte
@@ -325,11 +466,18 @@ int cg_coop_r(ofdft_ctx* c, const GridDev& g, const Weights<double>& Wneg, T* x,
   *used = false;
   // grids whose CG vectors overflow L2 run faster as two kernels with the
   // folded iterate update (at 256^3: 160 against 250 us per iteration)
-  if (cg_fold<T>(g)) return OFDFT_OK;
+  if (cg_fold<T>(c, g)) return OFDFT_OK;
   if (!zvec_ok<T>(g, LoadPlain<T>{r}, EpiCgAv<T>{pv, qv, 0, T(0)})) return OFDFT_OK;
   auto* kern = cg_coop_kernel<T, R, VW>;
   constexpr int smem = zsmem_bytes<T, R, VW, EpiCgAv<T>>();
-  static int per_sm = -1;  // co-resident blocks per SM of this instantiation (-1: not yet queried)
+  // co-resident blocks per SM of this instantiation, per device (the shared-memory
+  // attribute is a per-device setting; -1: not yet queried on that device)
+  static int per_sm_dev[64] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1,
+                               -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1,
+                               -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1,
+                               -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
+  if (c->device < 0 || c->device >= 64) return OFDFT_OK;
+  int& per_sm = per_sm_dev[c->device];
   if (per_sm < 0) {
     CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int nb = 0;
@@ -424,6 +572,25 @@ int cg_iterate(ofdft_ctx* c, int R, const GridDev& g, double h, const Weights<do
   TRY(tune_cg_split<T>(c, R, g, Wneg, r, reinterpret_cast<T*>(x)));
   const bool full_timed = (c->prof & (1 << OFDFT_K_CG_UPDATE)) != 0;
   const bool sampled = !full_timed && (c->prof & (1 << OFDFT_K_CG_DIR_STENCIL)) != 0;
+  const int nmg = mg_launches(c, mg);  // V-cycle launches per iteration
+  if (c->use_graphs && c->cond_graphs && !full_timed && !sampled && max_it > 0) {
+    // the whole loop on the device: one eager iteration (it also sets every kernel
+    // attribute outside the capture), then the WHILE graph for the rest
+    const int it0 = host_sc->iters;
+    TRY((cg_step<T, X>(c, R, g, Wneg, x, r, pv, qv, sc, pb, &mg)));
+    cudaGraphExec_t wexec = nullptr;
+    TRY((cg_while_graph<T, X>(c, R, g, h, Wneg, x, r, pv, qv, sc, pb, &wexec, &mg)));
+    CU(cudaGraphLaunch(wexec, c->stream));
+    if (cg_fold<T>(c, g)) TRY(cg_flush<T>(c, g, reinterpret_cast<T*>(x), pv, sc));
+    TRY(sync_scalars(c, sc, sizeof(CgScalars), host_sc));
+    const long long its = std::max(0, host_sc->iters - it0 - 1);  // iterations the graph ran
+    c->launches += (2 + nmg + 1) * its + 1;
+    c->kind_launches[OFDFT_K_CG_DIR_STENCIL] += its;
+    c->kind_launches[OFDFT_K_CG_UPDATE] += its;
+    c->kind_launches[OFDFT_K_MG] += nmg * its;
+    c->kind_launches[OFDFT_K_VECTOR] += its + 1;
+    return OFDFT_OK;
+  }
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
   if (c->use_graphs && !full_timed && max_it >= kChunk) {
     TRY((cg_graph<T, X>(c, R, g, h, Wneg, x, r, pv, qv, sc, pb, sampled ? 0 : -1, &exec[0], &mg)));
@@ -446,7 +613,6 @@ int cg_iterate(ofdft_ctx* c, int R, const GridDev& g, double h, const Weights<do
       CU(cudaGraphLaunch(exec[slot], c->stream));
       pending[slot] = sampled;
       launched += kChunk;
-      const int nmg = mg.ok ? 4 * mg.lc + 1 : 0;  // V-cycle launches per iteration
       c->launches += (2 + nmg) * kChunk;
       c->kind_launches[OFDFT_K_CG_DIR_STENCIL] += kChunk;
       c->kind_launches[OFDFT_K_CG_UPDATE] += kChunk;
@@ -464,7 +630,7 @@ int cg_iterate(ofdft_ctx* c, int R, const GridDev& g, double h, const Weights<do
     }
     ++chunks;
   }
-  if (cg_fold<T>(g)) TRY(cg_flush<T>(c, g, reinterpret_cast<T*>(x), pv, sc));
+  if (cg_fold<T>(c, g)) TRY(cg_flush<T>(c, g, reinterpret_cast<T*>(x), pv, sc));
   TRY(sync_scalars(c, sc, sizeof(CgScalars), host_sc));
   read_sample(0);
   read_sample(1);
@@ -533,19 +699,37 @@ int poisson_mixed(ofdft_ctx* c, int R, const GridDev& g, double h, const float* 
   CgScalars hs, hs32;
   const int max_rounds = 60;
   CU(cudaMemsetAsync(e32, 0, g.G * sizeof(float), c->stream));
+  // float-float residual pass: the potential and the pseudocharge as float-float
+  // pairs (phi2, b2), split once here and phi2 kept in step by every fold; the
+  // residual itself is written as pairs (r2, in the r64 buffer)
+  float2 *phi2 = nullptr, *b2 = nullptr;
+  float2* r2 = reinterpret_cast<float2*>(r64);
+  c->mixed_ff = c->ff_residual != 0;
+  if (c->mixed_ff) {
+    TRY(ensure(c, c->v[V_PHI2], g.G * sizeof(float2)));
+    phi2 = vec<float2>(c, V_PHI2);
+    if (!rho32) {
+      TRY(ensure(c, c->v[V_B2], g.G * sizeof(float2)));
+      b2 = vec<float2>(c, V_B2);
+    }
+    ProfScope ps_(c, OFDFT_K_VECTOR);
+    ff_split_kernel<<<pb, 256, 0, c->stream>>>(g.G, phi2, phi64, b2, b64);
+  }
+  const float2 fourpi = ff_of(4.0 * kPi);
   for (int round = 0; round <= max_rounds; ++round) {
     if (round > 0) {
       ProfScope ps_(c, OFDFT_K_VECTOR);
-      fold_kernel<<<pb, 256, 0, c->stream>>>(g.G, phi64, e32);
+      fold_kernel<<<pb, 256, 0, c->stream>>>(g.G, phi64, e32, phi2);
     }
-    if (rho32)
-      TRY(launch_z_r<double>(c, R, g, W, LoadPlain<double>{phi64},
-                             EpiResidual<double, float, double>{rho32, nullptr, nullptr, r64, c->sc, tol, max_it, 1},
-                             OFDFT_K_RESIDUAL));
-    else
-      TRY(launch_z_r<double>(c, R, g, W, LoadPlain<double>{phi64},
-                             EpiResidual<double, float, double>{nullptr, u, b64, r64, c->sc, tol, max_it, 1},
-                             OFDFT_K_RESIDUAL));
+    if (c->mixed_ff) {
+      const EpiResidualFF ep{rho32, rho32 ? nullptr : u, b2, r2, c->sc, tol, max_it, 0, fourpi};
+      TRY(launch_z_r<float2>(c, R, g, W, LoadPlain<float2>{phi2}, ep, OFDFT_K_RESIDUAL));
+    } else {
+      const EpiResidual<double, float, double> ep =
+          rho32 ? EpiResidual<double, float, double>{rho32, nullptr, nullptr, r64, c->sc, tol, max_it, 1}
+                : EpiResidual<double, float, double>{nullptr, u, b64, r64, c->sc, tol, max_it, 1};
+      TRY(launch_z_r<double>(c, R, g, W, LoadPlain<double>{phi64}, ep, OFDFT_K_RESIDUAL));
+    }
     TRY(sync_scalars(c, c->sc, sizeof(CgScalars), &hs));
     const double bb = hs.bb > 0 ? hs.bb : 1.0;
     if (st) {
@@ -566,9 +750,14 @@ int poisson_mixed(ofdft_ctx* c, int R, const GridDev& g, double h, const float* 
       // later rounds keep the search direction (plain CG); preconditioned CG
       // restarts from p = z: the replaced residual is not orthogonal to the old
       // directions, and keeping them let the FP32 PCG diverge on some states
-      refine_replace_kernel<<<pb, 256, 0, c->stream>>>(g.G, r32, r64, c->sc32, mixed_inner_tol(hs.rr, bb, tol),
-                                                       budget, (round == 0 || mg.ok) ? 1 : 0, mg.ok ? 1 : 0,
-                                                       red(c));
+      if (c->mixed_ff)
+        refine_replace_kernel<float2><<<pb, 256, 0, c->stream>>>(g.G, r32, r2, c->sc32,
+                                                                 mixed_inner_tol(hs.rr, bb, tol), budget,
+                                                                 (round == 0 || mg.ok) ? 1 : 0, mg.ok ? 1 : 0, red(c));
+      else
+        refine_replace_kernel<double><<<pb, 256, 0, c->stream>>>(g.G, r32, r64, c->sc32,
+                                                                 mixed_inner_tol(hs.rr, bb, tol), budget,
+                                                                 (round == 0 || mg.ok) ? 1 : 0, mg.ok ? 1 : 0, red(c));
     }
     CU(cudaGetLastError());
     TRY(sync_scalars(c, c->sc32, sizeof(CgScalars), &hs32));
@@ -596,7 +785,7 @@ int functional_pass(ofdft_ctx* c, int R, const GridDev& g, double h, const ofdft
                     const T* b, const T* phi, const T* rcg, double eta, double mu, double N,
                     const double* sum_uu_dev, T* G, T* s, const T* d, const T* s_old, EvalOut* out,
                     T* winv = nullptr, const double* phi64 = nullptr, const double* b64 = nullptr,
-                    const double* r64 = nullptr) {
+                    const double* r64 = nullptr, const CgScalars* es_sums = nullptr) {
   const Weights<double> W = lap_weights(R, h, 1.0);
   FuncScalars f;
   f.h3 = h * h * h;
@@ -609,7 +798,9 @@ int functional_pass(ofdft_ctx* c, int R, const GridDev& g, double h, const ofdft
   f.terms = p->terms;
   const bool es = p->terms & OFDFT_TERM_ES;
   EpiFunctional<T> ep{es ? phi : nullptr, b, es ? rcg : nullptr, d, s_old, G, s, winv, sum_uu_dev, f, c->scal};
-  if (es && phi64) {
+  if (es && es_sums) {
+    ep.es_sums = es_sums;
+  } else if (es && phi64) {
     ep.phi64 = phi64;
     ep.b64 = b64;
     ep.r64 = r64;
@@ -625,7 +816,9 @@ int functional_pass(ofdft_ctx* c, int R, const GridDev& g, double h, const ofdft
     if (rc_ != OFDFT_OK) return rc_; \
   } while (0)
 
-// Brent's minimiser (1973): parabolic steps through the three best points,
+// Brent's minimiser (R. P. Brent, "Algorithms for Minimization without
+// Derivatives", Prentice-Hall 1973, ch. 5, the published procedure restated
+// here): parabolic steps through the three best points,
 // golden-section steps when a parabola is not trusted, on a bracket a < x < b
 // (or b < x < a) with f(x) below both ends.  f(t, &value) returns a status;
 // rel_tol bounds the final bracket relative to |x|.  Returns the status and
@@ -753,7 +946,8 @@ struct Solver {
     EvalOut o;
     T* winv = (p->precond_rank1 && sout) ? vec<T>(c, V_W) : nullptr;
     TRY(functional_pass<T>(c, R, g, h, p, at, b, phi, rcg, eta, mu, N, sum_uu, Gout, sout, dd, s_old, &o, winv,
-                           mixed ? phi64 : nullptr, mixed ? b64 : nullptr, mixed ? vec<double>(c, V_R64) : nullptr));
+                           mixed ? phi64 : nullptr, mixed ? b64 : nullptr, mixed ? vec<double>(c, V_R64) : nullptr,
+                           (mixed && c->mixed_ff) ? c->sc : nullptr));
     stats->stencil_apps += 2;
     stats->grad_evals += 1;
     fill_energy(o, h, p, E_self, ezz, eta, mu, out);
@@ -1092,15 +1286,70 @@ int check_atoms(ofdft_ctx* c, const double* R, const double* Z, int M) {
   return OFDFT_OK;
 }
 
+// Per-atom tables (S1, S9): box of lattice nodes whose centre can lie within r_c
+// of the atom, plus one node of slack; b_J is tabulated on the box grown by R
+// (bdim) and V_J on the box grown by 2R (vdim).
+struct AtomTables {
+  int rb, box, bdim, vdim, batch;
+  long long vper, bper;
+};
+
+inline AtomTables atom_tables(double rc, double h, int R, int M, size_t budget) {
+  AtomTables t;
+  t.rb = (int)ceil(rc / h) + 1;
+  t.box = 2 * t.rb + 1;
+  t.bdim = t.box + 2 * R;
+  t.vdim = t.box + 4 * R;
+  t.vper = (long long)t.vdim * t.vdim * t.vdim;
+  t.bper = (long long)t.bdim * t.bdim * t.bdim;
+  t.batch = (int)std::max<long long>(1, std::min<long long>(M, (long long)budget / ((t.vper + t.bper) * 8)));
+  return t;
+}
+
+inline void atom_box_lo(const double* R_host, int a0, int na, const ofdft_grid* gr, int rb, std::vector<int>& lo) {
+  for (int a = 0; a < na; ++a)
+    for (int d = 0; d < 3; ++d)
+      lo[3 * a + d] = (int)floor((R_host[3 * (a0 + a) + d] - gr->origin[d]) / gr->h - 0.5) - rb + 1;
+}
+
 template <typename T, int R>
-int launch_pseudocharge(ofdft_ctx* c, const GridDev& g, const AtomArgs& A, const Weights<double>& W, T* b) {
-  dim3 grid((g.n1 + AT - 1) / AT, (g.n2 + AT - 1) / AT, (g.n3 + AT - 1) / AT);
+int launch_force_boxes(ofdft_ctx* c, const AtomArgs& A, int a0, int na, int vdim, int bdim, const int* lo,
+                       const Weights<double>& W, double* vbox, double* bbox);
+
+// b = sum_J b_J and E_self (Sec. 4): the atoms' V_J and b_J tables are built for
+// ranges of at most 512 atoms, then every node gathers the b_J of the atoms whose
+// box holds it, in atom order (FP64 running sums across ranges).
+template <typename T, int R>
+int pseudocharge_tables(ofdft_ctx* c, const ofdft_grid* gr, const GridDev& g, const AtomArgs& A,
+                        const double* R_host, int M, T* b, double* es_dev) {
+  const Weights<double> W = lap_weights(R, gr->h, 1.0);
+  AtomTables t = atom_tables(A.rc, gr->h, R, M, (size_t)768 << 20);
+  t.batch = std::min(t.batch, 512);
+  TRY(ensure(c, c->v[V_ATOM1], (size_t)t.batch * (t.vper + t.bper) * sizeof(double)));
+  TRY(ensure(c, c->v[V_ATOM2], (size_t)t.batch * 3 * sizeof(int) + 64));
+  const bool multi = M > t.batch;
+  if (multi) TRY(ensure(c, c->v[V_BACC], g.G * sizeof(double)));
+  double* vbox = vec<double>(c, V_ATOM1);
+  double* bbox = vbox + (size_t)t.batch * t.vper;
+  int* lo_dev = vec<int>(c, V_ATOM2);
+  double* bacc = multi ? vec<double>(c, V_BACC) : nullptr;
+  std::vector<int> lo((size_t)3 * t.batch);
+  const dim3 grid((g.n1 + AT - 1) / AT, (g.n2 + AT - 1) / AT, (g.n3 + AT - 1) / AT);
   TRY(ensure_partials(c, (long long)grid.x * grid.y * grid.z, 1));
-  {
-    ProfScope ps_(c, OFDFT_K_ATOMS);
-    pseudocharge_kernel<T, R><<<grid, dim3(AT, AT, AT), 0, c->stream>>>(g, A, W, b, c->scal + 20, red(c));
+  CU(cudaMemsetAsync(es_dev, 0, sizeof(double), c->stream));
+  for (int a0 = 0; a0 < M; a0 += t.batch) {
+    const int na = std::min(t.batch, M - a0);
+    atom_box_lo(R_host, a0, na, gr, t.rb, lo);
+    CU(cudaMemcpyAsync(lo_dev, lo.data(), 3 * na * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    TRY((launch_force_boxes<T, R>(c, A, a0, na, t.vdim, t.bdim, lo_dev, W, vbox, bbox)));
+    {
+      ProfScope ps_(c, OFDFT_K_ATOMS);
+      pseudocharge_gather_kernel<T><<<grid, dim3(AT, AT, AT), 0, c->stream>>>(
+          g, A, a0, na, t.box, t.bdim, t.vdim, R, lo_dev, vbox, bbox, bacc, a0 == 0 ? 1 : 0,
+          a0 + na >= M ? 1 : 0, b, es_dev, red(c));
+    }
+    CU(cudaGetLastError());
   }
-  CU(cudaGetLastError());
   return OFDFT_OK;
 }
 
@@ -1110,18 +1359,18 @@ int device_pseudocharge(ofdft_ctx* c, const ofdft_grid* gr, int R, const double*
   AtomArgs A;
   TRY(upload_atoms(c, R_host, Z_host, M, &A, gr, sigma, rc));
   const GridDev g = gdev(gr);
-  const Weights<double> W = lap_weights(R, gr->h, 1.0);
+  double* es_dev = c->scal + 20;
   switch (R) {
-    case 1: TRY((launch_pseudocharge<T, 1>(c, g, A, W, b))); break;
-    case 2: TRY((launch_pseudocharge<T, 2>(c, g, A, W, b))); break;
-    case 3: TRY((launch_pseudocharge<T, 3>(c, g, A, W, b))); break;
-    case 4: TRY((launch_pseudocharge<T, 4>(c, g, A, W, b))); break;
-    case 5: TRY((launch_pseudocharge<T, 5>(c, g, A, W, b))); break;
-    case 6: TRY((launch_pseudocharge<T, 6>(c, g, A, W, b))); break;
+    case 1: TRY((pseudocharge_tables<T, 1>(c, gr, g, A, R_host, M, b, es_dev))); break;
+    case 2: TRY((pseudocharge_tables<T, 2>(c, gr, g, A, R_host, M, b, es_dev))); break;
+    case 3: TRY((pseudocharge_tables<T, 3>(c, gr, g, A, R_host, M, b, es_dev))); break;
+    case 4: TRY((pseudocharge_tables<T, 4>(c, gr, g, A, R_host, M, b, es_dev))); break;
+    case 5: TRY((pseudocharge_tables<T, 5>(c, gr, g, A, R_host, M, b, es_dev))); break;
+    case 6: TRY((pseudocharge_tables<T, 6>(c, gr, g, A, R_host, M, b, es_dev))); break;
     default: return fail(c, OFDFT_EINVAL, "stencil radius %d", R);
   }
   double es;
-  TRY(sync_scalars(c, c->scal + 20, sizeof(double), &es));
+  TRY(sync_scalars(c, es_dev, sizeof(double), &es));
   *E_self = 0.5 * gr->h * gr->h * gr->h * es;
   return OFDFT_OK;
 }
@@ -1276,13 +1525,19 @@ int finish_solve(ofdft_ctx* c, Solver<T>& S, const ofdft_grid* gr, int R, const 
   st->grid = *gr;
   *energy = S.e.E;
   if (forces) {
-    TRY(device_forces<T>(c, gr, R, R_host, Z_host, M, p->sigma, p->rc, p->force_variant, S.phi, forces));
+    // MIXED: the forces take the FP64 potential of the last Poisson solve's
+    // residual correction (phi in the field type is its float rounding)
+    if (S.phi64)
+      TRY(device_forces<double>(c, gr, R, R_host, Z_host, M, p->sigma, p->rc, p->force_variant, S.phi64, forces));
+    else
+      TRY(device_forces<T>(c, gr, R, R_host, Z_host, M, p->sigma, p->rc, p->force_variant, S.phi, forces));
     if (p->ezz_correction)
       for (int i = 0; i < 3 * M; ++i) forces[i] += Fz[i];
   }
   if (u_out) CU(cudaMemcpyAsync(u_out, S.u, S.g.G * es, cudaMemcpyDeviceToDevice, c->stream));
   if (phi_out) CU(cudaMemcpyAsync(phi_out, S.phi, S.g.G * es, cudaMemcpyDeviceToDevice, c->stream));
   CU(cudaStreamSynchronize(c->stream));
+  TRY(zstream_fault_check(c));
   return converged ? OFDFT_OK : fail(c, OFDFT_ENOTCONV, "%s", notconv);
 }
 
@@ -1530,6 +1785,16 @@ int ofdft_create(ofdft_ctx** out, int device, void* stream) {
   if (ms && atoi(ms) >= 1) c->mg_sweeps = atoi(ms);
   const char* cz = getenv("OFDFT_COOP_NZ");  // launch-shape experiments: z-chunks of the persistent CG grid
   c->coop_nz = cz ? atoi(cz) : 0;
+  const char* tma = getenv("OFDFT_TMA");  // 1: TMA staging in the FP32 z-streaming passes that allow it
+  c->tma = (tma && tma[0] == '1') ? 1 : 0;
+  const char* cgr = getenv("OFDFT_COND_GRAPHS");  // 0: CG chunks of eight iterations polled by the host
+  c->cond_graphs = !(cgr && cgr[0] == '0');
+  const char* ffr = getenv("OFDFT_FF_RESIDUAL");  // 0: FP64 stencil in the mixed residual pass
+  c->ff_residual = !(ffr && ffr[0] == '0');
+  const char* mf = getenv("OFDFT_MG_FUSE_NODES");  // levels of at least this many nodes take the fused passes
+  if (mf) c->mg_fuse_nodes = atoll(mf);          // (-1: none)
+  const char* fb = getenv("OFDFT_CG_FOLD_BYTES");  // CG working set above which the iterate update is folded
+  if (fb && atof(fb) >= 0.0) c->cg_fold_bytes = atof(fb);
   const char* pw = getenv("OFDFT_POINTWISE_BLOCKS_PER_SM");  // launch-shape experiments (default 4)
   if (pw && atoi(pw) >= 1 && atoi(pw) <= 16) c->pw_per_sm = atoi(pw);
   cudaMemset(c->sc, 0, 3 * sizeof(CgScalars));
@@ -1645,6 +1910,7 @@ long long ofdft_struct_bytes(const char* name) {
   if (n == "ofdft_solve_stats") return (long long)sizeof(ofdft_solve_stats);
   if (n == "ofdft_counters") return (long long)sizeof(ofdft_counters);
   if (n == "ofdft_relax_stats") return (long long)sizeof(ofdft_relax_stats);
+  if (n == "ofdft_batch_stats") return (long long)sizeof(ofdft_batch_stats);
   return -1;
 }
 
@@ -1737,9 +2003,12 @@ int ofdft_poisson(ofdft_ctx* c, const ofdft_grid* g, int fd_order, int prec, con
   const GridDev gd = gdev(g);
   ofdft_cg_stats tmp;
   if (!st) st = &tmp;
-  if (prec == OFDFT_PREC_FP64)
-    return poisson_fp64(c, fd_order / 2, gd, g->h, (const double*)rho, (const double*)u, (const double*)b,
-                        (double*)phi, tol, max_it, st);
+  if (prec == OFDFT_PREC_FP64) {
+    const int rc = poisson_fp64(c, fd_order / 2, gd, g->h, (const double*)rho, (const double*)u, (const double*)b,
+                                (double*)phi, tol, max_it, st);
+    TRY(zstream_fault_check(c));
+    return rc;
+  }
   // mixed: FP64 copies of b and phi live in the context for the call
   TRY(ensure(c, c->v[V_PHI64], gd.G * sizeof(double)));
   TRY(ensure(c, c->v[V_B64], gd.G * sizeof(double)));
@@ -1755,8 +2024,10 @@ int ofdft_poisson(ofdft_ctx* c, const ofdft_grid* g, int fd_order, int prec, con
   CU(cudaGetLastError());
   ofdft_params dp;
   ofdft_default_params(&dp);
-  return poisson_mixed(c, fd_order / 2, gd, g->h, (const float*)rho, (const float*)u, vec<double>(c, V_B64),
-                       vec<double>(c, V_PHI64), (float*)phi, tol, max_it, dp.refine_every, st);
+  const int rc = poisson_mixed(c, fd_order / 2, gd, g->h, (const float*)rho, (const float*)u, vec<double>(c, V_B64),
+                               vec<double>(c, V_PHI64), (float*)phi, tol, max_it, dp.refine_every, st);
+  TRY(zstream_fault_check(c));
+  return rc;
 }
 
 int ofdft_energy_grad(ofdft_ctx* c, const ofdft_grid* g, const ofdft_params* p, const void* u, const void* b,
@@ -1830,7 +2101,8 @@ int ofdft_energy_grad(ofdft_ctx* c, const ofdft_grid* g, const ofdft_params* p, 
     TRY(functional_pass<float>(c, R, gd, g->h, p, (const float*)u, (const float*)b, (const float*)phi, nullptr, eta,
                                mu, N, sum_uu, (float*)grad, (float*)s, (const float*)d, (const float*)s_old, &o,
                                r1 ? vec<float>(c, V_W) : nullptr, es ? vec<double>(c, V_PHI64) : nullptr,
-                               es ? vec<double>(c, V_B64) : nullptr, es ? vec<double>(c, V_R64) : nullptr));
+                               es ? vec<double>(c, V_B64) : nullptr, es ? vec<double>(c, V_R64) : nullptr,
+                               (es && c->mixed_ff) ? c->sc : nullptr));
   fill_energy(o, g->h, p, E_self, 0.0, eta, mu, out);
   if (r1) {
     // the preconditioned residual includes the exact inverse of the rank-one term (4 h^3/mu) u u^T
@@ -1848,6 +2120,7 @@ int ofdft_energy_grad(ofdft_ctx* c, const ofdft_grid* g, const ofdft_params* p, 
     out->rs_pc -= h3 * gamma * o.sums[10];
   }
   out->poisson = cs;
+  TRY(zstream_fault_check(c));
   if (!isfinite(out->L)) return fail(c, OFDFT_ENONFINITE, "augmented Lagrangian is not finite");
   return OFDFT_OK;
 }

@@ -129,6 +129,27 @@ struct ofdft_batch {
   DevArena d_tiles, d_desc, d_segs, d_ops;
   std::vector<int> free_index;
   long long rounds = 0;
+  // CUDA graphs of the batched CG loop: a device-side WHILE loop over one CG
+  // iteration of every solve in the loop, keyed by the solves' buffers and the
+  // launch shape; the work lists the captured launches read live in the graph's
+  // own device arena
+  struct LoopGraph {
+    std::vector<long long> key;
+    cudaGraphExec_t exec = nullptr;
+    void* arena = nullptr;
+  };
+  std::vector<LoopGraph> graphs;
+  long long graph_captures = 0, graph_replays = 0, graph_iters = 0, eager_iters = 0;
+  int* one_pinned = nullptr;        // host-pinned 1: marks a slot's CG done without a host wait
+  bool capturing = false;           // work-list uploads go to the capture arena
+  std::vector<char> cap_host;       // staged contents of the capture arena
+  char* cap_dev = nullptr;          // the capture arena (device)
+  size_t cap_bytes = 0;
+  // autotuned launch shape of the batched z-streaming passes: planes per CTA
+  int zdepth = 16;
+  int ztuned = 0;
+  std::vector<std::vector<long long>> tuned_sets;  // grid sets the depth was tuned on
+  std::vector<std::pair<int, float>> tune_log;     // (depth, us) of the last tuning
   // type-erased slot lists (only the engine of the batch precision is used)
   std::vector<std::unique_ptr<Slot<double>>> s64_active, s64_done;
   std::vector<std::unique_ptr<Slot<float>>> s32_active, s32_done;
@@ -214,10 +235,9 @@ int carve(ofdft_ctx* c, Slot<T>* S, int prec) {
 }
 
 // Tiles of one grid for the z-streaming batch launch (BX x rows columns, z chunks
-// of 16 planes).
-void grid_tiles(const GridDev& g, int slot, int rows, std::vector<ZTile>& out, int* count) {
+// of zc planes).
+void grid_tiles(const GridDev& g, int slot, int rows, int zc, std::vector<ZTile>& out, int* count) {
   const int gx = (g.n1 + BX - 1) / BX, gy = (g.n2 + rows - 1) / rows;
-  const int zc = 16;
   int bid = 0;
   for (int z0 = 0; z0 < g.n3; z0 += zc)
     for (int by = 0; by < gy; ++by)
@@ -250,13 +270,33 @@ struct Engine {
 
   RedBuf slot_red(Slot<T>* S) { return RedBuf{S->partials, S->counter}; }
 
+  // A work list for the next launch: copied into arena `a` (ordinary launches),
+  // or staged into the capture arena while a graph is being captured (the copy
+  // to the device happens once, after the capture).  *dptr: its device address.
+  template <typename V>
+  int put(DevArena& a, const std::vector<V>& v, const void** dptr) {
+    if (B->capturing) {
+      const size_t off = (B->cap_host.size() + 255) & ~(size_t)255;
+      const size_t bytes = v.size() * sizeof(V);
+      if (off + bytes > B->cap_bytes) return fail(c, OFDFT_ENOMEM, "batched CG graph: work lists exceed the arena");
+      B->cap_host.resize(off + bytes);
+      if (bytes) memcpy(B->cap_host.data() + off, v.data(), bytes);
+      *dptr = B->cap_dev + off;
+      return OFDFT_OK;
+    }
+    TRY(upload(c, a, v));
+    *dptr = a.p;
+    return OFDFT_OK;
+  }
+
   template <typename TT, int R, int V, class L, class E>
   int launch_zb(int kind, unsigned nb, const ZTile* dt, const ZSlot<TT, L, E>* ds) {
     constexpr int smem = zsmem_bytes<TT, R, V, E>();
-    static bool attr = false;
-    if (!attr) {
+    static bool attr_dev[64] = {false};  // a per-device setting
+    if (c->device < 0 || c->device >= 64) return fail(c, OFDFT_EINVAL, "device index out of range");
+    if (!attr_dev[c->device]) {
       CU(cudaFuncSetAttribute(zbatch_kernel<TT, R, V, L, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-      attr = true;
+      attr_dev[c->device] = true;
     }
     {
       ProfScope ps_(c, kind);
@@ -283,7 +323,7 @@ struct Engine {
           if ((int)zvec_ok<TT>(S->g, le.first, le.second) != wide) continue;
           int cnt = 0;
           const int si = (int)desc.size();
-          grid_tiles(S->g, si, ZCfg<TT>::TY, tiles, &cnt);
+          grid_tiles(S->g, si, ZCfg<TT>::TY, B->zdepth, tiles, &cnt);
           ZSlot<TT, L, E> z;
           z.g = S->g;
           z.W = cast_weights<TT>(lap_weights(Rr, S->h, wscale));
@@ -294,10 +334,11 @@ struct Engine {
           desc.push_back(z);
         }
         if (tiles.empty()) continue;
-        TRY(upload(c, B->d_tiles, tiles));
-        TRY(upload(c, B->d_desc, desc));
-        const ZTile* dt = (const ZTile*)B->d_tiles.p;
-        const ZSlot<TT, L, E>* ds = (const ZSlot<TT, L, E>*)B->d_desc.p;
+        const void *pt = nullptr, *pd = nullptr;
+        TRY(put(B->d_tiles, tiles, &pt));
+        TRY(put(B->d_desc, desc, &pd));
+        const ZTile* dt = (const ZTile*)pt;
+        const ZSlot<TT, L, E>* ds = (const ZSlot<TT, L, E>*)pd;
         const unsigned nb = (unsigned)tiles.size();
         constexpr int VW = 16 / (int)sizeof(TT);
         switch (Rr * 2 + wide) {
@@ -330,12 +371,12 @@ struct Engine {
       ops.push_back(make(S, cnt));
     }
     if (segs.empty()) return OFDFT_OK;
-    TRY(upload(c, B->d_segs, segs));
-    TRY(upload(c, B->d_ops, ops));
+    const void *ps = nullptr, *po = nullptr;
+    TRY(put(B->d_segs, segs, &ps));
+    TRY(put(B->d_ops, ops, &po));
     {
       ProfScope ps_(c, kind);
-      pbatch_kernel<Op><<<(unsigned)segs.size(), 256, 0, c->stream>>>((const PSeg*)B->d_segs.p,
-                                                                     (const Op*)B->d_ops.p);
+      pbatch_kernel<Op><<<(unsigned)segs.size(), 256, 0, c->stream>>>((const PSeg*)ps, (const Op*)po);
     }
     CU(cudaGetLastError());
     return OFDFT_OK;
@@ -353,12 +394,12 @@ struct Engine {
       ops.push_back(make(S, cnt));
     }
     if (segs.empty()) return OFDFT_OK;
-    TRY(upload(c, B->d_segs, segs));
-    TRY(upload(c, B->d_ops, ops));
+    const void *ps = nullptr, *po = nullptr;
+    TRY(put(B->d_segs, segs, &ps));
+    TRY(put(B->d_ops, ops, &po));
     {
       ProfScope ps_(c, kind);
-      pbatch_kernel<Op><<<(unsigned)segs.size(), 256, 0, c->stream>>>((const PSeg*)B->d_segs.p,
-                                                                     (const Op*)B->d_ops.p);
+      pbatch_kernel<Op><<<(unsigned)segs.size(), 256, 0, c->stream>>>((const PSeg*)ps, (const Op*)po);
     }
     CU(cudaGetLastError());
     return OFDFT_OK;
@@ -409,22 +450,24 @@ struct Engine {
           smem = std::max(smem, S->mg.smem);
         }
       if (jobs.empty()) continue;
-      TRY(upload(c, B->d_ops, jobs));
+      const void* pj = nullptr;
+      TRY(put(B->d_ops, jobs, &pj));
       ProfScope ps_(c, OFDFT_K_MG);
-      static bool attr = false;  // per element type
-      if (!attr) {
+      static bool attr_dev[64] = {false};  // per element type and device
+      if (c->device < 0 || c->device >= 64) return fail(c, OFDFT_EINVAL, "device index out of range");
+      if (!attr_dev[c->device]) {
         CU(cudaFuncSetAttribute(mg_coarse_batch_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 200 * 1024));
         CU(cudaFuncSetAttribute(mg_coarse_batch_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 200 * 1024));
-        attr = true;
+        attr_dev[c->device] = true;
       }
       if (dot) {
         mg_coarse_batch_kernel<T, true><<<(unsigned)jobs.size(), 1024, smem, c->stream>>>(
-            (const MgCoarseJob<T>*)B->d_ops.p, om, c->mg_sweeps);
+            (const MgCoarseJob<T>*)pj, om, c->mg_sweeps);
       } else {
         mg_coarse_batch_kernel<T, false><<<(unsigned)jobs.size(), 1024, smem, c->stream>>>(
-            (const MgCoarseJob<T>*)B->d_ops.p, om, c->mg_sweeps);
+            (const MgCoarseJob<T>*)pj, om, c->mg_sweeps);
       }
       CU(cudaGetLastError());
     }
@@ -456,40 +499,283 @@ struct Engine {
     return OFDFT_OK;
   }
 
+  // One CG iteration on the given slots (S3): the V-cycle of the preconditioned
+  // slots, the stencil pass and the update; every kernel skips a slot whose CG
+  // is done.
+  template <class GetX, class GetR, class GetSc>
+  int cg_iteration(const std::vector<Slot<T>*>& slots, bool fold, GetX getx, GetR getr, GetSc getsc) {
+    // the stencil pass forms p and q from z = M r (preconditioned slots) or r
+    TRY(mg_cycle(slots, getr, getsc));
+    auto dir = [&](Slot<T>* S) -> const T* { return S->pc ? S->mz : getr(S); };
+    if (fold) {
+      TRY((zpass<T, LoadPlain<T>, EpiCgAX<T>>(slots, OFDFT_K_CG_DIR_STENCIL, -1.0, [&](Slot<T>* S) {
+        return std::make_pair(LoadPlain<T>{dir(S)}, EpiCgAX<T>{S->pv, S->qv, (T*)getx(S), getsc(S)});
+      })));
+      TRY((ppass<OpCgUpdateR<T>>(slots, OFDFT_K_CG_UPDATE, [&](Slot<T>* S, int nb) {
+        return OpCgUpdateR<T>{getr(S), S->qv, getsc(S), slot_red(S), nb};
+      })));
+    } else {
+      TRY((zpass<T, LoadPlain<T>, EpiCgA<T>>(slots, OFDFT_K_CG_DIR_STENCIL, -1.0, [&](Slot<T>* S) {
+        return std::make_pair(LoadPlain<T>{dir(S)}, EpiCgA<T>{S->pv, S->qv, getsc(S)});
+      })));
+      using X = std::remove_pointer_t<decltype(getx(slots[0]))>;
+      TRY((ppass<OpCgUpdate<T, X>>(slots, OFDFT_K_CG_UPDATE, [&](Slot<T>* S, int nb) {
+        return OpCgUpdate<T, X>{getx(S), getr(S), S->pv, S->qv, getsc(S), slot_red(S), nb};
+      })));
+    }
+    return OFDFT_OK;
+  }
+
+  // Autotuner of the batched z-streaming passes (S11): the planes per CTA of
+  // the CG stencil pass, timed on the loop's own grids (their r or z as input)
+  // with scratch p and q and private CG scalars, so no solve's state changes;
+  // tuned once per set of grids and kept for the batch.
+  template <class GetR>
+  int tune_zdepth(const std::vector<Slot<T>*>& slots, GetR getr) {
+    std::vector<long long> gset;
+    long long gmax = 0;
+    for (Slot<T>* S : slots) {
+      gset.push_back(((long long)S->g.n1 << 42) | ((long long)S->g.n2 << 21) | S->g.n3);
+      gmax = std::max(gmax, S->g.G);
+    }
+    std::sort(gset.begin(), gset.end());
+    for (auto& t : B->tuned_sets)
+      if (t == gset) return OFDFT_OK;
+    T* scratch = nullptr;
+    CgScalars* psc = nullptr;
+    CU(cudaMalloc(&scratch, 2 * gmax * sizeof(T)));
+    if (cudaMalloc(&psc, slots.size() * sizeof(CgScalars)) != cudaSuccess) {
+      cudaFree(scratch);
+      return fail(c, OFDFT_ENOMEM, "autotune: no room for scratch scalars");
+    }
+    std::vector<CgScalars> init(slots.size());
+    memset(init.data(), 0, init.size() * sizeof(CgScalars));
+    for (auto& x : init) {
+      x.first = 1;
+      x.max_it = 1 << 30;
+    }
+    std::vector<int> pos(B->capacity + 1, 0);
+    for (size_t i = 0; i < slots.size(); ++i) pos[slots[i]->index] = (int)i;
+    const int prof = c->prof;
+    c->prof = 0;
+    const long long launches = c->launches;
+    long long kinds[OFDFT_K_COUNT];
+    memcpy(kinds, c->kind_launches, sizeof(kinds));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = OFDFT_OK;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+      rc = fail(c, OFDFT_ECUDA, "autotune: event creation failed");
+    const int saved = B->zdepth;
+    int best = saved;
+    float best_ms = 1e30f;
+    B->tune_log.clear();
+    for (int zc : {8, 16, 32, 64}) {
+      if (rc != OFDFT_OK) break;
+      B->zdepth = zc;
+      float ms = 0.0f;
+      for (int rep = 0; rep < 4 && rc == OFDFT_OK; ++rep) {
+        if (cudaMemcpyAsync(psc, init.data(), init.size() * sizeof(CgScalars), cudaMemcpyHostToDevice, c->stream) !=
+                cudaSuccess ||
+            cudaEventRecord(e0, c->stream) != cudaSuccess) {
+          rc = fail(c, OFDFT_ECUDA, "autotune: enqueue failed");
+          break;
+        }
+        rc = zpass<T, LoadPlain<T>, EpiCgA<T>>(slots, OFDFT_K_CG_DIR_STENCIL, -1.0, [&](Slot<T>* S) {
+          return std::make_pair(LoadPlain<T>{S->pc ? S->mz : getr(S)},
+                                EpiCgA<T>{scratch, scratch + gmax, psc + pos[S->index]});
+        });
+        float t = 0.0f;
+        if (rc == OFDFT_OK && (cudaEventRecord(e1, c->stream) != cudaSuccess ||
+                               cudaEventSynchronize(e1) != cudaSuccess ||
+                               cudaEventElapsedTime(&t, e0, e1) != cudaSuccess))
+          rc = fail(c, OFDFT_ECUDA, "autotune: timing failed");
+        if (rep > 0) ms += t;  // the first launch of each depth warms up
+      }
+      if (rc == OFDFT_OK) B->tune_log.push_back({zc, ms / 3.0f * 1000.0f});
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = zc;
+      }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaStreamSynchronize(c->stream);
+    cudaFree(scratch);
+    cudaFree(psc);
+    c->prof = prof;
+    c->launches = launches;  // tuning launches are not the caller's work
+    memcpy(c->kind_launches, kinds, sizeof(kinds));
+    B->zdepth = (rc == OFDFT_OK) ? best : saved;
+    if (rc != OFDFT_OK) return rc;
+    B->tuned_sets.push_back(gset);
+    B->ztuned = 1;
+    return OFDFT_OK;
+  }
+
+  // The CG loop of these slots as one CUDA graph (captured on first use): a
+  // WHILE node over one iteration and batch_cond_kernel, which keeps the loop
+  // going while any of the slots is not done.
+  template <class GetX, class GetR, class GetSc>
+  int loop_graph(const std::vector<Slot<T>*>& slots, bool fold, GetX getx, GetR getr, GetSc getsc,
+                 cudaGraphExec_t* out) {
+    std::vector<long long> key = {(long long)sizeof(T), fold ? 1 : 0, B->zdepth, (long long)getsc(slots[0]),
+                                  (long long)c->partials.p};
+    std::vector<int> idx;
+    for (Slot<T>* S : slots) {
+      key.push_back((long long)S);
+      key.push_back((long long)getx(S));
+      key.push_back((long long)getr(S));
+      key.push_back((long long)getsc(S));
+      key.push_back(S->pc);
+      idx.push_back(S->index);
+    }
+    for (auto& e : B->graphs)
+      if (e.key == key) {
+        *out = e.exec;
+        return OFDFT_OK;
+      }
+    // the graph's own arena for the work lists its launches read
+    const size_t arena = (size_t)16 << 20;
+    void* dev = nullptr;
+    CU(cudaMalloc(&dev, arena));
+    cudaGraph_t graph = nullptr;
+    cudaGraphConditionalHandle handle;
+    cudaGraphNode_t init = nullptr, loop = nullptr;
+    cudaGraphNodeParams cp = {};
+    const CgScalars* base = getsc(slots[0]) - slots[0]->index;
+    int* idx_dev = (int*)dev;  // the slot indices first, then the work lists
+    const int n = (int)idx.size();
+    cudaError_t e = cudaGraphCreate(&graph, 0);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&handle, graph, 0, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) {
+      cudaKernelNodeParams kp = {};
+      const int* cidx = idx_dev;
+      int nn = n;
+      void* args[] = {&handle, &base, &cidx, &nn};
+      kp.func = (void*)batch_cond_kernel;
+      kp.gridDim = dim3(1);
+      kp.blockDim = dim3(256);
+      kp.kernelParams = args;
+      e = cudaGraphAddKernelNode(&init, graph, nullptr, 0, &kp);
+    }
+    if (e == cudaSuccess) {
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = handle;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      e = cudaGraphAddNode(&loop, graph, &init, nullptr, 1, &cp);
+    }
+    if (e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaFree(dev);
+      return fail(c, OFDFT_ECUDA, "batched CG graph: %s", cudaGetErrorString(e));
+    }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    B->cap_host.assign(256, 0);
+    memcpy(B->cap_host.data(), idx.data(), idx.size() * sizeof(int));
+    if (idx.size() * sizeof(int) > 256) {
+      B->cap_host.resize((idx.size() * sizeof(int) + 255) & ~(size_t)255);
+      memcpy(B->cap_host.data(), idx.data(), idx.size() * sizeof(int));
+    }
+    B->cap_dev = (char*)dev;
+    B->cap_bytes = arena;
+    B->capturing = true;
+    const int prof = c->prof;
+    c->prof = 0;
+    const long long launches = c->launches;
+    long long kinds[OFDFT_K_COUNT];
+    memcpy(kinds, c->kind_launches, sizeof(kinds));
+    cudaStream_t user = c->stream;
+    c->stream = c->gstream;
+    int rc = OFDFT_OK;
+    e = cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      rc = cg_iteration(slots, fold, getx, getr, getsc);
+      if (rc == OFDFT_OK) {
+        batch_cond_kernel<<<1, 256, 0, c->stream>>>(handle, base, idx_dev, n);
+        if (cudaGetLastError() != cudaSuccess) rc = fail(c, OFDFT_ECUDA, "batched CG graph: condition launch");
+      }
+      cudaGraph_t got = nullptr;
+      const cudaError_t ee = cudaStreamEndCapture(c->stream, &got);
+      if (rc == OFDFT_OK && ee != cudaSuccess) e = ee;
+    }
+    c->stream = user;
+    c->prof = prof;
+    c->launches = launches;
+    memcpy(c->kind_launches, kinds, sizeof(kinds));
+    B->capturing = false;
+    cudaGraphExec_t exec = nullptr;
+    if (rc == OFDFT_OK && e == cudaSuccess)
+      e = cudaMemcpy(dev, B->cap_host.data(), B->cap_host.size(), cudaMemcpyHostToDevice);
+    if (rc == OFDFT_OK && e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (rc != OFDFT_OK || e != cudaSuccess) {
+      cudaFree(dev);
+      if (rc != OFDFT_OK) return rc;
+      return fail(c, OFDFT_ECUDA, "batched CG graph: %s", cudaGetErrorString(e));
+    }
+    // keep the most recent graphs (a batch's composition changes on admit and retire)
+    if (B->graphs.size() >= 16) {
+      CU(cudaStreamSynchronize(c->stream));
+      cudaGraphExecDestroy(B->graphs.front().exec);
+      cudaFree(B->graphs.front().arena);
+      B->graphs.erase(B->graphs.begin());
+    }
+    B->graphs.push_back({key, exec, dev});
+    B->graph_captures++;
+    *out = exec;
+    return OFDFT_OK;
+  }
+
   // CG iterations on the given slots until each is done (S3), `x` the iterate,
-  // `r` the residual, `scp` the slot's CG scalars.
+  // `r` the residual, `scp` the slot's CG scalars.  With CUDA graphs: one eager
+  // iteration, then the rest in the loop's WHILE graph; otherwise chunks of
+  // eight iterations polled by the host.
+  // `set` is the round's set of evaluating slots (a superset of `slots`): the
+  // graph is captured for the whole set, so it is replayed round after round
+  // while the set stays the same; its slots outside `slots` are marked done
+  // first, and every kernel skips them.
   template <class GetX, class GetR, class GetSc, class HostSc>
-  int cg_loop(std::vector<Slot<T>*> slots, GetX getx, GetR getr, GetSc getsc, HostSc hostsc) {
+  int cg_loop(std::vector<Slot<T>*> slots, const std::vector<Slot<T>*>& set, GetX getx, GetR getr, GetSc getsc,
+              HostSc hostsc) {
     const int chunk = 8;
-    const std::vector<Slot<T>*> all = slots;
+    if (slots.empty()) return OFDFT_OK;
+    const bool graphs = c->use_graphs && c->cond_graphs && !(c->prof & (1 << OFDFT_K_CG_UPDATE));
+    const std::vector<Slot<T>*> all = graphs ? set : slots;
     // as ofdft_solve: when the batch's CG vectors do not fit in L2 the iterate
     // update of an iteration is folded into the next stencil pass (EpiCgAX), the
     // update only moves r, and a last flush applies the final pending x += alpha p
     double bytes = 0.0;
-    for (Slot<T>* S : slots) bytes += 5.0 * (double)S->g.G * sizeof(T);
-    const bool fold = bytes > 96.0 * (1 << 20);
-    while (!slots.empty()) {
-      for (int i = 0; i < chunk; ++i) {
-        // the stencil pass forms p and q from z = M r (preconditioned slots) or r
-        TRY(mg_cycle(slots, getr, getsc));
-        auto dir = [&](Slot<T>* S) -> const T* { return S->pc ? S->mz : getr(S); };
-        if (fold) {
-          TRY((zpass<T, LoadPlain<T>, EpiCgAX<T>>(slots, OFDFT_K_CG_DIR_STENCIL, -1.0, [&](Slot<T>* S) {
-            return std::make_pair(LoadPlain<T>{dir(S)}, EpiCgAX<T>{S->pv, S->qv, (T*)getx(S), getsc(S)});
-          })));
-          TRY((ppass<OpCgUpdateR<T>>(slots, OFDFT_K_CG_UPDATE, [&](Slot<T>* S, int nb) {
-            return OpCgUpdateR<T>{getr(S), S->qv, getsc(S), slot_red(S), nb};
-          })));
-        } else {
-          TRY((zpass<T, LoadPlain<T>, EpiCgA<T>>(slots, OFDFT_K_CG_DIR_STENCIL, -1.0, [&](Slot<T>* S) {
-            return std::make_pair(LoadPlain<T>{dir(S)}, EpiCgA<T>{S->pv, S->qv, getsc(S)});
-          })));
-          using X = std::remove_pointer_t<decltype(getx(slots[0]))>;
-          TRY((ppass<OpCgUpdate<T, X>>(slots, OFDFT_K_CG_UPDATE, [&](Slot<T>* S, int nb) {
-            return OpCgUpdate<T, X>{getx(S), getr(S), S->pv, S->qv, getsc(S), slot_red(S), nb};
-          })));
-        }
+    for (Slot<T>* S : all) bytes += 5.0 * (double)S->g.G * sizeof(T);
+    const bool fold = bytes > c->cg_fold_bytes;
+    if (graphs) {
+      if (!B->one_pinned) {
+        CU(cudaHostAlloc((void**)&B->one_pinned, sizeof(int), cudaHostAllocDefault));
+        *B->one_pinned = 1;
       }
+      std::vector<char> in(B->capacity + 1, 0);
+      for (Slot<T>* S : slots) in[S->index] = 1;
+      for (Slot<T>* S : set)
+        if (!in[S->index])
+          CU(cudaMemcpyAsync(&getsc(S)->done, B->one_pinned, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+      if (c->autotune) TRY(tune_zdepth(set, getr));
+      TRY(cg_iteration(set, fold, getx, getr, getsc));  // also sets kernel attributes outside the capture
+      B->eager_iters++;
+      cudaGraphExec_t exec = nullptr;
+      TRY(loop_graph(set, fold, getx, getr, getsc, &exec));
+      CU(cudaGraphLaunch(exec, c->stream));
+      B->graph_replays++;
+      TRY(read_scalars());
+      long long its = 0;
+      for (Slot<T>* S : slots) its = std::max<long long>(its, hostsc(S).iters);
+      B->graph_iters += its;
+      std::vector<Slot<T>*> still;
+      for (Slot<T>* S : slots)
+        if (!hostsc(S).done) still.push_back(S);
+      slots.swap(still);  // empty unless a graph failed to finish a loop
+    }
+    while (!slots.empty()) {
+      for (int i = 0; i < chunk; ++i) TRY(cg_iteration(slots, fold, getx, getr, getsc));
       TRY(read_scalars());
       std::vector<Slot<T>*> still;
       for (Slot<T>* S : slots)
@@ -516,7 +802,7 @@ struct Engine {
       for (Slot<T>* S : ev)
         if (!B->h_sc[S->index].done) run.push_back(S);
       TRY(cg_loop(
-          run, [](Slot<T>* S) { return S->phi; }, [](Slot<T>* S) { return S->r; },
+          run, ev, [](Slot<T>* S) { return S->phi; }, [](Slot<T>* S) { return S->r; },
           [&](Slot<T>* S) { return B->sc + S->index; }, [&](Slot<T>* S) -> CgScalars& { return B->h_sc[S->index]; }));
       for (Slot<T>* S : ev) {
         const CgScalars& h = B->h_sc[S->index];
@@ -570,7 +856,7 @@ struct Engine {
         if (!B->h_sc32[S->index].done) run.push_back(S);
       }
       TRY(cg_loop(
-          run, [](Slot<T>* S) { return (T*)S->e32; }, [](Slot<T>* S) { return S->r; },
+          run, ev, [](Slot<T>* S) { return (T*)S->e32; }, [](Slot<T>* S) { return S->r; },
           [&](Slot<T>* S) { return B->sc32 + S->index; },
           [&](Slot<T>* S) -> CgScalars& { return B->h_sc32[S->index]; }));
       for (Slot<T>* S : corr) S->ptotal += std::max(B->h_sc32[S->index].iters - before[S->index], 1);
@@ -1120,6 +1406,11 @@ int ofdft_batch_destroy(ofdft_batch* b) {
   drop(b->s32_active);
   drop(b->s64_done);
   drop(b->s32_done);
+  for (auto& gr : b->graphs) {
+    cudaGraphExecDestroy(gr.exec);
+    cudaFree(gr.arena);
+  }
+  if (b->one_pinned) cudaFreeHost(b->one_pinned);
   cudaFree(b->sc);
   cudaFree(b->sc32);
   cudaFree(b->out);
@@ -1178,6 +1469,25 @@ int ofdft_batch_run(ofdft_batch* b) {
     if (rc != OFDFT_OK) return rc;
     if (na == 0 && nq == 0) return OFDFT_OK;
   }
+}
+
+int ofdft_batch_info(const ofdft_batch* b, ofdft_batch_stats* out) {
+  if (!b || !out) return OFDFT_EINVAL;
+  memset(out, 0, sizeof(*out));
+  out->rounds = b->rounds;
+  out->graph_captures = b->graph_captures;
+  out->graph_replays = b->graph_replays;
+  out->graph_iterations = b->graph_iters;
+  out->eager_iterations = b->eager_iters;
+  out->z_depth = b->zdepth;
+  out->z_tuned = b->ztuned;
+  const int n = (int)std::min<size_t>(b->tune_log.size(), 8);
+  out->tune_candidates = n;
+  for (int i = 0; i < n; ++i) {
+    out->tune_depth[i] = b->tune_log[i].first;
+    out->tune_us[i] = b->tune_log[i].second;
+  }
+  return OFDFT_OK;
 }
 
 long long ofdft_batch_bytes(const ofdft_grid* g, int prec) {

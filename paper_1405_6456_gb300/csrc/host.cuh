@@ -2,6 +2,8 @@
 // the context (device workspaces, reduction scratch, trace counters), error
 // handling, stencil weights of Sec. 4, and kernel launch configuration.
 #pragma once
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdarg.h>
@@ -80,6 +82,12 @@ struct ofdft_ctx {
   int mg_sweeps = 20;                          // Jacobi sweeps on the multigrid bottom level
   DevBuf mgbuf;                                // multigrid levels below the finest
   int autotune = 1;
+  double cg_fold_bytes = 96.0 * (1 << 20);     // fold the CG iterate update above this CG working set
+  long long mg_fuse_nodes = -1;                // multigrid levels of at least this many nodes: two fused launches (-1: none)
+  int ff_residual = 1;                         // mixed residual pass in float-float (else FP64)
+  int cond_graphs = 1;                         // CG loops as one graph with a device-side WHILE node
+  int mixed_ff = 0;                            // the last mixed Poisson solve ran the float-float residual pass
+  int tma = 0;                                 // FP32 z-streaming passes stage planes by TMA where they can
 };
 
 namespace ofd {
@@ -93,6 +101,9 @@ enum Vec {
   V_W,                                 // u / Jacobi diagonal (rank-one preconditioner)
   V_PHI0,                              // FP64 potential at the origin of the current line search
   V_Z, V_T,                            // PCG: z = M r and the multigrid's finest-level scratch
+  V_PHI2,                              // mixed: the FP64 potential as float-float pairs (residual pass)
+  V_BACC,                              // FP64 running sums of the pseudocharge over atom ranges
+  V_B2,                                // mixed: the FP64 pseudocharge as float-float pairs (residual pass)
   V_COUNT
 };
 
@@ -267,6 +278,18 @@ Weights<T> cast_weights(const Weights<double>& W) {
   for (int p = 0; p <= kMaxR; ++p) o.w[p] = (T)W.w[p];
   return o;
 }
+// float-float weights: hi = nearest float, lo = nearest float of the remainder
+inline float2 ff_of(double v) {
+  const float hi = (float)v;
+  return make_float2(hi, (float)(v - (double)hi));
+}
+template <>
+inline Weights<float2> cast_weights<float2>(const Weights<double>& W) {
+  Weights<float2> o;
+  o.c = ff_of(W.c);
+  for (int p = 0; p <= kMaxR; ++p) o.w[p] = ff_of(W.w[p]);
+  return o;
+}
 
 inline int pointwise_blocks(ofdft_ctx* c, long long G) {
   long long b = (G + 1023) / 1024;
@@ -385,6 +408,7 @@ inline MgPlan mg_plan(const GridDev& g, double h, size_t es, double omega = kMgO
       break;
     }
   if (P.lc < 0) return P;  // the bottom level is too large for one block: plain CG
+  if (mg_nodes(P.d[0]) >= (1LL << 31)) return P;  // the level kernels index with 32-bit integers
   long long e = 0;
   for (int l = 1; l <= P.lc; ++l) {
     P.off[l] = e;
@@ -409,7 +433,11 @@ cudaError_t launch_k(ofdft_ctx* c, void (*kern)(KArgs...), dim3 grid, dim3 block
 template <typename T, int R, int V, class L, class E>
 int launch_zv(ofdft_ctx* c, const GridDev& g, const Weights<double>& W, L ld, E ep, int kind) {
   constexpr int smem = zsmem_bytes<T, R, V, E>();
-  static int per_sm = 0;  // resident blocks per SM of this kernel (dynamic smem above 48 KB needs an opt-in)
+  // resident blocks per SM of this kernel, per device (dynamic shared memory above
+  // 48 KB needs an opt-in, a per-device setting)
+  static int per_sm_dev[64] = {0};
+  if (c->device < 0 || c->device >= 64) return fail(c, OFDFT_EINVAL, "device index out of range");
+  int& per_sm = per_sm_dev[c->device];
   if (!per_sm) {
     CU(cudaFuncSetAttribute(zstream_kernel<T, R, V, L, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int nb = 0;
@@ -438,9 +466,97 @@ int launch_zv(ofdft_ctx* c, const GridDev& g, const Weights<double>& W, L ld, E 
   return OFDFT_OK;
 }
 
+// cuTensorMapEncodeTiled of the driver, found through the runtime (no link
+// against libcuda); nullptr when the driver does not offer it.
+inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// Tensor map of an FP32 grid array (x-fastest, n1 x n2 x n3) read in boxes of
+// bx x by x 1 elements; out-of-grid elements read as zero.
+inline bool fp32_grid_map(CUtensorMap* m, const void* base, const GridDev& g, int bx, int by) {
+  auto enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)g.n1, (cuuint64_t)g.n2, (cuuint64_t)g.n3};
+  const cuuint64_t strides[2] = {(cuuint64_t)g.n1 * 4, (cuuint64_t)g.n1 * g.n2 * 4};
+  const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The z-streaming pass with TMA staging (zstream_tma_kernel).  Returns false
+// (nothing launched) when the pass cannot take it: another element type or
+// staging width, a slot size off the 128-byte grid, an epilogue input that is
+// NULL, or no tensor-map encoder.
+template <typename T, int R, int V, class L, class E>
+int launch_zv_tma(ofdft_ctx* c, const GridDev& g, const Weights<double>& W, L ld, E ep, int kind, bool* done) {
+  *done = false;
+  if constexpr (!ztma_fits<T, R, V>() || E::NIN > 3) {
+    return OFDFT_OK;
+  } else {
+    if (!c->tma) return OFDFT_OK;
+    constexpr int TY = ZCfg<T>::TY, RA = zhalo_x<T, R, V>();
+    CUtensorMap mf, mi[3];
+    if (!fp32_grid_map(&mf, ld.f, g, BX + 2 * RA, TY + 2 * R)) return OFDFT_OK;
+    for (int j = 0; j < 3; ++j) mi[j] = mf;
+    for (int j = 0; j < E::NIN; ++j) {
+      const void* in = ep.input(j);
+      if (!in || !fp32_grid_map(&mi[j], in, g, BX, TY)) return OFDFT_OK;
+    }
+    constexpr int smem = zsmem_bytes<T, R, V, E>() + 128;
+    static int per_sm_dev[64] = {0};
+    if (c->device < 0 || c->device >= 64) return fail(c, OFDFT_EINVAL, "device index out of range");
+    int& per_sm = per_sm_dev[c->device];
+    if (!per_sm) {
+      CU(cudaFuncSetAttribute(zstream_tma_kernel<T, R, V, L, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+      int nb = 0;
+      CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, zstream_tma_kernel<T, R, V, L, E>, NT, smem));
+      per_sm = std::max(nb, 1);
+    }
+    const std::vector<long long> key = ztune_key((const void*)zstream_tma_kernel<T, R, V, L, E>, g);
+    int nz = 0;
+    if (c->force_nz >= 0) {
+      nz = c->force_nz;
+    } else {
+      for (auto& t : c->ztune)
+        if (t.first == key) {
+          nz = t.second;
+          break;
+        }
+    }
+    c->last_zkey = key;
+    const ZShape s = zshape<T>(c, g, R, per_sm, nz);
+    if (E::K > 0) TRY(ensure_partials(c, s.nblocks, E::K));
+    {
+      ProfScope ps_(c, kind);
+      CU(launch_k(c, zstream_tma_kernel<T, R, V, L, E>, s.grid, dim3(BX, BY), smem, mf, mi[0], mi[1], mi[2], g,
+                  cast_weights<T>(W), s.zchunk, ld, ep, red(c)));
+    }
+    *done = true;
+    return OFDFT_OK;
+  }
+}
+
 template <typename T, int R, class L, class E>
 int launch_z(ofdft_ctx* c, const GridDev& g, const Weights<double>& W, L ld, E ep, int kind) {
-  if (zvec_ok<T>(g, ld, ep)) return launch_zv<T, R, 16 / (int)sizeof(T)>(c, g, W, ld, ep, kind);
+  if (zvec_ok<T>(g, ld, ep)) {
+    bool done = false;
+    TRY((launch_zv_tma<T, R, 16 / (int)sizeof(T)>(c, g, W, ld, ep, kind, &done)));
+    if (done) return OFDFT_OK;
+    return launch_zv<T, R, 16 / (int)sizeof(T)>(c, g, W, ld, ep, kind);
+  }
   return launch_zv<T, R, 1>(c, g, W, ld, ep, kind);
 }
 

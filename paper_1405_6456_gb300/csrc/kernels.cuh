@@ -4,6 +4,7 @@
 // and epilogue (what is done with the result at each node).
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (the type only; no driver call is made from here)
 #include <math.h>
 
 #include "common.cuh"
@@ -28,6 +29,39 @@ struct ZCfg {
   static constexpr int ZD = sizeof(T) == 4 ? 3 : 2;
 };
 
+// Double-float32 ("float-float") numbers: an unevaluated sum hi + lo of two
+// floats with |lo| <= ulp(hi) / 2, about 48 significant bits.  Error-free
+// transformations: Knuth's TwoSum for the sum of two floats, Dekker's Fast2Sum
+// to renormalise, and the FMA for the exact rounding error of a product
+// (Dekker 1971; Hida, Li and Bailey 2001 for the double-double forms these
+// follow).  Every operation runs on the FP32 pipes, which on this GPU issue at
+// many times the FP64 rate; an add or multiply has an absolute error of a few
+// units of 2^-48 of its operands' magnitudes.
+__device__ __forceinline__ float2 ff_two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return make_float2(s, (a - (s - bb)) + (b - bb));
+}
+__device__ __forceinline__ float2 ff_fast_two_sum(float a, float b) {  // needs |a| >= |b| or a == 0
+  const float s = a + b;
+  return make_float2(s, b - (s - a));
+}
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
+  const float2 s = ff_two_sum(a.x, b.x);
+  return ff_fast_two_sum(s.x, s.y + (a.y + b.y));
+}
+__device__ __forceinline__ float2 ff_mul(float2 w, float2 a) {
+  const float p = w.x * a.x;
+  float e = fmaf(w.x, a.x, -p);  // exact rounding error of w.hi a.hi
+  e = fmaf(w.x, a.y, fmaf(w.y, a.x, e));
+  return ff_fast_two_sum(p, e);
+}
+
+template <typename T>
+__host__ __device__ __forceinline__ T zero_of() { return T(0); }
+template <>
+__host__ __device__ __forceinline__ float2 zero_of<float2>() { return make_float2(0.0f, 0.0f); }
+
 // Arithmetic on a thread's CX adjacent columns: one FP64 value, or an FP32 pair
 // computed with the packed FP32x2 instructions (each lane rounds as the scalar
 // operation does, so results equal the one-column code's bit for bit).
@@ -42,6 +76,17 @@ struct Lanes<T, 1> {
   __device__ static V fma(T w, V a, V c) { return ::fma(w, a, c); }
   __device__ static V make(const T* v) { return v[0]; }
   __device__ static T lane(V v, int) { return v; }
+};
+// float-float values (float2 = hi, lo), one column per thread
+template <>
+struct Lanes<float2, 1> {
+  using V = float2;
+  __device__ static V ld(const float2* p) { return *p; }
+  __device__ static V add(V a, V b) { return ff_add(a, b); }
+  __device__ static V mul(float2 w, V a) { return ff_mul(w, a); }
+  __device__ static V fma(float2 w, V a, V c) { return ff_add(ff_mul(w, a), c); }
+  __device__ static V make(const float2* v) { return v[0]; }
+  __device__ static float2 lane(V v, int) { return v; }
 };
 template <>
 struct Lanes<float, 2> {
@@ -75,6 +120,8 @@ struct CgScalars {
   int err;        // 1 when a grid barrier of the persistent CG kernel timed out
   int pc;         // 1: preconditioned CG (alpha = rz / pAp, beta from the preconditioner pass)
   double rz;      // r.z of the preconditioned residual z = M r (PCG)
+  double es_rho_phi;  // sum (u^2 + b) phi at the residual pass's phi (float-float residual pass)
+  double es_phi_r;    // sum phi r, r the residual it writes
 };
 
 // ---------------------------------------------------------------------------
@@ -159,11 +206,65 @@ template <typename T, int R, int V>
 constexpr int zring_bytes() {
   return (R + ZCfg<T>::ZD) * (ZCfg<T>::TY + 2 * R) * (BX + 2 * zhalo_x<T, R, V>()) * (int)sizeof(T);
 }
+// TMA staging applies when every staged slot starts on a 128-byte boundary:
+// FP32, 16-byte vectors, and a slot size that is a multiple of 128 bytes.
+template <typename T, int R, int V>
+constexpr bool ztma_fits() {
+  return sizeof(T) == 4 && V == 4 &&
+         ((ZCfg<T>::TY + 2 * R) * (BX + 2 * zhalo_x<T, R, V>()) * (int)sizeof(T)) % 128 == 0;
+}
 // Dynamic shared memory of a z-streaming pass: the stencil-input ring plus a
 // ring of ZD planes for each pointwise input the epilogue declares (NIN).
 template <typename T, int R, int V, class Epi>
 constexpr int zsmem_bytes() {
   return zring_bytes<T, R, V>() + ZCfg<T>::ZD * Epi::NIN * ZCfg<T>::TY * BX * (int)sizeof(T);
+}
+
+// ---------------------------------------------------------------------------
+// TMA staging (the tensor memory accelerator of sm_100-class GPUs): one thread
+// issues a tiled bulk copy of a whole staged plane (tile plus halo) from a
+// tensor map, the hardware fills every out-of-grid element with zero (the zero
+// Dirichlet values) and signals an mbarrier when the bytes have landed; the
+// other threads wait on that barrier.  Every wait is bounded: if a copy never
+// arrives the waiting thread raises zstream_fault and carries on, and the host
+// reports OFDFT_ETIMEOUT.
+__device__ int zstream_fault;
+
+struct ZTmaMaps {
+  const CUtensorMap* f;      // stencil input: box {SX, SY, 1}
+  const CUtensorMap* in[3];  // epilogue inputs: box {BX, TY, 1}
+};
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Waits for phase `parity` of bar to complete, at most ~2^22 polls.
+__device__ __forceinline__ void mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
+  for (int i = 0; i < (1 << 22); ++i)
+    if (mbar_try_wait(bar, parity)) return;
+  atomicExch(&zstream_fault, 1);
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                            unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];\n" ::"r"(smem_addr(dst)),
+      "l"((unsigned long long)map), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+      : "memory");
 }
 
 // One block's share of a z-streaming pass: tile (bx, by) of BX x TY columns,
@@ -179,10 +280,11 @@ constexpr int zsmem_bytes() {
 // inputs (ep.input(j)) at the block's own nodes travel in the same pipeline, so
 // the epilogue never waits on a global load.  In-plane offsets are 32-bit
 // (n1 * n2 < 2^31).
-template <typename T, int R, int V, class Epi>
+template <typename T, int R, int V, class Epi, bool TMA = false>
 __device__ __forceinline__ void zstream_tile(const GridDev& g, const Weights<T>& W, int bx, int by, int z0, int z1,
                                              const T* __restrict__ f, const Epi& ep_in, const RedBuf& red,
-                                             int nblocks, int bid, double* block_out = nullptr) {
+                                             int nblocks, int bid, double* block_out = nullptr,
+                                             const ZTmaMaps* tm = nullptr) {
   Epi ep = ep_in;  // block-local copy: load() caches the epilogue's device scalars in registers
   constexpr int CX = ZCfg<T>::CX, RY = ZCfg<T>::RY, THX = ZCfg<T>::THX, TY = ZCfg<T>::TY, ZD = ZCfg<T>::ZD;
   using L = Lanes<T, CX>;
@@ -200,10 +302,16 @@ __device__ __forceinline__ void zstream_tile(const GridDev& g, const Weights<T>&
   static_assert(NE <= 32 && NI * (NIN > 0 ? NIN : 1) <= 32, "staging masks hold 32 entries");
   static_assert(ICH % NT == 0, "input planes split evenly over the threads");
   static_assert(RE <= RA, "the x-window stays inside the staged halo");
-  extern __shared__ __align__(16) unsigned char zsm_raw[];
-  T(*ring)[SP] = reinterpret_cast<T(*)[SP]>(zsm_raw);
+  static_assert(!TMA || (sizeof(T) == 4 && V == 4), "TMA staging: FP32 fields with 16-byte rows");
+  extern __shared__ __align__(128) unsigned char zsm_raw[];
+  __shared__ __align__(8) unsigned long long zbar[TMA ? R + ZCfg<T>::ZD : 1];  // one barrier per ring slot
+  unsigned zphase = 0;  // bit s: parity of ring slot s's next completion
+  // TMA destinations must be 128-byte aligned: the launch adds 128 bytes of room
+  unsigned char* zsm = zsm_raw;
+  if constexpr (TMA) zsm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(zsm_raw) + 127) & ~uintptr_t(127));
+  T(*ring)[SP] = reinterpret_cast<T(*)[SP]>(zsm);
   T(*pin)[NIN > 0 ? NIN : 1][TY * BX] =
-      reinterpret_cast<T(*)[NIN > 0 ? NIN : 1][TY * BX]>(zsm_raw + zring_bytes<T, R, V>());
+      reinterpret_cast<T(*)[NIN > 0 ? NIN : 1][TY * BX]>(zsm + zring_bytes<T, R, V>());
   __shared__ double red_smem[(Epi::K > 0 ? Epi::K : 1) * (NT / 32)];
   const int tid = threadIdx.y * BX + threadIdx.x;
   const int tx = tid % THX, ty = tid / THX;  // column group and row group of this thread
@@ -247,6 +355,23 @@ __device__ __forceinline__ void zstream_tile(const GridDev& g, const Weights<T>&
   // stage plane p into ring slot sl and (for p - R inside the chunk) the
   // epilogue inputs of plane p - R into input slot isl; one commit group per call
   auto stage = [&](int p, int sl, int isl) {
+    if constexpr (TMA) {
+      if (tid == 0) {
+        const int pp = p - R;
+        const bool inputs = NIN > 0 && pp >= z0 && pp < z1;
+        // the slot was last read through the generic proxy (ordered by the
+        // caller's __syncthreads); order those reads before the async writes
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        mbar_expect_tx(&zbar[sl], (unsigned)(SP * sizeof(T) + (inputs ? NIN * TY * BX * sizeof(T) : 0)));
+        tma_load_3d(ring[sl], tm->f, bx * BX - RA, by * TY - R, p, &zbar[sl]);
+        if constexpr (NIN > 0) {
+          if (inputs)
+#pragma unroll
+            for (int j = 0; j < NIN; ++j) tma_load_3d(&pin[isl][j][0], tm->in[j], bx * BX, by * TY, pp, &zbar[sl]);
+        }
+      }
+      return;
+    }
     const bool pv = (p >= 0) && (p < g.n3);
     const T* fp = f + plane * (long long)(pv ? p : 0);
     T* dst = ring[sl];
@@ -289,13 +414,32 @@ __device__ __forceinline__ void zstream_tile(const GridDev& g, const Weights<T>&
       for (int l = 0; l < CX; ++l)
         v[l] = (((node_ok >> (i * CX + l)) & 1u) && kk >= 0 && kk < g.n3)
                    ? __ldcg(&f[(long long)g.n1 * (y0 + i) + x0 + l + plane * kk])  // L2: other blocks may have written it
-                   : T(0);
+                   : zero_of<T>();
       q[i][m] = L::make(v);
     }
   // ring slots advance by one per plane (no integer division in the loop):
   // stencil plane p lives in slot (p - z0) mod NS, input plane p in (p - z0) mod ZD
   int s_stage = 0, i_stage = (ZD - R % ZD) % ZD;
   auto bump = [](int v, int n) { return v + 1 == n ? 0 : v + 1; };
+  if constexpr (TMA) {
+    if (tid == 0) {
+#pragma unroll
+      for (int sl = 0; sl < NS; ++sl) mbar_init(&zbar[sl], 1);
+      asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+  }
+  // waits (TMA staging) for the copies of the slots a block issued but never
+  // consumed, so that no copy lands after the block has exited
+  auto drain = [&](int first_plane, int count) {
+    if constexpr (TMA) {
+      for (int p = first_plane; p < first_plane + count; ++p) {
+        const int sl = (p - z0) % NS;
+        mbar_wait_bounded(&zbar[sl], (zphase >> sl) & 1u);
+        zphase ^= 1u << sl;
+      }
+    }
+  };
   for (int p = z0; p < z0 + R + ZD - 1; ++p) {
     stage(p, s_stage, i_stage);
     s_stage = bump(s_stage, NS);
@@ -306,9 +450,14 @@ __device__ __forceinline__ void zstream_tile(const GridDev& g, const Weights<T>&
   // are read while the first planes are in flight
   if (ep.skip()) {
     cp_async_wait<0>();  // no copy may land in shared memory after the block exits
+    drain(z0, R + ZD - 1);
     return;
   }
   ep.load();
+  // TMA: the first R planes of the chunk are read (as plane k) before the loop
+  // waits on them as plane k + R, so wait for them here; the loop then waits for
+  // planes z0 + R .. z1 - 1 + R and the end for the rest
+  drain(z0, R);
 
   typename Epi::Acc acc[Epi::K > 0 ? Epi::K : 1];
 #pragma unroll
@@ -321,8 +470,13 @@ __device__ __forceinline__ void zstream_tile(const GridDev& g, const Weights<T>&
     stage(k + R + ZD - 1, s_stage, i_stage);  // refills that slot
     s_stage = bump(s_stage, NS);
     i_stage = bump(i_stage, ZD);
-    cp_async_wait<ZD - 1>();  // planes <= k + R have landed (this thread's copies)
-    __syncthreads();          // ... and every other thread's
+    if constexpr (TMA) {
+      mbar_wait_bounded(&zbar[sf], (zphase >> sf) & 1u);  // plane k + R and the inputs of plane k
+      zphase ^= 1u << sf;
+    } else {
+      cp_async_wait<ZD - 1>();  // planes <= k + R have landed (this thread's copies)
+      __syncthreads();          // ... and every other thread's
+    }
     const T* pk = ring[sk] + cb;  // (row offset m, first column) of plane k at pk[m * SX]
 #pragma unroll
     for (int i = 0; i < RY; ++i) q[i][2 * R] = L::ld(ring[sf] + cb + (i + R) * SX);
@@ -378,6 +532,7 @@ __device__ __forceinline__ void zstream_tile(const GridDev& g, const Weights<T>&
     ik = bump(ik, ZD);
   }
   cp_async_wait<0>();
+  drain(z1 + R, ZD - 1);
   if constexpr (Epi::K > 0) {
     double accd[Epi::K];
 #pragma unroll
@@ -567,6 +722,23 @@ __global__ void __launch_bounds__(NT, 2) zstream_kernel(GridDev g, Weights<T> W,
   const int nblocks = gridDim.x * gridDim.y * gridDim.z;
   const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
   zstream_tile<T, R, V>(g, W, blockIdx.x, blockIdx.y, z0, z1, ld.f, ep, red, nblocks, bid);
+}
+
+// Single grid with TMA staging (FP32, rows of whole 16-byte vectors): the
+// tensor maps travel as kernel parameters.
+template <typename T, int R, int V, class Loader, class Epi>
+__global__ void __launch_bounds__(NT, 2) zstream_tma_kernel(const __grid_constant__ CUtensorMap tmf,
+                                                            const __grid_constant__ CUtensorMap tm0,
+                                                            const __grid_constant__ CUtensorMap tm1,
+                                                            const __grid_constant__ CUtensorMap tm2, GridDev g,
+                                                            Weights<T> W, int zchunk, Loader ld, Epi ep, RedBuf red) {
+  const int z0 = blockIdx.z * zchunk;
+  const int z1 = min(z0 + zchunk, g.n3);
+  const int nblocks = gridDim.x * gridDim.y * gridDim.z;
+  const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  const ZTmaMaps maps{&tmf, {&tm0, &tm1, &tm2}};
+  zstream_tile<T, R, V, Epi, true>(g, W, blockIdx.x, blockIdx.y, z0, z1, ld.f, ep, red, nblocks, bid, nullptr,
+                                   &maps);
 }
 
 // Batched: uneven grids packed into one launch (S11).  Block b works on
@@ -788,11 +960,101 @@ struct EpiResidual {
   }
 };
 
+// The residual pass of the mixed Poisson rounds with the potential in
+// float-float form (phi64 = hi + lo, staged as float2): the stencil runs in
+// float-float arithmetic on the FP32 pipes (replacing 37 FP64 FMAs per node,
+// which bound the FP64 pass), and so does the epilogue:
+//   rho = u^2 + b (u^2 exact from an FMA, b as float-float pairs) or rho_in,
+//   r = 4 pi rho + L_h phi, written as float-float pairs,
+// with compensated FP32 sums (DotAcc) of u.u, ||4 pi rho||^2, ||r||^2 and, for
+// the variational electrostatic energy of the functional that follows, of
+// (u^2 + b) phi and phi r.  Accuracy: about 2^-48 of the magnitudes of the
+// stencil's terms (the FP64 pass: 2^-53).
+__device__ __forceinline__ float2 ff_prod(float a, float b) {  // a b exactly
+  const float p = a * b;
+  return make_float2(p, fmaf(a, b, -p));
+}
+
+struct EpiResidualFF {
+  static constexpr int K = 5;
+  static constexpr int NIN = 0;
+  using Acc = DotAcc<float>;
+  const float* rho;  // explicit density, or NULL for u^2 + b
+  const float* u;
+  const float2* b2;
+  float2* r2;
+  CgScalars* sc;
+  double tol;
+  int max_it;
+  int pc = 0;  // the CG that follows is preconditioned
+  float2 fourpi;
+  __device__ __forceinline__ bool skip() const { return false; }
+  __device__ __forceinline__ void load() {}
+  __host__ __device__ __forceinline__ const float2* input(int) const { return nullptr; }
+  __device__ __forceinline__ void apply(long long i, float2 ph, float2 lap, const float2*, Acc* acc) const {
+    float2 rr;
+    if (rho) {
+      rr = make_float2(rho[i], 0.0f);
+    } else {
+      const float ui = u[i];
+      acc[0].add(ui, ui);
+      rr = ff_add(ff_prod(ui, ui), b2[i]);
+    }
+    const float2 rh = ff_mul(fourpi, rr);
+    const float2 r = ff_add(rh, lap);
+    r2[i] = r;
+    acc[1].add(rh.x, rh.x);
+    acc[2].add(r.x, r.x);
+    acc[3].add(rr.x, ph.x);
+    acc[3].add(rr.x, ph.y);
+    acc[3].add(rr.y, ph.x);
+    acc[4].add(ph.x, r.x);
+    acc[4].add(ph.x, r.y);
+    acc[4].add(ph.y, r.x);
+  }
+  __device__ __forceinline__ void operator()(double* t) const {
+    sc->sum_uu = t[0];
+    sc->bb = t[1];
+    sc->rr = t[2];
+    sc->rr0 = t[2];
+    sc->es_rho_phi = t[3];
+    sc->es_phi_r = t[4];
+    sc->tol2 = tol * tol;
+    sc->iters = 0;
+    sc->max_it = max_it;
+    sc->first = 1;
+    sc->beta = 0.0;
+    sc->xdefer = 0;
+    sc->err = 0;
+    sc->pc = pc;
+    const double thr = tol * tol * (t[1] > 0.0 ? t[1] : 1.0);
+    sc->done = (t[2] <= thr || max_it <= 0) ? 1 : 0;
+  }
+};
+
+// phi2 = phi64 and b2 = b64 (if b2 is not NULL) split into float-float pairs
+// (hi = nearest float, lo = nearest float of the remainder).
+static __global__ void __launch_bounds__(256) ff_split_kernel(long long G, float2* phi2, const double* phi64,
+                                                              float2* b2, const double* b64) {
+  for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < G; i += (long long)gridDim.x * 256) {
+    const double v = phi64[i];
+    const float hi = (float)v;
+    phi2[i] = make_float2(hi, (float)(v - (double)hi));
+    if (b2) {
+      const double w = b64[i];
+      const float bh = (float)w;
+      b2[i] = make_float2(bh, (float)(w - (double)bh));
+    }
+  }
+}
+
 // ------------------------------------------------------------- functional ---
 // LDA exchange-correlation of Sec. 2 / Sec. 3 (Ceperley-Alder form), density
-// floor u^2 < 1e-30 -> 0.
+// floor u^2 < 1e-30 -> 0.  c13 = u^(2/3) = rho^(1/3) is passed in (the caller
+// already has cbrt(u) for the Thomas-Fermi term); one reciprocal per branch
+// replaces the divisions.
 template <typename T>
-__device__ __forceinline__ void xc_eval(T u, T& eps, T& v) {
+__device__ __forceinline__ void xc_eval(T u, T rho13, T& eps, T& v) {
   const T rho = u * u;
   if (!(rho >= (T)1e-30)) {
     eps = T(0);
@@ -802,16 +1064,15 @@ __device__ __forceinline__ void xc_eval(T u, T& eps, T& v) {
   const T g1 = (T)-0.1423, b1 = (T)1.0529, b2 = (T)0.3334;
   const T A1 = (T)0.0311, B1 = (T)-0.048, C1 = (T)0.002, D1 = (T)-0.0116;
   const T c3pi = (T)0.98474502184269641;  // (3/pi)^{1/3}
-  const T rho13 = cbrt(rho);
   const T ex = (T)-0.75 * c3pi * rho13;
   const T vx = -c3pi * rho13;
   const T rs = (T)0.62035049089940009 / rho13;  // (3/(4 pi))^{1/3} / rho^{1/3}
   T ec, vc;
   if (rs >= T(1)) {
     const T srs = sqrt(rs);
-    const T den = T(1) + b1 * srs + b2 * rs;
-    ec = g1 / den;
-    vc = (g1 + (T)(7.0 / 6.0) * g1 * b1 * srs + (T)(4.0 / 3.0) * g1 * b2 * rs) / (den * den);
+    const T iden = T(1) / (T(1) + b1 * srs + b2 * rs);
+    ec = g1 * iden;
+    vc = (g1 + (T)(7.0 / 6.0) * g1 * b1 * srs + (T)(4.0 / 3.0) * g1 * b2 * rs) * (iden * iden);
   } else {
     const T lr = log(rs);
     ec = A1 * lr + B1 + C1 * rs * lr + D1 * rs;
@@ -819,6 +1080,10 @@ __device__ __forceinline__ void xc_eval(T u, T& eps, T& v) {
   }
   eps = ex + ec;
   v = vx + vc;
+}
+template <typename T>
+__device__ __forceinline__ void xc_eval(T u, T& eps, T& v) {
+  xc_eval<T>(u, cbrt(u * u), eps, v);
 }
 
 struct FuncScalars {
@@ -833,7 +1098,7 @@ struct FuncScalars {
 template <typename T>
 struct EpiFunctional {
   static constexpr int K = 11;
-  static constexpr int NIN = 0;
+  static constexpr int NIN = 2;  // phi and b at the node, staged by the pipeline
   using Acc = FAcc<T>;
   const T* phi;
   const T* b;
@@ -855,6 +1120,9 @@ struct EpiFunctional {
   const double* phi64 = nullptr;
   const double* b64 = nullptr;
   const double* r64 = nullptr;
+  // MIXED with the float-float residual pass: that pass already summed (u^2 + b) phi
+  // and phi r in compensated arithmetic; the functional takes them from here
+  const CgScalars* es_sums = nullptr;
   __device__ __forceinline__ bool skip() const { return false; }
   __device__ __forceinline__ void load() {
     const double C = f.h3 * *sum_uu - f.N;
@@ -864,32 +1132,38 @@ struct EpiFunctional {
     lam_ = (T)(-f.lambda);
     kvw_ = (T)f.kin_vw;
   }
-  __host__ __device__ __forceinline__ const T* input(int) const { return nullptr; }
-  __device__ __forceinline__ void apply(long long i, T uc, T lap, const T*, Acc* acc) const {
+  __host__ __device__ __forceinline__ const T* input(int j) const {
+    if (j == 0) return (f.terms & 8) ? phi : nullptr;
+    return (f.terms & 8) ? b : nullptr;
+  }
+  __device__ __forceinline__ void apply(long long i, T uc, T lap, const T* vin, Acc* acc) const {
     const T mult = mult_;
     const bool tf = f.terms & 1, vw = f.terms & 2, xc = f.terms & 4, es = f.terms & 8;
     const T ux = fabs(uc);
     T vk = T(0), vxc = T(0), exc = T(0), ph = T(0);
+    const T c = (tf || xc) ? cbrt(ux) : T(0);
+    const T c2 = c * c;  // u^(2/3) = rho^(1/3)
     if (tf) {
-      const T c = cbrt(ux);
-      const T u43 = (c * c) * (c * c);
+      const T u43 = c2 * c2;
       vk = vk_ * u43;
       acc[0].add(cf_ * u43, ux * ux);
     }
     if (vw) acc[1].add(uc, lap);
     if (xc) {
-      xc_eval<T>(ux, exc, vxc);
+      xc_eval<T>(ux, c2, exc, vxc);
       acc[2].add(exc, ux * ux);
     }
     if (es) {
-      if (phi64) {
+      if (es_sums) {
+        ph = vin[0];
+      } else if (phi64) {
         const double phd = phi64[i];
         ph = (T)phd;
         acc[3].add_d(((double)uc * (double)uc + b64[i]) * phd);
         if (r64) acc[4].add_d(phd * r64[i]);
       } else {
-        ph = phi[i];
-        const T rho = uc * uc + b[i];
+        ph = vin[0];
+        const T rho = uc * uc + vin[1];
         acc[3].add(rho, ph);
         if (rcg) acc[4].add(ph, rcg[i]);
       }
@@ -899,8 +1173,9 @@ struct EpiFunctional {
     T md = kin + T(2) * (vxc + ph + mult);
     md = fmax(md, (T)0.25 * kin);
     md = fmax(md, (T)1e-10);
-    const T sx = -gx / md;
-    const T wv = uc / md;
+    const T inv = T(1) / md;
+    const T sx = -gx * inv;
+    const T wv = uc * inv;
     if (G) G[i] = gx;
     if (s) s[i] = sx;
     if (winv) winv[i] = wv;
@@ -914,6 +1189,10 @@ struct EpiFunctional {
   __device__ __forceinline__ void operator()(double* t) const {
 #pragma unroll
     for (int k = 0; k < 9; ++k) out[k] = t[k];
+    if (es_sums && (f.terms & 8)) {
+      out[3] = es_sums->es_rho_phi;
+      out[4] = es_sums->es_phi_r;
+    }
     out[9] = f.h3 * *sum_uu - f.N;
     out[10] = t[9];
     out[11] = t[10];
@@ -1144,6 +1423,26 @@ __global__ void __launch_bounds__(256) cg_update_r_kernel(long long G, T* __rest
   grid_sum<1, 256>(acc, smem, red, gridDim.x, blockIdx.x, threadIdx.x, fin);
 }
 
+// Condition of the device-side CG loop (a CUDA graph WHILE node): keep
+// iterating while the solve is not done.  `done` is raised by the CG kernels
+// themselves at convergence, at the iteration cap or on a non-finite residual,
+// so the loop always ends.
+static __global__ void cg_cond_kernel(cudaGraphConditionalHandle h, const CgScalars* sc) {
+  cudaGraphSetConditional(h, sc->done ? 0u : 1u);
+}
+
+// Condition of the batched CG loop graph: keep iterating while any of the n
+// solves base[idx[i]] is not done.
+static __global__ void batch_cond_kernel(cudaGraphConditionalHandle h, const CgScalars* base, const int* idx, int n) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    if (!base[idx[i]].done) any = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) cudaGraphSetConditional(h, any ? 1u : 0u);
+}
+
 // Applies a pending x += alpha p (xdefer) after the last CG iteration of a call.
 template <typename T>
 __global__ void __launch_bounds__(256) cg_xflush_kernel(long long G, T* __restrict__ x, const T* __restrict__ p,
@@ -1159,13 +1458,17 @@ static __global__ void cg_xclear_kernel(CgScalars* sc) { sc->xdefer = 0; }
 // residual).  On the first round the CG starts from scratch (p = r); later
 // rounds keep the search direction and rescale beta to the replaced residual.
 // The FP32 iterations of a round stop when r.r falls by inner_tol^2.
-static __global__ void __launch_bounds__(256) refine_replace_kernel(long long G, float* r32, const double* r64,
+__device__ __forceinline__ float nearest_float(double v) { return (float)v; }
+__device__ __forceinline__ float nearest_float(float2 v) { return v.x; }  // hi is the nearest float of hi + lo
+
+template <typename RS>
+__global__ void __launch_bounds__(256) refine_replace_kernel(long long G, float* r32, const RS* r64,
                                                                     CgScalars* sc, double inner_tol, int budget,
                                                                     int restart, int pc, RedBuf red) {
   __shared__ double smem[256 / 32];
   double acc[1] = {0.0};
   for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < G; i += (long long)gridDim.x * 256) {
-    const float v = (float)r64[i];
+    const float v = nearest_float(r64[i]);
     r32[i] = v;
     acc[0] += (double)v * (double)v;
   }
@@ -1236,11 +1539,15 @@ __device__ __forceinline__ T mg_nb_sum(const T* f, int i, int j, int k, const Mg
   return s;
 }
 
+// (i, j, k) of linear index idx on level d; every level holds fewer than 2^31
+// nodes (mg_plan), so 32-bit unsigned divisions suffice.
 __device__ __forceinline__ void mg_ijk(long long idx, const MgLevel& d, int& i, int& j, int& k) {
-  const long long jk = idx / d.n1;
-  i = (int)(idx - jk * d.n1);
-  k = (int)(jk / d.n2);
-  j = (int)(jk - (long long)k * d.n2);
+  const unsigned q = (unsigned)idx;
+  const unsigned jk = q / (unsigned)d.n1;
+  i = (int)(q - jk * (unsigned)d.n1);
+  const unsigned kk = jk / (unsigned)d.n2;
+  k = (int)kk;
+  j = (int)(jk - kk * (unsigned)d.n2);
 }
 
 // Coarse node c = I of one axis: full-weighting sum over fine 2I, 2I+1, 2I+2.
@@ -1306,17 +1613,21 @@ __device__ __forceinline__ T mg_prolong_at(const T* e, const MgLevel& c, int i, 
   return wz0 * (wy0 * a00 + wy1 * a01) + wz1 * (wy0 * a10 + wy1 * a11);
 }
 
+// The single-grid passes of the cycle walk x-rows: each warp takes one (j, k)
+// row at a time, its lanes the row's nodes (coalesced, one division per row).
 // down: t = (1 - omega) r + (omega / 6) sum_nb r on one level.
 template <typename T>
 __global__ void __launch_bounds__(256) mg_down_kernel(MgLevel d, const T* __restrict__ r, T* __restrict__ t,
                                                       T omega, const CgScalars* sc) {
   if (sc->done) return;
-  const long long plane = (long long)d.n1 * d.n2, G = plane * d.n3;
+  const long long plane = (long long)d.n1 * d.n2;
+  const int rows = d.n2 * d.n3;
   const T a = T(1) - omega, b = omega / T(6);
-  for (long long idx = (long long)blockIdx.x * 256 + threadIdx.x; idx < G; idx += (long long)gridDim.x * 256) {
-    int i, j, k;
-    mg_ijk(idx, d, i, j, k);
-    t[idx] = a * r[idx] + b * mg_nb_sum(r, i, j, k, d, idx, plane);
+  const int lane = threadIdx.x & 31;
+  for (int row = blockIdx.x * 8 + (threadIdx.x >> 5); row < rows; row += gridDim.x * 8) {
+    const int k = row / d.n2, j = row - k * d.n2;
+    const long long o = (long long)row * d.n1;
+    for (int i = lane; i < d.n1; i += 32) t[o + i] = a * r[o + i] + b * mg_nb_sum(r, i, j, k, d, o + i, plane);
   }
 }
 
@@ -1325,11 +1636,12 @@ template <typename T>
 __global__ void __launch_bounds__(256) mg_restrict_kernel(MgLevel f, MgLevel c, const T* __restrict__ t,
                                                           T* __restrict__ rc, const CgScalars* sc) {
   if (sc->done) return;
-  const long long Gc = (long long)c.n1 * c.n2 * c.n3;
-  for (long long idx = (long long)blockIdx.x * 256 + threadIdx.x; idx < Gc; idx += (long long)gridDim.x * 256) {
-    int I, J, K;
-    mg_ijk(idx, c, I, J, K);
-    rc[idx] = mg_restrict_at(t, f, I, J, K);
+  const int rows = c.n2 * c.n3;
+  const int lane = threadIdx.x & 31;
+  for (int row = blockIdx.x * 8 + (threadIdx.x >> 5); row < rows; row += gridDim.x * 8) {
+    const int K = row / c.n2, J = row - K * c.n2;
+    const long long o = (long long)row * c.n1;
+    for (int I = lane; I < c.n1; I += 32) rc[o + I] = mg_restrict_at(t, f, I, J, K);
   }
 }
 
@@ -1350,11 +1662,12 @@ __global__ void __launch_bounds__(256) mg_prolong_kernel(MgLevel f, MgLevel c, c
                                                          const T* __restrict__ ec, T* __restrict__ y, T s,
                                                          const CgScalars* sc) {
   if (sc->done) return;
-  const long long G = (long long)f.n1 * f.n2 * f.n3;
-  for (long long idx = (long long)blockIdx.x * 256 + threadIdx.x; idx < G; idx += (long long)gridDim.x * 256) {
-    int i, j, k;
-    mg_ijk(idx, f, i, j, k);
-    y[idx] = s * r[idx] + mg_prolong_at(ec, c, i, j, k);
+  const int rows = f.n2 * f.n3;
+  const int lane = threadIdx.x & 31;
+  for (int row = blockIdx.x * 8 + (threadIdx.x >> 5); row < rows; row += gridDim.x * 8) {
+    const int k = row / f.n2, j = row - k * f.n2;
+    const long long o = (long long)row * f.n1;
+    for (int i = lane; i < f.n1; i += 32) y[o + i] = s * r[o + i] + mg_prolong_at(ec, c, i, j, k);
   }
 }
 
@@ -1365,21 +1678,175 @@ __global__ void __launch_bounds__(256) mg_up_kernel(MgLevel d, const T* __restri
                                                     T* __restrict__ z, T omega, T s, CgScalars* sc, RedBuf red) {
   __shared__ double smem[256 / 32];
   if (sc->done) return;
-  const long long plane = (long long)d.n1 * d.n2, G = plane * d.n3;
+  const long long plane = (long long)d.n1 * d.n2;
+  const int rows = d.n2 * d.n3;
   const T a = T(1) - omega, b = omega / T(6);
+  const int lane = threadIdx.x & 31;
   DotAcc<T> acc;
-  for (long long idx = (long long)blockIdx.x * 256 + threadIdx.x; idx < G; idx += (long long)gridDim.x * 256) {
-    int i, j, k;
-    mg_ijk(idx, d, i, j, k);
-    const T ri = r[idx];
-    const T zi = a * y[idx] + s * ri + b * mg_nb_sum(y, i, j, k, d, idx, plane);
-    z[idx] = zi;
-    if constexpr (DOT) acc.add(ri, zi);
+  for (int row = blockIdx.x * 8 + (threadIdx.x >> 5); row < rows; row += gridDim.x * 8) {
+    const int k = row / d.n2, j = row - k * d.n2;
+    const long long o = (long long)row * d.n1;
+    for (int i = lane; i < d.n1; i += 32) {
+      const T ri = r[o + i];
+      const T zi = a * y[o + i] + s * ri + b * mg_nb_sum(y, i, j, k, d, o + i, plane);
+      z[o + i] = zi;
+      if constexpr (DOT) acc.add(ri, zi);
+    }
   }
   if constexpr (DOT) {
     double v[1] = {acc.value()};
     MgFin fin{sc};
     grid_sum<1, 256>(v, smem, red, gridDim.x, blockIdx.x, threadIdx.x, fin);
+  }
+}
+
+// Fused passes of one level (the single-solve V-cycle): each block works on a
+// 3-D tile through shared memory, so the smoothed residual t and the
+// prolongated correction y never go to global memory and a level costs two
+// launches instead of four.  The arithmetic, and its order, are those of the
+// separate passes above (zero-filled out-of-grid values add exact zeros).
+//
+// down + restrict: r_c = R t with t = (1 - omega) r + (omega / 6) sum_nb r, for
+// a tile of MgDR::CX x CY x CZ coarse nodes: r on the fine nodes 2 I0 - 1 ..
+// 2 (I0 + C) + 1 of each axis, t on 2 I0 .. 2 (I0 + C), both in shared memory.
+template <typename T>
+struct MgDR {  // at most 48 KB of static shared memory: 39.6 KB in FP32, 31.8 KB in FP64
+  static constexpr int CX = sizeof(T) == 4 ? 16 : 8, CY = 8, CZ = sizeof(T) == 4 ? 3 : 2;
+  static constexpr int TX = 2 * CX + 1, TY = 2 * CY + 1, TZ = 2 * CZ + 1;
+  static constexpr int RX = TX + 2, RY = TY + 2, RZ = TZ + 2;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) mg_down_restrict_kernel(MgLevel f, MgLevel c, const T* __restrict__ r,
+                                                               T* __restrict__ rc, T omega, const CgScalars* sc) {
+  using D = MgDR<T>;
+  __shared__ T rs[D::RZ * D::RY * D::RX];
+  __shared__ T ts[D::TZ * D::TY * D::TX];
+  if (sc->done) return;
+  const int I0 = blockIdx.x * D::CX, J0 = blockIdx.y * D::CY, K0 = blockIdx.z * D::CZ;
+  const int fx0 = 2 * I0 - 1, fy0 = 2 * J0 - 1, fz0 = 2 * K0 - 1;
+  for (int q = threadIdx.x; q < D::RX * D::RY * D::RZ; q += 256) {
+    const int x = q % D::RX, yz = q / D::RX, y = yz % D::RY, z = yz / D::RY;
+    const int gx = fx0 + x, gy = fy0 + y, gz = fz0 + z;
+    T v = T(0);
+    if (gx >= 0 && gx < f.n1 && gy >= 0 && gy < f.n2 && gz >= 0 && gz < f.n3)
+      v = r[((long long)gz * f.n2 + gy) * f.n1 + gx];
+    rs[q] = v;
+  }
+  __syncthreads();
+  const T a = T(1) - omega, b = omega / T(6);
+  constexpr int SY = D::RX, SZ = D::RX * D::RY;
+  for (int q = threadIdx.x; q < D::TX * D::TY * D::TZ; q += 256) {
+    const int x = q % D::TX, yz = q / D::TX, y = yz % D::TY, z = yz / D::TY;
+    T v = T(0);
+    if (fx0 + 1 + x < f.n1 && fy0 + 1 + y < f.n2 && fz0 + 1 + z < f.n3) {
+      const int o = (z + 1) * SZ + (y + 1) * SY + (x + 1);
+      v = a * rs[o] + b * (rs[o - 1] + rs[o + 1] + rs[o - SY] + rs[o + SY] + rs[o - SZ] + rs[o + SZ]);
+    }
+    ts[q] = v;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < D::CX * D::CY * D::CZ; q += 256) {
+    const int x = q % D::CX, yz = q / D::CX, y = yz % D::CY, z = yz / D::CY;
+    const int I = I0 + x, J = J0 + y, K = K0 + z;
+    if (I >= c.n1 || J >= c.n2 || K >= c.n3) continue;
+    T acc = T(0);
+#pragma unroll
+    for (int dk = 0; dk < 3; ++dk) {
+      const T wz = dk == 1 ? T(0.5) : T(0.25);
+#pragma unroll
+      for (int dj = 0; dj < 3; ++dj) {
+        const T wy = dj == 1 ? T(0.5) : T(0.25);
+        const T* row = ts + (2 * z + dk) * D::TY * D::TX + (2 * y + dj) * D::TX + 2 * x;
+        const T sx = T(0.25) * row[0] + T(0.5) * row[1] + T(0.25) * row[2];
+        acc += wz * wy * sx;
+      }
+    }
+    rc[((long long)K * c.n2 + J) * c.n1 + I] = acc;
+  }
+}
+
+// prolong + up: y = s r + P e_c on a tile of MgPU::FX x FY x FZ fine nodes and
+// a one-node halo, then z = (1 - omega) y + s r + (omega / 6) sum_nb y on the
+// tile; on the finest level (DOT) also r.z and the PCG scalars.
+template <typename T>
+struct MgPU {
+  static constexpr int FX = 32, FY = 8, FZ = sizeof(T) == 4 ? 8 : 4;
+  static constexpr int YX = FX + 2, YY = FY + 2, YZ = FZ + 2;          // y and r: fine x0 - 1 .. x0 + FX
+  static constexpr int EX = FX / 2 + 2, EY = FY / 2 + 2, EZ = FZ / 2 + 2;  // coarse x0/2 - 1 .. x0/2 + FX/2
+};
+
+template <typename T, bool DOT>
+__global__ void __launch_bounds__(256) mg_prolong_up_kernel(MgLevel f, MgLevel c, const T* __restrict__ r,
+                                                            const T* __restrict__ ec, T* __restrict__ z, T omega,
+                                                            T s, CgScalars* sc, RedBuf red) {
+  using D = MgPU<T>;
+  __shared__ T rs[D::YZ * D::YY * D::YX];
+  __shared__ T ys[D::YZ * D::YY * D::YX];
+  __shared__ T es[D::EZ * D::EY * D::EX];
+  __shared__ double smem[256 / 32];
+  if (sc->done) return;
+  const int x0 = blockIdx.x * D::FX, y0 = blockIdx.y * D::FY, z0 = blockIdx.z * D::FZ;
+  const int cx0 = x0 / 2 - 1, cy0 = y0 / 2 - 1, cz0 = z0 / 2 - 1;
+  for (int q = threadIdx.x; q < D::EX * D::EY * D::EZ; q += 256) {
+    const int x = q % D::EX, yz = q / D::EX, y = yz % D::EY, zz = yz / D::EY;
+    const int gx = cx0 + x, gy = cy0 + y, gz = cz0 + zz;
+    T v = T(0);
+    if (gx >= 0 && gx < c.n1 && gy >= 0 && gy < c.n2 && gz >= 0 && gz < c.n3)
+      v = ec[((long long)gz * c.n2 + gy) * c.n1 + gx];
+    es[q] = v;
+  }
+  for (int q = threadIdx.x; q < D::YX * D::YY * D::YZ; q += 256) {
+    const int x = q % D::YX, yz = q / D::YX, y = yz % D::YY, zz = yz / D::YY;
+    const int gx = x0 - 1 + x, gy = y0 - 1 + y, gz = z0 - 1 + zz;
+    T v = T(0);
+    if (gx >= 0 && gx < f.n1 && gy >= 0 && gy < f.n2 && gz >= 0 && gz < f.n3)
+      v = r[((long long)gz * f.n2 + gy) * f.n1 + gx];
+    rs[q] = v;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < D::YX * D::YY * D::YZ; q += 256) {
+    const int x = q % D::YX, yz = q / D::YX, y = yz % D::YY, zz = yz / D::YY;
+    const int gx = x0 - 1 + x, gy = y0 - 1 + y, gz = z0 - 1 + zz;
+    T v = T(0);
+    if (gx >= 0 && gx < f.n1 && gy >= 0 && gy < f.n2 && gz >= 0 && gz < f.n3) {
+      int ax0, ax1, ay0, ay1, az0, az1;
+      T wx0, wx1, wy0, wy1, wz0, wz1;
+      mg_axis(gx, c.n1, ax0, ax1, wx0, wx1);
+      mg_axis(gy, c.n2, ay0, ay1, wy0, wy1);
+      mg_axis(gz, c.n3, az0, az1, wz0, wz1);
+      const T* r00 = es + ((az0 - cz0) * D::EY + (ay0 - cy0)) * D::EX - cx0;
+      const T* r01 = es + ((az0 - cz0) * D::EY + (ay1 - cy0)) * D::EX - cx0;
+      const T* r10 = es + ((az1 - cz0) * D::EY + (ay0 - cy0)) * D::EX - cx0;
+      const T* r11 = es + ((az1 - cz0) * D::EY + (ay1 - cy0)) * D::EX - cx0;
+      const T a00 = wx0 * r00[ax0] + wx1 * r00[ax1];
+      const T a01 = wx0 * r01[ax0] + wx1 * r01[ax1];
+      const T a10 = wx0 * r10[ax0] + wx1 * r10[ax1];
+      const T a11 = wx0 * r11[ax0] + wx1 * r11[ax1];
+      v = s * rs[q] + (wz0 * (wy0 * a00 + wy1 * a01) + wz1 * (wy0 * a10 + wy1 * a11));
+    }
+    ys[q] = v;
+  }
+  __syncthreads();
+  const T a = T(1) - omega, b = omega / T(6);
+  constexpr int SY = D::YX, SZ = D::YX * D::YY;
+  DotAcc<T> acc;
+  for (int q = threadIdx.x; q < D::FX * D::FY * D::FZ; q += 256) {
+    const int x = q % D::FX, yz = q / D::FX, y = yz % D::FY, zz = yz / D::FY;
+    const int gx = x0 + x, gy = y0 + y, gz = z0 + zz;
+    if (gx >= f.n1 || gy >= f.n2 || gz >= f.n3) continue;
+    const int o = (zz + 1) * SZ + (y + 1) * SY + (x + 1);
+    const T ri = rs[o];
+    const T zi = a * ys[o] + s * ri + b * (ys[o - 1] + ys[o + 1] + ys[o - SY] + ys[o + SY] + ys[o - SZ] + ys[o + SZ]);
+    z[((long long)gz * f.n2 + gy) * f.n1 + gx] = zi;
+    if constexpr (DOT) acc.add(ri, zi);
+  }
+  if constexpr (DOT) {
+    double v[1] = {acc.value()};
+    MgFin fin{sc};
+    const int nb = gridDim.x * gridDim.y * gridDim.z;
+    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    grid_sum<1, 256>(v, smem, red, nb, bid, threadIdx.x, fin);
   }
 }
 
@@ -1629,10 +2096,15 @@ __global__ void __launch_bounds__(256) normalise_kernel(long long G, T* u, const
 }
 
 // phi64 += e; e = 0 (folds a round's FP32 correction into the FP64 potential).
-static __global__ void __launch_bounds__(256) fold_kernel(long long G, double* phi64, float* e) {
+static __global__ void __launch_bounds__(256) fold_kernel(long long G, double* phi64, float* e, float2* phi2) {
   for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < G; i += (long long)gridDim.x * 256) {
-    phi64[i] += (double)e[i];
+    const double v = phi64[i] + (double)e[i];
+    phi64[i] = v;
     e[i] = 0.0f;
+    if (phi2) {
+      const float hi = (float)v;
+      phi2[i] = make_float2(hi, (float)(v - (double)hi));
+    }
   }
 }
 
@@ -2046,65 +2518,6 @@ __device__ __forceinline__ int tile_atoms(const AtomArgs& A, int a0, double cx, 
   return total;
 }
 
-// b = sum_J -(1/4 pi) L_h V_J inside r_c (Sec. 4) and the self-energy partial
-// sums (1/2) h^3 b_J V_J, gathered per node over the atoms near its tile.
-template <typename T, int R>
-__global__ void __launch_bounds__(512) pseudocharge_kernel(GridDev g, AtomArgs A, Weights<double> W,
-                                                           T* b, double* es_out, RedBuf red) {
-  __shared__ int list[512];
-  __shared__ int warp_cnt[16];
-  __shared__ double smem[512 / 32];
-  const int x = blockIdx.x * AT + threadIdx.x, y = blockIdx.y * AT + threadIdx.y,
-            z = blockIdx.z * AT + threadIdx.z;
-  const int tid = threadIdx.x + AT * (threadIdx.y + AT * threadIdx.z);
-  const bool inside = x < g.n1 && y < g.n2 && z < g.n3;
-  const double half = 0.5 * AT * A.h;
-  const double cx = A.ox + (blockIdx.x * AT) * A.h + half, cy = A.oy + (blockIdx.y * AT) * A.h + half,
-               cz = A.oz + (blockIdx.z * AT) * A.h + half;
-  const double inv_s = 1.0 / A.sigma;
-  double bsum = 0.0, es = 0.0;
-  for (int a0 = 0; a0 < A.M; a0 += 512) {
-    const int cnt = tile_atoms(A, a0, cx, cy, cz, half, A.rc + A.h, list, warp_cnt);
-    if (inside) {
-      for (int t = 0; t < cnt; ++t) {
-        const int J = list[t];
-        const double rx = node_off(A.ox, x, A.h, A.R[3 * J]), ry = node_off(A.oy, y, A.h, A.R[3 * J + 1]),
-                     rz = node_off(A.oz, z, A.h, A.R[3 * J + 2]);
-        const double r = dist3(rx, ry, rz);
-        if (!(r < A.rc)) continue;
-        const double ZJ = A.Z[J];
-        const double vc = gauss_v(ZJ, inv_s, r);
-        double lap = W.c * vc;
-#pragma unroll
-        for (int p = 1; p <= R; ++p) {
-          const double ph = p * A.h;
-          double sum = 0.0;
-          sum += gauss_v(ZJ, inv_s, sqrt((rx + ph) * (rx + ph) + ry * ry + rz * rz));
-          sum += gauss_v(ZJ, inv_s, sqrt((rx - ph) * (rx - ph) + ry * ry + rz * rz));
-          sum += gauss_v(ZJ, inv_s, sqrt(rx * rx + (ry + ph) * (ry + ph) + rz * rz));
-          sum += gauss_v(ZJ, inv_s, sqrt(rx * rx + (ry - ph) * (ry - ph) + rz * rz));
-          sum += gauss_v(ZJ, inv_s, sqrt(rx * rx + ry * ry + (rz + ph) * (rz + ph)));
-          sum += gauss_v(ZJ, inv_s, sqrt(rx * rx + ry * ry + (rz - ph) * (rz - ph)));
-          lap = fma(W.w[p], sum, lap);
-        }
-        const double bj = -lap / (4.0 * kPi);
-        bsum += bj;
-        es += bj * vc;
-      }
-    }
-    __syncthreads();
-  }
-  if (inside) b[lin(g, x, y, z)] = (T)bsum;
-  double acc[1] = {es};
-  struct Fin {
-    double* out;
-    __device__ void operator()(double* t) const { out[0] = t[0]; }
-  } fin{es_out};
-  const int nb = gridDim.x * gridDim.y * gridDim.z;
-  const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-  grid_sum<1, 512>(acc, smem, red, nb, bid, tid, fin);
-}
-
 // rho_0 = sum_J Z_J (2 pi s^2)^{-3/2} exp(-r^2/(2 s^2)) (r < cut); writes
 // sqrt(rho_0) and reduces sum rho_0 (starting guess, Sec. 4).
 template <typename T>
@@ -2152,20 +2565,81 @@ struct AtomBox {
   int dim[3];
 };
 
-// V_J tabulated on the atom's box grown by 2R (forces, paper form): vbox[a][...].
+// V_J tabulated on the atom's box grown by 2R: vbox[a][...].  Only nodes within
+// r_c + R h of the atom are ever read (the stencil neighbours of the nodes of its
+// ball, where b_J is nonzero), so V_J is evaluated there only and the rest of
+// the cube holds 0.
 static __global__ void __launch_bounds__(256) force_vbox_kernel(AtomArgs A, int a0, int na, int vdim, int R,
                                                          const int* __restrict__ lo, double* vbox) {
   const long long per = (long long)vdim * vdim * vdim;
+  const double reach = A.rc + R * A.h + 1e-9 * (A.rc + A.h);
   for (long long t = (long long)blockIdx.x * 256 + threadIdx.x; t < per * na; t += (long long)gridDim.x * 256) {
     const int a = (int)(t / per);
     const long long e = t - (long long)a * per;
     const int i = (int)(e % vdim), j = (int)((e / vdim) % vdim), k = (int)(e / ((long long)vdim * vdim));
     const int J = a0 + a;
-    const double px = A.ox + (lo[3 * a] - 2 * R + i + 0.5) * A.h - A.R[3 * J];
-    const double py = A.oy + (lo[3 * a + 1] - 2 * R + j + 0.5) * A.h - A.R[3 * J + 1];
-    const double pz = A.oz + (lo[3 * a + 2] - 2 * R + k + 0.5) * A.h - A.R[3 * J + 2];
-    vbox[t] = gauss_v(A.Z[J], 1.0 / A.sigma, sqrt(px * px + py * py + pz * pz));
+    const double px = node_off(A.ox, lo[3 * a] - 2 * R + i, A.h, A.R[3 * J]);
+    const double py = node_off(A.oy, lo[3 * a + 1] - 2 * R + j, A.h, A.R[3 * J + 1]);
+    const double pz = node_off(A.oz, lo[3 * a + 2] - 2 * R + k, A.h, A.R[3 * J + 2]);
+    const double r = dist3(px, py, pz);
+    vbox[t] = (r <= reach) ? gauss_v(A.Z[J], 1.0 / A.sigma, r) : 0.0;
   }
+}
+
+// Pseudocharge from the atoms' tables (S1): for every node of a tile, the atoms
+// of [a0, a0 + na) (na <= 512) whose ball can reach the tile, in atom order,
+// add b_J (bbox, -(1/4 pi) L_h V_J inside r_c, 0 outside) to the node's running
+// FP64 sum (bacc, carried across launches of successive atom ranges) and
+// b_J V_J to the self-energy sum (added into es_out[0]).  The last range writes
+// b in the field type.
+template <typename T>
+__global__ void __launch_bounds__(512) pseudocharge_gather_kernel(GridDev g, AtomArgs A, int a0, int na, int box,
+                                                                  int bdim, int vdim, int R,
+                                                                  const int* __restrict__ lo,
+                                                                  const double* __restrict__ vbox,
+                                                                  const double* __restrict__ bbox, double* bacc,
+                                                                  int first, int last, T* b, double* es_out,
+                                                                  RedBuf red) {
+  __shared__ int list[512];
+  __shared__ int warp_cnt[16];
+  __shared__ double smem[512 / 32];
+  const int x = blockIdx.x * AT + threadIdx.x, y = blockIdx.y * AT + threadIdx.y,
+            z = blockIdx.z * AT + threadIdx.z;
+  const int tid = threadIdx.x + AT * (threadIdx.y + AT * threadIdx.z);
+  const bool inside = x < g.n1 && y < g.n2 && z < g.n3;
+  const double half = 0.5 * AT * A.h;
+  const double cx = A.ox + (blockIdx.x * AT) * A.h + half, cy = A.oy + (blockIdx.y * AT) * A.h + half,
+               cz = A.oz + (blockIdx.z * AT) * A.h + half;
+  AtomArgs Ar = A;
+  Ar.M = a0 + na;  // the list covers this range only
+  const int cnt = tile_atoms(Ar, a0, cx, cy, cz, half, A.rc + A.h, list, warp_cnt);
+  const long long bper = (long long)bdim * bdim * bdim, vper = (long long)vdim * vdim * vdim;
+  double es = 0.0;
+  if (inside) {
+    const long long node = lin(g, x, y, z);
+    double bsum = first ? 0.0 : bacc[node];
+    for (int t = 0; t < cnt; ++t) {
+      const int a = list[t] - a0;
+      const int ix = x - lo[3 * a], iy = y - lo[3 * a + 1], iz = z - lo[3 * a + 2];
+      if (ix < 0 || iy < 0 || iz < 0 || ix >= box || iy >= box || iz >= box) continue;
+      const double bj = bbox[a * bper + (ix + R) + (long long)bdim * ((iy + R) + (long long)bdim * (iz + R))];
+      if (bj == 0.0) continue;
+      bsum += bj;
+      es += bj * vbox[a * vper + (ix + 2 * R) + (long long)vdim * ((iy + 2 * R) + (long long)vdim * (iz + 2 * R))];
+    }
+    if (last)
+      b[node] = (T)bsum;
+    else
+      bacc[node] = bsum;
+  }
+  double acc[1] = {es};
+  struct Fin {
+    double* out;
+    __device__ void operator()(double* t) const { out[0] += t[0]; }
+  } fin{es_out};
+  const int nb = gridDim.x * gridDim.y * gridDim.z;
+  const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  grid_sum<1, 512>(acc, smem, red, nb, bid, tid, fin);
 }
 
 // b_J on the atom's box grown by R: -(1/4 pi) L_h V_J inside r_c, 0 outside.

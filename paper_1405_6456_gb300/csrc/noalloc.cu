@@ -23,25 +23,51 @@ constexpr long long kScratchBytes = 3 * kVecBytes + kPartialsBytes + 256 + 256;
 static __device__ __align__(256) unsigned char noalloc_scratch[kScratchBytes];
 
 std::mutex g_mutex;
-void* g_addr[256] = {nullptr};
+
+// Per-device set-up, done once by the first call on each device: the array's
+// device address, the SM count (launch split) and the dynamic shared-memory
+// limits of the kernels this entry point launches (a per-device attribute).
+struct DevSetup {
+  void* addr = nullptr;
+  int sms = 0;
+};
+DevSetup g_dev[256];
+
+template <int R>
+cudaError_t set_smem_attrs() {
+  cudaError_t e = cudaFuncSetAttribute(zstream_kernel<double, R, 1, LoadPlain<double>, EpiResidual<double>>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       zsmem_bytes<double, R, 1, EpiResidual<double>>());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(zstream_kernel<double, R, 1, LoadPlain<double>, EpiCgA<double>>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, zsmem_bytes<double, R, 1, EpiCgA<double>>());
+}
 
 int fail_na(const char* msg) {
   fprintf(stderr, "[ofdft_poisson_noalloc] %s\n", msg);
   return OFDFT_EINVAL;
 }
 
-// Device address of the array on the current device (set up once per device).
-int scratch_address(void** out) {
+// The current device's set-up (performed on its first call).
+int device_setup(DevSetup* out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return OFDFT_ECUDA;
   std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_addr[dev]) {
+  DevSetup& d = g_dev[dev];
+  if (!d.addr) {
     void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, noalloc_scratch);
-    if (e != cudaSuccess || !p) return OFDFT_ECUDA;
-    g_addr[dev] = p;
+    if (cudaGetSymbolAddress(&p, noalloc_scratch) != cudaSuccess || !p) return OFDFT_ECUDA;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+      return OFDFT_ECUDA;
+    if (set_smem_attrs<1>() != cudaSuccess || set_smem_attrs<2>() != cudaSuccess ||
+        set_smem_attrs<3>() != cudaSuccess || set_smem_attrs<4>() != cudaSuccess ||
+        set_smem_attrs<5>() != cudaSuccess || set_smem_attrs<6>() != cudaSuccess)
+      return OFDFT_ECUDA;
+    d.sms = sms;
+    d.addr = p;
   }
-  *out = g_addr[dev];
+  *out = d;
   return OFDFT_OK;
 }
 
@@ -49,8 +75,6 @@ template <int R>
 cudaError_t launch_stencil_pass(dim3 grid, int zchunk, const GridDev& g, const Weights<double>& W,
                                 const double* f, EpiResidual<double> ep, RedBuf red, cudaStream_t s) {
   constexpr int smem = zsmem_bytes<double, R, 1, EpiResidual<double>>();
-  cudaFuncSetAttribute(zstream_kernel<double, R, 1, LoadPlain<double>, EpiResidual<double>>,
-                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   zstream_kernel<double, R, 1, LoadPlain<double>, EpiResidual<double>>
       <<<grid, dim3(BX, BY), smem, s>>>(g, W, zchunk, LoadPlain<double>{f}, ep, red);
   return cudaGetLastError();
@@ -68,10 +92,10 @@ extern "C" int ofdft_poisson_noalloc(const ofdft_grid* gr, int fd_order, const d
   if (fd_order < 2 || fd_order > 2 * kMaxR || (fd_order & 1)) return fail_na("fd_order must be even in [2, 12]");
   if (!(tol > 0.0) || max_it < 0 || !(gr->h > 0.0)) return fail_na("need tol > 0, max_it >= 0, h > 0");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-  void* base = nullptr;
-  int rc = scratch_address(&base);
+  DevSetup dv;
+  int rc = device_setup(&dv);
   if (rc != OFDFT_OK) return rc;
-  char* p = static_cast<char*>(base);
+  char* p = static_cast<char*>(dv.addr);
   double* r = reinterpret_cast<double*>(p);
   double* pv = reinterpret_cast<double*>(p + kVecBytes);
   double* qv = reinterpret_cast<double*>(p + 2 * kVecBytes);
@@ -84,9 +108,9 @@ extern "C" int ofdft_poisson_noalloc(const ofdft_grid* gr, int fd_order, const d
   const GridDev g{gr->n[0], gr->n[1], gr->n[2], G};
   const int R = fd_order / 2;
   const Weights<double> W = lap_weights(R, gr->h, 1.0), Wneg = lap_weights(R, gr->h, -1.0);
-  // launch shape of the library's single-grid passes (152 SMs assumed for the split)
+  // launch shape of the library's single-grid passes: about four blocks per SM
   const int gx = (g.n1 + BX - 1) / BX, gy = (g.n2 + ZCfg<double>::TY - 1) / ZCfg<double>::TY;
-  int nz = std::max(1, (608 + gx * gy - 1) / (gx * gy));
+  int nz = std::max(1, (4 * dv.sms + gx * gy - 1) / (gx * gy));
   nz = std::min(nz, std::max(1, g.n3 / std::max(2 * R, 4)));
   const int zc = (g.n3 + nz - 1) / nz;
   nz = (g.n3 + zc - 1) / zc;
@@ -116,8 +140,6 @@ extern "C" int ofdft_poisson_noalloc(const ofdft_grid* gr, int fd_order, const d
 #define NA_CG(RR)                                                                                                \
   case RR: {                                                                                                     \
     constexpr int smem = zsmem_bytes<double, RR, 1, EpiCgA<double>>();                                         \
-    cudaFuncSetAttribute(zstream_kernel<double, RR, 1, LoadPlain<double>, EpiCgA<double>>,                     \
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);                                     \
     zstream_kernel<double, RR, 1, LoadPlain<double>, EpiCgA<double>>                                             \
         <<<zgrid, dim3(BX, BY), smem, s>>>(g, cast_weights<double>(Wneg), zc, LoadPlain<double>{r},             \
                                           EpiCgA<double>{pv, qv, sc}, red);                                      \

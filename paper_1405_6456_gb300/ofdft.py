@@ -107,6 +107,20 @@ class RelaxStats(C.Structure):
                 ("energy", C.c_double), ("converged", C.c_int)]
 
 
+class BatchStats(C.Structure):
+    _fields_ = [("rounds", C.c_longlong), ("graph_captures", C.c_longlong), ("graph_replays", C.c_longlong),
+                ("graph_iterations", C.c_longlong), ("eager_iterations", C.c_longlong), ("z_depth", C.c_int),
+                ("z_tuned", C.c_int), ("tune_candidates", C.c_int), ("tune_depth", C.c_int * 8),
+                ("tune_us", C.c_double * 8)]
+
+    def as_dict(self):
+        n = self.tune_candidates
+        return {"rounds": self.rounds, "graph_captures": self.graph_captures,
+                "graph_replays": self.graph_replays, "graph_iterations": self.graph_iterations,
+                "eager_iterations": self.eager_iterations, "z_depth": self.z_depth, "z_tuned": self.z_tuned,
+                "tuning_us_by_depth": {int(self.tune_depth[i]): round(float(self.tune_us[i]), 2) for i in range(n)}}
+
+
 _lib = None
 
 
@@ -159,6 +173,7 @@ def lib():
     L.ofdft_batch_run.argtypes = [vp]
     L.ofdft_batch_bytes.argtypes = [C.POINTER(Grid), ip]
     L.ofdft_batch_bytes.restype = C.c_longlong
+    L.ofdft_batch_info.argtypes = [vp, C.POINTER(BatchStats)]
     L.ofdft_mg_plan.argtypes = [C.POINTER(Grid), ip, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                 C.POINTER(C.c_int), C.POINTER(C.c_longlong)]
     L.ofdft_workspace_bytes.argtypes = [C.POINTER(Grid), ip, ip]
@@ -419,6 +434,13 @@ class Batch:
     def run(self):
         self.ctx._check(self.ctx._lib.ofdft_batch_run(self.h), "ofdft_batch_run")
 
+    def info(self) -> dict:
+        """Launch statistics: rounds, CG loop graphs captured and replayed, the
+        autotuned z-tile depth and its timings (ofdft_batch_info)."""
+        st = BatchStats()
+        self.ctx._check(self.ctx._lib.ofdft_batch_info(self.h, C.byref(st)), "ofdft_batch_info")
+        return st.as_dict()
+
 
 def batch_bytes(g: Grid, prec: int) -> int:
     return int(lib().ofdft_batch_bytes(C.byref(g), prec))
@@ -449,5 +471,5 @@ def exported_symbols():
             "ofdft_workspace_bytes", "ofdft_profile", "ofdft_get_counters", "ofdft_reset_counters",
             "ofdft_set_poisson_precond", "ofdft_mg_plan",
             "ofdft_batch_create", "ofdft_batch_destroy", "ofdft_batch_submit", "ofdft_batch_step",
-            "ofdft_batch_poll", "ofdft_batch_run", "ofdft_batch_bytes"]
+            "ofdft_batch_poll", "ofdft_batch_run", "ofdft_batch_bytes", "ofdft_batch_info"]
 

@@ -51,7 +51,8 @@ def test_binding_struct_layouts_match_the_library(lib):
     lib.ofdft_struct_bytes.argtypes = [ctypes.c_char_p]
     for name, cls in [("ofdft_grid", F.Grid), ("ofdft_params", F.Params), ("ofdft_cg_stats", F.CgStats),
                       ("ofdft_energy", F.Energy), ("ofdft_solve_stats", F.SolveStats),
-                      ("ofdft_counters", F.Counters), ("ofdft_relax_stats", F.RelaxStats)]:
+                      ("ofdft_counters", F.Counters), ("ofdft_relax_stats", F.RelaxStats),
+                      ("ofdft_batch_stats", F.BatchStats)]:
         assert lib.ofdft_struct_bytes(name.encode()) == ctypes.sizeof(cls), name
     assert lib.ofdft_struct_bytes(b"nothing") == -1
     p = F.default_params()

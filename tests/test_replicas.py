@@ -22,7 +22,7 @@ def _worker(rank, ws, port, q):
                       LOCAL_RANK=str(rank))
     import bench
     ws_, r, local, pg = bench.dist_setup(backend="gloo")
-    c = bench.replica_cluster(r, ws_)
+    c = bench.replica_cluster("fcc8", r, ws_)
     local_seconds = 1.0 + r  # rank 1 is the slower one
     rate, slowest = bench.job_rate(pg, ws_, 3, local_seconds, "cpu")
     bench.barrier(pg)
@@ -44,7 +44,7 @@ def test_two_gloo_replicas_take_distinct_clusters_and_the_slowest_time():
     out.sort()
     assert [o[0] for o in out] == [0, 1] and all(o[1] == 2 for o in out)
     assert out[0][2] != out[1][2]  # independent seeded clusters
-    assert out[0][3] == out[1][3] == 666
+    assert out[0][3] == out[1][3] == 2457  # the 8x8x8-cell workload of the benchmark
     for o in out:
         assert o[5] == 2.0  # max over ranks
         assert o[4] == pytest.approx(2 * 3 / 2.0)
