@@ -320,6 +320,7 @@ typedef struct {
   long long timed_launches[OFDFT_K_COUNT]; /* launches bracketed by CUDA events */
   double timed_ms[OFDFT_K_COUNT];          /* summed event durations (ms) */
   long long persistent_cg_iters;           /* CG iterations run by OFDFT_K_CG_PERSISTENT launches */
+  long long tma_launches;                  /* z-streaming passes whose planes were staged by TMA */
 } ofdft_counters;
 
 /* Tracing (no counterpart in the paper, which reports wall time and counts of

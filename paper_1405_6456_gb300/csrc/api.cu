@@ -1026,6 +1026,13 @@ struct Solver {
     TRY(direction(0.0));  // d = s
     double delta_new = e.rs_pc;
     int k = 0;
+    // stall detection: iterations in a row in which L fell by no more than its
+    // rounding resolution and h^3 r.s reached no new low.  A mixed-precision
+    // solve near its FP32 floor can cycle there between two iterates without
+    // ever meeting tol_inner; three such iterations end the loop (counted as
+    // converged in MIXED, where that floor is the precision's resolution)
+    double L_best = e.L, rs_best = e.rs;
+    int stalled = 0;
     for (int it = 0; it < p->max_nlcg; ++it) {
       if (e.rs < tol_in) {
         *converged = 1;
@@ -1106,6 +1113,17 @@ struct Solver {
         k = 0;
       } else {
         TRY(direction(beta));
+      }
+      if (e.L < L_best - l_resolution(e, mixed) || e.rs < rs_best)
+        stalled = 0;
+      else
+        ++stalled;
+      L_best = std::min(L_best, e.L);
+      rs_best = std::min(rs_best, e.rs);
+      if (stalled >= 3 && e.rs >= tol_in) {
+        if (trace) fprintf(stderr, "[ofdft] nlcg stalled at rs=%.6e (tol %.6e)\n", e.rs, tol_in);
+        if (mixed) *converged = 1;
+        break;
       }
     }
     if (!*converged && e.rs < tol_in) *converged = 1;
@@ -1785,6 +1803,8 @@ int ofdft_create(ofdft_ctx** out, int device, void* stream) {
   if (ms && atoi(ms) >= 1) c->mg_sweeps = atoi(ms);
   const char* cz = getenv("OFDFT_COOP_NZ");  // launch-shape experiments: z-chunks of the persistent CG grid
   c->coop_nz = cz ? atoi(cz) : 0;
+  const char* pdl = getenv("OFDFT_PDL");  // 1: programmatic dependent launch in the CG loop
+  c->pdl = (pdl && pdl[0] == '1') ? 1 : 0;
   const char* tma = getenv("OFDFT_TMA");  // 1: TMA staging in the FP32 z-streaming passes that allow it
   c->tma = (tma && tma[0] == '1') ? 1 : 0;
   const char* cgr = getenv("OFDFT_COND_GRAPHS");  // 0: CG chunks of eight iterations polled by the host
@@ -1859,6 +1879,7 @@ int ofdft_get_counters(ofdft_ctx* c, ofdft_counters* out) {
     out->timed_ms[k] = c->timed_ms[k];
   }
   out->persistent_cg_iters = c->coop_iters;
+  out->tma_launches = c->tma_launches;
   return OFDFT_OK;
 }
 
@@ -1874,6 +1895,7 @@ int ofdft_reset_counters(ofdft_ctx* c) {
     c->timed_ms[k] = 0.0;
   }
   c->coop_iters = 0;
+  c->tma_launches = 0;
   return OFDFT_OK;
 }
 

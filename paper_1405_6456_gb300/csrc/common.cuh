@@ -62,6 +62,21 @@ struct DotAcc<float> {
   __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
+// Programmatic dependent launch (sm_90 and later).  pdl_wait() blocks until
+// every kernel this grid depends on has completed and its memory is visible (a
+// no-op for a grid launched without the programmatic attribute);
+// pdl_launch_dependents() lets the next grid of the stream be scheduled once
+// every block of this one has called it or exited.  Kernels call both first,
+// in that order, so at most two grids overlap and none reads early.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+__device__ __forceinline__ void pdl_enter() {
+  pdl_wait();
+  pdl_launch_dependents();
+}
+
 // Sum K per-thread doubles over the block; the result is valid in thread 0.
 // NT is the block size (a multiple of 32); smem holds K * NT/32 doubles.
 template <int K, int NT>

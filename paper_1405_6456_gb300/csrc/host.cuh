@@ -75,6 +75,7 @@ struct ofdft_ctx {
   int coop = 0;                                // persistent cooperative CG iterations (opt-in)
   unsigned int* coop_bar = nullptr;            // arrival counter of its grid barriers
   long long coop_iters = 0;                    // CG iterations run by it (trace counter)
+  long long tma_launches = 0;                  // z-streaming passes staged by TMA (trace counter)
   int coop_nz = 0;                             // z-chunks of its grid (0: the default rule)
   int precond = 1;                             // Poisson CG preconditioner (OFDFT_PRECOND_*)
   int trace = 0;                               // OFDFT_TRACE=1: diagnostic lines on stderr
@@ -88,6 +89,7 @@ struct ofdft_ctx {
   int cond_graphs = 1;                         // CG loops as one graph with a device-side WHILE node
   int mixed_ff = 0;                            // the last mixed Poisson solve ran the float-float residual pass
   int tma = 0;                                 // FP32 z-streaming passes stage planes by TMA where they can
+  int pdl = 0;                                 // programmatic dependent launch for the CG-loop kernels
 };
 
 namespace ofd {
@@ -423,9 +425,27 @@ inline MgPlan mg_plan(const GridDev& g, double h, size_t es, double omega = kMgO
   return P;
 }
 
-// Launches kern on the context's stream.
+// Launches kern on the context's stream.  With c->pdl the launch allows
+// programmatic dependent launch: the grid may be scheduled while the previous
+// kernel of the stream is still finishing, and holds at pdl_wait() (the first
+// statement of every kernel launched here) until that kernel has completed and
+// its writes are visible; the previous kernel releases it early with
+// pdl_launch_dependents().  Only the launch latency overlaps, never the work.
 template <typename... KArgs, typename... Args>
 cudaError_t launch_k(ofdft_ctx* c, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, Args... args) {
+  if (c->pdl) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = c->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+  }
   kern<<<grid, block, smem, c->stream>>>(args...);
   return cudaGetLastError();
 }
@@ -544,6 +564,7 @@ int launch_zv_tma(ofdft_ctx* c, const GridDev& g, const Weights<double>& W, L ld
       CU(launch_k(c, zstream_tma_kernel<T, R, V, L, E>, s.grid, dim3(BX, BY), smem, mf, mi[0], mi[1], mi[2], g,
                   cast_weights<T>(W), s.zchunk, ld, ep, red(c)));
     }
+    c->tma_launches++;
     *done = true;
     return OFDFT_OK;
   }

@@ -56,6 +56,21 @@ __device__ __forceinline__ float2 ff_mul(float2 w, float2 a) {
   e = fmaf(w.x, a.y, fmaf(w.y, a.x, e));
   return ff_fast_two_sum(p, e);
 }
+// The same without the closing renormalisation: the pair stays an unevaluated
+// sum hi + lo whose lo may exceed ulp(hi) / 2 by the few roundings of the
+// chain it came from.  TwoSum and the FMA product are exact for any operands,
+// so a chain of these keeps the error bound of the normalised forms (a few
+// units of 2^-48 of its terms per operation) while skipping a Fast2Sum per
+// step; the chain's result is renormalised once, with a TwoSum.
+__device__ __forceinline__ float2 ff_add_lazy(float2 a, float2 b) {
+  const float2 s = ff_two_sum(a.x, b.x);
+  return make_float2(s.x, s.y + (a.y + b.y));
+}
+__device__ __forceinline__ float2 ff_mul_lazy(float2 w, float2 a) {
+  const float p = w.x * a.x;
+  const float e = fmaf(w.x, a.x, -p);
+  return make_float2(p, fmaf(w.x, a.y, fmaf(w.y, a.x, e)));
+}
 
 template <typename T>
 __host__ __device__ __forceinline__ T zero_of() { return T(0); }
@@ -77,14 +92,16 @@ struct Lanes<T, 1> {
   __device__ static V make(const T* v) { return v[0]; }
   __device__ static T lane(V v, int) { return v; }
 };
-// float-float values (float2 = hi, lo), one column per thread
+// float-float values (float2 = hi, lo), one column per thread; the stencil's
+// sums run unnormalised (the lazy forms) and the consumer renormalises the
+// result once
 template <>
 struct Lanes<float2, 1> {
   using V = float2;
   __device__ static V ld(const float2* p) { return *p; }
-  __device__ static V add(V a, V b) { return ff_add(a, b); }
-  __device__ static V mul(float2 w, V a) { return ff_mul(w, a); }
-  __device__ static V fma(float2 w, V a, V c) { return ff_add(ff_mul(w, a), c); }
+  __device__ static V add(V a, V b) { return ff_add_lazy(a, b); }
+  __device__ static V mul(float2 w, V a) { return ff_mul_lazy(w, a); }
+  __device__ static V fma(float2 w, V a, V c) { return ff_add_lazy(ff_mul_lazy(w, a), c); }
   __device__ static V make(const float2* v) { return v[0]; }
   __device__ static float2 lane(V v, int) { return v; }
 };
@@ -153,6 +170,7 @@ template <>
 struct FAcc<double> {
   double s = 0.0;
   __device__ __forceinline__ void add(double a, double b) { s += a * b; }
+  __device__ __forceinline__ void add_fast(double a, double b) { s += a * b; }
   __device__ __forceinline__ void add_d(double v) { s += v; }
   __device__ __forceinline__ double value() const { return s; }
 };
@@ -160,6 +178,10 @@ template <>
 struct FAcc<float> {
   DotAcc<float> a;
   __device__ __forceinline__ void add(float x, float y) { a.add(x, y); }
+  // plain FP32 accumulation (one FMA) for sums that only steer the line search
+  // and the stopping tests, where the FP32 relative accuracy of a thread's
+  // partial sum is enough; the pair's low part stays zero
+  __device__ __forceinline__ void add_fast(float x, float y) { a.hi = fmaf(x, y, a.hi); }
   __device__ __forceinline__ void add_d(double v) {
     const float hi = (float)v;
     a.add(hi, 1.0f);
@@ -717,6 +739,7 @@ __global__ void __launch_bounds__(NT, 2) cg_coop_kernel(GridDev g, Weights<T> W,
 template <typename T, int R, int V, class Loader, class Epi>
 __global__ void __launch_bounds__(NT, 2) zstream_kernel(GridDev g, Weights<T> W, int zchunk,
                                                      Loader ld, Epi ep, RedBuf red) {
+  pdl_enter();
   const int z0 = blockIdx.z * zchunk;
   const int z1 = min(z0 + zchunk, g.n3);
   const int nblocks = gridDim.x * gridDim.y * gridDim.z;
@@ -732,6 +755,7 @@ __global__ void __launch_bounds__(NT, 2) zstream_tma_kernel(const __grid_constan
                                                             const __grid_constant__ CUtensorMap tm1,
                                                             const __grid_constant__ CUtensorMap tm2, GridDev g,
                                                             Weights<T> W, int zchunk, Loader ld, Epi ep, RedBuf red) {
+  pdl_enter();
   const int z0 = blockIdx.z * zchunk;
   const int z1 = min(z0 + zchunk, g.n3);
   const int nblocks = gridDim.x * gridDim.y * gridDim.z;
@@ -991,7 +1015,9 @@ struct EpiResidualFF {
   __device__ __forceinline__ bool skip() const { return false; }
   __device__ __forceinline__ void load() {}
   __host__ __device__ __forceinline__ const float2* input(int) const { return nullptr; }
-  __device__ __forceinline__ void apply(long long i, float2 ph, float2 lap, const float2*, Acc* acc) const {
+  __device__ __forceinline__ void apply(long long i, float2 ph, float2 lap_raw, const float2*, Acc* acc) const {
+    // the stencil's float-float sum comes unnormalised (lazy chain): renormalise
+    const float2 lap = ff_two_sum(lap_raw.x, lap_raw.y);
     float2 rr;
     if (rho) {
       rr = make_float2(rho[i], 0.0f);
@@ -1179,12 +1205,15 @@ struct EpiFunctional {
     if (G) G[i] = gx;
     if (s) s[i] = sx;
     if (winv) winv[i] = wv;
-    if (d) acc[5].add(gx, d[i]);
-    if (s_old) acc[6].add(gx, s_old[i]);
-    acc[7].add(gx, -sx);  // g^2 / diag
-    acc[8].add(gx, gx);
-    acc[9].add(uc, sx);
-    acc[10].add(uc, wv);  // u^2 / diag
+    // the gradient sums (line search, Polak-Ribiere beta, stopping test,
+    // rank-one correction) in plain FP32 per thread; the energy sums above stay
+    // compensated
+    if (d) acc[5].add_fast(gx, d[i]);
+    if (s_old) acc[6].add_fast(gx, s_old[i]);
+    acc[7].add_fast(gx, -sx);  // g^2 / diag
+    acc[8].add_fast(gx, gx);
+    acc[9].add_fast(uc, sx);
+    acc[10].add_fast(uc, wv);  // u^2 / diag
   }
   __device__ __forceinline__ void operator()(double* t) const {
 #pragma unroll
@@ -1226,6 +1255,7 @@ __global__ void __launch_bounds__(256) cg_update_kernel(long long G, X* __restri
                                                         T* __restrict__ r, const T* __restrict__ p,
                                                         const T* __restrict__ Ap, CgScalars* sc,
                                                         RedBuf red) {
+  pdl_enter();
   __shared__ double smem[256 / 32];
   DotAcc<T> dacc;
   if constexpr (WIDE) {
@@ -1336,6 +1366,7 @@ __global__ void __launch_bounds__(256) cg_update_kernel(long long G, X* __restri
 template <typename T, bool WIDE = false>
 __global__ void __launch_bounds__(256) cg_update_r_kernel(long long G, T* __restrict__ r, const T* __restrict__ Ap,
                                                           CgScalars* sc, RedBuf red) {
+  pdl_enter();
   __shared__ double smem[256 / 32];
   DotAcc<T> dacc;
   if constexpr (WIDE) {
@@ -1466,12 +1497,13 @@ __global__ void __launch_bounds__(256) refine_replace_kernel(long long G, float*
                                                                     CgScalars* sc, double inner_tol, int budget,
                                                                     int restart, int pc, RedBuf red) {
   __shared__ double smem[256 / 32];
-  double acc[1] = {0.0};
+  DotAcc<float> rr;
   for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < G; i += (long long)gridDim.x * 256) {
     const float v = nearest_float(r64[i]);
     r32[i] = v;
-    acc[0] += (double)v * (double)v;
+    rr.add(v, v);
   }
+  double acc[1] = {rr.value()};
   struct Fin {
     CgScalars* sc;
     double tol;
@@ -1619,6 +1651,7 @@ __device__ __forceinline__ T mg_prolong_at(const T* e, const MgLevel& c, int i, 
 template <typename T>
 __global__ void __launch_bounds__(256) mg_down_kernel(MgLevel d, const T* __restrict__ r, T* __restrict__ t,
                                                       T omega, const CgScalars* sc) {
+  pdl_enter();
   if (sc->done) return;
   const long long plane = (long long)d.n1 * d.n2;
   const int rows = d.n2 * d.n3;
@@ -1635,6 +1668,7 @@ __global__ void __launch_bounds__(256) mg_down_kernel(MgLevel d, const T* __rest
 template <typename T>
 __global__ void __launch_bounds__(256) mg_restrict_kernel(MgLevel f, MgLevel c, const T* __restrict__ t,
                                                           T* __restrict__ rc, const CgScalars* sc) {
+  pdl_enter();
   if (sc->done) return;
   const int rows = c.n2 * c.n3;
   const int lane = threadIdx.x & 31;
@@ -1661,6 +1695,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) mg_prolong_kernel(MgLevel f, MgLevel c, const T* __restrict__ r,
                                                          const T* __restrict__ ec, T* __restrict__ y, T s,
                                                          const CgScalars* sc) {
+  pdl_enter();
   if (sc->done) return;
   const int rows = f.n2 * f.n3;
   const int lane = threadIdx.x & 31;
@@ -1676,6 +1711,7 @@ __global__ void __launch_bounds__(256) mg_prolong_kernel(MgLevel f, MgLevel c, c
 template <typename T, bool DOT>
 __global__ void __launch_bounds__(256) mg_up_kernel(MgLevel d, const T* __restrict__ r, const T* __restrict__ y,
                                                     T* __restrict__ z, T omega, T s, CgScalars* sc, RedBuf red) {
+  pdl_enter();
   __shared__ double smem[256 / 32];
   if (sc->done) return;
   const long long plane = (long long)d.n1 * d.n2;
@@ -1719,6 +1755,7 @@ struct MgDR {  // at most 48 KB of static shared memory: 39.6 KB in FP32, 31.8 K
 template <typename T>
 __global__ void __launch_bounds__(256) mg_down_restrict_kernel(MgLevel f, MgLevel c, const T* __restrict__ r,
                                                                T* __restrict__ rc, T omega, const CgScalars* sc) {
+  pdl_enter();
   using D = MgDR<T>;
   __shared__ T rs[D::RZ * D::RY * D::RX];
   __shared__ T ts[D::TZ * D::TY * D::TX];
@@ -1780,6 +1817,7 @@ template <typename T, bool DOT>
 __global__ void __launch_bounds__(256) mg_prolong_up_kernel(MgLevel f, MgLevel c, const T* __restrict__ r,
                                                             const T* __restrict__ ec, T* __restrict__ z, T omega,
                                                             T s, CgScalars* sc, RedBuf red) {
+  pdl_enter();
   using D = MgPU<T>;
   __shared__ T rs[D::YZ * D::YY * D::YX];
   __shared__ T ys[D::YZ * D::YY * D::YX];
@@ -1964,6 +2002,7 @@ template <typename T, bool DOT>
 __global__ void __launch_bounds__(1024) mg_coarse_kernel(MgLevel d0, int nlev, const T* __restrict__ r,
                                                          T* __restrict__ z, T omega, T s0, int sweeps,
                                                          CgScalars* sc) {
+  pdl_enter();
   mg_coarse_body<T, DOT>(d0, nlev, r, z, omega, s0, sweeps, sc);
 }
 
@@ -2011,16 +2050,19 @@ __global__ void __launch_bounds__(256) direction_kernel(long long G, T* d, const
     d[i] = (beta == 0.0) ? s[i] : fma(be, d[i], s[i]);
 }
 
-// out[0] = a.b, out[1] = c.e (FP64 accumulation; c may be NULL).
+// out[0] = a.b, out[1] = c.e (c may be NULL).  Per-thread sums in DotAcc: FP64
+// for double fields, compensated FP32 pairs for float fields (the FP64 pipe
+// issues at a small fraction of the FP32 rate here).
 template <typename T>
 __global__ void __launch_bounds__(256) dot2_kernel(long long G, const T* a, const T* b, const T* c,
                                                    const T* e, double* out, RedBuf red) {
   __shared__ double smem[2 * (256 / 32)];
-  double acc[2] = {0.0, 0.0};
+  DotAcc<T> d0, d1;
   for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < G; i += (long long)gridDim.x * 256) {
-    acc[0] += (double)a[i] * (double)b[i];
-    if (c) acc[1] += (double)c[i] * (double)e[i];
+    d0.add(a[i], b[i]);
+    if (c) d1.add(c[i], e[i]);
   }
+  double acc[2] = {d0.value(), d1.value()};
   struct Fin {
     double* out;
     __device__ void operator()(double* t) const {

@@ -91,7 +91,7 @@ PRECOND_NONE, PRECOND_MG = 0, 1
 class Counters(C.Structure):
     _fields_ = [("launches", C.c_longlong), ("kind_launches", C.c_longlong * K_COUNT),
                 ("timed_launches", C.c_longlong * K_COUNT), ("timed_ms", C.c_double * K_COUNT),
-                ("persistent_cg_iters", C.c_longlong)]
+                ("persistent_cg_iters", C.c_longlong), ("tma_launches", C.c_longlong)]
 
 
 class SolveStats(C.Structure):

@@ -40,7 +40,9 @@ def ctx():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     B.build()
-    c = F.Context(0)
+    # cp.async staging and plain launches whatever OFDFT_TMA / OFDFT_PDL say in
+    # the environment, so that the tests below compare against this path
+    c = _context(OFDFT_TMA=0, OFDFT_PDL=0)
     yield c
     c.close()
 
@@ -252,3 +254,99 @@ def test_overlap_correction_matches_oracle(ctx, prec):
 
 def _kw(p):
     return {k: getattr(p, k) for k, _ in type(p)._fields_}
+
+
+# ------------------------------------------------- TMA staging of the planes --
+@pytest.fixture(scope="module")
+def ctx_tma(ctx):
+    """A context whose FP32 z-streaming passes stage planes by TMA (tiled
+    cp.async.bulk.tensor copies completed on mbarriers, out-of-grid elements
+    filled with zero by the copy engine) wherever the pass allows it."""
+    c = _context(OFDFT_TMA=1)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("order", [4, 6, 8, 10, 12])
+def test_tma_staged_stencil_is_bit_identical_to_cp_async(ctx, ctx_tma, order):
+    """The staging changes how planes reach shared memory, not what arrives:
+    the stencil output is the same bit for bit (orders 4, 8, 10, 12 take TMA on
+    this grid; order 6, whose staged plane is not a whole number of 128-byte
+    lines, keeps cp.async), and matches the oracle at FP32 rounding."""
+    g = F.make_grid(64, 48, 40, 0.5)
+    f = np.random.default_rng(order).standard_normal(g.shape).astype(np.float32)
+    outs = []
+    for c in (ctx, ctx_tma):
+        c.reset_counters()
+        out = torch.empty(g.shape, dtype=torch.float32, device=DEV)
+        c.stencil(g, order, _t(f, torch.float32), out)
+        outs.append(_h(out))
+        used = c.counters().tma_launches
+        assert used == (1 if (c is ctx_tma and order != 6) else 0)
+    assert np.array_equal(outs[0], outs[1])
+    ref = O.laplacian(_ogrid(g), order // 2, f.astype(np.float64))
+    scale = np.abs(O.lap_weights(order // 2, g.h)).sum() * 6 * np.abs(f).max()
+    assert np.abs(outs[1] - ref).max() <= 2e-6 * scale
+
+
+def test_tma_staged_poisson_and_ground_state_match(ctx, ctx_tma):
+    """The FP32 CG passes with TMA staging give the same Poisson solution and
+    the same MIXED ground state (13-atom cluster) as with cp.async staging (each
+    context autotunes its own z-split, which orders the reductions' partial
+    sums, so results agree to rounding rather than bit for bit)."""
+    g = F.make_grid(48, 40, 36, 0.5)
+    rho = np.random.default_rng(9).standard_normal(g.shape)
+    sols = []
+    for c in (ctx, ctx_tma):
+        c.reset_counters()
+        phi = torch.zeros(g.shape, dtype=torch.float32, device=DEV)
+        st = c.poisson(g, 12, phi, rho=_t(rho, torch.float32), tol=1e-9)
+        assert st.rel_residual <= 1e-9
+        sols.append((_h(phi), st.iterations))
+        assert (c.counters().tma_launches > 0) == (c is ctx_tma)
+    assert abs(sols[0][1] - sols[1][1]) <= 1
+    assert np.abs(sols[0][0] - sols[1][0]).max() <= 2e-6 * np.abs(sols[0][0]).max()
+    cl = W.cluster_c1()
+    p = F.default_params(precision=F.PREC_MIXED)
+    E0, F0, s0 = ctx.solve(cl.R, cl.Z, cl.h, p)
+    E1, F1, s1 = ctx_tma.solve(cl.R, cl.Z, cl.h, p)
+    assert s0.converged and s1.converged
+    assert abs(E1 - E0) / cl.M <= 1e-7
+    assert np.abs(F1 - F0).max() <= 1e-5
+
+
+# ------------------------------------------ programmatic dependent launch --
+@pytest.fixture(scope="module")
+def ctx_fixed_pair(ctx):
+    """Two contexts with the fixed one-wave launch shapes (no autotuning), one
+    launching the CG-loop kernels with programmatic dependent launch."""
+    a = _context(OFDFT_AUTOTUNE=0, OFDFT_TMA=0, OFDFT_PDL=0)
+    b = _context(OFDFT_AUTOTUNE=0, OFDFT_TMA=0, OFDFT_PDL=1)
+    yield a, b
+    a.close()
+    b.close()
+
+
+def test_programmatic_dependent_launch_is_bit_identical(ctx_fixed_pair):
+    """Programmatic dependent launch overlaps a kernel's launch with the end of
+    the previous one; every kernel still waits for its predecessor's writes, so
+    the preconditioned Poisson solve and the MIXED ground state (13-atom
+    cluster, device-side CG loops in CUDA graphs) are the same bit for bit."""
+    a, b = ctx_fixed_pair
+    g = F.make_grid(48, 40, 36, 0.5)
+    rho = np.random.default_rng(11).standard_normal(g.shape)
+    sols = []
+    for c in (a, b):
+        phi = torch.zeros(g.shape, dtype=torch.float32, device=DEV)
+        st = c.poisson(g, 12, phi, rho=_t(rho, torch.float32), tol=1e-9)
+        assert st.rel_residual <= 1e-9
+        sols.append((_h(phi), st.iterations))
+    assert sols[0][1] == sols[1][1]
+    assert np.array_equal(sols[0][0], sols[1][0])
+    cl = W.cluster_c1()
+    p = F.default_params(precision=F.PREC_MIXED)
+    E0, F0, s0 = a.solve(cl.R, cl.Z, cl.h, p)
+    E1, F1, s1 = b.solve(cl.R, cl.Z, cl.h, p)
+    assert s0.converged and s1.converged
+    assert E0 == E1
+    assert np.array_equal(F0, F1)
