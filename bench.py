@@ -626,10 +626,13 @@ def run_serve(args):
     B.build()
     ctx = F.Context(0)
     rates = [float(x) for x in args.rates.split(",")]
+    prm = lambda c: F.default_params(precision=F.PREC_MIXED, fd_order=c.fd_order, vacuum=c.vacuum, round_to=16)
+    if args.serve_warmup > 0:  # warm-up: workspaces, CUDA graphs and tuned shapes (discarded)
+        S.serve(ctx, W.serving_requests_c5(100.0, args.serve_warmup, seed=99, max_m=args.max_m), prm,
+                precision=F.PREC_MIXED, hbm_budget_bytes=args.hbm_gb << 30)
     res = []
     for rate in rates:
         reqs = W.serving_requests_c5(rate, args.requests, max_m=args.max_m)
-        prm = lambda c: F.default_params(precision=F.PREC_MIXED, fd_order=c.fd_order, vacuum=c.vacuum, round_to=16)
         rep = S.serve(ctx, reqs, prm, precision=F.PREC_MIXED, hbm_budget_bytes=args.hbm_gb << 30)
         s = rep.summary()
         s["rate_per_s"] = rate

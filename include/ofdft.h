@@ -371,9 +371,11 @@ long long ofdft_batch_bytes(const ofdft_grid* g, int prec);
  * over one iteration of every solve in the round (V-cycles, stencil pass,
  * update, all solves packed into shared launches), captured the first time a
  * set of solves meets and replayed while the set stays the same (it changes on
- * admission and retirement).  Before the first capture on a new set of grids
- * the autotuner times the batched CG stencil pass at 8, 16, 32 and 64 planes
- * per CTA (z-tile depth) and keeps the fastest for the batch; the CTA shape
+ * admission and retirement).  The first time a grid shape meets the batch
+ * engine of a context, the autotuner times that grid's batched CG stencil pass
+ * at 8, 16, 32 and 64 planes per CTA (z-tile depth) and keeps the fastest for
+ * that shape (the depth sets the order of the grid's partial sums, so one
+ * choice per shape keeps every request's result independent of the mix); the CTA shape
  * itself (32 x 8 threads, 2 rows x 2 columns per thread in FP32, 2 x 1 in FP64)
  * is fixed by the register-blocked kernel. */
 typedef struct {
@@ -382,8 +384,9 @@ typedef struct {
   long long graph_replays;     /* CG loops run as one graph launch */
   long long graph_iterations;  /* CG iterations run inside those graphs (largest per loop, summed) */
   long long eager_iterations;  /* CG iterations launched one by one (one ahead of each graph launch) */
-  int z_depth;                 /* planes per CTA of the batched z-streaming passes */
-  int z_tuned;                 /* 1 once the autotuner has chosen z_depth */
+  int z_depth;                 /* planes per CTA of the most recently tuned grid's tiles (each grid shape
+                                  is tuned once per context; the depth fixes the order of its sums) */
+  int z_tuned;                 /* 1 once the autotuner has chosen a depth */
   int tune_candidates;         /* entries of tune_depth / tune_us from the last tuning */
   int tune_depth[8];
   double tune_us[8];           /* mean duration of the batched CG stencil pass at that depth */

@@ -1026,13 +1026,6 @@ struct Solver {
     TRY(direction(0.0));  // d = s
     double delta_new = e.rs_pc;
     int k = 0;
-    // stall detection: iterations in a row in which L fell by no more than its
-    // rounding resolution and h^3 r.s reached no new low.  A mixed-precision
-    // solve near its FP32 floor can cycle there between two iterates without
-    // ever meeting tol_inner; three such iterations end the loop (counted as
-    // converged in MIXED, where that floor is the precision's resolution)
-    double L_best = e.L, rs_best = e.rs;
-    int stalled = 0;
     for (int it = 0; it < p->max_nlcg; ++it) {
       if (e.rs < tol_in) {
         *converged = 1;
@@ -1113,17 +1106,6 @@ struct Solver {
         k = 0;
       } else {
         TRY(direction(beta));
-      }
-      if (e.L < L_best - l_resolution(e, mixed) || e.rs < rs_best)
-        stalled = 0;
-      else
-        ++stalled;
-      L_best = std::min(L_best, e.L);
-      rs_best = std::min(rs_best, e.rs);
-      if (stalled >= 3 && e.rs >= tol_in) {
-        if (trace) fprintf(stderr, "[ofdft] nlcg stalled at rs=%.6e (tol %.6e)\n", e.rs, tol_in);
-        if (mixed) *converged = 1;
-        break;
       }
     }
     if (!*converged && e.rs < tol_in) *converged = 1;
@@ -1342,6 +1324,7 @@ int pseudocharge_tables(ofdft_ctx* c, const ofdft_grid* gr, const GridDev& g, co
                         const double* R_host, int M, T* b, double* es_dev) {
   const Weights<double> W = lap_weights(R, gr->h, 1.0);
   AtomTables t = atom_tables(A.rc, gr->h, R, M, (size_t)768 << 20);
+  if (t.vdim > 1024) return fail(c, OFDFT_EINVAL, "r_c / h = %g is too large for the atom tables", A.rc / gr->h);
   t.batch = std::min(t.batch, 512);
   TRY(ensure(c, c->v[V_ATOM1], (size_t)t.batch * (t.vper + t.bper) * sizeof(double)));
   TRY(ensure(c, c->v[V_ATOM2], (size_t)t.batch * 3 * sizeof(int) + 64));
@@ -1418,14 +1401,20 @@ int device_guess(ofdft_ctx* c, const ofdft_grid* gr, const double* R_host, const
 template <typename T, int R>
 int launch_force_boxes(ofdft_ctx* c, const AtomArgs& A, int a0, int na, int vdim, int bdim, const int* lo,
                        const Weights<double>& W, double* vbox, double* bbox) {
+  // one block row per atom, about eight blocks per SM in total
+  auto grid_for = [&](long long per) {
+    const long long bx = std::max<long long>(1, std::min<long long>((per + 255) / 256, ((long long)c->sms * 8 + na - 1) / na));
+    return dim3((unsigned)bx, (unsigned)na);
+  };
   {
     ProfScope ps_(c, OFDFT_K_ATOMS);
-    force_vbox_kernel<<<c->sms * 8, 256, 0, c->stream>>>(A, a0, na, vdim, R, lo, vbox);
+    force_vbox_kernel<<<grid_for((long long)vdim * vdim * vdim), 256, 0, c->stream>>>(A, a0, vdim, R, lo, vbox);
   }
   CU(cudaGetLastError());
   {
     ProfScope ps_(c, OFDFT_K_ATOMS);
-    force_bbox_kernel<R><<<c->sms * 8, 256, 0, c->stream>>>(A, a0, na, vdim, bdim, lo, W, vbox, bbox);
+    force_bbox_kernel<R><<<grid_for((long long)bdim * bdim * bdim), 256, 0, c->stream>>>(A, a0, vdim, bdim, lo, W,
+                                                                                        vbox, bbox);
   }
   CU(cudaGetLastError());
   return OFDFT_OK;
@@ -1458,7 +1447,9 @@ int device_forces(ofdft_ctx* c, const ofdft_grid* gr, int R, const double* R_hos
   const long long vper = (long long)vdim * vdim * vdim, bper = (long long)bdim * bdim * bdim;
   const bool exact = (variant == OFDFT_FORCE_EXACT);
   // atoms per batch: keep the box scratch near 256 MB
+  if (vdim > 1024) return fail(c, OFDFT_EINVAL, "r_c / h = %g is too large for the atom tables", rc / h);
   int batch = (int)std::max<long long>(1, std::min<long long>(M, (256ll << 20) / ((vper + bper) * 8)));
+  batch = std::min(batch, 16384);  // atoms of one launch (one block row each)
   if (exact) batch = std::min(M, 4096);
   const int nblk = std::max(1, std::min(64, (int)((long long)box * box * box / 2048) + 1));
   TRY(ensure(c, c->v[V_ATOM1], exact ? 256 : (size_t)batch * (vper + bper) * sizeof(double)));

@@ -56,6 +56,8 @@ struct Slot {
   ofdft_grid grid;
   GridDev g;
   int Rr = 6;
+  int zdepth = 16;  // planes per CTA of this grid's tiles in the batched z-streaming passes
+  int ztuned = 0;   // zdepth chosen (autotuner or the context's cache)
   double h = 0.5, h3 = 0.125;
   size_t bytes = 0;
   void* mem = nullptr;
@@ -145,11 +147,12 @@ struct ofdft_batch {
   std::vector<char> cap_host;       // staged contents of the capture arena
   char* cap_dev = nullptr;          // the capture arena (device)
   size_t cap_bytes = 0;
-  // autotuned launch shape of the batched z-streaming passes: planes per CTA
-  int zdepth = 16;
+  // autotuned launch shape of the batched z-streaming passes: planes per CTA,
+  // chosen per grid shape (the tiles of a grid fix the order of its partial
+  // sums, so a request's result does not depend on the other grids in the mix)
+  int zdepth = 16;                             // depth of the most recently tuned grid
   int ztuned = 0;
-  std::vector<std::vector<long long>> tuned_sets;  // grid sets the depth was tuned on
-  std::vector<std::pair<int, float>> tune_log;     // (depth, us) of the last tuning
+  std::vector<std::pair<int, float>> tune_log;  // (depth, us) of the last tuning
   // type-erased slot lists (only the engine of the batch precision is used)
   std::vector<std::unique_ptr<Slot<double>>> s64_active, s64_done;
   std::vector<std::unique_ptr<Slot<float>>> s32_active, s32_done;
@@ -323,7 +326,7 @@ struct Engine {
           if ((int)zvec_ok<TT>(S->g, le.first, le.second) != wide) continue;
           int cnt = 0;
           const int si = (int)desc.size();
-          grid_tiles(S->g, si, ZCfg<TT>::TY, B->zdepth, tiles, &cnt);
+          grid_tiles(S->g, si, ZCfg<TT>::TY, S->zdepth, tiles, &cnt);
           ZSlot<TT, L, E> z;
           z.g = S->g;
           z.W = cast_weights<TT>(lap_weights(Rr, S->h, wscale));
@@ -527,35 +530,50 @@ struct Engine {
   }
 
   // Autotuner of the batched z-streaming passes (S11): the planes per CTA of
-  // the CG stencil pass, timed on the loop's own grids (their r or z as input)
-  // with scratch p and q and private CG scalars, so no solve's state changes;
-  // tuned once per set of grids and kept for the batch.
+  // each grid's tiles in the CG stencil pass, timed on the grid itself (its r
+  // or z as input) with scratch p and q and private CG scalars, so no solve's
+  // state changes; chosen once per grid shape for the context's lifetime, so a
+  // request's partial-sum order, and with it its result, is the same alone and
+  // in any mix.
   template <class GetR>
   int tune_zdepth(const std::vector<Slot<T>*>& slots, GetR getr) {
-    std::vector<long long> gset;
-    long long gmax = 0;
     for (Slot<T>* S : slots) {
-      gset.push_back(((long long)S->g.n1 << 42) | ((long long)S->g.n2 << 21) | S->g.n3);
-      gmax = std::max(gmax, S->g.G);
+      if (S->ztuned) continue;
+      // one choice per grid shape, stencil radius and element type for the
+      // context's lifetime
+      const std::vector<long long> key = {-1, (long long)sizeof(T), S->Rr, S->pc, S->g.n1, S->g.n2, S->g.n3};
+      bool found = false;
+      for (auto& t : c->ztune)
+        if (t.first == key) {
+          S->zdepth = t.second;
+          found = true;
+          break;
+        }
+      if (!found) {
+        TRY(tune_grid_zdepth(S, getr));
+        c->ztune.push_back({key, S->zdepth});
+      }
+      S->ztuned = 1;
     }
-    std::sort(gset.begin(), gset.end());
-    for (auto& t : B->tuned_sets)
-      if (t == gset) return OFDFT_OK;
+    return OFDFT_OK;
+  }
+
+  // Times the batched CG stencil pass of one grid alone at 8, 16, 32 and 64
+  // planes per CTA (scratch outputs, a private scalar block) and keeps the fastest.
+  template <class GetR>
+  int tune_grid_zdepth(Slot<T>* S, GetR getr) {
+    const long long G = S->g.G;
     T* scratch = nullptr;
     CgScalars* psc = nullptr;
-    CU(cudaMalloc(&scratch, 2 * gmax * sizeof(T)));
-    if (cudaMalloc(&psc, slots.size() * sizeof(CgScalars)) != cudaSuccess) {
+    CU(cudaMalloc(&scratch, 2 * G * sizeof(T)));
+    if (cudaMalloc(&psc, sizeof(CgScalars)) != cudaSuccess) {
       cudaFree(scratch);
       return fail(c, OFDFT_ENOMEM, "autotune: no room for scratch scalars");
     }
-    std::vector<CgScalars> init(slots.size());
-    memset(init.data(), 0, init.size() * sizeof(CgScalars));
-    for (auto& x : init) {
-      x.first = 1;
-      x.max_it = 1 << 30;
-    }
-    std::vector<int> pos(B->capacity + 1, 0);
-    for (size_t i = 0; i < slots.size(); ++i) pos[slots[i]->index] = (int)i;
+    CgScalars init;
+    memset(&init, 0, sizeof(init));
+    init.first = 1;
+    init.max_it = 1 << 30;
     const int prof = c->prof;
     c->prof = 0;
     const long long launches = c->launches;
@@ -565,24 +583,23 @@ struct Engine {
     int rc = OFDFT_OK;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
       rc = fail(c, OFDFT_ECUDA, "autotune: event creation failed");
-    const int saved = B->zdepth;
+    const int saved = S->zdepth;
     int best = saved;
     float best_ms = 1e30f;
     B->tune_log.clear();
+    const std::vector<Slot<T>*> one = {S};
     for (int zc : {8, 16, 32, 64}) {
       if (rc != OFDFT_OK) break;
-      B->zdepth = zc;
+      S->zdepth = zc;
       float ms = 0.0f;
       for (int rep = 0; rep < 4 && rc == OFDFT_OK; ++rep) {
-        if (cudaMemcpyAsync(psc, init.data(), init.size() * sizeof(CgScalars), cudaMemcpyHostToDevice, c->stream) !=
-                cudaSuccess ||
+        if (cudaMemcpyAsync(psc, &init, sizeof(CgScalars), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
             cudaEventRecord(e0, c->stream) != cudaSuccess) {
           rc = fail(c, OFDFT_ECUDA, "autotune: enqueue failed");
           break;
         }
-        rc = zpass<T, LoadPlain<T>, EpiCgA<T>>(slots, OFDFT_K_CG_DIR_STENCIL, -1.0, [&](Slot<T>* S) {
-          return std::make_pair(LoadPlain<T>{S->pc ? S->mz : getr(S)},
-                                EpiCgA<T>{scratch, scratch + gmax, psc + pos[S->index]});
+        rc = zpass<T, LoadPlain<T>, EpiCgA<T>>(one, OFDFT_K_CG_DIR_STENCIL, -1.0, [&](Slot<T>* X) {
+          return std::make_pair(LoadPlain<T>{X->pc ? X->mz : getr(X)}, EpiCgA<T>{scratch, scratch + G, psc});
         });
         float t = 0.0f;
         if (rc == OFDFT_OK && (cudaEventRecord(e1, c->stream) != cudaSuccess ||
@@ -605,9 +622,9 @@ struct Engine {
     c->prof = prof;
     c->launches = launches;  // tuning launches are not the caller's work
     memcpy(c->kind_launches, kinds, sizeof(kinds));
-    B->zdepth = (rc == OFDFT_OK) ? best : saved;
+    S->zdepth = (rc == OFDFT_OK) ? best : saved;
     if (rc != OFDFT_OK) return rc;
-    B->tuned_sets.push_back(gset);
+    B->zdepth = S->zdepth;
     B->ztuned = 1;
     return OFDFT_OK;
   }
@@ -618,11 +635,12 @@ struct Engine {
   template <class GetX, class GetR, class GetSc>
   int loop_graph(const std::vector<Slot<T>*>& slots, bool fold, GetX getx, GetR getr, GetSc getsc,
                  cudaGraphExec_t* out) {
-    std::vector<long long> key = {(long long)sizeof(T), fold ? 1 : 0, B->zdepth, (long long)getsc(slots[0]),
+    std::vector<long long> key = {(long long)sizeof(T), fold ? 1 : 0, (long long)getsc(slots[0]),
                                   (long long)c->partials.p};
     std::vector<int> idx;
     for (Slot<T>* S : slots) {
       key.push_back((long long)S);
+      key.push_back(S->zdepth);
       key.push_back((long long)getx(S));
       key.push_back((long long)getr(S));
       key.push_back((long long)getsc(S));

@@ -2523,6 +2523,27 @@ __device__ __forceinline__ double gauss_v(double Z, double inv_sigma, double r) 
   return -Z * erf(r * inv_sigma) / r;
 }
 
+// Conservative FP32 screen of node-to-atom distances.  The offset of a box's
+// first node is formed in FP64 once, then node i of an axis sits at
+// x0 + i h in FP32: on boxes of up to a few thousand nodes and offsets of up
+// to a few hundred bohr its error stays below 1e-4 bohr, so a node whose
+// screened distance exceeds r (1 + 1e-4) + 1e-3 is farther than r in exact
+// arithmetic too.  Nodes that pass take the unchanged FP64 path, so every
+// value and every inside/outside decision is the one the FP64 code takes;
+// the screen only skips FP64 work (a small fraction of the FP32 rate here) on
+// nodes that cannot contribute.
+struct DistScreen {
+  float x0, y0, z0, h, r2;
+  __device__ __forceinline__ bool maybe_within(int i, int j, int k) const {
+    const float x = fmaf((float)i, h, x0), y = fmaf((float)j, h, y0), z = fmaf((float)k, h, z0);
+    return x * x + y * y + z * z <= r2;
+  }
+};
+__device__ __forceinline__ float screen_r2(double r) {
+  const float rs = (float)(r * (1.0 + 1e-4) + 1e-3);
+  return rs * rs;
+}
+
 struct AtomArgs {
   const double* R;  // M x 3
   const double* Z;  // M
@@ -2576,12 +2597,19 @@ __global__ void __launch_bounds__(512) guess_kernel(GridDev g, AtomArgs A, doubl
   const double cx = A.ox + (blockIdx.x * AT) * A.h + half, cy = A.oy + (blockIdx.y * AT) * A.h + half,
                cz = A.oz + (blockIdx.z * AT) * A.h + half;
   const double norm = pow(2.0 * kPi * gsig * gsig, -1.5);
+  // FP32 screen of the node's distance to each listed atom (see DistScreen):
+  // node x sits at ox + (x + 1/2) h
+  const float fx = (float)(A.ox + (x + 0.5) * A.h), fy = (float)(A.oy + (y + 0.5) * A.h),
+              fz = (float)(A.oz + (z + 0.5) * A.h);
+  const float cut2 = screen_r2(gcut);
   double rho = 0.0;
   for (int a0 = 0; a0 < A.M; a0 += 512) {
     const int cnt = tile_atoms(A, a0, cx, cy, cz, half, gcut + A.h, list, warp_cnt);
     if (inside) {
       for (int t = 0; t < cnt; ++t) {
         const int J = list[t];
+        const float dx = fx - (float)A.R[3 * J], dy = fy - (float)A.R[3 * J + 1], dz = fz - (float)A.R[3 * J + 2];
+        if (dx * dx + dy * dy + dz * dz > cut2) continue;
         const double rx = node_off(A.ox, x, A.h, A.R[3 * J]), ry = node_off(A.oy, y, A.h, A.R[3 * J + 1]),
                      rz = node_off(A.oz, z, A.h, A.R[3 * J + 2]);
         const double r2 = dist3_sq(rx, ry, rz);
@@ -2607,24 +2635,33 @@ struct AtomBox {
   int dim[3];
 };
 
-// V_J tabulated on the atom's box grown by 2R: vbox[a][...].  Only nodes within
-// r_c + R h of the atom are ever read (the stencil neighbours of the nodes of its
-// ball, where b_J is nonzero), so V_J is evaluated there only and the rest of
-// the cube holds 0.
-static __global__ void __launch_bounds__(256) force_vbox_kernel(AtomArgs A, int a0, int na, int vdim, int R,
+// V_J tabulated on the atom's box grown by 2R: vbox[a][...], one block row per
+// atom (blockIdx.y).  Only nodes within r_c + R h of the atom are ever read
+// (the stencil neighbours of the nodes of its ball, where b_J is nonzero), so
+// V_J is evaluated there only and the rest of the cube holds 0.
+static __global__ void __launch_bounds__(256) force_vbox_kernel(AtomArgs A, int a0, int vdim, int R,
                                                          const int* __restrict__ lo, double* vbox) {
-  const long long per = (long long)vdim * vdim * vdim;
+  const int a = blockIdx.y;
+  const int J = a0 + a;
+  const unsigned per = (unsigned)vdim * vdim * vdim;
   const double reach = A.rc + R * A.h + 1e-9 * (A.rc + A.h);
-  for (long long t = (long long)blockIdx.x * 256 + threadIdx.x; t < per * na; t += (long long)gridDim.x * 256) {
-    const int a = (int)(t / per);
-    const long long e = t - (long long)a * per;
-    const int i = (int)(e % vdim), j = (int)((e / vdim) % vdim), k = (int)(e / ((long long)vdim * vdim));
-    const int J = a0 + a;
-    const double px = node_off(A.ox, lo[3 * a] - 2 * R + i, A.h, A.R[3 * J]);
-    const double py = node_off(A.oy, lo[3 * a + 1] - 2 * R + j, A.h, A.R[3 * J + 1]);
-    const double pz = node_off(A.oz, lo[3 * a + 2] - 2 * R + k, A.h, A.R[3 * J + 2]);
-    const double r = dist3(px, py, pz);
-    vbox[t] = (r <= reach) ? gauss_v(A.Z[J], 1.0 / A.sigma, r) : 0.0;
+  const int bx = lo[3 * a] - 2 * R, by = lo[3 * a + 1] - 2 * R, bz = lo[3 * a + 2] - 2 * R;
+  const double Rx = A.R[3 * J], Ry = A.R[3 * J + 1], Rz = A.R[3 * J + 2];
+  const DistScreen sc{(float)node_off(A.ox, bx, A.h, Rx), (float)node_off(A.oy, by, A.h, Ry),
+                      (float)node_off(A.oz, bz, A.h, Rz), (float)A.h, screen_r2(reach)};
+  double* out = vbox + (size_t)a * per;
+  for (unsigned e = blockIdx.x * 256 + threadIdx.x; e < per; e += gridDim.x * 256) {
+    const unsigned jk = e / (unsigned)vdim;
+    const int i = (int)(e - jk * (unsigned)vdim);
+    const int k = (int)(jk / (unsigned)vdim);
+    const int j = (int)(jk - (unsigned)k * (unsigned)vdim);
+    double v = 0.0;
+    if (sc.maybe_within(i, j, k)) {
+      const double r = dist3(node_off(A.ox, bx + i, A.h, Rx), node_off(A.oy, by + j, A.h, Ry),
+                             node_off(A.oz, bz + k, A.h, Rz));
+      if (r <= reach) v = gauss_v(A.Z[J], 1.0 / A.sigma, r);
+    }
+    out[e] = v;
   }
 }
 
@@ -2684,33 +2721,40 @@ __global__ void __launch_bounds__(512) pseudocharge_gather_kernel(GridDev g, Ato
   grid_sum<1, 512>(acc, smem, red, nb, bid, tid, fin);
 }
 
-// b_J on the atom's box grown by R: -(1/4 pi) L_h V_J inside r_c, 0 outside.
+// b_J on the atom's box grown by R: -(1/4 pi) L_h V_J inside r_c, 0 outside;
+// one block row per atom (blockIdx.y).
 template <int R>
-__global__ void __launch_bounds__(256) force_bbox_kernel(AtomArgs A, int a0, int na, int vdim, int bdim,
+__global__ void __launch_bounds__(256) force_bbox_kernel(AtomArgs A, int a0, int vdim, int bdim,
                                                          const int* __restrict__ lo, Weights<double> W,
                                                          const double* __restrict__ vbox, double* bbox) {
-  const long long per = (long long)bdim * bdim * bdim;
-  const long long vper = (long long)vdim * vdim * vdim;
-  for (long long t = (long long)blockIdx.x * 256 + threadIdx.x; t < per * na; t += (long long)gridDim.x * 256) {
-    const int a = (int)(t / per);
-    const long long e = t - (long long)a * per;
-    const int i = (int)(e % bdim), j = (int)((e / bdim) % bdim), k = (int)(e / ((long long)bdim * bdim));
-    const int J = a0 + a;
-    const double px = node_off(A.ox, lo[3 * a] - R + i, A.h, A.R[3 * J]);
-    const double py = node_off(A.oy, lo[3 * a + 1] - R + j, A.h, A.R[3 * J + 1]);
-    const double pz = node_off(A.oz, lo[3 * a + 2] - R + k, A.h, A.R[3 * J + 2]);
+  const int a = blockIdx.y;
+  const int J = a0 + a;
+  const unsigned per = (unsigned)bdim * bdim * bdim;
+  const size_t vper = (size_t)vdim * vdim * vdim;
+  const int bx = lo[3 * a] - R, by = lo[3 * a + 1] - R, bz = lo[3 * a + 2] - R;
+  const double Rx = A.R[3 * J], Ry = A.R[3 * J + 1], Rz = A.R[3 * J + 2];
+  const DistScreen sc{(float)node_off(A.ox, bx, A.h, Rx), (float)node_off(A.oy, by, A.h, Ry),
+                      (float)node_off(A.oz, bz, A.h, Rz), (float)A.h, screen_r2(A.rc)};
+  const double* v = vbox + (size_t)a * vper;
+  double* out = bbox + (size_t)a * per;
+  const long long sy = vdim, sz = (long long)vdim * vdim;
+  for (unsigned e = blockIdx.x * 256 + threadIdx.x; e < per; e += gridDim.x * 256) {
+    const unsigned jk = e / (unsigned)bdim;
+    const int i = (int)(e - jk * (unsigned)bdim);
+    const int k = (int)(jk / (unsigned)bdim);
+    const int j = (int)(jk - (unsigned)k * (unsigned)bdim);
     double val = 0.0;
-    if (dist3(px, py, pz) < A.rc) {
-      const double* v = vbox + (long long)a * vper;
-      const long long c = (long long)(i + R) + (long long)vdim * ((j + R) + (long long)vdim * (k + R));
-      const long long sy = vdim, sz = (long long)vdim * vdim;
+    if (sc.maybe_within(i, j, k) &&
+        dist3(node_off(A.ox, bx + i, A.h, Rx), node_off(A.oy, by + j, A.h, Ry), node_off(A.oz, bz + k, A.h, Rz)) <
+            A.rc) {
+      const long long c = (long long)(i + R) + sy * (j + R) + sz * (k + R);
       double lap = W.c * v[c];
 #pragma unroll
       for (int p = 1; p <= R; ++p)
         lap = fma(W.w[p], ((v[c + p] + v[c - p]) + (v[c + p * sy] + v[c - p * sy])) + (v[c + p * sz] + v[c - p * sz]), lap);
       val = -lap / (4.0 * kPi);
     }
-    bbox[t] = val;
+    out[e] = val;
   }
 }
 
@@ -2731,11 +2775,18 @@ __global__ void __launch_bounds__(256) force_ball_kernel(GridDev g, AtomArgs A, 
   const long long per = (long long)box * box * box;
   const long long bper = (long long)bdim * bdim * bdim;
   const double inv_s = 1.0 / A.sigma;
+  const DistScreen sc{(float)node_off(A.ox, lo[3 * a], A.h, A.R[3 * J]),
+                      (float)node_off(A.oy, lo[3 * a + 1], A.h, A.R[3 * J + 1]),
+                      (float)node_off(A.oz, lo[3 * a + 2], A.h, A.R[3 * J + 2]), (float)A.h, screen_r2(A.rc)};
   double acc[3] = {0.0, 0.0, 0.0};
-  for (long long t = (long long)blockIdx.x * 256 + threadIdx.x; t < per; t += (long long)gridDim.x * 256) {
-    const int i = (int)(t % box), j = (int)((t / box) % box), k = (int)(t / ((long long)box * box));
+  for (unsigned t = blockIdx.x * 256 + threadIdx.x; t < (unsigned)per; t += gridDim.x * 256) {
+    const unsigned jk = t / (unsigned)box;
+    const int i = (int)(t - jk * (unsigned)box);
+    const int k = (int)(jk / (unsigned)box);
+    const int j = (int)(jk - (unsigned)k * (unsigned)box);
     const int gi = lo[3 * a] + i, gj = lo[3 * a + 1] + j, gk = lo[3 * a + 2] + k;
     if (gi < 0 || gj < 0 || gk < 0 || gi >= g.n1 || gj >= g.n2 || gk >= g.n3) continue;
+    if (!sc.maybe_within(i, j, k)) continue;
     const double rx = node_off(A.ox, gi, A.h, A.R[3 * J]);
     const double ry = node_off(A.oy, gj, A.h, A.R[3 * J + 1]);
     const double rz = node_off(A.oz, gk, A.h, A.R[3 * J + 2]);
