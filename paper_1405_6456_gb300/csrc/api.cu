@@ -1316,22 +1316,39 @@ template <typename T, int R>
 int launch_force_boxes(ofdft_ctx* c, const AtomArgs& A, int a0, int na, int vdim, int bdim, const int* lo,
                        const Weights<double>& W, double* vbox, double* bbox);
 
+// Identity of the b_J tables of a geometry: everything they depend on.
+inline std::vector<double> btab_key(const ofdft_grid* gr, int R, const double* R_host, const double* Z_host, int M,
+                                    double sigma, double rc) {
+  std::vector<double> k = {(double)M, (double)R, gr->h, gr->origin[0], gr->origin[1], gr->origin[2],
+                           (double)gr->n[0], (double)gr->n[1], (double)gr->n[2], sigma, rc};
+  k.insert(k.end(), R_host, R_host + 3 * (size_t)M);
+  k.insert(k.end(), Z_host, Z_host + (size_t)M);
+  return k;
+}
+constexpr size_t kBtabMaxBytes = (size_t)4 << 30;  // b_J tables kept for the forces up to this size
+
 // b = sum_J b_J and E_self (Sec. 4): the atoms' V_J and b_J tables are built for
 // ranges of at most 512 atoms, then every node gathers the b_J of the atoms whose
-// box holds it, in atom order (FP64 running sums across ranges).
+// box holds it, in atom order (FP64 running sums across ranges).  With `keep`
+// the b_J tables of all atoms go to V_BTAB (at most kBtabMaxBytes) and stay
+// there for the forces of the same geometry (device_forces), which then skip
+// rebuilding them.
 template <typename T, int R>
 int pseudocharge_tables(ofdft_ctx* c, const ofdft_grid* gr, const GridDev& g, const AtomArgs& A,
-                        const double* R_host, int M, T* b, double* es_dev) {
+                        const double* R_host, const double* Z_host, int M, T* b, double* es_dev, bool keep) {
   const Weights<double> W = lap_weights(R, gr->h, 1.0);
   AtomTables t = atom_tables(A.rc, gr->h, R, M, (size_t)768 << 20);
   if (t.vdim > 1024) return fail(c, OFDFT_EINVAL, "r_c / h = %g is too large for the atom tables", A.rc / gr->h);
   t.batch = std::min(t.batch, 512);
-  TRY(ensure(c, c->v[V_ATOM1], (size_t)t.batch * (t.vper + t.bper) * sizeof(double)));
+  c->btab_key.clear();
+  keep = keep && (size_t)M * t.bper * sizeof(double) <= kBtabMaxBytes;
+  if (keep) TRY(ensure(c, c->v[V_BTAB], (size_t)M * t.bper * sizeof(double)));
+  TRY(ensure(c, c->v[V_ATOM1], (size_t)t.batch * (t.vper + (keep ? 0 : t.bper)) * sizeof(double)));
   TRY(ensure(c, c->v[V_ATOM2], (size_t)t.batch * 3 * sizeof(int) + 64));
   const bool multi = M > t.batch;
   if (multi) TRY(ensure(c, c->v[V_BACC], g.G * sizeof(double)));
   double* vbox = vec<double>(c, V_ATOM1);
-  double* bbox = vbox + (size_t)t.batch * t.vper;
+  double* btab = keep ? vec<double>(c, V_BTAB) : nullptr;
   int* lo_dev = vec<int>(c, V_ATOM2);
   double* bacc = multi ? vec<double>(c, V_BACC) : nullptr;
   std::vector<int> lo((size_t)3 * t.batch);
@@ -1340,6 +1357,7 @@ int pseudocharge_tables(ofdft_ctx* c, const ofdft_grid* gr, const GridDev& g, co
   CU(cudaMemsetAsync(es_dev, 0, sizeof(double), c->stream));
   for (int a0 = 0; a0 < M; a0 += t.batch) {
     const int na = std::min(t.batch, M - a0);
+    double* bbox = keep ? btab + (size_t)a0 * t.bper : vbox + (size_t)t.batch * t.vper;
     atom_box_lo(R_host, a0, na, gr, t.rb, lo);
     CU(cudaMemcpyAsync(lo_dev, lo.data(), 3 * na * sizeof(int), cudaMemcpyHostToDevice, c->stream));
     TRY((launch_force_boxes<T, R>(c, A, a0, na, t.vdim, t.bdim, lo_dev, W, vbox, bbox)));
@@ -1351,23 +1369,29 @@ int pseudocharge_tables(ofdft_ctx* c, const ofdft_grid* gr, const GridDev& g, co
     }
     CU(cudaGetLastError());
   }
+  if (keep) c->btab_key = btab_key(gr, R, R_host, Z_host, M, A.sigma, A.rc);
   return OFDFT_OK;
 }
 
 template <typename T>
 int device_pseudocharge(ofdft_ctx* c, const ofdft_grid* gr, int R, const double* R_host, const double* Z_host,
-                        int M, double sigma, double rc, T* b, double* E_self) {
+                        int M, double sigma, double rc, T* b, double* E_self, bool keep_tables) {
   AtomArgs A;
   TRY(upload_atoms(c, R_host, Z_host, M, &A, gr, sigma, rc));
   const GridDev g = gdev(gr);
   double* es_dev = c->scal + 20;
   switch (R) {
-    case 1: TRY((pseudocharge_tables<T, 1>(c, gr, g, A, R_host, M, b, es_dev))); break;
-    case 2: TRY((pseudocharge_tables<T, 2>(c, gr, g, A, R_host, M, b, es_dev))); break;
-    case 3: TRY((pseudocharge_tables<T, 3>(c, gr, g, A, R_host, M, b, es_dev))); break;
-    case 4: TRY((pseudocharge_tables<T, 4>(c, gr, g, A, R_host, M, b, es_dev))); break;
-    case 5: TRY((pseudocharge_tables<T, 5>(c, gr, g, A, R_host, M, b, es_dev))); break;
-    case 6: TRY((pseudocharge_tables<T, 6>(c, gr, g, A, R_host, M, b, es_dev))); break;
+#define PSC_CASE(RR)                                                                                         \
+  case RR:                                                                                                   \
+    TRY((pseudocharge_tables<T, RR>(c, gr, g, A, R_host, Z_host, M, b, es_dev, keep_tables)));              \
+    break;
+    PSC_CASE(1)
+    PSC_CASE(2)
+    PSC_CASE(3)
+    PSC_CASE(4)
+    PSC_CASE(5)
+    PSC_CASE(6)
+#undef PSC_CASE
     default: return fail(c, OFDFT_EINVAL, "stencil radius %d", R);
   }
   double es;
@@ -1452,7 +1476,10 @@ int device_forces(ofdft_ctx* c, const ofdft_grid* gr, int R, const double* R_hos
   batch = std::min(batch, 16384);  // atoms of one launch (one block row each)
   if (exact) batch = std::min(M, 4096);
   const int nblk = std::max(1, std::min(64, (int)((long long)box * box * box / 2048) + 1));
-  TRY(ensure(c, c->v[V_ATOM1], exact ? 256 : (size_t)batch * (vper + bper) * sizeof(double)));
+  // the b_J tables of this very geometry, kept by the solve's pseudocharge pass
+  const bool kept = !exact && !c->btab_key.empty() && c->btab_key == btab_key(gr, R, R_host, Z_host, M, sigma, rc);
+  if (kept) batch = std::min(M, 4096);
+  TRY(ensure(c, c->v[V_ATOM1], (exact || kept) ? 256 : (size_t)batch * (vper + bper) * sizeof(double)));
   TRY(ensure(c, c->v[V_ATOM2], (size_t)batch * (3 + nblk * 3) * sizeof(double) + (size_t)batch * 3 * sizeof(int) +
                                   (size_t)3 * M * sizeof(double) + 64));
   double* vbox = vec<double>(c, V_ATOM1);
@@ -1468,7 +1495,8 @@ int device_forces(ofdft_ctx* c, const ofdft_grid* gr, int R, const double* R_hos
       for (int d = 0; d < 3; ++d)
         lo[3 * a + d] = (int)floor((R_host[3 * (a0 + a) + d] - gr->origin[d]) / h - 0.5) - rb + 1;
     CU(cudaMemcpyAsync(lo_dev, lo.data(), 3 * na * sizeof(int), cudaMemcpyHostToDevice, c->stream));
-    if (!exact) {
+    if (kept) bbox = vec<double>(c, V_BTAB) + (size_t)a0 * bper;
+    if (!exact && !kept) {
       switch (R) {
         case 1: TRY((launch_force_boxes<T, 1>(c, A, a0, na, vdim, bdim, lo_dev, W, vbox, bbox))); break;
         case 2: TRY((launch_force_boxes<T, 2>(c, A, a0, na, vdim, bdim, lo_dev, W, vbox, bbox))); break;
@@ -1596,9 +1624,9 @@ int solve_impl(ofdft_ctx* c, const ofdft_grid* gr, const double* R_host, const d
   S.tol_p = (p->poisson_adapt > 0.0) ? std::max(p->tol_poisson, 1e-4) : p->tol_poisson;  // first solve from phi = 0
   // S1: pseudocharge (FP64 for the mixed path too), starting guess, phi = 0
   if (!mixed) {
-    TRY(device_pseudocharge<double>(c, gr, R, R_host, Z_host, M, p->sigma, p->rc, (double*)S.b, &S.E_self));
+    TRY(device_pseudocharge<double>(c, gr, R, R_host, Z_host, M, p->sigma, p->rc, (double*)S.b, &S.E_self, true));
   } else {
-    TRY(device_pseudocharge<double>(c, gr, R, R_host, Z_host, M, p->sigma, p->rc, S.b64, &S.E_self));
+    TRY(device_pseudocharge<double>(c, gr, R, R_host, Z_host, M, p->sigma, p->rc, S.b64, &S.E_self, true));
     {
       ProfScope ps_(c, OFDFT_K_VECTOR);
       convert_kernel<double, float><<<pointwise_blocks(c, g.G), 256, 0, c->stream>>>(g.G, (float*)S.b, S.b64);
@@ -1699,9 +1727,9 @@ int check_params(ofdft_ctx* c, const ofdft_params* p) {
 }
 
 template int device_pseudocharge<double>(ofdft_ctx*, const ofdft_grid*, int, const double*, const double*, int,
-                                         double, double, double*, double*);
+                                         double, double, double*, double*, bool);
 template int device_pseudocharge<float>(ofdft_ctx*, const ofdft_grid*, int, const double*, const double*, int,
-                                        double, double, float*, double*);
+                                        double, double, float*, double*, bool);
 template int device_guess<double>(ofdft_ctx*, const ofdft_grid*, const double*, const double*, int, double, double,
                                   double, double*);
 template int device_guess<float>(ofdft_ctx*, const ofdft_grid*, const double*, const double*, int, double, double,

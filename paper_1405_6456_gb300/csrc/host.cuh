@@ -90,6 +90,9 @@ struct ofdft_ctx {
   int mixed_ff = 0;                            // the last mixed Poisson solve ran the float-float residual pass
   int tma = 0;                                 // FP32 z-streaming passes stage planes by TMA where they can
   int pdl = 0;                                 // programmatic dependent launch for the CG-loop kernels
+  // the b_J tables in V_BTAB belong to this geometry (atoms, charges, grid,
+  // sigma, r_c, stencil radius); empty: none kept
+  std::vector<double> btab_key;
 };
 
 namespace ofd {
@@ -106,6 +109,7 @@ enum Vec {
   V_PHI2,                              // mixed: the FP64 potential as float-float pairs (residual pass)
   V_BACC,                              // FP64 running sums of the pseudocharge over atom ranges
   V_B2,                                // mixed: the FP64 pseudocharge as float-float pairs (residual pass)
+  V_BTAB,                              // b_J tables of every atom, kept from the pseudocharge for the forces
   V_COUNT
 };
 
@@ -632,7 +636,7 @@ int check_atoms(ofdft_ctx* c, const double* R, const double* Z, int M);
 int check_params(ofdft_ctx* c, const ofdft_params* p);
 template <typename T>
 int device_pseudocharge(ofdft_ctx* c, const ofdft_grid* gr, int R, const double* R_host, const double* Z_host,
-                        int M, double sigma, double rc, T* b, double* E_self);
+                        int M, double sigma, double rc, T* b, double* E_self, bool keep_tables = false);
 template <typename T>
 int device_guess(ofdft_ctx* c, const ofdft_grid* gr, const double* R_host, const double* Z_host, int M,
                  double gsig, double gcut, double N, T* u);

@@ -1205,14 +1205,16 @@ struct EpiFunctional {
     if (G) G[i] = gx;
     if (s) s[i] = sx;
     if (winv) winv[i] = wv;
-    // the gradient sums (line search, Polak-Ribiere beta, stopping test,
-    // rank-one correction) in plain FP32 per thread; the energy sums above stay
-    // compensated
-    if (d) acc[5].add_fast(gx, d[i]);
-    if (s_old) acc[6].add_fast(gx, s_old[i]);
+    // sums of terms of one sign (the stopping test's g^2 / diag, g.g, u^2 /
+    // diag) in plain FP32 per thread: no cancellation, so a thread's partial sum
+    // keeps FP32 relative accuracy; the sums of mixed-sign terms (line search,
+    // Polak-Ribiere beta, the rank-one correction's u.s), whose totals can be
+    // far smaller than their terms, stay compensated like the energy sums
+    if (d) acc[5].add(gx, d[i]);
+    if (s_old) acc[6].add(gx, s_old[i]);
     acc[7].add_fast(gx, -sx);  // g^2 / diag
     acc[8].add_fast(gx, gx);
-    acc[9].add_fast(uc, sx);
+    acc[9].add(uc, sx);
     acc[10].add_fast(uc, wv);  // u^2 / diag
   }
   __device__ __forceinline__ void operator()(double* t) const {
@@ -2517,10 +2519,15 @@ __device__ __forceinline__ double dist3_sq(double x, double y, double z) {
   return __dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z));
 }
 
-// Gaussian nucleus V(r) = -Z erf(r/sigma)/r and its r -> 0 limit.
+// Gaussian nucleus V(r) = -Z erf(r/sigma)/r and its r -> 0 limit.  From
+// r = 6 sigma on, 1 - erf(r/sigma) = erfc(r/sigma) < 2.2e-17 is below half a
+// unit in the last place of 1.0 (2^-54), so erf rounds to exactly 1 and
+// V = -Z/r; that skips the erf on most of an atom's table (r up to r_c + n h).
 __device__ __forceinline__ double gauss_v(double Z, double inv_sigma, double r) {
   if (r < 1e-12 / inv_sigma) return -2.0 * Z * inv_sigma * 0.56418958354775628;  // 1/sqrt(pi)
-  return -Z * erf(r * inv_sigma) / r;
+  const double x = r * inv_sigma;
+  if (x >= 6.0) return -Z / r;
+  return -Z * erf(x) / r;
 }
 
 // Conservative FP32 screen of node-to-atom distances.  The offset of a box's

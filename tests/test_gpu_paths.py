@@ -350,3 +350,25 @@ def test_programmatic_dependent_launch_is_bit_identical(ctx_fixed_pair):
     assert s0.converged and s1.converged
     assert E0 == E1
     assert np.array_equal(F0, F1)
+
+
+# ------------------------------------------------ kept atom tables (forces) --
+def test_forces_from_kept_tables_match_rebuilt_tables(ctx):
+    """A solve keeps the b_J tables of its pseudocharge pass for its forces
+    (Eq. Force:Nuclei needs the FD gradient of every b_J); forces of the same
+    potential from tables built afresh are the same bit for bit, and both match
+    the oracle's forces at that potential."""
+    c = W.cluster_c1()
+    g = F.ofdft_grid_for_atoms(c.R, c.h, c.vacuum, 16)
+    p = F.default_params(precision=F.PREC_FP64, vacuum=c.vacuum, round_to=16)
+    phi = torch.empty(g.shape, dtype=torch.float64, device=DEV)
+    _E, F_solve, st = ctx.solve(c.R, c.Z, c.h, p, grid=g, phi_out=phi)
+    assert st.converged
+    F_kept = ctx.forces(g, c.fd_order, c.R, c.Z, phi)
+    b = torch.empty(g.shape, dtype=torch.float64, device=DEV)
+    ctx.pseudocharge(g, c.fd_order, c.R, c.Z, b)  # a pseudocharge call of its own drops the kept tables
+    F_new = ctx.forces(g, c.fd_order, c.R, c.Z, phi)
+    assert np.array_equal(F_kept, F_new)
+    assert np.abs(F_solve - F_kept).max() <= 1e-12 * max(1.0, np.abs(F_kept).max())
+    F_ref = O.forces(_ogrid(g), c.fd_order // 2, c.R, c.Z, _h(phi))
+    assert np.abs(F_new - F_ref).max() <= 1e-10 * max(1.0, np.abs(F_ref).max())
