@@ -132,7 +132,17 @@ int mg_vcycle(ofdft_ctx* c, const MgPlan& P, const T* r, T* z, CgScalars* sc) {
   // tiles), smaller ones the four plain passes (more blocks for little work)
   auto fused = [&](int l) { return c->mg_fuse_nodes >= 0 && mg_nodes(P.d[l]) >= c->mg_fuse_nodes; };
   const T om = (T)c->mg_omega;
+  // mg_finest_smooth == 0: the finest level is not smoothed (its smoother is
+  // the scaled identity s r alone): r_c = R r and z = s r + P e_c.  M stays
+  // symmetric positive definite (s > 0, R = P^T / 8, M_c SPD).
+  const bool smooth0 = c->mg_finest_smooth != 0;
   for (int l = 0; l < P.lc; ++l) {
+    if (l == 0 && !smooth0) {
+      ProfScope ps_(c, OFDFT_K_MG);
+      CU(launch_k(c, mg_restrict_kernel<T>, dim3(rows_blocks(P.d[1])), dim3(256), 0, P.d[0], P.d[1], r, rl(1),
+                  (const CgScalars*)sc));
+      continue;
+    }
     if (fused(l)) {
       using D = MgDR<T>;
       const MgLevel& dc = P.d[l + 1];
@@ -167,6 +177,12 @@ int mg_vcycle(ofdft_ctx* c, const MgPlan& P, const T* r, T* z, CgScalars* sc) {
   }
   for (int l = P.lc - 1; l >= 0; --l) {
     s *= 0.25;
+    if (l == 0 && !smooth0) {
+      ProfScope ps_(c, OFDFT_K_MG);
+      CU(launch_k(c, mg_prolong_kernel<T, true>, dim3(pointwise_blocks(c, mg_nodes(P.d[0]))), dim3(256), 0, P.d[0],
+                  P.d[1], r, (const T*)zl(1), z, (T)s, sc, red(c)));
+      continue;
+    }
     if (fused(l)) {
       using D = MgPU<T>;
       const MgLevel& df = P.d[l];
@@ -182,8 +198,8 @@ int mg_vcycle(ofdft_ctx* c, const MgPlan& P, const T* r, T* z, CgScalars* sc) {
     }
     {
       ProfScope ps_(c, OFDFT_K_MG);
-      CU(launch_k(c, mg_prolong_kernel<T>, dim3(rows_blocks(P.d[l])), dim3(256), 0, P.d[l], P.d[l + 1],
-                  (const T*)rl(l), (const T*)zl(l + 1), tl(l), (T)s, (const CgScalars*)sc));
+      CU(launch_k(c, mg_prolong_kernel<T, false>, dim3(rows_blocks(P.d[l])), dim3(256), 0, P.d[l], P.d[l + 1],
+                  (const T*)rl(l), (const T*)zl(l + 1), tl(l), (T)s, sc, RedBuf{}));
     }
     ProfScope ps_(c, OFDFT_K_MG);
     if (l == 0)
@@ -200,7 +216,9 @@ int mg_vcycle(ofdft_ctx* c, const MgPlan& P, const T* r, T* z, CgScalars* sc) {
 inline int mg_launches(const ofdft_ctx* c, const MgPlan& P) {
   if (!P.ok) return 0;
   int n = 1;
-  for (int l = 0; l < P.lc; ++l) n += (c->mg_fuse_nodes >= 0 && mg_nodes(P.d[l]) >= c->mg_fuse_nodes) ? 2 : 4;
+  for (int l = 0; l < P.lc; ++l)
+    n += (l == 0 && !c->mg_finest_smooth) ? 2
+                                          : (c->mg_fuse_nodes >= 0 && mg_nodes(P.d[l]) >= c->mg_fuse_nodes) ? 2 : 4;
   return n;
 }
 
@@ -1822,6 +1840,8 @@ int ofdft_create(ofdft_ctx** out, int device, void* stream) {
   if (ms && atoi(ms) >= 1) c->mg_sweeps = atoi(ms);
   const char* cz = getenv("OFDFT_COOP_NZ");  // launch-shape experiments: z-chunks of the persistent CG grid
   c->coop_nz = cz ? atoi(cz) : 0;
+  const char* m0 = getenv("OFDFT_MG_FINEST_SMOOTH");  // 0: no smoothing on the finest multigrid level
+  if (m0) c->mg_finest_smooth = atoi(m0) != 0;
   const char* pdl = getenv("OFDFT_PDL");  // 1: programmatic dependent launch in the CG loop
   c->pdl = (pdl && pdl[0] == '1') ? 1 : 0;
   const char* tma = getenv("OFDFT_TMA");  // 1: TMA staging in the FP32 z-streaming passes that allow it

@@ -1692,19 +1692,33 @@ struct MgFin {
   }
 };
 
-// up, first half: y = s r + P e_c.
-template <typename T>
+// up, first half: y = s r + P e_c.  With DOT this is the whole up step of a
+// level that is not smoothed (the finest level with mg_finest_smooth = 0:
+// z = s r + P e_c), with r.z and the PCG scalars.
+template <typename T, bool DOT>
 __global__ void __launch_bounds__(256) mg_prolong_kernel(MgLevel f, MgLevel c, const T* __restrict__ r,
                                                          const T* __restrict__ ec, T* __restrict__ y, T s,
-                                                         const CgScalars* sc) {
+                                                         CgScalars* sc, RedBuf red) {
   pdl_enter();
+  __shared__ double smem[256 / 32];
   if (sc->done) return;
   const int rows = f.n2 * f.n3;
   const int lane = threadIdx.x & 31;
+  DotAcc<T> acc;
   for (int row = blockIdx.x * 8 + (threadIdx.x >> 5); row < rows; row += gridDim.x * 8) {
     const int k = row / f.n2, j = row - k * f.n2;
     const long long o = (long long)row * f.n1;
-    for (int i = lane; i < f.n1; i += 32) y[o + i] = s * r[o + i] + mg_prolong_at(ec, c, i, j, k);
+    for (int i = lane; i < f.n1; i += 32) {
+      const T ri = r[o + i];
+      const T yi = s * ri + mg_prolong_at(ec, c, i, j, k);
+      y[o + i] = yi;
+      if constexpr (DOT) acc.add(ri, yi);
+    }
+  }
+  if constexpr (DOT) {
+    double v[1] = {acc.value()};
+    MgFin fin{sc};
+    grid_sum<1, 256>(v, smem, red, gridDim.x, blockIdx.x, threadIdx.x, fin);
   }
 }
 

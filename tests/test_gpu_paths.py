@@ -372,3 +372,46 @@ def test_forces_from_kept_tables_match_rebuilt_tables(ctx):
     assert np.abs(F_solve - F_kept).max() <= 1e-12 * max(1.0, np.abs(F_kept).max())
     F_ref = O.forces(_ogrid(g), c.fd_order // 2, c.R, c.Z, _h(phi))
     assert np.abs(F_new - F_ref).max() <= 1e-10 * max(1.0, np.abs(F_ref).max())
+
+
+# ------------------------------------- V-cycle without finest-level smoothing --
+@pytest.fixture(scope="module")
+def ctx_nosmooth0(ctx):
+    """A context whose V-cycle skips the Jacobi sweeps on the finest level
+    (z = s r + P e_c there), the cheaper preconditioner OFDFT_MG_FINEST_SMOOTH=0
+    selects."""
+    c = _context(OFDFT_MG_FINEST_SMOOTH=0, OFDFT_TMA=0)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("dims,order", [((48, 40, 36), 12), ((37, 29, 23), 6), ((64, 64, 64), 12)])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_multigrid_without_finest_smoothing_matches_oracle(ctx_nosmooth0, dims, order, dtype):
+    """The preconditioner stays symmetric positive definite without the finest
+    level's sweeps, so the PCG still reaches the oracle's phi at the requested
+    residual, in at most a third of plain CG's iterations."""
+    g = F.make_grid(*dims, 0.5)
+    rho_h = np.random.default_rng(6).standard_normal(g.shape)
+    tol = 1e-10 if dtype == torch.float64 else 1e-9
+    phi_ref, it_ref, _ = O.poisson(_ogrid(g), order // 2, rho_h, tol=1e-12)
+    ctx_nosmooth0.reset_counters()
+    phi = torch.zeros(g.shape, dtype=dtype, device=DEV)
+    st = ctx_nosmooth0.poisson(g, order, phi, rho=_t(rho_h, dtype), tol=tol)
+    assert st.rel_residual <= tol
+    assert ctx_nosmooth0.counters().kind_launches[F.K_MG] > 0
+    err = np.abs(_h(phi) - phi_ref).max() / np.abs(phi_ref).max()
+    assert err <= (1e-8 if dtype == torch.float64 else 2e-6)
+    assert st.iterations <= max(40, it_ref // 3)
+
+
+def test_multigrid_without_finest_smoothing_ground_state(ctx, ctx_nosmooth0):
+    """The MIXED ground state of the 13-atom cluster with the cheaper cycle
+    agrees with the default cycle's within the solver tolerances."""
+    cl = W.cluster_c1()
+    p = F.default_params(precision=F.PREC_MIXED)
+    E0, F0, s0 = ctx.solve(cl.R, cl.Z, cl.h, p)
+    E1, F1, s1 = ctx_nosmooth0.solve(cl.R, cl.Z, cl.h, p)
+    assert s0.converged and s1.converged
+    assert abs(E1 - E0) / cl.M <= 1e-6
+    assert np.abs(F1 - F0).max() <= 1e-4
