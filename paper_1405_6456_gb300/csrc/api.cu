@@ -701,10 +701,13 @@ int poisson_fp64(ofdft_ctx* c, int R, const GridDev& g, double h, const double* 
 // keeps the search direction after the first round, so no Krylov information is
 // lost; preconditioned CG restarts from p = z) and FP32 iterations run until the FP32 residual falls by mixed_inner_tol (1e-4,
 // or less when the FP64 test needs less) or refine_every steps.  At the end
-// phi32 = (float) phi64.  rho32 (optional) replaces u^2 + b.
+// phi32 = (float) phi64.  rho32 (optional) replaces u^2 + b.  b2_valid
+// (optional): the caller's flag that V_B2 already holds b64 as float-float
+// pairs (the pseudocharge is fixed for a whole ground state, so a solve splits
+// it once); set here after a split.
 int poisson_mixed(ofdft_ctx* c, int R, const GridDev& g, double h, const float* rho32, const float* u,
                   const double* b64, double* phi64, float* phi32, double tol, int max_it, int refine_every,
-                  ofdft_cg_stats* st) {
+                  ofdft_cg_stats* st, int* b2_valid = nullptr) {
   TRY(ensure_cg_vectors(c, g.G, sizeof(float), true));
   const Weights<double> W = lap_weights(R, h, 1.0), Wneg = lap_weights(R, h, -1.0);
   double* r64 = vec<double>(c, V_R64);
@@ -730,8 +733,13 @@ int poisson_mixed(ofdft_ctx* c, int R, const GridDev& g, double h, const float* 
       TRY(ensure(c, c->v[V_B2], g.G * sizeof(float2)));
       b2 = vec<float2>(c, V_B2);
     }
-    ProfScope ps_(c, OFDFT_K_VECTOR);
-    ff_split_kernel<<<pb, 256, 0, c->stream>>>(g.G, phi2, phi64, b2, b64);
+    const bool split_b = b2 && !(b2_valid && *b2_valid);
+    {
+      ProfScope ps_(c, OFDFT_K_VECTOR);
+      ff_split_kernel<<<pb, 256, 0, c->stream>>>(g.G, phi2, phi64, split_b ? b2 : nullptr, b64);
+    }
+    CU(cudaGetLastError());
+    if (split_b && b2_valid) *b2_valid = 1;
   }
   const float2 fourpi = ff_of(4.0 * kPi);
   for (int round = 0; round <= max_rounds; ++round) {
@@ -923,6 +931,7 @@ struct Solver {
   ofdft_solve_stats* stats;
   ofdft_energy e;  // at the current point
   int trace = 0;   // OFDFT_TRACE=1: one line per evaluation on stderr
+  int b2_valid = 0;  // mixed: V_B2 holds b64 as float-float pairs (split by the first Poisson solve)
 
   int eval(const T* at, T* Gout, T* sout, const T* dd, const T* s_old, double eta, double mu, ofdft_energy* out) {
     const int rc = eval_inner(at, Gout, sout, dd, s_old, eta, mu, out);
@@ -945,7 +954,7 @@ struct Solver {
                           &cs);
       else
         rc = poisson_mixed(c, R, g, h, nullptr, (const float*)at, b64, phi64, (float*)phi, tol_p, p->max_cg,
-                           std::max(p->refine_every, 1), &cs);
+                           std::max(p->refine_every, 1), &cs, &b2_valid);
       if (rc != OFDFT_OK) return rc;
       stats->stencil_apps += cs.iterations + 1;
       stats->cg_iters += cs.iterations;

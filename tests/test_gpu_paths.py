@@ -415,3 +415,16 @@ def test_multigrid_without_finest_smoothing_ground_state(ctx, ctx_nosmooth0):
     assert s0.converged and s1.converged
     assert abs(E1 - E0) / cl.M <= 1e-6
     assert np.abs(F1 - F0).max() <= 1e-4
+
+
+def test_fp32_initial_guess_matches_oracle(ctx):
+    """The starting guess of an FP32 field (MIXED) evaluates its Gaussians in
+    FP32 (the cut at guess_cut decided in FP64): within FP32 rounding of the
+    oracle's guess, normalised the same way."""
+    c = W.cluster_c1()
+    g = F.ofdft_grid_for_atoms(c.R, c.h, c.vacuum, 16)
+    u = torch.empty(g.shape, dtype=torch.float32, device=DEV)
+    ctx.initial_guess(g, c.R, c.Z, u)
+    u_ref = O.initial_guess(_ogrid(g), c.R, c.Z)
+    assert np.abs(_h(u) - u_ref).max() <= 2e-6 * np.abs(u_ref).max()
+    assert np.sum(_h(u).astype(np.float64) ** 2) * g.h ** 3 == pytest.approx(c.Z.sum(), rel=1e-6)
