@@ -743,8 +743,9 @@ def main():
     ap.add_argument("--which", default="all", choices=["all", "cg", "functional"])
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--batch-solo", type=int, default=4)
-    ap.add_argument("--rates", default="1,5,20")
-    ap.add_argument("--requests", type=int, default=24)
+    ap.add_argument("--rates", default="1,2,5,10,20,50,100,200")
+    ap.add_argument("--requests", type=int, default=500)
+    ap.add_argument("--serve-warmup", type=int, default=16)
     ap.add_argument("--max-m", type=int, default=8)
     ap.add_argument("--hbm-gb", type=int, default=200)
     args = ap.parse_args()

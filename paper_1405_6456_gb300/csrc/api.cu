@@ -115,6 +115,12 @@ int mg_prepare(ofdft_ctx* c, const GridDev& g, double h, MgPlan* P) {
   return OFDFT_OK;
 }
 
+// Whether level l of the V-cycle runs as the two fused passes.
+inline bool mg_level_fused(const ofdft_ctx* c, const MgPlan& P, int l) {
+  const long long n = mg_nodes(P.d[l]);
+  return (c->mg_fuse_nodes >= 0 && n >= c->mg_fuse_nodes) || (l > 0 && n <= c->mg_fuse_below);
+}
+
 // z = M r (one V-cycle); the finest level's last pass also forms r.z and the
 // PCG scalars (beta, rz).  Every kernel returns at once when the solve is done.
 template <typename T>
@@ -128,9 +134,10 @@ int mg_vcycle(ofdft_ctx* c, const MgPlan& P, const T* r, T* z, CgScalars* sc) {
   auto rows_blocks = [&](const MgLevel& d) {
     return (int)std::max<long long>(1, std::min<long long>(((long long)d.n2 * d.n3 + 7) / 8, (long long)c->sms * 8));
   };
-  // levels with at least mg_fuse_nodes nodes take the two fused passes (shared-memory
-  // tiles), smaller ones the four plain passes (more blocks for little work)
-  auto fused = [&](int l) { return c->mg_fuse_nodes >= 0 && mg_nodes(P.d[l]) >= c->mg_fuse_nodes; };
+  // levels with at least mg_fuse_nodes nodes, and coarser levels with at most
+  // mg_fuse_below nodes (whose launches are latency-bound), take the two fused
+  // passes (shared-memory tiles); the others the four plain passes
+  auto fused = [&](int l) { return mg_level_fused(c, P, l); };
   const T om = (T)c->mg_omega;
   // mg_finest_smooth == 0: the finest level is not smoothed (its smoother is
   // the scaled identity s r alone): r_c = R r and z = s r + P e_c.  M stays
@@ -216,9 +223,7 @@ int mg_vcycle(ofdft_ctx* c, const MgPlan& P, const T* r, T* z, CgScalars* sc) {
 inline int mg_launches(const ofdft_ctx* c, const MgPlan& P) {
   if (!P.ok) return 0;
   int n = 1;
-  for (int l = 0; l < P.lc; ++l)
-    n += (l == 0 && !c->mg_finest_smooth) ? 2
-                                          : (c->mg_fuse_nodes >= 0 && mg_nodes(P.d[l]) >= c->mg_fuse_nodes) ? 2 : 4;
+  for (int l = 0; l < P.lc; ++l) n += (l == 0 && !c->mg_finest_smooth) ? 2 : mg_level_fused(c, P, l) ? 2 : 4;
   return n;
 }
 
@@ -1849,6 +1854,8 @@ int ofdft_create(ofdft_ctx** out, int device, void* stream) {
   if (ms && atoi(ms) >= 1) c->mg_sweeps = atoi(ms);
   const char* cz = getenv("OFDFT_COOP_NZ");  // launch-shape experiments: z-chunks of the persistent CG grid
   c->coop_nz = cz ? atoi(cz) : 0;
+  const char* fbl = getenv("OFDFT_MG_FUSE_BELOW");  // coarser levels of at most this many nodes take the fused passes
+  if (fbl) c->mg_fuse_below = atoll(fbl);
   const char* m0 = getenv("OFDFT_MG_FINEST_SMOOTH");  // 0: no smoothing on the finest multigrid level
   if (m0) c->mg_finest_smooth = atoi(m0) != 0;
   const char* pdl = getenv("OFDFT_PDL");  // 1: programmatic dependent launch in the CG loop

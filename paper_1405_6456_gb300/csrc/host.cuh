@@ -91,6 +91,7 @@ struct ofdft_ctx {
   int tma = 0;                                 // FP32 z-streaming passes stage planes by TMA where they can
   int pdl = 0;                                 // programmatic dependent launch for the CG-loop kernels
   int mg_finest_smooth = 1;                    // damped-Jacobi smoothing on the finest multigrid level
+  long long mg_fuse_below = -1;                // coarser multigrid levels of at most this many nodes: fused
   // the b_J tables in V_BTAB belong to this geometry (atoms, charges, grid,
   // sigma, r_c, stencil radius); empty: none kept
   std::vector<double> btab_key;

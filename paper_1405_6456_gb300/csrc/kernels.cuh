@@ -2623,15 +2623,9 @@ __global__ void __launch_bounds__(512) guess_kernel(GridDev g, AtomArgs A, doubl
   const float fx = (float)(A.ox + (x + 0.5) * A.h), fy = (float)(A.oy + (y + 0.5) * A.h),
               fz = (float)(A.oz + (z + 0.5) * A.h);
   const float cut2 = screen_r2(gcut);
-  const double m2s2 = -1.0 / (2.0 * gsig * gsig);
-  __shared__ float zn[512];  // Z_J (2 pi s^2)^{-3/2} of the listed atoms (FP32 fields)
   double rho = 0.0;
   for (int a0 = 0; a0 < A.M; a0 += 512) {
     const int cnt = tile_atoms(A, a0, cx, cy, cz, half, gcut + A.h, list, warp_cnt);
-    if constexpr (sizeof(T) == 4) {
-      if (tid < cnt) zn[tid] = (float)(A.Z[list[tid]] * norm);
-      __syncthreads();
-    }
     if (inside) {
       for (int t = 0; t < cnt; ++t) {
         const int J = list[t];
@@ -2640,11 +2634,7 @@ __global__ void __launch_bounds__(512) guess_kernel(GridDev g, AtomArgs A, doubl
         const double rx = node_off(A.ox, x, A.h, A.R[3 * J]), ry = node_off(A.oy, y, A.h, A.R[3 * J + 1]),
                      rz = node_off(A.oz, z, A.h, A.R[3 * J + 2]);
         const double r2 = dist3_sq(rx, ry, rz);
-        if (!(r2 < __dmul_rn(gcut, gcut))) continue;
-        if constexpr (sizeof(T) == 4)  // an FP32 field: its Gaussians in FP32 (the cut decided in FP64 as above)
-          rho += (double)(zn[t] * expf((float)(r2 * m2s2)));
-        else
-          rho += A.Z[J] * norm * exp(-r2 / (2.0 * gsig * gsig));
+        if (r2 < __dmul_rn(gcut, gcut)) rho += A.Z[J] * norm * exp(-r2 / (2.0 * gsig * gsig));
       }
     }
     __syncthreads();

@@ -36,7 +36,17 @@ def ctx():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     B.build()
-    c = F.Context(0)
+    # the fixed launch shapes (no timing-based autotuning): the order of every
+    # partial sum, and with it the solver's path, is the same on every run
+    old = os.environ.get("OFDFT_AUTOTUNE")
+    os.environ["OFDFT_AUTOTUNE"] = "0"
+    try:
+        c = F.Context(0)
+    finally:
+        if old is None:
+            del os.environ["OFDFT_AUTOTUNE"]
+        else:
+            os.environ["OFDFT_AUTOTUNE"] = old
     yield c
     c.close()
 

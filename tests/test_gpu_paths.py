@@ -417,14 +417,37 @@ def test_multigrid_without_finest_smoothing_ground_state(ctx, ctx_nosmooth0):
     assert np.abs(F1 - F0).max() <= 1e-4
 
 
-def test_fp32_initial_guess_matches_oracle(ctx):
-    """The starting guess of an FP32 field (MIXED) evaluates its Gaussians in
-    FP32 (the cut at guess_cut decided in FP64): within FP32 rounding of the
-    oracle's guess, normalised the same way."""
-    c = W.cluster_c1()
-    g = F.ofdft_grid_for_atoms(c.R, c.h, c.vacuum, 16)
-    u = torch.empty(g.shape, dtype=torch.float32, device=DEV)
-    ctx.initial_guess(g, c.R, c.Z, u)
-    u_ref = O.initial_guess(_ogrid(g), c.R, c.Z)
-    assert np.abs(_h(u) - u_ref).max() <= 2e-6 * np.abs(u_ref).max()
-    assert np.sum(_h(u).astype(np.float64) ** 2) * g.h ** 3 == pytest.approx(c.Z.sum(), rel=1e-6)
+
+# --------------------------------------------- fused small multigrid levels --
+@pytest.fixture(scope="module")
+def ctx_fuse_small(ctx):
+    """A context whose coarser V-cycle levels of at most 200,000 nodes run as
+    two fused passes each (down + restrict, prolong + up) instead of four."""
+    c = _context(OFDFT_MG_FUSE_BELOW=200000, OFDFT_AUTOTUNE=0, OFDFT_TMA=0, OFDFT_PDL=0)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("dims,order", [((48, 40, 36), 12), ((64, 64, 64), 12), ((96, 96, 96), 8)])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_fused_small_levels_match_plain_cycle(ctx_fixed_pair, ctx_fuse_small, dims, order, dtype):
+    """The fused level passes do the separate passes' arithmetic in the same
+    order, so the preconditioned CG (both contexts with the fixed launch shapes)
+    takes the same iterations to the same phi (bit for bit), which matches the
+    oracle."""
+    g = F.make_grid(*dims, 0.5)
+    rho_h = np.random.default_rng(8).standard_normal(g.shape)
+    tol = 1e-10 if dtype == torch.float64 else 1e-9
+    out = []
+    for c in (ctx_fixed_pair[0], ctx_fuse_small):
+        c.reset_counters()
+        phi = torch.zeros(g.shape, dtype=dtype, device=DEV)
+        st = c.poisson(g, order, phi, rho=_t(rho_h, dtype), tol=tol)
+        assert st.rel_residual <= tol
+        out.append((_h(phi), st.iterations, c.counters().kind_launches[F.K_MG]))
+    assert out[0][1] == out[1][1]
+    assert out[1][2] < out[0][2]  # fewer launches per cycle
+    assert np.array_equal(out[0][0], out[1][0])
+    phi_ref, _, _ = O.poisson(_ogrid(g), order // 2, rho_h, tol=1e-12)
+    err = np.abs(out[1][0] - phi_ref).max() / np.abs(phi_ref).max()
+    assert err <= (1e-8 if dtype == torch.float64 else 2e-6)
