@@ -110,6 +110,8 @@ int mg_prepare(ofdft_ctx* c, const GridDev& g, double h, MgPlan* P) {
   if (!attr_dev[c->device]) {
     CU(cudaFuncSetAttribute(mg_coarse_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     CU(cudaFuncSetAttribute(mg_coarse_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    CU(cudaFuncSetAttribute(mg_cluster_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)kMgClusterSmem));
     attr_dev[c->device] = true;
   }
   return OFDFT_OK;
@@ -143,7 +145,10 @@ int mg_vcycle(ofdft_ctx* c, const MgPlan& P, const T* r, T* z, CgScalars* sc) {
   // the scaled identity s r alone): r_c = R r and z = s r + P e_c.  M stays
   // symmetric positive definite (s > 0, R = P^T / 8, M_c SPD).
   const bool smooth0 = c->mg_finest_smooth != 0;
-  for (int l = 0; l < P.lc; ++l) {
+  // levels lq .. lc-1 and the coarse end on one thread-block cluster
+  const bool clus = c->mg_cluster && P.lq > 0;
+  const int ltop = clus ? P.lq : P.lc;  // levels above run as separate passes
+  for (int l = 0; l < ltop; ++l) {
     if (l == 0 && !smooth0) {
       ProfScope ps_(c, OFDFT_K_MG);
       CU(launch_k(c, mg_restrict_kernel<T>, dim3(rows_blocks(P.d[1])), dim3(256), 0, P.d[0], P.d[1], r, rl(1),
@@ -172,7 +177,30 @@ int mg_vcycle(ofdft_ctx* c, const MgPlan& P, const T* r, T* z, CgScalars* sc) {
   }
   double s = P.s0;
   for (int l = 0; l < P.lc; ++l) s *= 4.0;
-  {
+  if (clus) {
+    MgClusterArgs<T> A;
+    double sl = P.s0;
+    for (int l = 0; l <= P.lc; ++l, sl *= 4.0) {
+      if (l >= P.lq) {
+        A.L[l] = P.slab[l];
+        A.s[l] = (T)sl;
+      }
+    }
+    A.lq = P.lq;
+    A.lc = P.lc;
+    A.ncoarse = P.nlev - P.lc;
+    A.r_in = rl(P.lq);
+    A.z_out = zl(P.lq);
+    A.r_tail = rl(P.lc);
+    A.z_tail = zl(P.lc);
+    A.tail_off = P.tail_off;
+    A.omega = om;
+    A.sweeps = c->mg_sweeps;
+    ProfScope ps_(c, OFDFT_K_MG);
+    CU(launch_k(c, mg_cluster_kernel<T>, dim3(kMgClusterCtas), dim3(1024), P.csmem, A, sc));
+    for (int l = P.lc - 1; l >= P.lq; --l) s *= 0.25;
+  }
+  if (!clus) {
     ProfScope ps_(c, OFDFT_K_MG);
     const int nl = P.nlev - P.lc;
     if (P.lc == 0)
@@ -182,7 +210,7 @@ int mg_vcycle(ofdft_ctx* c, const MgPlan& P, const T* r, T* z, CgScalars* sc) {
       CU(launch_k(c, mg_coarse_kernel<T, false>, dim3(1), dim3(1024), P.smem, P.d[P.lc], nl, (const T*)rl(P.lc),
                   zl(P.lc), om, (T)s, c->mg_sweeps, sc));
   }
-  for (int l = P.lc - 1; l >= 0; --l) {
+  for (int l = ltop - 1; l >= 0; --l) {
     s *= 0.25;
     if (l == 0 && !smooth0) {
       ProfScope ps_(c, OFDFT_K_MG);
@@ -223,7 +251,8 @@ int mg_vcycle(ofdft_ctx* c, const MgPlan& P, const T* r, T* z, CgScalars* sc) {
 inline int mg_launches(const ofdft_ctx* c, const MgPlan& P) {
   if (!P.ok) return 0;
   int n = 1;
-  for (int l = 0; l < P.lc; ++l) n += (l == 0 && !c->mg_finest_smooth) ? 2 : mg_level_fused(c, P, l) ? 2 : 4;
+  const int ltop = (c->mg_cluster && P.lq > 0) ? P.lq : P.lc;
+  for (int l = 0; l < ltop; ++l) n += (l == 0 && !c->mg_finest_smooth) ? 2 : mg_level_fused(c, P, l) ? 2 : 4;
   return n;
 }
 
@@ -1854,6 +1883,8 @@ int ofdft_create(ofdft_ctx** out, int device, void* stream) {
   if (ms && atoi(ms) >= 1) c->mg_sweeps = atoi(ms);
   const char* cz = getenv("OFDFT_COOP_NZ");  // launch-shape experiments: z-chunks of the persistent CG grid
   c->coop_nz = cz ? atoi(cz) : 0;
+  const char* mcl = getenv("OFDFT_MG_CLUSTER");  // 1: coarse multigrid levels on one thread-block cluster
+  if (mcl) c->mg_cluster = atoi(mcl) != 0;
   const char* fbl = getenv("OFDFT_MG_FUSE_BELOW");  // coarser levels of at most this many nodes take the fused passes
   if (fbl) c->mg_fuse_below = atoll(fbl);
   const char* m0 = getenv("OFDFT_MG_FINEST_SMOOTH");  // 0: no smoothing on the finest multigrid level

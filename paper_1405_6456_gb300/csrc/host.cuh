@@ -92,6 +92,7 @@ struct ofdft_ctx {
   int pdl = 0;                                 // programmatic dependent launch for the CG-loop kernels
   int mg_finest_smooth = 1;                    // damped-Jacobi smoothing on the finest multigrid level
   long long mg_fuse_below = -1;                // coarser multigrid levels of at most this many nodes: fused
+  int mg_cluster = 0;                          // coarse levels on one thread-block cluster (mg_cluster_kernel)
   // the b_J tables in V_BTAB belong to this geometry (atoms, charges, grid,
   // sigma, r_c, stencil radius); empty: none kept
   std::vector<double> btab_key;
@@ -397,7 +398,14 @@ struct MgPlan {
   size_t smem = 0;                    // shared memory of the one-block kernel
   double s0 = 0.0;                    // omega h^2 / 6 of the finest level
   bool ok = false;
+  // the cluster end (mg_cluster_kernel): levels lq .. lc-1 in the distributed
+  // shared memory of one thread-block cluster (lq < 0: none fits)
+  int lq = -1;
+  MgSlab slab[kMgMaxLevels];
+  size_t csmem = 0;       // dynamic shared memory per block of the cluster kernel
+  unsigned tail_off = 0;  // byte offset of block 0's coarse-end arrays
 };
+constexpr size_t kMgClusterSmem = 220 * 1024;  // dynamic shared memory per cluster block (of 227 KB)
 
 inline long long mg_nodes(const MgLevel& d) { return (long long)d.n1 * d.n2 * d.n3; }
 
@@ -428,6 +436,24 @@ inline MgPlan mg_plan(const GridDev& g, double h, size_t es, double omega = kMgO
   P.smem = sm;
   P.s0 = omega * h * h / 6.0;
   P.ok = sm <= 200 * 1024;
+  if (!P.ok) return P;
+  // the cluster end: the most levels above lc (level 0 excluded: its pass forms
+  // r.z) whose z-plane slabs, with the coarse end's arrays in block 0, fit
+  for (int lq = 1; lq < P.lc && P.lq < 0; ++lq) {
+    size_t off = 0;  // bytes
+    for (int l = lq; l < P.lc; ++l) {
+      const MgLevel& d = P.d[l];
+      const int pl = (d.n3 + kMgClusterCtas - 1) / kMgClusterCtas;
+      P.slab[l] = MgSlab{d, pl, (unsigned)(off / es)};
+      off += ((3 * (size_t)pl * d.n1 * d.n2 * es + 15) / 16) * 16;
+    }
+    P.slab[P.lc] = MgSlab{P.d[P.lc], 0, 0};
+    if (off + sm <= kMgClusterSmem) {
+      P.lq = lq;
+      P.tail_off = (unsigned)off;
+      P.csmem = off + sm;
+    }
+  }
   return P;
 }
 

@@ -7,6 +7,8 @@
 #include <cuda.h>  // CUtensorMap (the type only; no driver call is made from here)
 #include <math.h>
 
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 
 namespace ofd {
@@ -1911,7 +1913,8 @@ __global__ void __launch_bounds__(256) mg_prolong_up_kernel(MgLevel f, MgLevel c
 // the block also forms r.z and the PCG scalars.
 template <typename T, bool DOT>
 __device__ __forceinline__ void mg_coarse_body(MgLevel d0, int nlev, const T* __restrict__ r, T* __restrict__ z,
-                                               T omega, T s0, int sweeps, CgScalars* sc) {
+                                               T omega, T s0, int sweeps, CgScalars* sc,
+                                               unsigned char* smbase = nullptr) {
   extern __shared__ __align__(16) unsigned char mg_sm[];
   __shared__ double red_sm[1024 / 32];
   if (sc->done) return;
@@ -1921,7 +1924,7 @@ __device__ __forceinline__ void mg_coarse_body(MgLevel d0, int nlev, const T* __
   T* Rl[kMgMaxLevels];
   T* Zl[kMgMaxLevels];
   T* Wl[kMgMaxLevels];
-  T* p = reinterpret_cast<T*>(mg_sm);
+  T* p = reinterpret_cast<T*>(smbase ? smbase : mg_sm);
   d[0] = d0;
   for (int l = 0; l < nlev; ++l) {
     if (l > 0) d[l] = MgLevel{d[l - 1].n1 / 2, d[l - 1].n2 / 2, d[l - 1].n3 / 2};
@@ -2020,6 +2023,216 @@ __global__ void __launch_bounds__(1024) mg_coarse_kernel(MgLevel d0, int nlev, c
                                                          CgScalars* sc) {
   pdl_enter();
   mg_coarse_body<T, DOT>(d0, nlev, r, z, omega, s0, sweeps, sc);
+}
+
+// The coarse end of the V-cycle on one thread-block cluster (single grids).
+// Levels lq .. lc-1, each small enough that its launches are latency-bound,
+// live in the distributed shared memory of kMgClusterCtas blocks: level l's
+// three arrays (r, w = t or y, z) are split by z-planes, block q of the
+// cluster holding planes [q P_l, (q + 1) P_l) at the same offset of its own
+// shared memory, and every pass reads its neighbours (other blocks' planes
+// included) through the cluster's shared-memory window.  A cluster barrier
+// (hardware, all blocks co-scheduled) separates the passes.  Levels lc and
+// below run as the one-block coarse end in block 0 (global r and z of level
+// lc).  Every node's arithmetic, and its order, are those of the separate
+// level passes (mg_down / restrict / prolong / up) and of mg_coarse_kernel, so
+// the cycle, and the PCG, are the same bit for bit.
+constexpr int kMgClusterCtas = 8;  // the portable cluster size
+struct MgSlab {
+  MgLevel d;
+  int P;         // z-planes per block
+  unsigned off;  // element offset of the level's arrays in each block's shared memory
+};
+template <typename T>
+struct MgClusterArgs {
+  MgSlab L[kMgMaxLevels];
+  T s[kMgMaxLevels];  // the cycle's scale s at each level, as the host forms it
+  int lq, lc, ncoarse;  // first cluster level, the coarse-end level, levels of the coarse end
+  const T* r_in;      // r of level lq (global)
+  T* z_out;           // z of level lq (global)
+  T* r_tail;          // r of level lc (global)
+  T* z_tail;          // z of level lc (global)
+  unsigned tail_off;  // byte offset of block 0's coarse-end arrays
+  T omega;
+  int sweeps;
+};
+
+// Rows (fixed j, k; contiguous in x) of array a of a cluster level, wherever
+// in the cluster they live.
+template <typename T>
+struct MgRows {
+  T* sm;  // this block's shared memory (element type)
+  MgSlab L;
+  int a;
+  __device__ __forceinline__ T* operator()(int j, int k) const {
+    namespace cg = cooperative_groups;
+    const int q = k / L.P;
+    T* local = sm + L.off + (size_t)a * L.P * L.d.n1 * L.d.n2 + ((size_t)(k - q * L.P) * L.d.n2 + j) * L.d.n1;
+    return cg::this_cluster().map_shared_rank(local, q);
+  }
+};
+
+// The level passes' per-node formulas over row accessors, in the order of
+// mg_nb_sum, mg_restrict_at and mg_prolong_at.
+template <typename T, class Rows>
+__device__ __forceinline__ T mgc_nb_sum(const Rows& f, int i, int j, int k, const MgLevel& d) {
+  const T* row = f(j, k);
+  T s = T(0);
+  if (i > 0) s += row[i - 1];
+  if (i + 1 < d.n1) s += row[i + 1];
+  if (j > 0) s += f(j - 1, k)[i];
+  if (j + 1 < d.n2) s += f(j + 1, k)[i];
+  if (k > 0) s += f(j, k - 1)[i];
+  if (k + 1 < d.n3) s += f(j, k + 1)[i];
+  return s;
+}
+template <typename T, class Rows>
+__device__ __forceinline__ T mgc_restrict_at(const Rows& t, const MgLevel& f, int I, int J, int K) {
+  T acc = T(0);
+#pragma unroll
+  for (int dk = 0; dk < 3; ++dk) {
+    const int kk = 2 * K + dk;
+    if (kk >= f.n3) continue;
+    const T wz = dk == 1 ? T(0.5) : T(0.25);
+#pragma unroll
+    for (int dj = 0; dj < 3; ++dj) {
+      const int jj = 2 * J + dj;
+      if (jj >= f.n2) continue;
+      const T wy = dj == 1 ? T(0.5) : T(0.25);
+      const T* row = t(jj, kk);
+      const int ii = 2 * I;
+      T sx = T(0.25) * row[ii] + T(0.5) * row[ii + 1];
+      if (ii + 2 < f.n1) sx += T(0.25) * row[ii + 2];
+      acc += wz * wy * sx;
+    }
+  }
+  return acc;
+}
+template <typename T, class Rows>
+__device__ __forceinline__ T mgc_prolong_at(const Rows& e, const MgLevel& c, int i, int j, int k) {
+  int x0, x1, y0, y1, z0, z1;
+  T wx0, wx1, wy0, wy1, wz0, wz1;
+  mg_axis(i, c.n1, x0, x1, wx0, wx1);
+  mg_axis(j, c.n2, y0, y1, wy0, wy1);
+  mg_axis(k, c.n3, z0, z1, wz0, wz1);
+  const T* r00 = e(y0, z0);
+  const T* r01 = e(y1, z0);
+  const T* r10 = e(y0, z1);
+  const T* r11 = e(y1, z1);
+  const T a00 = wx0 * r00[x0] + wx1 * r00[x1];
+  const T a01 = wx0 * r01[x0] + wx1 * r01[x1];
+  const T a10 = wx0 * r10[x0] + wx1 * r10[x1];
+  const T a11 = wx0 * r11[x0] + wx1 * r11[x1];
+  return wz0 * (wy0 * a00 + wy1 * a01) + wz1 * (wy0 * a10 + wy1 * a11);
+}
+// rows of a global level array
+template <typename T>
+struct MgGlobalRows {
+  T* f;
+  MgLevel d;
+  __device__ __forceinline__ T* operator()(int j, int k) const {
+    return f + (long long)d.n1 * d.n2 * k + (long long)d.n1 * j;
+  }
+};
+
+template <typename T>
+__global__ void __cluster_dims__(kMgClusterCtas, 1, 1) __launch_bounds__(1024)
+    mg_cluster_kernel(MgClusterArgs<T> A, CgScalars* sc) {
+  pdl_enter();
+  namespace cg = cooperative_groups;
+  extern __shared__ __align__(16) unsigned char mgc_sm[];
+  cg::cluster_group cluster = cg::this_cluster();
+  if (sc->done) return;  // the same flag for every block: the whole cluster returns
+  const int q = (int)cluster.block_rank();
+  const int tid = threadIdx.x;
+  T* sm = reinterpret_cast<T*>(mgc_sm);
+  const T a = T(1) - A.omega, b = A.omega / T(6);
+  // this block's nodes of level l: planes [q P, min((q + 1) P, n3))
+  auto own = [&](const MgSlab& L, int& k0, int& k1) {
+    k0 = min(q * L.P, L.d.n3);
+    k1 = min(k0 + L.P, L.d.n3);
+  };
+  {  // r of level lq from global memory
+    const MgSlab& L = A.L[A.lq];
+    int k0, k1;
+    own(L, k0, k1);
+    const int plane = L.d.n1 * L.d.n2;
+    const T* src = A.r_in + (long long)plane * k0;
+    T* dst = sm + L.off;
+    for (int e = tid; e < plane * (k1 - k0); e += 1024) dst[e] = src[e];
+  }
+  cluster.sync();
+  for (int l = A.lq; l < A.lc; ++l) {
+    const MgSlab& L = A.L[l];
+    const MgRows<T> R{sm, L, 0}, Wr{sm, L, 1};
+    int k0, k1;
+    own(L, k0, k1);
+    const int n1 = L.d.n1, n2 = L.d.n2;
+    for (int e = tid; e < n1 * n2 * (k1 - k0); e += 1024) {  // down: w = (1 - omega) r + (omega / 6) sum_nb r
+      const int i = e % n1, jk = e / n1, j = jk % n2, k = k0 + jk / n2;
+      Wr(j, k)[i] = a * R(j, k)[i] + b * mgc_nb_sum<T>(R, i, j, k, L.d);
+    }
+    cluster.sync();
+    const MgLevel& dc = A.L[l + 1].d;
+    if (l + 1 < A.lc) {  // restrict into the next cluster level's r
+      const MgSlab& C = A.L[l + 1];
+      const MgRows<T> Rc{sm, C, 0};
+      int c0, c1;
+      own(C, c0, c1);
+      for (int e = tid; e < dc.n1 * dc.n2 * (c1 - c0); e += 1024) {
+        const int I = e % dc.n1, JK = e / dc.n1, J = JK % dc.n2, K = c0 + JK / dc.n2;
+        Rc(J, K)[I] = mgc_restrict_at<T>(Wr, L.d, I, J, K);
+      }
+    } else {  // restrict into the coarse end's r (global), split over the blocks by planes
+      const MgGlobalRows<T> Rg{A.r_tail, dc};
+      const int Pc = (dc.n3 + kMgClusterCtas - 1) / kMgClusterCtas;
+      const int c0 = min(q * Pc, dc.n3), c1 = min(c0 + Pc, dc.n3);
+      for (int e = tid; e < dc.n1 * dc.n2 * (c1 - c0); e += 1024) {
+        const int I = e % dc.n1, JK = e / dc.n1, J = JK % dc.n2, K = c0 + JK / dc.n2;
+        Rg(J, K)[I] = mgc_restrict_at<T>(Wr, L.d, I, J, K);
+      }
+    }
+    cluster.sync();
+  }
+  // the coarse end in block 0 (levels lc and below, its own shared memory)
+  if (q == 0)
+    mg_coarse_body<T, false>(A.L[A.lc].d, A.ncoarse, A.r_tail, A.z_tail, A.omega, A.s[A.lc], A.sweeps, sc,
+                             mgc_sm + A.tail_off);
+  cluster.sync();
+  for (int l = A.lc - 1; l >= A.lq; --l) {
+    const MgSlab& L = A.L[l];
+    const MgRows<T> R{sm, L, 0}, Y{sm, L, 1}, Z{sm, L, 2};
+    const T s = A.s[l];
+    int k0, k1;
+    own(L, k0, k1);
+    const int n1 = L.d.n1, n2 = L.d.n2;
+    const MgLevel& dc = A.L[l + 1].d;
+    if (l + 1 < A.lc) {  // prolong: y = s r + P e_c
+      const MgRows<T> Ec{sm, A.L[l + 1], 2};
+      for (int e = tid; e < n1 * n2 * (k1 - k0); e += 1024) {
+        const int i = e % n1, jk = e / n1, j = jk % n2, k = k0 + jk / n2;
+        Y(j, k)[i] = s * R(j, k)[i] + mgc_prolong_at<T>(Ec, dc, i, j, k);
+      }
+    } else {
+      const MgGlobalRows<T> Ec{A.z_tail, dc};
+      for (int e = tid; e < n1 * n2 * (k1 - k0); e += 1024) {
+        const int i = e % n1, jk = e / n1, j = jk % n2, k = k0 + jk / n2;
+        Y(j, k)[i] = s * R(j, k)[i] + mgc_prolong_at<T>(Ec, dc, i, j, k);
+      }
+    }
+    cluster.sync();
+    // up: z = (1 - omega) y + s r + (omega / 6) sum_nb y; level lq's z goes to global memory
+    T* zg = (l == A.lq) ? A.z_out : nullptr;
+    for (int e = tid; e < n1 * n2 * (k1 - k0); e += 1024) {
+      const int i = e % n1, jk = e / n1, j = jk % n2, k = k0 + jk / n2;
+      const T zi = a * Y(j, k)[i] + s * R(j, k)[i] + b * mgc_nb_sum<T>(Y, i, j, k, L.d);
+      if (zg)
+        zg[((long long)k * n2 + j) * n1 + i] = zi;
+      else
+        Z(j, k)[i] = zi;
+    }
+    cluster.sync();
+  }
 }
 
 // The coarse end for several grids of a batch (S11): block b takes job b.

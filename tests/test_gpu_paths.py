@@ -451,3 +451,54 @@ def test_fused_small_levels_match_plain_cycle(ctx_fixed_pair, ctx_fuse_small, di
     phi_ref, _, _ = O.poisson(_ogrid(g), order // 2, rho_h, tol=1e-12)
     err = np.abs(out[1][0] - phi_ref).max() / np.abs(phi_ref).max()
     assert err <= (1e-8 if dtype == torch.float64 else 2e-6)
+
+
+# ------------------------------------------ coarse levels on a block cluster --
+@pytest.fixture(scope="module")
+def ctx_cluster(ctx):
+    """A context whose V-cycle runs its coarse levels (those whose z-plane
+    slabs fit in 8 blocks' shared memory) and the coarse end in one launch of a
+    thread-block cluster (distributed shared memory, cluster barriers)."""
+    c = _context(OFDFT_MG_CLUSTER=1, OFDFT_AUTOTUNE=0, OFDFT_TMA=0, OFDFT_PDL=0)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("dims,order", [((48, 40, 36), 12), ((64, 64, 64), 12), ((96, 96, 96), 8),
+                                        ((5, 70, 9), 4)])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_cluster_coarse_levels_match_plain_cycle(ctx_fixed_pair, ctx_cluster, dims, order, dtype):
+    """The cluster kernel does each node's arithmetic of the separate level
+    passes in the same order, so the PCG (fixed launch shapes on both sides)
+    takes the same iterations to the same phi, bit for bit, and matches the
+    oracle; where no level fits the cluster the plain cycle runs."""
+    g = F.make_grid(*dims, 0.5)
+    rho_h = np.random.default_rng(12).standard_normal(g.shape)
+    tol = 1e-10 if dtype == torch.float64 else 1e-9
+    out = []
+    for c in (ctx_fixed_pair[0], ctx_cluster):
+        c.reset_counters()
+        phi = torch.zeros(g.shape, dtype=dtype, device=DEV)
+        st = c.poisson(g, order, phi, rho=_t(rho_h, dtype), tol=tol)
+        assert st.rel_residual <= tol
+        out.append((_h(phi), st.iterations, c.counters().kind_launches[F.K_MG]))
+    assert out[0][1] == out[1][1]
+    assert np.array_equal(out[0][0], out[1][0])
+    if min(dims) >= 32:
+        assert out[1][2] < out[0][2]  # the cluster replaces launches
+    phi_ref, _, _ = O.poisson(_ogrid(g), order // 2, rho_h, tol=1e-12)
+    err = np.abs(out[1][0] - phi_ref).max() / np.abs(phi_ref).max()
+    assert err <= (1e-8 if dtype == torch.float64 else 2e-6)
+
+
+def test_cluster_coarse_levels_ground_state(ctx_fixed_pair, ctx_cluster):
+    """The MIXED ground state of the 666-atom cluster (128^3: the 32^3 level and
+    the coarse end on the cluster) is the same bit for bit with the cluster
+    coarse end."""
+    cl = W.cluster_c2()
+    p = F.default_params(precision=F.PREC_MIXED, vacuum=cl.vacuum, round_to=16)
+    E0, F0, s0 = ctx_fixed_pair[0].solve(cl.R, cl.Z, cl.h, p)
+    E1, F1, s1 = ctx_cluster.solve(cl.R, cl.Z, cl.h, p)
+    assert s0.converged and s1.converged
+    assert E0 == E1
+    assert np.array_equal(F0, F1)
