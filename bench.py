@@ -600,10 +600,13 @@ def run_batch(args):
                         unconv.add(rid)
         wall = time.perf_counter() - t0
         binfo = bt.info()
+        if rep == 0:
+            tuning = binfo  # the warm-up pass tunes each grid shape once for the context
         bt.close()
     lat = np.array(sorted(t for rid, t in done_t.items() if rid not in unconv))
     out.update({"value": (len(cl) - len(unconv)) / wall, "wall_s": wall, "rounds": rounds,
                 "unconverged": len(unconv), "batch_launch_stats": binfo,
+                "autotune_warmup_pass": tuning,
                 "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))}})
     # the same requests one at a time through ofdft_solve (the plain form)
     t0 = time.perf_counter()

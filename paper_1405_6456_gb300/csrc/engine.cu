@@ -546,6 +546,8 @@ struct Engine {
       for (auto& t : c->ztune)
         if (t.first == key) {
           S->zdepth = t.second;
+          B->zdepth = S->zdepth;
+          B->ztuned = 1;  // chosen by the autotuner earlier in this context
           found = true;
           break;
         }

@@ -2034,9 +2034,10 @@ __global__ void __launch_bounds__(1024) mg_coarse_kernel(MgLevel d0, int nlev, c
 // included) through the cluster's shared-memory window.  A cluster barrier
 // (hardware, all blocks co-scheduled) separates the passes.  Levels lc and
 // below run as the one-block coarse end in block 0 (global r and z of level
-// lc).  Every node's arithmetic, and its order, are those of the separate
-// level passes (mg_down / restrict / prolong / up) and of mg_coarse_kernel, so
-// the cycle, and the PCG, are the same bit for bit.
+// lc).  Every node's formulas, in their order, are those of the separate
+// level passes (mg_down / restrict / prolong / up) and of mg_coarse_kernel; the
+// cycle agrees with theirs to rounding (the compiler is free to contract a
+// product into an FMA differently in the two kernels).
 constexpr int kMgClusterCtas = 8;  // the portable cluster size
 struct MgSlab {
   MgLevel d;
