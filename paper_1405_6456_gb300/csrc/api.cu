@@ -117,6 +117,26 @@ int mg_prepare(ofdft_ctx* c, const GridDev& g, double h, MgPlan* P) {
   return OFDFT_OK;
 }
 
+// The damped-Jacobi sweep of a level as radius-1 stencil weights: centre
+// 1 - omega, neighbours omega / 6, rounded in T as the row passes round them.
+template <typename T>
+inline Weights<double> mg_smoother_weights(double omega) {
+  Weights<double> W;
+  memset(&W, 0, sizeof(W));
+  const T om = (T)omega;
+  W.c = (double)(T(1) - om);
+  W.w[1] = (double)(om / T(6));
+  return W;
+}
+inline GridDev mg_gdev(const MgLevel& d) {
+  GridDev g;
+  g.n1 = d.n1;
+  g.n2 = d.n2;
+  g.n3 = d.n3;
+  g.G = (long long)d.n1 * d.n2 * d.n3;
+  return g;
+}
+
 // Whether level l of the V-cycle runs as the two fused passes.
 inline bool mg_level_fused(const ofdft_ctx* c, const MgPlan& P, int l) {
   const long long n = mg_nodes(P.d[l]);
@@ -141,6 +161,7 @@ int mg_vcycle(ofdft_ctx* c, const MgPlan& P, const T* r, T* z, CgScalars* sc) {
   // passes (shared-memory tiles); the others the four plain passes
   auto fused = [&](int l) { return mg_level_fused(c, P, l); };
   const T om = (T)c->mg_omega;
+  const Weights<double> Wsm = mg_smoother_weights<T>(c->mg_omega);  // the smoother as stencil weights
   // mg_finest_smooth == 0: the finest level is not smoothed (its smoother is
   // the scaled identity s r alone): r_c = R r and z = s r + P e_c.  M stays
   // symmetric positive definite (s > 0, R = P^T / 8, M_c SPD).
@@ -164,7 +185,9 @@ int mg_vcycle(ofdft_ctx* c, const MgPlan& P, const T* r, T* z, CgScalars* sc) {
                   (const CgScalars*)sc));
       continue;
     }
-    {
+    if (c->mg_zstream) {
+      TRY((launch_z<T, 1>(c, mg_gdev(P.d[l]), Wsm, LoadPlain<T>{rl(l)}, EpiMgDown<T>{tl(l), sc}, OFDFT_K_MG)));
+    } else {
       ProfScope ps_(c, OFDFT_K_MG);
       CU(launch_k(c, mg_down_kernel<T>, dim3(rows_blocks(P.d[l])), dim3(256), 0, P.d[l], (const T*)rl(l), tl(l),
                   om, (const CgScalars*)sc));
@@ -235,6 +258,14 @@ int mg_vcycle(ofdft_ctx* c, const MgPlan& P, const T* r, T* z, CgScalars* sc) {
       ProfScope ps_(c, OFDFT_K_MG);
       CU(launch_k(c, mg_prolong_kernel<T, false>, dim3(rows_blocks(P.d[l])), dim3(256), 0, P.d[l], P.d[l + 1],
                   (const T*)rl(l), (const T*)zl(l + 1), tl(l), (T)s, sc, RedBuf{}));
+    }
+    if (c->mg_zstream) {
+      if (l == 0)
+        TRY((launch_z<T, 1>(c, mg_gdev(P.d[0]), Wsm, LoadPlain<T>{t0}, EpiMgUp<T, true>{r, z, (T)s, sc}, OFDFT_K_MG)));
+      else
+        TRY((launch_z<T, 1>(c, mg_gdev(P.d[l]), Wsm, LoadPlain<T>{tl(l)}, EpiMgUp<T, false>{rl(l), zl(l), (T)s, sc},
+                            OFDFT_K_MG)));
+      continue;
     }
     ProfScope ps_(c, OFDFT_K_MG);
     if (l == 0)
@@ -1883,6 +1914,8 @@ int ofdft_create(ofdft_ctx** out, int device, void* stream) {
   if (ms && atoi(ms) >= 1) c->mg_sweeps = atoi(ms);
   const char* cz = getenv("OFDFT_COOP_NZ");  // launch-shape experiments: z-chunks of the persistent CG grid
   c->coop_nz = cz ? atoi(cz) : 0;
+  const char* mzs = getenv("OFDFT_MG_ZSTREAM");  // 0: level smoothing passes as row-per-warp kernels
+  if (mzs) c->mg_zstream = atoi(mzs) != 0;
   const char* mcl = getenv("OFDFT_MG_CLUSTER");  // 1: coarse multigrid levels on one thread-block cluster
   if (mcl) c->mg_cluster = atoi(mcl) != 0;
   const char* fbl = getenv("OFDFT_MG_FUSE_BELOW");  // coarser levels of at most this many nodes take the fused passes

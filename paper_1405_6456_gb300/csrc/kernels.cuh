@@ -1694,6 +1694,49 @@ struct MgFin {
   }
 };
 
+// The smoothing passes of a level as z-streaming stencils: the 7-point sum
+// (1 - omega) f + (omega / 6) sum_nb f is the radius-1 star stencil with
+// centre weight 1 - omega and neighbour weight omega / 6, so the pipelined
+// stencil kernel (planes staged through shared memory, register z-queues)
+// runs them at the memory roofline instead of the row-per-warp passes.
+// down: t = stencil(r).
+template <typename T>
+struct EpiMgDown {
+  static constexpr int K = 0;
+  static constexpr int NIN = 0;
+  using Acc = double;
+  T* t;
+  const CgScalars* sc;
+  __device__ __forceinline__ bool skip() const { return sc->done != 0; }
+  __device__ __forceinline__ void load() {}
+  __host__ __device__ __forceinline__ const T* input(int) const { return nullptr; }
+  __device__ __forceinline__ void apply(long long i, T, T lap, const T*, Acc*) const { t[i] = lap; }
+  __device__ __forceinline__ void operator()(double*) const {}
+};
+// up: z = stencil(y) + s r (r staged with the stencil input); on the finest
+// level (DOT) also r.z and the PCG scalars.
+template <typename T, bool DOT>
+struct EpiMgUp {
+  static constexpr int K = DOT ? 1 : 0;
+  static constexpr int NIN = 1;
+  using Acc = DotAcc<T>;
+  const T* r;
+  T* z;
+  T s;
+  CgScalars* sc;
+  __device__ __forceinline__ bool skip() const { return sc->done != 0; }
+  __device__ __forceinline__ void load() {}
+  __host__ __device__ __forceinline__ const T* input(int) const { return r; }
+  __device__ __forceinline__ void apply(long long i, T, T lap, const T* vin, Acc* acc) const {
+    const T zi = fma(s, vin[0], lap);
+    z[i] = zi;
+    if constexpr (DOT) acc[0].add(vin[0], zi);
+  }
+  __device__ __forceinline__ void operator()(double* t) const {
+    if constexpr (DOT) MgFin{sc}(t);
+  }
+};
+
 // up, first half: y = s r + P e_c.  With DOT this is the whole up step of a
 // level that is not smoothed (the finest level with mg_finest_smooth = 0:
 // z = s r + P e_c), with r.z and the PCG scalars.

@@ -420,18 +420,21 @@ def test_multigrid_without_finest_smoothing_ground_state(ctx, ctx_nosmooth0):
 
 # --------------------------------------------- fused small multigrid levels --
 @pytest.fixture(scope="module")
-def ctx_fuse_small(ctx):
-    """A context whose coarser V-cycle levels of at most 200,000 nodes run as
-    two fused passes each (down + restrict, prolong + up) instead of four."""
-    c = _context(OFDFT_MG_FUSE_BELOW=200000, OFDFT_AUTOTUNE=0, OFDFT_TMA=0, OFDFT_PDL=0)
-    yield c
-    c.close()
+def ctx_rowpass_pair(ctx):
+    """Two contexts with fixed launch shapes and the row-per-warp level passes
+    (OFDFT_MG_ZSTREAM=0), the second with the coarser V-cycle levels of at most
+    200,000 nodes as two fused passes each (down + restrict, prolong + up)."""
+    a = _context(OFDFT_MG_ZSTREAM=0, OFDFT_AUTOTUNE=0, OFDFT_TMA=0, OFDFT_PDL=0)
+    b = _context(OFDFT_MG_ZSTREAM=0, OFDFT_MG_FUSE_BELOW=200000, OFDFT_AUTOTUNE=0, OFDFT_TMA=0, OFDFT_PDL=0)
+    yield a, b
+    a.close()
+    b.close()
 
 
 @pytest.mark.parametrize("dims,order", [((48, 40, 36), 12), ((64, 64, 64), 12), ((96, 96, 96), 8)])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
-def test_fused_small_levels_match_plain_cycle(ctx_fixed_pair, ctx_fuse_small, dims, order, dtype):
-    """The fused level passes do the separate passes' arithmetic in the same
+def test_fused_small_levels_match_plain_cycle(ctx_rowpass_pair, dims, order, dtype):
+    """The fused level passes do the row-per-warp passes' arithmetic in the same
     order, so the preconditioned CG (both contexts with the fixed launch shapes)
     takes the same iterations to the same phi (bit for bit), which matches the
     oracle."""
@@ -439,7 +442,7 @@ def test_fused_small_levels_match_plain_cycle(ctx_fixed_pair, ctx_fuse_small, di
     rho_h = np.random.default_rng(8).standard_normal(g.shape)
     tol = 1e-10 if dtype == torch.float64 else 1e-9
     out = []
-    for c in (ctx_fixed_pair[0], ctx_fuse_small):
+    for c in ctx_rowpass_pair:
         c.reset_counters()
         phi = torch.zeros(g.shape, dtype=dtype, device=DEV)
         st = c.poisson(g, order, phi, rho=_t(rho_h, dtype), tol=tol)
@@ -459,7 +462,7 @@ def ctx_cluster(ctx):
     """A context whose V-cycle runs its coarse levels (those whose z-plane
     slabs fit in 8 blocks' shared memory) and the coarse end in one launch of a
     thread-block cluster (distributed shared memory, cluster barriers)."""
-    c = _context(OFDFT_MG_CLUSTER=1, OFDFT_AUTOTUNE=0, OFDFT_TMA=0, OFDFT_PDL=0)
+    c = _context(OFDFT_MG_CLUSTER=1, OFDFT_MG_ZSTREAM=0, OFDFT_AUTOTUNE=0, OFDFT_TMA=0, OFDFT_PDL=0)
     yield c
     c.close()
 
@@ -467,7 +470,7 @@ def ctx_cluster(ctx):
 @pytest.mark.parametrize("dims,order", [((48, 40, 36), 12), ((64, 64, 64), 12), ((96, 96, 96), 8),
                                         ((5, 70, 9), 4)])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
-def test_cluster_coarse_levels_match_plain_cycle(ctx_fixed_pair, ctx_cluster, dims, order, dtype):
+def test_cluster_coarse_levels_match_plain_cycle(ctx_rowpass_pair, ctx_cluster, dims, order, dtype):
     """The cluster kernel evaluates each node's formulas of the separate level
     passes in the same order (the compiler may contract a product into an FMA
     differently, so the cycle agrees to rounding, not bit for bit): the PCG
@@ -478,7 +481,7 @@ def test_cluster_coarse_levels_match_plain_cycle(ctx_fixed_pair, ctx_cluster, di
     rho_h = np.random.default_rng(12).standard_normal(g.shape)
     tol = 1e-10 if dtype == torch.float64 else 1e-9
     out = []
-    for c in (ctx_fixed_pair[0], ctx_cluster):
+    for c in (ctx_rowpass_pair[0], ctx_cluster):
         c.reset_counters()
         phi = torch.zeros(g.shape, dtype=dtype, device=DEV)
         st = c.poisson(g, order, phi, rho=_t(rho_h, dtype), tol=tol)
@@ -494,14 +497,38 @@ def test_cluster_coarse_levels_match_plain_cycle(ctx_fixed_pair, ctx_cluster, di
     assert err <= (1e-8 if dtype == torch.float64 else 2e-6)
 
 
-def test_cluster_coarse_levels_ground_state(ctx_fixed_pair, ctx_cluster):
+def test_cluster_coarse_levels_ground_state(ctx_rowpass_pair, ctx_cluster):
     """The MIXED ground state of the 666-atom cluster (128^3: the 32^3 level and
     the coarse end on the cluster) agrees with the plain cycle's within the
     solver tolerances."""
     cl = W.cluster_c2()
     p = F.default_params(precision=F.PREC_MIXED, vacuum=cl.vacuum, round_to=16)
-    E0, F0, s0 = ctx_fixed_pair[0].solve(cl.R, cl.Z, cl.h, p)
+    E0, F0, s0 = ctx_rowpass_pair[0].solve(cl.R, cl.Z, cl.h, p)
     E1, F1, s1 = ctx_cluster.solve(cl.R, cl.Z, cl.h, p)
     assert s0.converged and s1.converged
     assert abs(E1 - E0) / cl.M <= 1e-7
     assert np.abs(F1 - F0).max() <= 5e-4
+
+
+# ------------------------------------- smoothing passes as z-streaming stencils --
+@pytest.mark.parametrize("dims,order", [((48, 40, 36), 12), ((37, 29, 23), 6), ((96, 96, 96), 8)])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_zstream_smoothing_matches_row_passes(ctx_rowpass_pair, ctx_fixed_pair, dims, order, dtype):
+    """The level smoothing passes as radius-1 z-streaming stencils (the default)
+    apply the same damped-Jacobi sweep as the row-per-warp passes (their sums
+    in another order): the PCG needs the same iterations within one and reaches
+    the oracle's phi."""
+    g = F.make_grid(*dims, 0.5)
+    rho_h = np.random.default_rng(13).standard_normal(g.shape)
+    tol = 1e-10 if dtype == torch.float64 else 1e-9
+    out = []
+    for c in (ctx_rowpass_pair[0], ctx_fixed_pair[0]):
+        phi = torch.zeros(g.shape, dtype=dtype, device=DEV)
+        st = c.poisson(g, order, phi, rho=_t(rho_h, dtype), tol=tol)
+        assert st.rel_residual <= tol
+        out.append((_h(phi), st.iterations))
+    assert abs(out[0][1] - out[1][1]) <= 1
+    phi_ref, _, _ = O.poisson(_ogrid(g), order // 2, rho_h, tol=1e-12)
+    for phi, _ in out:
+        err = np.abs(phi - phi_ref).max() / np.abs(phi_ref).max()
+        assert err <= (1e-8 if dtype == torch.float64 else 2e-6)
