@@ -156,7 +156,22 @@ void ofdft_default_params(ofdft_params* p);
  * cooperative launch per eight iterations where the grid's blocks fit on the
  * device at once), OFDFT_CG_FOLD_BYTES (bytes of the five CG vectors above which
  * a CG folds its iterate update into the next stencil pass; default 96 MiB),
- * OFDFT_TRACE=1 (one stderr line per evaluation). */
+ * multigrid variants (each gives the same preconditioner up to rounding):
+ * OFDFT_MG_ZSTREAM=1 (level smoothing passes as radius-1 z-streaming stencils
+ * instead of row-per-warp kernels), OFDFT_MG_FUSE_NODES / OFDFT_MG_FUSE_BELOW
+ * (levels of at least / coarser levels of at most this many nodes run smoothing,
+ * residual and restriction as one fused pass and prolongation and smoothing as
+ * another), OFDFT_MG_CLUSTER=1 (the coarse levels whose z-plane slabs fit and
+ * the coarse end in one launch of an 8-block thread-block cluster, in its
+ * distributed shared memory), OFDFT_MG_FINEST_SMOOTH=0 (no sweeps on the finest
+ * level: r_c = R r, z = s r + P e_c; a different, cheaper preconditioner);
+ * OFDFT_FF_RESIDUAL=0 (MIXED: FP64 stencil in the residual pass of each Poisson
+ * round instead of the float-float one), OFDFT_COND_GRAPHS=0 (CG chunks of eight
+ * iterations polled by the host instead of a device-side loop in a CUDA graph
+ * with a conditional node), OFDFT_TMA=1 (FP32 z-streaming passes stage their
+ * planes with tiled TMA copies where the tile allows it; results are identical),
+ * OFDFT_PDL=1 (CG-loop kernels with programmatic dependent launch; results are
+ * identical), OFDFT_TRACE=1 (one stderr line per evaluation). */
 int ofdft_create(ofdft_ctx** ctx, int device, void* cuda_stream);
 int ofdft_destroy(ofdft_ctx* ctx);
 

@@ -1914,7 +1914,7 @@ int ofdft_create(ofdft_ctx** out, int device, void* stream) {
   if (ms && atoi(ms) >= 1) c->mg_sweeps = atoi(ms);
   const char* cz = getenv("OFDFT_COOP_NZ");  // launch-shape experiments: z-chunks of the persistent CG grid
   c->coop_nz = cz ? atoi(cz) : 0;
-  const char* mzs = getenv("OFDFT_MG_ZSTREAM");  // 0: level smoothing passes as row-per-warp kernels
+  const char* mzs = getenv("OFDFT_MG_ZSTREAM");  // 1: level smoothing passes as z-streaming stencils
   if (mzs) c->mg_zstream = atoi(mzs) != 0;
   const char* mcl = getenv("OFDFT_MG_CLUSTER");  // 1: coarse multigrid levels on one thread-block cluster
   if (mcl) c->mg_cluster = atoi(mcl) != 0;

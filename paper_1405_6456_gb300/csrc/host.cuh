@@ -93,7 +93,7 @@ struct ofdft_ctx {
   int mg_finest_smooth = 1;                    // damped-Jacobi smoothing on the finest multigrid level
   long long mg_fuse_below = -1;                // coarser multigrid levels of at most this many nodes: fused
   int mg_cluster = 0;                          // coarse levels on one thread-block cluster (mg_cluster_kernel)
-  int mg_zstream = 1;                          // level smoothing passes as z-streaming radius-1 stencils
+  int mg_zstream = 0;                          // level smoothing passes as z-streaming radius-1 stencils
   // the b_J tables in V_BTAB belong to this geometry (atoms, charges, grid,
   // sigma, r_c, stencil radius); empty: none kept
   std::vector<double> btab_key;

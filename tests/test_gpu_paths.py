@@ -511,18 +511,27 @@ def test_cluster_coarse_levels_ground_state(ctx_rowpass_pair, ctx_cluster):
 
 
 # ------------------------------------- smoothing passes as z-streaming stencils --
+@pytest.fixture(scope="module")
+def ctx_zs(ctx):
+    """A context whose V-cycle smoothing passes run as radius-1 z-streaming
+    stencils (OFDFT_MG_ZSTREAM=1)."""
+    c = _context(OFDFT_MG_ZSTREAM=1, OFDFT_AUTOTUNE=0, OFDFT_TMA=0, OFDFT_PDL=0)
+    yield c
+    c.close()
+
+
 @pytest.mark.parametrize("dims,order", [((48, 40, 36), 12), ((37, 29, 23), 6), ((96, 96, 96), 8)])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
-def test_zstream_smoothing_matches_row_passes(ctx_rowpass_pair, ctx_fixed_pair, dims, order, dtype):
-    """The level smoothing passes as radius-1 z-streaming stencils (the default)
-    apply the same damped-Jacobi sweep as the row-per-warp passes (their sums
-    in another order): the PCG needs the same iterations within one and reaches
-    the oracle's phi."""
+def test_zstream_smoothing_matches_row_passes(ctx_rowpass_pair, ctx_zs, dims, order, dtype):
+    """The level smoothing passes as radius-1 z-streaming stencils apply the
+    same damped-Jacobi sweep as the row-per-warp passes (their sums in another
+    order): the PCG needs the same iterations within one and reaches the
+    oracle's phi."""
     g = F.make_grid(*dims, 0.5)
     rho_h = np.random.default_rng(13).standard_normal(g.shape)
     tol = 1e-10 if dtype == torch.float64 else 1e-9
     out = []
-    for c in (ctx_rowpass_pair[0], ctx_fixed_pair[0]):
+    for c in (ctx_rowpass_pair[0], ctx_zs):
         phi = torch.zeros(g.shape, dtype=dtype, device=DEV)
         st = c.poisson(g, order, phi, rho=_t(rho_h, dtype), tol=tol)
         assert st.rel_residual <= tol
