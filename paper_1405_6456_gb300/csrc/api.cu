@@ -162,6 +162,11 @@ int mg_vcycle(ofdft_ctx* c, const MgPlan& P, const T* r, T* z, CgScalars* sc) {
   auto fused = [&](int l) { return mg_level_fused(c, P, l); };
   const T om = (T)c->mg_omega;
   const Weights<double> Wsm = mg_smoother_weights<T>(c->mg_omega);  // the smoother as stencil weights
+  // levels whose smoothing passes run as z-streaming stencils: all with
+  // mg_zstream, else those of at least mg_zstream_nodes nodes (-1: none)
+  auto zs = [&](int l) {
+    return c->mg_zstream || (c->mg_zstream_nodes >= 0 && mg_nodes(P.d[l]) >= c->mg_zstream_nodes);
+  };
   // mg_finest_smooth == 0: the finest level is not smoothed (its smoother is
   // the scaled identity s r alone): r_c = R r and z = s r + P e_c.  M stays
   // symmetric positive definite (s > 0, R = P^T / 8, M_c SPD).
@@ -185,7 +190,7 @@ int mg_vcycle(ofdft_ctx* c, const MgPlan& P, const T* r, T* z, CgScalars* sc) {
                   (const CgScalars*)sc));
       continue;
     }
-    if (c->mg_zstream) {
+    if (zs(l)) {
       TRY((launch_z<T, 1>(c, mg_gdev(P.d[l]), Wsm, LoadPlain<T>{rl(l)}, EpiMgDown<T>{tl(l), sc}, OFDFT_K_MG)));
     } else {
       ProfScope ps_(c, OFDFT_K_MG);
@@ -259,7 +264,7 @@ int mg_vcycle(ofdft_ctx* c, const MgPlan& P, const T* r, T* z, CgScalars* sc) {
       CU(launch_k(c, mg_prolong_kernel<T, false>, dim3(rows_blocks(P.d[l])), dim3(256), 0, P.d[l], P.d[l + 1],
                   (const T*)rl(l), (const T*)zl(l + 1), tl(l), (T)s, sc, RedBuf{}));
     }
-    if (c->mg_zstream) {
+    if (zs(l)) {
       if (l == 0)
         TRY((launch_z<T, 1>(c, mg_gdev(P.d[0]), Wsm, LoadPlain<T>{t0}, EpiMgUp<T, true>{r, z, (T)s, sc}, OFDFT_K_MG)));
       else
@@ -1916,6 +1921,8 @@ int ofdft_create(ofdft_ctx** out, int device, void* stream) {
   c->coop_nz = cz ? atoi(cz) : 0;
   const char* mzs = getenv("OFDFT_MG_ZSTREAM");  // 1: level smoothing passes as z-streaming stencils
   if (mzs) c->mg_zstream = atoi(mzs) != 0;
+  const char* mzn = getenv("OFDFT_MG_ZSTREAM_NODES");  // levels of at least this many nodes: z-streaming smoothing
+  if (mzn) c->mg_zstream_nodes = atoll(mzn);
   const char* mcl = getenv("OFDFT_MG_CLUSTER");  // 1: coarse multigrid levels on one thread-block cluster
   if (mcl) c->mg_cluster = atoi(mcl) != 0;
   const char* fbl = getenv("OFDFT_MG_FUSE_BELOW");  // coarser levels of at most this many nodes take the fused passes
