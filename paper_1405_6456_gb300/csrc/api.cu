@@ -110,9 +110,13 @@ int mg_prepare(ofdft_ctx* c, const GridDev& g, double h, MgPlan* P) {
   if (!attr_dev[c->device]) {
     CU(cudaFuncSetAttribute(mg_coarse_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     CU(cudaFuncSetAttribute(mg_coarse_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr_dev[c->device] = true;
+  }
+  static bool cattr_dev[64] = {false};  // the cluster kernel's shared memory, only where it is used
+  if (c->mg_cluster && P->lq > 0 && !cattr_dev[c->device]) {
     CU(cudaFuncSetAttribute(mg_cluster_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)kMgClusterSmem));
-    attr_dev[c->device] = true;
+    cattr_dev[c->device] = true;
   }
   return OFDFT_OK;
 }
