@@ -294,3 +294,25 @@ def ezz_correction(R, Z, sigma=1.0):
     F = np.zeros(R.shape[0] * 3)
     E = lib().orc_ezz_correction(R, Z, R.shape[0], sigma, _ptr(F))
     return E, F.reshape(-1, 3)
+
+
+def overlap_correction(g: Grid, n: int, R, Z, sigma=1.0, rc=7.0, sigma_ref=0.4, rc_ref=1.8, tol=1e-12):
+    """(E_c, F_c) of Appendix A in its general form, on the grid: reference
+    pseudocharges b~_J (Gaussian nuclei of width sigma_ref cut at rc_ref, whose
+    balls must not overlap) next to the pseudocharges b_J of the method;
+    V and V~ from (-1/4 pi) L_h V = b and (-1/4 pi) L_h V~ = b~ (so V_c = V~ - V
+    solves (-1/4 pi) L_h V_c = b~ - b); Eq. RepulsiveCorrection2:
+        E_c = 1/2 h^3 sum (b~ + b) V_c + E_self(b) - E_self(b~),
+    E_self the self energies 1/2 h^3 sum_J sum b_J V_J of pseudocharge(); and the
+    force correction -dE_c/dR_J,
+        f_J = h^3 sum grad b~_J (V~ - V~_J) - h^3 sum grad b_J (V - V_J),
+    each the paper-form force expression of forces() at the given potential."""
+    R, Z = _f64(R), _f64(Z)
+    b, es = pseudocharge(g, n, R, Z, sigma, rc)
+    bt, est = pseudocharge(g, n, R, Z, sigma_ref, rc_ref)
+    V, _, _ = poisson(g, n, b, tol=tol)
+    Vt, _, _ = poisson(g, n, bt, tol=tol)
+    h3 = g.h ** 3
+    E = 0.5 * h3 * float(np.sum((bt + b) * (Vt - V))) + es - est
+    F = forces(g, n, R, Z, Vt, sigma_ref, rc_ref) - forces(g, n, R, Z, V, sigma, rc)
+    return E, F

@@ -590,3 +590,35 @@ def test_centre_atom_of_symmetric_cluster_feels_no_force():
     assert np.abs(F[0]).max() < 1e-3 * outer.min()
     assert np.abs(F.sum(axis=0)).max() < 1e-3 * outer.min()
     np.testing.assert_allclose(outer, outer.mean(), rtol=1e-4)  # all 12 are equivalent
+
+
+def test_overlap_correction_general_form_converges_to_gaussian_closed_form():
+    """Appendix A's general correction (reference charges b~_J, the extra
+    Poisson solves) is the difference of two discrete repulsive energies; for
+    Gaussian nuclei the continuum difference is sum_{I<J} Z_I Z_J
+    erfc(R_IJ / (sqrt2 sigma)) / R_IJ (the pair energy of point charges minus that
+    of the Gaussians).  On an overlapping dimer (R = 3.5 bohr, sigma = 1) the
+    grid's energy and force corrections approach it at high order as h shrinks."""
+    R = np.array([[-1.75, 0.0, 0.0], [1.75, 0.0, 0.0]])
+    Z = np.array([3.0, 3.0])
+    Ec, Fc = O.ezz_correction(R, Z, 1.0)
+    errs = []
+    for h in (0.25, 0.2):
+        g = O.grid_for_atoms(R, h, 8.0, 1)
+        E, F = O.overlap_correction(g, 6, R, Z, 1.0, 7.0, 0.4, 1.7)
+        errs.append((abs(E - Ec) / Ec, np.abs(F - Fc).max() / np.abs(Fc).max()))
+        assert np.abs(F[:, 1:]).max() < 1e-12 and abs(F[0, 0] + F[1, 0]) < 1e-12  # the dimer's symmetry
+    assert errs[1][0] < errs[0][0] / 4 and errs[1][0] < 5e-3
+    assert errs[1][1] < errs[0][1] / 2 and errs[1][1] < 1e-2
+
+
+def test_overlap_correction_general_form_vanishes_without_overlap():
+    """Atoms 16 bohr apart: neither the r_c = 7 balls of b nor the reference
+    balls overlap, so the correction is zero up to the grid's error (against a
+    pair energy Z^2 / R = 0.56 Ha)."""
+    R = np.array([[-8.0, 0.1, -0.05], [8.0, -0.1, 0.05]])
+    Z = np.array([3.0, 3.0])
+    g = O.grid_for_atoms(R, 0.3, 8.0, 1)
+    E, F = O.overlap_correction(g, 6, R, Z, 1.0, 7.0, 0.4, 1.8)
+    assert abs(E) < 1e-4
+    assert np.abs(F).max() < 5e-4
