@@ -267,6 +267,25 @@ int ofdft_forces(ofdft_ctx* ctx, const ofdft_grid* g, int fd_order, const double
                  const double* Z, int M, double sigma, double rc, int variant, int prec,
                  const void* phi, double* F);
 
+/* App. A - correction of the repulsive energy and the forces for overlapping
+ * pseudocharges, in the paper's general form (Eq. RepulsiveCorrection2 and the
+ * force expression after it): reference charges b~_J, Gaussian nuclei of width
+ * sigma_ref cut at rc_ref (each of charge Z_J on the grid; their balls must not
+ * overlap: every pair of atoms more than 2 rc_ref apart, else OFDFT_EINVAL), beside
+ * the method's b_J (sigma, rc); V and V~ from (-1/4 pi) L_h V = b and
+ * (-1/4 pi) L_h V~ = b~ (two FP64 Poisson solves to relative residual tol, so
+ * V_c = V~ - V), and
+ *   E_c = 1/2 h^3 sum (b~ + b) V_c + E_self(b) - E_self(b~),
+ *   f_J = h^3 sum grad_h b~_J (V~ - V~_J) - h^3 sum grad_h b_J (V - V_J)
+ * (the paper-form force of ofdft_forces at each potential).  Add E_c to the
+ * energy and f to the forces of a ground state computed with b.  For Gaussian
+ * nuclei E_c tends to sum_{I<J} Z_I Z_J erfc(R_IJ/(sqrt2 sigma))/R_IJ as h -> 0 (the
+ * closed form ofdft_params.ezz_correction adds).  E_c: host scalar; F_c: host
+ * array M x 3.  Synchronises. */
+int ofdft_overlap_correction(ofdft_ctx* ctx, const ofdft_grid* g, int fd_order, const double* R,
+                             const double* Z, int M, double sigma, double rc, double sigma_ref,
+                             double rc_ref, double tol, double* E_c, double* F_c);
+
 /* S1..S9 - ground state at fixed nuclei (Eq. GroundStateElectronic) by
  * Algorithm 1 (or the penalty method) around PR nonlinear CG with a secant line
  * search, the Jacobi preconditioner and u <- |u| (Sec. 4), then the forces.

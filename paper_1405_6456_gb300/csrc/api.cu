@@ -2277,6 +2277,65 @@ int ofdft_energy_grad(ofdft_ctx* c, const ofdft_grid* g, const ofdft_params* p, 
   return OFDFT_OK;
 }
 
+int ofdft_overlap_correction(ofdft_ctx* c, const ofdft_grid* g, int fd_order, const double* R, const double* Z,
+                             int M, double sigma, double rc, double sigma_ref, double rc_ref, double tol, double* E_c,
+                             double* F_c) {
+  if (!c) return OFDFT_EINVAL;
+  c->err.clear();
+  TRY(check_grid(c, g));
+  TRY(check_order(c, fd_order));
+  TRY(check_atoms(c, R, Z, M));
+  if (!E_c || !F_c) return fail(c, OFDFT_EINVAL, "null output pointer");
+  if (!(sigma > 0.0) || !(rc > 0.0) || !(sigma_ref > 0.0) || !(rc_ref > 0.0) || !(tol > 0.0))
+    return fail(c, OFDFT_EINVAL, "sigma, rc, sigma_ref, rc_ref and tol must be positive");
+  for (int i = 0; i < M; ++i)  // the reference charges must not overlap (App. A)
+    for (int j = i + 1; j < M; ++j) {
+      const double dx = R[3 * i] - R[3 * j], dy = R[3 * i + 1] - R[3 * j + 1], dz = R[3 * i + 2] - R[3 * j + 2];
+      const double d = sqrt(dx * dx + dy * dy + dz * dz);
+      if (!(d > 2.0 * rc_ref))
+        return fail(c, OFDFT_EINVAL, "reference charges of atoms %d and %d overlap (distance %g <= 2 rc_ref = %g)", i,
+                    j, d, 2.0 * rc_ref);
+    }
+  CU(cudaSetDevice(c->device));
+  const GridDev gd = gdev(g);
+  const int Rr = fd_order / 2;
+  TRY(ensure(c, c->v[V_OC], 4 * (size_t)gd.G * sizeof(double)));
+  double* b = vec<double>(c, V_OC);
+  double* bt = b + gd.G;
+  double* V = bt + gd.G;
+  double* Vt = V + gd.G;
+  double es = 0.0, est = 0.0;
+  TRY(device_pseudocharge<double>(c, g, Rr, R, Z, M, sigma, rc, b, &es));
+  TRY(device_pseudocharge<double>(c, g, Rr, R, Z, M, sigma_ref, rc_ref, bt, &est));
+  CU(cudaMemsetAsync(V, 0, 2 * (size_t)gd.G * sizeof(double), c->stream));
+  ofdft_cg_stats st{0, 0.0};
+  TRY(poisson_fp64(c, Rr, gd, g->h, b, nullptr, nullptr, V, tol, 20000, &st));
+  TRY(poisson_fp64(c, Rr, gd, g->h, bt, nullptr, nullptr, Vt, tol, 20000, &st));
+  // (b~ + b).(V~ - V) = b~.V~ - b~.V + b.V~ - b.V
+  const int pb = pointwise_blocks(c, gd.G);
+  TRY(ensure_partials(c, pb, 2));
+  double d1[2], d2[2];
+  {
+    ProfScope ps_(c, OFDFT_K_VECTOR);
+    dot2_kernel<double><<<pb, 256, 0, c->stream>>>(gd.G, bt, Vt, bt, V, c->scal + 16, red(c));
+  }
+  CU(cudaGetLastError());
+  TRY(sync_scalars(c, c->scal + 16, 2 * sizeof(double), d1));
+  {
+    ProfScope ps_(c, OFDFT_K_VECTOR);
+    dot2_kernel<double><<<pb, 256, 0, c->stream>>>(gd.G, b, Vt, b, V, c->scal + 16, red(c));
+  }
+  CU(cudaGetLastError());
+  TRY(sync_scalars(c, c->scal + 16, 2 * sizeof(double), d2));
+  const double h3 = g->h * g->h * g->h;
+  *E_c = 0.5 * h3 * ((d1[0] - d1[1]) + (d2[0] - d2[1])) + es - est;
+  std::vector<double> Ft(3 * (size_t)M), Fb(3 * (size_t)M);
+  TRY(device_forces<double>(c, g, Rr, R, Z, M, sigma_ref, rc_ref, OFDFT_FORCE_PAPER, Vt, Ft.data()));
+  TRY(device_forces<double>(c, g, Rr, R, Z, M, sigma, rc, OFDFT_FORCE_PAPER, V, Fb.data()));
+  for (size_t k = 0; k < Ft.size(); ++k) F_c[k] = Ft[k] - Fb[k];
+  return OFDFT_OK;
+}
+
 int ofdft_forces(ofdft_ctx* c, const ofdft_grid* g, int fd_order, const double* R, const double* Z, int M,
                  double sigma, double rc, int variant, int prec, const void* phi, double* F) {
   if (!c) return OFDFT_EINVAL;

@@ -115,6 +115,7 @@ enum Vec {
   V_BACC,                              // FP64 running sums of the pseudocharge over atom ranges
   V_B2,                                // mixed: the FP64 pseudocharge as float-float pairs (residual pass)
   V_BTAB,                              // b_J tables of every atom, kept from the pseudocharge for the forces
+  V_OC,                                // overlap correction: b, b~, V, V~ (FP64)
   V_COUNT
 };
 

@@ -152,6 +152,8 @@ def lib():
                                     C.POINTER(Energy)]
     L.ofdft_forces.argtypes = [vp, C.POINTER(Grid), ip, dp, dp, ip, C.c_double, C.c_double, ip, ip,
                                vp, dp]
+    L.ofdft_overlap_correction.argtypes = [vp, C.POINTER(Grid), ip, dp, dp, ip, C.c_double, C.c_double,
+                                           C.c_double, C.c_double, C.c_double, dp, dp]
     L.ofdft_solve.argtypes = [vp, C.POINTER(Grid), dp, dp, ip, C.c_double, C.POINTER(Params), vp,
                               vp, dp, dp, C.POINTER(SolveStats)]
     L.ofdft_solve_from.argtypes = [vp, C.POINTER(Grid), dp, dp, ip, C.c_double, C.POINTER(Params), vp, vp,
@@ -339,6 +341,19 @@ class Context:
                                            rc, variant, prec_of(phi), _ptr(phi), _dp(F)), "ofdft_forces")
         return F
 
+    # Appendix A, general form
+    def overlap_correction(self, g: Grid, fd_order: int, R, Z, sigma=1.0, rc=7.0, sigma_ref=0.4, rc_ref=1.8,
+                           tol=1e-12):
+        """(E_c, F_c): the repulsive-energy and force corrections for overlapping
+        pseudocharges with reference charges b~ (ofdft_overlap_correction)."""
+        R, Z = _host_f64(R).reshape(-1, 3), _host_f64(Z)
+        E = C.c_double()
+        F = np.zeros((R.shape[0], 3))
+        self._check(self._lib.ofdft_overlap_correction(self.h, C.byref(g), fd_order, _dp(R), _dp(Z), R.shape[0],
+                                                       sigma, rc, sigma_ref, rc_ref, tol, C.byref(E), _dp(F)),
+                    "ofdft_overlap_correction")
+        return E.value, F
+
     # S1..S9
     def solve(self, R, Z, h, p: Params, grid: Grid | None = None, u_out=None, phi_out=None,
               want_forces=True, allow_notconv=False):
@@ -467,7 +482,7 @@ def exported_symbols():
     """Names the header declares (for the load/export check)."""
     return ["ofdft_default_params", "ofdft_create", "ofdft_destroy", "ofdft_last_error",
             "ofdft_grid_for_atoms", "ofdft_stencil", "ofdft_pseudocharge", "ofdft_initial_guess",
-            "ofdft_poisson", "ofdft_energy_grad", "ofdft_forces", "ofdft_solve",
+            "ofdft_poisson", "ofdft_energy_grad", "ofdft_forces", "ofdft_overlap_correction", "ofdft_solve",
             "ofdft_workspace_bytes", "ofdft_profile", "ofdft_get_counters", "ofdft_reset_counters",
             "ofdft_set_poisson_precond", "ofdft_mg_plan",
             "ofdft_batch_create", "ofdft_batch_destroy", "ofdft_batch_submit", "ofdft_batch_step",

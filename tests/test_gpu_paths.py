@@ -541,3 +541,23 @@ def test_zstream_smoothing_matches_row_passes(ctx_rowpass_pair, ctx_zs, dims, or
     for phi, _ in out:
         err = np.abs(phi - phi_ref).max() / np.abs(phi_ref).max()
         assert err <= (1e-8 if dtype == torch.float64 else 2e-6)
+
+
+# ------------------------------------------- Appendix A, the general form --
+def test_overlap_correction_general_form_matches_oracle(ctx):
+    """Appendix A's general correction (reference charges b~_J, Poisson solves
+    for V and V~) through the C ABI against the oracle's on an overlapping
+    dimer: the same discrete quantity, so energies agree to the solves'
+    tolerance; both approach the Gaussian closed form within the grid's error;
+    overlapping reference charges are rejected."""
+    R = np.array([[-1.75, 0.0, 0.0], [1.75, 0.0, 0.0]])
+    Z = np.array([3.0, 3.0])
+    g = F.ofdft_grid_for_atoms(R, 0.25, 8.0, 1)
+    E, Fv = ctx.overlap_correction(g, 12, R, Z, 1.0, 7.0, 0.4, 1.7, tol=1e-12)
+    E_ref, F_ref = O.overlap_correction(_ogrid(g), 6, R, Z, 1.0, 7.0, 0.4, 1.7, tol=1e-12)
+    assert abs(E - E_ref) <= 1e-9
+    assert np.abs(Fv - F_ref).max() <= 1e-8
+    Ec, _ = O.ezz_correction(R, Z, 1.0)
+    assert abs(E - Ec) / Ec < 0.05  # 2% at h = 0.25, falling at high order with h
+    with pytest.raises(F.OfdftError):
+        ctx.overlap_correction(g, 12, R, Z, 1.0, 7.0, 0.4, 1.8)  # 2 x 1.8 > 3.5 bohr: reference balls overlap
