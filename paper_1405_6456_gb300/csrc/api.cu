@@ -897,7 +897,11 @@ int functional_pass(ofdft_ctx* c, int R, const GridDev& g, double h, const ofdft
   f.kin_vw = -p->lambda * W.c;  // -lambda 6 w_0 > 0
   f.terms = p->terms;
   const bool es = p->terms & OFDFT_TERM_ES;
-  EpiFunctional<T> ep{es ? phi : nullptr, b, es ? rcg : nullptr, d, s_old, G, s, winv, sum_uu_dev, f, c->scal};
+  // split_dots: G.d and G.s_old by a pointwise pass after the functional (which
+  // then reads neither d nor s_old) instead of inside it
+  const bool split_dots = c->func_split_dots && G && (d || s_old);
+  EpiFunctional<T> ep{es ? phi : nullptr, b, es ? rcg : nullptr, split_dots ? nullptr : d,
+                      split_dots ? nullptr : s_old, G, s, winv, sum_uu_dev, f, c->scal};
   if (es && es_sums) {
     ep.es_sums = es_sums;
   } else if (es && phi64) {
@@ -906,6 +910,17 @@ int functional_pass(ofdft_ctx* c, int R, const GridDev& g, double h, const ofdft
     ep.r64 = r64;
   }
   TRY(launch_z_r<T>(c, R, g, W, LoadPlain<T>{u}, ep, OFDFT_K_FUNCTIONAL));
+  if (split_dots) {  // sums 5 and 6 of the functional's row: G.d and G.s_old
+    const int pb = pointwise_blocks(c, g.G);
+    TRY(ensure_partials(c, pb, 2));
+    {
+      ProfScope ps_(c, OFDFT_K_VECTOR);
+      dot2_kernel<T><<<pb, 256, 0, c->stream>>>(g.G, G, d ? d : G, s_old ? G : nullptr, s_old, c->scal + 5,
+                                                red(c));
+    }
+    CU(cudaGetLastError());
+    if (!d) CU(cudaMemsetAsync(c->scal + 5, 0, sizeof(double), c->stream));
+  }
   TRY(sync_scalars(c, c->scal, 12 * sizeof(double), out->sums));
   return OFDFT_OK;
 }
@@ -1923,6 +1938,8 @@ int ofdft_create(ofdft_ctx** out, int device, void* stream) {
   if (ms && atoi(ms) >= 1) c->mg_sweeps = atoi(ms);
   const char* cz = getenv("OFDFT_COOP_NZ");  // launch-shape experiments: z-chunks of the persistent CG grid
   c->coop_nz = cz ? atoi(cz) : 0;
+  const char* fsd = getenv("OFDFT_FUNC_SPLIT_DOTS");  // 1: G.d, G.s_old after the functional pass
+  if (fsd) c->func_split_dots = atoi(fsd) != 0;
   const char* mzs = getenv("OFDFT_MG_ZSTREAM");  // 1: level smoothing passes as z-streaming stencils
   if (mzs) c->mg_zstream = atoi(mzs) != 0;
   const char* mzn = getenv("OFDFT_MG_ZSTREAM_NODES");  // levels of at least this many nodes: z-streaming smoothing

@@ -93,6 +93,7 @@ struct ofdft_ctx {
   int mg_finest_smooth = 1;                    // damped-Jacobi smoothing on the finest multigrid level
   long long mg_fuse_below = -1;                // coarser multigrid levels of at most this many nodes: fused
   int mg_cluster = 0;                          // coarse levels on one thread-block cluster (mg_cluster_kernel)
+  int func_split_dots = 0;                     // G.d and G.s_old by a pass after the functional
   int mg_zstream = 0;                          // level smoothing passes as z-streaming radius-1 stencils
   long long mg_zstream_nodes = -1;             // ... on the levels of at least this many nodes (-1: none)
   // the b_J tables in V_BTAB belong to this geometry (atoms, charges, grid,
