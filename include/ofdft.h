@@ -171,7 +171,10 @@ void ofdft_default_params(ofdft_params* p);
  * with a conditional node), OFDFT_TMA=1 (FP32 z-streaming passes stage their
  * planes with tiled TMA copies where the tile allows it; results are identical),
  * OFDFT_PDL=1 (CG-loop kernels with programmatic dependent launch; results are
- * identical), OFDFT_TRACE=1 (one stderr line per evaluation). */
+ * identical), OFDFT_FUNC_SPLIT_DOTS=1 (G.d and G.s_old of an evaluation by a pass
+ * after the functional instead of inside it), OFDFT_MG_ZSTREAM_NODES (z-streaming
+ * smoothing on the levels of at least this many nodes), OFDFT_TRACE=1 (one stderr
+ * line per evaluation). */
 int ofdft_create(ofdft_ctx** ctx, int device, void* cuda_stream);
 int ofdft_destroy(ofdft_ctx* ctx);
 

@@ -561,3 +561,26 @@ def test_overlap_correction_general_form_matches_oracle(ctx):
     assert abs(E - Ec) / Ec < 0.05  # 2% at h = 0.25, falling at high order with h
     with pytest.raises(F.OfdftError):
         ctx.overlap_correction(g, 12, R, Z, 1.0, 7.0, 0.4, 1.8)  # 2 x 1.8 > 3.5 bohr: reference balls overlap
+
+
+# ------------------------------------ G.d and G.s_old after the functional --
+def test_split_functional_dots_solve_matches_oracle(ctx, dimer):
+    """With G.d and G.s_old formed by a pointwise pass after the functional
+    (OFDFT_FUNC_SPLIT_DOTS=1) the line searches and the Polak-Ribiere beta see
+    the same sums up to rounding: the dimer's ground state matches the oracle's
+    in FP64 (1e-8 Ha/atom) and in MIXED (1e-5 Ha/atom)."""
+    c, g = dimer
+    res, _u, phi, _b = _oracle_solve(c, g, 6)
+    Fo = O.forces(_ogrid(g), 3, c.R, c.Z, phi)
+    cs = _context(OFDFT_FUNC_SPLIT_DOTS=1)
+    try:
+        E, Fv, st = cs.solve(c.R, c.Z, c.h, _parity_params(6), grid=g)
+        assert st.converged
+        assert abs(E - res.E) / c.M <= 1e-8
+        assert np.abs(Fv - Fo).max() <= 1e-5
+        p = _parity_params(6, precision=F.PREC_MIXED, tol_poisson=1e-9, tol_inner=1e-9, tol_E=1e-8)
+        E, Fv, st = cs.solve(c.R, c.Z, c.h, p, grid=g)
+        assert st.converged
+        assert abs(E - res.E) / c.M <= 1e-5
+    finally:
+        cs.close()
