@@ -1126,7 +1126,10 @@ struct FuncScalars {
 template <typename T>
 struct EpiFunctional {
   static constexpr int K = 11;
-  static constexpr int NIN = 2;  // phi and b at the node, staged by the pipeline
+  // staged by the pipeline: phi and b at the node, and in FP32 also the search
+  // direction d (the third input ring still leaves two blocks per SM; with the
+  // pseudocharge's electrostatic sums taken from the residual pass b is not read)
+  static constexpr int NIN = sizeof(T) == 4 ? 3 : 2;
   using Acc = FAcc<T>;
   const T* phi;
   const T* b;
@@ -1162,7 +1165,8 @@ struct EpiFunctional {
   }
   __host__ __device__ __forceinline__ const T* input(int j) const {
     if (j == 0) return (f.terms & 8) ? phi : nullptr;
-    return (f.terms & 8) ? b : nullptr;
+    if (j == 1) return ((f.terms & 8) && !es_sums) ? b : nullptr;
+    return d;
   }
   __device__ __forceinline__ void apply(long long i, T uc, T lap, const T* vin, Acc* acc) const {
     const T mult = mult_;
@@ -1212,7 +1216,12 @@ struct EpiFunctional {
     // keeps FP32 relative accuracy; the sums of mixed-sign terms (line search,
     // Polak-Ribiere beta, the rank-one correction's u.s), whose totals can be
     // far smaller than their terms, stay compensated like the energy sums
-    if (d) acc[5].add(gx, d[i]);
+    if (d) {
+      if constexpr (NIN == 3)
+        acc[5].add(gx, vin[2]);
+      else
+        acc[5].add(gx, d[i]);
+    }
     if (s_old) acc[6].add(gx, s_old[i]);
     acc[7].add_fast(gx, -sx);  // g^2 / diag
     acc[8].add_fast(gx, gx);
