@@ -1003,7 +1003,7 @@ __device__ __forceinline__ float2 ff_prod(float a, float b) {  // a b exactly
 
 struct EpiResidualFF {
   static constexpr int K = 5;
-  static constexpr int NIN = 0;
+  static constexpr int NIN = 1;  // b at the node (float-float pairs), staged by the pipeline
   using Acc = DotAcc<float>;
   const float* rho;  // explicit density, or NULL for u^2 + b
   const float* u;
@@ -1016,8 +1016,8 @@ struct EpiResidualFF {
   float2 fourpi;
   __device__ __forceinline__ bool skip() const { return false; }
   __device__ __forceinline__ void load() {}
-  __host__ __device__ __forceinline__ const float2* input(int) const { return nullptr; }
-  __device__ __forceinline__ void apply(long long i, float2 ph, float2 lap_raw, const float2*, Acc* acc) const {
+  __host__ __device__ __forceinline__ const float2* input(int) const { return rho ? nullptr : b2; }
+  __device__ __forceinline__ void apply(long long i, float2 ph, float2 lap_raw, const float2* vin, Acc* acc) const {
     // the stencil's float-float sum comes unnormalised (lazy chain): renormalise
     const float2 lap = ff_two_sum(lap_raw.x, lap_raw.y);
     float2 rr;
@@ -1026,7 +1026,7 @@ struct EpiResidualFF {
     } else {
       const float ui = u[i];
       acc[0].add(ui, ui);
-      rr = ff_add(ff_prod(ui, ui), b2[i]);
+      rr = ff_add(ff_prod(ui, ui), vin[0]);
     }
     const float2 rh = ff_mul(fourpi, rr);
     const float2 r = ff_add(rh, lap);
